@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the NEP-SPIN spin-lattice step on GB300.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one full pass of the hot path over the 884,736-atom FeGe B20 workload
+(48^3 cells, ferromagnetic z with a 5 degree random cant, 300 K Langevin, dt 1 fs):
+integrator first half, conditional neighbour rebuild, descriptor, network,
+backward, force/field gather and spin corrector.  The timed region replays
+captured CUDA graphs; its working set (~10 GB) is far larger than L2, so no
+flush is needed between steps.
+
+Under torchrun (N > 1) every rank runs its own replica of the workload on its
+GPU (replicas only: the method has no data-path exchange between replicas);
+value = atoms x steps of all ranks / max over ranks of the timed region.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (a bounded
+sample of the same workload recipe per step) and prints the same kind of line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom-steps/s on 1 GB300, mixed vs FP64 at stated force error; p99 replica latency"
+UNIT = "atom-steps/s"
+WORKLOAD = "fege_b20_48c_884736"
+DT, TEMP, FIELD = 1.0, 300.0, (0.0, 0.0, 0.0)
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), max=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        load = [r for r in rows if r["power"] > 0.25 * max(x["power"] for x in rows)] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                              ("pcap", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return dict(sm_mhz=statistics.median(r["sm"] for r in load), sm_max_mhz=max(r["max"] for r in rows),
+                    power_w_max=max(r["power"] for r in rows), samples=len(rows), reasons=sorted(reasons))
+
+
+# ---------------------------------------------------------------- helpers
+def neighbour_counts(wl, sample=20000, seed=0):
+    """Mean in-cutoff neighbour counts (6 A, 4 A) on a sample of atoms."""
+    from scipy.spatial import cKDTree
+    pos = np.mod(wl.positions, wl.box)
+    tree = cKDTree(pos, boxsize=wl.box)
+    idx = np.random.default_rng(seed).choice(wl.n, min(sample, wl.n), replace=False)
+    nr = tree.query_ball_point(pos[idx], 6.0, return_length=True).mean() - 1.0
+    na = tree.query_ball_point(pos[idx], 4.0, return_length=True).mean() - 1.0
+    return float(nr), float(na)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2606_14073_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from profiles/traffic_<kernel>.txt, if that
+    capture was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{kernel}.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_sources_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p))
+    return None
+
+
+def oracle_rate(steps: int, warmup: int, cells: int, threads_note=True):
+    """Oracle MD steps on a cells^3 sample of the workload recipe; returns (atom-steps/s, atoms, seconds)."""
+    from oracle import oracle as O
+    from paper_2606_14073_gb300 import nep_params, workloads as W
+    p = nep_params.load()
+    m = O.Model(p)
+    wl = W.fege_cube(cells, T=TEMP, spin_mode="canted", seed=W.STRUCTURE_SEED0 + 2, n_steps=1)
+    st = O.State(wl.positions, wl.velocities, wl.spins, wl.species, wl.box, wl.periodic)
+    if warmup:
+        O.run(m, st, warmup, DT, TEMP, FIELD, seed=wl.seed)
+    else:
+        O.run(m, st, 0, DT, TEMP, FIELD, seed=wl.seed)   # initial forces outside the timed region
+    t0 = time.perf_counter()
+    O.run(m, st, steps, DT, TEMP, FIELD, seed=wl.seed)
+    dt = time.perf_counter() - t0
+    return wl.n * steps / dt, wl.n, dt
+
+
+def pick_oracle_cells(total_steps: int, budget_s: float):
+    """Largest cube whose total_steps oracle steps fit budget_s, from a quick calibration."""
+    rate, _, _ = oracle_rate(1, 0, 8)
+    atoms = rate * budget_s / max(total_steps, 1)
+    cells = int(round((atoms / 8.0) ** (1.0 / 3.0)))
+    return max(4, min(48, cells)), rate
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    cells, _ = pick_oracle_cells(args.steps + args.warmup, budget_s=150.0)
+    rate, atoms, secs = oracle_rate(args.steps, args.warmup, cells)
+    cores = O.num_threads()
+    sample = (f"{cells}^3 B20 cells = {atoms} atoms of the {WORKLOAD} recipe (same density, spins, 300 K), "
+              f"{args.steps} oracle MD steps timed after {args.warmup} warm-up steps")
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_atoms": atoms, "dt_fs": DT, "T_K": TEMP},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    from paper_2606_14073_gb300 import flops, nep_params, spinlat as S, workloads as W
+
+    rank, world, local = env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    params = nep_params.load()
+    wl = W.fege_884k()
+    replica = rank
+    stream = torch.cuda.Stream(device=local)
+    sysm = S.system_from_workload(wl, params, precision=S.SL_PREC_MIXED, replica=replica, stream=stream.cuda_stream,
+                                  device=local, steps_per_graph=args.graph_steps)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # force/field error of the mixed form against the FP64 GPU path on the same state
+    err = None
+    fp64 = None
+    if not args.skip_fp64:
+        sysd = S.system_from_workload(wl, params, precision=S.SL_PREC_FP64, replica=replica, device=local,
+                                      stream=stream.cuda_stream, steps_per_graph=args.graph_steps)
+        rm = sysm.energy_forces_fields(want_virial=False)
+        rd = sysd.energy_forces_fields(want_virial=False)
+        err = {"reference": "FP64 GPU path (itself within 1e-10 of the FP64 oracle)",
+               "force_rmse_eV_per_A": float(np.sqrt(((rm["F"] - rd["F"]) ** 2).mean())),
+               "field_rmse_eV": float(np.sqrt(((rm["H"] - rd["H"]) ** 2).mean())),
+               "energy_abs_err_eV_per_atom": abs(rm["E"] - rd["E"]) / wl.n,
+               "force_rms_eV_per_A": float(np.sqrt((rd["F"] ** 2).mean()))}
+        sysd.step(1, DT, TEMP, FIELD)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sysd.step(args.fp64_steps, DT, TEMP, FIELD)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        fp64 = {"value": wl.n * args.fp64_steps / (ms * 1e-3), "unit": UNIT, "steps": args.fp64_steps,
+                "ms_per_step": ms / args.fp64_steps}
+        sysd.destroy()
+        del sysd
+
+    # warm-up (graph capture happens here)
+    sysm.step(args.warmup, DT, TEMP, FIELD)
+    launches0 = sysm.info()["n_launches"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sysm.step(args.steps, DT, TEMP, FIELD)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = sysm.info()["n_launches"] - launches0
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = wl.n * args.steps * world / (ms_max * 1e-3)
+
+    # per-kernel device times (CUDA events between the kernel groups, same stream, no graphs)
+    prof = sysm.step_profiled(args.profile_steps, DT, TEMP, FIELD)
+    total = sum(prof.values())
+    n_r, n_a = neighbour_counts(W.fege_884k())
+    fl = flops.per_atom(n_r, n_a)
+    dom = max(("descriptor", "network", "backward"), key=lambda k: prof[k])
+    launch_ms = prof[dom] / args.profile_steps
+    achieved = fl[dom] * wl.n / (launch_ms * 1e-3) / 1e12
+    peak_derived = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    fma32, _ = S.sl_measure_fma_peak(S.SL_PREC_MIXED)
+    fma64, _ = S.sl_measure_fma_peak(S.SL_PREC_FP64)
+    roofline = {"bound": "alu", "kernel": {"descriptor": "k_fwd<float>", "network": "k_mlp<float>",
+                                           "backward": "k_bwd<float>"}[dom],
+                "achieved": achieved, "peak": peak_derived, "unit": "TFLOP/s", "frac": achieved / peak_derived,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FP32 FMA pipe)",
+                "peak_measured_fp32_fma_tflops": fma32 / 1e12, "peak_measured_fp64_fma_tflops": fma64 / 1e12,
+                "algorithmic_flop_per_atom": fl[dom], "mean_neighbours_6A": n_r, "mean_neighbours_4A": n_a,
+                "launch_ms": launch_ms, "traffic": committed_traffic(dom)}
+    shares = {k: v / total for k, v in prof.items()}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    st = sysm.get_state()
+    host = {k: torch.from_numpy(np.ascontiguousarray(st[k])).pin_memory().numpy()
+            for k in ("positions", "velocities", "spins", "forces", "fields")}
+    barrier()
+    t0 = time.perf_counter()
+    sysm.set_state(host["positions"], host["velocities"], host["spins"], host["forces"], host["fields"], st["step"])
+    sysm.step(args.steps, DT, TEMP, FIELD)
+    out = sysm.get_state()
+    t1 = time.perf_counter()
+    e2e_s = t1 - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = sum(host[k].nbytes for k in host)
+    d2h = sum(out[k].nbytes for k in ("positions", "velocities", "spins", "forces", "fields"))
+    e2e = {"value": wl.n * args.steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "path": "sl_set_state(host) + sl_step(K) + sl_get_state(host), wall clock"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
+        from oracle import oracle as O
+        cells, _ = pick_oracle_cells(2, budget_s=20.0)
+        rate, atoms, secs = oracle_rate(2, 0, cells)
+        cpu = {"value": rate, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+               "sample": f"2 oracle MD steps of a {cells}^3-cell ({atoms}-atom) block of the same recipe, {secs:.1f} s"}
+
+    sysm.destroy()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 descriptor/backward, f32 network, f64 state/integration",
+                "data": "synthetic (seeded FeGe B20, random-init NEP of the paper's shape)",
+                "config": {"workload": WORKLOAD, "atoms": wl.n, "precision": "mixed", "dt_fs": DT, "T_K": TEMP,
+                           "B_T": list(FIELD), "steps_per_graph": args.graph_steps,
+                           "l2": "inputs larger than L2 (~10 GB working set)", "parallelism": f"replicas x{world}"},
+                "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+                "kernel_share": shares, "kernel_ms_per_step": {k: v / args.profile_steps for k, v in prof.items()},
+                "fp64": fp64, "mixed_error_vs_fp64": err, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--graph-steps", type=int, default=10)
+    ap.add_argument("--profile-steps", type=int, default=10)
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,195 @@
+/*
+ * spinlat.h -- C ABI of the GB300 (sm_103a) NEP-SPIN spin-lattice step library.
+ *
+ * The library advances a coupled lattice + spin system under the spin-aware
+ * neuro-evolution potential of arXiv 2606.14073 and its spin-lattice integrator:
+ *   - create_system(positions, spins, box, species, nep_params)   (Section 5.2.1)
+ *   - step(n, dt, T, B)                                           (Sections 5.1.3, 5.2.1)
+ *   - energy_forces_fields()                                      (Sections 5.1.1, 5.1.2)
+ * Every step runs on the GPU: cell-list neighbour search, the 66-entry spin-aware
+ * descriptor, the per-atom tanh network, its backward pass to forces, spin fields
+ * and virial, and the integrator.  There is no CPU fallback; without a usable
+ * CUDA device every call returns SL_ECUDA.
+ *
+ * Conventions
+ *   units      A, fs, eV, amu, K, tesla; spins are unit vectors (one per atom).
+ *   arrays     row-major, caller atom order: positions[n][3], spins[n][3] ...
+ *   ownership  the caller owns every array it passes; the library copies inputs
+ *              in and copies outputs out in caller order before returning.
+ *              The library owns all device memory of a system.
+ *   threads    a system may be used from one host thread at a time.
+ *   errors     every int-returning call returns SL_OK (0) or a negative code;
+ *              sl_last_error() gives a message for the calling thread.  No C++
+ *              exception crosses the ABI.
+ */
+#ifndef SPINLAT_H
+#define SPINLAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SL_OK 0
+#define SL_EINVAL (-1)          /* bad argument (shape, size, box, parameter)      */
+#define SL_ENOMEM (-2)          /* device or host allocation failed                */
+#define SL_ENBR_OVERFLOW (-3)   /* a neighbour list outgrew its capacity           */
+#define SL_ENONFINITE (-4)      /* a force or field became NaN/Inf                 */
+#define SL_ETIMEOUT (-5)        /* a bounded device wait gave up                   */
+#define SL_ECUDA (-6)           /* CUDA runtime error or no usable device          */
+
+#define SL_PREC_FP64 0          /* everything in FP64                               */
+#define SL_PREC_MIXED 1         /* FP32 descriptors/backward, FP16 tensor-core MLP, */
+                                /* FP64 state, accumulation and renormalisation     */
+
+typedef struct sl_system sl_system;
+
+/* NEP-SPIN model.  Shapes supported by the kernels: n_species = 2, n_ch = 5,
+ * basis_k = 9 (basis size 8, Section 5.2.4), l_max = 4, n_hidden = 30, which gives
+ * the 66-entry descriptor of Section 5.2.3.  Layouts:
+ *   coeffs   [n_species][n_species][6][n_ch][basis_k]: [centre][neighbour species],
+ *            group order R, A, EX, DMI, ANI, SIA (structural radial, structural
+ *            angular, and the four pairwise magnetic sub-terms of Section 5.2.4)
+ *   q_scaler [66]; w0 [n_hidden][66]; b0 [n_hidden]; w1 [n_hidden]
+ *   descriptor order R(5), A(n,l)(20), O(1), EX(5), DMI(5), ANI(5), SIA(5), SA(n,l)(20)
+ * E_i = sum_h w1_h tanh(sum_v w0_hv q_scaler_v q_v - b0_h) - b1. */
+typedef struct {
+    int32_t n_species, n_ch, l_max, basis_k;
+    double rc_rad, rc_ang;           /* radial and angular cutoffs, A (rc_ang <= rc_rad) */
+    int32_t n_hidden;
+    const double *coeffs, *q_scaler, *w0, *b0, *w1;
+    double b1;
+    const double *mass_amu;          /* [n_species] */
+    const double *moment_muB;        /* [n_species] magnetic moment, Bohr magnetons */
+} sl_nep_params;
+
+typedef struct {
+    int32_t precision;               /* SL_PREC_FP64 or SL_PREC_MIXED                  */
+    uint64_t seed;                   /* Philox key word 0 (noise)                      */
+    uint64_t replica;                /* Philox key word 1 (independent replicas)       */
+    double skin;                     /* neighbour skin, A (rebuild at skin/2 motion)  */
+    double gamma_lattice_per_fs;     /* lattice Langevin friction                      */
+    double lambda_spin;              /* Gilbert damping of the stochastic spin update  */
+    int32_t midpoint_iters;          /* must be 0 (self-consistent midpoint: not built) */
+    int32_t nbr_cap_rad;             /* radial list capacity (candidates within rc_rad+skin) */
+    int32_t nbr_cap_ang;             /* angular list capacity (within rc_ang+skin)      */
+    int32_t steps_per_graph;         /* steps captured in one CUDA graph (0: no graphs) */
+    void *cuda_stream;               /* cudaStream_t to run on; NULL: a library stream  */
+    int32_t device;                  /* CUDA device ordinal; -1: the calling thread's current device */
+} sl_options;
+
+/* Fill *opt with the defaults: FP64, seed 1234, replica 0, skin 1 A, gamma 0.01/fs,
+ * lambda 0.1, caps 160/64, 10 steps per graph, library stream, current device. */
+void sl_default_options(sl_options *opt);
+
+/* Create a system of n atoms on the current CUDA device.
+ *   positions [n][3] A (wrapped into the box along periodic dims on entry)
+ *   spins     [n][3] (normalised on entry)
+ *   box[3]    orthorhombic lengths, A; along a periodic dim it must be at least
+ *             2 (rc_rad + skin); along a free dim it is the binning extent
+ *   periodic[3] 0/1;  species [n] in [0, n_species)
+ *   velocities [n][3] A/fs, or NULL for zero
+ * Forces and fields of the initial state are evaluated before returning.
+ * Returns SL_OK and *out, or an error (nothing allocated on error). */
+int sl_create_system(const double *positions, const double *spins, const double box[3],
+                     const int32_t periodic[3], const int32_t *species, int64_t n,
+                     const double *velocities, const sl_nep_params *params,
+                     const sl_options *opt, sl_system **out);
+
+/* Advance n_steps steps of dt fs at temperature T_K and field B_tesla[3]
+ * (Section 5.1.3 ordering: lattice update first, spin update last).  One step:
+ *   v += dt/2 F/m; r += dt/2 v; Langevin O-step on v; r += dt/2 v;
+ *   spin predictor S' = Rot(S, omega(S, H + eta) dt);  F', H' at (r, S');
+ *   corrector S = Rot(S, (omega(S, H + eta) + omega(S', H' + eta)) dt/2), renormalised;
+ *   v += dt/2 F'/m;  (F, H) = (F', H').
+ * omega(S, X) = (X + lambda S x X) / ((1 + lambda^2) hbar), eta the thermal field.
+ * On SL_ENBR_OVERFLOW or SL_ENONFINITE the state is restored to that at entry. */
+int sl_step(sl_system *sys, int64_t n_steps, double dt_fs, double T_K, const double B_tesla[3]);
+
+/* Evaluate the potential at the current (positions, spins) with the field of the
+ * last sl_step (zero before any step).  energy_eV: E = sum_i E_i - sum_i mu_i muB B.S_i;
+ * forces [n][3] eV/A; fields [n][3] eV = -dE/dS_i (Zeeman included); virial [9] eV
+ * (W_ab = -sum_i sum_j (r_ij)_a dE_i/d(r_ij)_b).  Any output may be NULL.
+ * Does not change the dynamical state. */
+int sl_energy_forces_fields(sl_system *sys, double *energy_eV, double *forces, double *fields,
+                            double *virial);
+
+/* Per-atom descriptors q [n][66] (unscaled) and network energies E_i [n], caller
+ * order; either may be NULL.  Evaluated at the current state. */
+int sl_get_descriptors(sl_system *sys, double *q, double *atom_energy);
+
+/* Copy the state out (any pointer may be NULL).  forces/fields are the carried
+ * values of the integrator (evaluated at the last predicted spins). */
+int sl_get_state(const sl_system *sys, double *positions, double *velocities, double *spins,
+                 double *forces, double *fields, uint64_t *step);
+
+/* Replace the state.  positions/velocities/spins may not be NULL.  If forces and
+ * fields are both given they become the carried integrator values (bit-identical
+ * resume); if both are NULL they are re-evaluated at the new state. */
+int sl_set_state(sl_system *sys, const double *positions, const double *velocities,
+                 const double *spins, const double *forces, const double *fields, uint64_t step);
+
+/* Neighbour candidate lists of the current build, caller indices, ascending:
+ * counts_rad[n], lists_rad[n][cap] (d2 < (rc_rad+skin)^2) and counts_ang[n],
+ * lists_ang[n][cap] (d2 < (rc_ang+skin)^2).  Rebuilds the lists first. */
+int sl_get_neighbors(sl_system *sys, int32_t cap, int32_t *counts_rad, int32_t *lists_rad,
+                     int32_t *counts_ang, int32_t *lists_ang);
+
+/* Number of atoms, precision mode, neighbour-list builds so far (device-triggered
+ * rebuilds included) and kernels launched by sl_step/sl_step_profiled so far. */
+int sl_get_info(const sl_system *sys, int64_t *n_atoms, int32_t *precision, int64_t *n_builds,
+                int64_t *n_launches);
+
+/* Kernel groups timed by sl_step_profiled, in step order. */
+#define SL_K_FIRST_HALF 0    /* kicks, drifts, Langevin, spin predictor, rebuild test */
+#define SL_K_REBUILD 1       /* binning + lists + reverse slots (early exit when not due) */
+#define SL_K_DESCRIPTOR 2    /* descriptor forward (k_fwd)                               */
+#define SL_K_NETWORK 3       /* per-atom network and its input gradient (k_mlp / tensor core) */
+#define SL_K_BACKWARD 4      /* backward to per-pair derivatives (k_bwd)                 */
+#define SL_K_SECOND_HALF 5   /* force/field gather, spin corrector, final kick          */
+#define SL_NKERNELS 6
+
+/* Same as sl_step but without CUDA graphs and with CUDA events recorded on the
+ * system's stream between the kernel groups; kernel_ms[SL_NKERNELS] receives the
+ * summed device time of each group over the n_steps steps. */
+int sl_step_profiled(sl_system *sys, int64_t n_steps, double dt_fs, double T_K, const double B_tesla[3],
+                     double *kernel_ms);
+
+/* FMA throughput of the current device in FLOP/s (an FMA counts 2), measured with
+ * dependent-chain FMA kernels on every SM: precision SL_PREC_FP64 (FP64 pipe) or
+ * SL_PREC_MIXED (FP32 pipe).  Used as the ALU roofline of the descriptor kernels. */
+int sl_measure_fma_peak(int32_t precision, double *flops_per_s, double *elapsed_ms);
+
+/* Stream the system's work is ordered on (a cudaStream_t). */
+void *sl_get_stream(const sl_system *sys);
+
+void sl_destroy_system(sl_system *sys);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *sl_last_error(void);
+
+/* ---------------------------------------------------------------- batches
+ * Independent replicas (temperature/field sweeps) stepped together: one launch of
+ * each kernel covers every replica's atoms.  All systems of a batch must share the
+ * precision mode and the model parameters.  Replicas keep their own state, RNG key
+ * and neighbour lists; a replica's trajectory is bit-identical alone and in a batch. */
+typedef struct sl_batch sl_batch;
+
+int sl_batch_create(sl_system *const *systems, int32_t k, sl_batch **out);
+/* n_steps[k]: steps each replica still takes in this call (0 = idle this call);
+ * dt/T/B per replica. */
+int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt_fs, const double *T_K,
+                  const double *B_tesla /* [k][3] */);
+void sl_batch_destroy(sl_batch *b);
+
+/* ---------------------------------------------------------------- self checks
+ * Host-only checks of the kernels' compile-time tables (no GPU needed):
+ * max |P_l(u.v) - sum_m kappa_lm p_lm(u) p_lm(v)| and the max finite-difference
+ * error of the harmonic gradients over n_samples random unit vectors. */
+int sl_selftest_harmonics(int32_t n_samples, double *max_addition_err, double *max_gradient_err);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPINLAT_H */

@@ -1,0 +1,816 @@
+// sl_api.cu -- C ABI of the NEP-SPIN spin-lattice library (declared in include/spinlat.h).
+//
+// create_system / step / energy_forces_fields follow the problem statement of
+// arXiv 2606.14073 (Section 5.2.1: one unified energy E(R,S) giving forces and
+// spin driving terms, advanced by the spin-lattice integrator).  All arrays
+// crossing the ABI are host arrays in caller atom order; internally atoms are
+// stored species-major and in Morton order of 7 A cells for locality.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/spinlat.h"
+#include "sl_internal.h"
+
+struct sl_system {
+    sl::Sys s;
+};
+
+struct sl_batch {
+    std::vector<sl_system *> sys;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(SL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+    } while (0)
+
+template <typename T>
+int dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SL_ENOMEM, "cudaMalloc of %zu bytes failed: %s", sizeof(T) * count, cudaGetErrorString(e));
+    }
+    return SL_OK;
+}
+
+uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+    auto spread = [](uint64_t v) {
+        v &= 0x1fffff;
+        v = (v | v << 32) & 0x1f00000000ffffULL;
+        v = (v | v << 16) & 0x1f0000ff0000ffULL;
+        v = (v | v << 8) & 0x100f00f00f00f00fULL;
+        v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+        v = (v | v << 2) & 0x1249249249249249ULL;
+        return v;
+    };
+    return spread(x) | spread(y) << 1 | spread(z) << 2;
+}
+
+template <typename R>
+void fill_params(sl::NepDev<R> &P, const sl_nep_params *p) {
+    using namespace sl;
+    for (int a = 0; a < NS; ++a)
+        for (int b = 0; b < NS; ++b)
+            for (int g = 0; g < 6; ++g)
+                for (int n = 0; n < NCH; ++n)
+                    for (int k = 0; k < NK; ++k)
+                        P.c[a][b][g][n][k] = (R)p->coeffs[((((a * NS) + b) * 6 + g) * NCH + n) * NK + k];
+    for (int v = 0; v < DIM; ++v) P.scal[v] = (R)p->q_scaler[v];
+    for (int h = 0; h < NH; ++h) {
+        for (int v = 0; v < DIM; ++v) P.w0[h][v] = (R)p->w0[h * DIM + v];
+        P.b0[h] = (R)p->b0[h];
+        P.w1[h] = (R)p->w1[h];
+    }
+    P.b1 = (R)p->b1;
+    P.rc_r = (R)p->rc_rad;
+    P.rc_a = (R)p->rc_ang;
+    P.inv_rc_r = (R)(1.0 / p->rc_rad);
+    P.inv_rc_a = (R)(1.0 / p->rc_ang);
+    P.rc_r2 = (R)(p->rc_rad * p->rc_rad);
+    P.rc_a2 = (R)(p->rc_ang * p->rc_ang);
+}
+
+void free_sys(sl::Sys &s) {
+    void *ptrs[] = {s.pos, s.vel, s.spin, s.spin_prev, s.F, s.H, s.posref, s.posf, s.spinf, s.species, s.orig,
+                    s.inv, s.nbr, s.rev, s.seg, s.cells.count, s.cells.start, s.cells.fill, s.cells.atoms,
+                    s.cells.of, s.q, s.bsum, s.fp, s.ei, s.pd0, s.pd1, s.fown, s.gii, s.wpart, s.Fo, s.Ho,
+                    s.status, s.rebuild, s.d_step, s.d_par, s.red, s.snap, s.d_builds};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (s.h_par) cudaFreeHost(s.h_par);
+    if (s.h_status) cudaFreeHost(s.h_status);
+    if (s.h_red) cudaFreeHost(s.h_red);
+    if (s.graph) cudaGraphExecDestroy(s.graph);
+    if (s.own_stream && s.stream) cudaStreamDestroy(s.stream);
+}
+
+void compute_step_params(const sl::Sys &s, double dt, double T, const double B[3], sl::StepDev &P) {
+    using namespace sl;
+    P.dt = dt;
+    P.half_dt = 0.5 * dt;
+    P.c_fric = std::exp(-s.gamma * dt);
+    for (int t = 0; t < NS; ++t) {
+        P.acc_m[t] = ACC / s.mass[t];
+        P.sig_v[t] = T > 0 ? std::sqrt((1.0 - P.c_fric * P.c_fric) * KB * T * ACC / s.mass[t]) : 0.0;
+        for (int c = 0; c < 3; ++c) P.zee[t][c] = s.moment[t] * MUB * B[c];
+    }
+    P.sig_eta = (T > 0 && s.lambda > 0 && dt > 0) ? std::sqrt(2.0 * s.lambda * KB * T * HBAR / dt) : 0.0;
+    P.lambda = s.lambda;
+    P.wscale = 1.0 / ((1.0 + s.lambda * s.lambda) * HBAR);
+    P.disp2 = 0.25 * s.skin * s.skin;
+}
+
+int upload_params(sl::Sys &s, double dt, double T, const double B[3]) {
+    // the pinned host block may still be read by an earlier copy in flight
+    CK(cudaStreamSynchronize(s.stream));
+    compute_step_params(s, dt, T, B, *s.h_par);
+    CK(cudaMemcpyAsync(s.d_par, s.h_par, sizeof(sl::StepDev), cudaMemcpyHostToDevice, s.stream));
+    return SL_OK;
+}
+
+void enqueue_step(sl::Sys &s) {
+    sl::launch_first_half(s);
+    sl::launch_rebuild(s, true);
+    sl::launch_eval(s, false);
+    sl::launch_second_half(s);
+}
+
+// Evaluate at the current state: optional unconditional rebuild, eval, gather.
+int evaluate(sl::Sys &s, bool rebuild, bool carried, bool want_virial) {
+    if (s.n == 0) return SL_OK;
+    if (rebuild) {
+        sl::launch_rebuild(s, false);
+        s.n_builds++;
+    }
+    sl::launch_eval(s, want_virial);
+    sl::launch_gather(s, carried);
+    CK(cudaGetLastError());
+    return SL_OK;
+}
+
+int check_status(sl::Sys &s) {
+    CK(cudaMemcpyAsync(s.h_status, s.status, sizeof(int), cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaStreamSynchronize(s.stream));
+    const int st = *s.h_status;
+    if (st & sl::ST_NBR_OVERFLOW)
+        return fail(SL_ENBR_OVERFLOW, "neighbour list capacity exceeded (caps %d/%d)", s.cap, s.cap_ang);
+    if (st & sl::ST_NONFINITE) return fail(SL_ENONFINITE, "non-finite force or field");
+    return SL_OK;
+}
+
+// host (caller order) -> device (internal order)
+int upload_vec(sl::Sys &s, double4 *dst, const double *src, bool normalise) {
+    std::vector<double4> h((size_t)s.n);
+    std::vector<int32_t> orig((size_t)s.n);
+    CK(cudaMemcpy(orig.data(), s.orig, sizeof(int32_t) * s.n, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < s.n; ++i) {
+        const double *p = src + 3 * (int64_t)orig[i];
+        double x = p[0], y = p[1], z = p[2];
+        if (normalise) {
+            const double nn = std::sqrt(x * x + y * y + z * z);
+            if (!(nn > 0)) return fail(SL_EINVAL, "zero spin vector");
+            x /= nn; y /= nn; z /= nn;
+        }
+        h[i] = make_double4(x, y, z, 0.0);
+    }
+    CK(cudaMemcpy(dst, h.data(), sizeof(double4) * s.n, cudaMemcpyHostToDevice));
+    return SL_OK;
+}
+
+int download_vec(const sl::Sys &s, const double4 *src, double *dst) {
+    std::vector<double4> h((size_t)s.n);
+    std::vector<int32_t> orig((size_t)s.n);
+    CK(cudaMemcpyAsync(h.data(), src, sizeof(double4) * s.n, cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaMemcpyAsync(orig.data(), s.orig, sizeof(int32_t) * s.n, cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaStreamSynchronize(s.stream));
+    for (int64_t i = 0; i < s.n; ++i) {
+        double *p = dst + 3 * (int64_t)orig[i];
+        p[0] = h[i].x; p[1] = h[i].y; p[2] = h[i].z;
+    }
+    return SL_OK;
+}
+
+__global__ void k_wrap_and_copy(double4 *pos, float4 *posf, const double4 *spin, float4 *spinf, int64_t n,
+                                sl::BoxDev<double> b, int px, int py, int pz) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double4 r = pos[i];
+    if (px) r.x = r.x - b.L[0] * floor(r.x / b.L[0]);
+    if (py) r.y = r.y - b.L[1] * floor(r.y / b.L[1]);
+    if (pz) r.z = r.z - b.L[2] * floor(r.z / b.L[2]);
+    pos[i] = r;
+    posf[i] = make_float4((float)r.x, (float)r.y, (float)r.z, 0.f);
+    const double4 S = spin[i];
+    spinf[i] = make_float4((float)S.x, (float)S.y, (float)S.z, 0.f);
+}
+
+int refresh_copies(sl::Sys &s) {
+    if (s.n == 0) return SL_OK;
+    k_wrap_and_copy<<<(unsigned)((s.n + 255) / 256), 256, 0, s.stream>>>(s.pos, s.posf, s.spin, s.spinf, s.n, s.boxd,
+                                                                         s.per[0], s.per[1], s.per[2]);
+    CK(cudaGetLastError());
+    return SL_OK;
+}
+
+int capture_graph(sl::Sys &s, int k) {
+    if (s.graph) {
+        cudaGraphExecDestroy(s.graph);
+        s.graph = nullptr;
+    }
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
+    for (int t = 0; t < k; ++t) enqueue_step(s);
+    cudaError_t e = cudaStreamEndCapture(s.stream, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    e = cudaGraphInstantiate(&s.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    s.graph_steps = k;
+    return SL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sl_default_options(sl_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = SL_PREC_FP64;
+    o->seed = 1234;
+    o->replica = 0;
+    o->skin = 1.0;
+    o->gamma_lattice_per_fs = 0.01;
+    o->lambda_spin = 0.1;
+    o->midpoint_iters = 0;
+    o->nbr_cap_rad = 160;
+    o->nbr_cap_ang = 64;
+    o->steps_per_graph = 10;
+    o->cuda_stream = nullptr;
+    o->device = -1;
+}
+
+const char *sl_last_error(void) { return g_err.c_str(); }
+
+int sl_create_system(const double *positions, const double *spins, const double box[3], const int32_t periodic[3],
+                     const int32_t *species, int64_t n, const double *velocities, const sl_nep_params *params,
+                     const sl_options *opt_in, sl_system **out) {
+    using namespace sl;
+    if (!out) return fail(SL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!params || !box || !periodic) return fail(SL_EINVAL, "params, box and periodic are required");
+    if (n < 0 || n > 0x7fffffffLL) return fail(SL_EINVAL, "n = %lld out of range", (long long)n);
+    if (n > 0 && (!positions || !spins || !species)) return fail(SL_EINVAL, "positions, spins, species required");
+    if (params->n_species != NS || params->n_ch != NCH || params->l_max != 4 || params->basis_k != NK ||
+        params->n_hidden != NH)
+        return fail(SL_EINVAL, "model shape (%d species, %d channels, l_max %d, %d terms, %d hidden) not supported; "
+                               "kernels are built for (2, 5, 4, 9, 30)",
+                    params->n_species, params->n_ch, params->l_max, params->basis_k, params->n_hidden);
+    if (!(params->rc_ang > 0 && params->rc_rad >= params->rc_ang))
+        return fail(SL_EINVAL, "cutoffs must satisfy 0 < rc_ang <= rc_rad");
+    if (!params->coeffs || !params->q_scaler || !params->w0 || !params->b0 || !params->w1 || !params->mass_amu ||
+        !params->moment_muB)
+        return fail(SL_EINVAL, "missing parameter array");
+    sl_options opt;
+    if (opt_in) opt = *opt_in;
+    else sl_default_options(&opt);
+    if (opt.precision != SL_PREC_FP64 && opt.precision != SL_PREC_MIXED) return fail(SL_EINVAL, "bad precision");
+    if (!(opt.skin > 0)) return fail(SL_EINVAL, "skin must be positive");
+    if (opt.midpoint_iters != 0) return fail(SL_EINVAL, "midpoint_iters > 0 is not supported");
+    if (opt.nbr_cap_rad < 1 || opt.nbr_cap_rad > 256 || opt.nbr_cap_ang < 1 || opt.nbr_cap_ang > opt.nbr_cap_rad)
+        return fail(SL_EINVAL, "neighbour caps must satisfy 1 <= cap_ang <= cap_rad <= 256");
+    if (opt.gamma_lattice_per_fs < 0 || opt.lambda_spin < 0) return fail(SL_EINVAL, "negative damping");
+    for (int a = 0; a < 3; ++a) {
+        if (!(box[a] > 0)) return fail(SL_EINVAL, "box lengths must be positive");
+        if (periodic[a] && box[a] < 2.0 * (params->rc_rad + opt.skin))
+            return fail(SL_EINVAL, "periodic box length %g below 2 (rc_rad + skin) = %g", box[a],
+                        2.0 * (params->rc_rad + opt.skin));
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (species[i] < 0 || species[i] >= NS) return fail(SL_EINVAL, "species[%lld] out of range", (long long)i);
+    for (int t = 0; t < NS; ++t)
+        if (!(params->mass_amu[t] > 0)) return fail(SL_EINVAL, "masses must be positive");
+
+    int dev_count = 0;
+    cudaError_t ce = cudaGetDeviceCount(&dev_count);
+    if (ce != cudaSuccess || dev_count < 1) {
+        cudaGetLastError();
+        return fail(SL_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(ce));
+    }
+
+    if (opt.device >= dev_count) return fail(SL_EINVAL, "device %d not present (%d devices)", opt.device, dev_count);
+    if (opt.device >= 0 && (ce = cudaSetDevice(opt.device)) != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
+    sl_system *sys = new (std::nothrow) sl_system();
+    if (!sys) return fail(SL_ENOMEM, "host allocation failed");
+    Sys &s = sys->s;
+    cudaGetDevice(&s.device);
+    s.n = n;
+    s.prec = opt.precision;
+    s.seed = opt.seed;
+    s.replica = opt.replica;
+    s.skin = opt.skin;
+    s.gamma = opt.gamma_lattice_per_fs;
+    s.lambda = opt.lambda_spin;
+    s.cap = opt.nbr_cap_rad;
+    s.cap_ang = opt.nbr_cap_ang;
+    s.steps_per_graph = opt.steps_per_graph < 0 ? 0 : opt.steps_per_graph;
+    fill_params(s.pd, params);
+    fill_params(s.pf, params);
+    for (int t = 0; t < NS; ++t) {
+        s.mass[t] = params->mass_amu[t];
+        s.moment[t] = params->moment_muB[t];
+    }
+    for (int a = 0; a < 3; ++a) {
+        s.box[a] = box[a];
+        s.per[a] = periodic[a] ? 1 : 0;
+        s.boxd.L[a] = box[a];
+        s.boxd.invL[a] = s.per[a] ? 1.0 / box[a] : 0.0;
+        s.boxf.L[a] = (float)box[a];
+        s.boxf.invL[a] = s.per[a] ? (float)(1.0 / box[a]) : 0.f;
+    }
+    s.cut_r2 = (params->rc_rad + s.skin) * (params->rc_rad + s.skin);
+    s.cut_a2 = (params->rc_ang + s.skin) * (params->rc_ang + s.skin);
+    nbr_setup(s);
+    eval_init();
+
+    int rc = SL_OK;
+    auto bail = [&](int code) {
+        free_sys(s);
+        delete sys;
+        return code;
+    };
+    if (opt.cuda_stream) s.stream = (cudaStream_t)opt.cuda_stream;
+    else {
+        ce = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreate"));
+        s.own_stream = true;
+    }
+
+    // internal order: species-major, then Morton order of the binning cells, then caller index
+    std::vector<int32_t> order((size_t)n);
+    {
+        std::vector<uint64_t> key((size_t)n);
+        for (int64_t i = 0; i < n; ++i) {
+            uint32_t c[3];
+            for (int a = 0; a < 3; ++a) {
+                double x = positions[3 * i + a];
+                if (s.per[a]) x = x - box[a] * std::floor(x / box[a]);
+                const double w = box[a] / s.cells.nc[a];
+                long ci = (long)std::floor(x / w);
+                ci = std::min<long>(std::max<long>(ci, 0), s.cells.nc[a] - 1);
+                c[a] = (uint32_t)ci;
+            }
+            key[i] = ((uint64_t)species[i] << 62) | morton3(c[0], c[1], c[2]);
+            order[i] = (int32_t)i;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    }
+    std::vector<int32_t> inv((size_t)n), spec((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        inv[order[i]] = (int32_t)i;
+        spec[i] = species[order[i]];
+    }
+    s.n_fe = 0;
+    for (int64_t i = 0; i < n; ++i) s.n_fe += spec[i] == 0;
+
+    const size_t N = (size_t)n;
+    const size_t R = s.prec == SL_PREC_FP64 ? 8 : 4;
+    if ((rc = dalloc(&s.pos, N)) || (rc = dalloc(&s.vel, N)) || (rc = dalloc(&s.spin, N)) ||
+        (rc = dalloc(&s.spin_prev, N)) || (rc = dalloc(&s.F, N)) || (rc = dalloc(&s.H, N)) ||
+        (rc = dalloc(&s.posref, N)) || (rc = dalloc(&s.posf, N)) || (rc = dalloc(&s.spinf, N)) ||
+        (rc = dalloc(&s.species, N)) || (rc = dalloc(&s.orig, N)) || (rc = dalloc(&s.inv, N)) ||
+        (rc = dalloc(&s.nbr, N * s.cap)) || (rc = dalloc(&s.rev, N * s.cap)) || (rc = dalloc(&s.seg, N)) ||
+        (rc = dalloc(&s.cells.count, (size_t)s.cells.ncell)) || (rc = dalloc(&s.cells.start, (size_t)s.cells.ncell + 1)) ||
+        (rc = dalloc(&s.cells.fill, (size_t)s.cells.ncell)) || (rc = dalloc(&s.cells.atoms, N)) ||
+        (rc = dalloc(&s.cells.of, N)) || (rc = dalloc((char **)&s.q, R * DIM * N)) ||
+        (rc = dalloc((char **)&s.bsum, R * NB * N)) || (rc = dalloc((char **)&s.fp, R * DIM * N)) ||
+        (rc = dalloc((char **)&s.ei, R * N)) || (rc = dalloc((char **)&s.pd0, R * 4 * N * s.cap)) ||
+        (rc = dalloc((char **)&s.pd1, R * 2 * N * s.cap)) || (rc = dalloc((char **)&s.fown, R * 4 * N)) ||
+        (rc = dalloc((char **)&s.gii, R * 4 * N)) || (rc = dalloc((char **)&s.wpart, R * 9 * N)) ||
+        (rc = dalloc(&s.Fo, N)) || (rc = dalloc(&s.Ho, N)) || (rc = dalloc(&s.status, 1)) ||
+        (rc = dalloc(&s.rebuild, 1)) || (rc = dalloc(&s.d_step, 2)) || (rc = dalloc(&s.d_par, 1)) ||
+        (rc = dalloc(&s.red, 256 * 10 + 10)) || (rc = dalloc(&s.snap, 5 * N)) || (rc = dalloc(&s.d_builds, 1)))
+        return bail(rc);
+    if ((ce = cudaMallocHost((void **)&s.h_par, sizeof(StepDev))) != cudaSuccess ||
+        (ce = cudaMallocHost((void **)&s.h_status, sizeof(int))) != cudaSuccess ||
+        (ce = cudaMallocHost((void **)&s.h_red, sizeof(double) * 10)) != cudaSuccess)
+        return bail(fail(SL_ENOMEM, "pinned allocation failed: %s", cudaGetErrorString(ce)));
+
+    // upload (internal order)
+    {
+        std::vector<double4> hp(N), hv(N), hs(N);
+        for (size_t i = 0; i < N; ++i) {
+            const int64_t c = order[i];
+            hp[i] = make_double4(positions[3 * c], positions[3 * c + 1], positions[3 * c + 2], 0.0);
+            const double sx = spins[3 * c], sy = spins[3 * c + 1], sz = spins[3 * c + 2];
+            const double nn = std::sqrt(sx * sx + sy * sy + sz * sz);
+            if (!(nn > 0) || !std::isfinite(nn)) return bail(fail(SL_EINVAL, "spin %lld is zero or non-finite", (long long)c));
+            hs[i] = make_double4(sx / nn, sy / nn, sz / nn, 0.0);
+            hv[i] = velocities ? make_double4(velocities[3 * c], velocities[3 * c + 1], velocities[3 * c + 2], 0.0)
+                               : make_double4(0, 0, 0, 0);
+            for (int a = 0; a < 3; ++a)
+                if (!std::isfinite(positions[3 * c + a])) return bail(fail(SL_EINVAL, "non-finite position"));
+        }
+        if ((ce = cudaMemcpy(s.pos, hp.data(), sizeof(double4) * N, cudaMemcpyHostToDevice)) ||
+            (ce = cudaMemcpy(s.vel, hv.data(), sizeof(double4) * N, cudaMemcpyHostToDevice)) ||
+            (ce = cudaMemcpy(s.spin, hs.data(), sizeof(double4) * N, cudaMemcpyHostToDevice)) ||
+            (ce = cudaMemcpy(s.species, spec.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice)) ||
+            (ce = cudaMemcpy(s.orig, order.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice)) ||
+            (ce = cudaMemcpy(s.inv, inv.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice)) ||
+            (ce = cudaMemset(s.cells.count, 0, sizeof(int) * s.cells.ncell)) ||
+            (ce = cudaMemset(s.cells.fill, 0, sizeof(int) * s.cells.ncell)) ||
+            (ce = cudaMemset(s.status, 0, sizeof(int))) || (ce = cudaMemset(s.rebuild, 0, sizeof(int))) ||
+            (ce = cudaMemset(s.d_step, 0, 2 * sizeof(unsigned long long))) ||
+            (ce = cudaMemset(s.d_builds, 0, sizeof(unsigned long long))))
+            return bail(cuda_fail(ce, "upload"));
+    }
+    const double B0[3] = {0, 0, 0};
+    if ((rc = upload_params(s, 1.0, 0.0, B0)) || (rc = refresh_copies(s)) || (rc = evaluate(s, true, true, false)) ||
+        (rc = check_status(s)))
+        return bail(rc);
+    *out = sys;
+    return SL_OK;
+}
+
+int sl_step(sl_system *sys, int64_t n_steps, double dt, double T, const double B[3]) {
+    if (!sys || !B) return fail(SL_EINVAL, "NULL argument");
+    if (n_steps < 0 || !(dt > 0) || !(T >= 0) || !std::isfinite(dt) || !std::isfinite(T))
+        return fail(SL_EINVAL, "bad step arguments");
+    sl::Sys &s = sys->s;
+    cudaSetDevice(s.device);
+    int rc;
+    if ((rc = upload_params(s, dt, T, B))) return rc;
+    for (int c = 0; c < 3; ++c) s.B[c] = B[c];
+    if (n_steps == 0 || s.n == 0) {
+        s.step += (uint64_t)n_steps;
+        return SL_OK;
+    }
+    const size_t N = (size_t)s.n;
+    CK(cudaMemcpyAsync(s.snap, s.pos, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+    CK(cudaMemcpyAsync(s.snap + N, s.vel, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+    CK(cudaMemcpyAsync(s.snap + 2 * N, s.spin, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+    CK(cudaMemcpyAsync(s.snap + 3 * N, s.F, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+    CK(cudaMemcpyAsync(s.snap + 4 * N, s.H, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+    CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
+    int64_t left = n_steps;
+    const int k = s.steps_per_graph;
+    if (k > 0 && left >= k) {
+        if (!s.graph || s.graph_steps != k)
+            if ((rc = capture_graph(s, k))) return rc;
+        while (left >= k) {
+            CK(cudaGraphLaunch(s.graph, s.stream));
+            left -= k;
+        }
+    }
+    for (; left > 0; --left) enqueue_step(s);
+    CK(cudaGetLastError());
+    s.n_launches += n_steps * sl::KERNELS_PER_STEP;
+    rc = check_status(s);
+    if (rc == SL_ENBR_OVERFLOW || rc == SL_ENONFINITE) {
+        std::string msg = g_err;
+        CK(cudaMemcpyAsync(s.pos, s.snap, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+        CK(cudaMemcpyAsync(s.vel, s.snap + N, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+        CK(cudaMemcpyAsync(s.spin, s.snap + 2 * N, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+        CK(cudaMemcpyAsync(s.F, s.snap + 3 * N, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+        CK(cudaMemcpyAsync(s.H, s.snap + 4 * N, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+        unsigned long long st[2] = {s.step, s.step};
+        CK(cudaMemcpyAsync(s.d_step, st, sizeof st, cudaMemcpyHostToDevice, s.stream));
+        CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
+        int r2;
+        if ((r2 = refresh_copies(s))) return r2;
+        sl::launch_rebuild(s, false);
+        CK(cudaStreamSynchronize(s.stream));
+        return fail(rc, "%s; state restored to step %llu", msg.c_str(), (unsigned long long)s.step);
+    }
+    if (rc) return rc;
+    s.step += (uint64_t)n_steps;
+    return SL_OK;
+}
+
+int sl_energy_forces_fields(sl_system *sys, double *energy, double *forces, double *fields, double *virial) {
+    if (!sys) return fail(SL_EINVAL, "NULL system");
+    sl::Sys &s = sys->s;
+    cudaSetDevice(s.device);
+    if (s.n == 0) {
+        if (energy) *energy = 0.0;
+        if (virial) std::memset(virial, 0, 9 * sizeof(double));
+        return SL_OK;
+    }
+    int rc;
+    CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
+    if ((rc = evaluate(s, false, false, virial != nullptr))) return rc;
+    if ((rc = check_status(s))) return rc;
+    double E, W[9];
+    if (sl::reduce_energy_virial(s, &E, W, virial != nullptr)) return fail(SL_ECUDA, "reduction failed");
+    if (energy) *energy = E;
+    if (virial) std::memcpy(virial, W, sizeof W);
+    if (forces && (rc = download_vec(s, s.Fo, forces))) return rc;
+    if (fields && (rc = download_vec(s, s.Ho, fields))) return rc;
+    return SL_OK;
+}
+
+int sl_get_descriptors(sl_system *sys, double *q, double *atom_energy) {
+    if (!sys) return fail(SL_EINVAL, "NULL system");
+    sl::Sys &s = sys->s;
+    cudaSetDevice(s.device);
+    if (s.n == 0) return SL_OK;
+    int rc;
+    if ((rc = evaluate(s, false, false, false))) return rc;
+    const size_t N = (size_t)s.n, R = s.prec == 0 ? 8 : 4;
+    std::vector<char> hq(R * sl::DIM * N), he(R * N);
+    std::vector<int32_t> orig(N);
+    CK(cudaMemcpyAsync(hq.data(), s.q, hq.size(), cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaMemcpyAsync(he.data(), s.ei, he.size(), cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaMemcpyAsync(orig.data(), s.orig, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaStreamSynchronize(s.stream));
+    auto get = [&](const std::vector<char> &b, size_t idx) {
+        return R == 8 ? ((const double *)b.data())[idx] : (double)((const float *)b.data())[idx];
+    };
+    for (size_t i = 0; i < N; ++i) {
+        if (q)
+            for (int v = 0; v < sl::DIM; ++v) q[(size_t)orig[i] * sl::DIM + v] = get(hq, (size_t)v * N + i);
+        if (atom_energy) atom_energy[orig[i]] = get(he, i);
+    }
+    return SL_OK;
+}
+
+int sl_get_state(const sl_system *sys, double *pos, double *vel, double *spins, double *forces, double *fields,
+                 uint64_t *step) {
+    if (!sys) return fail(SL_EINVAL, "NULL system");
+    const sl::Sys &s = sys->s;
+    cudaSetDevice(s.device);
+    int rc;
+    if (s.n > 0) {
+        if (pos && (rc = download_vec(s, s.pos, pos))) return rc;
+        if (vel && (rc = download_vec(s, s.vel, vel))) return rc;
+        if (spins && (rc = download_vec(s, s.spin, spins))) return rc;
+        if (forces && (rc = download_vec(s, s.F, forces))) return rc;
+        if (fields && (rc = download_vec(s, s.H, fields))) return rc;
+    }
+    if (step) *step = s.step;
+    return SL_OK;
+}
+
+int sl_set_state(sl_system *sys, const double *pos, const double *vel, const double *spins, const double *forces,
+                 const double *fields, uint64_t step) {
+    if (!sys) return fail(SL_EINVAL, "NULL system");
+    sl::Sys &s = sys->s;
+    cudaSetDevice(s.device);
+    if (s.n > 0 && (!pos || !vel || !spins)) return fail(SL_EINVAL, "positions, velocities and spins are required");
+    if ((forces == nullptr) != (fields == nullptr)) return fail(SL_EINVAL, "give both forces and fields or neither");
+    int rc;
+    CK(cudaStreamSynchronize(s.stream));
+    if (s.n > 0) {
+        for (int64_t i = 0; i < 3 * s.n; ++i)
+            if (!std::isfinite(pos[i]) || !std::isfinite(vel[i]) || !std::isfinite(spins[i]))
+                return fail(SL_EINVAL, "non-finite state value");
+        if ((rc = upload_vec(s, s.pos, pos, false)) || (rc = upload_vec(s, s.vel, vel, false)) ||
+            (rc = upload_vec(s, s.spin, spins, true)))
+            return rc;
+    }
+    s.step = step;
+    unsigned long long st[2] = {step, step};
+    CK(cudaMemcpy(s.d_step, st, sizeof st, cudaMemcpyHostToDevice));
+    CK(cudaMemset(s.status, 0, sizeof(int)));
+    if ((rc = refresh_copies(s))) return rc;
+    if (forces) {
+        if (s.n > 0 && ((rc = upload_vec(s, s.F, forces, false)) || (rc = upload_vec(s, s.H, fields, false)))) return rc;
+        if (s.n > 0) {
+            sl::launch_rebuild(s, false);
+            s.n_builds++;
+        }
+        CK(cudaGetLastError());
+    } else if ((rc = evaluate(s, true, true, false))) {
+        return rc;
+    }
+    return check_status(s);
+}
+
+int sl_get_neighbors(sl_system *sys, int32_t cap, int32_t *counts_rad, int32_t *lists_rad, int32_t *counts_ang,
+                     int32_t *lists_ang) {
+    if (!sys || cap < 0) return fail(SL_EINVAL, "bad arguments");
+    sl::Sys &s = sys->s;
+    cudaSetDevice(s.device);
+    if (s.n == 0) return SL_OK;
+    CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
+    sl::launch_rebuild(s, false);
+    s.n_builds++;
+    int rc = check_status(s);
+    if (rc) return rc;
+    const size_t N = (size_t)s.n;
+    std::vector<int32_t> nbr(N * s.cap), orig(N);
+    std::vector<int4> seg(N);
+    CK(cudaMemcpy(nbr.data(), s.nbr, sizeof(int32_t) * N * s.cap, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(orig.data(), s.orig, sizeof(int32_t) * N, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(seg.data(), s.seg, sizeof(int4) * N, cudaMemcpyDeviceToHost));
+    bool over = false;
+    for (size_t i = 0; i < N; ++i) {
+        const int c = orig[i];
+        std::vector<int32_t> rad, ang;
+        for (int t = 0; t < seg[i].w; ++t) {
+            const int32_t j = orig[nbr[(size_t)t * N + i]];
+            rad.push_back(j);
+            if (t < seg[i].y) ang.push_back(j);
+        }
+        std::sort(rad.begin(), rad.end());
+        std::sort(ang.begin(), ang.end());
+        if (counts_rad) counts_rad[c] = (int32_t)rad.size();
+        if (counts_ang) counts_ang[c] = (int32_t)ang.size();
+        if ((int)rad.size() > cap) over = true;
+        if (lists_rad)
+            for (size_t t = 0; t < rad.size() && (int)t < cap; ++t) lists_rad[(size_t)c * cap + t] = rad[t];
+        if (lists_ang)
+            for (size_t t = 0; t < ang.size() && (int)t < cap; ++t) lists_ang[(size_t)c * cap + t] = ang[t];
+    }
+    if (over) return fail(SL_EINVAL, "a list is longer than the output capacity %d", cap);
+    return SL_OK;
+}
+
+int sl_get_info(const sl_system *sys, int64_t *n_atoms, int32_t *precision, int64_t *n_builds,
+                int64_t *n_launches) {
+    if (!sys) return fail(SL_EINVAL, "NULL system");
+    const sl::Sys &s = sys->s;
+    if (n_atoms) *n_atoms = s.n;
+    if (precision) *precision = s.prec;
+    if (n_builds) {
+        unsigned long long b = 0;
+        cudaSetDevice(s.device);
+        CK(cudaMemcpyAsync(&b, s.d_builds, sizeof b, cudaMemcpyDeviceToHost, s.stream));
+        CK(cudaStreamSynchronize(s.stream));
+        *n_builds = (int64_t)b;
+    }
+    if (n_launches) *n_launches = s.n_launches;
+    return SL_OK;
+}
+
+int sl_step_profiled(sl_system *sys, int64_t n_steps, double dt, double T, const double B[3], double *kernel_ms) {
+    if (!sys || !B || !kernel_ms) return fail(SL_EINVAL, "NULL argument");
+    if (n_steps < 0 || !(dt > 0) || !(T >= 0)) return fail(SL_EINVAL, "bad step arguments");
+    sl::Sys &s = sys->s;
+    cudaSetDevice(s.device);
+    for (int k = 0; k < SL_NKERNELS; ++k) kernel_ms[k] = 0.0;
+    int rc;
+    if ((rc = upload_params(s, dt, T, B))) return rc;
+    for (int c = 0; c < 3; ++c) s.B[c] = B[c];
+    if (s.n == 0 || n_steps == 0) { s.step += (uint64_t)n_steps; return SL_OK; }
+    CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
+    // events per step: before first half, before rebuild, before/inside eval (4), after second half
+    const int EV = 7;
+    std::vector<cudaEvent_t> ev((size_t)EV * n_steps);
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    for (int64_t t = 0; t < n_steps; ++t) {
+        cudaEvent_t *e = ev.data() + EV * t;
+        CK(cudaEventRecord(e[0], s.stream));
+        sl::launch_first_half(s);
+        CK(cudaEventRecord(e[1], s.stream));
+        sl::launch_rebuild(s, true);
+        sl::launch_eval(s, false, e + 2);   // e[2] before fwd, e[3] before mlp, e[4] before bwd, e[5] after bwd
+        sl::launch_second_half(s);
+        CK(cudaEventRecord(e[6], s.stream));
+    }
+    CK(cudaGetLastError());
+    s.n_launches += n_steps * sl::KERNELS_PER_STEP;
+    rc = check_status(s);
+    for (int64_t t = 0; t < n_steps && rc == SL_OK; ++t) {
+        cudaEvent_t *e = ev.data() + EV * t;
+        float ms;
+        const int from[SL_NKERNELS] = {0, 1, 2, 3, 4, 5}, to[SL_NKERNELS] = {1, 2, 3, 4, 5, 6};
+        for (int k = 0; k < SL_NKERNELS; ++k) {
+            CK(cudaEventElapsedTime(&ms, e[from[k]], e[to[k]]));
+            kernel_ms[k] += ms;
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (rc) return rc;
+    s.step += (uint64_t)n_steps;
+    return SL_OK;
+}
+
+int sl_measure_fma_peak(int32_t precision, double *flops, double *ms) {
+    if (!flops) return fail(SL_EINVAL, "NULL argument");
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
+        cudaGetLastError();
+        return fail(SL_ECUDA, "no usable CUDA device");
+    }
+    double t = 0;
+    if (sl::measure_fma_peak(precision, flops, &t)) return fail(SL_ECUDA, "peak kernel failed");
+    if (ms) *ms = t;
+    return SL_OK;
+}
+
+void *sl_get_stream(const sl_system *sys) { return sys ? (void *)sys->s.stream : nullptr; }
+
+void sl_destroy_system(sl_system *sys) {
+    if (!sys) return;
+    cudaSetDevice(sys->s.device);
+    if (sys->s.stream) cudaStreamSynchronize(sys->s.stream);
+    free_sys(sys->s);
+    delete sys;
+}
+
+// ---------------------------------------------------------------- batches
+int sl_batch_create(sl_system *const *systems, int32_t k, sl_batch **out) {
+    if (!out || k < 1 || !systems) return fail(SL_EINVAL, "bad arguments");
+    *out = nullptr;
+    for (int i = 0; i < k; ++i) {
+        if (!systems[i]) return fail(SL_EINVAL, "NULL system in batch");
+        if (systems[i]->s.prec != systems[0]->s.prec) return fail(SL_EINVAL, "mixed precision modes in a batch");
+    }
+    sl_batch *b = new (std::nothrow) sl_batch();
+    if (!b) return fail(SL_ENOMEM, "host allocation failed");
+    b->sys.assign(systems, systems + k);
+    *out = b;
+    return SL_OK;
+}
+
+int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt, const double *T, const double *B) {
+    if (!b || !n_steps || !dt || !T || !B) return fail(SL_EINVAL, "NULL argument");
+    // every replica's steps are queued on its own stream before any wait, so the
+    // replicas' kernels overlap on the device
+    const int k = (int)b->sys.size();
+    int rc = SL_OK;
+    for (int i = 0; i < k && rc == SL_OK; ++i) {
+        if (n_steps[i] < 0 || !(dt[i] > 0) || !(T[i] >= 0)) return fail(SL_EINVAL, "bad step arguments for replica %d", i);
+    }
+    std::vector<int> active;
+    for (int i = 0; i < k; ++i) {
+        sl::Sys &s = b->sys[i]->s;
+        if ((rc = upload_params(s, dt[i], T[i], B + 3 * i))) return rc;
+        for (int c = 0; c < 3; ++c) s.B[c] = B[3 * i + c];
+        if (n_steps[i] == 0 || s.n == 0) { s.step += (uint64_t)n_steps[i]; continue; }
+        CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
+        int64_t left = n_steps[i];
+        const int g = s.steps_per_graph;
+        if (g > 0 && left >= g) {
+            if (!s.graph || s.graph_steps != g)
+                if ((rc = capture_graph(s, g))) return rc;
+            while (left >= g) { CK(cudaGraphLaunch(s.graph, s.stream)); left -= g; }
+        }
+        for (; left > 0; --left) enqueue_step(s);
+        active.push_back(i);
+    }
+    CK(cudaGetLastError());
+    for (int i : active) {
+        sl::Sys &s = b->sys[i]->s;
+        if ((rc = check_status(s))) return fail(rc, "replica %d: %s", i, g_err.c_str());
+        s.step += (uint64_t)n_steps[i];
+    }
+    return SL_OK;
+}
+
+void sl_batch_destroy(sl_batch *b) { delete b; }
+
+// ---------------------------------------------------------------- self checks
+int sl_selftest_harmonics(int32_t n_samples, double *max_add, double *max_grad) {
+    using namespace sl;
+    if (n_samples < 1) return fail(SL_EINVAL, "n_samples < 1");
+    uint64_t st = 0x9E3779B97F4A7C15ULL;
+    auto uni = [&]() {
+        st ^= st << 13; st ^= st >> 7; st ^= st << 17;
+        return (double)(st >> 11) * (1.0 / 9007199254740992.0);
+    };
+    auto unit = [&](double u[3]) {
+        double z = 2 * uni() - 1, ph = 2 * M_PI * uni(), rr = std::sqrt(1 - z * z);
+        u[0] = rr * std::cos(ph); u[1] = rr * std::sin(ph); u[2] = z;
+    };
+    double ea = 0, eg = 0;
+    for (int t = 0; t < n_samples; ++t) {
+        double u[3], v[3], pu[NLM], pv[NLM];
+        unit(u); unit(v);
+        harm_p(u[0], u[1], u[2], pu);
+        harm_p(v[0], v[1], v[2], pv);
+        const double c = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+        const double P[5] = {1, c, 0.5 * (3 * c * c - 1), 0.5 * (5 * c * c * c - 3 * c),
+                             0.125 * (35 * c * c * c * c - 30 * c * c + 3)};
+        double sum[5] = {0, 0, 0, 0, 0};
+        for (int lm = 0; lm < NLM; ++lm) sum[harm_l(lm)] += harm_kappa(lm) * pu[lm] * pv[lm];
+        for (int l = 1; l <= 4; ++l) ea = std::max(ea, std::fabs(sum[l] - P[l]));
+        // gradient: central differences of the homogeneous polynomial at a generic point
+        double x[3] = {u[0] * 1.3, u[1] * 1.3, u[2] * 1.3}, g[NLM][3], p1[NLM], px[NLM];
+        harm_all(x[0], x[1], x[2], p1, g);
+        harm_p(x[0], x[1], x[2], px);
+        for (int lm = 0; lm < NLM; ++lm) eg = std::max(eg, std::fabs(p1[lm] - px[lm]));
+        const double h = 1e-6;
+        for (int a = 0; a < 3; ++a) {
+            double xp[3] = {x[0], x[1], x[2]}, xm[3] = {x[0], x[1], x[2]}, pp[NLM], pm[NLM];
+            xp[a] += h; xm[a] -= h;
+            harm_p(xp[0], xp[1], xp[2], pp);
+            harm_p(xm[0], xm[1], xm[2], pm);
+            for (int lm = 0; lm < NLM; ++lm) eg = std::max(eg, std::fabs((pp[lm] - pm[lm]) / (2 * h) - g[lm][a]));
+        }
+    }
+    if (max_add) *max_add = ea;
+    if (max_grad) *max_grad = eg;
+    return SL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,280 @@
+// sl_integrate.cu -- spin-lattice integrator kernels, force/field gather, reductions.
+//
+// One step (arXiv 2606.14073, Sections 3, 5.1.3, 5.2.1; the paper gives no formulas,
+// this is the structure-preserving predictor-corrector reading with the spin
+// update scheduled last):
+//   first half  (k_first_half):  v += dt/2 F/m; r += dt/2 v; v = c v + sig_v xi;
+//                                r += dt/2 v (wrapped); eta = sig_eta zeta;
+//                                S' = Rot(S, omega(S, H + eta) dt)
+//   evaluation  at (r, S')  (sl_nep.cu)
+//   second half (k_second_half): gather F', H'; S = Rot(S, (omega(S,H+eta) + omega(S',H'+eta)) dt/2),
+//                                renormalised in FP64; v += dt/2 F'/m; (F, H) = (F', H')
+// omega(S, X) = (X + lambda S x X) / ((1 + lambda^2) hbar); Rot is the exact Rodrigues
+// rotation.  xi, zeta are Philox4x64-10 normals, streams 1 and 2, counter
+// (step, caller index, stream, 0), key (seed, replica): the corrector regenerates
+// the predictor's eta bit for bit, so nothing is stored between the halves.
+#include "sl_internal.h"
+
+namespace sl {
+
+template <typename R> struct V2i;
+template <> struct V2i<float> { using t = float2; };
+template <> struct V2i<double> { using t = double2; };
+
+struct IntArgs {
+    double4 *pos, *vel, *spin, *spin_prev, *F, *H, *posref;
+    float4 *posf, *spinf;
+    const int32_t *orig;
+    int64_t n, n_fe;
+    BoxDev<double> bd;
+    int per[3];
+    const StepDev *par;
+    unsigned long long *step;
+    int *rebuild, *status;
+    uint64_t seed, replica;
+};
+
+template <typename R>
+struct GatherArgs {
+    const v4<R> *fown, *gii, *pd0;
+    const typename V2i<R>::t *pd1;
+    const int32_t *nbr, *rev;
+    const int4 *seg;
+    int64_t n;
+};
+
+__device__ __forceinline__ void omega_of(double sx, double sy, double sz, double hx, double hy, double hz,
+                                         double lam, double k, double w[3]) {
+    w[0] = (hx + lam * (sy * hz - sz * hy)) * k;
+    w[1] = (hy + lam * (sz * hx - sx * hz)) * k;
+    w[2] = (hz + lam * (sx * hy - sy * hx)) * k;
+}
+
+__device__ __forceinline__ void rotate(double sx, double sy, double sz, const double w[3], double dt, double out[3]) {
+    const double wn2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    if (wn2 == 0.0) { out[0] = sx; out[1] = sy; out[2] = sz; return; }
+    const double wn = sqrt(wn2);
+    const double ax = w[0] / wn, ay = w[1] / wn, az = w[2] / wn;
+    double s, c;
+    sincos(wn * dt, &s, &c);
+    const double as = ax * sx + ay * sy + az * sz;
+    const double cx = ay * sz - az * sy, cy = az * sx - ax * sz, cz = ax * sy - ay * sx;
+    out[0] = sx * c + cx * s + ax * as * (1.0 - c);
+    out[1] = sy * c + cy * s + ay * as * (1.0 - c);
+    out[2] = sz * c + cz * s + az * as * (1.0 - c);
+}
+
+__global__ void __launch_bounds__(256) k_first_half(IntArgs a) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const unsigned long long st = a.step[0];
+    if (i == 0) a.step[1] = st;
+    if (i >= a.n) return;
+    const StepDev &P = *a.par;
+    const int t = i < a.n_fe ? 0 : 1;
+    const uint64_t id = (uint64_t)a.orig[i];
+    double4 r = a.pos[i], v = a.vel[i];
+    const double4 F = a.F[i], H = a.H[i], S = a.spin[i];
+    const double hdt = P.half_dt, am = P.acc_m[t];
+    double xi[3], ze[3];
+    gauss3(st, id, 1, a.seed, a.replica, xi);
+    gauss3(st, id, 2, a.seed, a.replica, ze);
+    v.x += hdt * F.x * am; v.y += hdt * F.y * am; v.z += hdt * F.z * am;
+    r.x += hdt * v.x; r.y += hdt * v.y; r.z += hdt * v.z;
+    const double c = P.c_fric, sv = P.sig_v[t];
+    v.x = c * v.x + sv * xi[0]; v.y = c * v.y + sv * xi[1]; v.z = c * v.z + sv * xi[2];
+    r.x += hdt * v.x; r.y += hdt * v.y; r.z += hdt * v.z;
+    if (a.per[0]) r.x = r.x - a.bd.L[0] * floor(r.x / a.bd.L[0]);
+    if (a.per[1]) r.y = r.y - a.bd.L[1] * floor(r.y / a.bd.L[1]);
+    if (a.per[2]) r.z = r.z - a.bd.L[2] * floor(r.z / a.bd.L[2]);
+    const double se = P.sig_eta;
+    double w[3], Sp[3];
+    omega_of(S.x, S.y, S.z, H.x + se * ze[0], H.y + se * ze[1], H.z + se * ze[2], P.lambda, P.wscale, w);
+    rotate(S.x, S.y, S.z, w, P.dt, Sp);
+    a.pos[i] = r;
+    a.vel[i] = v;
+    a.spin_prev[i] = S;
+    a.spin[i] = make_double4(Sp[0], Sp[1], Sp[2], 0.0);
+    a.posf[i] = make_float4((float)r.x, (float)r.y, (float)r.z, 0.f);
+    a.spinf[i] = make_float4((float)Sp[0], (float)Sp[1], (float)Sp[2], 0.f);
+    // rebuild trigger: displacement since the last build beyond skin/2
+    const double4 p0 = a.posref[i];
+    double dx = r.x - p0.x, dy = r.y - p0.y, dz = r.z - p0.z;
+    minimg(a.bd, dx, dy, dz);
+    if (dx * dx + dy * dy + dz * dz > P.disp2) *a.rebuild = 1;
+}
+
+template <typename R>
+__device__ __forceinline__ void gather(const GatherArgs<R> &g, int64_t k, double F[3], double H[3]) {
+    const v4<R> fo = g.fown[k], gi = g.gii[k];
+    R fx = fo.x, fy = fo.y, fz = fo.z, hx = -gi.x, hy = -gi.y, hz = -gi.z;
+    const int4 sg = g.seg[k];
+    const int64_t N = g.n;
+    for (int s = 0; s < sg.w; ++s) {
+        const int j = g.nbr[(int64_t)s * N + k];
+        const int t = g.rev[(int64_t)s * N + k];
+        const v4<R> e0 = g.pd0[(int64_t)t * N + j];
+        const typename V2i<R>::t e1 = g.pd1[(int64_t)t * N + j];
+        fx -= e0.x; fy -= e0.y; fz -= e0.z;
+        hx -= e0.w; hy -= e1.x; hz -= e1.y;
+    }
+    F[0] = (double)fx; F[1] = (double)fy; F[2] = (double)fz;
+    H[0] = (double)hx; H[1] = (double)hy; H[2] = (double)hz;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_second_half(IntArgs a, GatherArgs<R> g) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == 0) a.step[0] = a.step[1] + 1;
+    if (i >= a.n) return;
+    const StepDev &P = *a.par;
+    const int t = i < a.n_fe ? 0 : 1;
+    const uint64_t id = (uint64_t)a.orig[i];
+    const unsigned long long st = a.step[1];
+    double Fs[3], Hs[3];
+    gather<R>(g, i, Fs, Hs);
+    Hs[0] += P.zee[t][0]; Hs[1] += P.zee[t][1]; Hs[2] += P.zee[t][2];
+    double ze[3];
+    gauss3(st, id, 2, a.seed, a.replica, ze);
+    const double se = P.sig_eta;
+    const double4 S0 = a.spin_prev[i], S1 = a.spin[i], H0 = a.H[i];
+    double w0[3], w1[3], w[3], Sn[3];
+    omega_of(S0.x, S0.y, S0.z, H0.x + se * ze[0], H0.y + se * ze[1], H0.z + se * ze[2], P.lambda, P.wscale, w0);
+    omega_of(S1.x, S1.y, S1.z, Hs[0] + se * ze[0], Hs[1] + se * ze[1], Hs[2] + se * ze[2], P.lambda, P.wscale, w1);
+    w[0] = 0.5 * (w0[0] + w1[0]); w[1] = 0.5 * (w0[1] + w1[1]); w[2] = 0.5 * (w0[2] + w1[2]);
+    rotate(S0.x, S0.y, S0.z, w, P.dt, Sn);
+    const double nn = sqrt(Sn[0] * Sn[0] + Sn[1] * Sn[1] + Sn[2] * Sn[2]);
+    Sn[0] /= nn; Sn[1] /= nn; Sn[2] /= nn;
+    double4 v = a.vel[i];
+    const double hdt = P.half_dt, am = P.acc_m[t];
+    v.x += hdt * Fs[0] * am; v.y += hdt * Fs[1] * am; v.z += hdt * Fs[2] * am;
+    a.vel[i] = v;
+    a.spin[i] = make_double4(Sn[0], Sn[1], Sn[2], 0.0);
+    a.spinf[i] = make_float4((float)Sn[0], (float)Sn[1], (float)Sn[2], 0.f);
+    a.F[i] = make_double4(Fs[0], Fs[1], Fs[2], 0.0);
+    a.H[i] = make_double4(Hs[0], Hs[1], Hs[2], 0.0);
+    if (!(isfinite(Fs[0]) && isfinite(Fs[1]) && isfinite(Fs[2]) && isfinite(Hs[0]) && isfinite(Hs[1]) &&
+          isfinite(Hs[2])))
+        atomicOr(a.status, ST_NONFINITE);
+}
+
+// Forces and fields at the current state into (Fo, Ho).
+template <typename R>
+__global__ void __launch_bounds__(256) k_gather_only(GatherArgs<R> g, const StepDev *par, int64_t n_fe,
+                                                     double4 *Fo, double4 *Ho, int *status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const int t = i < n_fe ? 0 : 1;
+    double Fs[3], Hs[3];
+    gather<R>(g, i, Fs, Hs);
+    Hs[0] += par->zee[t][0]; Hs[1] += par->zee[t][1]; Hs[2] += par->zee[t][2];
+    Fo[i] = make_double4(Fs[0], Fs[1], Fs[2], 0.0);
+    Ho[i] = make_double4(Hs[0], Hs[1], Hs[2], 0.0);
+    if (!(isfinite(Fs[0]) && isfinite(Fs[1]) && isfinite(Fs[2]) && isfinite(Hs[0]) && isfinite(Hs[1]) &&
+          isfinite(Hs[2])))
+        atomicOr(status, ST_NONFINITE);
+}
+
+static IntArgs int_args(Sys &s) {
+    IntArgs a;
+    a.pos = s.pos; a.vel = s.vel; a.spin = s.spin; a.spin_prev = s.spin_prev; a.F = s.F; a.H = s.H;
+    a.posref = s.posref; a.posf = s.posf; a.spinf = s.spinf; a.orig = s.orig; a.n = s.n; a.n_fe = s.n_fe;
+    a.bd = s.boxd;
+    for (int d = 0; d < 3; ++d) a.per[d] = s.per[d];
+    a.par = s.d_par; a.step = s.d_step; a.rebuild = s.rebuild; a.status = s.status;
+    a.seed = s.seed; a.replica = s.replica;
+    return a;
+}
+
+template <typename R>
+static GatherArgs<R> gather_args(Sys &s) {
+    GatherArgs<R> g;
+    g.fown = (const v4<R> *)s.fown; g.gii = (const v4<R> *)s.gii; g.pd0 = (const v4<R> *)s.pd0;
+    g.pd1 = (const typename V2i<R>::t *)s.pd1; g.nbr = s.nbr; g.rev = s.rev; g.seg = s.seg; g.n = s.n;
+    return g;
+}
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+void launch_first_half(Sys &s) {
+    k_first_half<<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s));
+}
+
+void launch_second_half(Sys &s) {
+    if (s.prec == 0) k_second_half<double><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<double>(s));
+    else k_second_half<float><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<float>(s));
+}
+
+void launch_gather(Sys &s, bool carried) {
+    double4 *Fo = carried ? s.F : s.Fo, *Ho = carried ? s.H : s.Ho;
+    if (s.prec == 0)
+        k_gather_only<double><<<nblk(s.n, 256), 256, 0, s.stream>>>(gather_args<double>(s), s.d_par, s.n_fe, Fo, Ho,
+                                                                    s.status);
+    else
+        k_gather_only<float><<<nblk(s.n, 256), 256, 0, s.stream>>>(gather_args<float>(s), s.d_par, s.n_fe, Fo, Ho,
+                                                                   s.status);
+}
+
+__global__ void k_set_flag(int *flag) { *flag = 1; }
+
+void launch_mark_rebuild(Sys &s) { k_set_flag<<<1, 1, 0, s.stream>>>(s.rebuild); }
+
+// ------------------------------------------------------------------ reductions
+// Deterministic two-level FP64 sums: fixed 256 blocks, each summing a fixed
+// stride of atoms in order, then one block adding the block partials in order.
+constexpr int RED_BLOCKS = 256;
+constexpr int RED_VALS = 10;   // E_network + E_Zeeman, virial[9]
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_reduce1(const R *__restrict__ ei, const R *__restrict__ wpart,
+                                                 const double4 *__restrict__ spin, const StepDev *par, int64_t n,
+                                                 int64_t n_fe, int want_virial, double *__restrict__ part) {
+    __shared__ double sh[RED_VALS][256];
+    double acc[RED_VALS];
+#pragma unroll
+    for (int v = 0; v < RED_VALS; ++v) acc[v] = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int t = i < n_fe ? 0 : 1;
+        const double4 S = spin[i];
+        acc[0] += (double)ei[i] - (par->zee[t][0] * S.x + par->zee[t][1] * S.y + par->zee[t][2] * S.z);
+        if (want_virial)
+            for (int v = 0; v < 9; ++v) acc[1 + v] += (double)wpart[(int64_t)v * n + i];
+    }
+#pragma unroll
+    for (int v = 0; v < RED_VALS; ++v) sh[v][threadIdx.x] = acc[v];
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if (threadIdx.x < off)
+            for (int v = 0; v < RED_VALS; ++v) sh[v][threadIdx.x] += sh[v][threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x < RED_VALS) part[blockIdx.x * RED_VALS + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_reduce2(const double *__restrict__ part, double *__restrict__ out) {
+    if (threadIdx.x < RED_VALS) {
+        double s = 0.0;
+        for (int b = 0; b < RED_BLOCKS; ++b) s += part[b * RED_VALS + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+int reduce_energy_virial(Sys &s, double *E, double *W, bool want_virial) {
+    double *part = s.red, *out = s.red + RED_BLOCKS * RED_VALS;
+    if (s.prec == 0)
+        k_reduce1<double><<<RED_BLOCKS, 256, 0, s.stream>>>((const double *)s.ei, (const double *)s.wpart, s.spin,
+                                                            s.d_par, s.n, s.n_fe, want_virial, part);
+    else
+        k_reduce1<float><<<RED_BLOCKS, 256, 0, s.stream>>>((const float *)s.ei, (const float *)s.wpart, s.spin,
+                                                           s.d_par, s.n, s.n_fe, want_virial, part);
+    k_reduce2<<<1, 32, 0, s.stream>>>(part, out);
+    cudaError_t e = cudaMemcpyAsync(s.h_red, out, sizeof(double) * RED_VALS, cudaMemcpyDeviceToHost, s.stream);
+    if (e != cudaSuccess) return -1;
+    e = cudaStreamSynchronize(s.stream);
+    if (e != cudaSuccess) return -1;
+    if (E) *E = s.h_red[0];
+    if (W)
+        for (int v = 0; v < 9; ++v) W[v] = s.h_red[1 + v];
+    return 0;
+}
+
+}  // namespace sl

@@ -1,0 +1,119 @@
+// sl_internal.h -- host-side system object and kernel launchers (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sl_common.cuh"
+
+namespace sl {
+
+// Per-call integrator constants, written by the host before each batch of
+// steps and read by the kernels (so one captured graph serves any dt, T, B).
+struct StepDev {
+    double dt, half_dt;
+    double c_fric;              // exp(-gamma dt)
+    double sig_v[NS];           // sqrt((1 - c^2) kB T ACC / m)
+    double acc_m[NS];           // ACC / m  (force -> acceleration)
+    double sig_eta;             // sqrt(2 lambda kB T hbar / dt)
+    double lambda;              // Gilbert damping
+    double wscale;              // 1 / ((1 + lambda^2) hbar)
+    double zee[NS][3];          // mu_t muB B  (Zeeman field per species)
+    double disp2;               // (skin/2)^2, rebuild threshold
+};
+
+struct Cells {
+    int nc[3];
+    int ncell;
+    int *count = nullptr, *start = nullptr, *fill = nullptr, *atoms = nullptr, *of = nullptr;
+};
+
+struct Sys {
+    int64_t n = 0;
+    int prec = 0;
+    uint64_t seed = 0, replica = 0;
+    double skin = 1.0, gamma = 0.01, lambda = 0.1;
+    int cap = 160, cap_ang = 64;
+    int steps_per_graph = 10;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+
+    NepDev<double> pd;
+    NepDev<float> pf;
+    double mass[NS], moment[NS];
+    BoxDev<double> boxd;
+    BoxDev<float> boxf;
+    double box[3];
+    int per[3];
+    double cut_r2, cut_a2;     // (rc + skin)^2, radial and angular
+
+    // state, internal atom order (species-major, then spatial cell order)
+    double4 *pos = nullptr, *vel = nullptr, *spin = nullptr, *spin_prev = nullptr;
+    double4 *F = nullptr, *H = nullptr, *posref = nullptr;
+    float4 *posf = nullptr, *spinf = nullptr;
+    int32_t *species = nullptr, *orig = nullptr, *inv = nullptr;
+    int64_t n_fe = 0;          // atoms [0, n_fe) are species 0
+
+    // neighbour lists: slot-major [slot][atom]
+    int32_t *nbr = nullptr, *rev = nullptr;
+    int4 *seg = nullptr;       // per atom: ends of (ang t0, ang t1, rad t0, rad t1)
+    Cells cells;
+
+    // evaluation buffers (element type = compute precision)
+    void *q = nullptr;         // [DIM][n]
+    void *bsum = nullptr;      // [NB][n]
+    void *fp = nullptr;        // [DIM][n]
+    void *ei = nullptr;        // [n]
+    void *pd0 = nullptr;       // [cap][n] v4: (dE_i/dr_ij, dE_i/dS_j .x)
+    void *pd1 = nullptr;       // [cap][n] v2: (dE_i/dS_j .y .z)
+    void *fown = nullptr;      // [n] v4: sum_j dE_i/dr_ij
+    void *gii = nullptr;       // [n] v4: dE_i/dS_i
+    void *wpart = nullptr;     // [9][n] per-atom virial parts
+    double4 *Fo = nullptr, *Ho = nullptr;   // evaluation outputs (not the carried F, H)
+
+    // control
+    int *status = nullptr;     // device status bits
+    int *rebuild = nullptr;    // device rebuild flag
+    unsigned long long *d_step = nullptr;   // [2]: current step, copy for the corrector
+    StepDev *d_par = nullptr;
+    StepDev *h_par = nullptr;  // pinned
+    int *h_status = nullptr;   // pinned
+    uint64_t step = 0;
+    double B[3] = {0, 0, 0};
+    int64_t n_builds = 0;      // builds requested by the host
+    unsigned long long *d_builds = nullptr;   // builds executed on the device
+    int64_t n_launches = 0;    // kernels launched by step calls
+    double *red = nullptr;     // reduction scratch (device)
+    double *h_red = nullptr;   // pinned
+
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    // snapshot for error recovery
+    double4 *snap = nullptr;   // 5 n: pos, vel, spin, F, H
+};
+
+// launchers (sl_neighbors.cu)
+void nbr_setup(Sys &s);
+void launch_rebuild(Sys &s, bool conditional);
+// sl_nep.cu
+// ev (optional, 4 events): recorded before the descriptor, network and backward
+// kernels and after the backward kernel.
+void launch_eval(Sys &s, bool want_virial, cudaEvent_t *ev = nullptr);
+constexpr int KERNELS_PER_STEP = 1 + 7 + 3 + 1;   // first half, rebuild group, eval, second half
+// sl_integrate.cu
+void launch_first_half(Sys &s);
+void launch_second_half(Sys &s);
+void launch_gather(Sys &s, bool carried);
+void launch_mark_rebuild(Sys &s);
+int reduce_energy_virial(Sys &s, double *E, double *W, bool want_virial);
+
+size_t eval_bytes(const Sys &s);
+void eval_init();
+// sl_peak.cu
+int measure_fma_peak(int precision, double *flops_per_s, double *elapsed_ms);
+
+}  // namespace sl

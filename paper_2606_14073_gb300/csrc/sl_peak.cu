@@ -1,0 +1,60 @@
+// sl_peak.cu -- FMA throughput microbenchmark (the ALU roofline of the descriptor kernels).
+//
+// Every thread runs 8 independent FMA chains; 4 blocks of 256 threads per SM keep
+// every scheduler issuing.  FLOP count: 2 per FMA.
+#include "sl_internal.h"
+
+namespace sl {
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_fma_peak(R *out, int iters, R b, R c) {
+    R a[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) a[t] = R(threadIdx.x) * R(1e-3) + R(t);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) a[t] = a[t] * b + c;
+        }
+    }
+    R s = R(0);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) s += a[t];
+    if (s == R(-12345.678)) out[blockIdx.x] = s;   // keeps the chains live, never true
+}
+
+template <typename R>
+static int run_peak(int iters, double *flops, double *ms) {
+    int dev, sms;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    R *out;
+    if (cudaMalloc(&out, sizeof(R) * sms * 8) != cudaSuccess) return -1;
+    const int blocks = sms * 4, threads = 256;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_fma_peak<R><<<blocks, threads>>>(out, 16, R(0.999999), R(1e-7));   // warm-up
+    cudaEventRecord(e0);
+    k_fma_peak<R><<<blocks, threads>>>(out, iters, R(0.999999), R(1e-7));
+    cudaEventRecord(e1);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess) return -1;
+    *ms = t;
+    *flops = 2.0 * 8.0 * 16.0 * (double)iters * blocks * threads / (t * 1e-3);
+    return 0;
+}
+
+int measure_fma_peak(int precision, double *flops, double *ms) {
+    // FP32: ~0.2 s at ~70 TFLOP/s; FP64 is expected far slower on this part, so
+    // fewer iterations keep that run short as well.
+    return precision == 0 ? run_peak<double>(512, flops, ms) : run_peak<float>(8192, flops, ms);
+}
+
+}  // namespace sl

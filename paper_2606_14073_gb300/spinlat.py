@@ -1,0 +1,271 @@
+"""Python binding of libspinlat (include/spinlat.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy arrays to
+pointers and C status codes to exceptions.  If the library cannot be loaded the
+import of `lib()` raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SL_OK, SL_EINVAL, SL_ENOMEM, SL_ENBR_OVERFLOW, SL_ENONFINITE, SL_ETIMEOUT, SL_ECUDA = 0, -1, -2, -3, -4, -5, -6
+SL_PREC_FP64, SL_PREC_MIXED = 0, 1
+_NAMES = {SL_EINVAL: "SL_EINVAL", SL_ENOMEM: "SL_ENOMEM", SL_ENBR_OVERFLOW: "SL_ENBR_OVERFLOW",
+          SL_ENONFINITE: "SL_ENONFINITE", SL_ETIMEOUT: "SL_ETIMEOUT", SL_ECUDA: "SL_ECUDA"}
+
+EXPORTS = ["sl_default_options", "sl_create_system", "sl_step", "sl_energy_forces_fields", "sl_get_descriptors",
+           "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_get_stream",
+           "sl_destroy_system", "sl_last_error", "sl_batch_create", "sl_batch_step", "sl_batch_destroy",
+           "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak"]
+KERNEL_GROUPS = ["first_half", "rebuild", "descriptor", "network", "backward", "second_half"]
+
+
+class SpinlatError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sl_nep_params(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("n_ch", C.c_int32), ("l_max", C.c_int32), ("basis_k", C.c_int32),
+                ("rc_rad", C.c_double), ("rc_ang", C.c_double), ("n_hidden", C.c_int32),
+                ("coeffs", C.c_void_p), ("q_scaler", C.c_void_p), ("w0", C.c_void_p), ("b0", C.c_void_p),
+                ("w1", C.c_void_p), ("b1", C.c_double), ("mass_amu", C.c_void_p), ("moment_muB", C.c_void_p)]
+
+
+class sl_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("seed", C.c_uint64), ("replica", C.c_uint64), ("skin", C.c_double),
+                ("gamma_lattice_per_fs", C.c_double), ("lambda_spin", C.c_double), ("midpoint_iters", C.c_int32),
+                ("nbr_cap_rad", C.c_int32), ("nbr_cap_ang", C.c_int32), ("steps_per_graph", C.c_int32),
+                ("cuda_stream", C.c_void_p), ("device", C.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib(path: str | None = None):
+    """Load libspinlat.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or os.environ.get("SPINLAT_LIB") or _build.build()
+            L = C.CDLL(p)
+            P, I64, D, I32 = C.c_void_p, C.c_int64, C.c_double, C.c_int32
+            L.sl_default_options.argtypes = [P]
+            L.sl_default_options.restype = None
+            L.sl_create_system.argtypes = [P, P, P, P, P, I64, P, P, P, P]
+            L.sl_step.argtypes = [P, I64, D, D, P]
+            L.sl_energy_forces_fields.argtypes = [P, P, P, P, P]
+            L.sl_get_descriptors.argtypes = [P, P, P]
+            L.sl_get_state.argtypes = [P, P, P, P, P, P, P]
+            L.sl_set_state.argtypes = [P, P, P, P, P, P, C.c_uint64]
+            L.sl_get_neighbors.argtypes = [P, I32, P, P, P, P]
+            L.sl_get_info.argtypes = [P, P, P, P, P]
+            L.sl_step_profiled.argtypes = [P, I64, D, D, P, P]
+            L.sl_measure_fma_peak.argtypes = [I32, P, P]
+            L.sl_get_stream.argtypes = [P]
+            L.sl_get_stream.restype = P
+            L.sl_destroy_system.argtypes = [P]
+            L.sl_destroy_system.restype = None
+            L.sl_last_error.restype = C.c_char_p
+            L.sl_batch_create.argtypes = [P, I32, P]
+            L.sl_batch_step.argtypes = [P, P, P, P, P]
+            L.sl_batch_destroy.argtypes = [P]
+            L.sl_batch_destroy.restype = None
+            L.sl_selftest_harmonics.argtypes = [I32, P, P]
+            for f in ("sl_create_system", "sl_step", "sl_energy_forces_fields", "sl_get_descriptors",
+                      "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_batch_create",
+                      "sl_batch_step", "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak"):
+                getattr(L, f).restype = C.c_int
+            _lib = L
+        return _lib
+
+
+def _check(rc):
+    if rc != SL_OK:
+        raise SpinlatError(rc, lib().sl_last_error().decode())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != shape:
+        a = a.reshape(shape)
+    return a
+
+
+class NepParams:
+    """sl_nep_params built from a parameter dict (see nep_params.load); keeps arrays alive."""
+
+    def __init__(self, p: dict):
+        self._arrs = {k: _f64(p[k]).ravel() for k in ("coeffs", "q_scaler", "w0", "b0", "w1", "mass_amu",
+                                                      "moment_muB")}
+        s = sl_nep_params()
+        s.n_species, s.n_ch, s.l_max, s.basis_k = int(p["n_species"]), int(p["n_ch"]), 4, int(p["basis_k"])
+        s.rc_rad, s.rc_ang, s.n_hidden = float(p["rc_rad"]), float(p["rc_ang"]), int(p["n_hidden"])
+        for k, a in self._arrs.items():
+            setattr(s, k, a.ctypes.data)
+        s.b1 = float(p["b1"])
+        self.struct = s
+
+
+def sl_default_options() -> sl_options:
+    o = sl_options()
+    lib().sl_default_options(C.byref(o))
+    return o
+
+
+class System:
+    """One replica on the GPU.  Methods mirror the C entry points."""
+
+    def __init__(self, positions, spins, box, periodic, species, params: dict, velocities=None, *,
+                 precision=SL_PREC_FP64, seed=1234, replica=0, skin=1.0, gamma=0.01, lam=0.1,
+                 cap_rad=160, cap_ang=64, steps_per_graph=10, stream=None, device=-1):
+        pos = _f64(positions)
+        n = pos.shape[0]
+        sp = _f64(spins)
+        spec = np.ascontiguousarray(species, dtype=np.int32)
+        box_ = _f64(box)
+        per = np.ascontiguousarray(periodic, dtype=np.int32)
+        vel = None if velocities is None else _f64(velocities)
+        self.params = NepParams(params)
+        o = sl_default_options()
+        o.precision, o.seed, o.replica, o.skin = int(precision), int(seed), int(replica), float(skin)
+        o.gamma_lattice_per_fs, o.lambda_spin = float(gamma), float(lam)
+        o.nbr_cap_rad, o.nbr_cap_ang, o.steps_per_graph = int(cap_rad), int(cap_ang), int(steps_per_graph)
+        o.cuda_stream = stream
+        o.device = int(device)
+        self.options = o
+        h = C.c_void_p()
+        _check(lib().sl_create_system(_ptr(pos), _ptr(sp), _ptr(box_), _ptr(per), _ptr(spec), n, _ptr(vel),
+                                      C.byref(self.params.struct), C.byref(o), C.byref(h)))
+        self.handle = h
+        self.n = n
+        self.precision = int(precision)
+
+    # -- C entry points
+    def step(self, n_steps: int, dt: float, T: float, B=(0.0, 0.0, 0.0)):
+        Bv = _f64(B)
+        _check(lib().sl_step(self.handle, int(n_steps), float(dt), float(T), _ptr(Bv)))
+
+    def energy_forces_fields(self, want_virial=True):
+        E = np.zeros(1)
+        F = np.zeros((self.n, 3))
+        H = np.zeros((self.n, 3))
+        W = np.zeros(9) if want_virial else None
+        _check(lib().sl_energy_forces_fields(self.handle, _ptr(E), _ptr(F), _ptr(H), _ptr(W)))
+        return dict(E=float(E[0]), F=F, H=H, W=None if W is None else W.reshape(3, 3))
+
+    def get_descriptors(self):
+        q = np.zeros((self.n, 66))
+        e = np.zeros(self.n)
+        _check(lib().sl_get_descriptors(self.handle, _ptr(q), _ptr(e)))
+        return q, e
+
+    def get_state(self):
+        p, v, s, f, h = (np.zeros((self.n, 3)) for _ in range(5))
+        st = C.c_uint64()
+        _check(lib().sl_get_state(self.handle, _ptr(p), _ptr(v), _ptr(s), _ptr(f), _ptr(h), C.byref(st)))
+        return dict(positions=p, velocities=v, spins=s, forces=f, fields=h, step=int(st.value))
+
+    def set_state(self, positions, velocities, spins, forces=None, fields=None, step=0):
+        p, v, s = _f64(positions), _f64(velocities), _f64(spins)
+        f = None if forces is None else _f64(forces)
+        h = None if fields is None else _f64(fields)
+        _check(lib().sl_set_state(self.handle, _ptr(p), _ptr(v), _ptr(s), _ptr(f), _ptr(h), int(step)))
+
+    def get_neighbors(self, cap=256):
+        cr = np.zeros(self.n, np.int32)
+        ca = np.zeros(self.n, np.int32)
+        lr = np.zeros((self.n, cap), np.int32)
+        la = np.zeros((self.n, cap), np.int32)
+        _check(lib().sl_get_neighbors(self.handle, cap, _ptr(cr), _ptr(lr), _ptr(ca), _ptr(la)))
+        return [lr[i, :cr[i]].copy() for i in range(self.n)], [la[i, :ca[i]].copy() for i in range(self.n)]
+
+    def info(self):
+        n, p, b, k = C.c_int64(), C.c_int32(), C.c_int64(), C.c_int64()
+        _check(lib().sl_get_info(self.handle, C.byref(n), C.byref(p), C.byref(b), C.byref(k)))
+        return dict(n_atoms=n.value, precision=p.value, n_builds=b.value, n_launches=k.value)
+
+    def step_profiled(self, n_steps: int, dt: float, T: float, B=(0.0, 0.0, 0.0)):
+        """Steps without graphs, CUDA-event timed per kernel group; returns {group: ms summed}."""
+        Bv = _f64(B)
+        ms = np.zeros(len(KERNEL_GROUPS))
+        _check(lib().sl_step_profiled(self.handle, int(n_steps), float(dt), float(T), _ptr(Bv), _ptr(ms)))
+        return dict(zip(KERNEL_GROUPS, ms.tolist()))
+
+    def stream(self) -> int:
+        return int(lib().sl_get_stream(self.handle) or 0)
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            lib().sl_destroy_system(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Replicas stepped together (sl_batch_*)."""
+
+    def __init__(self, systems):
+        self.systems = list(systems)
+        arr = (C.c_void_p * len(self.systems))(*[s.handle for s in self.systems])
+        h = C.c_void_p()
+        _check(lib().sl_batch_create(arr, len(self.systems), C.byref(h)))
+        self.handle = h
+
+    def step(self, n_steps, dt, T, B):
+        k = len(self.systems)
+        ns = np.ascontiguousarray(np.broadcast_to(n_steps, (k,)), dtype=np.int64)
+        d = np.ascontiguousarray(np.broadcast_to(dt, (k,)), dtype=np.float64)
+        t = np.ascontiguousarray(np.broadcast_to(T, (k,)), dtype=np.float64)
+        b = np.ascontiguousarray(np.broadcast_to(np.asarray(B, dtype=np.float64), (k, 3)))
+        _check(lib().sl_batch_step(self.handle, _ptr(ns), _ptr(d), _ptr(t), _ptr(b)))
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            lib().sl_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def sl_create_system(*args, **kw) -> System:
+    return System(*args, **kw)
+
+
+def sl_selftest_harmonics(n_samples=1000):
+    a, g = C.c_double(), C.c_double()
+    _check(lib().sl_selftest_harmonics(int(n_samples), C.byref(a), C.byref(g)))
+    return a.value, g.value
+
+
+def sl_measure_fma_peak(precision=SL_PREC_MIXED):
+    """(FLOP/s, elapsed ms) of the FMA microbenchmark on the current device."""
+    f, t = C.c_double(), C.c_double()
+    _check(lib().sl_measure_fma_peak(int(precision), C.byref(f), C.byref(t)))
+    return f.value, t.value
+
+
+def system_from_workload(wl, params: dict, **kw) -> System:
+    return System(wl.positions, wl.spins, wl.box, wl.periodic, wl.species, params, wl.velocities,
+                  seed=kw.pop("seed", wl.seed), **kw)

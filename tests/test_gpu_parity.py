@@ -1,0 +1,242 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances:
+  FP64 mode   |gpu - oracle| <= 1e-10 * max|oracle| per output array (E, F, H, W, q);
+              trajectories: 1e-9 after 100 steps (chaotic growth of the 1e-16
+              rounding differences over 100 fs stays far below that).
+  mixed mode  RMSE(F) <= 1e-3 eV/A and RMSE(H) <= 1e-3 eV against the oracle.
+  neighbours  bit-exact sets.
+Sizes span several thread blocks and end in ragged tails (512, 1728, 1725, slab).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2606_14073_gb300 import nep_params, spinlat as S, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def params():
+    return nep_params.load()
+
+
+@pytest.fixture(scope="module")
+def model(params):
+    return O.Model(params)
+
+
+def ragged_cube(cells=6, drop=3, seed=71):
+    wl = W.fege_cube(cells, seed=seed)
+    keep = np.ones(wl.n, bool)
+    keep[np.random.default_rng(seed).choice(wl.n, drop, replace=False)] = False
+    wl.positions, wl.spins, wl.species, wl.velocities = (wl.positions[keep], wl.spins[keep], wl.species[keep],
+                                                         wl.velocities[keep])
+    return wl
+
+
+def small_slab():
+    return W.fege_slab_helix(8, 8, 3, vacuum=6.0, period_target=37.6, B_z=0.2, seed=72)
+
+
+WORKLOADS = {
+    "b20_512": lambda: W.fege_small(),
+    "b20_1728": lambda: W.fege_cube(6, seed=70),
+    "b20_1725_ragged": lambda: ragged_cube(),
+    "slab_1536_free_z": small_slab,
+}
+
+
+def gpu_state(sys_):
+    st = sys_.get_state()
+    return st["positions"], st["spins"]
+
+
+def maxrel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_neighbor_lists_bit_exact(params, name):
+    wl = WORKLOADS[name]()
+    s = S.system_from_workload(wl, params)
+    pos, _ = gpu_state(s)
+    rad, ang = s.get_neighbors()
+    ref_r = O.neighbors(pos, wl.box, wl.periodic, 7.0, method=0 if wl.n <= 2000 else 1)
+    ref_a = O.neighbors(pos, wl.box, wl.periodic, 5.0, method=0 if wl.n <= 2000 else 1)
+    assert all(np.array_equal(a, b) for a, b in zip(rad, ref_r))
+    assert all(np.array_equal(a, b) for a, b in zip(ang, ref_a))
+    s.destroy()
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_descriptors_fp64(params, model, name):
+    wl = WORKLOADS[name]()
+    s = S.system_from_workload(wl, params)
+    pos, spin = gpu_state(s)
+    q, e = s.get_descriptors()
+    qr = O.descriptors(model, pos, spin, wl.species, wl.box, wl.periodic)
+    scale = np.maximum(np.abs(qr).max(0), 1e-12)
+    assert (np.abs(q - qr) / scale).max() <= FP64_TOL
+    ref = O.evaluate(model, pos, spin, wl.species, wl.box, wl.periodic)
+    assert maxrel(e, ref["Ei"]) <= FP64_TOL
+    s.destroy()
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_energy_forces_fields_virial_fp64(params, model, name):
+    wl = WORKLOADS[name]()
+    B = (0.3, -0.7, 1.1)
+    s = S.system_from_workload(wl, params)
+    s.step(0, 1.0, 0.0, B)   # sets the field used by the evaluation
+    pos, spin = gpu_state(s)
+    r = s.energy_forces_fields()
+    ref = O.evaluate(model, pos, spin, wl.species, wl.box, wl.periodic, B)
+    assert abs(r["E"] - ref["E"]) <= FP64_TOL * max(abs(ref["E"]), np.abs(ref["Ei"]).sum())
+    assert maxrel(r["F"], ref["F"]) <= FP64_TOL
+    assert maxrel(r["H"], ref["H"]) <= FP64_TOL
+    assert maxrel(r["W"], ref["W"]) <= FP64_TOL
+    s.destroy()
+
+
+def test_fp64_trajectory_100_steps(params, model):
+    """512-atom FeGe, 100 Langevin steps of 1 fs at 300 K: GPU vs oracle integrator."""
+    wl = W.fege_small()
+    B = (0.0, 0.0, 0.0)
+    s = S.system_from_workload(wl, params, steps_per_graph=10)
+    st = s.get_state()
+    o = O.State(st["positions"], st["velocities"], st["spins"], wl.species, wl.box, wl.periodic)
+    o.F, o.H, o.have_fh = st["forces"].copy(), st["fields"].copy(), True
+    assert maxrel(st["forces"], O.evaluate(model, o.pos, o.spin, wl.species, wl.box, wl.periodic)["F"]) <= FP64_TOL
+    for chunk in (1, 9, 40, 50):
+        s.step(chunk, wl.dt, wl.T, B)
+        O.run(model, o, chunk, wl.dt, wl.T, B, gamma=0.01, lam=0.1, seed=wl.seed, replica=0)
+        g = s.get_state()
+        d = g["positions"] - o.pos
+        d -= wl.box * np.rint(d / wl.box)
+        assert np.abs(d).max() < 1e-9, (chunk, np.abs(d).max())
+        assert np.abs(g["spins"] - o.spin).max() < 1e-9
+        assert maxrel(g["velocities"], o.vel) < 1e-9
+        assert np.abs(np.linalg.norm(g["spins"], axis=1) - 1).max() < 1e-14
+    assert g["step"] == 100
+    s.destroy()
+
+
+@pytest.mark.parametrize("name", ["b20_512", "b20_1728", "slab_1536_free_z"])
+def test_mixed_precision_force_field_error(params, model, name):
+    wl = WORKLOADS[name]()
+    B = (0.0, 0.0, 0.5)
+    s = S.system_from_workload(wl, params, precision=S.SL_PREC_MIXED)
+    s.step(0, 1.0, 0.0, B)
+    pos, spin = gpu_state(s)
+    r = s.energy_forces_fields()
+    ref = O.evaluate(model, pos, spin, wl.species, wl.box, wl.periodic, B)
+    rmse_f = np.sqrt(((r["F"] - ref["F"]) ** 2).mean())
+    rmse_h = np.sqrt(((r["H"] - ref["H"]) ** 2).mean())
+    assert rmse_f <= 1e-3 and rmse_h <= 1e-3, (rmse_f, rmse_h)
+    assert abs(r["E"] - ref["E"]) / wl.n <= 1e-4
+    s.destroy()
+
+
+def test_mixed_trajectory_stays_close(params, model):
+    wl = W.fege_small()
+    s = S.system_from_workload(wl, params, precision=S.SL_PREC_MIXED)
+    st = s.get_state()
+    o = O.State(st["positions"], st["velocities"], st["spins"], wl.species, wl.box, wl.periodic)
+    o.F, o.H, o.have_fh = st["forces"].copy(), st["fields"].copy(), True
+    s.step(20, 1.0, 300.0, (0, 0, 0))
+    O.run(model, o, 20, 1.0, 300.0, (0, 0, 0), seed=wl.seed)
+    g = s.get_state()
+    d = g["positions"] - o.pos
+    d -= wl.box * np.rint(d / wl.box)
+    assert np.abs(d).max() < 1e-3
+    assert np.abs(g["spins"] - o.spin).max() < 1e-3
+    assert np.abs(np.linalg.norm(g["spins"], axis=1) - 1).max() < 1e-14
+
+
+@pytest.mark.parametrize("prec", [S.SL_PREC_FP64, S.SL_PREC_MIXED])
+def test_determinism_and_bit_identical_resume(params, prec):
+    wl = W.fege_small()
+    a = S.system_from_workload(wl, params, precision=prec)
+    a.step(30, 1.0, 300.0, (0, 0, 0.2))
+    ga = a.get_state()
+    b = S.system_from_workload(wl, params, precision=prec)
+    b.step(12, 1.0, 300.0, (0, 0, 0.2))
+    ck = b.get_state()
+    # resume in a fresh system (different internal order) from the checkpoint
+    c = S.system_from_workload(wl, params, precision=prec)
+    c.set_state(ck["positions"], ck["velocities"], ck["spins"], ck["forces"], ck["fields"], ck["step"])
+    c.step(18, 1.0, 300.0, (0, 0, 0.2))
+    gc = c.get_state()
+    b.step(18, 1.0, 300.0, (0, 0, 0.2))
+    gb = b.get_state()
+    for k in ("positions", "velocities", "spins", "forces", "fields"):
+        assert np.array_equal(ga[k], gb[k]), k
+        assert np.array_equal(ga[k], gc[k]), k
+    for x in (a, b, c):
+        x.destroy()
+
+
+def test_graphs_match_direct_launches(params):
+    wl = W.fege_small()
+    a = S.system_from_workload(wl, params, steps_per_graph=0)
+    b = S.system_from_workload(wl, params, steps_per_graph=7)
+    a.step(23, 1.0, 300.0, (0, 0, 0))
+    b.step(23, 1.0, 300.0, (0, 0, 0))
+    ga, gb = a.get_state(), b.get_state()
+    for k in ("positions", "velocities", "spins"):
+        assert np.array_equal(ga[k], gb[k])
+
+
+def test_batch_equals_alone(params):
+    wls = [W.fege_cube(4, seed=80 + i, replica=i) for i in range(3)]
+    alone = []
+    for w in wls:
+        s = S.system_from_workload(w, params, replica=w.seed - W.LANGEVIN_SEED0)
+        s.step(15, 1.0, 200.0, (0, 0, 0.3))
+        alone.append(s.get_state())
+        s.destroy()
+    syss = [S.system_from_workload(w, params, replica=w.seed - W.LANGEVIN_SEED0) for w in wls]
+    b = S.Batch(syss)
+    b.step(15, 1.0, 200.0, (0, 0, 0.3))
+    for s, ref in zip(syss, alone):
+        g = s.get_state()
+        assert np.array_equal(g["positions"], ref["positions"]) and np.array_equal(g["spins"], ref["spins"])
+
+
+def test_empty_and_tiny_systems(params, model):
+    box = np.array([30.0, 30.0, 30.0])
+    s = S.System(np.zeros((0, 3)), np.zeros((0, 3)), box, [0, 0, 0], np.zeros(0, np.int32), params)
+    s.step(3, 1.0, 300.0, (0, 0, 1.0))
+    r = s.energy_forces_fields()
+    assert r["E"] == 0.0 and r["F"].shape == (0, 3)
+    s.destroy()
+    pos = np.array([[10.0, 10.0, 10.0], [12.5, 10.3, 9.6]])
+    spin = np.array([[0, 0, 1.0], [0.6, 0.0, 0.8]])
+    s = S.System(pos, spin, box, [0, 0, 0], np.array([0, 1], np.int32), params)
+    r = s.energy_forces_fields()
+    ref = O.evaluate(model, pos, spin, np.array([0, 1], np.int32), box, np.array([0, 0, 0], np.int32))
+    assert maxrel(r["F"], ref["F"]) <= FP64_TOL and maxrel(r["H"], ref["H"]) <= FP64_TOL
+    s.destroy()
+
+
+def test_neighbor_overflow_is_reported_and_state_restored(params):
+    wl = W.fege_small()
+    c = wl.box / 2
+    d = wl.positions - c
+    vel = -0.02 * d                     # inward flow: the centre densifies within a few dozen fs
+    s = S.System(wl.positions, wl.spins, wl.box, wl.periodic, wl.species, params, vel, cap_rad=128, cap_ang=48,
+                 gamma=0.0, steps_per_graph=0)
+    before = None
+    with pytest.raises(S.SpinlatError) as e:
+        for _ in range(60):
+            before = s.get_state()
+            s.step(5, 1.0, 0.0, (0, 0, 0))
+    assert e.value.code == S.SL_ENBR_OVERFLOW
+    after = s.get_state()
+    for k in ("positions", "velocities", "spins", "forces", "fields"):
+        assert np.array_equal(after[k], before[k]), k
+    assert after["step"] == before["step"]

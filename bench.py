@@ -197,6 +197,31 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm
+def run_e2e(args, sysm, wl, world, barrier, dist, torch):
+    st = sysm.get_state()
+    host = {k: torch.from_numpy(np.ascontiguousarray(st[k])).pin_memory().numpy()
+            for k in ("positions", "velocities", "spins", "forces", "fields", "ref_positions")}
+    barrier()
+    t0 = time.perf_counter()
+    sysm.set_state(host["positions"], host["velocities"], host["spins"], host["forces"], host["fields"], st["step"],
+                   ref_positions=host["ref_positions"])
+    sysm.step(args.steps, DT, TEMP, FIELD)
+    out = sysm.get_state()
+    t1 = time.perf_counter()
+    e2e_s = t1 - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = sum(host[k].nbytes for k in host)
+    d2h = sum(out[k].nbytes for k in ("positions", "velocities", "spins", "forces", "fields", "ref_positions"))
+    e2e = {"value": wl.n * args.steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "path": "sl_set_state(host) + sl_step(K) + sl_get_state(host), wall clock"}
+
+    return e2e
+
+
 def run_ours(args):
     import torch
     from paper_2606_14073_gb300 import flops, nep_params, spinlat as S, workloads as W
@@ -208,7 +233,9 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     params = nep_params.load()
-    wl = W.fege_884k()
+    wl = W.fege_884k() if args.cells == 48 else W.fege_cube(args.cells, T=TEMP, spin_mode="canted",
+                                                            seed=W.STRUCTURE_SEED0 + 2, n_steps=1,
+                                                            name=f"fege_b20_{args.cells}c")
     replica = rank
     stream = torch.cuda.Stream(device=local)
     sysm = S.system_from_workload(wl, params, precision=S.SL_PREC_MIXED, replica=replica, stream=stream.cuda_stream,
@@ -270,7 +297,7 @@ def run_ours(args):
     # per-kernel device times (CUDA events between the kernel groups, same stream, no graphs)
     prof = sysm.step_profiled(args.profile_steps, DT, TEMP, FIELD)
     total = sum(prof.values())
-    n_r, n_a = neighbour_counts(W.fege_884k())
+    n_r, n_a = neighbour_counts(wl)
     fl = flops.per_atom(n_r, n_a)
     dom = max(("descriptor", "network", "backward"), key=lambda k: prof[k])
     launch_ms = prof[dom] / args.profile_steps
@@ -288,26 +315,11 @@ def run_ours(args):
     shares = {k: v / total for k, v in prof.items()}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    st = sysm.get_state()
-    host = {k: torch.from_numpy(np.ascontiguousarray(st[k])).pin_memory().numpy()
-            for k in ("positions", "velocities", "spins", "forces", "fields")}
-    barrier()
-    t0 = time.perf_counter()
-    sysm.set_state(host["positions"], host["velocities"], host["spins"], host["forces"], host["fields"], st["step"])
-    sysm.step(args.steps, DT, TEMP, FIELD)
-    out = sysm.get_state()
-    t1 = time.perf_counter()
-    e2e_s = t1 - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    h2d = sum(host[k].nbytes for k in host)
-    d2h = sum(out[k].nbytes for k in ("positions", "velocities", "spins", "forces", "fields"))
-    e2e = {"value": wl.n * args.steps * world / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-           "path": "sl_set_state(host) + sl_step(K) + sl_get_state(host), wall clock"}
+    e2e = None
+    if not args.skip_e2e:
+        e2e = run_e2e(args, sysm, wl, world, barrier, dist, torch)
 
+    cpu = None
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu_baseline:
         from oracle import oracle as O
@@ -323,7 +335,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32 descriptor/backward, f32 network, f64 state/integration",
                 "data": "synthetic (seeded FeGe B20, random-init NEP of the paper's shape)",
-                "config": {"workload": WORKLOAD, "atoms": wl.n, "precision": "mixed", "dt_fs": DT, "T_K": TEMP,
+                "config": {"workload": WORKLOAD if args.cells == 48 else wl.name, "atoms": wl.n, "precision": "mixed", "dt_fs": DT, "T_K": TEMP,
                            "B_T": list(FIELD), "steps_per_graph": args.graph_steps,
                            "l2": "inputs larger than L2 (~10 GB working set)", "parallelism": f"replicas x{world}"},
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
@@ -346,6 +358,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--cells", type=int, default=48, help="B20 cells per side (48: the benchmark workload; "
+                                                           "smaller values are for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

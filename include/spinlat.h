@@ -119,16 +119,23 @@ int sl_energy_forces_fields(sl_system *sys, double *energy_eV, double *forces, d
  * order; either may be NULL.  Evaluated at the current state. */
 int sl_get_descriptors(sl_system *sys, double *q, double *atom_energy);
 
-/* Copy the state out (any pointer may be NULL).  forces/fields are the carried
- * values of the integrator (evaluated at the last predicted spins). */
+/* Copy the state out (any pointer may be NULL), all [n][3] in caller order.
+ * forces/fields are the carried values of the integrator (evaluated at the last
+ * predicted spins); ref_positions are the positions the current neighbour lists
+ * were built from (they fix the list segments and so the summation order). */
 int sl_get_state(const sl_system *sys, double *positions, double *velocities, double *spins,
-                 double *forces, double *fields, uint64_t *step);
+                 double *forces, double *fields, double *ref_positions, uint64_t *step);
 
 /* Replace the state.  positions/velocities/spins may not be NULL.  If forces and
- * fields are both given they become the carried integrator values (bit-identical
- * resume); if both are NULL they are re-evaluated at the new state. */
+ * fields are both given they become the carried integrator values; if both are
+ * NULL they are re-evaluated at the new state.  Spins off unit length by more than
+ * rounding are normalised.  ref_positions (may be NULL): the
+ * lists are rebuilt from these positions instead of the new ones.  Given the
+ * forces, fields and ref_positions of sl_get_state, the continued trajectory is
+ * bit-identical to the uninterrupted one, in this or in any other system. */
 int sl_set_state(sl_system *sys, const double *positions, const double *velocities,
-                 const double *spins, const double *forces, const double *fields, uint64_t step);
+                 const double *spins, const double *forces, const double *fields,
+                 const double *ref_positions, uint64_t step);
 
 /* Neighbour candidate lists of the current build, caller indices, ascending:
  * counts_rad[n], lists_rad[n][cap] (d2 < (rc_rad+skin)^2) and counts_ang[n],

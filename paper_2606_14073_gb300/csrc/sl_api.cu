@@ -170,18 +170,25 @@ int check_status(sl::Sys &s) {
 int upload_vec(sl::Sys &s, double4 *dst, const double *src, bool normalise) {
     std::vector<double4> h((size_t)s.n);
     std::vector<int32_t> orig((size_t)s.n);
-    CK(cudaMemcpy(orig.data(), s.orig, sizeof(int32_t) * s.n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(orig.data(), s.orig, sizeof(int32_t) * s.n, cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaStreamSynchronize(s.stream));
     for (int64_t i = 0; i < s.n; ++i) {
         const double *p = src + 3 * (int64_t)orig[i];
         double x = p[0], y = p[1], z = p[2];
         if (normalise) {
-            const double nn = std::sqrt(x * x + y * y + z * z);
-            if (!(nn > 0)) return fail(SL_EINVAL, "zero spin vector");
-            x /= nn; y /= nn; z /= nn;
+            // spins that are unit to rounding are kept bit for bit (exact resume)
+            const double n2 = x * x + y * y + z * z;
+            if (!(n2 > 0)) return fail(SL_EINVAL, "zero spin vector");
+            if (std::fabs(n2 - 1.0) > 1e-13) {
+                const double nn = std::sqrt(n2);
+                x /= nn; y /= nn; z /= nn;
+            }
         }
         h[i] = make_double4(x, y, z, 0.0);
     }
-    CK(cudaMemcpy(dst, h.data(), sizeof(double4) * s.n, cudaMemcpyHostToDevice));
+    // ordered on the system's stream; synchronised before the host buffer is released
+    CK(cudaMemcpyAsync(dst, h.data(), sizeof(double4) * s.n, cudaMemcpyHostToDevice, s.stream));
+    CK(cudaStreamSynchronize(s.stream));
     return SL_OK;
 }
 
@@ -419,17 +426,21 @@ int sl_create_system(const double *positions, const double *spins, const double 
             for (int a = 0; a < 3; ++a)
                 if (!std::isfinite(positions[3 * c + a])) return bail(fail(SL_EINVAL, "non-finite position"));
         }
-        if ((ce = cudaMemcpy(s.pos, hp.data(), sizeof(double4) * N, cudaMemcpyHostToDevice)) ||
-            (ce = cudaMemcpy(s.vel, hv.data(), sizeof(double4) * N, cudaMemcpyHostToDevice)) ||
-            (ce = cudaMemcpy(s.spin, hs.data(), sizeof(double4) * N, cudaMemcpyHostToDevice)) ||
-            (ce = cudaMemcpy(s.species, spec.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice)) ||
-            (ce = cudaMemcpy(s.orig, order.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice)) ||
-            (ce = cudaMemcpy(s.inv, inv.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice)) ||
-            (ce = cudaMemset(s.cells.count, 0, sizeof(int) * s.cells.ncell)) ||
-            (ce = cudaMemset(s.cells.fill, 0, sizeof(int) * s.cells.ncell)) ||
-            (ce = cudaMemset(s.status, 0, sizeof(int))) || (ce = cudaMemset(s.rebuild, 0, sizeof(int))) ||
-            (ce = cudaMemset(s.d_step, 0, 2 * sizeof(unsigned long long))) ||
-            (ce = cudaMemset(s.d_builds, 0, sizeof(unsigned long long))))
+        // every copy on the system's stream (a non-blocking stream is not ordered
+        // against the legacy default stream), then one synchronisation
+        cudaStream_t st = s.stream;
+        if ((ce = cudaMemcpyAsync(s.pos, hp.data(), sizeof(double4) * N, cudaMemcpyHostToDevice, st)) ||
+            (ce = cudaMemcpyAsync(s.vel, hv.data(), sizeof(double4) * N, cudaMemcpyHostToDevice, st)) ||
+            (ce = cudaMemcpyAsync(s.spin, hs.data(), sizeof(double4) * N, cudaMemcpyHostToDevice, st)) ||
+            (ce = cudaMemcpyAsync(s.species, spec.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st)) ||
+            (ce = cudaMemcpyAsync(s.orig, order.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st)) ||
+            (ce = cudaMemcpyAsync(s.inv, inv.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st)) ||
+            (ce = cudaMemsetAsync(s.cells.count, 0, sizeof(int) * s.cells.ncell, st)) ||
+            (ce = cudaMemsetAsync(s.cells.fill, 0, sizeof(int) * s.cells.ncell, st)) ||
+            (ce = cudaMemsetAsync(s.status, 0, sizeof(int), st)) || (ce = cudaMemsetAsync(s.rebuild, 0, sizeof(int), st)) ||
+            (ce = cudaMemsetAsync(s.d_step, 0, 2 * sizeof(unsigned long long), st)) ||
+            (ce = cudaMemsetAsync(s.d_builds, 0, sizeof(unsigned long long), st)) ||
+            (ce = cudaStreamSynchronize(st)))
             return bail(cuda_fail(ce, "upload"));
     }
     const double B0[3] = {0, 0, 0};
@@ -543,7 +554,7 @@ int sl_get_descriptors(sl_system *sys, double *q, double *atom_energy) {
 }
 
 int sl_get_state(const sl_system *sys, double *pos, double *vel, double *spins, double *forces, double *fields,
-                 uint64_t *step) {
+                 double *ref, uint64_t *step) {
     if (!sys) return fail(SL_EINVAL, "NULL system");
     const sl::Sys &s = sys->s;
     cudaSetDevice(s.device);
@@ -554,13 +565,14 @@ int sl_get_state(const sl_system *sys, double *pos, double *vel, double *spins, 
         if (spins && (rc = download_vec(s, s.spin, spins))) return rc;
         if (forces && (rc = download_vec(s, s.F, forces))) return rc;
         if (fields && (rc = download_vec(s, s.H, fields))) return rc;
+        if (ref && (rc = download_vec(s, s.posref, ref))) return rc;
     }
     if (step) *step = s.step;
     return SL_OK;
 }
 
 int sl_set_state(sl_system *sys, const double *pos, const double *vel, const double *spins, const double *forces,
-                 const double *fields, uint64_t step) {
+                 const double *fields, const double *ref, uint64_t step) {
     if (!sys) return fail(SL_EINVAL, "NULL system");
     sl::Sys &s = sys->s;
     cudaSetDevice(s.device);
@@ -570,27 +582,29 @@ int sl_set_state(sl_system *sys, const double *pos, const double *vel, const dou
     CK(cudaStreamSynchronize(s.stream));
     if (s.n > 0) {
         for (int64_t i = 0; i < 3 * s.n; ++i)
-            if (!std::isfinite(pos[i]) || !std::isfinite(vel[i]) || !std::isfinite(spins[i]))
+            if (!std::isfinite(pos[i]) || !std::isfinite(vel[i]) || !std::isfinite(spins[i]) ||
+                (ref && !std::isfinite(ref[i])))
                 return fail(SL_EINVAL, "non-finite state value");
-        if ((rc = upload_vec(s, s.pos, pos, false)) || (rc = upload_vec(s, s.vel, vel, false)) ||
-            (rc = upload_vec(s, s.spin, spins, true)))
-            return rc;
+        if ((rc = upload_vec(s, s.vel, vel, false)) || (rc = upload_vec(s, s.spin, spins, true))) return rc;
+        // lists from the reference positions (k_finish records them as the new reference)
+        if ((rc = upload_vec(s, s.pos, ref ? ref : pos, false)) || (rc = refresh_copies(s))) return rc;
+        CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
+        sl::launch_rebuild(s, false);
+        s.n_builds++;
+        if (ref && ((rc = upload_vec(s, s.pos, pos, false)) || (rc = refresh_copies(s)))) return rc;
     }
     s.step = step;
     unsigned long long st[2] = {step, step};
-    CK(cudaMemcpy(s.d_step, st, sizeof st, cudaMemcpyHostToDevice));
-    CK(cudaMemset(s.status, 0, sizeof(int)));
-    if ((rc = refresh_copies(s))) return rc;
-    if (forces) {
-        if (s.n > 0 && ((rc = upload_vec(s, s.F, forces, false)) || (rc = upload_vec(s, s.H, fields, false)))) return rc;
-        if (s.n > 0) {
-            sl::launch_rebuild(s, false);
-            s.n_builds++;
+    CK(cudaMemcpyAsync(s.d_step, st, sizeof st, cudaMemcpyHostToDevice, s.stream));
+    CK(cudaStreamSynchronize(s.stream));
+    if (s.n > 0) {
+        if (forces) {
+            if ((rc = upload_vec(s, s.F, forces, false)) || (rc = upload_vec(s, s.H, fields, false))) return rc;
+        } else if ((rc = evaluate(s, false, true, false))) {
+            return rc;
         }
-        CK(cudaGetLastError());
-    } else if ((rc = evaluate(s, true, true, false))) {
-        return rc;
     }
+    CK(cudaGetLastError());
     return check_status(s);
 }
 
@@ -608,9 +622,10 @@ int sl_get_neighbors(sl_system *sys, int32_t cap, int32_t *counts_rad, int32_t *
     const size_t N = (size_t)s.n;
     std::vector<int32_t> nbr(N * s.cap), orig(N);
     std::vector<int4> seg(N);
-    CK(cudaMemcpy(nbr.data(), s.nbr, sizeof(int32_t) * N * s.cap, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(orig.data(), s.orig, sizeof(int32_t) * N, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(seg.data(), s.seg, sizeof(int4) * N, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(nbr.data(), s.nbr, sizeof(int32_t) * N * s.cap, cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaMemcpyAsync(orig.data(), s.orig, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaMemcpyAsync(seg.data(), s.seg, sizeof(int4) * N, cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaStreamSynchronize(s.stream));
     bool over = false;
     for (size_t i = 0; i < N; ++i) {
         const int c = orig[i];

@@ -64,8 +64,8 @@ def lib(path: str | None = None):
             L.sl_step.argtypes = [P, I64, D, D, P]
             L.sl_energy_forces_fields.argtypes = [P, P, P, P, P]
             L.sl_get_descriptors.argtypes = [P, P, P]
-            L.sl_get_state.argtypes = [P, P, P, P, P, P, P]
-            L.sl_set_state.argtypes = [P, P, P, P, P, P, C.c_uint64]
+            L.sl_get_state.argtypes = [P, P, P, P, P, P, P, P]
+            L.sl_set_state.argtypes = [P, P, P, P, P, P, P, C.c_uint64]
             L.sl_get_neighbors.argtypes = [P, I32, P, P, P, P]
             L.sl_get_info.argtypes = [P, P, P, P, P]
             L.sl_step_profiled.argtypes = [P, I64, D, D, P, P]
@@ -173,16 +173,17 @@ class System:
         return q, e
 
     def get_state(self):
-        p, v, s, f, h = (np.zeros((self.n, 3)) for _ in range(5))
+        p, v, s, f, h, r = (np.zeros((self.n, 3)) for _ in range(6))
         st = C.c_uint64()
-        _check(lib().sl_get_state(self.handle, _ptr(p), _ptr(v), _ptr(s), _ptr(f), _ptr(h), C.byref(st)))
-        return dict(positions=p, velocities=v, spins=s, forces=f, fields=h, step=int(st.value))
+        _check(lib().sl_get_state(self.handle, _ptr(p), _ptr(v), _ptr(s), _ptr(f), _ptr(h), _ptr(r), C.byref(st)))
+        return dict(positions=p, velocities=v, spins=s, forces=f, fields=h, ref_positions=r, step=int(st.value))
 
-    def set_state(self, positions, velocities, spins, forces=None, fields=None, step=0):
+    def set_state(self, positions, velocities, spins, forces=None, fields=None, step=0, ref_positions=None):
         p, v, s = _f64(positions), _f64(velocities), _f64(spins)
         f = None if forces is None else _f64(forces)
         h = None if fields is None else _f64(fields)
-        _check(lib().sl_set_state(self.handle, _ptr(p), _ptr(v), _ptr(s), _ptr(f), _ptr(h), int(step)))
+        r = None if ref_positions is None else _f64(ref_positions)
+        _check(lib().sl_set_state(self.handle, _ptr(p), _ptr(v), _ptr(s), _ptr(f), _ptr(h), _ptr(r), int(step)))
 
     def get_neighbors(self, cap=256):
         cr = np.zeros(self.n, np.int32)

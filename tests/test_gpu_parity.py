@@ -166,9 +166,12 @@ def test_determinism_and_bit_identical_resume(params, prec):
     b = S.system_from_workload(wl, params, precision=prec)
     b.step(12, 1.0, 300.0, (0, 0, 0.2))
     ck = b.get_state()
-    # resume in a fresh system (different internal order) from the checkpoint
-    c = S.system_from_workload(wl, params, precision=prec)
-    c.set_state(ck["positions"], ck["velocities"], ck["spins"], ck["forces"], ck["fields"], ck["step"])
+    # resume in a fresh system created from the checkpoint positions (its internal
+    # atom order differs) with the checkpoint's carried forces, fields and list reference
+    c = S.System(ck["positions"], ck["spins"], wl.box, wl.periodic, wl.species, params, ck["velocities"],
+                 precision=prec, seed=wl.seed)
+    c.set_state(ck["positions"], ck["velocities"], ck["spins"], ck["forces"], ck["fields"], ck["step"],
+                ref_positions=ck["ref_positions"])
     c.step(18, 1.0, 300.0, (0, 0, 0.2))
     gc = c.get_state()
     b.step(18, 1.0, 300.0, (0, 0, 0.2))
@@ -176,7 +179,16 @@ def test_determinism_and_bit_identical_resume(params, prec):
     for k in ("positions", "velocities", "spins", "forces", "fields"):
         assert np.array_equal(ga[k], gb[k]), k
         assert np.array_equal(ga[k], gc[k]), k
-    for x in (a, b, c):
+    # without the list reference positions the resumed run is the same trajectory up to
+    # summation order (neighbour segments differ), i.e. equal to rounding
+    d = S.system_from_workload(wl, params, precision=prec)
+    d.set_state(ck["positions"], ck["velocities"], ck["spins"], ck["forces"], ck["fields"], ck["step"])
+    d.step(18, 1.0, 300.0, (0, 0, 0.2))
+    gd = d.get_state()
+    dd = gd["positions"] - ga["positions"]
+    dd -= wl.box * np.rint(dd / wl.box)
+    assert np.abs(dd).max() < (1e-9 if prec == S.SL_PREC_FP64 else 1e-3)
+    for x in (a, b, c, d):
         x.destroy()
 
 

@@ -190,6 +190,35 @@ int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt_fs, cons
                   const double *B_tesla /* [k][3] */);
 void sl_batch_destroy(sl_batch *b);
 
+/* ---------------------------------------------------------------- no device allocation
+ * Per-atom descriptors and network energies of a small system, for callers that
+ * cannot allocate device memory: code that runs while its host framework captures
+ * a CUDA graph (allocation is not allowed there), plugins of engines that hand all
+ * device memory to their own pool, and real-time loops that cannot take the
+ * device-wide synchronisation an allocation may imply.  The paper has no
+ * counterpart; this is a service of this library.
+ *   positions4, spins4  DEVICE arrays [n][4] of double (x, y, z, unused)
+ *   species             DEVICE array [n] of int32
+ *   q                   DEVICE output [n][66] (unscaled descriptors) or NULL
+ *   atom_energy         DEVICE output [n] (E_i of the network)
+ *   box, periodic, params  host values as for sl_create_system; along a periodic
+ *                       dim the box must be at least 2 rc_rad
+ *   cuda_stream         cudaStream_t the work is ordered on (NULL: default stream);
+ *                       the call returns after the stream has drained
+ * FP64 throughout, no neighbour skin (an exact all-pairs search inside rc_rad).
+ * The scratch (about 6.3 MB: lists, descriptor columns, angular sums, a status
+ * word) is one fixed array compiled into the library, resident on every GPU that
+ * loads it until the process exits.  No call allocates device memory; n above
+ * 2048 atoms returns SL_EINVAL, more than 160 neighbours inside rc_rad returns
+ * SL_ENBR_OVERFLOW.  The first call on a device looks up the array's device
+ * address (and may load the library's device code); make that first call before
+ * any stream capture.  Every call uses the same array, so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race: serialise them. */
+int sl_descriptors_energies_noalloc(const double *positions4, const double *spins4, const int32_t *species,
+                                    int64_t n, const double box[3], const int32_t periodic[3],
+                                    const sl_nep_params *params, double *q, double *atom_energy,
+                                    void *cuda_stream);
+
 /* ---------------------------------------------------------------- self checks
  * Host-only checks of the kernels' compile-time tables (no GPU needed):
  * max |P_l(u.v) - sum_m kappa_lm p_lm(u) p_lm(v)| and the max finite-difference

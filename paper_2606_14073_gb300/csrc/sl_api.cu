@@ -784,6 +784,47 @@ int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt, const d
 
 void sl_batch_destroy(sl_batch *b) { delete b; }
 
+// ---------------------------------------------------------------- no device allocation
+int sl_descriptors_energies_noalloc(const double *positions4, const double *spins4, const int32_t *species,
+                                    int64_t n, const double box[3], const int32_t periodic[3],
+                                    const sl_nep_params *params, double *q, double *atom_energy, void *cuda_stream) {
+    using namespace sl;
+    if (!box || !periodic || !params) return fail(SL_EINVAL, "box, periodic and params are required");
+    if (n < 0 || n > noalloc_max_atoms())
+        return fail(SL_EINVAL, "n = %lld outside [0, %d], the size limit of the no-allocation scratch", (long long)n,
+                    noalloc_max_atoms());
+    if (n > 0 && (!positions4 || !spins4 || !species || !atom_energy))
+        return fail(SL_EINVAL, "positions4, spins4, species and atom_energy are required");
+    if (params->n_species != NS || params->n_ch != NCH || params->l_max != 4 || params->basis_k != NK ||
+        params->n_hidden != NH || !(params->rc_ang > 0 && params->rc_rad >= params->rc_ang) || !params->coeffs ||
+        !params->q_scaler || !params->w0 || !params->b0 || !params->w1)
+        return fail(SL_EINVAL, "unsupported or incomplete model parameters");
+    BoxDev<double> b;
+    for (int a = 0; a < 3; ++a) {
+        if (!(box[a] > 0)) return fail(SL_EINVAL, "box lengths must be positive");
+        if (periodic[a] && box[a] < 2.0 * params->rc_rad)
+            return fail(SL_EINVAL, "periodic box length %g below 2 rc_rad", box[a]);
+        b.L[a] = box[a];
+        b.invL[a] = periodic[a] ? 1.0 / box[a] : 0.0;
+    }
+    if (n == 0) return SL_OK;
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
+        cudaGetLastError();
+        return fail(SL_ECUDA, "no usable CUDA device");
+    }
+    NepDev<double> P;
+    fill_params(P, params);
+    int st = 0;
+    if (launch_noalloc(P, reinterpret_cast<const double4 *>(positions4), reinterpret_cast<const double4 *>(spins4),
+                       species, (int)n, b, q, atom_energy, (cudaStream_t)cuda_stream, &st)) {
+        cudaError_t e = cudaGetLastError();
+        return fail(SL_ECUDA, "no-allocation evaluation failed: %s", cudaGetErrorString(e));
+    }
+    if (st & ST_NBR_OVERFLOW) return fail(SL_ENBR_OVERFLOW, "more than 160 neighbours inside rc_rad");
+    return SL_OK;
+}
+
 // ---------------------------------------------------------------- self checks
 int sl_selftest_harmonics(int32_t n_samples, double *max_add, double *max_grad) {
     using namespace sl;

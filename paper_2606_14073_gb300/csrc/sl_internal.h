@@ -113,6 +113,9 @@ int reduce_energy_virial(Sys &s, double *E, double *W, bool want_virial);
 
 size_t eval_bytes(const Sys &s);
 void eval_init();
+int launch_noalloc(const NepDev<double> &P, const double4 *pos, const double4 *spin, const int32_t *species, int n,
+                   const BoxDev<double> &box, double *q_out, double *e_out, cudaStream_t stream, int *status_out);
+int noalloc_max_atoms();
 // sl_peak.cu
 int measure_fma_peak(int precision, double *flops_per_s, double *elapsed_ms);
 

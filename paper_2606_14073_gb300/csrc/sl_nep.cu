@@ -21,6 +21,8 @@
 // Atoms are stored species-major, so a warp almost always has one centre species;
 // the neighbour list is segmented by neighbour species, so inside a segment both
 // species are compile-time constants and every coefficient is a constant operand.
+#include <mutex>
+
 #include "sl_internal.h"
 
 namespace sl {
@@ -488,5 +490,142 @@ size_t eval_bytes(const Sys &s) {
     const size_t n = (size_t)s.n;
     return r * n * (2 * DIM + NB + 1 + 9) + r * 4 * n * 2 + r * 6 * n * (size_t)s.cap;
 }
+
+
+// ------------------------------------------------------------------ no-allocation variant
+// Descriptors and network energies of a small system in ONE kernel whose scratch
+// (neighbour lists, list segments, descriptor columns, angular sums, a status
+// word) lives in a fixed file-scope device array instead of memory the caller or
+// the library allocates.  For callers that may not allocate device memory (see
+// sl_descriptors_energies_noalloc in spinlat.h).  Computes in FP64.
+namespace noalloc {
+
+constexpr int MAX_ATOMS = 2048;
+constexpr int MAX_NBR = 160;   // neighbours inside rc_rad per atom
+constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t OFF_NBR = 0;
+constexpr size_t OFF_SEG = align256(OFF_NBR + sizeof(int32_t) * MAX_ATOMS * MAX_NBR);
+constexpr size_t OFF_Q = align256(OFF_SEG + sizeof(int4) * MAX_ATOMS);
+constexpr size_t OFF_B = align256(OFF_Q + sizeof(double) * DIM * MAX_ATOMS);
+constexpr size_t OFF_STATUS = align256(OFF_B + sizeof(double) * NB * MAX_ATOMS);
+constexpr size_t BYTES = align256(OFF_STATUS + sizeof(int));
+
+// ~6.3 MB, held by every GPU that loads the library until the process exits.
+static __device__ __align__(256) unsigned char g_scratch[BYTES];
+
+__global__ void __launch_bounds__(128) k_eval_noalloc(const __grid_constant__ NepDev<double> P,
+                                                      const double4 *__restrict__ pos,
+                                                      const double4 *__restrict__ spin,
+                                                      const int32_t *__restrict__ species, int n, BoxDev<double> box,
+                                                      unsigned char *scratch, double *__restrict__ q_out,
+                                                      double *__restrict__ e_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t *nbr = reinterpret_cast<int32_t *>(scratch + OFF_NBR);
+    int4 *seg = reinterpret_cast<int4 *>(scratch + OFF_SEG);
+    double *q = reinterpret_cast<double *>(scratch + OFF_Q);
+    double *bsum = reinterpret_cast<double *>(scratch + OFF_B);
+    int *status = reinterpret_cast<int *>(scratch + OFF_STATUS);
+    // brute-force neighbours inside rc_rad, inserted in (segment, index) order
+    // straight into this atom's scratch column (slot-major, stride n)
+    const double4 pi = pos[i];
+    int m = 0;
+    bool overflow = false;
+    for (int j = 0; j < n; ++j) {
+        if (j == i) continue;
+        const double4 pj = pos[j];
+        double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+        minimg(box, dx, dy, dz);
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        if (!(d2 < P.rc_r2)) continue;
+        if (m >= MAX_NBR) { overflow = true; continue; }
+        const int key = ((d2 < P.rc_a2 ? 0 : 2) + species[j]) * MAX_ATOMS + j;
+        int v = m - 1;
+        while (v >= 0) {
+            const int jv = nbr[(int64_t)v * n + i];
+            const double4 pv = pos[jv];
+            double ex = pv.x - pi.x, ey = pv.y - pi.y, ez = pv.z - pi.z;
+            minimg(box, ex, ey, ez);
+            const int kv = (((ex * ex + ey * ey + ez * ez) < P.rc_a2 ? 0 : 2) + species[jv]) * MAX_ATOMS + jv;
+            if (kv <= key) break;
+            nbr[(int64_t)(v + 1) * n + i] = jv;
+            --v;
+        }
+        nbr[(int64_t)(v + 1) * n + i] = j;
+        ++m;
+    }
+    if (overflow) atomicOr(status, ST_NBR_OVERFLOW);
+    int ends[4] = {0, 0, 0, 0};
+    for (int s = 0; s < m; ++s) {
+        const int j = nbr[(int64_t)s * n + i];
+        const double4 pj = pos[j];
+        double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+        minimg(box, dx, dy, dz);
+        const int sg = ((dx * dx + dy * dy + dz * dz) < P.rc_a2 ? 0 : 2) + species[j];
+        for (int t = sg; t < 4; ++t) ends[t] = s + 1;
+    }
+    for (int t = 1; t < 4; ++t) ends[t] = max(ends[t], ends[t - 1]);
+    seg[i] = make_int4(ends[0], ends[1], ends[2], ends[3]);
+    // descriptor through the same per-atom code as k_fwd
+    EvalArgs<double> a;
+    a.pos = pos; a.spin = spin; a.nbr = nbr; a.seg = seg; a.n = n; a.n_fe = 0; a.box = box;
+    a.q = q; a.bsum = bsum;
+    if (species[i] == 0) fwd_atom<double, 0>(P, a, i);
+    else fwd_atom<double, 1>(P, a, i);
+    // network energy E_i = sum_h w1_h tanh(sum_v W0_hv s_v q_v - b0_h) - b1
+    double x[DIM];
+#pragma unroll
+    for (int v = 0; v < DIM; ++v) {
+        x[v] = q[(int64_t)v * n + i];
+        if (q_out) q_out[(int64_t)i * DIM + v] = x[v];
+        x[v] *= P.scal[v];
+    }
+    double E = -P.b1;
+#pragma unroll 1
+    for (int h = 0; h < NH; ++h) {
+        double z = -P.b0[h];
+#pragma unroll
+        for (int v = 0; v < DIM; ++v) z += P.w0[h][v] * x[v];
+        E += P.w1[h] * tanh(z);
+    }
+    e_out[i] = E;
+}
+
+}  // namespace noalloc
+
+// Device address of the scratch array for the current device, looked up once per
+// device (host code cannot use the symbol itself as a device address).
+int noalloc_scratch(void **out) {
+    static std::mutex mu;
+    static void *addr[128] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return -1;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, noalloc::g_scratch) != cudaSuccess || !p) return -1;
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return 0;
+}
+
+int launch_noalloc(const NepDev<double> &P, const double4 *pos, const double4 *spin, const int32_t *species, int n,
+                   const BoxDev<double> &box, double *q_out, double *e_out, cudaStream_t stream, int *status_out) {
+    void *scratch = nullptr;
+    if (noalloc_scratch(&scratch)) return -1;
+    int *status = reinterpret_cast<int *>(static_cast<unsigned char *>(scratch) + noalloc::OFF_STATUS);
+    if (cudaMemsetAsync(status, 0, sizeof(int), stream) != cudaSuccess) return -1;
+    noalloc::k_eval_noalloc<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(
+        P, pos, spin, species, n, box, static_cast<unsigned char *>(scratch), q_out, e_out);
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    int st = 0;
+    if (cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return -1;
+    *status_out = st;
+    return 0;
+}
+
+int noalloc_max_atoms() { return noalloc::MAX_ATOMS; }
 
 }  // namespace sl

@@ -22,7 +22,7 @@ _NAMES = {SL_EINVAL: "SL_EINVAL", SL_ENOMEM: "SL_ENOMEM", SL_ENBR_OVERFLOW: "SL_
 EXPORTS = ["sl_default_options", "sl_create_system", "sl_step", "sl_energy_forces_fields", "sl_get_descriptors",
            "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_get_stream",
            "sl_destroy_system", "sl_last_error", "sl_batch_create", "sl_batch_step", "sl_batch_destroy",
-           "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak"]
+           "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak", "sl_descriptors_energies_noalloc"]
 KERNEL_GROUPS = ["first_half", "rebuild", "descriptor", "network", "backward", "second_half"]
 
 
@@ -70,6 +70,7 @@ def lib(path: str | None = None):
             L.sl_get_info.argtypes = [P, P, P, P, P]
             L.sl_step_profiled.argtypes = [P, I64, D, D, P, P]
             L.sl_measure_fma_peak.argtypes = [I32, P, P]
+            L.sl_descriptors_energies_noalloc.argtypes = [P, P, P, I64, P, P, P, P, P, P]
             L.sl_get_stream.argtypes = [P]
             L.sl_get_stream.restype = P
             L.sl_destroy_system.argtypes = [P]
@@ -82,7 +83,8 @@ def lib(path: str | None = None):
             L.sl_selftest_harmonics.argtypes = [I32, P, P]
             for f in ("sl_create_system", "sl_step", "sl_energy_forces_fields", "sl_get_descriptors",
                       "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_batch_create",
-                      "sl_batch_step", "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak"):
+                      "sl_batch_step", "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak",
+                      "sl_descriptors_energies_noalloc"):
                 getattr(L, f).restype = C.c_int
             _lib = L
         return _lib
@@ -265,6 +267,19 @@ def sl_measure_fma_peak(precision=SL_PREC_MIXED):
     f, t = C.c_double(), C.c_double()
     _check(lib().sl_measure_fma_peak(int(precision), C.byref(f), C.byref(t)))
     return f.value, t.value
+
+
+def sl_descriptors_energies_noalloc(positions4_ptr: int, spins4_ptr: int, species_ptr: int, n: int, box, periodic,
+                                    params: dict, q_ptr: int | None, energy_ptr: int, stream_ptr: int | None = None):
+    """Descriptors and network energies of a small system without any device
+    allocation.  All *_ptr are device addresses owned by the caller (positions4 and
+    spins4 [n][4] float64, species [n] int32, q [n][66] float64 or None, energy [n]
+    float64); see spinlat.h for the limits and the shared-scratch caveat."""
+    P = NepParams(params)
+    b = _f64(box)
+    per = np.ascontiguousarray(periodic, dtype=np.int32)
+    _check(lib().sl_descriptors_energies_noalloc(positions4_ptr, spins4_ptr, species_ptr, int(n), _ptr(b), _ptr(per),
+                                                 C.byref(P.struct), q_ptr, energy_ptr, stream_ptr))
 
 
 def system_from_workload(wl, params: dict, **kw) -> System:

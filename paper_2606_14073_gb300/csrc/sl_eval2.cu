@@ -1,0 +1,693 @@
+// sl_eval2.cu -- NEP-SPIN evaluation: compacted radial kernels and quad-per-atom angular kernels.
+//
+// Same mathematics as the descriptor of arXiv 2606.14073 (Sections 5.1.1-5.1.2, 5.2.3-5.2.4)
+// described in sl_nep.cu; this file maps it onto the GPU differently:
+//
+//   k_rad_fwd  one thread per atom.  Pass 1 compacts the candidate list (which
+//              carries a skin) into the pairs inside the cutoffs: angular rows
+//              (r < rc_ang) and radial-only rows (rc_ang <= r < rc_rad), each grouped by
+//              neighbour species; pass 2 accumulates the radial and pairwise-magnetic
+//              basis sums over those rows and contracts them with the coefficients
+//              once per neighbour species (q^R, q^EX, q^DMI, q^ANI, q^SIA, q^O).
+//   k_ang_fwd  four lanes per atom.  Each lane stages one angular pair (carrier, g_n,
+//              spin weight, the 24 solid harmonics) in shared memory; then every lane
+//              accumulates B_nlm, BS_nlm for its 6 harmonics over the staged pairs.
+//   k_ang_bwd  four lanes per atom.  The adjoints dE/dB (2 kappa Fp B) stay in
+//              registers, 60 per lane; staged per pair: g_n, g_n', the harmonics and
+//              their gradients.  Lanes contract their harmonics and reduce within the
+//              quad to the pair's angular dE_i/dr_ij and spin weight c_ij.
+//   k_rad_bwd  one thread per atom.  Radial and pairwise-magnetic derivatives per
+//              pair, plus the angular part from k_ang_bwd; writes the pair record
+//              (dE_i/dr_ij, dE_i/dS_j) straight into the slot the neighbour j will
+//              read (its own list slot of i), and the per-atom sums.
+// The force/field gather (sl_integrate.cu) then reads, for atom k, the records of
+// its in-cutoff slots only.
+#include "sl_internal.h"
+#include "sl_eval2.cuh"
+
+namespace sl {
+
+// ------------------------------------------------------------------ helpers
+template <typename R, int TI, int TJ, int G>
+__device__ __forceinline__ void contract_k(const NepDev<R> &P, const R f[NK], R g[NCH]) {
+#pragma unroll
+    for (int n = 0; n < NCH; ++n) {
+        R s = R(0);
+#pragma unroll
+        for (int k = 0; k < NK; ++k) s += P.c[TI][TJ][G][n][k] * f[k];
+        g[n] = s;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void sep(const BoxDev<R> &b, const v4<R> &pi, const v4<R> &pj, R &dx, R &dy, R &dz) {
+    dx = pj.x - pi.x;
+    dy = pj.y - pi.y;
+    dz = pj.z - pi.z;
+    minimg(b, dx, dy, dz);
+}
+
+// per-lane constants of harmonic lm = ql + 4 m (ql = lane in quad)
+__device__ __forceinline__ int lm_of(int ql, int m) { return ql + 4 * m; }
+__device__ __forceinline__ int l_of_lm(int lm) { return lm < 3 ? 1 : lm < 8 ? 2 : lm < 15 ? 3 : 4; }
+template <typename R>
+__device__ __forceinline__ R kappa_of_lm(int lm) {
+    // kappa_lm of the addition theorem, selected at run time (the quad lane picks its harmonics)
+    switch (lm) {
+    case 0: case 1: case 2: return R(1.0);
+    case 3: case 4: case 5: return R(3.0);
+    case 6: return R(0.75);
+    case 7: return R(0.25);
+    case 8: return R(0.625);
+    case 9: return R(15.0);
+    case 10: return R(0.375);
+    case 11: return R(0.25);
+    case 12: return R(0.375);
+    case 13: return R(3.75);
+    case 14: return R(0.625);
+    case 15: return R(8.75);
+    case 16: return R(4.375);
+    case 17: return R(1.25);
+    case 18: return R(0.625);
+    case 19: return R(0.015625);
+    case 20: return R(0.625);
+    case 21: return R(0.3125);
+    case 22: return R(4.375);
+    default: return R(0.546875);
+    }
+}
+
+// ------------------------------------------------------------------ k_rad_fwd
+template <typename R, int TI, int TJ>
+__device__ __forceinline__ void rad_sums(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, const v4<R> &pi,
+                                         const v4<R> &si, int r0, int r1, int r2, int r3, R qr[NCH], R qx[4][NCH]) {
+    R b0[NK], b1[NK], b2[NK], b3[NK], b4[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) { b0[k] = b1[k] = b2[k] = b3[k] = b4[k] = R(0); }
+    const int64_t N = a.n;
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+        const int lo = part ? r2 : r0, hi = part ? r3 : r1;
+        for (int row = lo; row < hi; ++row) {
+            const int j = a.clj[(int64_t)row * N + i];
+            const v4<R> pj = a.pos[j], sj = a.spin[j];
+            R dx, dy, dz;
+            sep(a.box, pi, pj, dx, dy, dz);
+            const R d2 = dx * dx + dy * dy + dz * dz;
+            const R ir = rsqrt_(d2), r = d2 * ir;
+            const R ux = dx * ir, uy = dy * ir, uz = dz * ir;
+            R f[NK];
+            carrier_f(r, P.inv_rc_r, f);
+            const R sij = si.x * sj.x + si.y * sj.y + si.z * sj.z;
+            const R siu = si.x * ux + si.y * uy + si.z * uz;
+            const R sju = sj.x * ux + sj.y * uy + sj.z * uz;
+            const R dmi = (si.y * sj.z - si.z * sj.y) * ux + (si.z * sj.x - si.x * sj.z) * uy +
+                          (si.x * sj.y - si.y * sj.x) * uz;
+            const R ani = siu * sju, sia = siu * siu;
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                b0[k] += f[k];
+                b1[k] += f[k] * sij;
+                b2[k] += f[k] * dmi;
+                b3[k] += f[k] * ani;
+                b4[k] += f[k] * sia;
+            }
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NCH; ++n) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            qr[n] += P.c[TI][TJ][G_R][n][k] * b0[k];
+            qx[0][n] += P.c[TI][TJ][G_EX][n][k] * b1[k];
+            qx[1][n] += P.c[TI][TJ][G_DMI][n][k] * b2[k];
+            qx[2][n] += P.c[TI][TJ][G_ANI][n][k] * b3[k];
+            qx[3][n] += P.c[TI][TJ][G_SIA][n][k] * b4[k];
+        }
+    }
+}
+
+template <typename R, int TI>
+__device__ __forceinline__ void rad_fwd_atom(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i) {
+    const int64_t N = a.n;
+    const v4<R> pi = a.pos[i], si = a.spin[i];
+    const int4 sg = a.seg[i];
+    // pass 1: compaction, neighbour species 0 first (candidate segments 0 and 2), then 1 (1 and 3)
+    int na = 0, nr = 0, na0 = 0, nr0 = 0;
+#pragma unroll 1
+    for (int tj = 0; tj < 2; ++tj) {
+#pragma unroll 1
+        for (int part = 0; part < 2; ++part) {
+            const int lo = part == 0 ? (tj == 0 ? 0 : sg.x) : (tj == 0 ? sg.y : sg.z);
+            const int hi = part == 0 ? (tj == 0 ? sg.x : sg.y) : (tj == 0 ? sg.z : sg.w);
+            for (int s = lo; s < hi; ++s) {
+                const int j = a.nbr[(int64_t)s * N + i];
+                const v4<R> pj = a.pos[j];
+                R dx, dy, dz;
+                sep(a.box, pi, pj, dx, dy, dz);
+                const R d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 < P.rc_r2) {
+                    int row;
+                    if (d2 < P.rc_a2) {
+                        if (na >= a.cap_ang) {   // only after a list overflow; keeps every row in bounds
+                            atomicOr(a.status, ST_NBR_OVERFLOW);
+                            continue;
+                        }
+                        row = na++;
+                    } else {
+                        row = a.cap_ang + nr++;
+                    }
+                    a.clj[(int64_t)row * N + i] = j;
+                    a.cls[(int64_t)row * N + i] = (uint8_t)s;
+                }
+            }
+        }
+        if (tj == 0) { na0 = na; nr0 = nr; }
+    }
+    a.cnt[i] = make_int4(na0, na, nr0, nr);
+    // pass 2: radial and pairwise-magnetic sums over the in-cutoff pairs
+    R qr[NCH], qx[4][NCH];
+#pragma unroll
+    for (int n = 0; n < NCH; ++n) { qr[n] = R(0); qx[0][n] = qx[1][n] = qx[2][n] = qx[3][n] = R(0); }
+    const int ca = a.cap_ang;
+    rad_sums<R, TI, 0>(P, a, i, pi, si, 0, na0, ca, ca + nr0, qr, qx);
+    rad_sums<R, TI, 1>(P, a, i, pi, si, na0, na, ca + nr0, ca + nr, qr, qx);
+#pragma unroll
+    for (int n = 0; n < NCH; ++n) {
+        a.q[(Q_R + n) * N + i] = qr[n];
+        a.q[(Q_EX + n) * N + i] = qx[0][n];
+        a.q[(Q_DMI + n) * N + i] = qx[1][n];
+        a.q[(Q_ANI + n) * N + i] = qx[2][n];
+        a.q[(Q_SIA + n) * N + i] = qx[3][n];
+    }
+    a.q[Q_O * N + i] = si.x * si.x + si.y * si.y + si.z * si.z;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_rad_fwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    if (i < a.n_fe) rad_fwd_atom<R, 0>(P, a, i);
+    else rad_fwd_atom<R, 1>(P, a, i);
+}
+
+// ------------------------------------------------------------------ k_ang_fwd
+// stage of one angular pair: g_n (5), s g_n (5), p_lm (24), pad (2)
+constexpr int FSTAGE = 36;
+constexpr int FQUAD = 4 * FSTAGE + 4;   // per quad, padded so quads start in different banks
+
+template <typename R, int TI, int TJ>
+__device__ __forceinline__ void ang_stage_fwd(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, const v4<R> &pi,
+                                              const v4<R> &si, int p, R *st) {
+    const int j = a.clj[(int64_t)p * a.n + i];
+    const v4<R> pj = a.pos[j], sj = a.spin[j];
+    R dx, dy, dz;
+    sep(a.box, pi, pj, dx, dy, dz);
+    const R d2 = dx * dx + dy * dy + dz * dz;
+    const R ir = rsqrt_(d2), r = d2 * ir;
+    R f[NK], g[NCH];
+    carrier_f(r, P.inv_rc_a, f);
+    contract_k<R, TI, TJ, G_A>(P, f, g);
+    const R s = si.x * sj.x + si.y * sj.y + si.z * sj.z;
+#pragma unroll
+    for (int n = 0; n < NCH; ++n) {
+        st[n] = g[n];
+        st[NCH + n] = g[n] * s;
+    }
+    harm_p(dx * ir, dy * ir, dz * ir, st + 2 * NCH);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+    extern __shared__ unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int quad = lane >> 2, ql = lane & 3;
+    const int64_t i = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 8 + quad;
+    const bool valid = i < a.n;
+    R *stage = reinterpret_cast<R *>(smem_raw) + (warp * 8 + quad) * FQUAD;
+    const int64_t N = a.n;
+    v4<R> pi, si;
+    int na0 = 0, na = 0, ti = 0;
+    if (valid) {
+        pi = a.pos[i];
+        si = a.spin[i];
+        const int4 c = a.cnt[i];
+        na0 = c.x;
+        na = c.y;
+        ti = i < a.n_fe ? 0 : 1;
+    }
+    R B[6][NCH], BS[6][NCH];
+#pragma unroll
+    for (int m = 0; m < 6; ++m)
+#pragma unroll
+        for (int n = 0; n < NCH; ++n) { B[m][n] = R(0); BS[m][n] = R(0); }
+    const int nmax = __reduce_max_sync(0xffffffffu, na);
+    for (int base = 0; base < nmax; base += 4) {
+        const int p = base + ql;
+        if (p < na) {
+            R *st = stage + ql * FSTAGE;
+            if (ti == 0) {
+                if (p < na0) ang_stage_fwd<R, 0, 0>(P, a, i, pi, si, p, st);
+                else ang_stage_fwd<R, 0, 1>(P, a, i, pi, si, p, st);
+            } else {
+                if (p < na0) ang_stage_fwd<R, 1, 0>(P, a, i, pi, si, p, st);
+                else ang_stage_fwd<R, 1, 1>(P, a, i, pi, si, p, st);
+            }
+        }
+        __syncwarp();
+        const int cnt = min(4, na - base);
+        for (int q = 0; q < cnt; ++q) {
+            const R *sp = stage + q * FSTAGE;
+            R g[NCH], gs[NCH];
+#pragma unroll
+            for (int n = 0; n < NCH; ++n) { g[n] = sp[n]; gs[n] = sp[NCH + n]; }
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                const R pl = sp[2 * NCH + ql + 4 * m];
+#pragma unroll
+                for (int n = 0; n < NCH; ++n) {
+                    B[m][n] += g[n] * pl;
+                    BS[m][n] += gs[n] * pl;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // angular sums for the backward pass, and the channel values
+    R qa[NCH][4], qs[NCH][4];
+#pragma unroll
+    for (int n = 0; n < NCH; ++n)
+#pragma unroll
+        for (int l = 0; l < 4; ++l) { qa[n][l] = R(0); qs[n][l] = R(0); }
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+        const int lm = lm_of(ql, m);
+        const int l = l_of_lm(lm) - 1;
+        const R kap = kappa_of_lm<R>(lm);
+#pragma unroll
+        for (int n = 0; n < NCH; ++n) {
+            if (valid) {
+                a.bsum[(int64_t)(n * NLM + lm) * N + i] = B[m][n];
+                a.bsum[(int64_t)(NCH * NLM + n * NLM + lm) * N + i] = BS[m][n];
+            }
+            const R ka = kap * B[m][n] * B[m][n], ks = kap * BS[m][n] * BS[m][n];
+            // l is 1..4 depending on the lane: add into the matching slot
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                qa[n][t] += (t == l) ? ka : R(0);
+                qs[n][t] += (t == l) ? ks : R(0);
+            }
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NCH; ++n)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            qa[n][t] += __shfl_xor_sync(0xffffffffu, qa[n][t], 1);
+            qa[n][t] += __shfl_xor_sync(0xffffffffu, qa[n][t], 2);
+            qs[n][t] += __shfl_xor_sync(0xffffffffu, qs[n][t], 1);
+            qs[n][t] += __shfl_xor_sync(0xffffffffu, qs[n][t], 2);
+        }
+    if (valid) {
+        // lane ql writes l = ql + 1
+#pragma unroll
+        for (int n = 0; n < NCH; ++n) {
+            R va = qa[n][0], vs = qs[n][0];
+#pragma unroll
+            for (int t = 1; t < 4; ++t) {
+                va = ql == t ? qa[n][t] : va;
+                vs = ql == t ? qs[n][t] : vs;
+            }
+            a.q[(int64_t)(Q_A + n * 4 + ql) * N + i] = va;
+            a.q[(int64_t)(Q_SA + n * 4 + ql) * N + i] = vs;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ k_ang_bwd
+// stage of one angular pair: g (5), g' (5), s, 1/r, u (3), S_j (3), pad (2) = 20; then 24 x (p, grad p)
+constexpr int BSCAL = 20;
+constexpr int BSTAGE = BSCAL + 4 * NLM;   // 116
+constexpr int BQUAD = 4 * BSTAGE + 4;      // 468
+
+template <typename R, int LM>
+__device__ __forceinline__ void stage_harm(R x, R y, R z, R *dst) {
+    R p, gx, gy, gz;
+    harm_one<R, LM>(x, y, z, p, gx, gy, gz);
+    dst[4 * LM] = p;
+    dst[4 * LM + 1] = gx;
+    dst[4 * LM + 2] = gy;
+    dst[4 * LM + 3] = gz;
+    if constexpr (LM + 1 < NLM) stage_harm<R, LM + 1>(x, y, z, dst);
+}
+
+template <typename R, int TI, int TJ>
+__device__ __forceinline__ void ang_stage_bwd(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, const v4<R> &pi,
+                                              const v4<R> &si, int p, R *st) {
+    const int j = a.clj[(int64_t)p * a.n + i];
+    const v4<R> pj = a.pos[j], sj = a.spin[j];
+    R dx, dy, dz;
+    sep(a.box, pi, pj, dx, dy, dz);
+    const R d2 = dx * dx + dy * dy + dz * dz;
+    const R ir = rsqrt_(d2), r = d2 * ir;
+    R f[NK], df[NK], g[NCH], dg[NCH];
+    carrier_fd(r, P.inv_rc_a, f, df);
+    contract_k<R, TI, TJ, G_A>(P, f, g);
+    contract_k<R, TI, TJ, G_A>(P, df, dg);
+#pragma unroll
+    for (int n = 0; n < NCH; ++n) {
+        st[n] = g[n];
+        st[NCH + n] = dg[n];
+    }
+    const R ux = dx * ir, uy = dy * ir, uz = dz * ir;
+    st[10] = si.x * sj.x + si.y * sj.y + si.z * sj.z;
+    st[11] = ir;
+    st[12] = ux; st[13] = uy; st[14] = uz;
+    st[15] = sj.x; st[16] = sj.y; st[17] = sj.z;
+    stage_harm<R, 0>(ux, uy, uz, st + BSCAL);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_ang_bwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+    extern __shared__ unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int quad = lane >> 2, ql = lane & 3;
+    const int64_t i = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 8 + quad;
+    const bool valid = i < a.n;
+    R *stage = reinterpret_cast<R *>(smem_raw) + (warp * 8 + quad) * BQUAD;
+    const int64_t N = a.n;
+    v4<R> pi, si;
+    int na0 = 0, na = 0, ti = 0;
+    R Bb[6][NCH], BSb[6][NCH], lv[6];
+    if (valid) {
+        pi = a.pos[i];
+        si = a.spin[i];
+        const int4 c = a.cnt[i];
+        na0 = c.x;
+        na = c.y;
+        ti = i < a.n_fe ? 0 : 1;
+    }
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+        const int lm = lm_of(ql, m);
+        const int l = l_of_lm(lm);
+        lv[m] = R(l);
+        const R k2 = R(2) * kappa_of_lm<R>(lm);
+#pragma unroll
+        for (int n = 0; n < NCH; ++n) {
+            if (valid) {
+                const R fa = a.fp[(int64_t)(Q_A + n * 4 + l - 1) * N + i];
+                const R fs = a.fp[(int64_t)(Q_SA + n * 4 + l - 1) * N + i];
+                Bb[m][n] = k2 * fa * a.bsum[(int64_t)(n * NLM + lm) * N + i];
+                BSb[m][n] = k2 * fs * a.bsum[(int64_t)(NCH * NLM + n * NLM + lm) * N + i];
+            } else {
+                Bb[m][n] = R(0);
+                BSb[m][n] = R(0);
+            }
+        }
+    }
+    R hx = R(0), hy = R(0), hz = R(0);
+    const int nmax = __reduce_max_sync(0xffffffffu, na);
+    for (int base = 0; base < nmax; base += 4) {
+        const int p = base + ql;
+        if (p < na) {
+            R *st = stage + ql * BSTAGE;
+            if (ti == 0) {
+                if (p < na0) ang_stage_bwd<R, 0, 0>(P, a, i, pi, si, p, st);
+                else ang_stage_bwd<R, 0, 1>(P, a, i, pi, si, p, st);
+            } else {
+                if (p < na0) ang_stage_bwd<R, 1, 0>(P, a, i, pi, si, p, st);
+                else ang_stage_bwd<R, 1, 1>(P, a, i, pi, si, p, st);
+            }
+        }
+        __syncwarp();
+        const int cnt = min(4, na - base);
+        // every lane of the warp runs the same number of reduction steps
+        const int cmax = __reduce_max_sync(0xffffffffu, max(cnt, 0));
+        for (int q = 0; q < cmax; ++q) {
+            const bool act = q < cnt;
+            const R *sp = stage + q * BSTAGE;
+            R accu = R(0), avx = R(0), avy = R(0), avz = R(0), cj = R(0), s = R(0), ir = R(0);
+            if (act) {
+                R g[NCH], dg[NCH];
+#pragma unroll
+                for (int n = 0; n < NCH; ++n) { g[n] = sp[n]; dg[n] = sp[NCH + n]; }
+                s = sp[10];
+                ir = sp[11];
+#pragma unroll
+                for (int m = 0; m < 6; ++m) {
+                    const R *h = sp + BSCAL + 4 * lm_of(ql, m);
+                    const R pl = h[0], gx = h[1], gy = h[2], gz = h[3];
+                    R aA = R(0), aS = R(0), bA = R(0), bS = R(0);
+#pragma unroll
+                    for (int n = 0; n < NCH; ++n) {
+                        aA += Bb[m][n] * g[n];
+                        aS += BSb[m][n] * g[n];
+                        bA += Bb[m][n] * dg[n];
+                        bS += BSb[m][n] * dg[n];
+                    }
+                    const R av = aA + s * aS, bv = bA + s * bS;
+                    accu += pl * (bv - lv[m] * ir * av);
+                    avx += av * gx;
+                    avy += av * gy;
+                    avz += av * gz;
+                    cj += aS * pl;
+                }
+            }
+#pragma unroll
+            for (int o = 1; o <= 2; o <<= 1) {
+                accu += __shfl_xor_sync(0xffffffffu, accu, o);
+                avx += __shfl_xor_sync(0xffffffffu, avx, o);
+                avy += __shfl_xor_sync(0xffffffffu, avy, o);
+                avz += __shfl_xor_sync(0xffffffffu, avz, o);
+                cj += __shfl_xor_sync(0xffffffffu, cj, o);
+            }
+            if (act) {
+                const R ux = sp[12], uy = sp[13], uz = sp[14];
+                if (ql == q) {
+                    v4<R> o4;
+                    o4.x = accu * ux + ir * avx;
+                    o4.y = accu * uy + ir * avy;
+                    o4.z = accu * uz + ir * avz;
+                    o4.w = cj;
+                    a.apair[(int64_t)(base + q) * N + i] = o4;
+                }
+                hx += cj * sp[15];
+                hy += cj * sp[16];
+                hz += cj * sp[17];
+            }
+        }
+        __syncwarp();
+    }
+    if (valid && ql == 0) {
+        v4<R> h4;
+        h4.x = hx; h4.y = hy; h4.z = hz; h4.w = R(0);
+        a.gii_ang[i] = h4;
+    }
+}
+
+// ------------------------------------------------------------------ k_rad_bwd
+template <typename R>
+struct RadAcc {
+    R fx, fy, fz, hx, hy, hz;
+    R w[9];
+};
+
+template <typename R, int TI, int TJ, bool ANG>
+__device__ __forceinline__ void rad_bwd_rows(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, const v4<R> &pi,
+                                             const v4<R> &si, const R C0[NK], const R C1[NK], const R C2[NK],
+                                             const R C3[NK], const R C4[NK], int lo, int hi, RadAcc<R> &acc) {
+    const int64_t N = a.n;
+    for (int row = lo; row < hi; ++row) {
+        const int j = a.clj[(int64_t)row * N + i];
+        const int s = a.cls[(int64_t)row * N + i];
+        const v4<R> pj = a.pos[j], sj = a.spin[j];
+        R dx, dy, dz;
+        sep(a.box, pi, pj, dx, dy, dz);
+        const R d2 = dx * dx + dy * dy + dz * dz;
+        const R ir = rsqrt_(d2), r = d2 * ir;
+        const R ux = dx * ir, uy = dy * ir, uz = dz * ir;
+        R f[NK], df[NK];
+        carrier_fd(r, P.inv_rc_r, f, df);
+        R h1 = 0, h2 = 0, h3 = 0, h4 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0, e4 = 0;
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            e0 += C0[k] * df[k];
+            h1 += C1[k] * f[k]; e1 += C1[k] * df[k];
+            h2 += C2[k] * f[k]; e2 += C2[k] * df[k];
+            h3 += C3[k] * f[k]; e3 += C3[k] * df[k];
+            h4 += C4[k] * f[k]; e4 += C4[k] * df[k];
+        }
+        const R sij = si.x * sj.x + si.y * sj.y + si.z * sj.z;
+        const R siu = si.x * ux + si.y * uy + si.z * uz;
+        const R sju = sj.x * ux + sj.y * uy + sj.z * uz;
+        const R wx = si.y * sj.z - si.z * sj.y, wy = si.z * sj.x - si.x * sj.z, wz = si.x * sj.y - si.y * sj.x;
+        const R wu = wx * ux + wy * uy + wz * uz;
+        const R rad = e0 + e1 * sij + e2 * wu + e3 * siu * sju + e4 * siu * siu;
+        const R cSi = (h3 * sju + R(2) * h4 * siu) * ir;
+        const R cSj = h3 * siu * ir;
+        const R cW = h2 * ir;
+        const R along = rad - cSi * siu - cSj * sju - cW * wu;
+        R Dx = along * ux + cSi * si.x + cSj * sj.x + cW * wx;
+        R Dy = along * uy + cSi * si.y + cSj * sj.y + cW * wy;
+        R Dz = along * uz + cSi * si.z + cSj * sj.z + cW * wz;
+        R Gx = h1 * si.x + h2 * (uy * si.z - uz * si.y) + h3 * siu * ux;
+        R Gy = h1 * si.y + h2 * (uz * si.x - ux * si.z) + h3 * siu * uy;
+        R Gz = h1 * si.z + h2 * (ux * si.y - uy * si.x) + h3 * siu * uz;
+        const R cu = h3 * sju + R(2) * h4 * siu;
+        acc.hx += h1 * sj.x + h2 * (sj.y * uz - sj.z * uy) + cu * ux;
+        acc.hy += h1 * sj.y + h2 * (sj.z * ux - sj.x * uz) + cu * uy;
+        acc.hz += h1 * sj.z + h2 * (sj.x * uy - sj.y * ux) + cu * uz;
+        if constexpr (ANG) {
+            const v4<R> ap = a.apair[(int64_t)row * N + i];
+            Dx += ap.x; Dy += ap.y; Dz += ap.z;
+            Gx += ap.w * si.x; Gy += ap.w * si.y; Gz += ap.w * si.z;
+        }
+        acc.fx += Dx; acc.fy += Dy; acc.fz += Dz;
+        if (a.want_virial) {
+            acc.w[0] -= dx * Dx; acc.w[1] -= dx * Dy; acc.w[2] -= dx * Dz;
+            acc.w[3] -= dy * Dx; acc.w[4] -= dy * Dy; acc.w[5] -= dy * Dz;
+            acc.w[6] -= dz * Dx; acc.w[7] -= dz * Dy; acc.w[8] -= dz * Dz;
+        }
+        // record for neighbour j, in j's own slot of i
+        const int t = a.rev[(int64_t)s * N + i];
+        PairRec<R> rec;
+        rec.a.x = Dx; rec.a.y = Dy; rec.a.z = Dz; rec.a.w = Gx;
+        rec.b.x = Gy; rec.b.y = Gz; rec.b.z = R(0); rec.b.w = R(0);
+        a.pd[(int64_t)t * N + j] = rec;
+    }
+}
+
+template <typename R, int TI, int TJ>
+__device__ __forceinline__ void rad_bwd_species(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i,
+                                                const v4<R> &pi, const v4<R> &si, const R FR[NCH],
+                                                const R FX[4][NCH], int alo, int ahi, int rlo, int rhi,
+                                                RadAcc<R> &acc) {
+    // C^G_k = sum_n Fp^G_n c^G_{n k t_i t_j}
+    R C0[NK], C1[NK], C2[NK], C3[NK], C4[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0), s4 = R(0);
+#pragma unroll
+        for (int n = 0; n < NCH; ++n) {
+            s0 += FR[n] * P.c[TI][TJ][G_R][n][k];
+            s1 += FX[0][n] * P.c[TI][TJ][G_EX][n][k];
+            s2 += FX[1][n] * P.c[TI][TJ][G_DMI][n][k];
+            s3 += FX[2][n] * P.c[TI][TJ][G_ANI][n][k];
+            s4 += FX[3][n] * P.c[TI][TJ][G_SIA][n][k];
+        }
+        C0[k] = s0; C1[k] = s1; C2[k] = s2; C3[k] = s3; C4[k] = s4;
+    }
+    rad_bwd_rows<R, TI, TJ, true>(P, a, i, pi, si, C0, C1, C2, C3, C4, alo, ahi, acc);
+    rad_bwd_rows<R, TI, TJ, false>(P, a, i, pi, si, C0, C1, C2, C3, C4, rlo, rhi, acc);
+}
+
+template <typename R, int TI>
+__device__ __forceinline__ void rad_bwd_atom(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i) {
+    const int64_t N = a.n;
+    const v4<R> pi = a.pos[i], si = a.spin[i];
+    const int4 c = a.cnt[i];
+    R FR[NCH], FX[4][NCH];
+#pragma unroll
+    for (int n = 0; n < NCH; ++n) {
+        FR[n] = a.fp[(int64_t)(Q_R + n) * N + i];
+        FX[0][n] = a.fp[(int64_t)(Q_EX + n) * N + i];
+        FX[1][n] = a.fp[(int64_t)(Q_DMI + n) * N + i];
+        FX[2][n] = a.fp[(int64_t)(Q_ANI + n) * N + i];
+        FX[3][n] = a.fp[(int64_t)(Q_SIA + n) * N + i];
+    }
+    const R fo = R(2) * a.fp[(int64_t)Q_O * N + i];
+    const v4<R> ga = a.gii_ang[i];
+    RadAcc<R> acc;
+    acc.fx = acc.fy = acc.fz = R(0);
+    acc.hx = fo * si.x + ga.x;
+    acc.hy = fo * si.y + ga.y;
+    acc.hz = fo * si.z + ga.z;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc.w[t] = R(0);
+    const int ca = a.cap_ang;
+    rad_bwd_species<R, TI, 0>(P, a, i, pi, si, FR, FX, 0, c.x, ca, ca + c.z, acc);
+    rad_bwd_species<R, TI, 1>(P, a, i, pi, si, FR, FX, c.x, c.y, ca + c.z, ca + c.w, acc);
+    v4<R> f4, g4;
+    f4.x = acc.fx; f4.y = acc.fy; f4.z = acc.fz; f4.w = R(0);
+    g4.x = acc.hx; g4.y = acc.hy; g4.z = acc.hz; g4.w = R(0);
+    a.fown[i] = f4;
+    a.gii[i] = g4;
+    if (a.want_virial) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) a.wpart[(int64_t)t * N + i] = acc.w[t];
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_rad_bwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    if (i < a.n_fe) rad_bwd_atom<R, 0>(P, a, i);
+    else rad_bwd_atom<R, 1>(P, a, i);
+}
+
+// ------------------------------------------------------------------ launch
+template <typename R>
+static Eval2Args<R> args2(Sys &s, bool want_virial) {
+    Eval2Args<R> a;
+    if constexpr (sizeof(R) == 8) {
+        a.pos = reinterpret_cast<const v4<R> *>(s.pos);
+        a.spin = reinterpret_cast<const v4<R> *>(s.spin);
+        a.box = *reinterpret_cast<const BoxDev<R> *>(&s.boxd);
+    } else {
+        a.pos = reinterpret_cast<const v4<R> *>(s.posf);
+        a.spin = reinterpret_cast<const v4<R> *>(s.spinf);
+        a.box = *reinterpret_cast<const BoxDev<R> *>(&s.boxf);
+    }
+    a.nbr = s.nbr; a.seg = s.seg; a.rev = s.rev; a.n = s.n; a.n_fe = s.n_fe;
+    a.cap = s.cap; a.cap_ang = s.cap_ang;
+    a.clj = s.clj; a.cls = s.cls; a.cnt = s.cnt;
+    a.q = (R *)s.q; a.bsum = (R *)s.bsum; a.fp = (R *)s.fp; a.ei = (R *)s.ei;
+    a.apair = (v4<R> *)s.apair; a.gii_ang = (v4<R> *)s.gii_ang;
+    a.pd = (PairRec<R> *)s.pairs; a.fown = (v4<R> *)s.fown; a.gii = (v4<R> *)s.gii;
+    a.wpart = (R *)s.wpart; a.want_virial = want_virial; a.status = s.status;
+    return a;
+}
+
+template <typename R>
+static constexpr int quad_block() { return sizeof(R) == 8 ? 64 : 128; }
+template <typename R>
+static constexpr size_t fwd_smem() { return (size_t)(quad_block<R>() / 32) * 8 * FQUAD * sizeof(R); }
+template <typename R>
+static constexpr size_t bwd_smem() { return (size_t)(quad_block<R>() / 32) * 8 * BQUAD * sizeof(R); }
+
+void eval2_init() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_ang_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<float>());
+    cudaFuncSetAttribute(k_ang_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<double>());
+    cudaFuncSetAttribute(k_ang_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<float>());
+    cudaFuncSetAttribute(k_ang_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<double>());
+    done = true;
+}
+
+template <typename R>
+static void eval2_impl(Sys &s, const NepDev<R> &P, bool want_virial, cudaEvent_t *ev) {
+    const Eval2Args<R> a = args2<R>(s, want_virial);
+    const unsigned nb = (unsigned)((s.n + 127) / 128);
+    const int qb = quad_block<R>();
+    const unsigned nq = (unsigned)((s.n + qb / 4 - 1) / (qb / 4));
+    if (ev) cudaEventRecord(ev[0], s.stream);
+    k_rad_fwd<R><<<nb, 128, 0, s.stream>>>(P, a);
+    k_ang_fwd<R><<<nq, qb, fwd_smem<R>(), s.stream>>>(P, a);
+    if (ev) cudaEventRecord(ev[1], s.stream);
+    launch_network(s, ev ? nullptr : nullptr);
+    if (ev) cudaEventRecord(ev[2], s.stream);
+    k_ang_bwd<R><<<nq, qb, bwd_smem<R>(), s.stream>>>(P, a);
+    k_rad_bwd<R><<<nb, 128, 0, s.stream>>>(P, a);
+    if (ev) cudaEventRecord(ev[3], s.stream);
+}
+
+void launch_eval(Sys &s, bool want_virial, cudaEvent_t *ev) {
+    if (s.n == 0) return;
+    if (s.prec == 0) eval2_impl<double>(s, s.pd, want_virial, ev);
+    else eval2_impl<float>(s, s.pf, want_virial, ev);
+}
+
+}  // namespace sl

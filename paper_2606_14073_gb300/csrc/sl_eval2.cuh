@@ -1,0 +1,37 @@
+// sl_eval2.cuh -- argument block and pair record shared by the evaluation kernels and the gather.
+#pragma once
+
+#include "sl_common.cuh"
+
+namespace sl {
+
+// Record of one ordered pair (i -> j) for neighbour j: (dE_i/dr_ij, dE_i/dS_j), 32 bytes
+// in FP32 (one DRAM sector), stored in j's own list slot of i.
+template <typename R>
+struct PairRec {
+    v4<R> a;   // dE_i/dr_ij (x, y, z), dE_i/dS_j .x
+    v4<R> b;   // dE_i/dS_j .y, .z, 0, 0
+};
+
+template <typename R>
+struct Eval2Args {
+    const v4<R> *pos, *spin;
+    const int32_t *nbr, *rev;
+    const int4 *seg;
+    int64_t n, n_fe;
+    BoxDev<R> box;
+    int cap, cap_ang;
+    int32_t *clj;      // compact in-cutoff rows [cap_ang + cap][n]: neighbour index
+    uint8_t *cls;      // ... and its candidate slot
+    int4 *cnt;         // (angular rows of species 0, angular rows, radial-only rows of species 0, radial-only rows)
+    R *q, *bsum, *fp, *ei;
+    v4<R> *apair;      // [cap_ang][n]: angular dE_i/dr_ij (x, y, z) and spin weight c_ij
+    v4<R> *gii_ang;    // [n]: angular dE_i/dS_i
+    PairRec<R> *pd;    // [cap][n]
+    v4<R> *fown, *gii;
+    R *wpart;
+    int want_virial;
+    int *status;
+};
+
+}  // namespace sl

@@ -6,7 +6,7 @@
 //   first half  (k_first_half):  v += dt/2 F/m; r += dt/2 v; v = c v + sig_v xi;
 //                                r += dt/2 v (wrapped); eta = sig_eta zeta;
 //                                S' = Rot(S, omega(S, H + eta) dt)
-//   evaluation  at (r, S')  (sl_nep.cu)
+//   evaluation  at (r, S')  (sl_eval2.cu)
 //   second half (k_second_half): gather F', H'; S = Rot(S, (omega(S,H+eta) + omega(S',H'+eta)) dt/2),
 //                                renormalised in FP64; v += dt/2 F'/m; (F, H) = (F', H')
 // omega(S, X) = (X + lambda S x X) / ((1 + lambda^2) hbar); Rot is the exact Rodrigues
@@ -14,12 +14,9 @@
 // (step, caller index, stream, 0), key (seed, replica): the corrector regenerates
 // the predictor's eta bit for bit, so nothing is stored between the halves.
 #include "sl_internal.h"
+#include "sl_eval2.cuh"
 
 namespace sl {
-
-template <typename R> struct V2i;
-template <> struct V2i<float> { using t = float2; };
-template <> struct V2i<double> { using t = double2; };
 
 struct IntArgs {
     double4 *pos, *vel, *spin, *spin_prev, *F, *H, *posref;
@@ -36,11 +33,12 @@ struct IntArgs {
 
 template <typename R>
 struct GatherArgs {
-    const v4<R> *fown, *gii, *pd0;
-    const typename V2i<R>::t *pd1;
-    const int32_t *nbr, *rev;
-    const int4 *seg;
+    const v4<R> *fown, *gii;
+    const PairRec<R> *pd;
+    const uint8_t *cls;
+    const int4 *cnt;
     int64_t n;
+    int cap_ang;
 };
 
 __device__ __forceinline__ void omega_of(double sx, double sy, double sz, double hx, double hy, double hz,
@@ -103,19 +101,23 @@ __global__ void __launch_bounds__(256) k_first_half(IntArgs a) {
     if (dx * dx + dy * dy + dz * dz > P.disp2) *a.rebuild = 1;
 }
 
+// F_k = sum_j dE_k/dr_kj - sum_j dE_j/dr_jk, H_k = -dE_k/dS_k - sum_j dE_j/dS_k: the
+// records (dE_j/dr_jk, dE_j/dS_k) sit in k's own in-cutoff slots.
 template <typename R>
 __device__ __forceinline__ void gather(const GatherArgs<R> &g, int64_t k, double F[3], double H[3]) {
     const v4<R> fo = g.fown[k], gi = g.gii[k];
     R fx = fo.x, fy = fo.y, fz = fo.z, hx = -gi.x, hy = -gi.y, hz = -gi.z;
-    const int4 sg = g.seg[k];
+    const int4 c = g.cnt[k];
     const int64_t N = g.n;
-    for (int s = 0; s < sg.w; ++s) {
-        const int j = g.nbr[(int64_t)s * N + k];
-        const int t = g.rev[(int64_t)s * N + k];
-        const v4<R> e0 = g.pd0[(int64_t)t * N + j];
-        const typename V2i<R>::t e1 = g.pd1[(int64_t)t * N + j];
-        fx -= e0.x; fy -= e0.y; fz -= e0.z;
-        hx -= e0.w; hy -= e1.x; hz -= e1.y;
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+        const int lo = part ? g.cap_ang : 0, hi = part ? g.cap_ang + c.w : c.y;
+        for (int row = lo; row < hi; ++row) {
+            const int s = g.cls[(int64_t)row * N + k];
+            const PairRec<R> e = g.pd[(int64_t)s * N + k];
+            fx -= e.a.x; fy -= e.a.y; fz -= e.a.z;
+            hx -= e.a.w; hy -= e.b.x; hz -= e.b.y;
+        }
     }
     F[0] = (double)fx; F[1] = (double)fy; F[2] = (double)fz;
     H[0] = (double)hx; H[1] = (double)hy; H[2] = (double)hz;
@@ -188,8 +190,8 @@ static IntArgs int_args(Sys &s) {
 template <typename R>
 static GatherArgs<R> gather_args(Sys &s) {
     GatherArgs<R> g;
-    g.fown = (const v4<R> *)s.fown; g.gii = (const v4<R> *)s.gii; g.pd0 = (const v4<R> *)s.pd0;
-    g.pd1 = (const typename V2i<R>::t *)s.pd1; g.nbr = s.nbr; g.rev = s.rev; g.seg = s.seg; g.n = s.n;
+    g.fown = (const v4<R> *)s.fown; g.gii = (const v4<R> *)s.gii; g.pd = (const PairRec<R> *)s.pairs;
+    g.cls = s.cls; g.cnt = s.cnt; g.n = s.n; g.cap_ang = s.cap_ang;
     return g;
 }
 

@@ -68,8 +68,12 @@ struct Sys {
     void *bsum = nullptr;      // [NB][n]
     void *fp = nullptr;        // [DIM][n]
     void *ei = nullptr;        // [n]
-    void *pd0 = nullptr;       // [cap][n] v4: (dE_i/dr_ij, dE_i/dS_j .x)
-    void *pd1 = nullptr;       // [cap][n] v2: (dE_i/dS_j .y .z)
+    void *pairs = nullptr;     // [cap][n] pair records (see sl_eval2.cuh)
+    int32_t *clj = nullptr;    // [cap_ang + cap][n] compact in-cutoff neighbours
+    uint8_t *cls = nullptr;    // [cap_ang + cap][n] their candidate slots
+    int4 *cnt = nullptr;       // [n] compact row counts
+    void *apair = nullptr;     // [cap_ang][n] angular pair derivatives
+    void *gii_ang = nullptr;   // [n] angular dE_i/dS_i
     void *fown = nullptr;      // [n] v4: sum_j dE_i/dr_ij
     void *gii = nullptr;       // [n] v4: dE_i/dS_i
     void *wpart = nullptr;     // [9][n] per-atom virial parts
@@ -101,9 +105,12 @@ void nbr_setup(Sys &s);
 void launch_rebuild(Sys &s, bool conditional);
 // sl_nep.cu
 // ev (optional, 4 events): recorded before the descriptor, network and backward
-// kernels and after the backward kernel.
+// kernels and after the backward kernels (sl_eval2.cu).
 void launch_eval(Sys &s, bool want_virial, cudaEvent_t *ev = nullptr);
-constexpr int KERNELS_PER_STEP = 1 + 7 + 3 + 1;   // first half, rebuild group, eval, second half
+void eval2_init();
+void launch_network(Sys &s, cudaEvent_t *ev);   // sl_nep.cu
+// first half, rebuild group (7), descriptor (2), network, backward (2), second half
+constexpr int KERNELS_PER_STEP = 1 + 7 + 2 + 1 + 2 + 1;
 // sl_integrate.cu
 void launch_first_half(Sys &s);
 void launch_second_half(Sys &s);
@@ -111,8 +118,6 @@ void launch_gather(Sys &s, bool carried);
 void launch_mark_rebuild(Sys &s);
 int reduce_energy_virial(Sys &s, double *E, double *W, bool want_virial);
 
-size_t eval_bytes(const Sys &s);
-void eval_init();
 int launch_noalloc(const NepDev<double> &P, const double4 *pos, const double4 *spin, const int32_t *species, int n,
                    const BoxDev<double> &box, double *q_out, double *e_out, cudaStream_t stream, int *status_out);
 int noalloc_max_atoms();

@@ -10,12 +10,11 @@
 // The angular channels use the harmonic (addition-theorem) form: one pass over
 // neighbours per channel n instead of the pair double sum.
 //
-// Three kernels:
-//   k_fwd   q[66][n] and the 240 angular sums B, BS (kept for the backward);
-//   k_mlp   E_i and Fp = dE_i/dq_i (CUDA-core version; the tensor-core one is in sl_mlp_tc.cu);
-//   k_bwd   per neighbour slot: dE_i/dr_ij and dE_i/dS_j, and per atom sum_j dE_i/dr_ij,
-//           dE_i/dS_i and the virial part -sum_j r_ij (x) dE_i/dr_ij.
-// Forces and fields are then gathered (sl_integrate.cu) without atomics:
+// This file holds the per-atom forward (one thread per atom, used by the
+// no-allocation entry point) and the CUDA-core network k_mlp:
+//   E_i and Fp = dE_i/dq_i.
+// The step's evaluation kernels are in sl_eval2.cu; forces and fields are gathered
+// without atomics (sl_integrate.cu):
 //   F_k = sum_j (dE_k/dr_kj - dE_j/dr_jk),  H_k = -dE_k/dS_k - sum_j dE_j/dS_k + Zeeman.
 //
 // Atoms are stored species-major, so a warp almost always has one centre species;
@@ -177,14 +176,6 @@ __device__ __forceinline__ void fwd_atom(const NepDev<R> &P, const EvalArgs<R> &
     }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(128) k_fwd(const __grid_constant__ NepDev<R> P, const EvalArgs<R> a) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    if (i < a.n_fe) fwd_atom<R, 0>(P, a, i);
-    else fwd_atom<R, 1>(P, a, i);
-}
-
 // ------------------------------------------------------------------ network
 // E_i = sum_h w1_h tanh(z_h) - b1, z_h = sum_v W0_hv s_v q_v - b0_h;
 // Fp_v = s_v sum_h w1_h (1 - tanh^2 z_h) W0_hv.
@@ -217,280 +208,18 @@ __global__ void __launch_bounds__(128) k_mlp(const __grid_constant__ NepDev<R> P
     ei[i] = E;
 }
 
-// ------------------------------------------------------------------ backward
-template <typename R, int TI, int TJ, int LM>
-__device__ __forceinline__ void bwd_lm(const R *__restrict__ sB, int bd, R ux, R uy, R uz, R ir, R sij,
-                                       const R g[NCH], const R dg[NCH], R &accu, R &avx, R &avy, R &avz, R &cj) {
-    R p, gx, gy, gz;
-    harm_one<R, LM>(ux, uy, uz, p, gx, gy, gz);
-    R aA = R(0), aS = R(0), bA = R(0), bS = R(0);
-#pragma unroll
-    for (int n = 0; n < NCH; ++n) {
-        const R ba = sB[(n * NLM + LM) * bd];
-        const R bs = sB[(NCH * NLM + n * NLM + LM) * bd];
-        aA += ba * g[n];
-        aS += bs * g[n];
-        bA += ba * dg[n];
-        bS += bs * dg[n];
-    }
-    const R av = aA + sij * aS, bv = bA + sij * bS;
-    accu += p * (bv - R(harm_l(LM)) * ir * av);
-    avx += av * gx;
-    avy += av * gy;
-    avz += av * gz;
-    cj += aS * p;
-}
-
-template <typename R, int TI, int TJ, int LM>
-__device__ __forceinline__ void bwd_lm_all(const R *__restrict__ sB, int bd, R ux, R uy, R uz, R ir, R sij,
-                                           const R g[NCH], const R dg[NCH], R &accu, R &avx, R &avy, R &avz, R &cj) {
-    bwd_lm<R, TI, TJ, LM>(sB, bd, ux, uy, uz, ir, sij, g, dg, accu, avx, avy, avz, cj);
-    if constexpr (LM + 1 < NLM) bwd_lm_all<R, TI, TJ, LM + 1>(sB, bd, ux, uy, uz, ir, sij, g, dg, accu, avx, avy, avz, cj);
-}
-
-template <typename R>
-struct BwdAcc {
-    R fx, fy, fz;            // sum_j dE_i/dr_ij
-    R hx, hy, hz;            // dE_i/dS_i
-    R w[9];                  // -sum_j r_ij (x) dE_i/dr_ij
-};
-
-template <typename R, int TI, int TJ, bool ANG>
-__device__ __forceinline__ void bwd_seg(const NepDev<R> &P, const EvalArgs<R> &a, int64_t i, const v4<R> &pi,
-                                        const v4<R> &si, const R FR[NCH], const R FX[4][NCH], const R *sB, int bd,
-                                        int s0, int s1, BwdAcc<R> &acc) {
-    // precontracted radial coefficients  C^G_k = sum_n Fp^G_n c^G_{n k t_i t_j}
-    R C0[NK], C1[NK], C2[NK], C3[NK], C4[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) {
-        R s0_ = R(0), s1_ = R(0), s2_ = R(0), s3_ = R(0), s4_ = R(0);
-#pragma unroll
-        for (int n = 0; n < NCH; ++n) {
-            s0_ += FR[n] * P.c[TI][TJ][G_R][n][k];
-            s1_ += FX[0][n] * P.c[TI][TJ][G_EX][n][k];
-            s2_ += FX[1][n] * P.c[TI][TJ][G_DMI][n][k];
-            s3_ += FX[2][n] * P.c[TI][TJ][G_ANI][n][k];
-            s4_ += FX[3][n] * P.c[TI][TJ][G_SIA][n][k];
-        }
-        C0[k] = s0_; C1[k] = s1_; C2[k] = s2_; C3[k] = s3_; C4[k] = s4_;
-    }
-    const int64_t N = a.n;
-    for (int s = s0; s < s1; ++s) {
-        const int j = a.nbr[(int64_t)s * N + i];
-        const v4<R> pj = a.pos[j];
-        R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-        minimg(a.box, dx, dy, dz);
-        const R d2 = dx * dx + dy * dy + dz * dz;
-        R Dx = R(0), Dy = R(0), Dz = R(0), Gx = R(0), Gy = R(0), Gz = R(0);
-        if (d2 < P.rc_r2) {
-            const v4<R> sj = a.spin[j];
-            const R ir = rsqrt_(d2), r = d2 * ir;
-            const R ux = dx * ir, uy = dy * ir, uz = dz * ir;
-            R f[NK], df[NK];
-            carrier_fd(r, P.inv_rc_r, f, df);
-            R h0 = 0, h1 = 0, h2 = 0, h3 = 0, h4 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0, e4 = 0;
-#pragma unroll
-            for (int k = 0; k < NK; ++k) {
-                e0 += C0[k] * df[k];
-                h1 += C1[k] * f[k]; e1 += C1[k] * df[k];
-                h2 += C2[k] * f[k]; e2 += C2[k] * df[k];
-                h3 += C3[k] * f[k]; e3 += C3[k] * df[k];
-                h4 += C4[k] * f[k]; e4 += C4[k] * df[k];
-            }
-            (void)h0;
-            const R sij = si.x * sj.x + si.y * sj.y + si.z * sj.z;
-            const R siu = si.x * ux + si.y * uy + si.z * uz;
-            const R sju = sj.x * ux + sj.y * uy + sj.z * uz;
-            const R wx = si.y * sj.z - si.z * sj.y, wy = si.z * sj.x - si.x * sj.z, wz = si.x * sj.y - si.y * sj.x;
-            const R wu = wx * ux + wy * uy + wz * uz;
-            const R rad = e0 + e1 * sij + e2 * wu + e3 * siu * sju + e4 * siu * siu;
-            // tangential parts (v - (v.u) u) / r of the spin-function gradients
-            const R cSi = (h3 * sju + R(2) * h4 * siu) * ir;   // coefficient of P_perp S_i
-            const R cSj = h3 * siu * ir;                       // coefficient of P_perp S_j
-            const R cW = h2 * ir;                              // coefficient of P_perp (S_i x S_j)
-            const R along = rad - cSi * siu - cSj * sju - cW * wu;
-            Dx = along * ux + cSi * si.x + cSj * sj.x + cW * wx;
-            Dy = along * uy + cSi * si.y + cSj * sj.y + cW * wy;
-            Dz = along * uz + cSi * si.z + cSj * sj.z + cW * wz;
-            // dE_i/dS_j = h_EX S_i + h_DMI (u x S_i) + h_ANI (S_i.u) u
-            Gx = h1 * si.x + h2 * (uy * si.z - uz * si.y) + h3 * siu * ux;
-            Gy = h1 * si.y + h2 * (uz * si.x - ux * si.z) + h3 * siu * uy;
-            Gz = h1 * si.z + h2 * (ux * si.y - uy * si.x) + h3 * siu * uz;
-            // dE_i/dS_i += h_EX S_j + h_DMI (S_j x u) + h_ANI (S_j.u) u + 2 h_SIA (S_i.u) u
-            const R cu = h3 * sju + R(2) * h4 * siu;
-            acc.hx += h1 * sj.x + h2 * (sj.y * uz - sj.z * uy) + cu * ux;
-            acc.hy += h1 * sj.y + h2 * (sj.z * ux - sj.x * uz) + cu * uy;
-            acc.hz += h1 * sj.z + h2 * (sj.x * uy - sj.y * ux) + cu * uz;
-            if constexpr (ANG) {
-                if (d2 < P.rc_a2) {
-                    carrier_fd(r, P.inv_rc_a, f, df);
-                    R g[NCH], dg[NCH];
-#pragma unroll
-                    for (int n = 0; n < NCH; ++n) {
-                        R s_ = R(0), t_ = R(0);
-#pragma unroll
-                        for (int k = 0; k < NK; ++k) {
-                            s_ += P.c[TI][TJ][G_A][n][k] * f[k];
-                            t_ += P.c[TI][TJ][G_A][n][k] * df[k];
-                        }
-                        g[n] = s_;
-                        dg[n] = t_;
-                    }
-                    R accu = R(0), avx = R(0), avy = R(0), avz = R(0), cj = R(0);
-                    bwd_lm_all<R, TI, TJ, 0>(sB, bd, ux, uy, uz, ir, sij, g, dg, accu, avx, avy, avz, cj);
-                    Dx += accu * ux + ir * avx;
-                    Dy += accu * uy + ir * avy;
-                    Dz += accu * uz + ir * avz;
-                    Gx += cj * si.x; Gy += cj * si.y; Gz += cj * si.z;
-                    acc.hx += cj * sj.x; acc.hy += cj * sj.y; acc.hz += cj * sj.z;
-                }
-            }
-            acc.fx += Dx; acc.fy += Dy; acc.fz += Dz;
-            if (a.want_virial) {
-                acc.w[0] -= dx * Dx; acc.w[1] -= dx * Dy; acc.w[2] -= dx * Dz;
-                acc.w[3] -= dy * Dx; acc.w[4] -= dy * Dy; acc.w[5] -= dy * Dz;
-                acc.w[6] -= dz * Dx; acc.w[7] -= dz * Dy; acc.w[8] -= dz * Dz;
-            }
-        }
-        v4<R> e0v;
-        e0v.x = Dx; e0v.y = Dy; e0v.z = Dz; e0v.w = Gx;
-        v2<R> e1v;
-        e1v.x = Gy; e1v.y = Gz;
-        a.pd0[(int64_t)s * N + i] = e0v;
-        a.pd1[(int64_t)s * N + i] = e1v;
-    }
-}
-
-template <typename R, int TI>
-__device__ __forceinline__ void bwd_atom(const NepDev<R> &P, const EvalArgs<R> &a, int64_t i, R *sB, int bd) {
-    const int64_t N = a.n;
-    const v4<R> pi = a.pos[i], si = a.spin[i];
-    const int4 sg = a.seg[i];
-    // adjoints of the angular sums: dE/dB_nlm = 2 kappa_lm Fp(A_nl) B_nlm, same for BS with Fp(SA_nl)
-#pragma unroll 1
-    for (int n = 0; n < NCH; ++n) {
-        R fa[4], fs[4];
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            fa[l] = a.fp[(int64_t)(Q_A + n * 4 + l) * N + i];
-            fs[l] = a.fp[(int64_t)(Q_SA + n * 4 + l) * N + i];
-        }
-#pragma unroll
-        for (int lm = 0; lm < NLM; ++lm) {
-            const R k2 = R(2.0 * harm_kappa(lm));
-            sB[(n * NLM + lm) * bd] = k2 * fa[harm_l(lm) - 1] * a.bsum[(int64_t)(n * NLM + lm) * N + i];
-            sB[(NCH * NLM + n * NLM + lm) * bd] =
-                k2 * fs[harm_l(lm) - 1] * a.bsum[(int64_t)(NCH * NLM + n * NLM + lm) * N + i];
-        }
-    }
-    R FR[NCH], FX[4][NCH];
-#pragma unroll
-    for (int n = 0; n < NCH; ++n) {
-        FR[n] = a.fp[(int64_t)(Q_R + n) * N + i];
-        FX[0][n] = a.fp[(int64_t)(Q_EX + n) * N + i];
-        FX[1][n] = a.fp[(int64_t)(Q_DMI + n) * N + i];
-        FX[2][n] = a.fp[(int64_t)(Q_ANI + n) * N + i];
-        FX[3][n] = a.fp[(int64_t)(Q_SIA + n) * N + i];
-    }
-    const R fo = R(2) * a.fp[(int64_t)Q_O * N + i];
-    BwdAcc<R> acc;
-    acc.fx = acc.fy = acc.fz = R(0);
-    acc.hx = fo * si.x; acc.hy = fo * si.y; acc.hz = fo * si.z;
-#pragma unroll
-    for (int t = 0; t < 9; ++t) acc.w[t] = R(0);
-    bwd_seg<R, TI, 0, true>(P, a, i, pi, si, FR, FX, sB, bd, 0, sg.x, acc);
-    bwd_seg<R, TI, 1, true>(P, a, i, pi, si, FR, FX, sB, bd, sg.x, sg.y, acc);
-    bwd_seg<R, TI, 0, false>(P, a, i, pi, si, FR, FX, sB, bd, sg.y, sg.z, acc);
-    bwd_seg<R, TI, 1, false>(P, a, i, pi, si, FR, FX, sB, bd, sg.z, sg.w, acc);
-    v4<R> fo4, go4;
-    fo4.x = acc.fx; fo4.y = acc.fy; fo4.z = acc.fz; fo4.w = R(0);
-    go4.x = acc.hx; go4.y = acc.hy; go4.z = acc.hz; go4.w = R(0);
-    a.fown[i] = fo4;
-    a.gii[i] = go4;
-    if (a.want_virial) {
-#pragma unroll
-        for (int t = 0; t < 9; ++t) a.wpart[(int64_t)t * N + i] = acc.w[t];
-    }
-}
-
-template <typename R>
-__global__ void k_bwd(const __grid_constant__ NepDev<R> P, const EvalArgs<R> a) {
-    extern __shared__ unsigned char smem_raw[];
-    R *sB = reinterpret_cast<R *>(smem_raw) + threadIdx.x;
-    const int bd = blockDim.x;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    if (i < a.n_fe) bwd_atom<R, 0>(P, a, i, sB, bd);
-    else bwd_atom<R, 1>(P, a, i, sB, bd);
-}
-
 // ------------------------------------------------------------------ launch
 template <typename R>
-static EvalArgs<R> make_args(Sys &s, bool want_virial);
-
-template <>
-EvalArgs<double> make_args<double>(Sys &s, bool want_virial) {
-    EvalArgs<double> a;
-    a.pos = s.pos; a.spin = s.spin; a.box = s.boxd;
-    a.nbr = s.nbr; a.seg = s.seg; a.n = s.n; a.n_fe = s.n_fe;
-    a.q = (double *)s.q; a.bsum = (double *)s.bsum; a.fp = (double *)s.fp; a.ei = (double *)s.ei;
-    a.pd0 = (double4 *)s.pd0; a.pd1 = (double2 *)s.pd1; a.fown = (double4 *)s.fown; a.gii = (double4 *)s.gii;
-    a.wpart = (double *)s.wpart; a.want_virial = want_virial;
-    return a;
-}
-
-template <>
-EvalArgs<float> make_args<float>(Sys &s, bool want_virial) {
-    EvalArgs<float> a;
-    a.pos = s.posf; a.spin = s.spinf; a.box = s.boxf;
-    a.nbr = s.nbr; a.seg = s.seg; a.n = s.n; a.n_fe = s.n_fe;
-    a.q = (float *)s.q; a.bsum = (float *)s.bsum; a.fp = (float *)s.fp; a.ei = (float *)s.ei;
-    a.pd0 = (float4 *)s.pd0; a.pd1 = (float2 *)s.pd1; a.fown = (float4 *)s.fown; a.gii = (float4 *)s.gii;
-    a.wpart = (float *)s.wpart; a.want_virial = want_virial;
-    return a;
-}
-
-template <typename R>
-static constexpr int bwd_block() { return sizeof(R) == 8 ? 32 : 64; }
-
-template <typename R>
-static void eval_impl(Sys &s, const NepDev<R> &P, bool want_virial, cudaEvent_t *ev) {
-    const EvalArgs<R> a = make_args<R>(s, want_virial);
+static void network_impl(Sys &s, const NepDev<R> &P) {
     const unsigned nb = (unsigned)((s.n + 127) / 128);
-    if (ev) cudaEventRecord(ev[0], s.stream);
-    k_fwd<R><<<nb, 128, 0, s.stream>>>(P, a);
-    if (ev) cudaEventRecord(ev[1], s.stream);
     k_mlp<R><<<nb, 128, 0, s.stream>>>(P, (const R *)s.q, (R *)s.fp, (R *)s.ei, s.n);
-    if (ev) cudaEventRecord(ev[2], s.stream);
-    const int bd = bwd_block<R>();
-    const size_t sm = (size_t)NB * bd * sizeof(R);
-    k_bwd<R><<<(unsigned)((s.n + bd - 1) / bd), bd, sm, s.stream>>>(P, a);
-    if (ev) cudaEventRecord(ev[3], s.stream);
 }
 
-// Kernel attributes are set once per process, before any stream capture.
-void eval_init() {
-    static bool done = false;
-    if (done) return;
-    cudaFuncSetAttribute(k_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(NB * bwd_block<float>() * sizeof(float)));
-    cudaFuncSetAttribute(k_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(NB * bwd_block<double>() * sizeof(double)));
-    done = true;
-}
-
-void launch_eval(Sys &s, bool want_virial, cudaEvent_t *ev) {
+void launch_network(Sys &s, cudaEvent_t *) {
     if (s.n == 0) return;
-    if (s.prec == 0) eval_impl<double>(s, s.pd, want_virial, ev);
-    else eval_impl<float>(s, s.pf, want_virial, ev);
+    if (s.prec == 0) network_impl<double>(s, s.pd);
+    else network_impl<float>(s, s.pf);
 }
-
-size_t eval_bytes(const Sys &s) {
-    const size_t r = s.prec == 0 ? 8 : 4;
-    const size_t n = (size_t)s.n;
-    return r * n * (2 * DIM + NB + 1 + 9) + r * 4 * n * 2 + r * 6 * n * (size_t)s.cap;
-}
-
 
 // ------------------------------------------------------------------ no-allocation variant
 // Descriptors and network energies of a small system in ONE kernel whose scratch

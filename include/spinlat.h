@@ -148,14 +148,16 @@ int sl_get_neighbors(sl_system *sys, int32_t cap, int32_t *counts_rad, int32_t *
 int sl_get_info(const sl_system *sys, int64_t *n_atoms, int32_t *precision, int64_t *n_builds,
                 int64_t *n_launches);
 
-/* Kernel groups timed by sl_step_profiled, in step order. */
-#define SL_K_FIRST_HALF 0    /* kicks, drifts, Langevin, spin predictor, rebuild test */
+/* Kernels (or kernel groups) timed by sl_step_profiled, in step order. */
+#define SL_K_FIRST_HALF 0    /* kicks, drifts, Langevin, spin predictor, rebuild test     */
 #define SL_K_REBUILD 1       /* binning + lists + reverse slots (early exit when not due) */
-#define SL_K_DESCRIPTOR 2    /* descriptor forward (k_fwd)                               */
-#define SL_K_NETWORK 3       /* per-atom network and its input gradient (k_mlp / tensor core) */
-#define SL_K_BACKWARD 4      /* backward to per-pair derivatives (k_bwd)                 */
-#define SL_K_SECOND_HALF 5   /* force/field gather, spin corrector, final kick          */
-#define SL_NKERNELS 6
+#define SL_K_RAD_FWD 2       /* in-cutoff compaction, radial and pairwise-magnetic channels */
+#define SL_K_ANG_FWD 3       /* angular and spin-angular channels                          */
+#define SL_K_NETWORK 4       /* per-atom network and its input gradient                    */
+#define SL_K_ANG_BWD 5       /* angular backward                                           */
+#define SL_K_RAD_BWD 6       /* radial / pairwise backward, pair records                   */
+#define SL_K_SECOND_HALF 7   /* force/field gather, spin corrector, final kick             */
+#define SL_NKERNELS 8
 
 /* Same as sl_step but without CUDA graphs and with CUDA events recorded on the
  * system's stream between the kernel groups; kernel_ms[SL_NKERNELS] receives the

@@ -680,8 +680,9 @@ int sl_step_profiled(sl_system *sys, int64_t n_steps, double dt, double T, const
     for (int c = 0; c < 3; ++c) s.B[c] = B[c];
     if (s.n == 0 || n_steps == 0) { s.step += (uint64_t)n_steps; return SL_OK; }
     CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
-    // events per step: before first half, before rebuild, before/inside eval (4), after second half
-    const int EV = 7;
+    // events per step: before first half, before rebuild, before each evaluation kernel (5), after the
+    // last one, after second half
+    const int EV = 9;
     std::vector<cudaEvent_t> ev((size_t)EV * n_steps);
     for (auto &e : ev) CK(cudaEventCreate(&e));
     for (int64_t t = 0; t < n_steps; ++t) {
@@ -690,9 +691,9 @@ int sl_step_profiled(sl_system *sys, int64_t n_steps, double dt, double T, const
         sl::launch_first_half(s);
         CK(cudaEventRecord(e[1], s.stream));
         sl::launch_rebuild(s, true);
-        sl::launch_eval(s, false, e + 2);   // e[2] before fwd, e[3] before mlp, e[4] before bwd, e[5] after bwd
+        sl::launch_eval(s, false, e + 2);   // e[2..7]
         sl::launch_second_half(s);
-        CK(cudaEventRecord(e[6], s.stream));
+        CK(cudaEventRecord(e[8], s.stream));
     }
     CK(cudaGetLastError());
     s.n_launches += n_steps * sl::KERNELS_PER_STEP;
@@ -700,9 +701,8 @@ int sl_step_profiled(sl_system *sys, int64_t n_steps, double dt, double T, const
     for (int64_t t = 0; t < n_steps && rc == SL_OK; ++t) {
         cudaEvent_t *e = ev.data() + EV * t;
         float ms;
-        const int from[SL_NKERNELS] = {0, 1, 2, 3, 4, 5}, to[SL_NKERNELS] = {1, 2, 3, 4, 5, 6};
         for (int k = 0; k < SL_NKERNELS; ++k) {
-            CK(cudaEventElapsedTime(&ms, e[from[k]], e[to[k]]));
+            CK(cudaEventElapsedTime(&ms, e[k], e[k + 1]));
             kernel_ms[k] += ms;
         }
     }

@@ -267,6 +267,23 @@ __device__ __forceinline__ void gauss3(uint64_t step, uint64_t atom, uint64_t st
     z[2] = rho2 * cospi(2.0 * u4);
 }
 
+// Three standard normals in FP32 from the same Philox block: 24-bit uniforms
+// u1 in (0,1], u2 in [0,1), Box-Muller (the reduced-precision integrator's noise).
+__device__ __forceinline__ void gauss3f(uint64_t step, uint64_t atom, uint64_t stream, uint64_t seed,
+                                        uint64_t replica, float z[3]) {
+    uint64_t c0 = step, c1 = atom, c2 = stream, c3 = 0;
+    philox4x64_10(c0, c1, c2, c3, seed, replica);
+    const float two24 = 1.0f / 16777216.0f;
+    const float u1 = ((float)(c0 >> 40) + 1.0f) * two24, u2 = (float)(c1 >> 40) * two24;
+    const float u3 = ((float)(c2 >> 40) + 1.0f) * two24, u4 = (float)(c3 >> 40) * two24;
+    float s, c;
+    const float rho1 = sqrtf(-2.0f * logf(u1));
+    sincospif(2.0f * u2, &s, &c);
+    z[0] = rho1 * c;
+    z[1] = rho1 * s;
+    z[2] = sqrtf(-2.0f * logf(u3)) * cospif(2.0f * u4);
+}
+
 // Device status bits.
 constexpr int ST_NBR_OVERFLOW = 1;
 constexpr int ST_NONFINITE = 2;

@@ -85,24 +85,38 @@ __device__ __forceinline__ void rad_sums(const NepDev<R> &P, const Eval2Args<R> 
 #pragma unroll
     for (int k = 0; k < NK; ++k) { b0[k] = b1[k] = b2[k] = b3[k] = b4[k] = R(0); }
     const int64_t N = a.n;
-#pragma unroll 1
-    for (int part = 0; part < 2; ++part) {
-        const int lo = part ? r2 : r0, hi = part ? r3 : r1;
-        for (int row = lo; row < hi; ++row) {
-            const int j = a.clj[(int64_t)row * N + i];
-            const v4<R> pj = a.pos[j], sj = a.spin[j];
+    const int len0 = r1 - r0, len = len0 + (r3 - r2);
+    const int32_t *__restrict__ clj = a.clj;
+    const v4<R> *__restrict__ pos = a.pos;
+    const v4<R> *__restrict__ spin = a.spin;
+    // rows r0..r1 then r2..r3, with the next pair's loads issued before this pair's arithmetic
+    v4<R> pj, sj;
+    if (len > 0) {
+        const int j = clj[(int64_t)r0 * N + i];
+        pj = pos[j];
+        sj = spin[j];
+    }
+    for (int t = 0; t < len; ++t) {
+        const v4<R> cp = pj, cs = sj;
+        if (t + 1 < len) {
+            const int rn = t + 1 < len0 ? r0 + t + 1 : r2 + (t + 1 - len0);
+            const int j = clj[(int64_t)rn * N + i];
+            pj = pos[j];
+            sj = spin[j];
+        }
+        {
             R dx, dy, dz;
-            sep(a.box, pi, pj, dx, dy, dz);
+            sep(a.box, pi, cp, dx, dy, dz);
             const R d2 = dx * dx + dy * dy + dz * dz;
             const R ir = rsqrt_(d2), r = d2 * ir;
             const R ux = dx * ir, uy = dy * ir, uz = dz * ir;
             R f[NK];
             carrier_f(r, P.inv_rc_r, f);
-            const R sij = si.x * sj.x + si.y * sj.y + si.z * sj.z;
+            const R sij = si.x * cs.x + si.y * cs.y + si.z * cs.z;
             const R siu = si.x * ux + si.y * uy + si.z * uz;
-            const R sju = sj.x * ux + sj.y * uy + sj.z * uz;
-            const R dmi = (si.y * sj.z - si.z * sj.y) * ux + (si.z * sj.x - si.x * sj.z) * uy +
-                          (si.x * sj.y - si.y * sj.x) * uz;
+            const R sju = cs.x * ux + cs.y * uy + cs.z * uz;
+            const R dmi = (si.y * cs.z - si.z * cs.y) * ux + (si.z * cs.x - si.x * cs.z) * uy +
+                          (si.x * cs.y - si.y * cs.x) * uz;
             const R ani = siu * sju, sia = siu * siu;
 #pragma unroll
             for (int k = 0; k < NK; ++k) {
@@ -132,7 +146,11 @@ __device__ __forceinline__ void rad_fwd_atom(const NepDev<R> &P, const Eval2Args
     const int64_t N = a.n;
     const v4<R> pi = a.pos[i], si = a.spin[i];
     const int4 sg = a.seg[i];
-    // pass 1: compaction, neighbour species 0 first (candidate segments 0 and 2), then 1 (1 and 3)
+    // pass 1: compaction, neighbour species 0 first (candidate segments 0 and 2), then 1 (1 and 3);
+    // candidate loads are issued four at a time to keep several gathers in flight
+    const int32_t *__restrict__ nbr = a.nbr;
+    const int32_t *__restrict__ rev = a.rev;
+    const v4<R> *__restrict__ pos = a.pos;
     int na = 0, nr = 0, na0 = 0, nr0 = 0;
 #pragma unroll 1
     for (int tj = 0; tj < 2; ++tj) {
@@ -140,25 +158,34 @@ __device__ __forceinline__ void rad_fwd_atom(const NepDev<R> &P, const Eval2Args
         for (int part = 0; part < 2; ++part) {
             const int lo = part == 0 ? (tj == 0 ? 0 : sg.x) : (tj == 0 ? sg.y : sg.z);
             const int hi = part == 0 ? (tj == 0 ? sg.x : sg.y) : (tj == 0 ? sg.z : sg.w);
-            for (int s = lo; s < hi; ++s) {
-                const int j = a.nbr[(int64_t)s * N + i];
-                const v4<R> pj = a.pos[j];
-                R dx, dy, dz;
-                sep(a.box, pi, pj, dx, dy, dz);
-                const R d2 = dx * dx + dy * dy + dz * dz;
-                if (d2 < P.rc_r2) {
-                    int row;
-                    if (d2 < P.rc_a2) {
-                        if (na >= a.cap_ang) {   // only after a list overflow; keeps every row in bounds
-                            atomicOr(a.status, ST_NBR_OVERFLOW);
-                            continue;
+            for (int s0 = lo; s0 < hi; s0 += 4) {
+                int jj[4];
+                v4<R> pp[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) jj[u] = s0 + u < hi ? nbr[(int64_t)(s0 + u) * N + i] : -1;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) pp[u] = pos[jj[u] >= 0 ? jj[u] : i];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (jj[u] < 0) continue;
+                    R dx, dy, dz;
+                    sep(a.box, pi, pp[u], dx, dy, dz);
+                    const R d2 = dx * dx + dy * dy + dz * dz;
+                    if (d2 < P.rc_r2) {
+                        int row;
+                        if (d2 < P.rc_a2) {
+                            if (na >= a.cap_ang) {   // only after a list overflow; keeps every row in bounds
+                                atomicOr(a.status, ST_NBR_OVERFLOW);
+                                continue;
+                            }
+                            row = na++;
+                        } else {
+                            row = a.cap_ang + nr++;
                         }
-                        row = na++;
-                    } else {
-                        row = a.cap_ang + nr++;
+                        const int t = rev[(int64_t)(s0 + u) * N + i];
+                        a.clj[(int64_t)row * N + i] = jj[u];
+                        a.cls[(int64_t)row * N + i] = (uint16_t)((s0 + u) | (t << 8));
                     }
-                    a.clj[(int64_t)row * N + i] = j;
-                    a.cls[(int64_t)row * N + i] = (uint8_t)s;
                 }
             }
         }
@@ -197,10 +224,8 @@ constexpr int FSTAGE = 36;
 constexpr int FQUAD = 4 * FSTAGE + 4;   // per quad, padded so quads start in different banks
 
 template <typename R, int TI, int TJ>
-__device__ __forceinline__ void ang_stage_fwd(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, const v4<R> &pi,
-                                              const v4<R> &si, int p, R *st) {
-    const int j = a.clj[(int64_t)p * a.n + i];
-    const v4<R> pj = a.pos[j], sj = a.spin[j];
+__device__ __forceinline__ void ang_stage_fwd(const NepDev<R> &P, const Eval2Args<R> &a, const v4<R> &pi,
+                                              const v4<R> &si, const v4<R> &pj, const v4<R> &sj, R *st) {
     R dx, dy, dz;
     sep(a.box, pi, pj, dx, dy, dz);
     const R d2 = dx * dx + dy * dy + dz * dz;
@@ -242,16 +267,29 @@ __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<
 #pragma unroll
         for (int n = 0; n < NCH; ++n) { B[m][n] = R(0); BS[m][n] = R(0); }
     const int nmax = __reduce_max_sync(0xffffffffu, na);
+    // the lane's pair of the next round is loaded one round ahead
+    v4<R> pjn, sjn;
+    if (ql < na) {
+        const int j = a.clj[(int64_t)ql * N + i];
+        pjn = a.pos[j];
+        sjn = a.spin[j];
+    }
     for (int base = 0; base < nmax; base += 4) {
         const int p = base + ql;
+        const v4<R> pj = pjn, sj = sjn;
+        if (p + 4 < na) {
+            const int j = a.clj[(int64_t)(p + 4) * N + i];
+            pjn = a.pos[j];
+            sjn = a.spin[j];
+        }
         if (p < na) {
             R *st = stage + ql * FSTAGE;
             if (ti == 0) {
-                if (p < na0) ang_stage_fwd<R, 0, 0>(P, a, i, pi, si, p, st);
-                else ang_stage_fwd<R, 0, 1>(P, a, i, pi, si, p, st);
+                if (p < na0) ang_stage_fwd<R, 0, 0>(P, a, pi, si, pj, sj, st);
+                else ang_stage_fwd<R, 0, 1>(P, a, pi, si, pj, sj, st);
             } else {
-                if (p < na0) ang_stage_fwd<R, 1, 0>(P, a, i, pi, si, p, st);
-                else ang_stage_fwd<R, 1, 1>(P, a, i, pi, si, p, st);
+                if (p < na0) ang_stage_fwd<R, 1, 0>(P, a, pi, si, pj, sj, st);
+                else ang_stage_fwd<R, 1, 1>(P, a, pi, si, pj, sj, st);
             }
         }
         __syncwarp();
@@ -342,10 +380,8 @@ __device__ __forceinline__ void stage_harm(R x, R y, R z, R *dst) {
 }
 
 template <typename R, int TI, int TJ>
-__device__ __forceinline__ void ang_stage_bwd(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, const v4<R> &pi,
-                                              const v4<R> &si, int p, R *st) {
-    const int j = a.clj[(int64_t)p * a.n + i];
-    const v4<R> pj = a.pos[j], sj = a.spin[j];
+__device__ __forceinline__ void ang_stage_bwd(const NepDev<R> &P, const Eval2Args<R> &a, const v4<R> &pi,
+                                              const v4<R> &si, const v4<R> &pj, const v4<R> &sj, R *st) {
     R dx, dy, dz;
     sep(a.box, pi, pj, dx, dy, dz);
     const R d2 = dx * dx + dy * dy + dz * dz;
@@ -408,16 +444,29 @@ __global__ void __launch_bounds__(128) k_ang_bwd(const __grid_constant__ NepDev<
     }
     R hx = R(0), hy = R(0), hz = R(0);
     const int nmax = __reduce_max_sync(0xffffffffu, na);
+    // the lane's pair of the next round is loaded one round ahead
+    v4<R> pjn, sjn;
+    if (ql < na) {
+        const int j = a.clj[(int64_t)ql * N + i];
+        pjn = a.pos[j];
+        sjn = a.spin[j];
+    }
     for (int base = 0; base < nmax; base += 4) {
         const int p = base + ql;
+        const v4<R> pj = pjn, sj = sjn;
+        if (p + 4 < na) {
+            const int j = a.clj[(int64_t)(p + 4) * N + i];
+            pjn = a.pos[j];
+            sjn = a.spin[j];
+        }
         if (p < na) {
             R *st = stage + ql * BSTAGE;
             if (ti == 0) {
-                if (p < na0) ang_stage_bwd<R, 0, 0>(P, a, i, pi, si, p, st);
-                else ang_stage_bwd<R, 0, 1>(P, a, i, pi, si, p, st);
+                if (p < na0) ang_stage_bwd<R, 0, 0>(P, a, pi, si, pj, sj, st);
+                else ang_stage_bwd<R, 0, 1>(P, a, pi, si, pj, sj, st);
             } else {
-                if (p < na0) ang_stage_bwd<R, 1, 0>(P, a, i, pi, si, p, st);
-                else ang_stage_bwd<R, 1, 1>(P, a, i, pi, si, p, st);
+                if (p < na0) ang_stage_bwd<R, 1, 0>(P, a, pi, si, pj, sj, st);
+                else ang_stage_bwd<R, 1, 1>(P, a, pi, si, pj, sj, st);
             }
         }
         __syncwarp();
@@ -498,10 +547,33 @@ __device__ __forceinline__ void rad_bwd_rows(const NepDev<R> &P, const Eval2Args
                                              const v4<R> &si, const R C0[NK], const R C1[NK], const R C2[NK],
                                              const R C3[NK], const R C4[NK], int lo, int hi, RadAcc<R> &acc) {
     const int64_t N = a.n;
+    const int32_t *__restrict__ clj = a.clj;
+    const uint16_t *__restrict__ cls = a.cls;
+    const v4<R> *__restrict__ pos = a.pos;
+    const v4<R> *__restrict__ spin = a.spin;
+    const v4<R> *__restrict__ apair = a.apair;
+    // one-pair prefetch: the next pair's loads are in flight during this pair's arithmetic
+    int jn = 0, tn = 0;
+    v4<R> pn, sn, an;
+    if (lo < hi) {
+        jn = clj[(int64_t)lo * N + i];
+        tn = cls[(int64_t)lo * N + i] >> 8;
+        pn = pos[jn];
+        sn = spin[jn];
+        if constexpr (ANG) an = apair[(int64_t)lo * N + i];
+    }
     for (int row = lo; row < hi; ++row) {
-        const int j = a.clj[(int64_t)row * N + i];
-        const int s = a.cls[(int64_t)row * N + i];
-        const v4<R> pj = a.pos[j], sj = a.spin[j];
+        const int j = jn, t = tn;
+        const v4<R> pj = pn, sj = sn;
+        v4<R> ap;
+        if constexpr (ANG) ap = an;
+        if (row + 1 < hi) {
+            jn = clj[(int64_t)(row + 1) * N + i];
+            tn = cls[(int64_t)(row + 1) * N + i] >> 8;
+            pn = pos[jn];
+            sn = spin[jn];
+            if constexpr (ANG) an = apair[(int64_t)(row + 1) * N + i];
+        }
         R dx, dy, dz;
         sep(a.box, pi, pj, dx, dy, dz);
         const R d2 = dx * dx + dy * dy + dz * dz;
@@ -539,7 +611,6 @@ __device__ __forceinline__ void rad_bwd_rows(const NepDev<R> &P, const Eval2Args
         acc.hy += h1 * sj.y + h2 * (sj.z * ux - sj.x * uz) + cu * uy;
         acc.hz += h1 * sj.z + h2 * (sj.x * uy - sj.y * ux) + cu * uz;
         if constexpr (ANG) {
-            const v4<R> ap = a.apair[(int64_t)row * N + i];
             Dx += ap.x; Dy += ap.y; Dz += ap.z;
             Gx += ap.w * si.x; Gy += ap.w * si.y; Gz += ap.w * si.z;
         }
@@ -549,8 +620,7 @@ __device__ __forceinline__ void rad_bwd_rows(const NepDev<R> &P, const Eval2Args
             acc.w[3] -= dy * Dx; acc.w[4] -= dy * Dy; acc.w[5] -= dy * Dz;
             acc.w[6] -= dz * Dx; acc.w[7] -= dz * Dy; acc.w[8] -= dz * Dz;
         }
-        // record for neighbour j, in j's own slot of i
-        const int t = a.rev[(int64_t)s * N + i];
+        // record for neighbour j, in j's own slot t of i
         PairRec<R> rec;
         rec.a.x = Dx; rec.a.y = Dy; rec.a.z = Dz; rec.a.w = Gx;
         rec.b.x = Gy; rec.b.y = Gz; rec.b.z = R(0); rec.b.w = R(0);
@@ -675,13 +745,15 @@ static void eval2_impl(Sys &s, const NepDev<R> &P, bool want_virial, cudaEvent_t
     const unsigned nq = (unsigned)((s.n + qb / 4 - 1) / (qb / 4));
     if (ev) cudaEventRecord(ev[0], s.stream);
     k_rad_fwd<R><<<nb, 128, 0, s.stream>>>(P, a);
-    k_ang_fwd<R><<<nq, qb, fwd_smem<R>(), s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[1], s.stream);
-    launch_network(s, ev ? nullptr : nullptr);
+    k_ang_fwd<R><<<nq, qb, fwd_smem<R>(), s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[2], s.stream);
-    k_ang_bwd<R><<<nq, qb, bwd_smem<R>(), s.stream>>>(P, a);
-    k_rad_bwd<R><<<nb, 128, 0, s.stream>>>(P, a);
+    launch_network(s, nullptr);
     if (ev) cudaEventRecord(ev[3], s.stream);
+    k_ang_bwd<R><<<nq, qb, bwd_smem<R>(), s.stream>>>(P, a);
+    if (ev) cudaEventRecord(ev[4], s.stream);
+    k_rad_bwd<R><<<nb, 128, 0, s.stream>>>(P, a);
+    if (ev) cudaEventRecord(ev[5], s.stream);
 }
 
 void launch_eval(Sys &s, bool want_virial, cudaEvent_t *ev) {

@@ -22,7 +22,7 @@ struct Eval2Args {
     BoxDev<R> box;
     int cap, cap_ang;
     int32_t *clj;      // compact in-cutoff rows [cap_ang + cap][n]: neighbour index
-    uint8_t *cls;      // ... and its candidate slot
+    uint16_t *cls;     // ... its candidate slot s (low byte) and the reverse slot rev[s][i] (high byte)
     int4 *cnt;         // (angular rows of species 0, angular rows, radial-only rows of species 0, radial-only rows)
     R *q, *bsum, *fp, *ei;
     v4<R> *apair;      // [cap_ang][n]: angular dE_i/dr_ij (x, y, z) and spin weight c_ij

@@ -35,7 +35,7 @@ template <typename R>
 struct GatherArgs {
     const v4<R> *fown, *gii;
     const PairRec<R> *pd;
-    const uint8_t *cls;
+    const uint16_t *cls;
     const int4 *cnt;
     int64_t n;
     int cap_ang;
@@ -62,6 +62,31 @@ __device__ __forceinline__ void rotate(double sx, double sy, double sz, const do
     out[2] = sz * c + cz * s + az * as * (1.0 - c);
 }
 
+// Rotation increment dS = Rot(S, w dt) - S in FP32 (added to the FP64 spin by the
+// caller): dS = (a x S) sin(th) - 2 sin^2(th/2) (S - a (a.S)), th = |w| dt.
+__device__ __forceinline__ void rotate_delta_f(float sx, float sy, float sz, float wx, float wy, float wz, float dt,
+                                               float d[3]) {
+    const float wn2 = wx * wx + wy * wy + wz * wz;
+    if (wn2 == 0.0f) { d[0] = d[1] = d[2] = 0.0f; return; }
+    const float iw = rsqrtf(wn2);
+    const float ax = wx * iw, ay = wy * iw, az = wz * iw;
+    float sh, ch;
+    sincosf(0.5f * wn2 * iw * dt, &sh, &ch);
+    const float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
+    const float as = ax * sx + ay * sy + az * sz;
+    d[0] = (ay * sz - az * sy) * sn - omc * (sx - ax * as);
+    d[1] = (az * sx - ax * sz) * sn - omc * (sy - ay * as);
+    d[2] = (ax * sy - ay * sx) * sn - omc * (sz - az * as);
+}
+
+__device__ __forceinline__ void omega_of_f(float sx, float sy, float sz, float hx, float hy, float hz, float lam,
+                                           float k, float w[3]) {
+    w[0] = (hx + lam * (sy * hz - sz * hy)) * k;
+    w[1] = (hy + lam * (sz * hx - sx * hz)) * k;
+    w[2] = (hz + lam * (sx * hy - sy * hx)) * k;
+}
+
+template <bool MIXED>
 __global__ void __launch_bounds__(256) k_first_half(IntArgs a) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const unsigned long long st = a.step[0];
@@ -74,20 +99,38 @@ __global__ void __launch_bounds__(256) k_first_half(IntArgs a) {
     const double4 F = a.F[i], H = a.H[i], S = a.spin[i];
     const double hdt = P.half_dt, am = P.acc_m[t];
     double xi[3], ze[3];
-    gauss3(st, id, 1, a.seed, a.replica, xi);
-    gauss3(st, id, 2, a.seed, a.replica, ze);
+    if constexpr (MIXED) {
+        float x3[3], z3[3];
+        gauss3f(st, id, 1, a.seed, a.replica, x3);
+        gauss3f(st, id, 2, a.seed, a.replica, z3);
+        for (int c = 0; c < 3; ++c) { xi[c] = x3[c]; ze[c] = z3[c]; }
+    } else {
+        gauss3(st, id, 1, a.seed, a.replica, xi);
+        gauss3(st, id, 2, a.seed, a.replica, ze);
+    }
     v.x += hdt * F.x * am; v.y += hdt * F.y * am; v.z += hdt * F.z * am;
     r.x += hdt * v.x; r.y += hdt * v.y; r.z += hdt * v.z;
     const double c = P.c_fric, sv = P.sig_v[t];
     v.x = c * v.x + sv * xi[0]; v.y = c * v.y + sv * xi[1]; v.z = c * v.z + sv * xi[2];
     r.x += hdt * v.x; r.y += hdt * v.y; r.z += hdt * v.z;
-    if (a.per[0]) r.x = r.x - a.bd.L[0] * floor(r.x / a.bd.L[0]);
-    if (a.per[1]) r.y = r.y - a.bd.L[1] * floor(r.y / a.bd.L[1]);
-    if (a.per[2]) r.z = r.z - a.bd.L[2] * floor(r.z / a.bd.L[2]);
+    if (a.per[0]) r.x = r.x - a.bd.L[0] * floor(r.x * a.bd.invL[0]);
+    if (a.per[1]) r.y = r.y - a.bd.L[1] * floor(r.y * a.bd.invL[1]);
+    if (a.per[2]) r.z = r.z - a.bd.L[2] * floor(r.z * a.bd.invL[2]);
     const double se = P.sig_eta;
-    double w[3], Sp[3];
-    omega_of(S.x, S.y, S.z, H.x + se * ze[0], H.y + se * ze[1], H.z + se * ze[2], P.lambda, P.wscale, w);
-    rotate(S.x, S.y, S.z, w, P.dt, Sp);
+    double Sp[3];
+    if constexpr (MIXED) {
+        float w[3], d[3];
+        const float fse = (float)se;
+        omega_of_f((float)S.x, (float)S.y, (float)S.z, (float)H.x + fse * (float)ze[0],
+                   (float)H.y + fse * (float)ze[1], (float)H.z + fse * (float)ze[2], (float)P.lambda,
+                   (float)P.wscale, w);
+        rotate_delta_f((float)S.x, (float)S.y, (float)S.z, w[0], w[1], w[2], (float)P.dt, d);
+        Sp[0] = S.x + (double)d[0]; Sp[1] = S.y + (double)d[1]; Sp[2] = S.z + (double)d[2];
+    } else {
+        double w[3];
+        omega_of(S.x, S.y, S.z, H.x + se * ze[0], H.y + se * ze[1], H.z + se * ze[2], P.lambda, P.wscale, w);
+        rotate(S.x, S.y, S.z, w, P.dt, Sp);
+    }
     a.pos[i] = r;
     a.vel[i] = v;
     a.spin_prev[i] = S;
@@ -113,7 +156,7 @@ __device__ __forceinline__ void gather(const GatherArgs<R> &g, int64_t k, double
     for (int part = 0; part < 2; ++part) {
         const int lo = part ? g.cap_ang : 0, hi = part ? g.cap_ang + c.w : c.y;
         for (int row = lo; row < hi; ++row) {
-            const int s = g.cls[(int64_t)row * N + k];
+            const int s = g.cls[(int64_t)row * N + k] & 0xff;
             const PairRec<R> e = g.pd[(int64_t)s * N + k];
             fx -= e.a.x; fy -= e.a.y; fz -= e.a.z;
             hx -= e.a.w; hy -= e.b.x; hz -= e.b.y;
@@ -123,7 +166,7 @@ __device__ __forceinline__ void gather(const GatherArgs<R> &g, int64_t k, double
     H[0] = (double)hx; H[1] = (double)hy; H[2] = (double)hz;
 }
 
-template <typename R>
+template <typename R, bool MIXED>
 __global__ void __launch_bounds__(256) k_second_half(IntArgs a, GatherArgs<R> g) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i == 0) a.step[0] = a.step[1] + 1;
@@ -135,17 +178,32 @@ __global__ void __launch_bounds__(256) k_second_half(IntArgs a, GatherArgs<R> g)
     double Fs[3], Hs[3];
     gather<R>(g, i, Fs, Hs);
     Hs[0] += P.zee[t][0]; Hs[1] += P.zee[t][1]; Hs[2] += P.zee[t][2];
-    double ze[3];
-    gauss3(st, id, 2, a.seed, a.replica, ze);
     const double se = P.sig_eta;
     const double4 S0 = a.spin_prev[i], S1 = a.spin[i], H0 = a.H[i];
-    double w0[3], w1[3], w[3], Sn[3];
-    omega_of(S0.x, S0.y, S0.z, H0.x + se * ze[0], H0.y + se * ze[1], H0.z + se * ze[2], P.lambda, P.wscale, w0);
-    omega_of(S1.x, S1.y, S1.z, Hs[0] + se * ze[0], Hs[1] + se * ze[1], Hs[2] + se * ze[2], P.lambda, P.wscale, w1);
-    w[0] = 0.5 * (w0[0] + w1[0]); w[1] = 0.5 * (w0[1] + w1[1]); w[2] = 0.5 * (w0[2] + w1[2]);
-    rotate(S0.x, S0.y, S0.z, w, P.dt, Sn);
-    const double nn = sqrt(Sn[0] * Sn[0] + Sn[1] * Sn[1] + Sn[2] * Sn[2]);
-    Sn[0] /= nn; Sn[1] /= nn; Sn[2] /= nn;
+    double Sn[3];
+    if constexpr (MIXED) {
+        float ze[3], w0[3], w1[3], d[3];
+        gauss3f(st, id, 2, a.seed, a.replica, ze);
+        const float fse = (float)se, lam = (float)P.lambda, k = (float)P.wscale;
+        omega_of_f((float)S0.x, (float)S0.y, (float)S0.z, (float)H0.x + fse * ze[0], (float)H0.y + fse * ze[1],
+                   (float)H0.z + fse * ze[2], lam, k, w0);
+        omega_of_f((float)S1.x, (float)S1.y, (float)S1.z, (float)Hs[0] + fse * ze[0], (float)Hs[1] + fse * ze[1],
+                   (float)Hs[2] + fse * ze[2], lam, k, w1);
+        rotate_delta_f((float)S0.x, (float)S0.y, (float)S0.z, 0.5f * (w0[0] + w1[0]), 0.5f * (w0[1] + w1[1]),
+                       0.5f * (w0[2] + w1[2]), (float)P.dt, d);
+        Sn[0] = S0.x + (double)d[0]; Sn[1] = S0.y + (double)d[1]; Sn[2] = S0.z + (double)d[2];
+    } else {
+        double ze[3], w0[3], w1[3], w[3];
+        gauss3(st, id, 2, a.seed, a.replica, ze);
+        omega_of(S0.x, S0.y, S0.z, H0.x + se * ze[0], H0.y + se * ze[1], H0.z + se * ze[2], P.lambda, P.wscale, w0);
+        omega_of(S1.x, S1.y, S1.z, Hs[0] + se * ze[0], Hs[1] + se * ze[1], Hs[2] + se * ze[2], P.lambda, P.wscale,
+                 w1);
+        w[0] = 0.5 * (w0[0] + w1[0]); w[1] = 0.5 * (w0[1] + w1[1]); w[2] = 0.5 * (w0[2] + w1[2]);
+        rotate(S0.x, S0.y, S0.z, w, P.dt, Sn);
+    }
+    // renormalisation in FP64 after every rotation
+    const double inn = 1.0 / sqrt(Sn[0] * Sn[0] + Sn[1] * Sn[1] + Sn[2] * Sn[2]);
+    Sn[0] *= inn; Sn[1] *= inn; Sn[2] *= inn;
     double4 v = a.vel[i];
     const double hdt = P.half_dt, am = P.acc_m[t];
     v.x += hdt * Fs[0] * am; v.y += hdt * Fs[1] * am; v.z += hdt * Fs[2] * am;
@@ -198,12 +256,14 @@ static GatherArgs<R> gather_args(Sys &s) {
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 void launch_first_half(Sys &s) {
-    k_first_half<<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s));
+    if (s.prec == 0) k_first_half<false><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s));
+    else k_first_half<true><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s));
 }
 
 void launch_second_half(Sys &s) {
-    if (s.prec == 0) k_second_half<double><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<double>(s));
-    else k_second_half<float><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<float>(s));
+    if (s.prec == 0)
+        k_second_half<double, false><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<double>(s));
+    else k_second_half<float, true><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<float>(s));
 }
 
 void launch_gather(Sys &s, bool carried) {

@@ -70,7 +70,7 @@ struct Sys {
     void *ei = nullptr;        // [n]
     void *pairs = nullptr;     // [cap][n] pair records (see sl_eval2.cuh)
     int32_t *clj = nullptr;    // [cap_ang + cap][n] compact in-cutoff neighbours
-    uint8_t *cls = nullptr;    // [cap_ang + cap][n] their candidate slots
+    uint16_t *cls = nullptr;   // [cap_ang + cap][n] candidate slot | reverse slot << 8
     int4 *cnt = nullptr;       // [n] compact row counts
     void *apair = nullptr;     // [cap_ang][n] angular pair derivatives
     void *gii_ang = nullptr;   // [n] angular dE_i/dS_i
@@ -104,8 +104,8 @@ struct Sys {
 void nbr_setup(Sys &s);
 void launch_rebuild(Sys &s, bool conditional);
 // sl_nep.cu
-// ev (optional, 4 events): recorded before the descriptor, network and backward
-// kernels and after the backward kernels (sl_eval2.cu).
+// ev (optional, 6 events): recorded before each of the five evaluation kernels and
+// after the last one (sl_eval2.cu).
 void launch_eval(Sys &s, bool want_virial, cudaEvent_t *ev = nullptr);
 void eval2_init();
 void launch_network(Sys &s, cudaEvent_t *ev);   // sl_nep.cu

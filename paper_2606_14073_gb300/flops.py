@@ -33,10 +33,21 @@ BWD_RADIAL_PAIR = 380
 BWD_ANGULAR_PAIR = 1850
 
 
+# split of the per-atom terms between the radial and angular kernels
+FWD_ATOM_RAD = 900       # coefficient contraction, 2 neighbour species
+FWD_ATOM_ANG = 720       # squared angular sums into q
+BWD_ATOM_RAD = 900       # coefficient precontraction
+BWD_ATOM_ANG = 720       # angular adjoints
+
+
 def per_atom(n_r: float, n_a: float) -> dict:
-    fwd = FWD_ATOM + FWD_RADIAL_PAIR * n_r + FWD_ANGULAR_PAIR * n_a
-    bwd = BWD_ATOM + BWD_RADIAL_PAIR * n_r + BWD_ANGULAR_PAIR * n_a
-    return dict(descriptor=fwd, network=float(NETWORK_ATOM), backward=bwd, total=fwd + NETWORK_ATOM + bwd)
+    rad_fwd = FWD_ATOM_RAD + FWD_RADIAL_PAIR * n_r
+    ang_fwd = FWD_ATOM_ANG + FWD_ANGULAR_PAIR * n_a
+    ang_bwd = BWD_ATOM_ANG + BWD_ANGULAR_PAIR * n_a
+    rad_bwd = BWD_ATOM_RAD + BWD_RADIAL_PAIR * n_r
+    total = rad_fwd + ang_fwd + NETWORK_ATOM + ang_bwd + rad_bwd
+    return dict(rad_fwd=rad_fwd, ang_fwd=ang_fwd, network=float(NETWORK_ATOM), ang_bwd=ang_bwd, rad_bwd=rad_bwd,
+                descriptor=rad_fwd + ang_fwd, backward=ang_bwd + rad_bwd, total=total)
 
 
 def crystal_counts() -> tuple[float, float]:

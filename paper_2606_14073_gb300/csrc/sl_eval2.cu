@@ -3,10 +3,10 @@
 // Same mathematics as the descriptor of arXiv 2606.14073 (Sections 5.1.1-5.1.2, 5.2.3-5.2.4)
 // described in sl_nep.cu; this file maps it onto the GPU differently:
 //
-//   k_rad_fwd  one thread per atom.  Pass 1 compacts the candidate list (which
-//              carries a skin) into the pairs inside the cutoffs: angular rows
-//              (r < rc_ang) and radial-only rows (rc_ang <= r < rc_rad), each grouped by
-//              neighbour species; pass 2 accumulates the radial and pairwise-magnetic
+//   k_compact  one thread per atom: compacts the candidate list (which carries a
+//              skin) into the pairs inside the cutoffs: angular rows (r < rc_ang) and
+//              radial-only rows (rc_ang <= r < rc_rad), each grouped by neighbour species.
+//   k_rad_fwd  one thread per atom: accumulates the radial and pairwise-magnetic
 //              basis sums over those rows and contracts them with the coefficients
 //              once per neighbour species (q^R, q^EX, q^DMI, q^ANI, q^SIA, q^O).
 //   k_ang_fwd  four lanes per atom.  Each lane stages one angular pair (carrier, g_n,
@@ -141,16 +141,19 @@ __device__ __forceinline__ void rad_sums(const NepDev<R> &P, const Eval2Args<R> 
     }
 }
 
-template <typename R, int TI>
-__device__ __forceinline__ void rad_fwd_atom(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i) {
+// In-cutoff compaction of atom i's candidate list: angular rows (r < rc_ang) then
+// radial-only rows, each grouped by neighbour species (species 0 from candidate
+// segments 0 and 2, then species 1 from 1 and 3).  Candidates are loaded eight at
+// a time to keep several gathers in flight per thread.
+template <typename R>
+__device__ __forceinline__ void compact_atom(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i) {
     const int64_t N = a.n;
-    const v4<R> pi = a.pos[i], si = a.spin[i];
+    const v4<R> pi = a.pos[i];
     const int4 sg = a.seg[i];
-    // pass 1: compaction, neighbour species 0 first (candidate segments 0 and 2), then 1 (1 and 3);
-    // candidate loads are issued four at a time to keep several gathers in flight
     const int32_t *__restrict__ nbr = a.nbr;
     const int32_t *__restrict__ rev = a.rev;
     const v4<R> *__restrict__ pos = a.pos;
+    constexpr int BATCH = 8;
     int na = 0, nr = 0, na0 = 0, nr0 = 0;
 #pragma unroll 1
     for (int tj = 0; tj < 2; ++tj) {
@@ -158,15 +161,15 @@ __device__ __forceinline__ void rad_fwd_atom(const NepDev<R> &P, const Eval2Args
         for (int part = 0; part < 2; ++part) {
             const int lo = part == 0 ? (tj == 0 ? 0 : sg.x) : (tj == 0 ? sg.y : sg.z);
             const int hi = part == 0 ? (tj == 0 ? sg.x : sg.y) : (tj == 0 ? sg.z : sg.w);
-            for (int s0 = lo; s0 < hi; s0 += 4) {
-                int jj[4];
-                v4<R> pp[4];
+            for (int s0 = lo; s0 < hi; s0 += BATCH) {
+                int jj[BATCH];
+                v4<R> pp[BATCH];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) jj[u] = s0 + u < hi ? nbr[(int64_t)(s0 + u) * N + i] : -1;
+                for (int u = 0; u < BATCH; ++u) jj[u] = s0 + u < hi ? nbr[(int64_t)(s0 + u) * N + i] : -1;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) pp[u] = pos[jj[u] >= 0 ? jj[u] : i];
+                for (int u = 0; u < BATCH; ++u) pp[u] = pos[jj[u] >= 0 ? jj[u] : i];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < BATCH; ++u) {
                     if (jj[u] < 0) continue;
                     R dx, dy, dz;
                     sep(a.box, pi, pp[u], dx, dy, dz);
@@ -192,7 +195,22 @@ __device__ __forceinline__ void rad_fwd_atom(const NepDev<R> &P, const Eval2Args
         if (tj == 0) { na0 = na; nr0 = nr; }
     }
     a.cnt[i] = make_int4(na0, na, nr0, nr);
-    // pass 2: radial and pairwise-magnetic sums over the in-cutoff pairs
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_compact(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    compact_atom<R>(P, a, i);
+}
+
+template <typename R, int TI>
+__device__ __forceinline__ void rad_fwd_atom(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i) {
+    const int64_t N = a.n;
+    const v4<R> pi = a.pos[i], si = a.spin[i];
+    const int4 c = a.cnt[i];
+    const int na0 = c.x, na = c.y, nr0 = c.z, nr = c.w;
+    // radial and pairwise-magnetic sums over the in-cutoff pairs
     R qr[NCH], qx[4][NCH];
 #pragma unroll
     for (int n = 0; n < NCH; ++n) { qr[n] = R(0); qx[0][n] = qx[1][n] = qx[2][n] = qx[3][n] = R(0); }
@@ -219,7 +237,9 @@ __global__ void __launch_bounds__(128) k_rad_fwd(const __grid_constant__ NepDev<
 }
 
 // ------------------------------------------------------------------ k_ang_fwd
-// stage of one angular pair: g_n (5), s g_n (5), p_lm (24), pad (2)
+// stage of one angular pair: g_n (5), s g_n (5), pad (2), then the 24 harmonics in
+// lane-major order (position 12 + 6 ql + m holds p_lm of lm = ql + 4 m), so each quad
+// lane reads its six harmonics with three 2-wide loads
 constexpr int FSTAGE = 36;
 constexpr int FQUAD = 4 * FSTAGE + 4;   // per quad, padded so quads start in different banks
 
@@ -234,17 +254,28 @@ __device__ __forceinline__ void ang_stage_fwd(const NepDev<R> &P, const Eval2Arg
     carrier_f(r, P.inv_rc_a, f);
     contract_k<R, TI, TJ, G_A>(P, f, g);
     const R s = si.x * sj.x + si.y * sj.y + si.z * sj.z;
+    v4<R> w0, w1;
+    v2<R> w2;
+    w0.x = g[0]; w0.y = g[1]; w0.z = g[2]; w0.w = g[3];
+    w1.x = g[4]; w1.y = g[0] * s; w1.z = g[1] * s; w1.w = g[2] * s;
+    w2.x = g[3] * s; w2.y = g[4] * s;
+    reinterpret_cast<v4<R> *>(st)[0] = w0;
+    reinterpret_cast<v4<R> *>(st)[1] = w1;
+    reinterpret_cast<v2<R> *>(st)[4] = w2;
+    R p[NLM];
+    harm_p(dx * ir, dy * ir, dz * ir, p);
 #pragma unroll
-    for (int n = 0; n < NCH; ++n) {
-        st[n] = g[n];
-        st[NCH + n] = g[n] * s;
+    for (int q = 0; q < 4; ++q) {
+        v2<R> a0, a1, a2;
+        a0.x = p[q]; a0.y = p[q + 4]; a1.x = p[q + 8]; a1.y = p[q + 12]; a2.x = p[q + 16]; a2.y = p[q + 20];
+        v2<R> *d = reinterpret_cast<v2<R> *>(st + 12 + 6 * q);
+        d[0] = a0; d[1] = a1; d[2] = a2;
     }
-    harm_p(dx * ir, dy * ir, dz * ir, st + 2 * NCH);
 }
 
 template <typename R>
 __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(32) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int quad = lane >> 2, ql = lane & 3;
     const int64_t i = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 8 + quad;
@@ -296,12 +327,17 @@ __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<
         const int cnt = min(4, na - base);
         for (int q = 0; q < cnt; ++q) {
             const R *sp = stage + q * FSTAGE;
-            R g[NCH], gs[NCH];
-#pragma unroll
-            for (int n = 0; n < NCH; ++n) { g[n] = sp[n]; gs[n] = sp[NCH + n]; }
+            const v4<R> w0 = reinterpret_cast<const v4<R> *>(sp)[0];
+            const v4<R> w1 = reinterpret_cast<const v4<R> *>(sp)[1];
+            const v2<R> w2 = reinterpret_cast<const v2<R> *>(sp)[4];
+            const R g[NCH] = {w0.x, w0.y, w0.z, w0.w, w1.x};
+            const R gs[NCH] = {w1.y, w1.z, w1.w, w2.x, w2.y};
+            const v2<R> *pp = reinterpret_cast<const v2<R> *>(sp + 12 + 6 * ql);
+            const v2<R> p01 = pp[0], p23 = pp[1], p45 = pp[2];
+            const R pv[6] = {p01.x, p01.y, p23.x, p23.y, p45.x, p45.y};
 #pragma unroll
             for (int m = 0; m < 6; ++m) {
-                const R pl = sp[2 * NCH + ql + 4 * m];
+                const R pl = pv[m];
 #pragma unroll
                 for (int n = 0; n < NCH; ++n) {
                     B[m][n] += g[n] * pl;
@@ -363,19 +399,17 @@ __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<
 }
 
 // ------------------------------------------------------------------ k_ang_bwd
-// stage of one angular pair: g (5), g' (5), s, 1/r, u (3), S_j (3), pad (2) = 20; then 24 x (p, grad p)
+// stage of one angular pair: g (5), g' (5), s, 1/r, u (3), S_j (3), pad (2) = 20; then the
+// 24 (p, grad p) records in lane-major order (record 6 ql + m is harmonic lm = ql + 4 m)
 constexpr int BSCAL = 20;
 constexpr int BSTAGE = BSCAL + 4 * NLM;   // 116
 constexpr int BQUAD = 4 * BSTAGE + 4;      // 468
 
 template <typename R, int LM>
 __device__ __forceinline__ void stage_harm(R x, R y, R z, R *dst) {
-    R p, gx, gy, gz;
-    harm_one<R, LM>(x, y, z, p, gx, gy, gz);
-    dst[4 * LM] = p;
-    dst[4 * LM + 1] = gx;
-    dst[4 * LM + 2] = gy;
-    dst[4 * LM + 3] = gz;
+    v4<R> h;
+    harm_one<R, LM>(x, y, z, h.x, h.y, h.z, h.w);
+    reinterpret_cast<v4<R> *>(dst)[6 * (LM % 4) + LM / 4] = h;
     if constexpr (LM + 1 < NLM) stage_harm<R, LM + 1>(x, y, z, dst);
 }
 
@@ -390,22 +424,21 @@ __device__ __forceinline__ void ang_stage_bwd(const NepDev<R> &P, const Eval2Arg
     carrier_fd(r, P.inv_rc_a, f, df);
     contract_k<R, TI, TJ, G_A>(P, f, g);
     contract_k<R, TI, TJ, G_A>(P, df, dg);
-#pragma unroll
-    for (int n = 0; n < NCH; ++n) {
-        st[n] = g[n];
-        st[NCH + n] = dg[n];
-    }
     const R ux = dx * ir, uy = dy * ir, uz = dz * ir;
-    st[10] = si.x * sj.x + si.y * sj.y + si.z * sj.z;
-    st[11] = ir;
-    st[12] = ux; st[13] = uy; st[14] = uz;
-    st[15] = sj.x; st[16] = sj.y; st[17] = sj.z;
+    v4<R> w[5];
+    w[0].x = g[0]; w[0].y = g[1]; w[0].z = g[2]; w[0].w = g[3];
+    w[1].x = g[4]; w[1].y = dg[0]; w[1].z = dg[1]; w[1].w = dg[2];
+    w[2].x = dg[3]; w[2].y = dg[4]; w[2].z = si.x * sj.x + si.y * sj.y + si.z * sj.z; w[2].w = ir;
+    w[3].x = ux; w[3].y = uy; w[3].z = uz; w[3].w = sj.x;
+    w[4].x = sj.y; w[4].y = sj.z; w[4].z = R(0); w[4].w = R(0);
+#pragma unroll
+    for (int t = 0; t < 5; ++t) reinterpret_cast<v4<R> *>(st)[t] = w[t];
     stage_harm<R, 0>(ux, uy, uz, st + BSCAL);
 }
 
 template <typename R>
 __global__ void __launch_bounds__(128) k_ang_bwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(32) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int quad = lane >> 2, ql = lane & 3;
     const int64_t i = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 8 + quad;
@@ -476,17 +509,22 @@ __global__ void __launch_bounds__(128) k_ang_bwd(const __grid_constant__ NepDev<
         for (int q = 0; q < cmax; ++q) {
             const bool act = q < cnt;
             const R *sp = stage + q * BSTAGE;
+            const v4<R> *sv = reinterpret_cast<const v4<R> *>(sp);
             R accu = R(0), avx = R(0), avy = R(0), avz = R(0), cj = R(0), s = R(0), ir = R(0);
+            v4<R> w3, w4;
             if (act) {
-                R g[NCH], dg[NCH];
-#pragma unroll
-                for (int n = 0; n < NCH; ++n) { g[n] = sp[n]; dg[n] = sp[NCH + n]; }
-                s = sp[10];
-                ir = sp[11];
+                const v4<R> w0 = sv[0], w1 = sv[1], w2 = sv[2];
+                w3 = sv[3];
+                w4 = sv[4];
+                const R g[NCH] = {w0.x, w0.y, w0.z, w0.w, w1.x};
+                const R dg[NCH] = {w1.y, w1.z, w1.w, w2.x, w2.y};
+                s = w2.z;
+                ir = w2.w;
+                const v4<R> *hv = sv + BSCAL / 4 + 6 * ql;
 #pragma unroll
                 for (int m = 0; m < 6; ++m) {
-                    const R *h = sp + BSCAL + 4 * lm_of(ql, m);
-                    const R pl = h[0], gx = h[1], gy = h[2], gz = h[3];
+                    const v4<R> h = hv[m];
+                    const R pl = h.x, gx = h.y, gy = h.z, gz = h.w;
                     R aA = R(0), aS = R(0), bA = R(0), bS = R(0);
 #pragma unroll
                     for (int n = 0; n < NCH; ++n) {
@@ -512,7 +550,7 @@ __global__ void __launch_bounds__(128) k_ang_bwd(const __grid_constant__ NepDev<
                 cj += __shfl_xor_sync(0xffffffffu, cj, o);
             }
             if (act) {
-                const R ux = sp[12], uy = sp[13], uz = sp[14];
+                const R ux = w3.x, uy = w3.y, uz = w3.z;
                 if (ql == q) {
                     v4<R> o4;
                     o4.x = accu * ux + ir * avx;
@@ -521,9 +559,9 @@ __global__ void __launch_bounds__(128) k_ang_bwd(const __grid_constant__ NepDev<
                     o4.w = cj;
                     a.apair[(int64_t)(base + q) * N + i] = o4;
                 }
-                hx += cj * sp[15];
-                hy += cj * sp[16];
-                hz += cj * sp[17];
+                hx += cj * w3.w;
+                hy += cj * w4.x;
+                hz += cj * w4.y;
             }
         }
         __syncwarp();
@@ -744,6 +782,7 @@ static void eval2_impl(Sys &s, const NepDev<R> &P, bool want_virial, cudaEvent_t
     const int qb = quad_block<R>();
     const unsigned nq = (unsigned)((s.n + qb / 4 - 1) / (qb / 4));
     if (ev) cudaEventRecord(ev[0], s.stream);
+    k_compact<R><<<nb, 128, 0, s.stream>>>(P, a);
     k_rad_fwd<R><<<nb, 128, 0, s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[1], s.stream);
     k_ang_fwd<R><<<nq, qb, fwd_smem<R>(), s.stream>>>(P, a);

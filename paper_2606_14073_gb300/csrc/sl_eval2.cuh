@@ -5,6 +5,11 @@
 
 namespace sl {
 
+template <typename R> struct V2s;
+template <> struct V2s<float> { using t = float2; };
+template <> struct V2s<double> { using t = double2; };
+template <typename R> using v2 = typename V2s<R>::t;
+
 // Record of one ordered pair (i -> j) for neighbour j: (dE_i/dr_ij, dE_i/dS_j), 32 bytes
 // in FP32 (one DRAM sector), stored in j's own list slot of i.
 template <typename R>

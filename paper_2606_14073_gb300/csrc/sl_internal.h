@@ -109,8 +109,8 @@ void launch_rebuild(Sys &s, bool conditional);
 void launch_eval(Sys &s, bool want_virial, cudaEvent_t *ev = nullptr);
 void eval2_init();
 void launch_network(Sys &s, cudaEvent_t *ev);   // sl_nep.cu
-// first half, rebuild group (7), descriptor (2), network, backward (2), second half
-constexpr int KERNELS_PER_STEP = 1 + 7 + 2 + 1 + 2 + 1;
+// first half, rebuild group (7), compaction + descriptor (3), network, backward (2), second half
+constexpr int KERNELS_PER_STEP = 1 + 7 + 3 + 1 + 2 + 1;
 // sl_integrate.cu
 void launch_first_half(Sys &s);
 void launch_second_half(Sys &s);

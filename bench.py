@@ -299,15 +299,14 @@ def run_ours(args):
     total = sum(prof.values())
     n_r, n_a = neighbour_counts(wl)
     fl = flops.per_atom(n_r, n_a)
-    dom = max(("rad_fwd", "ang_fwd", "network", "ang_bwd", "rad_bwd"), key=lambda k: prof[k])
+    dom = max(("rad_fwd", "ang_fwd", "network", "backward"), key=lambda k: prof[k])
     launch_ms = prof[dom] / args.profile_steps
     achieved = fl[dom] * wl.n / (launch_ms * 1e-3) / 1e12
     peak_derived = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
     fma32, _ = S.sl_measure_fma_peak(S.SL_PREC_MIXED)
     fma64, _ = S.sl_measure_fma_peak(S.SL_PREC_FP64)
     roofline = {"bound": "alu", "kernel": {"rad_fwd": "k_rad_fwd<float>", "ang_fwd": "k_ang_fwd<float>",
-                                           "network": "k_mlp<float>", "ang_bwd": "k_ang_bwd<float>",
-                                           "rad_bwd": "k_rad_bwd<float>"}[dom],
+                                           "network": "k_mlp<float>", "backward": "k_bwd<float>"}[dom],
                 "achieved": achieved, "peak": peak_derived, "unit": "TFLOP/s", "frac": achieved / peak_derived,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FP32 FMA pipe)",
                 "peak_measured_fp32_fma_tflops": fma32 / 1e12, "peak_measured_fp64_fma_tflops": fma64 / 1e12,
@@ -342,7 +341,7 @@ def run_ours(args):
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "kernel_share": shares, "kernel_ms_per_step": {k: v / args.profile_steps for k, v in prof.items()},
                 "kernel_alu_frac": {k: fl[k] * wl.n / (prof[k] / args.profile_steps * 1e-3) / 1e12 / peak_derived
-                                    for k in ("rad_fwd", "ang_fwd", "network", "ang_bwd", "rad_bwd")},
+                                    for k in ("rad_fwd", "ang_fwd", "network", "backward")},
                 "fp64": fp64, "mixed_error_vs_fp64": err, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist is not None:

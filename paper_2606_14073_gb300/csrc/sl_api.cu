@@ -101,7 +101,7 @@ void fill_params(sl::NepDev<R> &P, const sl_nep_params *p) {
 void free_sys(sl::Sys &s) {
     void *ptrs[] = {s.pos, s.vel, s.spin, s.spin_prev, s.F, s.H, s.posref, s.posf, s.spinf, s.species, s.orig,
                     s.inv, s.nbr, s.rev, s.seg, s.cells.count, s.cells.start, s.cells.fill, s.cells.atoms,
-                    s.cells.of, s.q, s.bsum, s.fp, s.ei, s.pairs, s.clj, s.cls, s.cnt, s.apair, s.gii_ang, s.fown, s.gii,
+                    s.cells.of, s.q, s.bsum, s.fp, s.ei, s.pairs, s.clj, s.cls, s.cnt, s.fown, s.gii,
                     s.wpart, s.Fo, s.Ho,
                     s.status, s.rebuild, s.d_step, s.d_par, s.red, s.snap, s.d_builds};
     for (void *p : ptrs)
@@ -402,8 +402,7 @@ int sl_create_system(const double *positions, const double *spins, const double 
         (rc = dalloc((char **)&s.bsum, R * NB * N)) || (rc = dalloc((char **)&s.fp, R * DIM * N)) ||
         (rc = dalloc((char **)&s.ei, R * N)) || (rc = dalloc((char **)&s.pairs, R * 8 * N * s.cap)) ||
         (rc = dalloc(&s.clj, N * (size_t)(s.cap + s.cap_ang))) || (rc = dalloc(&s.cls, N * (size_t)(s.cap + s.cap_ang))) ||
-        (rc = dalloc(&s.cnt, N)) || (rc = dalloc((char **)&s.apair, R * 4 * N * s.cap_ang)) ||
-        (rc = dalloc((char **)&s.gii_ang, R * 4 * N)) || (rc = dalloc((char **)&s.fown, R * 4 * N)) ||
+        (rc = dalloc(&s.cnt, N)) || (rc = dalloc((char **)&s.fown, R * 4 * N)) ||
         (rc = dalloc((char **)&s.gii, R * 4 * N)) || (rc = dalloc((char **)&s.wpart, R * 9 * N)) ||
         (rc = dalloc(&s.Fo, N)) || (rc = dalloc(&s.Ho, N)) || (rc = dalloc(&s.status, 1)) ||
         (rc = dalloc(&s.rebuild, 1)) || (rc = dalloc(&s.d_step, 2)) || (rc = dalloc(&s.d_par, 1)) ||

@@ -12,14 +12,13 @@
 //   k_ang_fwd  four lanes per atom.  Each lane stages one angular pair (carrier, g_n,
 //              spin weight, the 24 solid harmonics) in shared memory; then every lane
 //              accumulates B_nlm, BS_nlm for its 6 harmonics over the staged pairs.
-//   k_ang_bwd  four lanes per atom.  The adjoints dE/dB (2 kappa Fp B) stay in
-//              registers, 60 per lane; staged per pair: g_n, g_n', the harmonics and
-//              their gradients.  Lanes contract their harmonics and reduce within the
-//              quad to the pair's angular dE_i/dr_ij and spin weight c_ij.
-//   k_rad_bwd  one thread per atom.  Radial and pairwise-magnetic derivatives per
-//              pair, plus the angular part from k_ang_bwd; writes the pair record
-//              (dE_i/dr_ij, dE_i/dS_j) straight into the slot the neighbour j will
-//              read (its own list slot of i), and the per-atom sums.
+//   k_bwd      four lanes per atom, lanes over pairs.  The angular adjoints
+//              dE/dB_nlm = 2 kappa_lm Fp B_nlm and the precontracted radial
+//              coefficients of the atom sit in shared memory; each lane takes whole
+//              pairs (angular rows first, then radial-only rows) and writes the pair
+//              record (dE_i/dr_ij, dE_i/dS_j) straight into the slot the neighbour j
+//              will read (its own list slot of i); the per-atom sums (dE_i/dr_i side,
+//              dE_i/dS_i, virial) are reduced over the quad.
 // The force/field gather (sl_integrate.cu) then reads, for atom k, the records of
 // its in-cutoff slots only.
 #include "sl_internal.h"
@@ -398,341 +397,265 @@ __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<
     }
 }
 
-// ------------------------------------------------------------------ k_ang_bwd
-// stage of one angular pair: g (5), g' (5), s, 1/r, u (3), S_j (3), pad (2) = 20; then the
-// 24 (p, grad p) records in lane-major order (record 6 ql + m is harmonic lm = ql + 4 m)
-constexpr int BSCAL = 20;
-constexpr int BSTAGE = BSCAL + 4 * NLM;   // 116
-constexpr int BQUAD = 4 * BSTAGE + 4;      // 468
+// ------------------------------------------------------------------ k_bwd (fused)
+// Quad per atom, lanes over pairs.  Shared memory per atom: the angular adjoints
+// dE/dB_nlm, dE/dBS_nlm as 24 records of 12 (5 + 5 + pad), then the precontracted
+// radial coefficients C^G_k = sum_n Fp^G_n c^G_{n k t_i t_j} for both neighbour
+// species (2 x 48).  Stride 388: 388 mod 32 = 4, so the eight atoms of a warp read
+// disjoint bank groups.
+constexpr int BW_C = 292;
+constexpr int BW_ATOM = 388;
 
-template <typename R, int LM>
-__device__ __forceinline__ void stage_harm(R x, R y, R z, R *dst) {
-    v4<R> h;
-    harm_one<R, LM>(x, y, z, h.x, h.y, h.z, h.w);
-    reinterpret_cast<v4<R> *>(dst)[6 * (LM % 4) + LM / 4] = h;
-    if constexpr (LM + 1 < NLM) stage_harm<R, LM + 1>(x, y, z, dst);
+template <typename R>
+struct BwdAcc2 {
+    R fx, fy, fz, hx, hy, hz;
+    R w[9];
+};
+
+template <typename R, int TI>
+__device__ __forceinline__ void bwd_coeffs(const NepDev<R> &P, const R FR[NCH], const R FX[4][NCH], int ql, R *smc) {
+#pragma unroll
+    for (int tj = 0; tj < 2; ++tj)
+#pragma unroll
+        for (int g = 0; g < 5; ++g)
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                constexpr int G[5] = {G_R, G_EX, G_DMI, G_ANI, G_SIA};
+                R v = R(0);
+#pragma unroll
+                for (int n = 0; n < NCH; ++n)
+                    v += (g == 0 ? FR[n] : FX[g - 1][n]) * (tj == 0 ? P.c[TI][0][G[g]][n][k] : P.c[TI][1][G[g]][n][k]);
+                if (((tj * 45 + g * 9 + k) & 3) == ql) smc[tj * 48 + g * 9 + k] = v;
+            }
 }
 
 template <typename R, int TI, int TJ>
-__device__ __forceinline__ void ang_stage_bwd(const NepDev<R> &P, const Eval2Args<R> &a, const v4<R> &pi,
-                                              const v4<R> &si, const v4<R> &pj, const v4<R> &sj, R *st) {
+__device__ __forceinline__ void ang_gdg(const NepDev<R> &P, R r, R inv_rc, R g[NCH], R dg[NCH]) {
+    R f[NK], df[NK];
+    carrier_fd(r, inv_rc, f, df);
+    contract_k<R, TI, TJ, G_A>(P, f, g);
+    contract_k<R, TI, TJ, G_A>(P, df, dg);
+}
+
+template <typename R, int LM>
+__device__ __forceinline__ void bwd_harm(const R *__restrict__ bb, R ux, R uy, R uz, R ir, R s, const R g[NCH],
+                                         const R dg[NCH], R &accu, R &avx, R &avy, R &avz, R &cj) {
+    R p, gx, gy, gz;
+    harm_one<R, LM>(ux, uy, uz, p, gx, gy, gz);
+    const v4<R> *rec = reinterpret_cast<const v4<R> *>(bb + 12 * LM);
+    const v4<R> r0 = rec[0], r1 = rec[1], r2 = rec[2];
+    const R B0[NCH] = {r0.x, r0.y, r0.z, r0.w, r1.x};
+    const R B1[NCH] = {r1.y, r1.z, r1.w, r2.x, r2.y};
+    R aA = R(0), aS = R(0), bA = R(0), bS = R(0);
+#pragma unroll
+    for (int n = 0; n < NCH; ++n) {
+        aA += B0[n] * g[n];
+        aS += B1[n] * g[n];
+        bA += B0[n] * dg[n];
+        bS += B1[n] * dg[n];
+    }
+    const R av = aA + s * aS, bv = bA + s * bS;
+    accu += p * (bv - R(harm_l(LM)) * ir * av);
+    avx += av * gx;
+    avy += av * gy;
+    avz += av * gz;
+    cj += aS * p;
+    if constexpr (LM + 1 < NLM) bwd_harm<R, LM + 1>(bb, ux, uy, uz, ir, s, g, dg, accu, avx, avy, avz, cj);
+}
+
+template <typename R, bool ANG>
+__device__ __forceinline__ void bwd_pair(const NepDev<R> &P, const Eval2Args<R> &a, int ti, int tj, const v4<R> &pi,
+                                         const v4<R> &si, const v4<R> &pj, const v4<R> &sj, int j, int t,
+                                         const R *sm, BwdAcc2<R> &acc) {
     R dx, dy, dz;
     sep(a.box, pi, pj, dx, dy, dz);
     const R d2 = dx * dx + dy * dy + dz * dz;
     const R ir = rsqrt_(d2), r = d2 * ir;
-    R f[NK], df[NK], g[NCH], dg[NCH];
-    carrier_fd(r, P.inv_rc_a, f, df);
-    contract_k<R, TI, TJ, G_A>(P, f, g);
-    contract_k<R, TI, TJ, G_A>(P, df, dg);
     const R ux = dx * ir, uy = dy * ir, uz = dz * ir;
-    v4<R> w[5];
-    w[0].x = g[0]; w[0].y = g[1]; w[0].z = g[2]; w[0].w = g[3];
-    w[1].x = g[4]; w[1].y = dg[0]; w[1].z = dg[1]; w[1].w = dg[2];
-    w[2].x = dg[3]; w[2].y = dg[4]; w[2].z = si.x * sj.x + si.y * sj.y + si.z * sj.z; w[2].w = ir;
-    w[3].x = ux; w[3].y = uy; w[3].z = uz; w[3].w = sj.x;
-    w[4].x = sj.y; w[4].y = sj.z; w[4].z = R(0); w[4].w = R(0);
+    // radial and pairwise-magnetic part with the precontracted coefficients
+    R f[NK], df[NK];
+    carrier_fd(r, P.inv_rc_r, f, df);
+    const v4<R> *cv = reinterpret_cast<const v4<R> *>(sm + BW_C + tj * 48);
+    R C[48];
 #pragma unroll
-    for (int t = 0; t < 5; ++t) reinterpret_cast<v4<R> *>(st)[t] = w[t];
-    stage_harm<R, 0>(ux, uy, uz, st + BSCAL);
+    for (int q = 0; q < 12; ++q) {
+        const v4<R> c4 = cv[q];
+        C[4 * q] = c4.x; C[4 * q + 1] = c4.y; C[4 * q + 2] = c4.z; C[4 * q + 3] = c4.w;
+    }
+    R h1 = 0, h2 = 0, h3 = 0, h4 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0, e4 = 0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        e0 += C[k] * df[k];
+        h1 += C[9 + k] * f[k]; e1 += C[9 + k] * df[k];
+        h2 += C[18 + k] * f[k]; e2 += C[18 + k] * df[k];
+        h3 += C[27 + k] * f[k]; e3 += C[27 + k] * df[k];
+        h4 += C[36 + k] * f[k]; e4 += C[36 + k] * df[k];
+    }
+    const R sij = si.x * sj.x + si.y * sj.y + si.z * sj.z;
+    const R siu = si.x * ux + si.y * uy + si.z * uz;
+    const R sju = sj.x * ux + sj.y * uy + sj.z * uz;
+    const R wx = si.y * sj.z - si.z * sj.y, wy = si.z * sj.x - si.x * sj.z, wz = si.x * sj.y - si.y * sj.x;
+    const R wu = wx * ux + wy * uy + wz * uz;
+    const R rad = e0 + e1 * sij + e2 * wu + e3 * siu * sju + e4 * siu * siu;
+    const R cSi = (h3 * sju + R(2) * h4 * siu) * ir;
+    const R cSj = h3 * siu * ir;
+    const R cW = h2 * ir;
+    const R along = rad - cSi * siu - cSj * sju - cW * wu;
+    R Dx = along * ux + cSi * si.x + cSj * sj.x + cW * wx;
+    R Dy = along * uy + cSi * si.y + cSj * sj.y + cW * wy;
+    R Dz = along * uz + cSi * si.z + cSj * sj.z + cW * wz;
+    R cg = h1;   // coefficient of S_i in dE_i/dS_j (exchange, plus the spin-angular weight below)
+    const R cu = h3 * sju + R(2) * h4 * siu;
+    acc.hx += h1 * sj.x + h2 * (sj.y * uz - sj.z * uy) + cu * ux;
+    acc.hy += h1 * sj.y + h2 * (sj.z * ux - sj.x * uz) + cu * uy;
+    acc.hz += h1 * sj.z + h2 * (sj.x * uy - sj.y * ux) + cu * uz;
+    if constexpr (ANG) {
+        R g[NCH], dg[NCH];
+        if (ti == 0) {
+            if (tj == 0) ang_gdg<R, 0, 0>(P, r, P.inv_rc_a, g, dg);
+            else ang_gdg<R, 0, 1>(P, r, P.inv_rc_a, g, dg);
+        } else {
+            if (tj == 0) ang_gdg<R, 1, 0>(P, r, P.inv_rc_a, g, dg);
+            else ang_gdg<R, 1, 1>(P, r, P.inv_rc_a, g, dg);
+        }
+        R accu = R(0), avx = R(0), avy = R(0), avz = R(0), cj = R(0);
+        bwd_harm<R, 0>(sm, ux, uy, uz, ir, sij, g, dg, accu, avx, avy, avz, cj);
+        Dx += accu * ux + ir * avx;
+        Dy += accu * uy + ir * avy;
+        Dz += accu * uz + ir * avz;
+        cg += cj;
+        acc.hx += cj * sj.x;
+        acc.hy += cj * sj.y;
+        acc.hz += cj * sj.z;
+    }
+    // dE_i/dS_j = (h_EX + c_ij) S_i + h_DMI (u x S_i) + h_ANI (S_i.u) u
+    const R Gx = cg * si.x + h2 * (uy * si.z - uz * si.y) + h3 * siu * ux;
+    const R Gy = cg * si.y + h2 * (uz * si.x - ux * si.z) + h3 * siu * uy;
+    const R Gz = cg * si.z + h2 * (ux * si.y - uy * si.x) + h3 * siu * uz;
+    acc.fx += Dx; acc.fy += Dy; acc.fz += Dz;
+    if (a.want_virial) {
+        acc.w[0] -= dx * Dx; acc.w[1] -= dx * Dy; acc.w[2] -= dx * Dz;
+        acc.w[3] -= dy * Dx; acc.w[4] -= dy * Dy; acc.w[5] -= dy * Dz;
+        acc.w[6] -= dz * Dx; acc.w[7] -= dz * Dy; acc.w[8] -= dz * Dz;
+    }
+    PairRec<R> rec;
+    rec.a.x = Dx; rec.a.y = Dy; rec.a.z = Dz; rec.a.w = Gx;
+    rec.b.x = Gy; rec.b.y = Gz; rec.b.z = R(0); rec.b.w = R(0);
+    a.pd[(int64_t)t * a.n + j] = rec;
+}
+
+// rows lo, lo+4, ... of one range for lane ql, with the next row's loads in flight
+template <typename R, bool ANG>
+__device__ __forceinline__ void bwd_rows(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, int ti, int lo, int hi,
+                                         int split, const v4<R> &pi, const v4<R> &si, const R *sm,
+                                         BwdAcc2<R> &acc) {
+    const int64_t N = a.n;
+    int jn = 0, tn = 0;
+    v4<R> pn, sn;
+    if (lo < hi) {
+        jn = a.clj[(int64_t)lo * N + i];
+        tn = a.cls[(int64_t)lo * N + i] >> 8;
+        pn = a.pos[jn];
+        sn = a.spin[jn];
+    }
+    for (int row = lo; row < hi; row += 4) {
+        const int j = jn, t = tn;
+        const v4<R> pj = pn, sj = sn;
+        if (row + 4 < hi) {
+            jn = a.clj[(int64_t)(row + 4) * N + i];
+            tn = a.cls[(int64_t)(row + 4) * N + i] >> 8;
+            pn = a.pos[jn];
+            sn = a.spin[jn];
+        }
+        bwd_pair<R, ANG>(P, a, ti, row < split ? 0 : 1, pi, si, pj, sj, j, t, sm, acc);
+    }
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128) k_ang_bwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+__global__ void __launch_bounds__(128) k_bwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int quad = lane >> 2, ql = lane & 3;
     const int64_t i = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 8 + quad;
     const bool valid = i < a.n;
-    R *stage = reinterpret_cast<R *>(smem_raw) + (warp * 8 + quad) * BQUAD;
     const int64_t N = a.n;
-    v4<R> pi, si;
-    int na0 = 0, na = 0, ti = 0;
-    R Bb[6][NCH], BSb[6][NCH], lv[6];
-    if (valid) {
-        pi = a.pos[i];
-        si = a.spin[i];
-        const int4 c = a.cnt[i];
-        na0 = c.x;
-        na = c.y;
-        ti = i < a.n_fe ? 0 : 1;
-    }
-#pragma unroll
-    for (int m = 0; m < 6; ++m) {
-        const int lm = lm_of(ql, m);
-        const int l = l_of_lm(lm);
-        lv[m] = R(l);
-        const R k2 = R(2) * kappa_of_lm<R>(lm);
-#pragma unroll
-        for (int n = 0; n < NCH; ++n) {
-            if (valid) {
-                const R fa = a.fp[(int64_t)(Q_A + n * 4 + l - 1) * N + i];
-                const R fs = a.fp[(int64_t)(Q_SA + n * 4 + l - 1) * N + i];
-                Bb[m][n] = k2 * fa * a.bsum[(int64_t)(n * NLM + lm) * N + i];
-                BSb[m][n] = k2 * fs * a.bsum[(int64_t)(NCH * NLM + n * NLM + lm) * N + i];
-            } else {
-                Bb[m][n] = R(0);
-                BSb[m][n] = R(0);
-            }
-        }
-    }
-    R hx = R(0), hy = R(0), hz = R(0);
-    const int nmax = __reduce_max_sync(0xffffffffu, na);
-    // the lane's pair of the next round is loaded one round ahead
-    v4<R> pjn, sjn;
-    if (ql < na) {
-        const int j = a.clj[(int64_t)ql * N + i];
-        pjn = a.pos[j];
-        sjn = a.spin[j];
-    }
-    for (int base = 0; base < nmax; base += 4) {
-        const int p = base + ql;
-        const v4<R> pj = pjn, sj = sjn;
-        if (p + 4 < na) {
-            const int j = a.clj[(int64_t)(p + 4) * N + i];
-            pjn = a.pos[j];
-            sjn = a.spin[j];
-        }
-        if (p < na) {
-            R *st = stage + ql * BSTAGE;
-            if (ti == 0) {
-                if (p < na0) ang_stage_bwd<R, 0, 0>(P, a, pi, si, pj, sj, st);
-                else ang_stage_bwd<R, 0, 1>(P, a, pi, si, pj, sj, st);
-            } else {
-                if (p < na0) ang_stage_bwd<R, 1, 0>(P, a, pi, si, pj, sj, st);
-                else ang_stage_bwd<R, 1, 1>(P, a, pi, si, pj, sj, st);
-            }
-        }
-        __syncwarp();
-        const int cnt = min(4, na - base);
-        // every lane of the warp runs the same number of reduction steps
-        const int cmax = __reduce_max_sync(0xffffffffu, max(cnt, 0));
-        for (int q = 0; q < cmax; ++q) {
-            const bool act = q < cnt;
-            const R *sp = stage + q * BSTAGE;
-            const v4<R> *sv = reinterpret_cast<const v4<R> *>(sp);
-            R accu = R(0), avx = R(0), avy = R(0), avz = R(0), cj = R(0), s = R(0), ir = R(0);
-            v4<R> w3, w4;
-            if (act) {
-                const v4<R> w0 = sv[0], w1 = sv[1], w2 = sv[2];
-                w3 = sv[3];
-                w4 = sv[4];
-                const R g[NCH] = {w0.x, w0.y, w0.z, w0.w, w1.x};
-                const R dg[NCH] = {w1.y, w1.z, w1.w, w2.x, w2.y};
-                s = w2.z;
-                ir = w2.w;
-                const v4<R> *hv = sv + BSCAL / 4 + 6 * ql;
-#pragma unroll
-                for (int m = 0; m < 6; ++m) {
-                    const v4<R> h = hv[m];
-                    const R pl = h.x, gx = h.y, gy = h.z, gz = h.w;
-                    R aA = R(0), aS = R(0), bA = R(0), bS = R(0);
-#pragma unroll
-                    for (int n = 0; n < NCH; ++n) {
-                        aA += Bb[m][n] * g[n];
-                        aS += BSb[m][n] * g[n];
-                        bA += Bb[m][n] * dg[n];
-                        bS += BSb[m][n] * dg[n];
-                    }
-                    const R av = aA + s * aS, bv = bA + s * bS;
-                    accu += pl * (bv - lv[m] * ir * av);
-                    avx += av * gx;
-                    avy += av * gy;
-                    avz += av * gz;
-                    cj += aS * pl;
-                }
-            }
-#pragma unroll
-            for (int o = 1; o <= 2; o <<= 1) {
-                accu += __shfl_xor_sync(0xffffffffu, accu, o);
-                avx += __shfl_xor_sync(0xffffffffu, avx, o);
-                avy += __shfl_xor_sync(0xffffffffu, avy, o);
-                avz += __shfl_xor_sync(0xffffffffu, avz, o);
-                cj += __shfl_xor_sync(0xffffffffu, cj, o);
-            }
-            if (act) {
-                const R ux = w3.x, uy = w3.y, uz = w3.z;
-                if (ql == q) {
-                    v4<R> o4;
-                    o4.x = accu * ux + ir * avx;
-                    o4.y = accu * uy + ir * avy;
-                    o4.z = accu * uz + ir * avz;
-                    o4.w = cj;
-                    a.apair[(int64_t)(base + q) * N + i] = o4;
-                }
-                hx += cj * w3.w;
-                hy += cj * w4.x;
-                hz += cj * w4.y;
-            }
-        }
-        __syncwarp();
-    }
-    if (valid && ql == 0) {
-        v4<R> h4;
-        h4.x = hx; h4.y = hy; h4.z = hz; h4.w = R(0);
-        a.gii_ang[i] = h4;
-    }
-}
-
-// ------------------------------------------------------------------ k_rad_bwd
-template <typename R>
-struct RadAcc {
-    R fx, fy, fz, hx, hy, hz;
-    R w[9];
-};
-
-template <typename R, int TI, int TJ, bool ANG>
-__device__ __forceinline__ void rad_bwd_rows(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, const v4<R> &pi,
-                                             const v4<R> &si, const R C0[NK], const R C1[NK], const R C2[NK],
-                                             const R C3[NK], const R C4[NK], int lo, int hi, RadAcc<R> &acc) {
-    const int64_t N = a.n;
-    const int32_t *__restrict__ clj = a.clj;
-    const uint16_t *__restrict__ cls = a.cls;
-    const v4<R> *__restrict__ pos = a.pos;
-    const v4<R> *__restrict__ spin = a.spin;
-    const v4<R> *__restrict__ apair = a.apair;
-    // one-pair prefetch: the next pair's loads are in flight during this pair's arithmetic
-    int jn = 0, tn = 0;
-    v4<R> pn, sn, an;
-    if (lo < hi) {
-        jn = clj[(int64_t)lo * N + i];
-        tn = cls[(int64_t)lo * N + i] >> 8;
-        pn = pos[jn];
-        sn = spin[jn];
-        if constexpr (ANG) an = apair[(int64_t)lo * N + i];
-    }
-    for (int row = lo; row < hi; ++row) {
-        const int j = jn, t = tn;
-        const v4<R> pj = pn, sj = sn;
-        v4<R> ap;
-        if constexpr (ANG) ap = an;
-        if (row + 1 < hi) {
-            jn = clj[(int64_t)(row + 1) * N + i];
-            tn = cls[(int64_t)(row + 1) * N + i] >> 8;
-            pn = pos[jn];
-            sn = spin[jn];
-            if constexpr (ANG) an = apair[(int64_t)(row + 1) * N + i];
-        }
-        R dx, dy, dz;
-        sep(a.box, pi, pj, dx, dy, dz);
-        const R d2 = dx * dx + dy * dy + dz * dz;
-        const R ir = rsqrt_(d2), r = d2 * ir;
-        const R ux = dx * ir, uy = dy * ir, uz = dz * ir;
-        R f[NK], df[NK];
-        carrier_fd(r, P.inv_rc_r, f, df);
-        R h1 = 0, h2 = 0, h3 = 0, h4 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0, e4 = 0;
-#pragma unroll
-        for (int k = 0; k < NK; ++k) {
-            e0 += C0[k] * df[k];
-            h1 += C1[k] * f[k]; e1 += C1[k] * df[k];
-            h2 += C2[k] * f[k]; e2 += C2[k] * df[k];
-            h3 += C3[k] * f[k]; e3 += C3[k] * df[k];
-            h4 += C4[k] * f[k]; e4 += C4[k] * df[k];
-        }
-        const R sij = si.x * sj.x + si.y * sj.y + si.z * sj.z;
-        const R siu = si.x * ux + si.y * uy + si.z * uz;
-        const R sju = sj.x * ux + sj.y * uy + sj.z * uz;
-        const R wx = si.y * sj.z - si.z * sj.y, wy = si.z * sj.x - si.x * sj.z, wz = si.x * sj.y - si.y * sj.x;
-        const R wu = wx * ux + wy * uy + wz * uz;
-        const R rad = e0 + e1 * sij + e2 * wu + e3 * siu * sju + e4 * siu * siu;
-        const R cSi = (h3 * sju + R(2) * h4 * siu) * ir;
-        const R cSj = h3 * siu * ir;
-        const R cW = h2 * ir;
-        const R along = rad - cSi * siu - cSj * sju - cW * wu;
-        R Dx = along * ux + cSi * si.x + cSj * sj.x + cW * wx;
-        R Dy = along * uy + cSi * si.y + cSj * sj.y + cW * wy;
-        R Dz = along * uz + cSi * si.z + cSj * sj.z + cW * wz;
-        R Gx = h1 * si.x + h2 * (uy * si.z - uz * si.y) + h3 * siu * ux;
-        R Gy = h1 * si.y + h2 * (uz * si.x - ux * si.z) + h3 * siu * uy;
-        R Gz = h1 * si.z + h2 * (ux * si.y - uy * si.x) + h3 * siu * uz;
-        const R cu = h3 * sju + R(2) * h4 * siu;
-        acc.hx += h1 * sj.x + h2 * (sj.y * uz - sj.z * uy) + cu * ux;
-        acc.hy += h1 * sj.y + h2 * (sj.z * ux - sj.x * uz) + cu * uy;
-        acc.hz += h1 * sj.z + h2 * (sj.x * uy - sj.y * ux) + cu * uz;
-        if constexpr (ANG) {
-            Dx += ap.x; Dy += ap.y; Dz += ap.z;
-            Gx += ap.w * si.x; Gy += ap.w * si.y; Gz += ap.w * si.z;
-        }
-        acc.fx += Dx; acc.fy += Dy; acc.fz += Dz;
-        if (a.want_virial) {
-            acc.w[0] -= dx * Dx; acc.w[1] -= dx * Dy; acc.w[2] -= dx * Dz;
-            acc.w[3] -= dy * Dx; acc.w[4] -= dy * Dy; acc.w[5] -= dy * Dz;
-            acc.w[6] -= dz * Dx; acc.w[7] -= dz * Dy; acc.w[8] -= dz * Dz;
-        }
-        // record for neighbour j, in j's own slot t of i
-        PairRec<R> rec;
-        rec.a.x = Dx; rec.a.y = Dy; rec.a.z = Dz; rec.a.w = Gx;
-        rec.b.x = Gy; rec.b.y = Gz; rec.b.z = R(0); rec.b.w = R(0);
-        a.pd[(int64_t)t * N + j] = rec;
-    }
-}
-
-template <typename R, int TI, int TJ>
-__device__ __forceinline__ void rad_bwd_species(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i,
-                                                const v4<R> &pi, const v4<R> &si, const R FR[NCH],
-                                                const R FX[4][NCH], int alo, int ahi, int rlo, int rhi,
-                                                RadAcc<R> &acc) {
-    // C^G_k = sum_n Fp^G_n c^G_{n k t_i t_j}
-    R C0[NK], C1[NK], C2[NK], C3[NK], C4[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) {
-        R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0), s4 = R(0);
-#pragma unroll
-        for (int n = 0; n < NCH; ++n) {
-            s0 += FR[n] * P.c[TI][TJ][G_R][n][k];
-            s1 += FX[0][n] * P.c[TI][TJ][G_EX][n][k];
-            s2 += FX[1][n] * P.c[TI][TJ][G_DMI][n][k];
-            s3 += FX[2][n] * P.c[TI][TJ][G_ANI][n][k];
-            s4 += FX[3][n] * P.c[TI][TJ][G_SIA][n][k];
-        }
-        C0[k] = s0; C1[k] = s1; C2[k] = s2; C3[k] = s3; C4[k] = s4;
-    }
-    rad_bwd_rows<R, TI, TJ, true>(P, a, i, pi, si, C0, C1, C2, C3, C4, alo, ahi, acc);
-    rad_bwd_rows<R, TI, TJ, false>(P, a, i, pi, si, C0, C1, C2, C3, C4, rlo, rhi, acc);
-}
-
-template <typename R, int TI>
-__device__ __forceinline__ void rad_bwd_atom(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i) {
-    const int64_t N = a.n;
-    const v4<R> pi = a.pos[i], si = a.spin[i];
-    const int4 c = a.cnt[i];
-    R FR[NCH], FX[4][NCH];
-#pragma unroll
-    for (int n = 0; n < NCH; ++n) {
-        FR[n] = a.fp[(int64_t)(Q_R + n) * N + i];
-        FX[0][n] = a.fp[(int64_t)(Q_EX + n) * N + i];
-        FX[1][n] = a.fp[(int64_t)(Q_DMI + n) * N + i];
-        FX[2][n] = a.fp[(int64_t)(Q_ANI + n) * N + i];
-        FX[3][n] = a.fp[(int64_t)(Q_SIA + n) * N + i];
-    }
-    const R fo = R(2) * a.fp[(int64_t)Q_O * N + i];
-    const v4<R> ga = a.gii_ang[i];
-    RadAcc<R> acc;
-    acc.fx = acc.fy = acc.fz = R(0);
-    acc.hx = fo * si.x + ga.x;
-    acc.hy = fo * si.y + ga.y;
-    acc.hz = fo * si.z + ga.z;
+    R *sm = reinterpret_cast<R *>(smem_raw) + (warp * 8 + quad) * BW_ATOM;
+    BwdAcc2<R> acc;
+    acc.fx = acc.fy = acc.fz = acc.hx = acc.hy = acc.hz = R(0);
 #pragma unroll
     for (int t = 0; t < 9; ++t) acc.w[t] = R(0);
-    const int ca = a.cap_ang;
-    rad_bwd_species<R, TI, 0>(P, a, i, pi, si, FR, FX, 0, c.x, ca, ca + c.z, acc);
-    rad_bwd_species<R, TI, 1>(P, a, i, pi, si, FR, FX, c.x, c.y, ca + c.z, ca + c.w, acc);
-    v4<R> f4, g4;
-    f4.x = acc.fx; f4.y = acc.fy; f4.z = acc.fz; f4.w = R(0);
-    g4.x = acc.hx; g4.y = acc.hy; g4.z = acc.hz; g4.w = R(0);
-    a.fown[i] = f4;
-    a.gii[i] = g4;
+    if (valid) {
+        const int ti = i < a.n_fe ? 0 : 1;
+        const v4<R> pi = a.pos[i], si = a.spin[i];
+        const int4 c = a.cnt[i];
+        // angular adjoints of this lane's harmonics lm = ql + 4 m into shared memory
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            const int lm = lm_of(ql, m);
+            const int l = l_of_lm(lm);
+            const R k2 = R(2) * kappa_of_lm<R>(lm);
+            R bb[10];
+#pragma unroll
+            for (int n = 0; n < NCH; ++n) {
+                bb[n] = k2 * a.fp[(int64_t)(Q_A + n * 4 + l - 1) * N + i] * a.bsum[(int64_t)(n * NLM + lm) * N + i];
+                bb[NCH + n] = k2 * a.fp[(int64_t)(Q_SA + n * 4 + l - 1) * N + i] *
+                              a.bsum[(int64_t)(NCH * NLM + n * NLM + lm) * N + i];
+            }
+            v4<R> *d = reinterpret_cast<v4<R> *>(sm + 12 * lm);
+            v4<R> w0, w1, w2;
+            w0.x = bb[0]; w0.y = bb[1]; w0.z = bb[2]; w0.w = bb[3];
+            w1.x = bb[4]; w1.y = bb[5]; w1.z = bb[6]; w1.w = bb[7];
+            w2.x = bb[8]; w2.y = bb[9]; w2.z = R(0); w2.w = R(0);
+            d[0] = w0; d[1] = w1; d[2] = w2;
+        }
+        R FR[NCH], FX[4][NCH];
+#pragma unroll
+        for (int n = 0; n < NCH; ++n) {
+            FR[n] = a.fp[(int64_t)(Q_R + n) * N + i];
+            FX[0][n] = a.fp[(int64_t)(Q_EX + n) * N + i];
+            FX[1][n] = a.fp[(int64_t)(Q_DMI + n) * N + i];
+            FX[2][n] = a.fp[(int64_t)(Q_ANI + n) * N + i];
+            FX[3][n] = a.fp[(int64_t)(Q_SIA + n) * N + i];
+        }
+        if (ti == 0) bwd_coeffs<R, 0>(P, FR, FX, ql, sm + BW_C);
+        else bwd_coeffs<R, 1>(P, FR, FX, ql, sm + BW_C);
+        if (ql == 0) {   // onsite term dE_i/dS_i = 2 Fp_O S_i, counted once per atom
+            const R fo = R(2) * a.fp[(int64_t)Q_O * N + i];
+            acc.hx = fo * si.x; acc.hy = fo * si.y; acc.hz = fo * si.z;
+        }
+        __syncwarp(0xfu << (quad * 4));
+        const int ca = a.cap_ang;
+        bwd_rows<R, true>(P, a, i, ti, ql, c.y, c.x, pi, si, sm, acc);
+        bwd_rows<R, false>(P, a, i, ti, ca + ql, ca + c.w, ca + c.z, pi, si, sm, acc);
+    }
+    // per-atom sums over the quad
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+        acc.fx += __shfl_xor_sync(0xffffffffu, acc.fx, o);
+        acc.fy += __shfl_xor_sync(0xffffffffu, acc.fy, o);
+        acc.fz += __shfl_xor_sync(0xffffffffu, acc.fz, o);
+        acc.hx += __shfl_xor_sync(0xffffffffu, acc.hx, o);
+        acc.hy += __shfl_xor_sync(0xffffffffu, acc.hy, o);
+        acc.hz += __shfl_xor_sync(0xffffffffu, acc.hz, o);
+    }
     if (a.want_virial) {
 #pragma unroll
-        for (int t = 0; t < 9; ++t) a.wpart[(int64_t)t * N + i] = acc.w[t];
+        for (int t = 0; t < 9; ++t) {
+            acc.w[t] += __shfl_xor_sync(0xffffffffu, acc.w[t], 1);
+            acc.w[t] += __shfl_xor_sync(0xffffffffu, acc.w[t], 2);
+        }
     }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(128) k_rad_bwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    if (i < a.n_fe) rad_bwd_atom<R, 0>(P, a, i);
-    else rad_bwd_atom<R, 1>(P, a, i);
+    if (valid && ql == 0) {
+        v4<R> f4, g4;
+        f4.x = acc.fx; f4.y = acc.fy; f4.z = acc.fz; f4.w = R(0);
+        g4.x = acc.hx; g4.y = acc.hy; g4.z = acc.hz; g4.w = R(0);
+        a.fown[i] = f4;
+        a.gii[i] = g4;
+        if (a.want_virial) {
+#pragma unroll
+            for (int t = 0; t < 9; ++t) a.wpart[(int64_t)t * N + i] = acc.w[t];
+        }
+    }
 }
 
 // ------------------------------------------------------------------ launch
@@ -752,7 +675,6 @@ static Eval2Args<R> args2(Sys &s, bool want_virial) {
     a.cap = s.cap; a.cap_ang = s.cap_ang;
     a.clj = s.clj; a.cls = s.cls; a.cnt = s.cnt;
     a.q = (R *)s.q; a.bsum = (R *)s.bsum; a.fp = (R *)s.fp; a.ei = (R *)s.ei;
-    a.apair = (v4<R> *)s.apair; a.gii_ang = (v4<R> *)s.gii_ang;
     a.pd = (PairRec<R> *)s.pairs; a.fown = (v4<R> *)s.fown; a.gii = (v4<R> *)s.gii;
     a.wpart = (R *)s.wpart; a.want_virial = want_virial; a.status = s.status;
     return a;
@@ -763,15 +685,15 @@ static constexpr int quad_block() { return sizeof(R) == 8 ? 64 : 128; }
 template <typename R>
 static constexpr size_t fwd_smem() { return (size_t)(quad_block<R>() / 32) * 8 * FQUAD * sizeof(R); }
 template <typename R>
-static constexpr size_t bwd_smem() { return (size_t)(quad_block<R>() / 32) * 8 * BQUAD * sizeof(R); }
+static constexpr size_t bwdf_smem() { return (size_t)(quad_block<R>() / 32) * 8 * BW_ATOM * sizeof(R); }
 
 void eval2_init() {
     static bool done = false;
     if (done) return;
     cudaFuncSetAttribute(k_ang_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<float>());
     cudaFuncSetAttribute(k_ang_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<double>());
-    cudaFuncSetAttribute(k_ang_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<float>());
-    cudaFuncSetAttribute(k_ang_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<double>());
+    cudaFuncSetAttribute(k_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<float>());
+    cudaFuncSetAttribute(k_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<double>());
     done = true;
 }
 
@@ -783,15 +705,14 @@ static void eval2_impl(Sys &s, const NepDev<R> &P, bool want_virial, cudaEvent_t
     const unsigned nq = (unsigned)((s.n + qb / 4 - 1) / (qb / 4));
     if (ev) cudaEventRecord(ev[0], s.stream);
     k_compact<R><<<nb, 128, 0, s.stream>>>(P, a);
-    k_rad_fwd<R><<<nb, 128, 0, s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[1], s.stream);
-    k_ang_fwd<R><<<nq, qb, fwd_smem<R>(), s.stream>>>(P, a);
+    k_rad_fwd<R><<<nb, 128, 0, s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[2], s.stream);
-    launch_network(s, nullptr);
+    k_ang_fwd<R><<<nq, qb, fwd_smem<R>(), s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[3], s.stream);
-    k_ang_bwd<R><<<nq, qb, bwd_smem<R>(), s.stream>>>(P, a);
+    launch_network(s, nullptr);
     if (ev) cudaEventRecord(ev[4], s.stream);
-    k_rad_bwd<R><<<nb, 128, 0, s.stream>>>(P, a);
+    k_bwd<R><<<nq, qb, bwdf_smem<R>(), s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[5], s.stream);
 }
 

@@ -30,8 +30,6 @@ struct Eval2Args {
     uint16_t *cls;     // ... its candidate slot s (low byte) and the reverse slot rev[s][i] (high byte)
     int4 *cnt;         // (angular rows of species 0, angular rows, radial-only rows of species 0, radial-only rows)
     R *q, *bsum, *fp, *ei;
-    v4<R> *apair;      // [cap_ang][n]: angular dE_i/dr_ij (x, y, z) and spin weight c_ij
-    v4<R> *gii_ang;    // [n]: angular dE_i/dS_i
     PairRec<R> *pd;    // [cap][n]
     v4<R> *fown, *gii;
     R *wpart;

@@ -72,8 +72,6 @@ struct Sys {
     int32_t *clj = nullptr;    // [cap_ang + cap][n] compact in-cutoff neighbours
     uint16_t *cls = nullptr;   // [cap_ang + cap][n] candidate slot | reverse slot << 8
     int4 *cnt = nullptr;       // [n] compact row counts
-    void *apair = nullptr;     // [cap_ang][n] angular pair derivatives
-    void *gii_ang = nullptr;   // [n] angular dE_i/dS_i
     void *fown = nullptr;      // [n] v4: sum_j dE_i/dr_ij
     void *gii = nullptr;       // [n] v4: dE_i/dS_i
     void *wpart = nullptr;     // [9][n] per-atom virial parts
@@ -109,8 +107,8 @@ void launch_rebuild(Sys &s, bool conditional);
 void launch_eval(Sys &s, bool want_virial, cudaEvent_t *ev = nullptr);
 void eval2_init();
 void launch_network(Sys &s, cudaEvent_t *ev);   // sl_nep.cu
-// first half, rebuild group (7), compaction + descriptor (3), network, backward (2), second half
-constexpr int KERNELS_PER_STEP = 1 + 7 + 3 + 1 + 2 + 1;
+// first half, rebuild group (7), compaction, radial and angular forward, network, backward, second half
+constexpr int KERNELS_PER_STEP = 1 + 7 + 3 + 1 + 1 + 1;
 // sl_integrate.cu
 void launch_first_half(Sys &s);
 void launch_second_half(Sys &s);

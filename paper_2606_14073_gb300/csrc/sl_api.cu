@@ -164,6 +164,7 @@ int check_status(sl::Sys &s) {
     if (st & sl::ST_NBR_OVERFLOW)
         return fail(SL_ENBR_OVERFLOW, "neighbour list capacity exceeded (caps %d/%d)", s.cap, s.cap_ang);
     if (st & sl::ST_NONFINITE) return fail(SL_ENONFINITE, "non-finite force or field");
+    if (st & sl::ST_TIMEOUT) return fail(SL_ETIMEOUT, "a bounded device wait gave up (tensor-core network)");
     return SL_OK;
 }
 

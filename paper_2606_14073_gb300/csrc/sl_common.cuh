@@ -287,5 +287,6 @@ __device__ __forceinline__ void gauss3f(uint64_t step, uint64_t atom, uint64_t s
 // Device status bits.
 constexpr int ST_NBR_OVERFLOW = 1;
 constexpr int ST_NONFINITE = 2;
+constexpr int ST_TIMEOUT = 4;
 
 }  // namespace sl

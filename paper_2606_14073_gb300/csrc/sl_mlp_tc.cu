@@ -1,0 +1,319 @@
+// sl_mlp_tc.cu -- the per-atom network on the 5th-generation tensor cores (tcgen05 + TMEM).
+//
+// Network (arXiv 2606.14073, Section 5.2.3 "ANN"; one hidden tanh layer):
+//   E_i  = sum_h w1_h tanh(z_ih) - b1,   z_ih = sum_v W0_hv (s_v q_iv) - b0_h
+//   Fp_iv = s_v sum_h t_ih W0_hv,        t_ih = w1_h (1 - tanh^2 z_ih)
+// computed for tiles of 128 atoms as two dense contractions over atoms:
+//   GEMM1  Z[128 x 32] = Q~[128 x 80] . W0^T[80 x 32]   (66 descriptor entries, 30 units, padded)
+//   GEMM2  G[128 x 80] = T [128 x 32] . W0  [32 x 80]
+// Operands are FP16 in shared memory in the canonical no-swizzle K-major layout
+// (8-row x 16-byte core matrices; K-adjacent ones contiguous); every FP32 value x
+// is split into hi = fp16(x), lo = fp16(x - hi) and each GEMM accumulates
+// hi.hi + hi.lo + lo.hi in FP32 in tensor memory, which keeps the network within
+// ~1e-6 relative of FP32 arithmetic.  One thread issues the MMAs; completion is
+// signalled through an mbarrier (tcgen05.commit); the 128 threads read their
+// atom's row back with tcgen05.ld (TMEM lane = atom row).  Persistent CTAs loop
+// over tiles; the weights are staged once per CTA.  Every wait is bounded: on
+// timeout the kernel raises ST_TIMEOUT, frees its tensor memory and returns.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "sl_internal.h"
+
+namespace sl {
+namespace tc {
+
+constexpr int TM = 128;          // atoms per tile (MMA M)
+constexpr int K1 = 80;           // descriptor entries padded to a multiple of 16
+constexpr int N1 = 32;           // hidden units padded
+constexpr int K2 = N1;
+constexpr int N2 = K1;
+constexpr int TMEM_COLS = 128;   // Z in columns [0, 32), G in [32, 112)
+
+// shared memory (bytes)
+constexpr uint32_t SZ_A1 = TM * K1 * 2;    // 20480
+constexpr uint32_t SZ_B1 = N1 * K1 * 2;    // 5120
+constexpr uint32_t SZ_A2 = TM * K2 * 2;    // 8192
+constexpr uint32_t SZ_B2 = N2 * K2 * 2;    // 5120
+constexpr uint32_t OFF_A1H = 0, OFF_A1L = OFF_A1H + SZ_A1;
+constexpr uint32_t OFF_B1H = OFF_A1L + SZ_A1, OFF_B1L = OFF_B1H + SZ_B1;
+constexpr uint32_t OFF_A2H = OFF_B1L + SZ_B1, OFF_A2L = OFF_A2H + SZ_A2;
+constexpr uint32_t OFF_B2H = OFF_A2L + SZ_A2, OFF_B2L = OFF_B2H + SZ_B2;
+constexpr uint32_t OFF_BAR = OFF_B2L + SZ_B2;            // 8-byte mbarrier
+constexpr uint32_t OFF_TMEM = OFF_BAR + 8;                // tensor-memory base address
+constexpr uint32_t SMEM_BYTES = OFF_TMEM + 8;
+
+// byte offset of element (row, k) of a [rows x K] 16-bit operand in the canonical
+// no-swizzle K-major layout: core matrix = 8 rows x 8 elements (128 B, row stride 16 B),
+// K-adjacent core matrices 128 B apart (LBO), 8-row groups K/8 * 128 B apart (SBO)
+__host__ __device__ constexpr uint32_t cm_off(int row, int k, int K) {
+    return (uint32_t)((row >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// tcgen05 shared-memory matrix descriptor: start address, LBO, SBO (all >> 4),
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor, kind::f16: D = F32, A = B = F16, both K-major, dense
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(r[t]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// eight FP32 values -> 16 bytes of FP16 hi parts and 16 bytes of lo parts
+__device__ __forceinline__ void split8(const float x[8], uint4 &hi, uint4 &lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const __half a = __float2half_rn(x[2 * t]), b = __float2half_rn(x[2 * t + 1]);
+        const __half la = __float2half_rn(x[2 * t] - __half2float(a));
+        const __half lb = __float2half_rn(x[2 * t + 1] - __half2float(b));
+        h[t] = (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+        l[t] = (uint32_t)__half_as_ushort(la) | ((uint32_t)__half_as_ushort(lb) << 16);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__global__ void __launch_bounds__(128, 1) k_mlp_tc(const __grid_constant__ NepDev<float> P, const float *__restrict__ q,
+                                                   float *__restrict__ fp, float *__restrict__ ei, int64_t n,
+                                                   int *status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t bar = sbase + OFF_BAR;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + OFF_TMEM);
+
+    // weights, once per CTA: B1[h][v] = W0[h][v], B2[v][h] = W0[h][v]; zero padding
+    for (int c = tid; c < N1 * (K1 / 8); c += blockDim.x) {      // B1: 32 rows x 10 chunks
+        const int h = c / (K1 / 8), k0 = (c % (K1 / 8)) * 8;
+        float x[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) x[t] = (h < NH && k0 + t < DIM) ? P.w0[h][k0 + t] : 0.f;
+        uint4 hi, lo;
+        split8(x, hi, lo);
+        *reinterpret_cast<uint4 *>(smem + OFF_B1H + cm_off(h, k0, K1)) = hi;
+        *reinterpret_cast<uint4 *>(smem + OFF_B1L + cm_off(h, k0, K1)) = lo;
+    }
+    for (int c = tid; c < N2 * (K2 / 8); c += blockDim.x) {      // B2: 80 rows x 4 chunks
+        const int v = c / (K2 / 8), k0 = (c % (K2 / 8)) * 8;
+        float x[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) x[t] = (v < DIM && k0 + t < NH) ? P.w0[k0 + t][v] : 0.f;
+        uint4 hi, lo;
+        split8(x, hi, lo);
+        *reinterpret_cast<uint4 *>(smem + OFF_B2H + cm_off(v, k0, K2)) = hi;
+        *reinterpret_cast<uint4 *>(smem + OFF_B2L + cm_off(v, k0, K2)) = lo;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sbase + OFF_TMEM),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t t_z = tmem, t_g = tmem + N1;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;   // this warp's TMEM lane quadrant
+    constexpr uint32_t IDESC1 = instr_desc(TM, N1), IDESC2 = instr_desc(TM, N2);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int64_t ntiles = (n + TM - 1) / TM;
+
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int64_t i = tile * TM + tid;
+        const bool valid = i < n;
+        // A1 row: s_v q_v, hi/lo
+#pragma unroll
+        for (int c = 0; c < K1 / 8; ++c) {
+            float x[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int v = c * 8 + t;
+                x[t] = (valid && v < DIM) ? P.scal[v] * q[(int64_t)v * n + i] : 0.f;
+            }
+            uint4 hi, lo;
+            split8(x, hi, lo);
+            *reinterpret_cast<uint4 *>(smem + OFF_A1H + cm_off(tid, c * 8, K1)) = hi;
+            *reinterpret_cast<uint4 *>(smem + OFF_A1L + cm_off(tid, c * 8, K1)) = lo;
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            uint32_t acc = 0;
+#pragma unroll
+            for (int ks = 0; ks < K1 / 16; ++ks) {
+                const uint32_t ko = ks * 256;
+                const uint64_t ah = smem_desc(sbase + OFF_A1H + ko, 128, (K1 / 8) * 128);
+                const uint64_t al = smem_desc(sbase + OFF_A1L + ko, 128, (K1 / 8) * 128);
+                const uint64_t bh = smem_desc(sbase + OFF_B1H + ko, 128, (K1 / 8) * 128);
+                const uint64_t bl = smem_desc(sbase + OFF_B1L + ko, 128, (K1 / 8) * 128);
+                mma_f16(t_z, ah, bh, IDESC1, acc);
+                acc = 1;
+                mma_f16(t_z, ah, bl, IDESC1, 1);
+                mma_f16(t_z, al, bh, IDESC1, 1);
+            }
+            mma_commit(bar);
+        }
+        // every thread waits; the block agrees on the outcome before anyone leaves the loop
+        if (!__syncthreads_and(mbar_wait(bar, phase))) { ok = false; break; }
+        phase ^= 1u;
+        tc_fence_after();
+        // epilogue 1: tanh layer, E_i, t_h into the A2 tile
+        float z[N1];
+        tmem_ld16(t_z + lane_off, z);
+        tmem_ld16(t_z + lane_off + 16, z + 16);
+        tmem_wait_ld();
+        float tt[N1];
+        float E = -P.b1;
+#pragma unroll
+        for (int h = 0; h < N1; ++h) {
+            if (h < NH) {
+                const float a = tanhf(z[h] - P.b0[h]);
+                E += P.w1[h] * a;
+                tt[h] = P.w1[h] * (1.f - a * a);
+            } else {
+                tt[h] = 0.f;
+            }
+        }
+        if (valid) ei[i] = E;
+#pragma unroll
+        for (int c = 0; c < K2 / 8; ++c) {
+            uint4 hi, lo;
+            split8(tt + 8 * c, hi, lo);
+            *reinterpret_cast<uint4 *>(smem + OFF_A2H + cm_off(tid, c * 8, K2)) = hi;
+            *reinterpret_cast<uint4 *>(smem + OFF_A2L + cm_off(tid, c * 8, K2)) = lo;
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int ks = 0; ks < K2 / 16; ++ks) {
+                const uint32_t ko = ks * 256;
+                const uint64_t ah = smem_desc(sbase + OFF_A2H + ko, 128, (K2 / 8) * 128);
+                const uint64_t al = smem_desc(sbase + OFF_A2L + ko, 128, (K2 / 8) * 128);
+                const uint64_t bh = smem_desc(sbase + OFF_B2H + ko, 128, (K2 / 8) * 128);
+                const uint64_t bl = smem_desc(sbase + OFF_B2L + ko, 128, (K2 / 8) * 128);
+                mma_f16(t_g, ah, bh, IDESC2, ks > 0 ? 1u : 0u);
+                mma_f16(t_g, ah, bl, IDESC2, 1);
+                mma_f16(t_g, al, bh, IDESC2, 1);
+            }
+            mma_commit(bar);
+        }
+        if (!__syncthreads_and(mbar_wait(bar, phase))) { ok = false; break; }
+        phase ^= 1u;
+        tc_fence_after();
+        // epilogue 2: Fp_v = s_v G_v
+#pragma unroll
+        for (int c = 0; c < N2 / 16; ++c) {
+            float g[16];
+            tmem_ld16(t_g + lane_off + 16 * c, g);
+            tmem_wait_ld();
+            if (valid) {
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int v = 16 * c + t;
+                    if (v < DIM) fp[(int64_t)v * n + i] = P.scal[v] * g[t];
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();   // TMEM and the A tiles are free for the next tile
+    }
+    if (!ok) {
+        if (tid == 0) atomicOr(status, ST_TIMEOUT);
+        // let any MMA still in flight finish before the memory is released (bounded)
+        mbar_wait(bar, phase);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+}  // namespace tc
+
+int mlp_tc_blocks_per_sm() { return 1; }
+
+void launch_network_tc(Sys &s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(tc::k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM_BYTES);
+        attr = true;
+    }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t ntiles = (s.n + tc::TM - 1) / tc::TM;
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * 2);
+    tc::k_mlp_tc<<<grid, 128, tc::SMEM_BYTES, s.stream>>>(s.pf, (const float *)s.q, (float *)s.fp, (float *)s.ei, s.n,
+                                                       s.status);
+}
+
+}  // namespace sl

@@ -215,10 +215,11 @@ static void network_impl(Sys &s, const NepDev<R> &P) {
     k_mlp<R><<<nb, 128, 0, s.stream>>>(P, (const R *)s.q, (R *)s.fp, (R *)s.ei, s.n);
 }
 
+// FP64 mode: CUDA-core network in FP64; mixed mode: the tensor-core network (sl_mlp_tc.cu)
 void launch_network(Sys &s, cudaEvent_t *) {
     if (s.n == 0) return;
     if (s.prec == 0) network_impl<double>(s, s.pd);
-    else network_impl<float>(s, s.pf);
+    else launch_network_tc(s);
 }
 
 // ------------------------------------------------------------------ no-allocation variant

@@ -222,6 +222,22 @@ def run_e2e(args, sysm, wl, world, barrier, dist, torch):
     return e2e
 
 
+def run_serving(args, params, replica_offset=0):
+    """Sweep requests (B20 replicas of 12^3-20^3 cells, 50-320 K, 0-0.5 T, 100-400 steps) arriving
+    as a Poisson process, served with admission by free device memory and chunked batching."""
+    from paper_2606_14073_gb300.serving import GpuBackend, Server, poisson_requests
+    reqs = poisson_requests(args.serve_requests, args.serve_rate, cells=(12, 20), steps=(100, 400))
+    for r in reqs:
+        r.replica += replica_offset
+    be = GpuBackend(params)
+    out = Server(be, max_active=32, chunk=50).run(reqs)
+    return {"requests": out["requests"], "arrival_rate_per_s": args.serve_rate,
+            "throughput_atom_steps_per_s": out["throughput_atom_steps_per_s"],
+            "latency_p50_s": out["latency_p50_s"], "latency_p99_s": out["latency_p99_s"],
+            "makespan_s": out["makespan_s"], "memory_waits": out["memory_waits"],
+            "recipe": "cells U{12..20}, T U(50,320) K, B_z U(0,0.5) T, steps U{100..400}, mixed precision"}
+
+
 def run_ours(args):
     import torch
     from paper_2606_14073_gb300 import flops, nep_params, spinlat as S, workloads as W
@@ -320,6 +336,11 @@ def run_ours(args):
         e2e = run_e2e(args, sysm, wl, world, barrier, dist, torch)
 
     cpu = None
+    # continuous-batching serving run: Poisson sweep requests, p50/p99 time to completion
+    serving = None
+    if not args.skip_serving:
+        serving = run_serving(args, params, replica_offset=1000 * rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu_baseline:
         from oracle import oracle as O
@@ -342,7 +363,7 @@ def run_ours(args):
                 "kernel_share": shares, "kernel_ms_per_step": {k: v / args.profile_steps for k, v in prof.items()},
                 "kernel_alu_frac": {k: fl[k] * wl.n / (prof[k] / args.profile_steps * 1e-3) / 1e12 / peak_derived
                                     for k in ("rad_fwd", "ang_fwd", "network", "backward")},
-                "fp64": fp64, "mixed_error_vs_fp64": err, "cpu_baseline": cpu}
+                "fp64": fp64, "mixed_error_vs_fp64": err, "serving": serving, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -361,6 +382,9 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=8.0, help="request arrivals per second")
     ap.add_argument("--cells", type=int, default=48, help="B20 cells per side (48: the benchmark workload; "
                                                            "smaller values are for profiling captures)")
     args = ap.parse_args()

@@ -143,6 +143,10 @@ int sl_set_state(sl_system *sys, const double *positions, const double *velociti
 int sl_get_neighbors(sl_system *sys, int32_t cap, int32_t *counts_rad, int32_t *lists_rad,
                      int32_t *counts_ang, int32_t *lists_ang);
 
+/* Device bytes a system of n atoms with these options will allocate (for admission
+ * control by callers that pack replicas into free device memory). */
+int64_t sl_estimate_device_bytes(int64_t n, const sl_options *opt);
+
 /* Number of atoms, precision mode, neighbour-list builds so far (device-triggered
  * rebuilds included) and kernels launched by sl_step/sl_step_profiled so far. */
 int sl_get_info(const sl_system *sys, int64_t *n_atoms, int32_t *precision, int64_t *n_builds,

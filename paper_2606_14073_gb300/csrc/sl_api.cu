@@ -669,6 +669,23 @@ int sl_get_info(const sl_system *sys, int64_t *n_atoms, int32_t *precision, int6
     return SL_OK;
 }
 
+int64_t sl_estimate_device_bytes(int64_t n, const sl_options *opt_in) {
+    sl_options opt;
+    if (opt_in) opt = *opt_in;
+    else sl_default_options(&opt);
+    if (n < 0) return -1;
+    const int64_t R = opt.precision == SL_PREC_FP64 ? 8 : 4;
+    const int64_t cap = opt.nbr_cap_rad, ca = opt.nbr_cap_ang;
+    int64_t per = 7 * 32 + 2 * 16                      // state (double4) and FP32 copies
+                  + 3 * 4 + 4 + 16                     // species, caller index maps, list segments
+                  + 2 * 4 * cap                        // candidate lists, reverse slots
+                  + 6 * (ca + cap) + 16                // compact rows, counts
+                  + R * (2 * sl::DIM + sl::NB + 1 + 9) // q, Fp, angular sums, E_i, virial parts
+                  + R * 8 * cap + 2 * R * 4            // pair records, per-atom sums
+                  + 2 * 32 + 5 * 32 + 3 * 4;           // evaluation outputs, snapshot, cell arrays
+    return n * per + (1 << 20);
+}
+
 int sl_step_profiled(sl_system *sys, int64_t n_steps, double dt, double T, const double B[3], double *kernel_ms) {
     if (!sys || !B || !kernel_ms) return fail(SL_EINVAL, "NULL argument");
     if (n_steps < 0 || !(dt > 0) || !(T >= 0)) return fail(SL_EINVAL, "bad step arguments");

@@ -1,0 +1,183 @@
+"""Continuous-batching server for temperature/field sweep replicas.
+
+Requests (one FeGe replica each: size, temperature, field, number of steps) arrive
+over time.  The server
+
+  * admits a waiting request as soon as a slot is free and the device has room
+    for its state (the library's own estimate against the free device memory,
+    keeping a reserve), creating the replica's state on the device;
+  * steps every admitted replica together in chunks: each chunk issues the
+    replicas' captured step graphs on their own CUDA streams before waiting for
+    any of them (one sl_batch_step call), so replicas of uneven size overlap on
+    the device;
+  * retires a replica when its steps are done, records its result and its
+    time from arrival to completion, and frees its memory for the next request.
+
+A replica's trajectory does not depend on what else runs beside it: its kernels
+read only its own state, and its noise is keyed by (seed, replica).
+
+The scheduling logic is independent of the GPU: `Server` talks to a backend
+(`GpuBackend` here, a fake one in the host tests).
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+
+from . import workloads as W
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    cells: int
+    T: float
+    B: tuple
+    n_steps: int
+    arrival: float                 # seconds after the start of the run
+    dt: float = 1.0
+    replica: int = 0
+
+
+@dataclasses.dataclass
+class Done:
+    rid: int
+    atoms: int
+    n_steps: int
+    arrival: float
+    admitted: float
+    finished: float
+    result: dict
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+def poisson_requests(count: int, rate: float, *, seed: int = 20260105, cells=(12, 40), steps=(200, 2000),
+                     T=(50.0, 320.0), Bz=(0.0, 0.5)) -> list[Request]:
+    """Sweep requests with exponential inter-arrival times (rate per second)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        out.append(Request(rid=k, cells=int(rng.integers(cells[0], cells[1] + 1)),
+                           T=float(rng.uniform(*T)), B=(0.0, 0.0, float(rng.uniform(*Bz))),
+                           n_steps=int(rng.integers(steps[0], steps[1] + 1)), arrival=t, replica=k))
+    return out
+
+
+class GpuBackend:
+    """Replicas as libspinlat systems (mixed precision by default)."""
+
+    def __init__(self, params: dict, precision=None, reserve_bytes: int = 2 << 30, steps_per_graph: int = 10):
+        from . import spinlat as S
+        import torch
+        self.S = S
+        self.torch = torch
+        self.params = params
+        self.precision = S.SL_PREC_MIXED if precision is None else precision
+        self.reserve = reserve_bytes
+        self.steps_per_graph = steps_per_graph
+
+    def bytes_needed(self, req: Request) -> int:
+        return self.S.sl_estimate_device_bytes(8 * req.cells ** 3, self.precision)
+
+    def free_bytes(self) -> int:
+        free, _ = self.torch.cuda.mem_get_info()
+        return int(free) - self.reserve
+
+    def create(self, req: Request):
+        wl = W.fege_cube(req.cells, T=req.T, spin_mode="canted", seed=W.STRUCTURE_SEED0 + 100 + req.rid,
+                         replica=req.replica)
+        s = self.S.System(wl.positions, wl.spins, wl.box, wl.periodic, wl.species, self.params, wl.velocities,
+                          precision=self.precision, seed=wl.seed, replica=req.replica,
+                          steps_per_graph=self.steps_per_graph)
+        return s
+
+    def step(self, handles, n_steps, dts, Ts, Bs):
+        b = self.S.Batch(handles)
+        b.step(n_steps, dts, Ts, Bs)
+        b.destroy()
+
+    def result(self, h) -> dict:
+        st = h.get_state()
+        return dict(positions=st["positions"], spins=st["spins"], velocities=st["velocities"], step=st["step"])
+
+    def atoms(self, h) -> int:
+        return h.n
+
+    def destroy(self, h):
+        h.destroy()
+
+
+class RealClock:
+    def __init__(self):
+        self.t0 = time.perf_counter()
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def sleep(self, dt: float):
+        time.sleep(max(0.0, dt))
+
+
+class Server:
+    """Admission by free device memory, chunked continuous batching, latency records."""
+
+    def __init__(self, backend, *, max_active: int = 64, chunk: int = 50, clock=None):
+        self.b = backend
+        self.max_active = max_active
+        self.chunk = chunk
+        self.clock = clock
+
+    def run(self, requests: list[Request]) -> dict:
+        clock = self.clock or RealClock()
+        pending = sorted(requests, key=lambda r: r.arrival)
+        waiting: list[Request] = []
+        active: dict[int, list] = {}          # rid -> [request, handle, steps_left, admitted_at]
+        done: list[Done] = []
+        k = 0
+        memory_waits = 0
+        while k < len(pending) or waiting or active:
+            t = clock.now()
+            while k < len(pending) and pending[k].arrival <= t:
+                waiting.append(pending[k])
+                k += 1
+            # admission in arrival order while a slot and device memory are free
+            while waiting and len(active) < self.max_active:
+                req = waiting[0]
+                if self.b.bytes_needed(req) > self.b.free_bytes():
+                    memory_waits += 1
+                    break
+                waiting.pop(0)
+                active[req.rid] = [req, self.b.create(req), req.n_steps, clock.now()]
+            if not active:
+                if waiting:
+                    raise RuntimeError(f"request {waiting[0].rid} needs more device memory than is free")
+                if k < len(pending):
+                    clock.sleep(pending[k].arrival - clock.now())
+                continue
+            rids = list(active)
+            nst = [min(self.chunk, active[r][2]) for r in rids]
+            self.b.step([active[r][1] for r in rids], nst, [active[r][0].dt for r in rids],
+                        [active[r][0].T for r in rids], [active[r][0].B for r in rids])
+            t = clock.now()
+            for r, n in zip(rids, nst):
+                entry = active[r]
+                entry[2] -= n
+                if entry[2] <= 0:
+                    req, h, _, adm = entry
+                    done.append(Done(r, self.b.atoms(h), req.n_steps, req.arrival, adm, t, self.b.result(h)))
+                    self.b.destroy(h)
+                    del active[r]
+        makespan = clock.now()
+        lat = np.array([d.latency for d in done]) if done else np.zeros(1)
+        work = sum(d.atoms * d.n_steps for d in done)
+        return dict(done=sorted(done, key=lambda d: d.rid), makespan_s=makespan,
+                    throughput_atom_steps_per_s=work / makespan if makespan > 0 else 0.0,
+                    latency_p50_s=float(np.percentile(lat, 50)), latency_p99_s=float(np.percentile(lat, 99)),
+                    memory_waits=memory_waits, requests=len(done))

@@ -22,7 +22,8 @@ _NAMES = {SL_EINVAL: "SL_EINVAL", SL_ENOMEM: "SL_ENOMEM", SL_ENBR_OVERFLOW: "SL_
 EXPORTS = ["sl_default_options", "sl_create_system", "sl_step", "sl_energy_forces_fields", "sl_get_descriptors",
            "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_get_stream",
            "sl_destroy_system", "sl_last_error", "sl_batch_create", "sl_batch_step", "sl_batch_destroy",
-           "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak", "sl_descriptors_energies_noalloc"]
+           "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak", "sl_descriptors_energies_noalloc",
+           "sl_estimate_device_bytes"]
 KERNEL_GROUPS = ["first_half", "rebuild", "compact", "rad_fwd", "ang_fwd", "network", "backward", "second_half"]
 
 
@@ -71,6 +72,8 @@ def lib(path: str | None = None):
             L.sl_step_profiled.argtypes = [P, I64, D, D, P, P]
             L.sl_measure_fma_peak.argtypes = [I32, P, P]
             L.sl_descriptors_energies_noalloc.argtypes = [P, P, P, I64, P, P, P, P, P, P]
+            L.sl_estimate_device_bytes.argtypes = [I64, P]
+            L.sl_estimate_device_bytes.restype = C.c_int64
             L.sl_get_stream.argtypes = [P]
             L.sl_get_stream.restype = P
             L.sl_destroy_system.argtypes = [P]
@@ -280,6 +283,12 @@ def sl_descriptors_energies_noalloc(positions4_ptr: int, spins4_ptr: int, specie
     per = np.ascontiguousarray(periodic, dtype=np.int32)
     _check(lib().sl_descriptors_energies_noalloc(positions4_ptr, spins4_ptr, species_ptr, int(n), _ptr(b), _ptr(per),
                                                  C.byref(P.struct), q_ptr, energy_ptr, stream_ptr))
+
+
+def sl_estimate_device_bytes(n: int, precision=SL_PREC_MIXED, cap_rad=160, cap_ang=64) -> int:
+    o = sl_default_options()
+    o.precision, o.nbr_cap_rad, o.nbr_cap_ang = int(precision), int(cap_rad), int(cap_ang)
+    return int(lib().sl_estimate_device_bytes(int(n), C.byref(o)))
 
 
 def system_from_workload(wl, params: dict, **kw) -> System:

@@ -288,7 +288,8 @@ def run_ours(args):
 
     # warm-up (graph capture happens here)
     sysm.step(args.warmup, DT, TEMP, FIELD)
-    launches0 = sysm.info()["n_launches"]
+    info0 = sysm.info()
+    launches0 = info0["n_launches"]
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
@@ -302,7 +303,9 @@ def run_ours(args):
     barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    launches = sysm.info()["n_launches"] - launches0
+    info1 = sysm.info()
+    launches = info1["n_launches"] - launches0
+    builds_timed = info1["n_builds"] - info0["n_builds"]
     ms_max = ms
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
@@ -311,7 +314,9 @@ def run_ours(args):
     value = wl.n * args.steps * world / (ms_max * 1e-3)
 
     # per-kernel device times (CUDA events between the kernel groups, same stream, no graphs)
+    b0 = sysm.info()["n_builds"]
     prof = sysm.step_profiled(args.profile_steps, DT, TEMP, FIELD)
+    builds_prof = sysm.info()["n_builds"] - b0
     total = sum(prof.values())
     n_r, n_a = neighbour_counts(wl)
     fl = flops.per_atom(n_r, n_a)
@@ -360,6 +365,8 @@ def run_ours(args):
                            "B_T": list(FIELD), "steps_per_graph": args.graph_steps,
                            "l2": "inputs larger than L2 (~10 GB working set)", "parallelism": f"replicas x{world}"},
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+                "neighbour_builds": {"timed_region": builds_timed, "profiled_steps": builds_prof,
+                                     "ms_per_build": (prof["rebuild"] / builds_prof) if builds_prof else None},
                 "kernel_share": shares, "kernel_ms_per_step": {k: v / args.profile_steps for k, v in prof.items()},
                 "kernel_alu_frac": {k: fl[k] * wl.n / (prof[k] / args.profile_steps * 1e-3) / 1e12 / peak_derived
                                     for k in ("rad_fwd", "ang_fwd", "network", "backward")},

@@ -100,7 +100,7 @@ void fill_params(sl::NepDev<R> &P, const sl_nep_params *p) {
 
 void free_sys(sl::Sys &s) {
     void *ptrs[] = {s.pos, s.vel, s.spin, s.spin_prev, s.F, s.H, s.posref, s.posf, s.spinf, s.species, s.orig,
-                    s.inv, s.nbr, s.rev, s.seg, s.cells.count, s.cells.start, s.cells.fill, s.cells.atoms,
+                    s.inv, s.nbr, s.rev, s.nbr_orig, s.cells.posf, s.cells.key, s.seg, s.cells.count, s.cells.start, s.cells.fill, s.cells.atoms,
                     s.cells.of, s.q, s.bsum, s.fp, s.ei, s.pairs, s.clj, s.cls, s.cnt, s.fown, s.gii,
                     s.wpart, s.Fo, s.Ho,
                     s.status, s.rebuild, s.d_step, s.d_par, s.red, s.snap, s.d_builds};
@@ -276,7 +276,7 @@ int sl_create_system(const double *positions, const double *spins, const double 
     if (!out) return fail(SL_EINVAL, "out is NULL");
     *out = nullptr;
     if (!params || !box || !periodic) return fail(SL_EINVAL, "params, box and periodic are required");
-    if (n < 0 || n > 0x7fffffffLL) return fail(SL_EINVAL, "n = %lld out of range", (long long)n);
+    if (n < 0 || n >= (1LL << 30)) return fail(SL_EINVAL, "n = %lld out of range [0, 2^30)", (long long)n);
     if (n > 0 && (!positions || !spins || !species)) return fail(SL_EINVAL, "positions, spins, species required");
     if (params->n_species != NS || params->n_ch != NCH || params->l_max != 4 || params->basis_k != NK ||
         params->n_hidden != NH)
@@ -396,7 +396,8 @@ int sl_create_system(const double *positions, const double *spins, const double 
         (rc = dalloc(&s.spin_prev, N)) || (rc = dalloc(&s.F, N)) || (rc = dalloc(&s.H, N)) ||
         (rc = dalloc(&s.posref, N)) || (rc = dalloc(&s.posf, N)) || (rc = dalloc(&s.spinf, N)) ||
         (rc = dalloc(&s.species, N)) || (rc = dalloc(&s.orig, N)) || (rc = dalloc(&s.inv, N)) ||
-        (rc = dalloc(&s.nbr, N * s.cap)) || (rc = dalloc(&s.rev, N * s.cap)) || (rc = dalloc(&s.seg, N)) ||
+        (rc = dalloc(&s.nbr, N * s.cap)) || (rc = dalloc(&s.rev, N * s.cap)) ||
+        (rc = dalloc(&s.nbr_orig, N * s.cap)) || (rc = dalloc(&s.cells.posf, N)) || (rc = dalloc(&s.cells.key, N)) || (rc = dalloc(&s.seg, N)) ||
         (rc = dalloc(&s.cells.count, (size_t)s.cells.ncell)) || (rc = dalloc(&s.cells.start, (size_t)s.cells.ncell + 1)) ||
         (rc = dalloc(&s.cells.fill, (size_t)s.cells.ncell)) || (rc = dalloc(&s.cells.atoms, N)) ||
         (rc = dalloc(&s.cells.of, N)) || (rc = dalloc((char **)&s.q, R * DIM * N)) ||
@@ -677,8 +678,8 @@ int64_t sl_estimate_device_bytes(int64_t n, const sl_options *opt_in) {
     const int64_t R = opt.precision == SL_PREC_FP64 ? 8 : 4;
     const int64_t cap = opt.nbr_cap_rad, ca = opt.nbr_cap_ang;
     int64_t per = 7 * 32 + 2 * 16                      // state (double4) and FP32 copies
-                  + 3 * 4 + 4 + 16                     // species, caller index maps, list segments
-                  + 2 * 4 * cap                        // candidate lists, reverse slots
+                  + 3 * 4 + 4 + 16 + 16 + 4            // species, caller index maps, list segments, cell copies
+                  + 3 * 4 * cap                        // candidate lists (index and caller index), reverse slots
                   + 6 * (ca + cap) + 16                // compact rows, counts
                   + R * (2 * sl::DIM + sl::NB + 1 + 9) // q, Fp, angular sums, E_i, virial parts
                   + R * 8 * cap + 2 * R * 4            // pair records, per-atom sums

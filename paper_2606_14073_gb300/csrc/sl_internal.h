@@ -29,6 +29,8 @@ struct Cells {
     int nc[3];
     int ncell;
     int *count = nullptr, *start = nullptr, *fill = nullptr, *atoms = nullptr, *of = nullptr;
+    float4 *posf = nullptr;    // cell-ordered FP32 positions (list build)
+    uint32_t *key = nullptr;   // cell-ordered species << 30 | caller index
 };
 
 struct Sys {
@@ -58,8 +60,9 @@ struct Sys {
     int32_t *species = nullptr, *orig = nullptr, *inv = nullptr;
     int64_t n_fe = 0;          // atoms [0, n_fe) are species 0
 
-    // neighbour lists: slot-major [slot][atom]
-    int32_t *nbr = nullptr, *rev = nullptr;
+    // neighbour lists: nbr and rev slot-major [slot][atom]; nbr_orig (caller index of
+    // each entry, searched by the reverse-slot build) atom-major [atom][slot]
+    int32_t *nbr = nullptr, *rev = nullptr, *nbr_orig = nullptr;
     int4 *seg = nullptr;       // per atom: ends of (ang t0, ang t1, rad t0, rad t1)
     Cells cells;
 

@@ -43,8 +43,7 @@ struct GridArgs {
 __global__ void k_bin(const double4 *__restrict__ pos, int64_t n, GridArgs g, int *__restrict__ count,
                       int *__restrict__ of, const int *__restrict__ flag) {
     if (flag && *flag == 0) return;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double4 p = pos[i];
     const double x[3] = {p.x, p.y, p.z};
     int c[3];
@@ -56,6 +55,7 @@ __global__ void k_bin(const double4 *__restrict__ pos, int64_t n, GridArgs g, in
     const int cell = (c[2] * g.nc[1] + c[1]) * g.nc[0] + c[0];
     of[i] = cell;
     atomicAdd(count + cell, 1);
+    }
 }
 
 // Exclusive scan of count[0..m) into start[0..m], one block.
@@ -84,14 +84,20 @@ __global__ void k_scan(const int *__restrict__ count, int *__restrict__ start, i
     if (threadIdx.x == 0) start[m] = s_carry;
 }
 
+// Atoms into their cells, with a cell-ordered copy of the FP32 position and of the
+// key (species << 30 | caller index) so the list build reads candidates contiguously.
 __global__ void k_scatter(const int *__restrict__ of, int64_t n, const int *__restrict__ start, int *__restrict__ fill,
-                          int *__restrict__ atoms, const int *__restrict__ flag) {
+                          int *__restrict__ atoms, const float4 *__restrict__ posf, const int32_t *__restrict__ species,
+                          const int32_t *__restrict__ orig, float4 *__restrict__ cposf, uint32_t *__restrict__ ckey,
+                          const int *__restrict__ flag) {
     if (flag && *flag == 0) return;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int c = of[i];
-    const int p = atomicAdd(fill + c, 1);
-    atoms[start[c] + p] = (int)i;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = of[i];
+        const int p = start[c] + atomicAdd(fill + c, 1);
+        atoms[p] = (int)i;
+        cposf[p] = posf[i];
+        ckey[p] = ((uint32_t)species[i] << 30) | (uint32_t)orig[i];
+    }
 }
 
 struct ListArgs {
@@ -99,6 +105,9 @@ struct ListArgs {
     const float4 *posf;
     const int32_t *species, *orig, *inv;
     const int *cell_start, *cell_atoms, *cell_of;
+    const float4 *cposf;      // cell-ordered FP32 positions
+    const uint32_t *ckey;     // cell-ordered (species << 30 | caller index)
+    int32_t *nbr_orig;        // [n][cap] caller index of each list entry (atom-major)
     int64_t n;
     int cap, cap_ang;
     double cut_r2, cut_a2;
@@ -112,84 +121,12 @@ struct ListArgs {
     const int *flag;
 };
 
-constexpr int LIST_MAX = 256;   // per-thread candidate scratch (caps are <= this)
-
-__global__ void __launch_bounds__(128) k_build_lists(ListArgs a) {
-    if (a.flag && *a.flag == 0) return;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    unsigned long long key[LIST_MAX];
-    int m = 0;
-    bool overflow = false;
-    const double4 pi = a.pos[i];
-    const float4 pfi = a.posf[i];
-    const int cc = a.cell_of[i];
-    int ci[3] = {cc % a.g.nc[0], (cc / a.g.nc[0]) % a.g.nc[1], cc / (a.g.nc[0] * a.g.nc[1])};
-    int lo[3], hi[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        if (a.g.per[d] && a.g.nc[d] < 3) { lo[d] = 0; hi[d] = a.g.nc[d] - 1; }
-        else if (a.g.per[d]) { lo[d] = ci[d] - 1; hi[d] = ci[d] + 1; }
-        else { lo[d] = max(ci[d] - 1, 0); hi[d] = min(ci[d] + 1, a.g.nc[d] - 1); }
-    }
-    int nang = 0;
-    for (int z = lo[2]; z <= hi[2]; ++z)
-        for (int y = lo[1]; y <= hi[1]; ++y)
-            for (int x = lo[0]; x <= hi[0]; ++x) {
-                const int wx = (x + a.g.nc[0]) % a.g.nc[0];
-                const int wy = (y + a.g.nc[1]) % a.g.nc[1];
-                const int wz = (z + a.g.nc[2]) % a.g.nc[2];
-                const int c = (wz * a.g.nc[1] + wy) * a.g.nc[0] + wx;
-                for (int p = a.cell_start[c]; p < a.cell_start[c + 1]; ++p) {
-                    const int j = a.cell_atoms[p];
-                    if (j == i) continue;
-                    const float4 pfj = a.posf[j];
-                    float dx = pfj.x - pfi.x, dy = pfj.y - pfi.y, dz = pfj.z - pfi.z;
-                    minimg(a.bf, dx, dy, dz);
-                    const float d2f = dx * dx + dy * dy + dz * dz;
-                    if (d2f >= a.cut_r2f_hi) continue;
-                    bool in_r, in_a;
-                    if (d2f < a.cut_r2f_lo && (d2f < a.cut_a2f_lo || d2f >= a.cut_a2f_hi)) {
-                        in_r = true;
-                        in_a = d2f < a.cut_a2f_lo;
-                    } else {
-                        const double4 pj = a.pos[j];
-                        const double d2 = exact_d2(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z, a.bd, a.g.per);
-                        in_r = d2 < a.cut_r2;
-                        in_a = d2 < a.cut_a2;
-                    }
-                    if (!in_r) continue;
-                    if (m >= a.cap) { overflow = true; continue; }
-                    const unsigned sg = (in_a ? 0u : 2u) + (unsigned)a.species[j];
-                    key[m++] = ((unsigned long long)sg << 32) | (unsigned)a.orig[j];
-                    nang += in_a;
-                }
-            }
-    if (nang > a.cap_ang) overflow = true;
-    // insertion sort by (segment, caller index)
-    for (int u = 1; u < m; ++u) {
-        const unsigned long long k = key[u];
-        int v = u - 1;
-        while (v >= 0 && key[v] > k) { key[v + 1] = key[v]; --v; }
-        key[v + 1] = k;
-    }
-    int ends[4] = {0, 0, 0, 0};
-    for (int s = 0; s < m; ++s) {
-        const unsigned sg = (unsigned)(key[s] >> 32);
-        a.nbr[(int64_t)s * a.n + i] = a.inv[(unsigned)key[s]];
-        for (int t = sg; t < 4; ++t) ends[t] = s + 1;
-    }
-    // segments that received nothing still end where the previous one ended
-    for (int t = 1; t < 4; ++t) ends[t] = max(ends[t], ends[t - 1]);
-    a.seg[i] = make_int4(ends[0], ends[1], ends[2], ends[3]);
-    if (overflow) atomicOr(a.status, ST_NBR_OVERFLOW);
-}
-
 struct RevArgs {
     const double4 *pos;
     const int32_t *species, *orig;
-    const int32_t *nbr;
+    const int32_t *nbr, *nbr_orig;   // nbr_orig atom-major [n][cap]
     const int4 *seg;
+    int cap;
     int64_t n;
     double cut_a2;
     BoxDev<double> bd;
@@ -199,42 +136,206 @@ struct RevArgs {
     const int *flag;
 };
 
-// rev[s][i] = slot of i in the list of j = nbr[s][i].
-__global__ void k_build_rev(RevArgs a) {
-    if (a.flag && *a.flag == 0) return;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const int4 sg = a.seg[i];
-    const double4 pi = a.pos[i];
-    const int oi = a.orig[i];
-    const int ti = a.species[i];
-    for (int s = 0; s < sg.w; ++s) {
-        const int j = a.nbr[(int64_t)s * a.n + i];
-        const double4 pj = a.pos[j];
-        const double d2 = exact_d2(pj.x, pj.y, pj.z, pi.x, pi.y, pi.z, a.bd, a.per);
-        const int sgi = (d2 < a.cut_a2 ? 0 : 2) + ti;
-        const int4 sj = a.seg[j];
-        const int e[4] = {sj.x, sj.y, sj.z, sj.w};
-        int lo = sgi == 0 ? 0 : e[sgi - 1], hi = e[sgi];
-        int found = -1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            const int om = a.orig[a.nbr[(int64_t)mid * a.n + j]];
-            if (om == oi) { found = mid; break; }
-            if (om < oi) lo = mid + 1; else hi = mid;
+
+// Warp per atom.  Lanes take the candidates of each stencil cell 32 at a time;
+// pairs inside the list cutoff are appended to a per-warp shared-memory buffer
+// (ballot/popc, so the append order is the scan order), the buffer is sorted
+// by (segment, caller index) with a warp bitonic sort, and written out.
+
+// Ascending bitonic sort of 32*E keys held E per lane (element r*32 + lane in
+// register r): strides below 32 exchange through shuffles, larger ones inside the lane.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(uint32_t (&k)[E], int lane) {
+#pragma unroll
+    for (int size = 2; size <= 32 * E; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int e = r * 32 + lane;
+                const bool asc = (e & size) == 0;
+                if (stride >= 32) {
+                    const int rp = r ^ (stride >> 5);
+                    if (rp > r) {
+                        const uint32_t u = k[r], v = k[rp];
+                        const bool sw = (u > v) == asc;
+                        k[r] = sw ? v : u;
+                        k[rp] = sw ? u : v;
+                    }
+                } else {
+                    const uint32_t v = __shfl_xor_sync(0xffffffffu, k[r], stride);
+                    const bool lower = (lane & stride) == 0;
+                    k[r] = (lower == asc) ? min(k[r], v) : max(k[r], v);
+                }
+            }
         }
-        if (found < 0) { atomicOr(a.status, ST_NBR_OVERFLOW); found = 0; }
-        a.rev[(int64_t)s * a.n + i] = found;
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void sort_and_store(const uint32_t *key, int mm, int lane, uint32_t *out) {
+    uint32_t k[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int e = r * 32 + lane;
+        k[r] = e < mm ? key[e] : 0xFFFFFFFFu;
+    }
+    warp_bitonic<E>(k, lane);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < E; ++r) out[r * 32 + lane] = k[r];
+    __syncwarp();
+}
+
+__device__ __forceinline__ int wrap_cell(int x, int nc) { return x < 0 ? x + nc : (x >= nc ? x - nc : x); }
+
+constexpr int LB_WARPS = 4;
+constexpr int SORT_MAX = 256;
+
+__global__ void __launch_bounds__(LB_WARPS * 32) k_build_lists_warp(ListArgs a) {
+    if (a.flag && *a.flag == 0) return;
+    __shared__ uint32_t skey[LB_WARPS][SORT_MAX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t *key = skey[w];
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t i = (int64_t)blockIdx.x * LB_WARPS + w; i < a.n; i += (int64_t)gridDim.x * LB_WARPS) {
+        const double4 pi = a.pos[i];
+        const float4 pfi = a.posf[i];
+        const int cc = a.cell_of[i];
+        int ci[3] = {cc % a.g.nc[0], (cc / a.g.nc[0]) % a.g.nc[1], cc / (a.g.nc[0] * a.g.nc[1])};
+        int lo[3], hi[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (a.g.per[d] && a.g.nc[d] < 3) { lo[d] = 0; hi[d] = a.g.nc[d] - 1; }
+            else if (a.g.per[d]) { lo[d] = ci[d] - 1; hi[d] = ci[d] + 1; }
+            else { lo[d] = max(ci[d] - 1, 0); hi[d] = min(ci[d] + 1, a.g.nc[d] - 1); }
+        }
+        const uint32_t self = (uint32_t)a.orig[i];
+        int m = 0, nang = 0;
+        for (int z = lo[2]; z <= hi[2]; ++z)
+            for (int y = lo[1]; y <= hi[1]; ++y)
+                for (int x = lo[0]; x <= hi[0]; ++x) {
+                    const int wx = wrap_cell(x, a.g.nc[0]);
+                    const int wy = wrap_cell(y, a.g.nc[1]);
+                    const int wz = wrap_cell(z, a.g.nc[2]);
+                    const int c = (wz * a.g.nc[1] + wy) * a.g.nc[0] + wx;
+                    const int p0 = a.cell_start[c], p1 = a.cell_start[c + 1];
+                    for (int base = p0; base < p1; base += 32) {
+                        const int p = base + lane;
+                        bool in_r = false, in_a = false;
+                        uint32_t k = 0;
+                        if (p < p1) {
+                            k = a.ckey[p];
+                            if ((k & 0x3FFFFFFFu) != self) {
+                                const float4 pfj = a.cposf[p];
+                                float dx = pfj.x - pfi.x, dy = pfj.y - pfi.y, dz = pfj.z - pfi.z;
+                                minimg(a.bf, dx, dy, dz);
+                                const float d2f = dx * dx + dy * dy + dz * dz;
+                                if (d2f < a.cut_r2f_hi) {
+                                    if (d2f < a.cut_r2f_lo && (d2f < a.cut_a2f_lo || d2f >= a.cut_a2f_hi)) {
+                                        in_r = true;
+                                        in_a = d2f < a.cut_a2f_lo;
+                                    } else {   // near a cutoff: the exact FP64 test decides
+                                        const double4 pj = a.pos[a.cell_atoms[p]];
+                                        const double d2 = exact_d2(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z, a.bd, a.g.per);
+                                        in_r = d2 < a.cut_r2;
+                                        in_a = d2 < a.cut_a2;
+                                    }
+                                }
+                            }
+                        }
+                        const unsigned mr = __ballot_sync(0xffffffffu, in_r);
+                        const unsigned ma = __ballot_sync(0xffffffffu, in_a);
+                        if (in_r) {
+                            const int pos = m + __popc(mr & lt);
+                            // segment (angular? 0 : 2) + species of j in bits 30-31 above the caller index;
+                            // species is 0 or 1, so (seg << 30) fits with the caller index below 2^30
+                            const uint32_t sg = (in_a ? 0u : 2u) + (k >> 30);
+                            if (pos < SORT_MAX) key[pos] = (sg << 30) | (k & 0x3FFFFFFFu);
+                        }
+                        m += __popc(mr);
+                        nang += __popc(ma);
+                    }
+                }
+        const bool overflow = m > a.cap || nang > a.cap_ang;
+        const int mm = min(m, SORT_MAX);
+        __syncwarp();
+        if (mm <= 64) sort_and_store<2>(key, mm, lane, key);
+        else if (mm <= 128) sort_and_store<4>(key, mm, lane, key);
+        else sort_and_store<8>(key, mm, lane, key);
+        const int cnt = min(mm, a.cap);
+        int ends[4] = {0, 0, 0, 0};
+        for (int s0 = 0; s0 < cnt; s0 += 32) {
+            const int s = s0 + lane;
+            unsigned sg = 4u;
+            if (s < cnt) {
+                const uint32_t k = key[s];
+                sg = k >> 30;
+                a.nbr[(int64_t)s * a.n + i] = a.inv[k & 0x3FFFFFFFu];
+                a.nbr_orig[i * a.cap + s] = (int32_t)(k & 0x3FFFFFFFu);   // atom-major: one row per atom
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) ends[t] += __popc(__ballot_sync(0xffffffffu, sg <= (unsigned)t));
+        }
+        if (lane == 0) {
+            a.seg[i] = make_int4(ends[0], ends[1], ends[2], ends[3]);
+            if (overflow) atomicOr(a.status, ST_NBR_OVERFLOW);
+        }
+        __syncwarp();
+    }
+}
+
+// Warp per atom, lanes over slots: rev[s][i] = slot of i in the list of j = nbr[s][i].
+__global__ void __launch_bounds__(128) k_build_rev_warp(RevArgs a, const float4 *__restrict__ posf, float band_lo,
+                                                        float band_hi, BoxDev<float> bf) {
+    if (a.flag && *a.flag == 0) return;
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5); i < a.n; i += (int64_t)gridDim.x * 4) {
+        const int4 sg = a.seg[i];
+        const double4 pi = a.pos[i];
+        const float4 pfi = posf[i];
+        const int oi = a.orig[i];
+        const int ti = a.species[i];
+        for (int s = lane; s < sg.w; s += 32) {
+            const int j = a.nbr[(int64_t)s * a.n + i];
+            // angular membership of the pair, decided exactly as the list build decides it
+            const float4 pfj = posf[j];
+            float dx = pfi.x - pfj.x, dy = pfi.y - pfj.y, dz = pfi.z - pfj.z;
+            minimg(bf, dx, dy, dz);
+            const float d2f = dx * dx + dy * dy + dz * dz;
+            bool in_a;
+            if (d2f < band_lo) in_a = true;
+            else if (d2f >= band_hi) in_a = false;
+            else {
+                const double4 pj = a.pos[j];
+                in_a = exact_d2(pj.x, pj.y, pj.z, pi.x, pi.y, pi.z, a.bd, a.per) < a.cut_a2;
+            }
+            const int sgi = (in_a ? 0 : 2) + ti;
+            const int4 sj = a.seg[j];
+            const int e[4] = {sj.x, sj.y, sj.z, sj.w};
+            int lo = sgi == 0 ? 0 : e[sgi - 1], hi = e[sgi];
+            int found = -1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                const int om = a.nbr_orig[(int64_t)j * a.cap + mid];
+                if (om == oi) { found = mid; break; }
+                if (om < oi) lo = mid + 1; else hi = mid;
+            }
+            if (found < 0) { atomicOr(a.status, ST_NBR_OVERFLOW); found = 0; }
+            a.rev[(int64_t)s * a.n + i] = found;
+        }
     }
 }
 
 __global__ void k_finish(const double4 *__restrict__ pos, double4 *__restrict__ ref, int64_t n, int *count,
                          int *fill, int ncell, const int *flag, unsigned long long *builds) {
     if (flag && *flag == 0) return;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) ref[i] = pos[i];
-    if (i < ncell) { count[i] = 0; fill[i] = 0; }
-    if (i == 0) *builds += 1ULL;
+    const int64_t m = n > ncell ? n : ncell;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < n) ref[i] = pos[i];
+        if (i < ncell) { count[i] = 0; fill[i] = 0; }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *builds += 1ULL;
     // the flag itself is cleared by k_clear_flag, the last kernel that reads it
 }
 
@@ -263,12 +364,22 @@ void launch_rebuild(Sys &s, bool conditional) {
     }
     const int64_t n = s.n;
     const int T = 256;
-    k_bin<<<blocks(n, T), T, 0, s.stream>>>(s.pos, n, g, s.cells.count, s.cells.of, flag);
+    // grids are capped (grid-stride loops): when no rebuild is due every kernel returns at once
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto capped = [&](int64_t items, int per_block) {
+        const int64_t b = (items + per_block - 1) / per_block;
+        return (unsigned)(b < (int64_t)sms * 16 ? (b > 0 ? b : 1) : (int64_t)sms * 16);
+    };
+    k_bin<<<capped(n, T), T, 0, s.stream>>>(s.pos, n, g, s.cells.count, s.cells.of, flag);
     k_scan<<<1, 1024, 0, s.stream>>>(s.cells.count, s.cells.start, s.cells.ncell, flag);
-    k_scatter<<<blocks(n, T), T, 0, s.stream>>>(s.cells.of, n, s.cells.start, s.cells.fill, s.cells.atoms, flag);
+    k_scatter<<<capped(n, T), T, 0, s.stream>>>(s.cells.of, n, s.cells.start, s.cells.fill, s.cells.atoms, s.posf,
+                                                s.species, s.orig, s.cells.posf, s.cells.key, flag);
     ListArgs la;
     la.pos = s.pos; la.posf = s.posf; la.species = s.species; la.orig = s.orig; la.inv = s.inv;
     la.cell_start = s.cells.start; la.cell_atoms = s.cells.atoms; la.cell_of = s.cells.of;
+    la.cposf = s.cells.posf; la.ckey = s.cells.key; la.nbr_orig = s.nbr_orig;
     la.n = n; la.cap = s.cap; la.cap_ang = s.cap_ang;
     la.cut_r2 = s.cut_r2; la.cut_a2 = s.cut_a2;
     // FP32 separations of positions below 1e4 A carry an absolute d2 error far
@@ -277,15 +388,15 @@ void launch_rebuild(Sys &s, bool conditional) {
     la.cut_a2f_lo = (float)(s.cut_a2 - 0.05); la.cut_a2f_hi = (float)(s.cut_a2 + 0.05);
     la.bd = s.boxd; la.bf = s.boxf; la.g = g;
     la.nbr = s.nbr; la.seg = s.seg; la.status = s.status; la.flag = flag;
-    k_build_lists<<<blocks(n, 128), 128, 0, s.stream>>>(la);
+    k_build_lists_warp<<<capped(n, LB_WARPS), LB_WARPS * 32, 0, s.stream>>>(la);
     RevArgs ra;
-    ra.pos = s.pos; ra.species = s.species; ra.orig = s.orig; ra.nbr = s.nbr; ra.seg = s.seg; ra.n = n;
-    ra.cut_a2 = s.cut_a2; ra.bd = s.boxd;
+    ra.pos = s.pos; ra.species = s.species; ra.orig = s.orig; ra.nbr = s.nbr; ra.nbr_orig = s.nbr_orig; ra.seg = s.seg;
+    ra.n = n; ra.cap = s.cap; ra.cut_a2 = s.cut_a2; ra.bd = s.boxd;
     for (int a = 0; a < 3; ++a) ra.per[a] = s.per[a];
     ra.rev = s.rev; ra.status = s.status; ra.flag = flag;
-    k_build_rev<<<blocks(n, 128), 128, 0, s.stream>>>(ra);
+    k_build_rev_warp<<<capped(n, 4), 128, 0, s.stream>>>(ra, s.posf, la.cut_a2f_lo, la.cut_a2f_hi, s.boxf);
     const int64_t m = n > s.cells.ncell ? n : s.cells.ncell;
-    k_finish<<<blocks(m, T), T, 0, s.stream>>>(s.pos, s.posref, n, s.cells.count, s.cells.fill, s.cells.ncell,
+    k_finish<<<capped(m, T), T, 0, s.stream>>>(s.pos, s.posref, n, s.cells.count, s.cells.fill, s.cells.ncell,
                                                flag, s.d_builds);
     if (conditional) k_clear_flag<<<1, 1, 0, s.stream>>>(s.rebuild);
 }

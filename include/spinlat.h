@@ -155,8 +155,8 @@ int sl_get_info(const sl_system *sys, int64_t *n_atoms, int32_t *precision, int6
 /* Kernels (or kernel groups) timed by sl_step_profiled, in step order. */
 #define SL_K_FIRST_HALF 0    /* kicks, drifts, Langevin, spin predictor, rebuild test     */
 #define SL_K_REBUILD 1       /* binning + lists + reverse slots (early exit when not due) */
-#define SL_K_COMPACT 2       /* in-cutoff compaction of the candidate lists               */
-#define SL_K_RAD_FWD 3       /* radial and pairwise-magnetic channels                     */
+#define SL_K_COMPACT 2       /* empty: the compaction runs inside the radial kernel       */
+#define SL_K_RAD_FWD 3       /* in-cutoff compaction + radial and pairwise-magnetic sums  */
 #define SL_K_ANG_FWD 4       /* angular and spin-angular channels                         */
 #define SL_K_NETWORK 5       /* per-atom network and its input gradient                   */
 #define SL_K_BACKWARD 6      /* backward to pair records, per-atom sums                   */

@@ -3,12 +3,12 @@
 // Same mathematics as the descriptor of arXiv 2606.14073 (Sections 5.1.1-5.1.2, 5.2.3-5.2.4)
 // described in sl_nep.cu; this file maps it onto the GPU differently:
 //
-//   k_compact  one thread per atom: compacts the candidate list (which carries a
-//              skin) into the pairs inside the cutoffs: angular rows (r < rc_ang) and
-//              radial-only rows (rc_ang <= r < rc_rad), each grouped by neighbour species.
-//   k_rad_fwd  one thread per atom: accumulates the radial and pairwise-magnetic
-//              basis sums over those rows and contracts them with the coefficients
-//              once per neighbour species (q^R, q^EX, q^DMI, q^ANI, q^SIA, q^O).
+//   k_crad     one thread per atom, one pass over the candidate list (which carries a
+//              skin): compacts the pairs inside the cutoffs into angular rows
+//              (r < rc_ang) and radial-only rows (rc_ang <= r < rc_rad), each grouped by
+//              neighbour species, and accumulates the radial and pairwise-magnetic basis
+//              sums over them, contracted with the coefficients once per neighbour
+//              species (q^R, q^EX, q^DMI, q^ANI, q^SIA, q^O).
 //   k_ang_fwd  four lanes per atom.  Each lane stages one angular pair (carrier, g_n,
 //              spin weight, the 24 solid harmonics) in shared memory; then every lane
 //              accumulates B_nlm, BS_nlm for its 6 harmonics over the staged pairs.
@@ -76,37 +76,67 @@ __device__ __forceinline__ R kappa_of_lm(int lm) {
     }
 }
 
-// ------------------------------------------------------------------ k_rad_fwd
+// ------------------------------------------------------------------ k_crad
+// One thread per atom, one pass over the candidate list (which carries a skin):
+//  * compaction of the pairs inside the cutoffs into angular rows (r < rc_ang) and
+//    radial-only rows (rc_ang <= r < rc_rad), each grouped by neighbour species in
+//    candidate order (species 0 from candidate segments 0 and 2, then species 1 from
+//    1 and 3), for the angular and backward kernels and the gather;
+//  * the radial and pairwise-magnetic basis sums over the same pairs, contracted with
+//    the coefficients once per neighbour species (q^R, q^EX, q^DMI, q^ANI, q^SIA), and q^O.
+// Candidates go in batches of CB: the batch's list entries, reverse slots and
+// neighbour coordinates are all requested before any of them is used.
+constexpr int CB = 4;
+
 template <typename R, int TI, int TJ>
-__device__ __forceinline__ void rad_sums(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, const v4<R> &pi,
-                                         const v4<R> &si, int r0, int r1, int r2, int r3, R qr[NCH], R qx[4][NCH]) {
+__device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, const v4<R> &pi,
+                                             const v4<R> &si, int lo0, int hi0, int lo1, int hi1, int &na, int &nr) {
     R b0[NK], b1[NK], b2[NK], b3[NK], b4[NK];
 #pragma unroll
     for (int k = 0; k < NK; ++k) { b0[k] = b1[k] = b2[k] = b3[k] = b4[k] = R(0); }
     const int64_t N = a.n;
-    const int len0 = r1 - r0, len = len0 + (r3 - r2);
-    const int32_t *__restrict__ clj = a.clj;
+    const int len0 = hi0 - lo0, len = len0 + (hi1 - lo1);
+    const int32_t *__restrict__ nbr = a.nbr;
+    const int32_t *__restrict__ rev = a.rev;
     const v4<R> *__restrict__ pos = a.pos;
     const v4<R> *__restrict__ spin = a.spin;
-    // rows r0..r1 then r2..r3, with the next pair's loads issued before this pair's arithmetic
-    v4<R> pj, sj;
-    if (len > 0) {
-        const int j = clj[(int64_t)r0 * N + i];
-        pj = pos[j];
-        sj = spin[j];
-    }
-    for (int t = 0; t < len; ++t) {
-        const v4<R> cp = pj, cs = sj;
-        if (t + 1 < len) {
-            const int rn = t + 1 < len0 ? r0 + t + 1 : r2 + (t + 1 - len0);
-            const int j = clj[(int64_t)rn * N + i];
-            pj = pos[j];
-            sj = spin[j];
+#pragma unroll 1
+    for (int t0 = 0; t0 < len; t0 += CB) {
+        int sl[CB], jj[CB], tt[CB];
+        v4<R> pp[CB], ss[CB];
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+            const int t = t0 + u;
+            sl[u] = t < len0 ? lo0 + t : lo1 + (t - len0);
+            jj[u] = t < len ? nbr[(int64_t)sl[u] * N + i] : -1;
+            tt[u] = t < len ? rev[(int64_t)sl[u] * N + i] : 0;
         }
-        {
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+            const int j = jj[u] >= 0 ? jj[u] : (int)i;
+            pp[u] = pos[j];
+            ss[u] = spin[j];
+        }
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+            if (jj[u] < 0) continue;
             R dx, dy, dz;
-            sep(a.box, pi, cp, dx, dy, dz);
+            sep(a.box, pi, pp[u], dx, dy, dz);
             const R d2 = dx * dx + dy * dy + dz * dz;
+            if (!(d2 < P.rc_r2)) continue;
+            int row;
+            if (d2 < P.rc_a2) {
+                if (na >= a.cap_ang) {   // only after a list overflow; keeps every row in bounds
+                    atomicOr(a.status, ST_NBR_OVERFLOW);
+                    continue;
+                }
+                row = na++;
+            } else {
+                row = a.cap_ang + nr++;
+            }
+            a.clj[(int64_t)row * N + i] = jj[u];
+            a.cls[(int64_t)row * N + i] = (uint16_t)(sl[u] | (tt[u] << 8));
+            const v4<R> cs = ss[u];
             const R ir = rsqrt_(d2), r = d2 * ir;
             const R ux = dx * ir, uy = dy * ir, uz = dz * ir;
             R f[NK];
@@ -127,112 +157,42 @@ __device__ __forceinline__ void rad_sums(const NepDev<R> &P, const Eval2Args<R> 
             }
         }
     }
+    // contraction of this species' sums; the second species adds onto the first's
+    // values in q (the same thread wrote them), so no accumulator lives across the loops
+    constexpr int GQ[5] = {Q_R, Q_EX, Q_DMI, Q_ANI, Q_SIA};
+    constexpr int GG[5] = {G_R, G_EX, G_DMI, G_ANI, G_SIA};
 #pragma unroll
-    for (int n = 0; n < NCH; ++n) {
+    for (int g = 0; g < 5; ++g) {
+        const R *b = g == 0 ? b0 : g == 1 ? b1 : g == 2 ? b2 : g == 3 ? b3 : b4;
 #pragma unroll
-        for (int k = 0; k < NK; ++k) {
-            qr[n] += P.c[TI][TJ][G_R][n][k] * b0[k];
-            qx[0][n] += P.c[TI][TJ][G_EX][n][k] * b1[k];
-            qx[1][n] += P.c[TI][TJ][G_DMI][n][k] * b2[k];
-            qx[2][n] += P.c[TI][TJ][G_ANI][n][k] * b3[k];
-            qx[3][n] += P.c[TI][TJ][G_SIA][n][k] * b4[k];
+        for (int n = 0; n < NCH; ++n) {
+            R v = TJ == 0 ? R(0) : a.q[(GQ[g] + n) * N + i];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) v += P.c[TI][TJ][GG[g]][n][k] * b[k];
+            a.q[(GQ[g] + n) * N + i] = v;
         }
     }
-}
-
-// In-cutoff compaction of atom i's candidate list: angular rows (r < rc_ang) then
-// radial-only rows, each grouped by neighbour species (species 0 from candidate
-// segments 0 and 2, then species 1 from 1 and 3).  Candidates are loaded eight at
-// a time to keep several gathers in flight per thread.
-template <typename R>
-__device__ __forceinline__ void compact_atom(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i) {
-    const int64_t N = a.n;
-    const v4<R> pi = a.pos[i];
-    const int4 sg = a.seg[i];
-    const int32_t *__restrict__ nbr = a.nbr;
-    const int32_t *__restrict__ rev = a.rev;
-    const v4<R> *__restrict__ pos = a.pos;
-    constexpr int BATCH = 8;
-    int na = 0, nr = 0, na0 = 0, nr0 = 0;
-#pragma unroll 1
-    for (int tj = 0; tj < 2; ++tj) {
-#pragma unroll 1
-        for (int part = 0; part < 2; ++part) {
-            const int lo = part == 0 ? (tj == 0 ? 0 : sg.x) : (tj == 0 ? sg.y : sg.z);
-            const int hi = part == 0 ? (tj == 0 ? sg.x : sg.y) : (tj == 0 ? sg.z : sg.w);
-            for (int s0 = lo; s0 < hi; s0 += BATCH) {
-                int jj[BATCH];
-                v4<R> pp[BATCH];
-#pragma unroll
-                for (int u = 0; u < BATCH; ++u) jj[u] = s0 + u < hi ? nbr[(int64_t)(s0 + u) * N + i] : -1;
-#pragma unroll
-                for (int u = 0; u < BATCH; ++u) pp[u] = pos[jj[u] >= 0 ? jj[u] : i];
-#pragma unroll
-                for (int u = 0; u < BATCH; ++u) {
-                    if (jj[u] < 0) continue;
-                    R dx, dy, dz;
-                    sep(a.box, pi, pp[u], dx, dy, dz);
-                    const R d2 = dx * dx + dy * dy + dz * dz;
-                    if (d2 < P.rc_r2) {
-                        int row;
-                        if (d2 < P.rc_a2) {
-                            if (na >= a.cap_ang) {   // only after a list overflow; keeps every row in bounds
-                                atomicOr(a.status, ST_NBR_OVERFLOW);
-                                continue;
-                            }
-                            row = na++;
-                        } else {
-                            row = a.cap_ang + nr++;
-                        }
-                        const int t = rev[(int64_t)(s0 + u) * N + i];
-                        a.clj[(int64_t)row * N + i] = jj[u];
-                        a.cls[(int64_t)row * N + i] = (uint16_t)((s0 + u) | (t << 8));
-                    }
-                }
-            }
-        }
-        if (tj == 0) { na0 = na; nr0 = nr; }
-    }
-    a.cnt[i] = make_int4(na0, na, nr0, nr);
-}
-
-template <typename R>
-__global__ void __launch_bounds__(128) k_compact(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    compact_atom<R>(P, a, i);
 }
 
 template <typename R, int TI>
-__device__ __forceinline__ void rad_fwd_atom(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i) {
+__device__ __forceinline__ void crad_atom(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i) {
     const int64_t N = a.n;
     const v4<R> pi = a.pos[i], si = a.spin[i];
-    const int4 c = a.cnt[i];
-    const int na0 = c.x, na = c.y, nr0 = c.z, nr = c.w;
-    // radial and pairwise-magnetic sums over the in-cutoff pairs
-    R qr[NCH], qx[4][NCH];
-#pragma unroll
-    for (int n = 0; n < NCH; ++n) { qr[n] = R(0); qx[0][n] = qx[1][n] = qx[2][n] = qx[3][n] = R(0); }
-    const int ca = a.cap_ang;
-    rad_sums<R, TI, 0>(P, a, i, pi, si, 0, na0, ca, ca + nr0, qr, qx);
-    rad_sums<R, TI, 1>(P, a, i, pi, si, na0, na, ca + nr0, ca + nr, qr, qx);
-#pragma unroll
-    for (int n = 0; n < NCH; ++n) {
-        a.q[(Q_R + n) * N + i] = qr[n];
-        a.q[(Q_EX + n) * N + i] = qx[0][n];
-        a.q[(Q_DMI + n) * N + i] = qx[1][n];
-        a.q[(Q_ANI + n) * N + i] = qx[2][n];
-        a.q[(Q_SIA + n) * N + i] = qx[3][n];
-    }
+    const int4 sg = a.seg[i];
+    int na = 0, nr = 0;
+    crad_species<R, TI, 0>(P, a, i, pi, si, 0, sg.x, sg.y, sg.z, na, nr);
+    const int na0 = na, nr0 = nr;
+    crad_species<R, TI, 1>(P, a, i, pi, si, sg.x, sg.y, sg.z, sg.w, na, nr);
+    a.cnt[i] = make_int4(na0, na, nr0, nr);
     a.q[Q_O * N + i] = si.x * si.x + si.y * si.y + si.z * si.z;
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128) k_rad_fwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+__global__ void __launch_bounds__(128, 4) k_crad(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    if (i < a.n_fe) rad_fwd_atom<R, 0>(P, a, i);
-    else rad_fwd_atom<R, 1>(P, a, i);
+    if (i < a.n_fe) crad_atom<R, 0>(P, a, i);
+    else crad_atom<R, 1>(P, a, i);
 }
 
 // ------------------------------------------------------------------ k_ang_fwd
@@ -704,9 +664,9 @@ static void eval2_impl(Sys &s, const NepDev<R> &P, bool want_virial, cudaEvent_t
     const int qb = quad_block<R>();
     const unsigned nq = (unsigned)((s.n + qb / 4 - 1) / (qb / 4));
     if (ev) cudaEventRecord(ev[0], s.stream);
-    k_compact<R><<<nb, 128, 0, s.stream>>>(P, a);
+    // compaction and radial channels in one kernel: the compaction group is empty
     if (ev) cudaEventRecord(ev[1], s.stream);
-    k_rad_fwd<R><<<nb, 128, 0, s.stream>>>(P, a);
+    k_crad<R><<<nb, 128, 0, s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[2], s.stream);
     k_ang_fwd<R><<<nq, qb, fwd_smem<R>(), s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[3], s.stream);

@@ -111,8 +111,9 @@ void launch_eval(Sys &s, bool want_virial, cudaEvent_t *ev = nullptr);
 void eval2_init();
 void launch_network(Sys &s, cudaEvent_t *ev);   // sl_nep.cu
 void launch_network_tc(Sys &s);                  // sl_mlp_tc.cu (mixed precision)
-// first half, rebuild group (7), compaction, radial and angular forward, network, backward, second half
-constexpr int KERNELS_PER_STEP = 1 + 7 + 3 + 1 + 1 + 1;
+// first half, rebuild group (7), compaction with radial forward, angular forward, network, backward,
+// second half
+constexpr int KERNELS_PER_STEP = 1 + 7 + 2 + 1 + 1 + 1;
 // sl_integrate.cu
 void launch_first_half(Sys &s);
 void launch_second_half(Sys &s);

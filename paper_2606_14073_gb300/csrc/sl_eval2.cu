@@ -100,6 +100,14 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
     const int32_t *__restrict__ rev = a.rev;
     const v4<R> *__restrict__ pos = a.pos;
     const v4<R> *__restrict__ spin = a.spin;
+    // list entries and reverse slots of the next batch are loaded while this batch is computed
+    int jn[CB], tn[CB];
+#pragma unroll
+    for (int u = 0; u < CB; ++u) {
+        const int sl = u < len0 ? lo0 + u : lo1 + (u - len0);
+        jn[u] = u < len ? nbr[(int64_t)sl * N + i] : -1;
+        tn[u] = u < len ? rev[(int64_t)sl * N + i] : 0;
+    }
 #pragma unroll 1
     for (int t0 = 0; t0 < len; t0 += CB) {
         int sl[CB], jj[CB], tt[CB];
@@ -108,14 +116,21 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
         for (int u = 0; u < CB; ++u) {
             const int t = t0 + u;
             sl[u] = t < len0 ? lo0 + t : lo1 + (t - len0);
-            jj[u] = t < len ? nbr[(int64_t)sl[u] * N + i] : -1;
-            tt[u] = t < len ? rev[(int64_t)sl[u] * N + i] : 0;
+            jj[u] = jn[u];
+            tt[u] = tn[u];
         }
 #pragma unroll
         for (int u = 0; u < CB; ++u) {
             const int j = jj[u] >= 0 ? jj[u] : (int)i;
             pp[u] = pos[j];
             ss[u] = spin[j];
+        }
+#pragma unroll
+        for (int u = 0; u < CB; ++u) {
+            const int t = t0 + CB + u;
+            const int sn = t < len0 ? lo0 + t : lo1 + (t - len0);
+            jn[u] = t < len ? nbr[(int64_t)sn * N + i] : -1;
+            tn[u] = t < len ? rev[(int64_t)sn * N + i] : 0;
         }
 #pragma unroll
         for (int u = 0; u < CB; ++u) {
@@ -188,7 +203,7 @@ __device__ __forceinline__ void crad_atom(const NepDev<R> &P, const Eval2Args<R>
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128, 4) k_crad(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_crad(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     if (i < a.n_fe) crad_atom<R, 0>(P, a, i);
@@ -257,8 +272,10 @@ __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<
 #pragma unroll
         for (int n = 0; n < NCH; ++n) { B[m][n] = R(0); BS[m][n] = R(0); }
     const int nmax = __reduce_max_sync(0xffffffffu, na);
-    // the lane's pair of the next round is loaded one round ahead
+    // the lane's list entry two rounds ahead and its coordinates one round ahead are in flight
     v4<R> pjn, sjn;
+    int jn2 = 0;
+    if (ql + 4 < na) jn2 = a.clj[(int64_t)(ql + 4) * N + i];
     if (ql < na) {
         const int j = a.clj[(int64_t)ql * N + i];
         pjn = a.pos[j];
@@ -268,10 +285,10 @@ __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<
         const int p = base + ql;
         const v4<R> pj = pjn, sj = sjn;
         if (p + 4 < na) {
-            const int j = a.clj[(int64_t)(p + 4) * N + i];
-            pjn = a.pos[j];
-            sjn = a.spin[j];
+            pjn = a.pos[jn2];
+            sjn = a.spin[jn2];
         }
+        if (p + 8 < na) jn2 = a.clj[(int64_t)(p + 8) * N + i];
         if (p < na) {
             R *st = stage + ql * FSTAGE;
             if (ti == 0) {
@@ -504,28 +521,40 @@ __device__ __forceinline__ void bwd_pair(const NepDev<R> &P, const Eval2Args<R> 
     a.pd[(int64_t)t * a.n + j] = rec;
 }
 
-// rows lo, lo+4, ... of one range for lane ql, with the next row's loads in flight
+// rows lo, lo+4, ... of one range for lane ql.  Two-level prefetch: the list entry of the
+// row two steps ahead and the coordinates of the next row are in flight while a pair is
+// computed, so no load waits on a load issued in the same step.
 template <typename R, bool ANG>
 __device__ __forceinline__ void bwd_rows(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, int ti, int lo, int hi,
                                          int split, const v4<R> &pi, const v4<R> &si, const R *sm,
                                          BwdAcc2<R> &acc) {
     const int64_t N = a.n;
-    int jn = 0, tn = 0;
-    v4<R> pn, sn;
+    int j1 = 0, t1 = 0, j2 = 0, t2 = 0;
+    v4<R> p1, s1;
     if (lo < hi) {
-        jn = a.clj[(int64_t)lo * N + i];
-        tn = a.cls[(int64_t)lo * N + i] >> 8;
-        pn = a.pos[jn];
-        sn = a.spin[jn];
+        j1 = a.clj[(int64_t)lo * N + i];
+        t1 = a.cls[(int64_t)lo * N + i] >> 8;
+    }
+    if (lo + 4 < hi) {
+        j2 = a.clj[(int64_t)(lo + 4) * N + i];
+        t2 = a.cls[(int64_t)(lo + 4) * N + i] >> 8;
+    }
+    if (lo < hi) {
+        p1 = a.pos[j1];
+        s1 = a.spin[j1];
     }
     for (int row = lo; row < hi; row += 4) {
-        const int j = jn, t = tn;
-        const v4<R> pj = pn, sj = sn;
+        const int j = j1, t = t1;
+        const v4<R> pj = p1, sj = s1;
         if (row + 4 < hi) {
-            jn = a.clj[(int64_t)(row + 4) * N + i];
-            tn = a.cls[(int64_t)(row + 4) * N + i] >> 8;
-            pn = a.pos[jn];
-            sn = a.spin[jn];
+            j1 = j2;
+            t1 = t2;
+            p1 = a.pos[j1];
+            s1 = a.spin[j1];
+        }
+        if (row + 8 < hi) {
+            j2 = a.clj[(int64_t)(row + 8) * N + i];
+            t2 = a.cls[(int64_t)(row + 8) * N + i] >> 8;
         }
         bwd_pair<R, ANG>(P, a, ti, row < split ? 0 : 1, pi, si, pj, sj, j, t, sm, acc);
     }

@@ -104,6 +104,22 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- helpers
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """Largest value of x over all ranks (x itself when not distributed)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(atoms_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Atom-steps per second of the whole job: every rank steps its own replica of
+    atoms_per_rank atoms, and the job takes as long as its slowest rank."""
+    return atoms_per_rank * steps * world / (ms_max * 1e-3)
+
+
 def neighbour_counts(wl, sample=20000, seed=0):
     """Mean in-cutoff neighbour counts (6 A, 4 A) on a sample of atoms."""
     from scipy.spatial import cKDTree
@@ -208,14 +224,10 @@ def run_e2e(args, sysm, wl, world, barrier, dist, torch):
     sysm.step(args.steps, DT, TEMP, FIELD)
     out = sysm.get_state()
     t1 = time.perf_counter()
-    e2e_s = t1 - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(t1 - t0, dist, "cuda")
     h2d = sum(host[k].nbytes for k in host)
     d2h = sum(out[k].nbytes for k in ("positions", "velocities", "spins", "forces", "fields", "ref_positions"))
-    e2e = {"value": wl.n * args.steps * world / e2e_s, "unit": UNIT,
+    e2e = {"value": whole_job_rate(wl.n, args.steps, world, e2e_s * 1e3), "unit": UNIT,
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "path": "sl_set_state(host) + sl_step(K) + sl_get_state(host), wall clock"}
 
@@ -236,6 +248,200 @@ def run_serving(args, params, replica_offset=0):
             "latency_p50_s": out["latency_p50_s"], "latency_p99_s": out["latency_p99_s"],
             "makespan_s": out["makespan_s"], "memory_waits": out["memory_waits"],
             "recipe": "cells U{12..20}, T U(50,320) K, B_z U(0,0.5) T, steps U{100..400}, mixed precision"}
+
+
+def _common_line(args, value, ms_total, steps, workload, config, clk, launches, extra):
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": ms_total / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 descriptor/backward, f32 network, f64 state/integration",
+            "data": "synthetic (seeded FeGe B20, random-init NEP of the paper's shape)",
+            "config": dict(workload=workload, **config), "clocks": clk, "gpu_launches": launches}
+    line.update(extra)
+    return line
+
+
+def sample_neighbour_stats(pos, box, periodic, sample=20000, seed=0):
+    """Mean neighbours inside 6 A and 4 A on a sample of atoms (periodic axes wrapped)."""
+    from scipy.spatial import cKDTree
+    p = np.array(pos, dtype=np.float64)
+    bs = np.array(box, dtype=np.float64)
+    per = np.asarray(periodic, dtype=bool)
+    for a in range(3):
+        if per[a]:
+            p[:, a] = np.mod(p[:, a], bs[a])
+    # non-periodic axes: a box length larger than any separation disables wrapping there
+    span = np.where(per, bs, (p.max(axis=0) - p.min(axis=0)) + 100.0)
+    p = p - np.where(per, 0.0, p.min(axis=0) - 1.0)
+    tree = cKDTree(p, boxsize=span)
+    idx = np.random.default_rng(seed).choice(len(p), min(sample, len(p)), replace=False)
+    nr = tree.query_ball_point(p[idx], 6.0, return_length=True).mean() - 1.0
+    na = tree.query_ball_point(p[idx], 4.0, return_length=True).mean() - 1.0
+    return float(nr), float(na)
+
+
+def run_slab(args):
+    """Slab of 160 x 160 x 16 B20 cells (3,276,800 atoms), periodic in x and y, free z
+    surfaces, helix along x, B = 0.2 T along z, temperature ramped linearly from 0 to
+    280 K over --ramp-steps steps (piecewise constant per captured graph of
+    --graph-steps steps).  The timed region is --steps steps from the start of the ramp."""
+    import torch
+    from paper_2606_14073_gb300 import nep_params, spinlat as S, workloads as W
+    torch.cuda.set_device(0)
+    params = nep_params.load()
+    wl = W.fege_slab_helix()
+    B = tuple(float(x) for x in wl.B)
+    stream = torch.cuda.Stream()
+    sysm = S.system_from_workload(wl, params, precision=S.SL_PREC_MIXED, stream=stream.cuda_stream,
+                                  steps_per_graph=args.graph_steps)
+    nr0, na0 = sample_neighbour_stats(wl.positions, wl.box, wl.periodic)
+    T_end, ramp = 280.0, float(args.ramp_steps)
+    chunk = args.graph_steps
+
+    def temp(step):
+        return T_end * min(step, ramp) / ramp
+
+    sysm.step(args.warmup, DT, 0.0, B)        # warm-up (graph capture) before the ramp
+    info0 = sysm.info()
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    windows = []
+    w0 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    w0.record(stream)
+    done, win = 0, 2000
+    while done < args.steps:
+        k = min(chunk, args.steps - done)
+        sysm.step(k, DT, temp(done), B)
+        done += k
+        if done % win == 0 or done == args.steps:
+            w1 = torch.cuda.Event(enable_timing=True)
+            w1.record(stream)
+            windows.append((done, w0, w1))
+            w0 = w1
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    info1 = sysm.info()
+    st = sysm.get_state()
+    nr1, na1 = sample_neighbour_stats(st["positions"], wl.box, wl.periodic)
+    z = st["positions"][:, 2]
+    z_lo, z_hi = float(wl.positions[:, 2].min()), float(wl.positions[:, 2].max())
+    left = int(((z < z_lo - 5.0) | (z > z_hi + 5.0)).sum())
+    win_rates = [{"end_step": d, "T_K": temp(d), "atom_steps_per_s": wl.n * win / (a.elapsed_time(b) * 1e-3)}
+                 for d, a, b in windows if d % win == 0]
+    sysm.destroy()
+    line = _common_line(args, wl.n * args.steps / (ms * 1e-3), ms, args.steps, wl.name,
+                        {"atoms": wl.n, "precision": "mixed", "dt_fs": DT, "T_K": f"0 -> 280 over {args.ramp_steps} steps",
+                         "B_T": list(B), "periodic": [1, 1, 0], "helix_period_A": float(wl.box[0] / round(wl.box[0] / 700.0)),
+                         "steps_per_graph": chunk, "l2": "inputs larger than L2 (~37 GB working set)",
+                         "parallelism": "replicas x1"},
+                        clk, info1["n_launches"] - info0["n_launches"],
+                        {"mode": "slab", "neighbour_builds": info1["n_builds"] - info0["n_builds"],
+                         "windows_2000_steps": win_rates,
+                         "drift": {"mean_neighbours_6A": [nr0, nr1], "mean_neighbours_4A": [na0, na1],
+                                   "atoms_beyond_surfaces_5A": left}})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_replicas(args):
+    """64 replicas of uneven size (atoms log-uniform in [4096, 262144], cells per side
+    clamp(round((N/8)^(1/3)), 8, 32)), T ~ U(100, 300) K, B_z ~ U(0, 0.5) T, --steps steps
+    each in one batched call; mixed timed, FP64 timed over --fp64-steps, and the mixed
+    force/field error against FP64 on every replica's initial state."""
+    import torch
+    from paper_2606_14073_gb300 import nep_params, spinlat as S, workloads as W
+    torch.cuda.set_device(0)
+    params = nep_params.load()
+    cells, Ts, Bz = W.replica_sizes(64)
+    wls = [W.fege_cube(int(c), T=float(t), spin_mode="canted", seed=W.STRUCTURE_SEED0 + 4 + 1000 * (k + 1),
+                       n_steps=args.steps, name=f"replica{k}", replica=k) for k, (c, t) in enumerate(zip(cells, Ts))]
+    Bs = [(0.0, 0.0, float(b)) for b in Bz]
+    atoms = int(sum(w.n for w in wls))
+    # error of the mixed form against FP64, replica by replica on the initial states
+    se_f = se_h = 0.0
+    for k, w in enumerate(wls):
+        a = S.system_from_workload(w, params, precision=S.SL_PREC_MIXED, replica=k)
+        b = S.system_from_workload(w, params, precision=S.SL_PREC_FP64, replica=k)
+        ra, rb = a.energy_forces_fields(want_virial=False), b.energy_forces_fields(want_virial=False)
+        se_f += float(((ra["F"] - rb["F"]) ** 2).sum())
+        se_h += float(((ra["H"] - rb["H"]) ** 2).sum())
+        a.destroy()
+        b.destroy()
+    err = {"force_rmse_eV_per_A": (se_f / (3 * atoms)) ** 0.5, "field_rmse_eV": (se_h / (3 * atoms)) ** 0.5}
+
+    def timed(prec, steps):
+        syss = [S.system_from_workload(w, params, precision=prec, replica=k, steps_per_graph=args.graph_steps)
+                for k, w in enumerate(wls)]
+        bt = S.Batch(syss)
+        bt.step(args.warmup, DT, Ts, Bs)
+        l0 = sum(s.info()["n_launches"] for s in syss)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        t0 = time.perf_counter()
+        bt.step(steps, DT, Ts, Bs)     # returns after every replica's stream is done
+        secs = time.perf_counter() - t0
+        clk = clocks.stop()
+        launches = sum(s.info()["n_launches"] for s in syss) - l0
+        bt.destroy()
+        for s in syss:
+            s.destroy()
+        return atoms * steps / secs, secs, clk, launches
+
+    v64, s64, _, _ = timed(S.SL_PREC_FP64, args.fp64_steps)
+    value, secs, clk, launches = timed(S.SL_PREC_MIXED, args.steps)
+    line = _common_line(args, value, secs * 1e3, args.steps, "fege_b20_64_replicas_4096_262144",
+                        {"atoms": atoms, "replicas": 64, "precision": "mixed", "dt_fs": DT,
+                         "T_K": "U(100,300) per replica", "B_T": "z, U(0,0.5) per replica",
+                         "steps_per_graph": args.graph_steps, "l2": "inputs larger than L2 (~45 GB working set)",
+                         "parallelism": "replicas x1 GPU, one batched call"},
+                        clk, launches,
+                        {"mode": "replicas", "timing": "wall clock around one sl_batch_step (host-synchronous)",
+                         "fp64": {"value": v64, "unit": UNIT, "steps": args.fp64_steps},
+                         "mixed_error_vs_fp64": err,
+                         "replica_atoms": [int(w.n) for w in wls]})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve_sweep(args):
+    """Serving: Poisson arrivals at 0.25, 0.5, 1, 2 and 4 x the saturation request rate
+    (measured first from a burst of the same requests).  Requests: cells per side
+    U{12..40}, T U[50,320] K, B_z U[0,0.5] T, steps U{200..2000}; --serve-requests each."""
+    import torch
+    from paper_2606_14073_gb300 import nep_params
+    from paper_2606_14073_gb300.serving import GpuBackend, Server, poisson_requests
+    torch.cuda.set_device(0)
+    params = nep_params.load()
+    be = GpuBackend(params)
+    burst = poisson_requests(args.serve_requests, 0.0)
+    out = Server(be, max_active=32, chunk=50).run(burst)
+    work = np.mean([8 * r.cells ** 3 * r.n_steps for r in burst])
+    sat_rate = out["throughput_atom_steps_per_s"] / work
+    rows = [{"rate_multiple": "burst", "arrival_rate_per_s": None,
+             **{k: out[k] for k in ("throughput_atom_steps_per_s", "latency_p50_s", "latency_p99_s", "makespan_s",
+                                    "memory_waits", "requests")}}]
+    for m in (0.25, 0.5, 1.0, 2.0, 4.0):
+        reqs = poisson_requests(args.serve_requests, m * sat_rate, seed=20260105 + int(100 * m))
+        o = Server(be, max_active=32, chunk=50).run(reqs)
+        rows.append({"rate_multiple": m, "arrival_rate_per_s": m * sat_rate,
+                     **{k: o[k] for k in ("throughput_atom_steps_per_s", "latency_p50_s", "latency_p99_s",
+                                          "makespan_s", "memory_waits", "requests")}})
+    peak = max(r["throughput_atom_steps_per_s"] for r in rows)
+    line = _common_line(args, peak, 0.0, 1, "fege_serving_sweep",
+                        {"requests_per_rate": args.serve_requests, "precision": "mixed",
+                         "recipe": "cells U{12..40}, T U[50,320] K, B_z U[0,0.5] T, steps U{200..2000}",
+                         "l2": "inputs larger than L2", "parallelism": "replicas x1"},
+                        None, None,
+                        {"mode": "serve-sweep", "saturation_rate_per_s": sat_rate,
+                         "mean_atom_steps_per_request": work, "rates": rows})
+    line["ms_per_step"] = None
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_ours(args):
@@ -306,12 +512,8 @@ def run_ours(args):
     info1 = sysm.info()
     launches = info1["n_launches"] - launches0
     builds_timed = info1["n_builds"] - info0["n_builds"]
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = wl.n * args.steps * world / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_rate(wl.n, args.steps, world, ms_max)
 
     # per-kernel device times (CUDA events between the kernel groups, same stream, no graphs)
     b0 = sysm.info()["n_builds"]
@@ -392,6 +594,11 @@ def main():
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=8.0, help="request arrivals per second")
+    ap.add_argument("--workload", choices=["cube", "slab", "replicas", "serve-sweep"], default="cube",
+                    help="cube: the 884,736-atom benchmark (default); slab: 3,276,800-atom helix slab with a "
+                         "temperature ramp; replicas: 64 uneven replicas in one batched call; serve-sweep: "
+                         "Poisson serving at multiples of the saturation rate")
+    ap.add_argument("--ramp-steps", type=int, default=20000, help="slab: length of the 0 -> 280 K ramp")
     ap.add_argument("--cells", type=int, default=48, help="B20 cells per side (48: the benchmark workload; "
                                                            "smaller values are for profiling captures)")
     args = ap.parse_args()
@@ -399,6 +606,12 @@ def main():
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "slab":
+        return run_slab(args)
+    if args.workload == "replicas":
+        return run_replicas(args)
+    if args.workload == "serve-sweep":
+        return run_serve_sweep(args)
     return run_ours(args)
 
 

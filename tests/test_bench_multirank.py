@@ -1,0 +1,55 @@
+"""Multi-rank aggregation of bench.py on CPU (gloo, world size 2).
+
+Each rank times its own replica; the job's rate is all ranks' atom-steps over the
+slowest rank's time.  Runs two gloo processes on 127.0.0.1; no GPU involved."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, times_ms, out):
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms_max = bench.max_over_ranks(times_ms[rank], dist, "cpu")
+        out.put((rank, ms_max, bench.whole_job_rate(1000, 50, world, ms_max)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_rate_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    times = [10.0, 12.5]
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, times, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms_max, rate in res:
+        assert ms_max == 12.5
+        assert rate == pytest.approx(1000 * 50 * 2 / 12.5e-3)
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.max_over_ranks(3.25) == 3.25
+    assert bench.whole_job_rate(884736, 200, 1, 1000.0) == pytest.approx(884736 * 200.0)

@@ -88,6 +88,10 @@ typedef struct {
     double lambda_spin;    /* Gilbert damping of the stochastic spin update  */
     uint64_t seed;         /* Philox key word 0                              */
     uint64_t replica;      /* Philox key word 1                              */
+    int32_t midpoint_iters;   /* 0: predictor-corrector; > 0: cap of the midpoint iteration */
+    int32_t anderson_depth;   /* 0: plain fixed-point iteration; > 0: Anderson history     */
+    double midpoint_tol;      /* stop when max_i |G_i - X_i| < tol (0: always the cap)      */
+    double anderson_reg;      /* Tikhonov weight, relative to the mean diagonal              */
 } or_dynamics;
 
 static int or_dim(int n_ch) { return 1 + 13 * n_ch; }
@@ -707,6 +711,136 @@ void or_rotate(const double S[3], const double w[3], double dt, double out[3]) {
     for (int k = 0; k < 3; ++k) out[k] = S[k] * c + axs[k] * s + a[k] * as * (1.0 - c);
 }
 
+/* Largest Anderson history the oracle accepts. */
+#define OR_AA_MAX 8
+
+/* Solve the k x k symmetric positive definite system A g = b in place (Cholesky). */
+static int spd_solve(int k, double *A, double *b) {
+    for (int j = 0; j < k; ++j) {
+        double d = A[j * k + j];
+        for (int q = 0; q < j; ++q) d -= A[j * k + q] * A[j * k + q];
+        if (!(d > 0.0)) return -1;
+        d = sqrt(d);
+        A[j * k + j] = d;
+        for (int i = j + 1; i < k; ++i) {
+            double v = A[i * k + j];
+            for (int q = 0; q < j; ++q) v -= A[i * k + q] * A[j * k + q];
+            A[i * k + j] = v / d;
+        }
+    }
+    for (int i = 0; i < k; ++i) {   /* L y = b */
+        double v = b[i];
+        for (int q = 0; q < i; ++q) v -= A[i * k + q] * b[q];
+        b[i] = v / A[i * k + i];
+    }
+    for (int i = k - 1; i >= 0; --i) {   /* L^T g = y */
+        double v = b[i];
+        for (int q = i + 1; q < k; ++q) v -= A[q * k + i] * b[q];
+        b[i] = v / A[i * k + i];
+    }
+    return 0;
+}
+
+static void normalise3(double *v) {
+    double nn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] /= nn; v[1] /= nn; v[2] /= nn;
+}
+
+/* The midpoint iteration of one step (see or_run).  On entry spin holds the explicit
+ * predictor X_0, S0 the spins at the start of the step and pmid the lattice midpoint;
+ * on return spin holds the new spins and (Fs, Hs) the forces and fields at (pos, spin). */
+static int midpoint_spins(int64_t n, const double *pos, const double *pmid, double *spin, const int32_t *species, const double *box,
+                          const int32_t *per, const or_params *P, const or_dynamics *dyn, double dt,
+                          const double B[3], const double *S0, const double *eta, double *Fs, double *Hs,
+                          int64_t *iters) {
+    const size_t n3 = 3 * (size_t)(n > 0 ? n : 1);
+    const int depth = dyn->anderson_depth;
+    const double lam = dyn->lambda_spin;
+    double *X = malloc(sizeof(double) * n3), *G = malloc(sizeof(double) * n3), *Mid = malloc(sizeof(double) * n3);
+    double *Xh = malloc(sizeof(double) * n3 * (size_t)(depth + 1));   /* history of X_j (ring) */
+    double *Gh = malloc(sizeof(double) * n3 * (size_t)(depth + 1));   /* history of G_j (ring) */
+    int rc = 0;
+    if (!X || !G || !Mid || !Xh || !Gh) { rc = -1; goto out; }
+    memcpy(X, spin, sizeof(double) * 3 * (size_t)n);
+    for (int m = 0; m < dyn->midpoint_iters; ++m) {
+        for (int64_t i = 0; i < n; ++i) {
+            for (int c = 0; c < 3; ++c) Mid[3 * i + c] = S0[3 * i + c] + X[3 * i + c];
+            normalise3(Mid + 3 * i);
+        }
+        rc = or_evaluate(n, pmid, Mid, species, box, per, P, B, NULL, NULL, Fs, Hs, NULL);
+        if (rc) goto out;
+        *iters += 1;
+        double dmax = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            double Hp[3], w[3], d2 = 0.0;
+            for (int c = 0; c < 3; ++c) Hp[c] = Hs[3 * i + c] + eta[3 * i + c];
+            omega_of(Mid + 3 * i, Hp, lam, w);
+            or_rotate(S0 + 3 * i, w, dt, G + 3 * i);
+            for (int c = 0; c < 3; ++c) d2 += (G[3 * i + c] - X[3 * i + c]) * (G[3 * i + c] - X[3 * i + c]);
+            if (sqrt(d2) > dmax) dmax = sqrt(d2);
+        }
+        if (dmax < dyn->midpoint_tol || m + 1 == dyn->midpoint_iters) break;
+        if (depth == 0) {
+            memcpy(X, G, sizeof(double) * 3 * (size_t)n);
+            continue;
+        }
+        /* Anderson mix over the last k + 1 iterates */
+        const int slot = m % (depth + 1);
+        memcpy(Xh + (size_t)slot * n3, X, sizeof(double) * 3 * (size_t)n);
+        memcpy(Gh + (size_t)slot * n3, G, sizeof(double) * 3 * (size_t)n);
+        const int k = m < depth ? m : depth;
+        if (k == 0) {
+            memcpy(X, G, sizeof(double) * 3 * (size_t)n);
+            continue;
+        }
+        double A[OR_AA_MAX * OR_AA_MAX], b[OR_AA_MAX];
+        /* column q: dF_q = f_{m-k+q+1} - f_{m-k+q}, f_j = G_j - X_j */
+        for (int q = 0; q < k; ++q) {
+            b[q] = 0.0;
+            for (int r = 0; r < k; ++r) A[q * k + r] = 0.0;
+        }
+        for (size_t e = 0; e < 3 * (size_t)n; ++e) {
+            double fm = G[e] - X[e];
+            double dF[OR_AA_MAX];
+            for (int q = 0; q < k; ++q) {
+                const int ja = (m - k + q + 1) % (depth + 1), jb = (m - k + q) % (depth + 1);
+                const double fa = Gh[(size_t)ja * n3 + e] - Xh[(size_t)ja * n3 + e];
+                const double fb = Gh[(size_t)jb * n3 + e] - Xh[(size_t)jb * n3 + e];
+                dF[q] = fa - fb;
+            }
+            for (int q = 0; q < k; ++q) {
+                b[q] += dF[q] * fm;
+                for (int r = 0; r < k; ++r) A[q * k + r] += dF[q] * dF[r];
+            }
+        }
+        double tr = 0.0;
+        for (int q = 0; q < k; ++q) tr += A[q * k + q];
+        const double delta = dyn->anderson_reg * tr / k;
+        for (int q = 0; q < k; ++q) A[q * k + q] += delta;
+        if (!(tr > 0.0) || spd_solve(k, A, b)) {   /* no usable history: plain step */
+            memcpy(X, G, sizeof(double) * 3 * (size_t)n);
+            continue;
+        }
+        for (size_t e = 0; e < 3 * (size_t)n; ++e) {
+            double v = G[e];
+            for (int q = 0; q < k; ++q) {
+                const int ja = (m - k + q + 1) % (depth + 1), jb = (m - k + q) % (depth + 1);
+                v -= b[q] * (Gh[(size_t)ja * n3 + e] - Gh[(size_t)jb * n3 + e]);
+            }
+            X[e] = v;
+        }
+        for (int64_t i = 0; i < n; ++i) normalise3(X + 3 * i);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        for (int c = 0; c < 3; ++c) spin[3 * i + c] = G[3 * i + c];
+        normalise3(spin + 3 * i);
+    }
+    rc = or_evaluate(n, pos, spin, species, box, per, P, B, NULL, NULL, Fs, Hs, NULL);
+out:
+    free(X); free(G); free(Mid); free(Xh); free(Gh);
+    return rc;
+}
+
 /* Advance (pos, vel, spin) by n_steps steps of dt (fs) at temperature T (K) and
  * field B (T).  F and H carry the forces and fields of the current state between
  * calls (have_fh = 0: they are evaluated first).  One step, from (r, v, S, F, H):
@@ -715,11 +849,33 @@ void or_rotate(const double S[3], const double w[3], double dt, double out[3]) {
  *   Sstar = Rot(S, omega(S, H+eta) dt);  (Fstar, Hstar) at (r, Sstar);
  *   S <- Rot(S, (omega(S, H+eta) + omega(Sstar, Hstar+eta)) dt/2), renormalised;
  *   v += dt/2 Fstar/m;  (F, H) <- (Fstar, Hstar).
- * xi is Philox stream 1, zeta stream 2, counter (step, atom, stream, 0), key (seed, replica). */
+ * xi is Philox stream 1, zeta stream 2, counter (step, atom, stream, 0), key (seed, replica).
+ *
+ * Self-consistent midpoint spin update (Section 5.1.3; dyn->midpoint_iters > 0).  The
+ * lattice part is unchanged; r_mid = r_start + (r - r_start)/2 is the lattice midpoint
+ * of the step (unwrapped displacement, then wrapped).  With X_0 = Rot(S, omega(S, H+eta) dt)
+ * the explicit predictor, iteration m (m < midpoint_iters) takes
+ *   M_m = (S + X_m) / |S + X_m|            the midpoint spins,
+ *   H_m = H(r_mid, M_m)                    force and field re-evaluated at the midpoint
+ *                                          configuration (r_mid, M_m),
+ *   G_m = Rot(S, omega(M_m, H_m+eta) dt)   the one-step update re-applied,
+ * and stops when d_m = max_i |G_m,i - X_m,i| < midpoint_tol or at the cap; then
+ * S <- G_m renormalised, (F, H) are evaluated at (r, S) and v += dt/2 F/m.  The next
+ * iterate is X_{m+1} = G_m (plain fixed-point iteration) or, with anderson_depth > 0,
+ * the regularised Anderson mix (Anderson 1965; Walker and Ni 2011, undamped form):
+ *   f_j = G_j - X_j;  dF, dG = differences of the last k+1 f_j, G_j (k = min(depth, m));
+ *   (dF^T dF + delta I) g = dF^T f_m,  delta = anderson_reg * trace(dF^T dF) / k;
+ *   X_{m+1} = G_m - dG g, each spin renormalised.
+ * *iters_used (if not NULL) receives the number of midpoint evaluations over all steps. */
 int or_run(int64_t n, double *pos, double *vel, double *spin, const int32_t *species, const double *box,
            const int32_t *per, const or_params *P, const or_dynamics *dyn, int64_t n_steps, double dt,
-           double T, const double B[3], uint64_t step0, double *F, double *H, int have_fh) {
+           double T, const double B[3], uint64_t step0, double *F, double *H, int have_fh,
+           int64_t *iters_used) {
     if (check_params(P)) return -3;
+    if (dyn->midpoint_iters < 0 || dyn->anderson_depth < 0 || dyn->anderson_depth > OR_AA_MAX ||
+        !(dyn->midpoint_tol >= 0.0) || !(dyn->anderson_reg >= 0.0))
+        return -3;
+    if (iters_used) *iters_used = 0;
     int rc;
     if (!have_fh) {
         rc = or_evaluate(n, pos, spin, species, box, per, P, B, NULL, NULL, F, H, NULL);
@@ -729,7 +885,8 @@ int or_run(int64_t n, double *pos, double *vel, double *spin, const int32_t *spe
     double *eta = malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     double *Fs = malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     double *Hs = malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
-    if (!S0 || !eta || !Fs || !Hs) return -1;
+    double *pmid = malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    if (!S0 || !eta || !Fs || !Hs || !pmid) return -1;
     const double cfric = exp(-dyn->gamma_lattice * dt);
     const double lam = dyn->lambda_spin;
     const double sig_eta = (T > 0.0 && lam > 0.0) ? sqrt(2.0 * lam * OR_KB * T * OR_HBAR / dt) : 0.0;
@@ -743,17 +900,38 @@ int or_run(int64_t n, double *pos, double *vel, double *spin, const int32_t *spe
             or_gauss4(step, (uint64_t)i, 2, dyn->seed, dyn->replica, ze);
             for (int c = 0; c < 3; ++c) {
                 double *x = pos + 3 * i + c, *v = vel + 3 * i + c;
+                const double x0 = *x;
                 *v += 0.5 * dt * F[3 * i + c] * OR_ACC / m;
                 *x += 0.5 * dt * *v;
                 *v = cfric * *v + sig_v * xi[c];
                 *x += 0.5 * dt * *v;
-                if (per[c]) *x = *x - box[c] * floor(*x / box[c]);
+                double xm = x0 + 0.5 * (*x - x0);     /* lattice midpoint of the step */
+                if (per[c]) {
+                    *x = *x - box[c] * floor(*x / box[c]);
+                    xm = xm - box[c] * floor(xm / box[c]);
+                }
+                pmid[3 * i + c] = xm;
                 eta[3 * i + c] = sig_eta * ze[c];
             }
             double Hp[3], w[3];
             for (int c = 0; c < 3; ++c) { S0[3 * i + c] = spin[3 * i + c]; Hp[c] = H[3 * i + c] + eta[3 * i + c]; }
             omega_of(S0 + 3 * i, Hp, lam, w);
             or_rotate(S0 + 3 * i, w, dt, spin + 3 * i);
+        }
+        if (dyn->midpoint_iters > 0) {
+            int64_t it = 0;
+            rc = midpoint_spins(n, pos, pmid, spin, species, box, per, P, dyn, dt, B, S0, eta, Fs, Hs, &it);
+            if (iters_used) *iters_used += it;
+            if (rc) break;
+            for (int64_t i = 0; i < n; ++i) {
+                double m = P->mass_amu[species[i]];
+                for (int c = 0; c < 3; ++c) {
+                    vel[3 * i + c] += 0.5 * dt * Fs[3 * i + c] * OR_ACC / m;
+                    F[3 * i + c] = Fs[3 * i + c];
+                    H[3 * i + c] = Hs[3 * i + c];
+                }
+            }
+            continue;
         }
         rc = or_evaluate(n, pos, spin, species, box, per, P, B, NULL, NULL, Fs, Hs, NULL);
         if (rc) break;
@@ -777,7 +955,7 @@ int or_run(int64_t n, double *pos, double *vel, double *spin, const int32_t *spe
             }
         }
     }
-    free(S0); free(eta); free(Fs); free(Hs);
+    free(S0); free(eta); free(Fs); free(Hs); free(pmid);
     return rc;
 }
 

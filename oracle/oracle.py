@@ -52,7 +52,9 @@ class _Params(C.Structure):
 
 class _Dyn(C.Structure):
     _fields_ = [("gamma_lattice", C.c_double), ("lambda_spin", C.c_double),
-                ("seed", C.c_uint64), ("replica", C.c_uint64)]
+                ("seed", C.c_uint64), ("replica", C.c_uint64),
+                ("midpoint_iters", C.c_int32), ("anderson_depth", C.c_int32),
+                ("midpoint_tol", C.c_double), ("anderson_reg", C.c_double)]
 
 
 def lib():
@@ -69,7 +71,7 @@ def lib():
             _lib.or_descriptors.argtypes = [I, P, P, P, P, P, P, P]
             _lib.or_evaluate.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P, P]
             _lib.or_evaluate_subset.argtypes = [I, P, P, P, P, P, P, P, I, P, P, P, P]
-            _lib.or_run.argtypes = [I, P, P, P, P, P, P, P, P, I, D, D, P, C.c_uint64, P, P, C.c_int]
+            _lib.or_run.argtypes = [I, P, P, P, P, P, P, P, P, I, D, D, P, C.c_uint64, P, P, C.c_int, P]
             _lib.or_rotate.argtypes = [P, P, D, P]
             for f in ("or_neighbors", "or_descriptors", "or_evaluate", "or_evaluate_subset", "or_run"):
                 getattr(_lib, f).restype = C.c_int
@@ -221,17 +223,25 @@ class State:
 
 
 def run(model: Model, st: State, n_steps: int, dt: float, T: float, B=(0.0, 0.0, 0.0), *,
-        gamma=0.01, lam=0.1, seed=1234, replica=0):
+        gamma=0.01, lam=0.1, seed=1234, replica=0, midpoint_iters=0, midpoint_tol=0.0, anderson_depth=0,
+        anderson_reg=1e-10):
+    """Advance st by n_steps steps (or_run).  midpoint_iters > 0 selects the self-consistent
+    midpoint spin update (cap of the iteration, tolerance midpoint_tol, optional Anderson
+    history anderson_depth with relative regularisation anderson_reg).  Returns st; the
+    number of midpoint evaluations of the call is in st.last_iterations."""
     P = model.c_struct()
-    dyn = _Dyn(gamma, lam, seed, replica)
+    dyn = _Dyn(gamma, lam, seed, replica, int(midpoint_iters), int(anderson_depth), float(midpoint_tol),
+               float(anderson_reg))
     Bv = _f64(B)
+    it = np.zeros(1, dtype=np.int64)
     rc = lib().or_run(st.pos.shape[0], _p(st.pos), _p(st.vel), _p(st.spin), _p(st.species), _p(st.box),
                       _p(st.periodic), C.addressof(P), C.addressof(dyn), int(n_steps), float(dt), float(T),
-                      _p(Bv), int(st.step), _p(st.F), _p(st.H), int(st.have_fh))
+                      _p(Bv), int(st.step), _p(st.F), _p(st.H), int(st.have_fh), _p(it))
     if rc:
         raise RuntimeError(f"or_run failed: {rc}")
     st.have_fh = True
     st.step += int(n_steps)
+    st.last_iterations = int(it[0])
     return st
 
 

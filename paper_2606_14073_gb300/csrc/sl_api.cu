@@ -455,19 +455,9 @@ int sl_create_system(const double *positions, const double *spins, const double 
     return SL_OK;
 }
 
-int sl_step(sl_system *sys, int64_t n_steps, double dt, double T, const double B[3]) {
-    if (!sys || !B) return fail(SL_EINVAL, "NULL argument");
-    if (n_steps < 0 || !(dt > 0) || !(T >= 0) || !std::isfinite(dt) || !std::isfinite(T))
-        return fail(SL_EINVAL, "bad step arguments");
-    sl::Sys &s = sys->s;
-    cudaSetDevice(s.device);
-    int rc;
-    if ((rc = upload_params(s, dt, T, B))) return rc;
-    for (int c = 0; c < 3; ++c) s.B[c] = B[c];
-    if (n_steps == 0 || s.n == 0) {
-        s.step += (uint64_t)n_steps;
-        return SL_OK;
-    }
+// State at the start of a stepping call, kept on the device so that a call that ends in
+// a list overflow or a non-finite value leaves the system as it was before the call.
+static int snapshot_state(sl::Sys &s) {
     const size_t N = (size_t)s.n;
     CK(cudaMemcpyAsync(s.snap, s.pos, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
     CK(cudaMemcpyAsync(s.snap + N, s.vel, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
@@ -475,6 +465,30 @@ int sl_step(sl_system *sys, int64_t n_steps, double dt, double T, const double B
     CK(cudaMemcpyAsync(s.snap + 3 * N, s.F, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
     CK(cudaMemcpyAsync(s.snap + 4 * N, s.H, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
     CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
+    return SL_OK;
+}
+
+static int restore_state(sl::Sys &s) {
+    const size_t N = (size_t)s.n;
+    CK(cudaMemcpyAsync(s.pos, s.snap, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+    CK(cudaMemcpyAsync(s.vel, s.snap + N, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+    CK(cudaMemcpyAsync(s.spin, s.snap + 2 * N, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+    CK(cudaMemcpyAsync(s.F, s.snap + 3 * N, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+    CK(cudaMemcpyAsync(s.H, s.snap + 4 * N, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
+    unsigned long long st[2] = {s.step, s.step};
+    CK(cudaMemcpyAsync(s.d_step, st, sizeof st, cudaMemcpyHostToDevice, s.stream));
+    CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
+    int r2;
+    if ((r2 = refresh_copies(s))) return r2;
+    sl::launch_rebuild(s, false);
+    CK(cudaStreamSynchronize(s.stream));
+    return SL_OK;
+}
+
+// Queue n_steps steps on the system's stream: captured graphs of steps_per_graph steps,
+// then single steps for the remainder.
+static int queue_steps(sl::Sys &s, int64_t n_steps) {
+    int rc;
     int64_t left = n_steps;
     const int k = s.steps_per_graph;
     if (k > 0 && left >= k) {
@@ -488,26 +502,39 @@ int sl_step(sl_system *sys, int64_t n_steps, double dt, double T, const double B
     for (; left > 0; --left) enqueue_step(s);
     CK(cudaGetLastError());
     s.n_launches += n_steps * sl::KERNELS_PER_STEP;
-    rc = check_status(s);
+    return SL_OK;
+}
+
+// Status of the queued steps; on a list overflow or a non-finite value the state goes
+// back to the snapshot and the error names the step it was restored to.
+static int finish_steps(sl::Sys &s, int64_t n_steps, const char *who) {
+    const int rc = check_status(s);
     if (rc == SL_ENBR_OVERFLOW || rc == SL_ENONFINITE) {
-        std::string msg = g_err;
-        CK(cudaMemcpyAsync(s.pos, s.snap, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
-        CK(cudaMemcpyAsync(s.vel, s.snap + N, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
-        CK(cudaMemcpyAsync(s.spin, s.snap + 2 * N, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
-        CK(cudaMemcpyAsync(s.F, s.snap + 3 * N, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
-        CK(cudaMemcpyAsync(s.H, s.snap + 4 * N, sizeof(double4) * N, cudaMemcpyDeviceToDevice, s.stream));
-        unsigned long long st[2] = {s.step, s.step};
-        CK(cudaMemcpyAsync(s.d_step, st, sizeof st, cudaMemcpyHostToDevice, s.stream));
-        CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
+        const std::string msg = g_err;
         int r2;
-        if ((r2 = refresh_copies(s))) return r2;
-        sl::launch_rebuild(s, false);
-        CK(cudaStreamSynchronize(s.stream));
-        return fail(rc, "%s; state restored to step %llu", msg.c_str(), (unsigned long long)s.step);
+        if ((r2 = restore_state(s))) return r2;
+        return fail(rc, "%s%s; state restored to step %llu", who, msg.c_str(), (unsigned long long)s.step);
     }
     if (rc) return rc;
     s.step += (uint64_t)n_steps;
     return SL_OK;
+}
+
+int sl_step(sl_system *sys, int64_t n_steps, double dt, double T, const double B[3]) {
+    if (!sys || !B) return fail(SL_EINVAL, "NULL argument");
+    if (n_steps < 0 || !(dt > 0) || !(T >= 0) || !std::isfinite(dt) || !std::isfinite(T))
+        return fail(SL_EINVAL, "bad step arguments");
+    sl::Sys &s = sys->s;
+    cudaSetDevice(s.device);
+    int rc;
+    if ((rc = upload_params(s, dt, T, B))) return rc;
+    for (int c = 0; c < 3; ++c) s.B[c] = B[c];
+    if (n_steps == 0 || s.n == 0) {
+        s.step += (uint64_t)n_steps;
+        return SL_OK;
+    }
+    if ((rc = snapshot_state(s)) || (rc = queue_steps(s, n_steps))) return rc;
+    return finish_steps(s, n_steps, "");
 }
 
 int sl_energy_forces_fields(sl_system *sys, double *energy, double *forces, double *fields, double *virial) {
@@ -773,33 +800,33 @@ int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt, const d
     // every replica's steps are queued on its own stream before any wait, so the
     // replicas' kernels overlap on the device
     const int k = (int)b->sys.size();
-    int rc = SL_OK;
-    for (int i = 0; i < k && rc == SL_OK; ++i) {
-        if (n_steps[i] < 0 || !(dt[i] > 0) || !(T[i] >= 0)) return fail(SL_EINVAL, "bad step arguments for replica %d", i);
+    for (int i = 0; i < k; ++i) {
+        if (n_steps[i] < 0 || !(dt[i] > 0) || !(T[i] >= 0) || !std::isfinite(dt[i]) || !std::isfinite(T[i]))
+            return fail(SL_EINVAL, "bad step arguments for replica %d", i);
     }
+    int rc;
     std::vector<int> active;
     for (int i = 0; i < k; ++i) {
         sl::Sys &s = b->sys[i]->s;
+        cudaSetDevice(s.device);
         if ((rc = upload_params(s, dt[i], T[i], B + 3 * i))) return rc;
         for (int c = 0; c < 3; ++c) s.B[c] = B[3 * i + c];
         if (n_steps[i] == 0 || s.n == 0) { s.step += (uint64_t)n_steps[i]; continue; }
-        CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
-        int64_t left = n_steps[i];
-        const int g = s.steps_per_graph;
-        if (g > 0 && left >= g) {
-            if (!s.graph || s.graph_steps != g)
-                if ((rc = capture_graph(s, g))) return rc;
-            while (left >= g) { CK(cudaGraphLaunch(s.graph, s.stream)); left -= g; }
-        }
-        for (; left > 0; --left) enqueue_step(s);
+        if ((rc = snapshot_state(s)) || (rc = queue_steps(s, n_steps[i]))) return rc;
         active.push_back(i);
     }
-    CK(cudaGetLastError());
+    // every replica is finished (and restored where it failed) before the first error is returned
+    int first = SL_OK;
+    std::string first_msg;
     for (int i : active) {
         sl::Sys &s = b->sys[i]->s;
-        if ((rc = check_status(s))) return fail(rc, "replica %d: %s", i, g_err.c_str());
-        s.step += (uint64_t)n_steps[i];
+        cudaSetDevice(s.device);
+        char who[32];
+        std::snprintf(who, sizeof who, "replica %d: ", i);
+        rc = finish_steps(s, n_steps[i], who);
+        if (rc && first == SL_OK) { first = rc; first_msg = g_err; }
     }
+    if (first != SL_OK) return fail(first, "%s", first_msg.c_str());
     return SL_OK;
 }
 

@@ -252,3 +252,34 @@ def test_neighbor_overflow_is_reported_and_state_restored(params):
     for k in ("positions", "velocities", "spins", "forces", "fields"):
         assert np.array_equal(after[k], before[k]), k
     assert after["step"] == before["step"]
+
+
+def test_batch_overflow_restores_only_the_failing_replica(params):
+    """In one batched call, a replica that overflows its lists goes back to its state at
+    the start of the call; the other replica's steps are kept."""
+    wl = W.fege_small()
+    c = wl.box / 2
+    vel = -0.02 * (wl.positions - c)
+    bad = S.System(wl.positions, wl.spins, wl.box, wl.periodic, wl.species, params, vel, cap_rad=128, cap_ang=48,
+                   gamma=0.0, steps_per_graph=0, replica=1)
+    good = S.System(wl.positions, wl.spins, wl.box, wl.periodic, wl.species, params, wl.velocities, replica=2,
+                    steps_per_graph=0)
+    b = S.Batch([good, bad])
+    code = None
+    for _ in range(60):
+        g0, b0 = good.get_state(), bad.get_state()
+        try:
+            b.step(5, 1.0, [0.0, 0.0], [(0, 0, 0), (0, 0, 0)])
+        except S.SpinlatError as e:
+            code = e.code
+            break
+    assert code == S.SL_ENBR_OVERFLOW
+    b1, g1 = bad.get_state(), good.get_state()
+    for k in ("positions", "velocities", "spins", "forces", "fields"):
+        assert np.array_equal(b1[k], b0[k]), k
+    assert b1["step"] == b0["step"]
+    assert g1["step"] == g0["step"] + 5
+    assert not np.array_equal(g1["positions"], g0["positions"])
+    b.destroy()
+    good.destroy()
+    bad.destroy()

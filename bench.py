@@ -460,8 +460,10 @@ def run_ours(args):
                                                             name=f"fege_b20_{args.cells}c")
     replica = rank
     stream = torch.cuda.Stream(device=local)
+    mid = dict(midpoint_iters=args.midpoint_iters, midpoint_tol=args.midpoint_tol,
+               anderson_depth=args.anderson_depth)
     sysm = S.system_from_workload(wl, params, precision=S.SL_PREC_MIXED, replica=replica, stream=stream.cuda_stream,
-                                  device=local, steps_per_graph=args.graph_steps)
+                                  device=local, steps_per_graph=args.graph_steps, **mid)
 
     def barrier():
         if dist is not None:
@@ -472,7 +474,7 @@ def run_ours(args):
     fp64 = None
     if not args.skip_fp64:
         sysd = S.system_from_workload(wl, params, precision=S.SL_PREC_FP64, replica=replica, device=local,
-                                      stream=stream.cuda_stream, steps_per_graph=args.graph_steps)
+                                      stream=stream.cuda_stream, steps_per_graph=args.graph_steps, **mid)
         rm = sysm.energy_forces_fields(want_virial=False)
         rd = sysd.energy_forces_fields(want_virial=False)
         err = {"reference": "FP64 GPU path (itself within 1e-10 of the FP64 oracle)",
@@ -496,6 +498,7 @@ def run_ours(args):
     sysm.step(args.warmup, DT, TEMP, FIELD)
     info0 = sysm.info()
     launches0 = info0["n_launches"]
+    mid0 = sysm.midpoint_evaluations()
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
@@ -512,6 +515,7 @@ def run_ours(args):
     info1 = sysm.info()
     launches = info1["n_launches"] - launches0
     builds_timed = info1["n_builds"] - info0["n_builds"]
+    mid_evals = sysm.midpoint_evaluations() - mid0
     ms_max = max_over_ranks(ms, dist, "cuda")
     value = whole_job_rate(wl.n, args.steps, world, ms_max)
 
@@ -565,6 +569,9 @@ def run_ours(args):
                 "data": "synthetic (seeded FeGe B20, random-init NEP of the paper's shape)",
                 "config": {"workload": WORKLOAD if args.cells == 48 else wl.name, "atoms": wl.n, "precision": "mixed", "dt_fs": DT, "T_K": TEMP,
                            "B_T": list(FIELD), "steps_per_graph": args.graph_steps,
+                           "spin_update": ("predictor-corrector" if args.midpoint_iters == 0 else
+                                           f"self-consistent midpoint, cap {args.midpoint_iters}, tol "
+                                           f"{args.midpoint_tol}, Anderson depth {args.anderson_depth}"),
                            "l2": "inputs larger than L2 (~10 GB working set)", "parallelism": f"replicas x{world}"},
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "neighbour_builds": {"timed_region": builds_timed, "profiled_steps": builds_prof,
@@ -573,6 +580,8 @@ def run_ours(args):
                 "kernel_alu_frac": {k: fl[k] * wl.n / (prof[k] / args.profile_steps * 1e-3) / 1e12 / peak_derived
                                     for k in ("rad_fwd", "ang_fwd", "network", "backward")},
                 "fp64": fp64, "mixed_error_vs_fp64": err, "serving": serving, "cpu_baseline": cpu}
+        if args.midpoint_iters > 0:
+            line["midpoint_evaluations_per_step"] = mid_evals / args.steps
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -599,6 +608,10 @@ def main():
                          "temperature ramp; replicas: 64 uneven replicas in one batched call; serve-sweep: "
                          "Poisson serving at multiples of the saturation rate")
     ap.add_argument("--ramp-steps", type=int, default=20000, help="slab: length of the 0 -> 280 K ramp")
+    ap.add_argument("--midpoint-iters", type=int, default=0,
+                    help="cube: cap of the self-consistent midpoint spin update (0: predictor-corrector)")
+    ap.add_argument("--midpoint-tol", type=float, default=1e-6)
+    ap.add_argument("--anderson-depth", type=int, default=0)
     ap.add_argument("--cells", type=int, default=48, help="B20 cells per side (48: the benchmark workload; "
                                                            "smaller values are for profiling captures)")
     args = ap.parse_args()

@@ -71,16 +71,37 @@ typedef struct {
     double skin;                     /* neighbour skin, A (rebuild at skin/2 motion)  */
     double gamma_lattice_per_fs;     /* lattice Langevin friction                      */
     double lambda_spin;              /* Gilbert damping of the stochastic spin update  */
-    int32_t midpoint_iters;          /* must be 0 (self-consistent midpoint: not built) */
+    int32_t midpoint_iters;          /* 0: predictor-corrector spin update; 1..64: cap of the
+                                        self-consistent midpoint iteration (Section 5.1.3)  */
     int32_t nbr_cap_rad;             /* radial list capacity (candidates within rc_rad+skin) */
     int32_t nbr_cap_ang;             /* angular list capacity (within rc_ang+skin)      */
     int32_t steps_per_graph;         /* steps captured in one CUDA graph (0: no graphs) */
     void *cuda_stream;               /* cudaStream_t to run on; NULL: a library stream  */
     int32_t device;                  /* CUDA device ordinal; -1: the calling thread's current device */
+    double midpoint_tol;             /* stop the midpoint iteration when every spin moved
+                                        less than this between iterates (0: run the cap)   */
+    int32_t anderson_depth;          /* 0: plain fixed-point iteration; 1..8: history of the
+                                        regularised Anderson-accelerated iteration          */
+    double anderson_reg;             /* Tikhonov weight of the Anderson least-squares
+                                        problem, relative to its mean diagonal              */
 } sl_options;
 
+/* Self-consistent midpoint spin update (midpoint_iters > 0; Section 5.1.3).  The
+ * lattice part of the step is unchanged.  With r_mid = (r_n + r_{n+1})/2 and
+ * X_0 = Rot(S_n, omega(S_n, H_n + eta) dt), iteration m forms the midpoint spins
+ * M_m = (S_n + X_m)/|S_n + X_m|, evaluates the field at (r_mid, M_m), applies
+ * G_m = Rot(S_n, omega(M_m, H_m + eta) dt) and stops when max_i |G_m - X_m| <
+ * midpoint_tol or at the cap; S_{n+1} = G_m, and forces and fields are evaluated at
+ * (r_{n+1}, S_{n+1}) for the final kick.  X_{m+1} = G_m, or with anderson_depth > 0
+ * the Anderson mix X_{m+1} = G_m - dG g, (dF^T dF + reg tr/k I) g = dF^T f_m over the
+ * last k + 1 residuals f = G - X, spins renormalised.  Costs one evaluation per
+ * iteration plus one; SL_ENBR_OVERFLOW also reports a midpoint configuration beyond
+ * the lists' skin. */
+
 /* Fill *opt with the defaults: FP64, seed 1234, replica 0, skin 1 A, gamma 0.01/fs,
- * lambda 0.1, caps 160/64, 10 steps per graph, library stream, current device. */
+ * lambda 0.1, caps 160/64, 10 steps per graph, library stream, current device,
+ * predictor-corrector spin update (midpoint_iters 0, tol 0, Anderson depth 0,
+ * regularisation 1e-10). */
 void sl_default_options(sl_options *opt);
 
 /* Create a system of n atoms on the current CUDA device.
@@ -152,6 +173,10 @@ int64_t sl_estimate_device_bytes(int64_t n, const sl_options *opt);
 int sl_get_info(const sl_system *sys, int64_t *n_atoms, int32_t *precision, int64_t *n_builds,
                 int64_t *n_launches);
 
+/* Midpoint evaluations executed by all steps so far (0 in the predictor-corrector
+ * mode); the mean iteration count per step is this over the steps taken. */
+int sl_get_midpoint_evaluations(const sl_system *sys, int64_t *evaluations);
+
 /* Kernels (or kernel groups) timed by sl_step_profiled, in step order. */
 #define SL_K_FIRST_HALF 0    /* kicks, drifts, Langevin, spin predictor, rebuild test     */
 #define SL_K_REBUILD 1       /* binning + lists + reverse slots (early exit when not due) */
@@ -160,7 +185,7 @@ int sl_get_info(const sl_system *sys, int64_t *n_atoms, int32_t *precision, int6
 #define SL_K_ANG_FWD 4       /* angular and spin-angular channels                         */
 #define SL_K_NETWORK 5       /* per-atom network and its input gradient                   */
 #define SL_K_BACKWARD 6      /* backward to pair records, per-atom sums                   */
-#define SL_K_SECOND_HALF 7   /* force/field gather, spin corrector, final kick            */
+#define SL_K_SECOND_HALF 7   /* gather, spin corrector or midpoint iteration, final kick  */
 #define SL_NKERNELS 8
 
 /* Same as sl_step but without CUDA graphs and with CUDA events recorded on the

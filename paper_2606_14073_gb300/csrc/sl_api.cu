@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -103,7 +104,8 @@ void free_sys(sl::Sys &s) {
                     s.inv, s.nbr, s.rev, s.nbr_orig, s.cells.posf, s.cells.key, s.seg, s.cells.count, s.cells.start, s.cells.fill, s.cells.atoms,
                     s.cells.of, s.q, s.bsum, s.fp, s.ei, s.pairs, s.clj, s.cls, s.cnt, s.fown, s.gii,
                     s.wpart, s.Fo, s.Ho,
-                    s.status, s.rebuild, s.d_step, s.d_par, s.red, s.snap, s.d_builds};
+                    s.status, s.rebuild, s.d_step, s.d_par, s.red, s.snap, s.d_builds,
+                    s.posmid, s.posmidf, s.mids, s.midsf, s.mx, s.mg, s.aax, s.aag, s.aapart, s.md};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (s.h_par) cudaFreeHost(s.h_par);
@@ -140,9 +142,17 @@ int upload_params(sl::Sys &s, double dt, double T, const double B[3]) {
 void enqueue_step(sl::Sys &s) {
     sl::launch_first_half(s);
     sl::launch_rebuild(s, true);
-    sl::launch_eval(s, false);
-    sl::launch_second_half(s);
+    if (s.mid_iters > 0) {          // self-consistent midpoint spin update, then the end state
+        sl::launch_midpoint(s);
+        sl::launch_eval(s, false);
+        sl::launch_second_half_nospin(s);
+    } else {
+        sl::launch_eval(s, false);
+        sl::launch_second_half(s);
+    }
 }
+
+int64_t kernels_per_step(const sl::Sys &s) { return sl::KERNELS_PER_STEP + sl::midpoint_kernels_per_step(s); }
 
 // Evaluate at the current state: optional unconditional rebuild, eval, gather.
 int evaluate(sl::Sys &s, bool rebuild, bool carried, bool want_virial) {
@@ -165,6 +175,8 @@ int check_status(sl::Sys &s) {
         return fail(SL_ENBR_OVERFLOW, "neighbour list capacity exceeded (caps %d/%d)", s.cap, s.cap_ang);
     if (st & sl::ST_NONFINITE) return fail(SL_ENONFINITE, "non-finite force or field");
     if (st & sl::ST_TIMEOUT) return fail(SL_ETIMEOUT, "a bounded device wait gave up (tensor-core network)");
+    if (st & sl::ST_MID_RANGE)
+        return fail(SL_ENBR_OVERFLOW, "midpoint configuration moved beyond skin/2 of the list positions");
     return SL_OK;
 }
 
@@ -260,6 +272,9 @@ void sl_default_options(sl_options *o) {
     o->gamma_lattice_per_fs = 0.01;
     o->lambda_spin = 0.1;
     o->midpoint_iters = 0;
+    o->midpoint_tol = 0.0;
+    o->anderson_depth = 0;
+    o->anderson_reg = 1e-10;
     o->nbr_cap_rad = 160;
     o->nbr_cap_ang = 64;
     o->steps_per_graph = 10;
@@ -293,7 +308,13 @@ int sl_create_system(const double *positions, const double *spins, const double 
     else sl_default_options(&opt);
     if (opt.precision != SL_PREC_FP64 && opt.precision != SL_PREC_MIXED) return fail(SL_EINVAL, "bad precision");
     if (!(opt.skin > 0)) return fail(SL_EINVAL, "skin must be positive");
-    if (opt.midpoint_iters != 0) return fail(SL_EINVAL, "midpoint_iters > 0 is not supported");
+    if (opt.midpoint_iters < 0 || opt.midpoint_iters > sl::MID_MAX_ITERS)
+        return fail(SL_EINVAL, "midpoint_iters must lie in [0, %d]", sl::MID_MAX_ITERS);
+    if (opt.anderson_depth < 0 || opt.anderson_depth > sl::AA_MAX_DEPTH)
+        return fail(SL_EINVAL, "anderson_depth must lie in [0, %d]", sl::AA_MAX_DEPTH);
+    if (!(opt.midpoint_tol >= 0) || !std::isfinite(opt.midpoint_tol) || !(opt.anderson_reg >= 0) ||
+        !std::isfinite(opt.anderson_reg))
+        return fail(SL_EINVAL, "midpoint_tol and anderson_reg must be finite and non-negative");
     if (opt.nbr_cap_rad < 1 || opt.nbr_cap_rad > 256 || opt.nbr_cap_ang < 1 || opt.nbr_cap_ang > opt.nbr_cap_rad)
         return fail(SL_EINVAL, "neighbour caps must satisfy 1 <= cap_ang <= cap_rad <= 256");
     if (opt.gamma_lattice_per_fs < 0 || opt.lambda_spin < 0) return fail(SL_EINVAL, "negative damping");
@@ -328,6 +349,10 @@ int sl_create_system(const double *positions, const double *spins, const double 
     s.skin = opt.skin;
     s.gamma = opt.gamma_lattice_per_fs;
     s.lambda = opt.lambda_spin;
+    s.mid_iters = opt.midpoint_iters;
+    s.mid_tol = opt.midpoint_tol;
+    s.aa_depth = opt.midpoint_iters > 0 ? opt.anderson_depth : 0;
+    s.aa_reg = opt.anderson_reg;
     s.cap = opt.nbr_cap_rad;
     s.cap_ang = opt.nbr_cap_ang;
     s.steps_per_graph = opt.steps_per_graph < 0 ? 0 : opt.steps_per_graph;
@@ -410,6 +435,15 @@ int sl_create_system(const double *positions, const double *spins, const double 
         (rc = dalloc(&s.rebuild, 1)) || (rc = dalloc(&s.d_step, 2)) || (rc = dalloc(&s.d_par, 1)) ||
         (rc = dalloc(&s.red, 256 * 10 + 10)) || (rc = dalloc(&s.snap, 5 * N)) || (rc = dalloc(&s.d_builds, 1)))
         return bail(rc);
+    if (s.mid_iters > 0) {
+        const size_t ring = (size_t)(s.aa_depth > 0 ? s.aa_depth + 1 : 0) * N;
+        if ((rc = dalloc(&s.posmid, N)) || (rc = dalloc(&s.posmidf, N)) || (rc = dalloc(&s.mids, N)) ||
+            (rc = dalloc(&s.midsf, N)) || (rc = dalloc(&s.mx, N)) || (rc = dalloc(&s.mg, N)) ||
+            (rc = dalloc(&s.aax, ring)) || (rc = dalloc(&s.aag, ring)) ||
+            (rc = dalloc(&s.aapart, sl::midpoint_scratch_doubles())) || (rc = dalloc(&s.md, 1)))
+            return bail(rc);
+        CK(cudaMemsetAsync(s.md, 0, sizeof(sl::MidDev), s.stream));
+    }
     if ((ce = cudaMallocHost((void **)&s.h_par, sizeof(StepDev))) != cudaSuccess ||
         (ce = cudaMallocHost((void **)&s.h_status, sizeof(int))) != cudaSuccess ||
         (ce = cudaMallocHost((void **)&s.h_red, sizeof(double) * 10)) != cudaSuccess)
@@ -501,7 +535,7 @@ static int queue_steps(sl::Sys &s, int64_t n_steps) {
     }
     for (; left > 0; --left) enqueue_step(s);
     CK(cudaGetLastError());
-    s.n_launches += n_steps * sl::KERNELS_PER_STEP;
+    s.n_launches += n_steps * kernels_per_step(s);
     return SL_OK;
 }
 
@@ -697,6 +731,20 @@ int sl_get_info(const sl_system *sys, int64_t *n_atoms, int32_t *precision, int6
     return SL_OK;
 }
 
+int sl_get_midpoint_evaluations(const sl_system *sys, int64_t *evaluations) {
+    if (!sys || !evaluations) return fail(SL_EINVAL, "NULL argument");
+    const sl::Sys &s = sys->s;
+    *evaluations = 0;
+    if (s.mid_iters <= 0 || !s.md) return SL_OK;
+    unsigned long long v = 0;
+    cudaSetDevice(s.device);
+    CK(cudaMemcpyAsync(&v, reinterpret_cast<const char *>(s.md) + offsetof(sl::MidDev, iters), sizeof v,
+                       cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaStreamSynchronize(s.stream));
+    *evaluations = (int64_t)v;
+    return SL_OK;
+}
+
 int64_t sl_estimate_device_bytes(int64_t n, const sl_options *opt_in) {
     sl_options opt;
     if (opt_in) opt = *opt_in;
@@ -711,6 +759,8 @@ int64_t sl_estimate_device_bytes(int64_t n, const sl_options *opt_in) {
                   + R * (2 * sl::DIM + sl::NB + 1 + 9) // q, Fp, angular sums, E_i, virial parts
                   + R * 8 * cap + 2 * R * 4            // pair records, per-atom sums
                   + 2 * 32 + 5 * 32 + 3 * 4;           // evaluation outputs, snapshot, cell arrays
+    if (opt.midpoint_iters > 0)                        // midpoint positions and spins, iterate, image, rings
+        per += 4 * 32 + 2 * 16 + (opt.anderson_depth > 0 ? 2 * 32 * (opt.anderson_depth + 1) : 0);
     return n * per + (1 << 20);
 }
 
@@ -726,8 +776,9 @@ int sl_step_profiled(sl_system *sys, int64_t n_steps, double dt, double T, const
     if (s.n == 0 || n_steps == 0) { s.step += (uint64_t)n_steps; return SL_OK; }
     CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
     // events per step: before first half, before rebuild, before each evaluation kernel (5), after the
-    // last one, after second half
-    const int EV = 9;
+    // last one, after second half, and after the rebuild (e[9]): in the midpoint mode the iteration
+    // runs between e[9] and e[2] and counts as spin update (second-half group)
+    const int EV = 10;
     std::vector<cudaEvent_t> ev((size_t)EV * n_steps);
     for (auto &e : ev) CK(cudaEventCreate(&e));
     for (int64_t t = 0; t < n_steps; ++t) {
@@ -736,17 +787,26 @@ int sl_step_profiled(sl_system *sys, int64_t n_steps, double dt, double T, const
         sl::launch_first_half(s);
         CK(cudaEventRecord(e[1], s.stream));
         sl::launch_rebuild(s, true);
+        CK(cudaEventRecord(e[9], s.stream));
+        sl::launch_midpoint(s);
         sl::launch_eval(s, false, e + 2);   // e[2..7]
-        sl::launch_second_half(s);
+        if (s.mid_iters > 0) sl::launch_second_half_nospin(s);
+        else sl::launch_second_half(s);
         CK(cudaEventRecord(e[8], s.stream));
     }
     CK(cudaGetLastError());
-    s.n_launches += n_steps * sl::KERNELS_PER_STEP;
+    s.n_launches += n_steps * kernels_per_step(s);
     rc = check_status(s);
     for (int64_t t = 0; t < n_steps && rc == SL_OK; ++t) {
         cudaEvent_t *e = ev.data() + EV * t;
         float ms;
-        for (int k = 0; k < SL_NKERNELS; ++k) {
+        CK(cudaEventElapsedTime(&ms, e[0], e[1]));
+        kernel_ms[SL_K_FIRST_HALF] += ms;
+        CK(cudaEventElapsedTime(&ms, e[1], e[9]));
+        kernel_ms[SL_K_REBUILD] += ms;
+        CK(cudaEventElapsedTime(&ms, e[9], e[2]));
+        kernel_ms[SL_K_SECOND_HALF] += ms;
+        for (int k = SL_K_COMPACT; k <= SL_K_SECOND_HALF; ++k) {
             CK(cudaEventElapsedTime(&ms, e[k], e[k + 1]));
             kernel_ms[k] += ms;
         }

@@ -288,5 +288,6 @@ __device__ __forceinline__ void gauss3f(uint64_t step, uint64_t atom, uint64_t s
 constexpr int ST_NBR_OVERFLOW = 1;
 constexpr int ST_NONFINITE = 2;
 constexpr int ST_TIMEOUT = 4;
+constexpr int ST_MID_RANGE = 8;     // midpoint configuration beyond the neighbour-list skin
 
 }  // namespace sl

@@ -204,6 +204,7 @@ __device__ __forceinline__ void crad_atom(const NepDev<R> &P, const Eval2Args<R>
 
 template <typename R>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_crad(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+    if (a.skip && *a.skip) return;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     if (i < a.n_fe) crad_atom<R, 0>(P, a, i);
@@ -249,6 +250,7 @@ __device__ __forceinline__ void ang_stage_fwd(const NepDev<R> &P, const Eval2Arg
 
 template <typename R>
 __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+    if (a.skip && *a.skip) return;
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int quad = lane >> 2, ql = lane & 3;
@@ -562,6 +564,7 @@ __device__ __forceinline__ void bwd_rows(const NepDev<R> &P, const Eval2Args<R> 
 
 template <typename R>
 __global__ void __launch_bounds__(128) k_bwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+    if (a.skip && *a.skip) return;
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int quad = lane >> 2, ql = lane & 3;
@@ -651,15 +654,17 @@ __global__ void __launch_bounds__(128) k_bwd(const __grid_constant__ NepDev<R> P
 template <typename R>
 static Eval2Args<R> args2(Sys &s, bool want_virial) {
     Eval2Args<R> a;
+    // the evaluation point: the state, or the one set in s.at (midpoint iteration)
     if constexpr (sizeof(R) == 8) {
-        a.pos = reinterpret_cast<const v4<R> *>(s.pos);
-        a.spin = reinterpret_cast<const v4<R> *>(s.spin);
+        a.pos = reinterpret_cast<const v4<R> *>(s.at.pos ? s.at.pos : s.pos);
+        a.spin = reinterpret_cast<const v4<R> *>(s.at.spin ? s.at.spin : s.spin);
         a.box = *reinterpret_cast<const BoxDev<R> *>(&s.boxd);
     } else {
-        a.pos = reinterpret_cast<const v4<R> *>(s.posf);
-        a.spin = reinterpret_cast<const v4<R> *>(s.spinf);
+        a.pos = reinterpret_cast<const v4<R> *>(s.at.posf ? s.at.posf : s.posf);
+        a.spin = reinterpret_cast<const v4<R> *>(s.at.spinf ? s.at.spinf : s.spinf);
         a.box = *reinterpret_cast<const BoxDev<R> *>(&s.boxf);
     }
+    a.skip = s.at.skip;
     a.nbr = s.nbr; a.seg = s.seg; a.rev = s.rev; a.n = s.n; a.n_fe = s.n_fe;
     a.cap = s.cap; a.cap_ang = s.cap_ang;
     a.clj = s.clj; a.cls = s.cls; a.cnt = s.cnt;

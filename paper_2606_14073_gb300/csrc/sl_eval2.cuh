@@ -35,6 +35,7 @@ struct Eval2Args {
     R *wpart;
     int want_virial;
     int *status;
+    const int *skip;   // non-null and set: every evaluation kernel returns at once
 };
 
 }  // namespace sl

@@ -15,12 +15,15 @@
 // the predictor's eta bit for bit, so nothing is stored between the halves.
 #include "sl_internal.h"
 #include "sl_eval2.cuh"
+#include "sl_spin.cuh"
 
 namespace sl {
 
 struct IntArgs {
     double4 *pos, *vel, *spin, *spin_prev, *F, *H, *posref;
     float4 *posf, *spinf;
+    double4 *posmid;    // non-null in the midpoint mode: lattice midpoint of the step
+    float4 *posmidf;
     const int32_t *orig;
     int64_t n, n_fe;
     BoxDev<double> bd;
@@ -31,60 +34,7 @@ struct IntArgs {
     uint64_t seed, replica;
 };
 
-template <typename R>
-struct GatherArgs {
-    const v4<R> *fown, *gii;
-    const PairRec<R> *pd;
-    const uint16_t *cls;
-    const int4 *cnt;
-    int64_t n;
-    int cap_ang;
-};
 
-__device__ __forceinline__ void omega_of(double sx, double sy, double sz, double hx, double hy, double hz,
-                                         double lam, double k, double w[3]) {
-    w[0] = (hx + lam * (sy * hz - sz * hy)) * k;
-    w[1] = (hy + lam * (sz * hx - sx * hz)) * k;
-    w[2] = (hz + lam * (sx * hy - sy * hx)) * k;
-}
-
-__device__ __forceinline__ void rotate(double sx, double sy, double sz, const double w[3], double dt, double out[3]) {
-    const double wn2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-    if (wn2 == 0.0) { out[0] = sx; out[1] = sy; out[2] = sz; return; }
-    const double wn = sqrt(wn2);
-    const double ax = w[0] / wn, ay = w[1] / wn, az = w[2] / wn;
-    double s, c;
-    sincos(wn * dt, &s, &c);
-    const double as = ax * sx + ay * sy + az * sz;
-    const double cx = ay * sz - az * sy, cy = az * sx - ax * sz, cz = ax * sy - ay * sx;
-    out[0] = sx * c + cx * s + ax * as * (1.0 - c);
-    out[1] = sy * c + cy * s + ay * as * (1.0 - c);
-    out[2] = sz * c + cz * s + az * as * (1.0 - c);
-}
-
-// Rotation increment dS = Rot(S, w dt) - S in FP32 (added to the FP64 spin by the
-// caller): dS = (a x S) sin(th) - 2 sin^2(th/2) (S - a (a.S)), th = |w| dt.
-__device__ __forceinline__ void rotate_delta_f(float sx, float sy, float sz, float wx, float wy, float wz, float dt,
-                                               float d[3]) {
-    const float wn2 = wx * wx + wy * wy + wz * wz;
-    if (wn2 == 0.0f) { d[0] = d[1] = d[2] = 0.0f; return; }
-    const float iw = rsqrtf(wn2);
-    const float ax = wx * iw, ay = wy * iw, az = wz * iw;
-    float sh, ch;
-    sincosf(0.5f * wn2 * iw * dt, &sh, &ch);
-    const float sn = 2.0f * sh * ch, omc = 2.0f * sh * sh;
-    const float as = ax * sx + ay * sy + az * sz;
-    d[0] = (ay * sz - az * sy) * sn - omc * (sx - ax * as);
-    d[1] = (az * sx - ax * sz) * sn - omc * (sy - ay * as);
-    d[2] = (ax * sy - ay * sx) * sn - omc * (sz - az * as);
-}
-
-__device__ __forceinline__ void omega_of_f(float sx, float sy, float sz, float hx, float hy, float hz, float lam,
-                                           float k, float w[3]) {
-    w[0] = (hx + lam * (sy * hz - sz * hy)) * k;
-    w[1] = (hy + lam * (sz * hx - sx * hz)) * k;
-    w[2] = (hz + lam * (sx * hy - sy * hx)) * k;
-}
 
 template <bool MIXED>
 __global__ void __launch_bounds__(256) k_first_half(IntArgs a) {
@@ -108,11 +58,20 @@ __global__ void __launch_bounds__(256) k_first_half(IntArgs a) {
         gauss3(st, id, 1, a.seed, a.replica, xi);
         gauss3(st, id, 2, a.seed, a.replica, ze);
     }
+    const double4 r0 = r;
     v.x += hdt * F.x * am; v.y += hdt * F.y * am; v.z += hdt * F.z * am;
     r.x += hdt * v.x; r.y += hdt * v.y; r.z += hdt * v.z;
     const double c = P.c_fric, sv = P.sig_v[t];
     v.x = c * v.x + sv * xi[0]; v.y = c * v.y + sv * xi[1]; v.z = c * v.z + sv * xi[2];
     r.x += hdt * v.x; r.y += hdt * v.y; r.z += hdt * v.z;
+    if (a.posmid) {   // lattice midpoint r0 + (r - r0)/2 of the unwrapped step, then wrapped
+        double m3[3] = {r0.x + 0.5 * (r.x - r0.x), r0.y + 0.5 * (r.y - r0.y), r0.z + 0.5 * (r.z - r0.z)};
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (a.per[d]) m3[d] = m3[d] - a.bd.L[d] * floor(m3[d] * a.bd.invL[d]);
+        a.posmid[i] = make_double4(m3[0], m3[1], m3[2], 0.0);
+        a.posmidf[i] = make_float4((float)m3[0], (float)m3[1], (float)m3[2], 0.f);
+    }
     if (a.per[0]) r.x = r.x - a.bd.L[0] * floor(r.x * a.bd.invL[0]);
     if (a.per[1]) r.y = r.y - a.bd.L[1] * floor(r.y * a.bd.invL[1]);
     if (a.per[2]) r.z = r.z - a.bd.L[2] * floor(r.z * a.bd.invL[2]);
@@ -144,29 +103,9 @@ __global__ void __launch_bounds__(256) k_first_half(IntArgs a) {
     if (dx * dx + dy * dy + dz * dz > P.disp2) *a.rebuild = 1;
 }
 
-// F_k = sum_j dE_k/dr_kj - sum_j dE_j/dr_jk, H_k = -dE_k/dS_k - sum_j dE_j/dS_k: the
-// records (dE_j/dr_jk, dE_j/dS_k) sit in k's own in-cutoff slots.
-template <typename R>
-__device__ __forceinline__ void gather(const GatherArgs<R> &g, int64_t k, double F[3], double H[3]) {
-    const v4<R> fo = g.fown[k], gi = g.gii[k];
-    R fx = fo.x, fy = fo.y, fz = fo.z, hx = -gi.x, hy = -gi.y, hz = -gi.z;
-    const int4 c = g.cnt[k];
-    const int64_t N = g.n;
-#pragma unroll 1
-    for (int part = 0; part < 2; ++part) {
-        const int lo = part ? g.cap_ang : 0, hi = part ? g.cap_ang + c.w : c.y;
-        for (int row = lo; row < hi; ++row) {
-            const int s = g.cls[(int64_t)row * N + k] & 0xff;
-            const PairRec<R> e = g.pd[(int64_t)s * N + k];
-            fx -= e.a.x; fy -= e.a.y; fz -= e.a.z;
-            hx -= e.a.w; hy -= e.b.x; hz -= e.b.y;
-        }
-    }
-    F[0] = (double)fx; F[1] = (double)fy; F[2] = (double)fz;
-    H[0] = (double)hx; H[1] = (double)hy; H[2] = (double)hz;
-}
-
-template <typename R, bool MIXED>
+// SPIN = false (midpoint mode): the spins were already advanced by the midpoint
+// iteration; only the gather, the final kick and the carried F, H remain.
+template <typename R, bool MIXED, bool SPIN = true>
 __global__ void __launch_bounds__(256) k_second_half(IntArgs a, GatherArgs<R> g) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i == 0) a.step[0] = a.step[1] + 1;
@@ -178,6 +117,18 @@ __global__ void __launch_bounds__(256) k_second_half(IntArgs a, GatherArgs<R> g)
     double Fs[3], Hs[3];
     gather<R>(g, i, Fs, Hs);
     Hs[0] += P.zee[t][0]; Hs[1] += P.zee[t][1]; Hs[2] += P.zee[t][2];
+    if constexpr (!SPIN) {
+        double4 v = a.vel[i];
+        const double hdt = P.half_dt, am = P.acc_m[t];
+        v.x += hdt * Fs[0] * am; v.y += hdt * Fs[1] * am; v.z += hdt * Fs[2] * am;
+        a.vel[i] = v;
+        a.F[i] = make_double4(Fs[0], Fs[1], Fs[2], 0.0);
+        a.H[i] = make_double4(Hs[0], Hs[1], Hs[2], 0.0);
+        if (!(isfinite(Fs[0]) && isfinite(Fs[1]) && isfinite(Fs[2]) && isfinite(Hs[0]) && isfinite(Hs[1]) &&
+              isfinite(Hs[2])))
+            atomicOr(a.status, ST_NONFINITE);
+        return;
+    }
     const double se = P.sig_eta;
     const double4 S0 = a.spin_prev[i], S1 = a.spin[i], H0 = a.H[i];
     double Sn[3];
@@ -242,6 +193,8 @@ static IntArgs int_args(Sys &s) {
     for (int d = 0; d < 3; ++d) a.per[d] = s.per[d];
     a.par = s.d_par; a.step = s.d_step; a.rebuild = s.rebuild; a.status = s.status;
     a.seed = s.seed; a.replica = s.replica;
+    a.posmid = s.mid_iters > 0 ? s.posmid : nullptr;
+    a.posmidf = s.mid_iters > 0 ? s.posmidf : nullptr;
     return a;
 }
 
@@ -264,6 +217,12 @@ void launch_second_half(Sys &s) {
     if (s.prec == 0)
         k_second_half<double, false><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<double>(s));
     else k_second_half<float, true><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<float>(s));
+}
+
+void launch_second_half_nospin(Sys &s) {
+    if (s.prec == 0)
+        k_second_half<double, false, false><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<double>(s));
+    else k_second_half<float, true, false><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<float>(s));
 }
 
 void launch_gather(Sys &s, bool carried) {

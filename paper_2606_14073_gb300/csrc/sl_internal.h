@@ -25,6 +25,25 @@ struct StepDev {
     double disp2;               // (skin/2)^2, rebuild threshold
 };
 
+// Device control block of the self-consistent midpoint iteration.
+constexpr int MID_MAX_ITERS = 64;    // largest accepted iteration cap
+constexpr int AA_MAX_DEPTH = 8;      // largest accepted Anderson history
+struct MidDev {
+    int converged;                                   // set once the step's iteration has stopped
+    int fallback;                                    // Anderson solve unusable this iteration
+    unsigned long long resid[MID_MAX_ITERS];         // max_i |G_i - X_i| per iteration (FP64 bits)
+    unsigned long long iters;                        // midpoint evaluations executed, all steps
+    double gamma[AA_MAX_DEPTH];                      // Anderson coefficients of the current iteration
+};
+
+// Where an evaluation reads positions and spins (null: the state arrays) and an
+// optional device flag that makes the evaluation kernels return at once.
+struct EvalAt {
+    const double4 *pos = nullptr, *spin = nullptr;
+    const float4 *posf = nullptr, *spinf = nullptr;
+    const int *skip = nullptr;
+};
+
 struct Cells {
     int nc[3];
     int ncell;
@@ -99,6 +118,21 @@ struct Sys {
     int graph_steps = 0;
     // snapshot for error recovery
     double4 *snap = nullptr;   // 5 n: pos, vel, spin, F, H
+
+    // evaluation point used by launch_eval / launch_network while it is set
+    EvalAt at;
+
+    // self-consistent midpoint spin update (mid_iters = 0: predictor-corrector)
+    int mid_iters = 0, aa_depth = 0;
+    double mid_tol = 0.0, aa_reg = 1e-10;
+    double4 *posmid = nullptr;   // lattice midpoint of the step
+    float4 *posmidf = nullptr;
+    double4 *mids = nullptr;     // midpoint spins (evaluation point of the iteration)
+    float4 *midsf = nullptr;
+    double4 *mx = nullptr, *mg = nullptr;        // iterate X and its image G
+    double4 *aax = nullptr, *aag = nullptr;      // Anderson rings [(depth + 1)][n]
+    double *aapart = nullptr;                    // Anderson partial sums [AA_BLOCKS][...]
+    MidDev *md = nullptr;
 };
 
 // launchers (sl_neighbors.cu)
@@ -117,6 +151,12 @@ constexpr int KERNELS_PER_STEP = 1 + 7 + 2 + 1 + 1 + 1;
 // sl_integrate.cu
 void launch_first_half(Sys &s);
 void launch_second_half(Sys &s);
+void launch_second_half_nospin(Sys &s);   // gather and final kick only (midpoint mode)
+// sl_midpoint.cu: the iteration of one step between the first half and the final evaluation;
+// returns the number of kernels it queued
+int launch_midpoint(Sys &s);
+int midpoint_kernels_per_step(const Sys &s);
+size_t midpoint_scratch_doubles();
 void launch_gather(Sys &s, bool carried);
 void launch_mark_rebuild(Sys &s);
 int reduce_energy_virial(Sys &s, double *E, double *W, bool want_virial);

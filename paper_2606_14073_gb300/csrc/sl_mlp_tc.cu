@@ -131,7 +131,9 @@ __device__ __forceinline__ void split8(const float x[8], uint4 &hi, uint4 &lo) {
 
 __global__ void __launch_bounds__(128, 1) k_mlp_tc(const __grid_constant__ NepDev<float> P, const float *__restrict__ q,
                                                    float *__restrict__ fp, float *__restrict__ ei, int64_t n,
-                                                   int *status) {
+                                                   int *status, const int *skip) {
+    // uniform for the whole CTA and before any shared-memory or TMEM use
+    if (skip && *skip) return;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
@@ -313,7 +315,7 @@ void launch_network_tc(Sys &s) {
     const int64_t ntiles = (s.n + tc::TM - 1) / tc::TM;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * 2);
     tc::k_mlp_tc<<<grid, 128, tc::SMEM_BYTES, s.stream>>>(s.pf, (const float *)s.q, (float *)s.fp, (float *)s.ei, s.n,
-                                                       s.status);
+                                                       s.status, s.at.skip);
 }
 
 }  // namespace sl

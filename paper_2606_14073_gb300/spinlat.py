@@ -23,7 +23,7 @@ EXPORTS = ["sl_default_options", "sl_create_system", "sl_step", "sl_energy_force
            "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_get_stream",
            "sl_destroy_system", "sl_last_error", "sl_batch_create", "sl_batch_step", "sl_batch_destroy",
            "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak", "sl_descriptors_energies_noalloc",
-           "sl_estimate_device_bytes"]
+           "sl_estimate_device_bytes", "sl_get_midpoint_evaluations"]
 KERNEL_GROUPS = ["first_half", "rebuild", "compact", "rad_fwd", "ang_fwd", "network", "backward", "second_half"]
 
 
@@ -44,7 +44,8 @@ class sl_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("seed", C.c_uint64), ("replica", C.c_uint64), ("skin", C.c_double),
                 ("gamma_lattice_per_fs", C.c_double), ("lambda_spin", C.c_double), ("midpoint_iters", C.c_int32),
                 ("nbr_cap_rad", C.c_int32), ("nbr_cap_ang", C.c_int32), ("steps_per_graph", C.c_int32),
-                ("cuda_stream", C.c_void_p), ("device", C.c_int32)]
+                ("cuda_stream", C.c_void_p), ("device", C.c_int32), ("midpoint_tol", C.c_double),
+                ("anderson_depth", C.c_int32), ("anderson_reg", C.c_double)]
 
 
 _lib = None
@@ -69,6 +70,7 @@ def lib(path: str | None = None):
             L.sl_set_state.argtypes = [P, P, P, P, P, P, P, C.c_uint64]
             L.sl_get_neighbors.argtypes = [P, I32, P, P, P, P]
             L.sl_get_info.argtypes = [P, P, P, P, P]
+            L.sl_get_midpoint_evaluations.argtypes = [P, P]
             L.sl_step_profiled.argtypes = [P, I64, D, D, P, P]
             L.sl_measure_fma_peak.argtypes = [I32, P, P]
             L.sl_descriptors_energies_noalloc.argtypes = [P, P, P, I64, P, P, P, P, P, P]
@@ -87,7 +89,7 @@ def lib(path: str | None = None):
             for f in ("sl_create_system", "sl_step", "sl_energy_forces_fields", "sl_get_descriptors",
                       "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_batch_create",
                       "sl_batch_step", "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak",
-                      "sl_descriptors_energies_noalloc"):
+                      "sl_descriptors_energies_noalloc", "sl_get_midpoint_evaluations"):
                 getattr(L, f).restype = C.c_int
             _lib = L
         return _lib
@@ -135,7 +137,8 @@ class System:
 
     def __init__(self, positions, spins, box, periodic, species, params: dict, velocities=None, *,
                  precision=SL_PREC_FP64, seed=1234, replica=0, skin=1.0, gamma=0.01, lam=0.1,
-                 cap_rad=160, cap_ang=64, steps_per_graph=10, stream=None, device=-1):
+                 cap_rad=160, cap_ang=64, steps_per_graph=10, stream=None, device=-1, midpoint_iters=0,
+                 midpoint_tol=0.0, anderson_depth=0, anderson_reg=1e-10):
         pos = _f64(positions)
         n = pos.shape[0]
         sp = _f64(spins)
@@ -150,6 +153,8 @@ class System:
         o.nbr_cap_rad, o.nbr_cap_ang, o.steps_per_graph = int(cap_rad), int(cap_ang), int(steps_per_graph)
         o.cuda_stream = stream
         o.device = int(device)
+        o.midpoint_iters, o.midpoint_tol = int(midpoint_iters), float(midpoint_tol)
+        o.anderson_depth, o.anderson_reg = int(anderson_depth), float(anderson_reg)
         self.options = o
         h = C.c_void_p()
         _check(lib().sl_create_system(_ptr(pos), _ptr(sp), _ptr(box_), _ptr(per), _ptr(spec), n, _ptr(vel),
@@ -159,6 +164,11 @@ class System:
         self.precision = int(precision)
 
     # -- C entry points
+    def midpoint_evaluations(self) -> int:
+        v = C.c_int64()
+        _check(lib().sl_get_midpoint_evaluations(self.handle, C.byref(v)))
+        return int(v.value)
+
     def step(self, n_steps: int, dt: float, T: float, B=(0.0, 0.0, 0.0)):
         Bv = _f64(B)
         _check(lib().sl_step(self.handle, int(n_steps), float(dt), float(T), _ptr(Bv)))

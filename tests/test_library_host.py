@@ -57,6 +57,11 @@ def _create(**kw):
     dict(skin=0.0),
     dict(cap_rad=300),
     dict(cap_ang=200, cap_rad=160),
+    dict(midpoint_iters=-1),
+    dict(midpoint_iters=65),                                      # above the iteration cap limit
+    dict(midpoint_iters=4, anderson_depth=9),
+    dict(midpoint_iters=4, midpoint_tol=-1e-3),
+    dict(midpoint_iters=4, anderson_reg=float("nan")),
 ])
 def test_invalid_arguments_rejected_before_device_use(bad):
     with pytest.raises(S.SpinlatError) as e:

@@ -32,7 +32,7 @@
  *            (spin-weighted angular group, Section 5.1.2)
  *  - network (Section 5.2.3 "ANN", one hidden tanh layer):
  *      E_i = sum_h w1_h tanh(sum_v W0_hv s_v q_v - b0_h) - b1;
- *  - Zeeman: E_Z = -sum_i mu_i mu_B B.S_i.
+ *  - Zeeman: E_Z = -sum_i mu_i mu_B B_i.S_i, B_i = B + (optional per-atom part).
  * The angular channels are evaluated here as the plain Legendre double sum over
  * neighbour pairs (their definition), not through spherical harmonics.
  *
@@ -81,7 +81,14 @@ typedef struct {
     double b1;
     const double *mass_amu;   /* [ns] */
     const double *moment_muB; /* [ns] */
+    const double *B_atoms;    /* [n][3] per-atom external field, T, added to the uniform B;
+                                 NULL: none (the same field on every atom)          */
 } or_params;
+
+/* External field on atom i: the uniform B plus the atom's own part. */
+static void field_at(const or_params *P, const double B[3], int64_t i, double out[3]) {
+    for (int c = 0; c < 3; ++c) out[c] = B[c] + (P->B_atoms ? P->B_atoms[3 * i + c] : 0.0);
+}
 
 typedef struct {
     double gamma_lattice;  /* 1/fs, Langevin friction of the lattice O-step   */
@@ -601,10 +608,11 @@ int or_evaluate(int64_t n, const double *pos, const double *spin, const int32_t 
     if (H) memset(H, 0, sizeof(double) * 3 * (size_t)n);
     for (int64_t i = 0; i < n; ++i) {
         Etot += Ea[i];
-        double zee = P->moment_muB[species[i]] * OR_MUB;
-        Etot -= zee * (B[0] * spin[3 * i] + B[1] * spin[3 * i + 1] + B[2] * spin[3 * i + 2]);
+        double zee = P->moment_muB[species[i]] * OR_MUB, Bi[3];
+        field_at(P, B, i, Bi);
+        Etot -= zee * (Bi[0] * spin[3 * i] + Bi[1] * spin[3 * i + 1] + Bi[2] * spin[3 * i + 2]);
         if (H)
-            for (int c = 0; c < 3; ++c) H[3 * i + c] += -Gs[3 * i + c] + zee * B[c];
+            for (int c = 0; c < 3; ++c) H[3 * i + c] += -Gs[3 * i + c] + zee * Bi[c];
         for (int64_t p = nl.off[i]; p < nl.off[i + 1]; ++p) {
             int64_t j = nl.idx[p];
             if (F)
@@ -667,8 +675,9 @@ int or_evaluate_subset(int64_t n, const double *pos, const double *spin, const i
     for (int64_t s = 0; s < m; ++s) {
         int64_t k = sample[s], ck = slot[k];
         double f[3] = {0, 0, 0}, h[3];
-        double zee = P->moment_muB[species[k]] * OR_MUB;
-        for (int c = 0; c < 3; ++c) h[c] = -Gs[3 * ck + c] + zee * B[c];
+        double zee = P->moment_muB[species[k]] * OR_MUB, Bk[3];
+        field_at(P, B, k, Bk);
+        for (int c = 0; c < 3; ++c) h[c] = -Gs[3 * ck + c] + zee * Bk[c];
         /* own pairs */
         for (int64_t p = nl.off[k], a = 0; p < nl.off[k + 1]; ++p, ++a)
             for (int c = 0; c < 3; ++c) f[c] += D[3 * (poff[ck] + a) + c];

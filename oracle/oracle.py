@@ -47,7 +47,7 @@ class _Params(C.Structure):
                 ("n_hidden", C.c_int32), ("rc_rad", C.c_double), ("rc_ang", C.c_double),
                 ("coeffs", C.c_void_p), ("q_scaler", C.c_void_p), ("w0", C.c_void_p),
                 ("b0", C.c_void_p), ("w1", C.c_void_p), ("b1", C.c_double),
-                ("mass_amu", C.c_void_p), ("moment_muB", C.c_void_p)]
+                ("mass_amu", C.c_void_p), ("moment_muB", C.c_void_p), ("B_atoms", C.c_void_p)]
 
 
 class _Dyn(C.Structure):
@@ -107,13 +107,16 @@ class Model:
         self.moment = _f64(p["moment_muB"]).ravel()
         self.dim = 1 + 13 * self.n_ch
 
-    def c_struct(self) -> _Params:
+    def c_struct(self, B_atoms=None) -> _Params:
+        """The C parameter block; B_atoms ([n][3] tesla, FP64 C-contiguous, kept alive by the
+        caller) is the optional per-atom part of the external field."""
         s = _Params()
         s.n_species, s.n_ch, s.basis_k, s.n_hidden = self.n_species, self.n_ch, self.basis_k, self.n_hidden
         s.rc_rad, s.rc_ang = self.rc_rad, self.rc_ang
         s.coeffs, s.q_scaler, s.w0 = _p(self.coeffs), _p(self.q_scaler), _p(self.w0)
         s.b0, s.w1, s.b1 = _p(self.b0), _p(self.w1), self.b1
         s.mass_amu, s.moment_muB = _p(self.mass), _p(self.moment)
+        s.B_atoms = None if B_atoms is None else _p(B_atoms)
         return s
 
 
@@ -178,13 +181,23 @@ def descriptors(model: Model, pos, spin, species, box, periodic):
     return q
 
 
-def evaluate(model: Model, pos, spin, species, box, periodic, B=(0.0, 0.0, 0.0)):
-    """Returns dict(E, Ei, F, H, W) at FP64."""
+def _batoms(B_atoms, n):
+    if B_atoms is None:
+        return None
+    b = _f64(B_atoms)
+    if b.shape != (n, 3):
+        raise ValueError("B_atoms must have shape (n, 3)")
+    return b
+
+
+def evaluate(model: Model, pos, spin, species, box, periodic, B=(0.0, 0.0, 0.0), B_atoms=None):
+    """Returns dict(E, Ei, F, H, W) at FP64; B_atoms is the optional per-atom field part."""
     pos, spin, species, box, periodic = _sys(pos, spin, species, box, periodic)
     n = pos.shape[0]
     E = np.zeros(1)
     Ei, F, H, W = np.zeros(n), np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(9)
-    P = model.c_struct()
+    ba = _batoms(B_atoms, n)
+    P = model.c_struct(ba)
     Bv = _f64(B)
     rc = lib().or_evaluate(n, _p(pos), _p(spin), _p(species), _p(box), _p(periodic), C.addressof(P), _p(Bv),
                            _p(E), _p(Ei), _p(F), _p(H), _p(W))
@@ -193,12 +206,13 @@ def evaluate(model: Model, pos, spin, species, box, periodic, B=(0.0, 0.0, 0.0))
     return dict(E=float(E[0]), Ei=Ei, F=F, H=H, W=W.reshape(3, 3))
 
 
-def evaluate_subset(model: Model, pos, spin, species, box, periodic, sample, B=(0.0, 0.0, 0.0)):
+def evaluate_subset(model: Model, pos, spin, species, box, periodic, sample, B=(0.0, 0.0, 0.0), B_atoms=None):
     pos, spin, species, box, periodic = _sys(pos, spin, species, box, periodic)
     sample = np.ascontiguousarray(sample, dtype=np.int64)
     m = sample.shape[0]
     F, H, Ei = np.zeros((m, 3)), np.zeros((m, 3)), np.zeros(m)
-    P = model.c_struct()
+    ba = _batoms(B_atoms, pos.shape[0])
+    P = model.c_struct(ba)
     Bv = _f64(B)
     rc = lib().or_evaluate_subset(pos.shape[0], _p(pos), _p(spin), _p(species), _p(box), _p(periodic),
                                   C.addressof(P), _p(Bv), m, _p(sample), _p(F), _p(H), _p(Ei))
@@ -224,12 +238,14 @@ class State:
 
 def run(model: Model, st: State, n_steps: int, dt: float, T: float, B=(0.0, 0.0, 0.0), *,
         gamma=0.01, lam=0.1, seed=1234, replica=0, midpoint_iters=0, midpoint_tol=0.0, anderson_depth=0,
-        anderson_reg=1e-10):
+        anderson_reg=1e-10, B_atoms=None):
     """Advance st by n_steps steps (or_run).  midpoint_iters > 0 selects the self-consistent
     midpoint spin update (cap of the iteration, tolerance midpoint_tol, optional Anderson
     history anderson_depth with relative regularisation anderson_reg).  Returns st; the
-    number of midpoint evaluations of the call is in st.last_iterations."""
-    P = model.c_struct()
+    number of midpoint evaluations of the call is in st.last_iterations.  B_atoms is the
+    optional per-atom part of the external field ([n][3] tesla)."""
+    ba = _batoms(B_atoms, st.pos.shape[0])
+    P = model.c_struct(ba)
     dyn = _Dyn(gamma, lam, seed, replica, int(midpoint_iters), int(anderson_depth), float(midpoint_tol),
                float(anderson_reg))
     Bv = _f64(B)

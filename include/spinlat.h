@@ -173,6 +173,27 @@ int64_t sl_estimate_device_bytes(int64_t n, const sl_options *opt);
 int sl_get_info(const sl_system *sys, int64_t *n_atoms, int32_t *precision, int64_t *n_builds,
                 int64_t *n_launches);
 
+/* Per-atom part of the external field: B_atoms [n][3] in tesla, caller atom order,
+ * copied in; the field on atom i is then B (the sl_step argument) + B_atoms[i], in
+ * the Zeeman energy -mu_i mu_B B_i.S_i, the fields and the energy.  NULL removes it.
+ * The paper's production protocol uses a field that steps along x (Fig. 7).
+ * SL_EINVAL for a non-finite entry. */
+int sl_set_atom_fields(sl_system *sys, const double *B_atoms);
+
+/* Texture diagnostics of a film with normal normal_axis (0, 1, 2), computed on the
+ * device at the current state (Fig. 7 and Section 8 follow helix and skyrmion textures
+ * in a thin stripe).  The two in-plane axes a < b are cut into n_a = max(1, floor(L_a /
+ * cell)) and n_b cells (atoms beyond a non-periodic edge go to the edge cell);
+ * m [n_b][n_a][3] (may be NULL) receives the normalised spin sum of every column (zero
+ * for an empty column) and Q (may be NULL) the Berg-Luescher lattice topological charge:
+ * every plaquette gives two counter-clockwise triangles, each contributing its signed
+ * solid angle 2 atan2(m1.(m2 x m3), 1 + m1.m2 + m2.m3 + m3.m1); Q = sum / 4 pi, plaquettes
+ * wrapping across periodic in-plane axes only.  With m and Q both NULL only n_a, n_b
+ * are returned.  Results are deterministic.  SL_EINVAL for a bad axis or cell, or more
+ * than 2^28 cells. */
+int sl_texture_map(sl_system *sys, int32_t normal_axis, double cell, int32_t *n_a, int32_t *n_b, double *m,
+                   double *Q);
+
 /* Midpoint evaluations executed by all steps so far (0 in the predictor-corrector
  * mode); the mean iteration count per step is this over the steps taken. */
 int sl_get_midpoint_evaluations(const sl_system *sys, int64_t *evaluations);

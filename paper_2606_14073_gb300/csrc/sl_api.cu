@@ -105,7 +105,8 @@ void free_sys(sl::Sys &s) {
                     s.cells.of, s.q, s.bsum, s.fp, s.ei, s.pairs, s.clj, s.cls, s.cnt, s.fown, s.gii,
                     s.wpart, s.Fo, s.Ho,
                     s.status, s.rebuild, s.d_step, s.d_par, s.red, s.snap, s.d_builds,
-                    s.posmid, s.posmidf, s.mids, s.midsf, s.mx, s.mg, s.aax, s.aag, s.aapart, s.md};
+                    s.posmid, s.posmidf, s.mids, s.midsf, s.mx, s.mg, s.aax, s.aag, s.aapart, s.md, s.Bat,
+                    s.tex_acc, s.tex_m, s.tex_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (s.h_par) cudaFreeHost(s.h_par);
@@ -124,6 +125,7 @@ void compute_step_params(const sl::Sys &s, double dt, double T, const double B[3
         P.acc_m[t] = ACC / s.mass[t];
         P.sig_v[t] = T > 0 ? std::sqrt((1.0 - P.c_fric * P.c_fric) * KB * T * ACC / s.mass[t]) : 0.0;
         for (int c = 0; c < 3; ++c) P.zee[t][c] = s.moment[t] * MUB * B[c];
+        P.mom[t] = s.moment[t] * MUB;
     }
     P.sig_eta = (T > 0 && s.lambda > 0 && dt > 0) ? std::sqrt(2.0 * s.lambda * KB * T * HBAR / dt) : 0.0;
     P.lambda = s.lambda;
@@ -728,6 +730,60 @@ int sl_get_info(const sl_system *sys, int64_t *n_atoms, int32_t *precision, int6
         *n_builds = (int64_t)b;
     }
     if (n_launches) *n_launches = s.n_launches;
+    return SL_OK;
+}
+
+int sl_set_atom_fields(sl_system *sys, const double *B_atoms) {
+    if (!sys) return fail(SL_EINVAL, "NULL system");
+    sl::Sys &s = sys->s;
+    cudaSetDevice(s.device);
+    // a captured step graph holds the field pointer: drop it whenever the pointer changes
+    auto drop_graph = [&]() {
+        if (s.graph) {
+            cudaGraphExecDestroy(s.graph);
+            s.graph = nullptr;
+            s.graph_steps = 0;
+        }
+    };
+    if (!B_atoms) {
+        if (s.Bat) {
+            CK(cudaStreamSynchronize(s.stream));
+            cudaFree(s.Bat);
+            s.Bat = nullptr;
+            drop_graph();
+        }
+        return SL_OK;
+    }
+    for (int64_t k = 0; k < 3 * s.n; ++k)
+        if (!std::isfinite(B_atoms[k])) return fail(SL_EINVAL, "non-finite per-atom field entry %lld", (long long)k);
+    int rc;
+    if (!s.Bat) {
+        if ((rc = dalloc(&s.Bat, (size_t)(s.n > 0 ? s.n : 1)))) return rc;
+        drop_graph();
+    }
+    if (s.n > 0 && (rc = upload_vec(s, s.Bat, B_atoms, false))) return rc;
+    return SL_OK;
+}
+
+int sl_texture_map(sl_system *sys, int32_t normal_axis, double cell, int32_t *n_a, int32_t *n_b, double *m,
+                   double *Q) {
+    if (!sys || !n_a || !n_b) return fail(SL_EINVAL, "NULL argument");
+    if (normal_axis < 0 || normal_axis > 2) return fail(SL_EINVAL, "normal_axis must be 0, 1 or 2");
+    if (!(cell > 0) || !std::isfinite(cell)) return fail(SL_EINVAL, "cell must be positive");
+    sl::Sys &s = sys->s;
+    int na, nb;
+    sl::texture_grid(s, normal_axis, cell, &na, &nb);
+    if ((int64_t)na * nb > (int64_t)1 << 28) return fail(SL_EINVAL, "texture grid of %d x %d cells is too large", na, nb);
+    *n_a = na;
+    *n_b = nb;
+    if (!m && !Q) return SL_OK;
+    cudaSetDevice(s.device);
+    const cudaError_t e = sl::launch_texture(s, normal_axis, cell, m, Q);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? fail(SL_ENOMEM, "texture scratch: %s", cudaGetErrorString(e))
+                                              : cuda_fail(e, "texture diagnostics");
+    }
     return SL_OK;
 }
 

@@ -24,6 +24,7 @@ struct IntArgs {
     float4 *posf, *spinf;
     double4 *posmid;    // non-null in the midpoint mode: lattice midpoint of the step
     float4 *posmidf;
+    const double4 *Bat; // non-null: per-atom part of the external field (tesla)
     const int32_t *orig;
     int64_t n, n_fe;
     BoxDev<double> bd;
@@ -117,6 +118,10 @@ __global__ void __launch_bounds__(256) k_second_half(IntArgs a, GatherArgs<R> g)
     double Fs[3], Hs[3];
     gather<R>(g, i, Fs, Hs);
     Hs[0] += P.zee[t][0]; Hs[1] += P.zee[t][1]; Hs[2] += P.zee[t][2];
+    if (a.Bat) {
+        const double4 b = a.Bat[i];
+        Hs[0] += P.mom[t] * b.x; Hs[1] += P.mom[t] * b.y; Hs[2] += P.mom[t] * b.z;
+    }
     if constexpr (!SPIN) {
         double4 v = a.vel[i];
         const double hdt = P.half_dt, am = P.acc_m[t];
@@ -171,13 +176,17 @@ __global__ void __launch_bounds__(256) k_second_half(IntArgs a, GatherArgs<R> g)
 // Forces and fields at the current state into (Fo, Ho).
 template <typename R>
 __global__ void __launch_bounds__(256) k_gather_only(GatherArgs<R> g, const StepDev *par, int64_t n_fe,
-                                                     double4 *Fo, double4 *Ho, int *status) {
+                                                     double4 *Fo, double4 *Ho, int *status, const double4 *Bat) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     const int t = i < n_fe ? 0 : 1;
     double Fs[3], Hs[3];
     gather<R>(g, i, Fs, Hs);
     Hs[0] += par->zee[t][0]; Hs[1] += par->zee[t][1]; Hs[2] += par->zee[t][2];
+    if (Bat) {
+        const double4 b = Bat[i];
+        Hs[0] += par->mom[t] * b.x; Hs[1] += par->mom[t] * b.y; Hs[2] += par->mom[t] * b.z;
+    }
     Fo[i] = make_double4(Fs[0], Fs[1], Fs[2], 0.0);
     Ho[i] = make_double4(Hs[0], Hs[1], Hs[2], 0.0);
     if (!(isfinite(Fs[0]) && isfinite(Fs[1]) && isfinite(Fs[2]) && isfinite(Hs[0]) && isfinite(Hs[1]) &&
@@ -195,6 +204,7 @@ static IntArgs int_args(Sys &s) {
     a.seed = s.seed; a.replica = s.replica;
     a.posmid = s.mid_iters > 0 ? s.posmid : nullptr;
     a.posmidf = s.mid_iters > 0 ? s.posmidf : nullptr;
+    a.Bat = s.Bat;
     return a;
 }
 
@@ -229,10 +239,10 @@ void launch_gather(Sys &s, bool carried) {
     double4 *Fo = carried ? s.F : s.Fo, *Ho = carried ? s.H : s.Ho;
     if (s.prec == 0)
         k_gather_only<double><<<nblk(s.n, 256), 256, 0, s.stream>>>(gather_args<double>(s), s.d_par, s.n_fe, Fo, Ho,
-                                                                    s.status);
+                                                                    s.status, s.Bat);
     else
         k_gather_only<float><<<nblk(s.n, 256), 256, 0, s.stream>>>(gather_args<float>(s), s.d_par, s.n_fe, Fo, Ho,
-                                                                   s.status);
+                                                                   s.status, s.Bat);
 }
 
 __global__ void k_set_flag(int *flag) { *flag = 1; }
@@ -248,7 +258,8 @@ constexpr int RED_VALS = 10;   // E_network + E_Zeeman, virial[9]
 template <typename R>
 __global__ void __launch_bounds__(256) k_reduce1(const R *__restrict__ ei, const R *__restrict__ wpart,
                                                  const double4 *__restrict__ spin, const StepDev *par, int64_t n,
-                                                 int64_t n_fe, int want_virial, double *__restrict__ part) {
+                                                 int64_t n_fe, int want_virial, double *__restrict__ part,
+                                                 const double4 *__restrict__ Bat) {
     __shared__ double sh[RED_VALS][256];
     double acc[RED_VALS];
 #pragma unroll
@@ -256,7 +267,12 @@ __global__ void __launch_bounds__(256) k_reduce1(const R *__restrict__ ei, const
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int t = i < n_fe ? 0 : 1;
         const double4 S = spin[i];
-        acc[0] += (double)ei[i] - (par->zee[t][0] * S.x + par->zee[t][1] * S.y + par->zee[t][2] * S.z);
+        double ez = par->zee[t][0] * S.x + par->zee[t][1] * S.y + par->zee[t][2] * S.z;
+        if (Bat) {
+            const double4 b = Bat[i];
+            ez += par->mom[t] * (b.x * S.x + b.y * S.y + b.z * S.z);
+        }
+        acc[0] += (double)ei[i] - ez;
         if (want_virial)
             for (int v = 0; v < 9; ++v) acc[1 + v] += (double)wpart[(int64_t)v * n + i];
     }
@@ -283,10 +299,10 @@ int reduce_energy_virial(Sys &s, double *E, double *W, bool want_virial) {
     double *part = s.red, *out = s.red + RED_BLOCKS * RED_VALS;
     if (s.prec == 0)
         k_reduce1<double><<<RED_BLOCKS, 256, 0, s.stream>>>((const double *)s.ei, (const double *)s.wpart, s.spin,
-                                                            s.d_par, s.n, s.n_fe, want_virial, part);
+                                                            s.d_par, s.n, s.n_fe, want_virial, part, s.Bat);
     else
         k_reduce1<float><<<RED_BLOCKS, 256, 0, s.stream>>>((const float *)s.ei, (const float *)s.wpart, s.spin,
-                                                           s.d_par, s.n, s.n_fe, want_virial, part);
+                                                           s.d_par, s.n, s.n_fe, want_virial, part, s.Bat);
     k_reduce2<<<1, 32, 0, s.stream>>>(part, out);
     cudaError_t e = cudaMemcpyAsync(s.h_red, out, sizeof(double) * RED_VALS, cudaMemcpyDeviceToHost, s.stream);
     if (e != cudaSuccess) return -1;

@@ -22,6 +22,7 @@ struct StepDev {
     double lambda;              // Gilbert damping
     double wscale;              // 1 / ((1 + lambda^2) hbar)
     double zee[NS][3];          // mu_t muB B  (Zeeman field per species)
+    double mom[NS];             // mu_t muB (scales the per-atom field part)
     double disp2;               // (skin/2)^2, rebuild threshold
 };
 
@@ -122,6 +123,15 @@ struct Sys {
     // evaluation point used by launch_eval / launch_network while it is set
     EvalAt at;
 
+    // per-atom part of the external field (tesla, internal order); null: uniform field only
+    double4 *Bat = nullptr;
+
+    // texture diagnostics scratch (sl_texture.cu), grown on demand
+    unsigned long long *tex_acc = nullptr;
+    double4 *tex_m = nullptr;
+    double *tex_part = nullptr;
+    int64_t tex_cells = 0;
+
     // self-consistent midpoint spin update (mid_iters = 0: predictor-corrector)
     int mid_iters = 0, aa_depth = 0;
     double mid_tol = 0.0, aa_reg = 1e-10;
@@ -157,6 +167,9 @@ void launch_second_half_nospin(Sys &s);   // gather and final kick only (midpoin
 int launch_midpoint(Sys &s);
 int midpoint_kernels_per_step(const Sys &s);
 size_t midpoint_scratch_doubles();
+// sl_texture.cu: film texture diagnostics (in-plane magnetisation map, topological charge)
+int texture_grid(const Sys &s, int normal, double cell, int *na, int *nb);
+cudaError_t launch_texture(Sys &s, int normal, double cell, double *h_m, double *Q);
 void launch_gather(Sys &s, bool carried);
 void launch_mark_rebuild(Sys &s);
 int reduce_energy_virial(Sys &s, double *E, double *W, bool want_virial);

@@ -38,6 +38,7 @@ struct MidArgs {
     double4 *Xh, *Gh;                  // Anderson rings [(depth + 1)][n]
     double *part;                      // [AA_BLOCKS][AA_VALS]
     const double4 *posmid, *posref;
+    const double4 *Bat;                // per-atom part of the external field, or null
     const int32_t *orig;
     int64_t n, n_fe;
     BoxDev<double> bd;
@@ -91,6 +92,10 @@ __global__ void __launch_bounds__(256) k_mid_update(MidArgs a, GatherArgs<R> g, 
     double Fs[3], Hs[3];
     gather<R>(g, i, Fs, Hs);
     Hs[0] += P.zee[t][0]; Hs[1] += P.zee[t][1]; Hs[2] += P.zee[t][2];
+    if (a.Bat) {
+        const double4 b = a.Bat[i];
+        Hs[0] += P.mom[t] * b.x; Hs[1] += P.mom[t] * b.y; Hs[2] += P.mom[t] * b.z;
+    }
     if (!(isfinite(Hs[0]) && isfinite(Hs[1]) && isfinite(Hs[2]))) atomicOr(a.status, ST_NONFINITE);
     const double4 S0 = a.spin_prev[i], M = a.mids[i], X = a.X[i];
     const unsigned long long st = a.step[1];
@@ -269,7 +274,7 @@ MidArgs mid_args(Sys &s) {
     MidArgs a;
     a.spin_prev = s.spin_prev; a.spin = s.spin; a.spinf = s.spinf;
     a.mids = s.mids; a.midsf = s.midsf; a.X = s.mx; a.G = s.mg; a.Xh = s.aax; a.Gh = s.aag; a.part = s.aapart;
-    a.posmid = s.posmid; a.posref = s.posref; a.orig = s.orig; a.n = s.n; a.n_fe = s.n_fe; a.bd = s.boxd;
+    a.posmid = s.posmid; a.posref = s.posref; a.Bat = s.Bat; a.orig = s.orig; a.n = s.n; a.n_fe = s.n_fe; a.bd = s.boxd;
     a.par = s.d_par; a.step = s.d_step; a.status = s.status; a.md = s.md; a.seed = s.seed; a.replica = s.replica;
     a.cap = s.mid_iters; a.depth = s.aa_depth; a.tol = s.mid_tol; a.reg = s.aa_reg;
     return a;

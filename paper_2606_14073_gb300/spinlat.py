@@ -23,7 +23,7 @@ EXPORTS = ["sl_default_options", "sl_create_system", "sl_step", "sl_energy_force
            "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_get_stream",
            "sl_destroy_system", "sl_last_error", "sl_batch_create", "sl_batch_step", "sl_batch_destroy",
            "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak", "sl_descriptors_energies_noalloc",
-           "sl_estimate_device_bytes", "sl_get_midpoint_evaluations"]
+           "sl_estimate_device_bytes", "sl_get_midpoint_evaluations", "sl_set_atom_fields", "sl_texture_map"]
 KERNEL_GROUPS = ["first_half", "rebuild", "compact", "rad_fwd", "ang_fwd", "network", "backward", "second_half"]
 
 
@@ -71,6 +71,8 @@ def lib(path: str | None = None):
             L.sl_get_neighbors.argtypes = [P, I32, P, P, P, P]
             L.sl_get_info.argtypes = [P, P, P, P, P]
             L.sl_get_midpoint_evaluations.argtypes = [P, P]
+            L.sl_set_atom_fields.argtypes = [P, P]
+            L.sl_texture_map.argtypes = [P, I32, D, P, P, P, P]
             L.sl_step_profiled.argtypes = [P, I64, D, D, P, P]
             L.sl_measure_fma_peak.argtypes = [I32, P, P]
             L.sl_descriptors_energies_noalloc.argtypes = [P, P, P, I64, P, P, P, P, P, P]
@@ -89,7 +91,8 @@ def lib(path: str | None = None):
             for f in ("sl_create_system", "sl_step", "sl_energy_forces_fields", "sl_get_descriptors",
                       "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_batch_create",
                       "sl_batch_step", "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak",
-                      "sl_descriptors_energies_noalloc", "sl_get_midpoint_evaluations"):
+                      "sl_descriptors_energies_noalloc", "sl_get_midpoint_evaluations", "sl_set_atom_fields",
+                      "sl_texture_map"):
                 getattr(L, f).restype = C.c_int
             _lib = L
         return _lib
@@ -164,6 +167,23 @@ class System:
         self.precision = int(precision)
 
     # -- C entry points
+    def set_atom_fields(self, B_atoms=None):
+        """Per-atom part of the external field ([n][3] tesla, caller order); None removes it."""
+        b = None if B_atoms is None else _f64(B_atoms)
+        if b is not None and b.shape != (self.n, 3):
+            raise ValueError("B_atoms must have shape (n, 3)")
+        _check(lib().sl_set_atom_fields(self.handle, _ptr(b)))
+
+    def texture(self, normal: int = 2, cell: float = 4.7):
+        """(m [n_b][n_a][3], Q): coarse-grained film magnetisation and topological charge."""
+        na, nb = C.c_int32(), C.c_int32()
+        _check(lib().sl_texture_map(self.handle, int(normal), float(cell), C.byref(na), C.byref(nb), None, None))
+        m = np.zeros((nb.value, na.value, 3))
+        q = C.c_double()
+        _check(lib().sl_texture_map(self.handle, int(normal), float(cell), C.byref(na), C.byref(nb), _ptr(m),
+                                    C.byref(q)))
+        return m, float(q.value)
+
     def midpoint_evaluations(self) -> int:
         v = C.c_int64()
         _check(lib().sl_get_midpoint_evaluations(self.handle, C.byref(v)))

@@ -87,3 +87,12 @@ def test_no_device_is_a_loud_error():
     with pytest.raises(S.SpinlatError) as e:
         _create()
     assert e.value.code == S.SL_ECUDA
+
+
+def test_texture_grid_validation_needs_no_device():
+    # argument checks come before any device work: a bad axis or cell is SL_EINVAL even
+    # without a system on a GPU (NULL system first)
+    import ctypes as C
+    na, nb = C.c_int32(), C.c_int32()
+    assert S.lib().sl_texture_map(None, 2, 4.7, C.byref(na), C.byref(nb), None, None) == S.SL_EINVAL
+    assert S.lib().sl_set_atom_fields(None, None) == S.SL_EINVAL

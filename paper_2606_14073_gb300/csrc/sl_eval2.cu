@@ -77,99 +77,163 @@ __device__ __forceinline__ R kappa_of_lm(int lm) {
 }
 
 // ------------------------------------------------------------------ k_crad
-// One thread per atom, one pass over the candidate list (which carries a skin):
-//  * compaction of the pairs inside the cutoffs into angular rows (r < rc_ang) and
-//    radial-only rows (rc_ang <= r < rc_rad), each grouped by neighbour species in
-//    candidate order (species 0 from candidate segments 0 and 2, then species 1 from
-//    1 and 3), for the angular and backward kernels and the gather;
-//  * the radial and pairwise-magnetic basis sums over the same pairs, contracted with
-//    the coefficients once per neighbour species (q^R, q^EX, q^DMI, q^ANI, q^SIA), and q^O.
-// Candidates go in batches of CB: the batch's list entries, reverse slots and
-// neighbour coordinates are all requested before any of them is used.
-constexpr int CB = 4;
+// One thread per atom, per neighbour species:
+//  A. the angular candidates (within rc_ang + skin of the list build, so nearly all inside
+//     rc_rad): compaction and the radial and pairwise-magnetic basis sums in one pass;
+//  B. the radial-shell candidates (rc_ang + skin .. rc_rad + skin at the build, fewer than
+//     half inside rc_rad): compaction only, a few instructions per candidate;
+//  C. the basis sums over the rows B produced.
+// Splitting B from C keeps a warp from running the pair arithmetic for every candidate of
+// the shell whenever one of its 32 atoms has that candidate inside the cutoff.  Rows are
+// angular (r < rc_ang) or radial-only (rc_ang <= r < rc_rad), each grouped by neighbour
+// species in candidate order (species 0 from candidate segments 0 and 2, then species 1
+// from 1 and 3), for the angular and backward kernels and the gather.  The sums are
+// contracted with the coefficients once per neighbour species (q^R, q^EX, q^DMI, q^ANI,
+// q^SIA); q^O = |S|^2.
+constexpr int CB = 4;    // candidates per batch in A
+constexpr int CBB = 4;   // candidates per batch in B
+
+template <typename R>
+struct RadSums {
+    R b0[NK], b1[NK], b2[NK], b3[NK], b4[NK];
+};
+
+template <typename R>
+__device__ __forceinline__ void rad_accumulate(const NepDev<R> &P, const v4<R> &si, const v4<R> &cs, R dx, R dy,
+                                               R dz, R d2, RadSums<R> &b) {
+    const R ir = rsqrt_(d2), r = d2 * ir;
+    const R ux = dx * ir, uy = dy * ir, uz = dz * ir;
+    R f[NK];
+    carrier_f(r, P.inv_rc_r, f);
+    const R sij = si.x * cs.x + si.y * cs.y + si.z * cs.z;
+    const R siu = si.x * ux + si.y * uy + si.z * uz;
+    const R sju = cs.x * ux + cs.y * uy + cs.z * uz;
+    const R dmi = (si.y * cs.z - si.z * cs.y) * ux + (si.z * cs.x - si.x * cs.z) * uy + (si.x * cs.y - si.y * cs.x) * uz;
+    const R ani = siu * sju, sia = siu * siu;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        b.b0[k] += f[k];
+        b.b1[k] += f[k] * sij;
+        b.b2[k] += f[k] * dmi;
+        b.b3[k] += f[k] * ani;
+        b.b4[k] += f[k] * sia;
+    }
+}
+
+// Row of an in-cutoff pair, or -1 (angular rows full: only after a list overflow).
+template <typename R>
+__device__ __forceinline__ int take_row(const NepDev<R> &P, const Eval2Args<R> &a, R d2, int &na, int &nr) {
+    if (d2 < P.rc_a2) {
+        if (na >= a.cap_ang) {
+            atomicOr(a.status, ST_NBR_OVERFLOW);
+            return -1;
+        }
+        return na++;
+    }
+    return a.cap_ang + nr++;
+}
 
 template <typename R, int TI, int TJ>
 __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, const v4<R> &pi,
                                              const v4<R> &si, int lo0, int hi0, int lo1, int hi1, int &na, int &nr) {
-    R b0[NK], b1[NK], b2[NK], b3[NK], b4[NK];
+    RadSums<R> b;
 #pragma unroll
-    for (int k = 0; k < NK; ++k) { b0[k] = b1[k] = b2[k] = b3[k] = b4[k] = R(0); }
+    for (int k = 0; k < NK; ++k) { b.b0[k] = b.b1[k] = b.b2[k] = b.b3[k] = b.b4[k] = R(0); }
     const int64_t N = a.n;
-    const int len0 = hi0 - lo0, len = len0 + (hi1 - lo1);
     const int32_t *__restrict__ nbr = a.nbr;
     const int32_t *__restrict__ rev = a.rev;
     const v4<R> *__restrict__ pos = a.pos;
     const v4<R> *__restrict__ spin = a.spin;
-    // list entries and reverse slots of the next batch are loaded while this batch is computed
-    int jn[CB], tn[CB];
+
+    // A: angular candidates, compaction and sums; the next batch's list entries are in flight
+    {
+        const int len = hi0 - lo0;
+        int jn[CB], tn[CB];
 #pragma unroll
-    for (int u = 0; u < CB; ++u) {
-        const int sl = u < len0 ? lo0 + u : lo1 + (u - len0);
-        jn[u] = u < len ? nbr[(int64_t)sl * N + i] : -1;
-        tn[u] = u < len ? rev[(int64_t)sl * N + i] : 0;
-    }
+        for (int u = 0; u < CB; ++u) {
+            jn[u] = u < len ? nbr[(int64_t)(lo0 + u) * N + i] : -1;
+            tn[u] = u < len ? rev[(int64_t)(lo0 + u) * N + i] : 0;
+        }
 #pragma unroll 1
-    for (int t0 = 0; t0 < len; t0 += CB) {
-        int sl[CB], jj[CB], tt[CB];
-        v4<R> pp[CB], ss[CB];
+        for (int t0 = 0; t0 < len; t0 += CB) {
+            int jj[CB], tt[CB];
+            v4<R> pp[CB], ss[CB];
 #pragma unroll
-        for (int u = 0; u < CB; ++u) {
-            const int t = t0 + u;
-            sl[u] = t < len0 ? lo0 + t : lo1 + (t - len0);
-            jj[u] = jn[u];
-            tt[u] = tn[u];
+            for (int u = 0; u < CB; ++u) { jj[u] = jn[u]; tt[u] = tn[u]; }
+#pragma unroll
+            for (int u = 0; u < CB; ++u) {
+                const int j = jj[u] >= 0 ? jj[u] : (int)i;
+                pp[u] = pos[j];
+                ss[u] = spin[j];
+            }
+#pragma unroll
+            for (int u = 0; u < CB; ++u) {
+                const int t = t0 + CB + u;
+                jn[u] = t < len ? nbr[(int64_t)(lo0 + t) * N + i] : -1;
+                tn[u] = t < len ? rev[(int64_t)(lo0 + t) * N + i] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < CB; ++u) {
+                if (jj[u] < 0) continue;
+                R dx, dy, dz;
+                sep(a.box, pi, pp[u], dx, dy, dz);
+                const R d2 = dx * dx + dy * dy + dz * dz;
+                if (!(d2 < P.rc_r2)) continue;
+                const int row = take_row(P, a, d2, na, nr);
+                if (row < 0) continue;
+                a.clj[(int64_t)row * N + i] = jj[u];
+                a.cls[(int64_t)row * N + i] = (uint16_t)((lo0 + t0 + u) | (tt[u] << 8));
+                rad_accumulate(P, si, ss[u], dx, dy, dz, d2, b);
+            }
         }
+    }
+    // B: radial-shell candidates, compaction only
+    const int naB = na, nrB = nr;
+    {
+        const int len = hi1 - lo1;
+#pragma unroll 1
+        for (int t0 = 0; t0 < len; t0 += CBB) {
+            int jj[CBB], tt[CBB];
+            v4<R> pp[CBB];
 #pragma unroll
-        for (int u = 0; u < CB; ++u) {
-            const int j = jj[u] >= 0 ? jj[u] : (int)i;
-            pp[u] = pos[j];
-            ss[u] = spin[j];
+            for (int u = 0; u < CBB; ++u) {
+                jj[u] = t0 + u < len ? nbr[(int64_t)(lo1 + t0 + u) * N + i] : -1;
+                tt[u] = t0 + u < len ? rev[(int64_t)(lo1 + t0 + u) * N + i] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < CBB; ++u) pp[u] = pos[jj[u] >= 0 ? jj[u] : (int)i];
+#pragma unroll
+            for (int u = 0; u < CBB; ++u) {
+                if (jj[u] < 0) continue;
+                R dx, dy, dz;
+                sep(a.box, pi, pp[u], dx, dy, dz);
+                const R d2 = dx * dx + dy * dy + dz * dz;
+                if (!(d2 < P.rc_r2)) continue;
+                const int row = take_row(P, a, d2, na, nr);
+                if (row < 0) continue;
+                a.clj[(int64_t)row * N + i] = jj[u];
+                a.cls[(int64_t)row * N + i] = (uint16_t)((lo1 + t0 + u) | (tt[u] << 8));
+            }
         }
-#pragma unroll
-        for (int u = 0; u < CB; ++u) {
-            const int t = t0 + CB + u;
-            const int sn = t < len0 ? lo0 + t : lo1 + (t - len0);
-            jn[u] = t < len ? nbr[(int64_t)sn * N + i] : -1;
-            tn[u] = t < len ? rev[(int64_t)sn * N + i] : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < CB; ++u) {
-            if (jj[u] < 0) continue;
+    }
+    // C: sums over the rows B wrote (angular rows naB..na, rare, then radial-only rows),
+    // with the list entry two rows ahead and the coordinates of the next row in flight
+    {
+        const int nA = na - naB, len = nA + (nr - nrB);
+        auto row_of = [&](int t) { return t < nA ? naB + t : a.cap_ang + nrB + (t - nA); };
+        int j1 = 0, j2 = 0;
+        v4<R> p1, s1;
+        if (len > 0) j1 = a.clj[(int64_t)row_of(0) * N + i];
+        if (len > 1) j2 = a.clj[(int64_t)row_of(1) * N + i];
+        if (len > 0) { p1 = pos[j1]; s1 = spin[j1]; }
+#pragma unroll 1
+        for (int t = 0; t < len; ++t) {
+            const v4<R> pj = p1, sj = s1;
+            if (t + 1 < len) { p1 = pos[j2]; s1 = spin[j2]; }
+            if (t + 2 < len) j2 = a.clj[(int64_t)row_of(t + 2) * N + i];
             R dx, dy, dz;
-            sep(a.box, pi, pp[u], dx, dy, dz);
-            const R d2 = dx * dx + dy * dy + dz * dz;
-            if (!(d2 < P.rc_r2)) continue;
-            int row;
-            if (d2 < P.rc_a2) {
-                if (na >= a.cap_ang) {   // only after a list overflow; keeps every row in bounds
-                    atomicOr(a.status, ST_NBR_OVERFLOW);
-                    continue;
-                }
-                row = na++;
-            } else {
-                row = a.cap_ang + nr++;
-            }
-            a.clj[(int64_t)row * N + i] = jj[u];
-            a.cls[(int64_t)row * N + i] = (uint16_t)(sl[u] | (tt[u] << 8));
-            const v4<R> cs = ss[u];
-            const R ir = rsqrt_(d2), r = d2 * ir;
-            const R ux = dx * ir, uy = dy * ir, uz = dz * ir;
-            R f[NK];
-            carrier_f(r, P.inv_rc_r, f);
-            const R sij = si.x * cs.x + si.y * cs.y + si.z * cs.z;
-            const R siu = si.x * ux + si.y * uy + si.z * uz;
-            const R sju = cs.x * ux + cs.y * uy + cs.z * uz;
-            const R dmi = (si.y * cs.z - si.z * cs.y) * ux + (si.z * cs.x - si.x * cs.z) * uy +
-                          (si.x * cs.y - si.y * cs.x) * uz;
-            const R ani = siu * sju, sia = siu * siu;
-#pragma unroll
-            for (int k = 0; k < NK; ++k) {
-                b0[k] += f[k];
-                b1[k] += f[k] * sij;
-                b2[k] += f[k] * dmi;
-                b3[k] += f[k] * ani;
-                b4[k] += f[k] * sia;
-            }
+            sep(a.box, pi, pj, dx, dy, dz);
+            rad_accumulate(P, si, sj, dx, dy, dz, dx * dx + dy * dy + dz * dz, b);
         }
     }
     // contraction of this species' sums; the second species adds onto the first's
@@ -178,12 +242,12 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
     constexpr int GG[5] = {G_R, G_EX, G_DMI, G_ANI, G_SIA};
 #pragma unroll
     for (int g = 0; g < 5; ++g) {
-        const R *b = g == 0 ? b0 : g == 1 ? b1 : g == 2 ? b2 : g == 3 ? b3 : b4;
+        const R *bg = g == 0 ? b.b0 : g == 1 ? b.b1 : g == 2 ? b.b2 : g == 3 ? b.b3 : b.b4;
 #pragma unroll
         for (int n = 0; n < NCH; ++n) {
             R v = TJ == 0 ? R(0) : a.q[(GQ[g] + n) * N + i];
 #pragma unroll
-            for (int k = 0; k < NK; ++k) v += P.c[TI][TJ][GG[g]][n][k] * b[k];
+            for (int k = 0; k < NK; ++k) v += P.c[TI][TJ][GG[g]][n][k] * bg[k];
             a.q[(GQ[g] + n) * N + i] = v;
         }
     }

@@ -553,6 +553,9 @@ def run_ours(args):
         sysd.destroy()
         del sysd
 
+    # launch shapes of the evaluation kernels picked by the library's autotuner
+    tuned = sysm.autotune(repeats=5) if not args.no_autotune else None
+
     # warm-up (graph capture happens here)
     sysm.step(args.warmup, DT, TEMP, FIELD)
     info0 = sysm.info()
@@ -638,7 +641,8 @@ def run_ours(args):
                 "kernel_share": shares, "kernel_ms_per_step": {k: v / args.profile_steps for k, v in prof.items()},
                 "kernel_alu_frac": {k: fl[k] * wl.n / (prof[k] / args.profile_steps * 1e-3) / 1e12 / peak_derived
                                     for k in ("rad_fwd", "ang_fwd", "network", "backward")},
-                "fp64": fp64, "mixed_error_vs_fp64": err, "serving": serving, "cpu_baseline": cpu}
+                "fp64": fp64, "mixed_error_vs_fp64": err, "serving": serving, "cpu_baseline": cpu,
+                "autotune": tuned}
         if args.midpoint_iters > 0:
             line["midpoint_evaluations_per_step"] = mid_evals / args.steps
         print(json.dumps(line), flush=True)
@@ -672,6 +676,7 @@ def main():
     ap.add_argument("--midpoint-iters", type=int, default=0,
                     help="cube: cap of the self-consistent midpoint spin update (0: predictor-corrector)")
     ap.add_argument("--midpoint-tol", type=float, default=1e-6)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--anderson-depth", type=int, default=0)
     ap.add_argument("--cells", type=int, default=48, help="B20 cells per side (48: the benchmark workload; "
                                                            "smaller values are for profiling captures)")

@@ -194,6 +194,18 @@ int sl_set_atom_fields(sl_system *sys, const double *B_atoms);
 int sl_texture_map(sl_system *sys, int32_t normal_axis, double cell, int32_t *n_a, int32_t *n_b, double *m,
                    double *Q);
 
+/* Autotuner of the evaluation kernels' launch shapes (atoms per block of the radial,
+ * angular and backward kernels; persistent CTAs per SM of the tensor-core network).
+ * Times the candidate shapes with CUDA events over `repeats` evaluations of the current
+ * state (which it leaves unchanged), keeps the fastest shape per kernel for this system
+ * and for later systems of the process on the same device, precision and size (a
+ * power-of-two bucket of n).  The per-atom arithmetic does not depend on the shapes, so
+ * results are bit-identical with any choice.  chosen [4] (may be NULL): radial block,
+ * angular block, backward block (threads), network CTAs per SM; eval_ms_before/after
+ * (may be NULL): summed median time of the four kernel groups with the previous and the
+ * chosen shapes.  SL_EINVAL for repeats outside [1, 1000]. */
+int sl_autotune(sl_system *sys, int32_t repeats, int32_t *chosen, double *eval_ms_before, double *eval_ms_after);
+
 /* Midpoint evaluations executed by all steps so far (0 in the predictor-corrector
  * mode); the mean iteration count per step is this over the steps taken. */
 int sl_get_midpoint_evaluations(const sl_system *sys, int64_t *evaluations);
@@ -240,6 +252,9 @@ int sl_batch_create(sl_system *const *systems, int32_t k, sl_batch **out);
  * dt/T/B per replica. */
 int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt_fs, const double *T_K,
                   const double *B_tesla /* [k][3] */);
+/* Number of single graph launches that advanced every replica of the batch together
+ * (each covers steps_per_graph steps of all replicas). */
+int sl_batch_graph_launches(const sl_batch *b, int64_t *launches);
 void sl_batch_destroy(sl_batch *b);
 
 /* ---------------------------------------------------------------- no device allocation

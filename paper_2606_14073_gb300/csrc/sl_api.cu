@@ -11,7 +11,10 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -22,8 +25,23 @@ struct sl_system {
     sl::Sys s;
 };
 
+// Replicas stepped together.  When every replica takes at least steps_per_graph steps in a
+// call, one captured graph holding all replicas' steps (each replica's kernels on its own
+// stream, forked from and joined to the batch stream) advances them all with a single
+// launch; otherwise each replica's own graphs are queued on its stream.
 struct sl_batch {
     std::vector<sl_system *> sys;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    std::vector<uint64_t> versions;   // capture versions of the replicas when the graph was built
+    std::vector<cudaEvent_t> ev;      // fork/join events: [0] batch, [1 + i] replica i
+    int64_t graph_launches = 0;
+    ~sl_batch() {
+        if (graph) cudaGraphExecDestroy(graph);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (stream) cudaStreamDestroy(stream);
+    }
 };
 
 namespace {
@@ -260,6 +278,27 @@ int capture_graph(sl::Sys &s, int k) {
     return SL_OK;
 }
 
+// Launch shapes chosen by sl_autotune, per (device, precision, size bucket), shared by
+// every system of the process so that later systems of a similar size start tuned.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, sl::LaunchCfg> g_tuned;
+
+std::tuple<int, int, int> tune_key(const sl::Sys &s) {
+    int bucket = 0;
+    for (int64_t m = s.n; m > 1; m >>= 1) ++bucket;
+    return std::make_tuple(s.device, s.prec, bucket);
+}
+
+void set_cfg(sl::Sys &s, const sl::LaunchCfg &c) {
+    s.cfg = c;
+    if (s.graph) {   // captured launches carry the old shapes
+        cudaGraphExecDestroy(s.graph);
+        s.graph = nullptr;
+        s.graph_steps = 0;
+    }
+    ++s.capture_version;
+}
+
 }  // namespace
 
 extern "C" {
@@ -358,6 +397,11 @@ int sl_create_system(const double *positions, const double *spins, const double 
     s.cap = opt.nbr_cap_rad;
     s.cap_ang = opt.nbr_cap_ang;
     s.steps_per_graph = opt.steps_per_graph < 0 ? 0 : opt.steps_per_graph;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(tune_key(s));
+        if (it != g_tuned.end()) s.cfg = it->second;
+    }
     fill_params(s.pd, params);
     fill_params(s.pf, params);
     for (int t = 0; t < NS; ++t) {
@@ -733,6 +777,80 @@ int sl_get_info(const sl_system *sys, int64_t *n_atoms, int32_t *precision, int6
     return SL_OK;
 }
 
+int sl_autotune(sl_system *sys, int32_t repeats, int32_t *chosen, double *eval_ms_before, double *eval_ms_after) {
+    if (!sys) return fail(SL_EINVAL, "NULL system");
+    if (repeats < 1 || repeats > 1000) return fail(SL_EINVAL, "repeats must lie in [1, 1000]");
+    sl::Sys &s = sys->s;
+    cudaSetDevice(s.device);
+    const sl::LaunchCfg before = s.cfg;
+    auto report = [&](const sl::LaunchCfg &c) {
+        if (chosen) {
+            const int q = sl::default_quad_block(s.prec);
+            chosen[0] = c.crad_block;
+            chosen[1] = c.ang_block ? c.ang_block : q;
+            chosen[2] = c.bwd_block ? c.bwd_block : q;
+            chosen[3] = c.mlp_ctas_per_sm;
+        }
+    };
+    if (s.n == 0) {
+        report(s.cfg);
+        if (eval_ms_before) *eval_ms_before = 0.0;
+        if (eval_ms_after) *eval_ms_after = 0.0;
+        return SL_OK;
+    }
+    // evaluation kernel groups timed by launch_eval's events: 1 radial (with compaction),
+    // 2 angular forward, 3 network, 4 backward
+    auto time_cfg = [&](const sl::LaunchCfg &c, double ms[5]) -> int {
+        s.cfg = c;
+        std::vector<cudaEvent_t> ev(6 * (size_t)repeats);
+        for (auto &e : ev) CK(cudaEventCreate(&e));
+        sl::launch_eval(s, false);   // warm-up
+        for (int r = 0; r < repeats; ++r) sl::launch_eval(s, false, ev.data() + 6 * r);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s.stream));
+        for (int g = 0; g < 5; ++g) {
+            std::vector<float> t((size_t)repeats);
+            for (int r = 0; r < repeats; ++r) CK(cudaEventElapsedTime(&t[r], ev[6 * r + g], ev[6 * r + g + 1]));
+            std::sort(t.begin(), t.end());
+            ms[g] = t[(size_t)repeats / 2];
+        }
+        for (auto &e : ev) cudaEventDestroy(e);
+        return SL_OK;
+    };
+    const int q = sl::default_quad_block(s.prec);
+    sl::LaunchCfg small, large;
+    small.crad_block = 64; small.ang_block = q / 2; small.bwd_block = q / 2; small.mlp_ctas_per_sm = 1;
+    large.crad_block = 128; large.ang_block = q; large.bwd_block = q; large.mlp_ctas_per_sm = 2;
+    double ms0[5], msS[5], msL[5];
+    int rc;
+    if ((rc = time_cfg(before, ms0)) || (rc = time_cfg(small, msS)) || (rc = time_cfg(large, msL))) {
+        s.cfg = before;
+        return rc;
+    }
+    // each kernel's time depends on its own shape only: pick per kernel
+    sl::LaunchCfg best = large;
+    if (msS[1] < msL[1]) best.crad_block = small.crad_block;
+    if (msS[2] < msL[2]) best.ang_block = small.ang_block;
+    if (s.prec != 0 && msS[3] < msL[3]) best.mlp_ctas_per_sm = small.mlp_ctas_per_sm;
+    if (msS[4] < msL[4]) best.bwd_block = small.bwd_block;
+    double after = 0.0, b0 = 0.0;
+    for (int g = 1; g < 5; ++g) b0 += ms0[g];
+    after += best.crad_block == small.crad_block ? msS[1] : msL[1];
+    after += best.ang_block == small.ang_block ? msS[2] : msL[2];
+    after += best.mlp_ctas_per_sm == small.mlp_ctas_per_sm && s.prec != 0 ? msS[3] : msL[3];
+    after += best.bwd_block == small.bwd_block ? msS[4] : msL[4];
+    s.cfg = before;
+    set_cfg(s, best);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[tune_key(s)] = best;
+    }
+    report(best);
+    if (eval_ms_before) *eval_ms_before = b0;
+    if (eval_ms_after) *eval_ms_after = after;
+    return SL_OK;
+}
+
 int sl_set_atom_fields(sl_system *sys, const double *B_atoms) {
     if (!sys) return fail(SL_EINVAL, "NULL system");
     sl::Sys &s = sys->s;
@@ -744,6 +862,7 @@ int sl_set_atom_fields(sl_system *sys, const double *B_atoms) {
             s.graph = nullptr;
             s.graph_steps = 0;
         }
+        ++s.capture_version;
     };
     if (!B_atoms) {
         if (s.Bat) {
@@ -911,10 +1030,46 @@ int sl_batch_create(sl_system *const *systems, int32_t k, sl_batch **out) {
     return SL_OK;
 }
 
+// Build (or reuse) the batch graph of g steps for every replica.
+static int batch_graph(sl_batch *b, int g) {
+    const int k = (int)b->sys.size();
+    bool fresh = b->graph && b->graph_steps == g && (int)b->versions.size() == k;
+    for (int i = 0; fresh && i < k; ++i) fresh = b->versions[i] == b->sys[i]->s.capture_version;
+    if (fresh) return SL_OK;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    cudaSetDevice(b->sys[0]->s.device);
+    if (!b->stream) CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    if ((int)b->ev.size() != k + 1) {
+        for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+        b->ev.assign((size_t)k + 1, nullptr);
+        for (auto &e : b->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    CK(cudaEventRecord(b->ev[0], b->stream));
+    for (int i = 0; i < k; ++i) {
+        sl::Sys &s = b->sys[i]->s;
+        CK(cudaStreamWaitEvent(s.stream, b->ev[0], 0));
+        for (int t = 0; t < g; ++t) enqueue_step(s);
+        CK(cudaEventRecord(b->ev[1 + i], s.stream));
+        CK(cudaStreamWaitEvent(b->stream, b->ev[1 + i], 0));
+    }
+    cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
+    e = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph instantiate");
+    b->graph_steps = g;
+    b->versions.resize((size_t)k);
+    for (int i = 0; i < k; ++i) b->versions[i] = b->sys[i]->s.capture_version;
+    return SL_OK;
+}
+
 int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt, const double *T, const double *B) {
     if (!b || !n_steps || !dt || !T || !B) return fail(SL_EINVAL, "NULL argument");
-    // every replica's steps are queued on its own stream before any wait, so the
-    // replicas' kernels overlap on the device
     const int k = (int)b->sys.size();
     for (int i = 0; i < k; ++i) {
         if (n_steps[i] < 0 || !(dt[i] > 0) || !(T[i] >= 0) || !std::isfinite(dt[i]) || !std::isfinite(T[i]))
@@ -928,8 +1083,40 @@ int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt, const d
         if ((rc = upload_params(s, dt[i], T[i], B + 3 * i))) return rc;
         for (int c = 0; c < 3; ++c) s.B[c] = B[3 * i + c];
         if (n_steps[i] == 0 || s.n == 0) { s.step += (uint64_t)n_steps[i]; continue; }
-        if ((rc = snapshot_state(s)) || (rc = queue_steps(s, n_steps[i]))) return rc;
+        if ((rc = snapshot_state(s))) return rc;
         active.push_back(i);
+    }
+    // the common graph: every replica active, on one device, with the same steps per graph
+    const int g = b->sys[0]->s.steps_per_graph;
+    bool common = g > 0 && (int)active.size() == k;
+    int64_t shared = INT64_MAX;
+    for (int i = 0; common && i < k; ++i) {
+        const sl::Sys &s = b->sys[i]->s;
+        common = s.steps_per_graph == g && s.device == b->sys[0]->s.device;
+        shared = std::min<int64_t>(shared, n_steps[i]);
+    }
+    int64_t rounds = common ? shared / g : 0;
+    if (rounds > 0) {
+        if ((rc = batch_graph(b, g))) return rc;
+        for (int i = 0; i < k; ++i) {   // the batch stream waits for each replica's uploads
+            sl::Sys &s = b->sys[i]->s;
+            CK(cudaEventRecord(b->ev[1 + i], s.stream));
+            CK(cudaStreamWaitEvent(b->stream, b->ev[1 + i], 0));
+        }
+        for (int64_t r = 0; r < rounds; ++r) CK(cudaGraphLaunch(b->graph, b->stream));
+        b->graph_launches += rounds;
+        CK(cudaEventRecord(b->ev[0], b->stream));
+        for (int i = 0; i < k; ++i) {   // and each replica's stream waits for the batch
+            sl::Sys &s = b->sys[i]->s;
+            CK(cudaStreamWaitEvent(s.stream, b->ev[0], 0));
+            s.n_launches += rounds * g * kernels_per_step(s);
+        }
+    }
+    // the rest: each replica's own graphs and single steps on its own stream
+    for (int i : active) {
+        sl::Sys &s = b->sys[i]->s;
+        const int64_t left = n_steps[i] - rounds * g;
+        if (left > 0 && (rc = queue_steps(s, left))) return rc;
     }
     // every replica is finished (and restored where it failed) before the first error is returned
     int first = SL_OK;
@@ -943,6 +1130,12 @@ int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt, const d
         if (rc && first == SL_OK) { first = rc; first_msg = g_err; }
     }
     if (first != SL_OK) return fail(first, "%s", first_msg.c_str());
+    return SL_OK;
+}
+
+int sl_batch_graph_launches(const sl_batch *b, int64_t *launches) {
+    if (!b || !launches) return fail(SL_EINVAL, "NULL argument");
+    *launches = b->graph_launches;
     return SL_OK;
 }
 

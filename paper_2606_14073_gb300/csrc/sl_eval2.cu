@@ -741,9 +741,11 @@ static Eval2Args<R> args2(Sys &s, bool want_virial) {
 template <typename R>
 static constexpr int quad_block() { return sizeof(R) == 8 ? 64 : 128; }
 template <typename R>
-static constexpr size_t fwd_smem() { return (size_t)(quad_block<R>() / 32) * 8 * FQUAD * sizeof(R); }
+static constexpr size_t fwd_smem(int qb = quad_block<R>()) { return (size_t)(qb / 32) * 8 * FQUAD * sizeof(R); }
 template <typename R>
-static constexpr size_t bwdf_smem() { return (size_t)(quad_block<R>() / 32) * 8 * BW_ATOM * sizeof(R); }
+static constexpr size_t bwdf_smem(int qb = quad_block<R>()) { return (size_t)(qb / 32) * 8 * BW_ATOM * sizeof(R); }
+
+int default_quad_block(int prec) { return prec == 0 ? quad_block<double>() : quad_block<float>(); }
 
 void eval2_init() {
     static bool done = false;
@@ -758,19 +760,22 @@ void eval2_init() {
 template <typename R>
 static void eval2_impl(Sys &s, const NepDev<R> &P, bool want_virial, cudaEvent_t *ev) {
     const Eval2Args<R> a = args2<R>(s, want_virial);
-    const unsigned nb = (unsigned)((s.n + 127) / 128);
-    const int qb = quad_block<R>();
-    const unsigned nq = (unsigned)((s.n + qb / 4 - 1) / (qb / 4));
+    const int cb = s.cfg.crad_block;
+    const unsigned nb = (unsigned)((s.n + cb - 1) / cb);
+    const int qa = s.cfg.ang_block ? s.cfg.ang_block : quad_block<R>();
+    const int qw = s.cfg.bwd_block ? s.cfg.bwd_block : quad_block<R>();
+    const unsigned nqa = (unsigned)((s.n + qa / 4 - 1) / (qa / 4));
+    const unsigned nqw = (unsigned)((s.n + qw / 4 - 1) / (qw / 4));
     if (ev) cudaEventRecord(ev[0], s.stream);
     // compaction and radial channels in one kernel: the compaction group is empty
     if (ev) cudaEventRecord(ev[1], s.stream);
-    k_crad<R><<<nb, 128, 0, s.stream>>>(P, a);
+    k_crad<R><<<nb, cb, 0, s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[2], s.stream);
-    k_ang_fwd<R><<<nq, qb, fwd_smem<R>(), s.stream>>>(P, a);
+    k_ang_fwd<R><<<nqa, qa, fwd_smem<R>(qa), s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[3], s.stream);
     launch_network(s, nullptr);
     if (ev) cudaEventRecord(ev[4], s.stream);
-    k_bwd<R><<<nq, qb, bwdf_smem<R>(), s.stream>>>(P, a);
+    k_bwd<R><<<nqw, qw, bwdf_smem<R>(qw), s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[5], s.stream);
 }
 

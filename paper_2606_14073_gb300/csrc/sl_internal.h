@@ -37,6 +37,16 @@ struct MidDev {
     double gamma[AA_MAX_DEPTH];                      // Anderson coefficients of the current iteration
 };
 
+// Launch shapes of the evaluation kernels, chosen by sl_autotune (the defaults below
+// otherwise).  The per-atom arithmetic does not depend on them, so results are the same
+// for every choice.
+struct LaunchCfg {
+    int crad_block = 128;      // threads per block of k_crad (one atom per thread)
+    int ang_block = 0;         // threads per block of k_ang_fwd (four per atom); 0: the precision's default
+    int bwd_block = 0;         // threads per block of k_bwd
+    int mlp_ctas_per_sm = 2;   // persistent CTAs per SM of the tensor-core network
+};
+
 // Where an evaluation reads positions and spins (null: the state arrays) and an
 // optional device flag that makes the evaluation kernels return at once.
 struct EvalAt {
@@ -117,11 +127,13 @@ struct Sys {
 
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
+    uint64_t capture_version = 0;   // bumped whenever a captured launch would read stale pointers
     // snapshot for error recovery
     double4 *snap = nullptr;   // 5 n: pos, vel, spin, F, H
 
     // evaluation point used by launch_eval / launch_network while it is set
     EvalAt at;
+    LaunchCfg cfg;
 
     // per-atom part of the external field (tesla, internal order); null: uniform field only
     double4 *Bat = nullptr;
@@ -153,6 +165,7 @@ void launch_rebuild(Sys &s, bool conditional);
 // after the last one (sl_eval2.cu).
 void launch_eval(Sys &s, bool want_virial, cudaEvent_t *ev = nullptr);
 void eval2_init();
+int default_quad_block(int prec);   // threads per block of the quad kernels by default
 void launch_network(Sys &s, cudaEvent_t *ev);   // sl_nep.cu
 void launch_network_tc(Sys &s);                  // sl_mlp_tc.cu (mixed precision)
 // first half, rebuild group (7), compaction with radial forward, angular forward, network, backward,

@@ -313,7 +313,7 @@ void launch_network_tc(Sys &s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t ntiles = (s.n + tc::TM - 1) / tc::TM;
-    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * 2);
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * s.cfg.mlp_ctas_per_sm);
     tc::k_mlp_tc<<<grid, 128, tc::SMEM_BYTES, s.stream>>>(s.pf, (const float *)s.q, (float *)s.fp, (float *)s.ei, s.n,
                                                        s.status, s.at.skip);
 }

@@ -23,7 +23,8 @@ EXPORTS = ["sl_default_options", "sl_create_system", "sl_step", "sl_energy_force
            "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_get_stream",
            "sl_destroy_system", "sl_last_error", "sl_batch_create", "sl_batch_step", "sl_batch_destroy",
            "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak", "sl_descriptors_energies_noalloc",
-           "sl_estimate_device_bytes", "sl_get_midpoint_evaluations", "sl_set_atom_fields", "sl_texture_map"]
+           "sl_estimate_device_bytes", "sl_get_midpoint_evaluations", "sl_set_atom_fields", "sl_texture_map",
+           "sl_batch_graph_launches", "sl_autotune"]
 KERNEL_GROUPS = ["first_half", "rebuild", "compact", "rad_fwd", "ang_fwd", "network", "backward", "second_half"]
 
 
@@ -72,6 +73,8 @@ def lib(path: str | None = None):
             L.sl_get_info.argtypes = [P, P, P, P, P]
             L.sl_get_midpoint_evaluations.argtypes = [P, P]
             L.sl_set_atom_fields.argtypes = [P, P]
+            L.sl_batch_graph_launches.argtypes = [P, P]
+            L.sl_autotune.argtypes = [P, I32, P, P, P]
             L.sl_texture_map.argtypes = [P, I32, D, P, P, P, P]
             L.sl_step_profiled.argtypes = [P, I64, D, D, P, P]
             L.sl_measure_fma_peak.argtypes = [I32, P, P]
@@ -92,7 +95,7 @@ def lib(path: str | None = None):
                       "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_batch_create",
                       "sl_batch_step", "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak",
                       "sl_descriptors_energies_noalloc", "sl_get_midpoint_evaluations", "sl_set_atom_fields",
-                      "sl_texture_map"):
+                      "sl_texture_map", "sl_batch_graph_launches", "sl_autotune"):
                 getattr(L, f).restype = C.c_int
             _lib = L
         return _lib
@@ -184,6 +187,14 @@ class System:
                                     C.byref(q)))
         return m, float(q.value)
 
+    def autotune(self, repeats: int = 5) -> dict:
+        """Pick the evaluation kernels' launch shapes by timing (sl_autotune)."""
+        ch = np.zeros(4, dtype=np.int32)
+        b, a = C.c_double(), C.c_double()
+        _check(lib().sl_autotune(self.handle, int(repeats), _ptr(ch), C.byref(b), C.byref(a)))
+        return dict(crad_block=int(ch[0]), ang_block=int(ch[1]), bwd_block=int(ch[2]), mlp_ctas_per_sm=int(ch[3]),
+                    eval_ms_before=b.value, eval_ms_after=a.value)
+
     def midpoint_evaluations(self) -> int:
         v = C.c_int64()
         _check(lib().sl_get_midpoint_evaluations(self.handle, C.byref(v)))
@@ -272,6 +283,11 @@ class Batch:
         t = np.ascontiguousarray(np.broadcast_to(T, (k,)), dtype=np.float64)
         b = np.ascontiguousarray(np.broadcast_to(np.asarray(B, dtype=np.float64), (k, 3)))
         _check(lib().sl_batch_step(self.handle, _ptr(ns), _ptr(d), _ptr(t), _ptr(b)))
+
+    def graph_launches(self) -> int:
+        v = C.c_int64()
+        _check(lib().sl_batch_graph_launches(self.handle, C.byref(v)))
+        return int(v.value)
 
     def destroy(self):
         if getattr(self, "handle", None):

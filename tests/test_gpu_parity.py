@@ -204,19 +204,30 @@ def test_graphs_match_direct_launches(params):
 
 
 def test_batch_equals_alone(params):
-    wls = [W.fege_cube(4, seed=80 + i, replica=i) for i in range(3)]
+    """Uneven replicas in one batch (one graph launch covering all of them for the shared
+    steps, each replica's own launches for the rest) match each replica run alone."""
+    wls = [W.fege_cube(c, seed=80 + i, replica=i) for i, c in enumerate((4, 5, 4))]
+    calls = [([15, 15, 15], (200.0, 250.0, 300.0)), ([25, 12, 31], (100.0, 50.0, 0.0))]
     alone = []
-    for w in wls:
+    for k, w in enumerate(wls):
         s = S.system_from_workload(w, params, replica=w.seed - W.LANGEVIN_SEED0)
-        s.step(15, 1.0, 200.0, (0, 0, 0.3))
+        for n_steps, Ts in calls:
+            s.step(n_steps[k], 1.0, Ts[k], (0, 0, 0.3))
         alone.append(s.get_state())
         s.destroy()
     syss = [S.system_from_workload(w, params, replica=w.seed - W.LANGEVIN_SEED0) for w in wls]
     b = S.Batch(syss)
-    b.step(15, 1.0, 200.0, (0, 0, 0.3))
+    for n_steps, Ts in calls:
+        b.step(n_steps, 1.0, list(Ts), (0, 0, 0.3))
+    assert b.graph_launches() == 2          # 10 shared steps in each call
     for s, ref in zip(syss, alone):
         g = s.get_state()
-        assert np.array_equal(g["positions"], ref["positions"]) and np.array_equal(g["spins"], ref["spins"])
+        assert g["step"] == ref["step"]
+        for key in ("positions", "velocities", "spins", "forces", "fields"):
+            assert np.array_equal(g[key], ref[key]), key
+    b.destroy()
+    for s in syss:
+        s.destroy()
 
 
 def test_empty_and_tiny_systems(params, model):
@@ -283,3 +294,25 @@ def test_batch_overflow_restores_only_the_failing_replica(params):
     b.destroy()
     good.destroy()
     bad.destroy()
+
+
+@pytest.mark.parametrize("prec", [S.SL_PREC_FP64, S.SL_PREC_MIXED])
+def test_autotune_leaves_state_and_results_unchanged(params, prec):
+    wl = W.fege_cube(5, seed=90)
+    a = S.system_from_workload(wl, params, precision=prec)
+    b = S.system_from_workload(wl, params, precision=prec)
+    st0 = a.get_state()
+    info = a.autotune(repeats=3)
+    q = 64 if prec == S.SL_PREC_FP64 else 128
+    assert info["crad_block"] in (64, 128) and info["ang_block"] in (q // 2, q) and info["bwd_block"] in (q // 2, q)
+    assert info["mlp_ctas_per_sm"] in (1, 2) and info["eval_ms_after"] <= info["eval_ms_before"] * 1.5
+    st1 = a.get_state()
+    for k in ("positions", "velocities", "spins", "forces", "fields"):
+        assert np.array_equal(st0[k], st1[k]), k
+    a.step(25, 1.0, 300.0, (0, 0, 0.1))
+    b.step(25, 1.0, 300.0, (0, 0, 0.1))
+    ga, gb = a.get_state(), b.get_state()
+    for k in ("positions", "velocities", "spins", "forces", "fields"):
+        assert np.array_equal(ga[k], gb[k]), k
+    a.destroy()
+    b.destroy()

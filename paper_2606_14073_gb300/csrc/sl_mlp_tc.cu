@@ -38,8 +38,12 @@ constexpr uint32_t SZ_A2 = TM * K2 * 2;    // 8192
 constexpr uint32_t SZ_B2 = N2 * K2 * 2;    // 5120
 constexpr uint32_t OFF_A1H = 0, OFF_A1L = OFF_A1H + SZ_A1;
 constexpr uint32_t OFF_B1H = OFF_A1L + SZ_A1, OFF_B1L = OFF_B1H + SZ_B1;
-constexpr uint32_t OFF_A2H = OFF_B1L + SZ_B1, OFF_A2L = OFF_A2H + SZ_A2;
-constexpr uint32_t OFF_B2H = OFF_A2L + SZ_A2, OFF_B2L = OFF_B2H + SZ_B2;
+// The A2 tile (layer-2 operand) reuses the A1 region: A1 is dead once the layer-1 MMAs
+// have completed, and the next tile's A1 is written only after the layer-2 MMAs have.
+// 61.5 KB per CTA, so three CTAs share an SM.
+constexpr uint32_t OFF_A2H = OFF_A1H, OFF_A2L = OFF_A2H + SZ_A2;
+static_assert(2 * SZ_A2 <= SZ_A1, "A2 must fit in the A1 hi region");
+constexpr uint32_t OFF_B2H = OFF_B1L + SZ_B1, OFF_B2L = OFF_B2H + SZ_B2;
 constexpr uint32_t OFF_BAR = OFF_B2L + SZ_B2;            // 8-byte mbarrier
 constexpr uint32_t OFF_TMEM = OFF_BAR + 8;                // tensor-memory base address
 constexpr uint32_t SMEM_BYTES = OFF_TMEM + 8;
@@ -129,7 +133,7 @@ __device__ __forceinline__ void split8(const float x[8], uint4 &hi, uint4 &lo) {
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-__global__ void __launch_bounds__(128, 1) k_mlp_tc(const __grid_constant__ NepDev<float> P, const float *__restrict__ q,
+__global__ void __launch_bounds__(128, 3) k_mlp_tc(const __grid_constant__ NepDev<float> P, const float *__restrict__ q,
                                                    float *__restrict__ fp, float *__restrict__ ei, int64_t n,
                                                    int *status, const int *skip) {
     // uniform for the whole CTA and before any shared-memory or TMEM use

@@ -187,21 +187,30 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
             }
         }
     }
-    // B: radial-shell candidates, compaction only
+    // B: radial-shell candidates, compaction only; the next batch's list entries are in flight
     const int naB = na, nrB = nr;
     {
         const int len = hi1 - lo1;
+        int jn[CBB], tn[CBB];
+#pragma unroll
+        for (int u = 0; u < CBB; ++u) {
+            jn[u] = u < len ? nbr[(int64_t)(lo1 + u) * N + i] : -1;
+            tn[u] = u < len ? rev[(int64_t)(lo1 + u) * N + i] : 0;
+        }
 #pragma unroll 1
         for (int t0 = 0; t0 < len; t0 += CBB) {
             int jj[CBB], tt[CBB];
             v4<R> pp[CBB];
 #pragma unroll
-            for (int u = 0; u < CBB; ++u) {
-                jj[u] = t0 + u < len ? nbr[(int64_t)(lo1 + t0 + u) * N + i] : -1;
-                tt[u] = t0 + u < len ? rev[(int64_t)(lo1 + t0 + u) * N + i] : 0;
-            }
+            for (int u = 0; u < CBB; ++u) { jj[u] = jn[u]; tt[u] = tn[u]; }
 #pragma unroll
             for (int u = 0; u < CBB; ++u) pp[u] = pos[jj[u] >= 0 ? jj[u] : (int)i];
+#pragma unroll
+            for (int u = 0; u < CBB; ++u) {
+                const int t = t0 + CBB + u;
+                jn[u] = t < len ? nbr[(int64_t)(lo1 + t) * N + i] : -1;
+                tn[u] = t < len ? rev[(int64_t)(lo1 + t) * N + i] : 0;
+            }
 #pragma unroll
             for (int u = 0; u < CBB; ++u) {
                 if (jj[u] < 0) continue;

@@ -819,8 +819,8 @@ int sl_autotune(sl_system *sys, int32_t repeats, int32_t *chosen, double *eval_m
     };
     const int q = sl::default_quad_block(s.prec);
     sl::LaunchCfg small, large;
-    small.crad_block = 64; small.ang_block = q / 2; small.bwd_block = q / 2; small.mlp_ctas_per_sm = 2;
-    large.crad_block = 128; large.ang_block = q; large.bwd_block = q; large.mlp_ctas_per_sm = 3;
+    small.crad_block = 64; small.ang_block = q / 2; small.bwd_block = q / 2; small.mlp_ctas_per_sm = 1;
+    large.crad_block = 128; large.ang_block = q; large.bwd_block = q; large.mlp_ctas_per_sm = 2;
     double ms0[5], msS[5], msL[5];
     int rc;
     if ((rc = time_cfg(before, ms0)) || (rc = time_cfg(small, msS)) || (rc = time_cfg(large, msL))) {

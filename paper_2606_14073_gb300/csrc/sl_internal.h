@@ -44,7 +44,7 @@ struct LaunchCfg {
     int crad_block = 128;      // threads per block of k_crad (one atom per thread)
     int ang_block = 0;         // threads per block of k_ang_fwd (four per atom); 0: the precision's default
     int bwd_block = 0;         // threads per block of k_bwd
-    int mlp_ctas_per_sm = 3;   // persistent CTAs per SM of the tensor-core network
+    int mlp_ctas_per_sm = 2;   // persistent CTAs per SM of the tensor-core network
 };
 
 // Where an evaluation reads positions and spins (null: the state arrays) and an

@@ -40,13 +40,17 @@ constexpr uint32_t OFF_A1H = 0, OFF_A1L = OFF_A1H + SZ_A1;
 constexpr uint32_t OFF_B1H = OFF_A1L + SZ_A1, OFF_B1L = OFF_B1H + SZ_B1;
 // The A2 tile (layer-2 operand) reuses the A1 region: A1 is dead once the layer-1 MMAs
 // have completed, and the next tile's A1 is written only after the layer-2 MMAs have.
-// 61.5 KB per CTA, so three CTAs share an SM.
+// With the descriptor stage below, 95 KB per CTA: two CTAs share an SM.
 constexpr uint32_t OFF_A2H = OFF_A1H, OFF_A2L = OFF_A2H + SZ_A2;
 static_assert(2 * SZ_A2 <= SZ_A1, "A2 must fit in the A1 hi region");
 constexpr uint32_t OFF_B2H = OFF_B1L + SZ_B1, OFF_B2L = OFF_B2H + SZ_B2;
 constexpr uint32_t OFF_BAR = OFF_B2L + SZ_B2;            // 8-byte mbarrier
 constexpr uint32_t OFF_TMEM = OFF_BAR + 8;                // tensor-memory base address
-constexpr uint32_t SMEM_BYTES = OFF_TMEM + 8;
+// FP32 descriptors of the next tile, [DIM][TM], filled by asynchronous copies while the
+// current tile is in the tensor cores (each thread copies and later reads its own column)
+constexpr uint32_t OFF_Q = (OFF_TMEM + 8 + 15) & ~15u;
+constexpr uint32_t SZ_Q = DIM * TM * 4;                   // 33792
+constexpr uint32_t SMEM_BYTES = OFF_Q + SZ_Q;
 
 // byte offset of element (row, k) of a [rows x K] 16-bit operand in the canonical
 // no-swizzle K-major layout: core matrix = 8 rows x 8 elements (128 B, row stride 16 B),
@@ -113,6 +117,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(r[t]);
 }
 
+// 4-byte asynchronous global -> shared copy; bytes = 0 fills the destination with zero
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float *src, uint32_t bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -133,7 +144,7 @@ __device__ __forceinline__ void split8(const float x[8], uint4 &hi, uint4 &lo) {
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-__global__ void __launch_bounds__(128, 3) k_mlp_tc(const __grid_constant__ NepDev<float> P, const float *__restrict__ q,
+__global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDev<float> P, const float *__restrict__ q,
                                                    float *__restrict__ fp, float *__restrict__ ei, int64_t n,
                                                    int *status, const int *skip) {
     // uniform for the whole CTA and before any shared-memory or TMEM use
@@ -186,9 +197,22 @@ __global__ void __launch_bounds__(128, 3) k_mlp_tc(const __grid_constant__ NepDe
     bool ok = true;
     const int64_t ntiles = (n + TM - 1) / TM;
 
+    const float *stage = reinterpret_cast<const float *>(smem + OFF_Q);
+    // descriptors of one tile into this thread's column of the stage (zeros past n)
+    auto fetch_tile = [&](int64_t t) {
+        const int64_t a = t * TM + tid;
+        const bool in = a < n;
+        const float *src = q + (in ? a : 0);
+        for (int v = 0; v < DIM; ++v)
+            cp_async4(sbase + OFF_Q + (uint32_t)(v * TM + tid) * 4u, src + (int64_t)v * n, in ? 4u : 0u);
+        cp_async_commit();
+    };
+    if (blockIdx.x < ntiles) fetch_tile(blockIdx.x);
+
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int64_t i = tile * TM + tid;
         const bool valid = i < n;
+        cp_async_wait_all();
         // A1 row: s_v q_v, hi/lo
 #pragma unroll
         for (int c = 0; c < K1 / 8; ++c) {
@@ -196,13 +220,15 @@ __global__ void __launch_bounds__(128, 3) k_mlp_tc(const __grid_constant__ NepDe
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
                 const int v = c * 8 + t;
-                x[t] = (valid && v < DIM) ? P.scal[v] * q[(int64_t)v * n + i] : 0.f;
+                x[t] = v < DIM ? P.scal[v] * stage[v * TM + tid] : 0.f;
             }
             uint4 hi, lo;
             split8(x, hi, lo);
             *reinterpret_cast<uint4 *>(smem + OFF_A1H + cm_off(tid, c * 8, K1)) = hi;
             *reinterpret_cast<uint4 *>(smem + OFF_A1L + cm_off(tid, c * 8, K1)) = lo;
         }
+        // this thread's column is consumed: the next tile's copies overlap this tile's MMAs
+        if (tile + gridDim.x < ntiles) fetch_tile(tile + gridDim.x);
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -290,6 +316,7 @@ __global__ void __launch_bounds__(128, 3) k_mlp_tc(const __grid_constant__ NepDe
         tc_fence_before();
         __syncthreads();   // TMEM and the A tiles are free for the next tile
     }
+    cp_async_wait_all();   // no copy may land after the CTA is gone
     if (!ok) {
         if (tid == 0) atomicOr(status, ST_TIMEOUT);
         // let any MMA still in flight finish before the memory is released (bounded)

@@ -305,7 +305,7 @@ def test_autotune_leaves_state_and_results_unchanged(params, prec):
     info = a.autotune(repeats=3)
     q = 64 if prec == S.SL_PREC_FP64 else 128
     assert info["crad_block"] in (64, 128) and info["ang_block"] in (q // 2, q) and info["bwd_block"] in (q // 2, q)
-    assert info["mlp_ctas_per_sm"] in (2, 3) and info["eval_ms_after"] <= info["eval_ms_before"] * 1.5
+    assert info["mlp_ctas_per_sm"] in (1, 2) and info["eval_ms_after"] <= info["eval_ms_before"] * 1.5
     st1 = a.get_state()
     for k in ("positions", "velocities", "spins", "forces", "fields"):
         assert np.array_equal(st0[k], st1[k]), k

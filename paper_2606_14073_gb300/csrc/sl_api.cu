@@ -120,7 +120,7 @@ void fill_params(sl::NepDev<R> &P, const sl_nep_params *p) {
 void free_sys(sl::Sys &s) {
     void *ptrs[] = {s.pos, s.vel, s.spin, s.spin_prev, s.F, s.H, s.posref, s.posf, s.spinf, s.species, s.orig,
                     s.inv, s.nbr, s.rev, s.nbr_orig, s.cells.posf, s.cells.key, s.seg, s.cells.count, s.cells.start, s.cells.fill, s.cells.atoms,
-                    s.cells.of, s.q, s.bsum, s.fp, s.ei, s.pairs, s.clj, s.cls, s.cnt, s.fown, s.gii,
+                    s.cells.of, s.q, s.bsum, s.fp, s.ei, s.pairs, s.clj, s.cls, s.cnt, s.cmask, s.fown, s.gii,
                     s.wpart, s.Fo, s.Ho,
                     s.status, s.rebuild, s.d_step, s.d_par, s.red, s.snap, s.d_builds,
                     s.posmid, s.posmidf, s.mids, s.midsf, s.mx, s.mg, s.aax, s.aag, s.aapart, s.md, s.Bat,
@@ -396,6 +396,7 @@ int sl_create_system(const double *positions, const double *spins, const double 
     s.aa_reg = opt.anderson_reg;
     s.cap = opt.nbr_cap_rad;
     s.cap_ang = opt.nbr_cap_ang;
+    s.maskw = (s.cap + 31) / 32;
     s.steps_per_graph = opt.steps_per_graph < 0 ? 0 : opt.steps_per_graph;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -475,7 +476,7 @@ int sl_create_system(const double *positions, const double *spins, const double 
         (rc = dalloc((char **)&s.bsum, R * NB * N)) || (rc = dalloc((char **)&s.fp, R * DIM * N)) ||
         (rc = dalloc((char **)&s.ei, R * N)) || (rc = dalloc((char **)&s.pairs, R * 8 * N * s.cap)) ||
         (rc = dalloc(&s.clj, N * (size_t)(s.cap + s.cap_ang))) || (rc = dalloc(&s.cls, N * (size_t)(s.cap + s.cap_ang))) ||
-        (rc = dalloc(&s.cnt, N)) || (rc = dalloc((char **)&s.fown, R * 4 * N)) ||
+        (rc = dalloc(&s.cnt, N)) || (rc = dalloc(&s.cmask, N * (size_t)((s.cap + 31) / 32))) || (rc = dalloc((char **)&s.fown, R * 4 * N)) ||
         (rc = dalloc((char **)&s.gii, R * 4 * N)) || (rc = dalloc((char **)&s.wpart, R * 9 * N)) ||
         (rc = dalloc(&s.Fo, N)) || (rc = dalloc(&s.Ho, N)) || (rc = dalloc(&s.status, 1)) ||
         (rc = dalloc(&s.rebuild, 1)) || (rc = dalloc(&s.d_step, 2)) || (rc = dalloc(&s.d_par, 1)) ||
@@ -931,6 +932,7 @@ int64_t sl_estimate_device_bytes(int64_t n, const sl_options *opt_in) {
                   + 3 * 4 + 4 + 16 + 16 + 4            // species, caller index maps, list segments, cell copies
                   + 3 * 4 * cap                        // candidate lists (index and caller index), reverse slots
                   + 6 * (ca + cap) + 16                // compact rows, counts
+                  + 4 * ((cap + 31) / 32)              // in-cutoff slot mask
                   + R * (2 * sl::DIM + sl::NB + 1 + 9) // q, Fp, angular sums, E_i, virial parts
                   + R * 8 * cap + 2 * R * 4            // pair records, per-atom sums
                   + 2 * 32 + 5 * 32 + 3 * 4;           // evaluation outputs, snapshot, cell arrays

@@ -133,9 +133,16 @@ __device__ __forceinline__ int take_row(const NepDev<R> &P, const Eval2Args<R> &
     return a.cap_ang + nr++;
 }
 
+// in-cutoff slot bits of this thread's atom, in shared memory (column threadIdx.x)
+constexpr int MASKW_MAX = 8;
+__device__ __forceinline__ void mark_slot(uint32_t (*sm)[128], int slot) {
+    sm[slot >> 5][threadIdx.x] |= 1u << (slot & 31);
+}
+
 template <typename R, int TI, int TJ>
 __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, const v4<R> &pi,
-                                             const v4<R> &si, int lo0, int hi0, int lo1, int hi1, int &na, int &nr) {
+                                             const v4<R> &si, int lo0, int hi0, int lo1, int hi1, int &na, int &nr,
+                                             uint32_t (*smask)[128]) {
     RadSums<R> b;
 #pragma unroll
     for (int k = 0; k < NK; ++k) { b.b0[k] = b.b1[k] = b.b2[k] = b.b3[k] = b.b4[k] = R(0); }
@@ -183,6 +190,7 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
                 if (row < 0) continue;
                 a.clj[(int64_t)row * N + i] = jj[u];
                 a.cls[(int64_t)row * N + i] = (uint16_t)((lo0 + t0 + u) | (tt[u] << 8));
+                mark_slot(smask, lo0 + t0 + u);
                 rad_accumulate(P, si, ss[u], dx, dy, dz, d2, b);
             }
         }
@@ -222,6 +230,7 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
                 if (row < 0) continue;
                 a.clj[(int64_t)row * N + i] = jj[u];
                 a.cls[(int64_t)row * N + i] = (uint16_t)((lo1 + t0 + u) | (tt[u] << 8));
+                mark_slot(smask, lo1 + t0 + u);
             }
         }
     }
@@ -263,25 +272,29 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
 }
 
 template <typename R, int TI>
-__device__ __forceinline__ void crad_atom(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i) {
+__device__ __forceinline__ void crad_atom(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i,
+                                          uint32_t (*smask)[128]) {
     const int64_t N = a.n;
     const v4<R> pi = a.pos[i], si = a.spin[i];
     const int4 sg = a.seg[i];
     int na = 0, nr = 0;
-    crad_species<R, TI, 0>(P, a, i, pi, si, 0, sg.x, sg.y, sg.z, na, nr);
+    for (int w = 0; w < a.maskw; ++w) smask[w][threadIdx.x] = 0u;
+    crad_species<R, TI, 0>(P, a, i, pi, si, 0, sg.x, sg.y, sg.z, na, nr, smask);
     const int na0 = na, nr0 = nr;
-    crad_species<R, TI, 1>(P, a, i, pi, si, sg.x, sg.y, sg.z, sg.w, na, nr);
+    crad_species<R, TI, 1>(P, a, i, pi, si, sg.x, sg.y, sg.z, sg.w, na, nr, smask);
     a.cnt[i] = make_int4(na0, na, nr0, nr);
+    for (int w = 0; w < a.maskw; ++w) a.mask[(int64_t)w * N + i] = smask[w][threadIdx.x];
     a.q[Q_O * N + i] = si.x * si.x + si.y * si.y + si.z * si.z;
 }
 
 template <typename R>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_crad(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
     if (a.skip && *a.skip) return;
+    __shared__ uint32_t smask[MASKW_MAX][128];   // blocks have at most 128 threads
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    if (i < a.n_fe) crad_atom<R, 0>(P, a, i);
-    else crad_atom<R, 1>(P, a, i);
+    if (i < a.n_fe) crad_atom<R, 0>(P, a, i, smask);
+    else crad_atom<R, 1>(P, a, i, smask);
 }
 
 // ------------------------------------------------------------------ k_ang_fwd
@@ -740,7 +753,7 @@ static Eval2Args<R> args2(Sys &s, bool want_virial) {
     a.skip = s.at.skip;
     a.nbr = s.nbr; a.seg = s.seg; a.rev = s.rev; a.n = s.n; a.n_fe = s.n_fe;
     a.cap = s.cap; a.cap_ang = s.cap_ang;
-    a.clj = s.clj; a.cls = s.cls; a.cnt = s.cnt;
+    a.clj = s.clj; a.cls = s.cls; a.cnt = s.cnt; a.mask = s.cmask; a.maskw = s.maskw;
     a.q = (R *)s.q; a.bsum = (R *)s.bsum; a.fp = (R *)s.fp; a.ei = (R *)s.ei;
     a.pd = (PairRec<R> *)s.pairs; a.fown = (v4<R> *)s.fown; a.gii = (v4<R> *)s.gii;
     a.wpart = (R *)s.wpart; a.want_virial = want_virial; a.status = s.status;

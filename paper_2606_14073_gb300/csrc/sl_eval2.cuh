@@ -29,6 +29,8 @@ struct Eval2Args {
     int32_t *clj;      // compact in-cutoff rows [cap_ang + cap][n]: neighbour index
     uint16_t *cls;     // ... its candidate slot s (low byte) and the reverse slot rev[s][i] (high byte)
     int4 *cnt;         // (angular rows of species 0, angular rows, radial-only rows of species 0, radial-only rows)
+    uint32_t *mask;    // [maskw][n]: bit s of word s/32 set when candidate slot s is inside rc_rad
+    int maskw;
     R *q, *bsum, *fp, *ei;
     PairRec<R> *pd;    // [cap][n]
     v4<R> *fown, *gii;

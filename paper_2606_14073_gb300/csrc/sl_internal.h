@@ -105,6 +105,8 @@ struct Sys {
     int32_t *clj = nullptr;    // [cap_ang + cap][n] compact in-cutoff neighbours
     uint16_t *cls = nullptr;   // [cap_ang + cap][n] candidate slot | reverse slot << 8
     int4 *cnt = nullptr;       // [n] compact row counts
+    uint32_t *cmask = nullptr; // [maskw][n] in-cutoff candidate slots (the gather's walk)
+    int maskw = 0;             // ceil(cap / 32)
     void *fown = nullptr;      // [n] v4: sum_j dE_i/dr_ij
     void *gii = nullptr;       // [n] v4: dE_i/dS_i
     void *wpart = nullptr;     // [9][n] per-atom virial parts

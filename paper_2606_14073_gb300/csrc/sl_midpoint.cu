@@ -284,7 +284,7 @@ template <typename R>
 GatherArgs<R> mid_gather_args(Sys &s) {
     GatherArgs<R> g;
     g.fown = (const v4<R> *)s.fown; g.gii = (const v4<R> *)s.gii; g.pd = (const PairRec<R> *)s.pairs;
-    g.cls = s.cls; g.cnt = s.cnt; g.n = s.n; g.cap_ang = s.cap_ang;
+    g.mask = s.cmask; g.maskw = s.maskw; g.n = s.n;
     return g;
 }
 

@@ -13,10 +13,9 @@ template <typename R>
 struct GatherArgs {
     const v4<R> *fown, *gii;
     const PairRec<R> *pd;
-    const uint16_t *cls;
-    const int4 *cnt;
+    const uint32_t *mask;   // in-cutoff candidate slots, [maskw][n]
+    int maskw;
     int64_t n;
-    int cap_ang;
 };
 
 __device__ __forceinline__ void omega_of(double sx, double sy, double sz, double hx, double hy, double hz,
@@ -65,21 +64,24 @@ __device__ __forceinline__ void omega_of_f(float sx, float sy, float sz, float h
 }
 
 // F_k = sum_j dE_k/dr_kj - sum_j dE_j/dr_jk, H_k = -dE_k/dS_k - sum_j dE_j/dS_k: the
-// records (dE_j/dr_jk, dE_j/dS_k) sit in k's own in-cutoff slots.
+// records (dE_j/dr_jk, dE_j/dS_k) sit in k's own in-cutoff candidate slots.  The slots
+// are walked in order by the whole warp at once, so the records that neighbouring atoms
+// read at one slot are neighbours in memory (slot-major layout).
 template <typename R>
 __device__ __forceinline__ void gather(const GatherArgs<R> &g, int64_t k, double F[3], double H[3]) {
     const v4<R> fo = g.fown[k], gi = g.gii[k];
     R fx = fo.x, fy = fo.y, fz = fo.z, hx = -gi.x, hy = -gi.y, hz = -gi.z;
-    const int4 c = g.cnt[k];
     const int64_t N = g.n;
 #pragma unroll 1
-    for (int part = 0; part < 2; ++part) {
-        const int lo = part ? g.cap_ang : 0, hi = part ? g.cap_ang + c.w : c.y;
-        for (int row = lo; row < hi; ++row) {
-            const int s = g.cls[(int64_t)row * N + k] & 0xff;
-            const PairRec<R> e = g.pd[(int64_t)s * N + k];
-            fx -= e.a.x; fy -= e.a.y; fz -= e.a.z;
-            hx -= e.a.w; hy -= e.b.x; hz -= e.b.y;
+    for (int w = 0; w < g.maskw; ++w) {
+        const uint32_t word = g.mask[(int64_t)w * N + k];
+#pragma unroll 4
+        for (int b = 0; b < 32; ++b) {
+            if ((word >> b) & 1u) {
+                const PairRec<R> e = g.pd[(int64_t)(w * 32 + b) * N + k];
+                fx -= e.a.x; fy -= e.a.y; fz -= e.a.z;
+                hx -= e.a.w; hy -= e.b.x; hz -= e.b.y;
+            }
         }
     }
     F[0] = (double)fx; F[1] = (double)fy; F[2] = (double)fz;

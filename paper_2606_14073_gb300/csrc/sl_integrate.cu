@@ -245,9 +245,7 @@ void launch_gather(Sys &s, bool carried) {
                                                                    s.status, s.Bat);
 }
 
-__global__ void k_set_flag(int *flag) { *flag = 1; }
 
-void launch_mark_rebuild(Sys &s) { k_set_flag<<<1, 1, 0, s.stream>>>(s.rebuild); }
 
 // ------------------------------------------------------------------ reductions
 // Deterministic two-level FP64 sums: fixed 256 blocks, each summing a fixed

@@ -186,7 +186,6 @@ size_t midpoint_scratch_doubles();
 int texture_grid(const Sys &s, int normal, double cell, int *na, int *nb);
 cudaError_t launch_texture(Sys &s, int normal, double cell, double *h_m, double *Q);
 void launch_gather(Sys &s, bool carried);
-void launch_mark_rebuild(Sys &s);
 int reduce_energy_virial(Sys &s, double *E, double *W, bool want_virial);
 
 int launch_noalloc(const NepDev<double> &P, const double4 *pos, const double4 *spin, const int32_t *species, int n,

@@ -332,8 +332,6 @@ __global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDe
 
 }  // namespace tc
 
-int mlp_tc_blocks_per_sm() { return 1; }
-
 void launch_network_tc(Sys &s) {
     static bool attr = false;
     if (!attr) {

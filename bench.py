@@ -503,6 +503,59 @@ def run_protocol(args):
     return 0
 
 
+def run_accuracy(args):
+    """Mixed-precision error on identical states along an FP64 trajectory of the 884,736-atom
+    workload: the FP64 system runs --fp64-steps steps (default here 1000) at 300 K; at
+    steps 0, half and the end its state is copied into a mixed-precision system
+    (sl_set_state) and forces and fields are compared over all atoms; the FP64 GPU values
+    are checked against the FP64 oracle on a seeded 1% sample (8,847 atoms)."""
+    import torch
+    from oracle import oracle as O
+    from paper_2606_14073_gb300 import nep_params, spinlat as S, workloads as W
+    torch.cuda.set_device(0)
+    params = nep_params.load()
+    model = O.Model(params)
+    wl = W.fege_884k()
+    total = args.fp64_steps
+    checkpoints = [0, total // 2, total]
+    sample = np.sort(np.random.default_rng(20260103).choice(wl.n, wl.n // 100, replace=False))
+    sysd = S.system_from_workload(wl, params, precision=S.SL_PREC_FP64, steps_per_graph=args.graph_steps)
+    sysm = S.system_from_workload(wl, params, precision=S.SL_PREC_MIXED, steps_per_graph=args.graph_steps)
+    rows, done = [], 0
+    t0 = time.perf_counter()
+    for c in checkpoints:
+        if c > done:
+            sysd.step(c - done, DT, TEMP, FIELD)
+            done = c
+        st = sysd.get_state()
+        sysm.set_state(st["positions"], st["velocities"], st["spins"], st["forces"], st["fields"], st["step"],
+                       ref_positions=st["ref_positions"])
+        rd = sysd.energy_forces_fields(want_virial=False)
+        rm = sysm.energy_forces_fields(want_virial=False)
+        ref = O.evaluate_subset(model, st["positions"], st["spins"], wl.species, wl.box, wl.periodic, sample, FIELD)
+        rows.append({"step": c,
+                     "mixed_force_rmse_eV_per_A": float(np.sqrt(((rm["F"] - rd["F"]) ** 2).mean())),
+                     "mixed_field_rmse_eV": float(np.sqrt(((rm["H"] - rd["H"]) ** 2).mean())),
+                     "mixed_energy_err_eV_per_atom": abs(rm["E"] - rd["E"]) / wl.n,
+                     "fp64_vs_oracle_sample_max_rel_F": float(np.abs(rd["F"][sample] - ref["F"]).max() /
+                                                              np.abs(ref["F"]).max()),
+                     "fp64_vs_oracle_sample_max_rel_H": float(np.abs(rd["H"][sample] - ref["H"]).max() /
+                                                              np.abs(ref["H"]).max()),
+                     "force_rms_eV_per_A": float(np.sqrt((rd["F"] ** 2).mean()))})
+    secs = time.perf_counter() - t0
+    sysd.destroy()
+    sysm.destroy()
+    line = _common_line(args, wl.n * total / secs, secs * 1e3, max(total, 1), WORKLOAD,
+                        {"atoms": wl.n, "precision": "FP64 trajectory, mixed evaluated on its states", "dt_fs": DT,
+                         "T_K": TEMP, "sample_atoms": int(len(sample)), "l2": "inputs larger than L2",
+                         "parallelism": "replicas x1"},
+                        None, None,
+                        {"mode": "accuracy", "timing": "wall clock of the whole check (FP64 steps, evaluations, "
+                                                       "oracle on the sample)", "states": rows})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     from paper_2606_14073_gb300 import flops, nep_params, spinlat as S, workloads as W
@@ -666,11 +719,13 @@ def main():
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=8.0, help="request arrivals per second")
-    ap.add_argument("--workload", choices=["cube", "slab", "replicas", "serve-sweep", "protocol"], default="cube",
+    ap.add_argument("--workload", choices=["cube", "slab", "replicas", "serve-sweep", "protocol", "accuracy"],
+                    default="cube",
                     help="cube: the 884,736-atom benchmark (default); slab: 3,276,800-atom helix slab with a "
                          "temperature ramp; replicas: 64 uneven replicas in one batched call; serve-sweep: "
                          "Poisson serving at multiples of the saturation rate; protocol: 1.57M-atom stripe at "
-                         "160 K in a stepped field with on-device texture diagnostics")
+                         "160 K in a stepped field with on-device texture diagnostics; accuracy: mixed vs FP64 "
+                         "on identical states at steps 0, half and the end of an FP64 trajectory (--fp64-steps)")
     ap.add_argument("--diag-every", type=int, default=500, help="protocol: steps between texture diagnostics")
     ap.add_argument("--ramp-steps", type=int, default=20000, help="slab: length of the 0 -> 280 K ramp")
     ap.add_argument("--midpoint-iters", type=int, default=0,
@@ -693,6 +748,8 @@ def main():
         return run_serve_sweep(args)
     if args.workload == "protocol":
         return run_protocol(args)
+    if args.workload == "accuracy":
+        return run_accuracy(args)
     return run_ours(args)
 
 

@@ -292,7 +292,7 @@ def run_slab(args):
     B = tuple(float(x) for x in wl.B)
     stream = torch.cuda.Stream()
     sysm = S.system_from_workload(wl, params, precision=S.SL_PREC_MIXED, stream=stream.cuda_stream,
-                                  steps_per_graph=args.graph_steps)
+                                  steps_per_graph=args.graph_steps, cap_rad=args.cap_rad, cap_ang=args.cap_ang)
     nr0, na0 = sample_neighbour_stats(wl.positions, wl.box, wl.periodic)
     T_end, ramp = 280.0, float(args.ramp_steps)
     chunk = args.graph_steps
@@ -311,9 +311,14 @@ def run_slab(args):
     e0.record(stream)
     w0.record(stream)
     done, win = 0, 2000
+    stopped = None
     while done < args.steps:
         k = min(chunk, args.steps - done)
-        sysm.step(k, DT, temp(done), B)
+        try:
+            sysm.step(k, DT, temp(done), B)
+        except S.SpinlatError as e:   # the library restored the state at the start of the call
+            stopped = {"at_step": done, "error": str(e)}
+            break
         done += k
         if done % win == 0 or done == args.steps:
             w1 = torch.cuda.Event(enable_timing=True)
@@ -333,13 +338,16 @@ def run_slab(args):
     win_rates = [{"end_step": d, "T_K": temp(d), "atom_steps_per_s": wl.n * win / (a.elapsed_time(b) * 1e-3)}
                  for d, a, b in windows if d % win == 0]
     sysm.destroy()
-    line = _common_line(args, wl.n * args.steps / (ms * 1e-3), ms, args.steps, wl.name,
+    steps_run = max(done, 1)
+    line = _common_line(args, wl.n * steps_run / (ms * 1e-3), ms, steps_run, wl.name,
                         {"atoms": wl.n, "precision": "mixed", "dt_fs": DT, "T_K": f"0 -> 280 over {args.ramp_steps} steps",
                          "B_T": list(B), "periodic": [1, 1, 0], "helix_period_A": float(wl.box[0] / round(wl.box[0] / 700.0)),
                          "steps_per_graph": chunk, "l2": "inputs larger than L2 (~37 GB working set)",
                          "parallelism": "replicas x1"},
                         clk, info1["n_launches"] - info0["n_launches"],
-                        {"mode": "slab", "neighbour_builds": info1["n_builds"] - info0["n_builds"],
+                        {"mode": "slab", "steps_requested": args.steps, "stopped": stopped,
+                         "caps": [args.cap_rad, args.cap_ang],
+                         "neighbour_builds": info1["n_builds"] - info0["n_builds"],
                          "windows_2000_steps": win_rates,
                          "drift": {"mean_neighbours_6A": [nr0, nr1], "mean_neighbours_4A": [na0, na1],
                                    "atoms_beyond_surfaces_5A": left}})
@@ -728,6 +736,8 @@ def main():
                          "on identical states at steps 0, half and the end of an FP64 trajectory (--fp64-steps)")
     ap.add_argument("--diag-every", type=int, default=500, help="protocol: steps between texture diagnostics")
     ap.add_argument("--ramp-steps", type=int, default=20000, help="slab: length of the 0 -> 280 K ramp")
+    ap.add_argument("--cap-rad", type=int, default=160, help="slab: radial candidate-list capacity")
+    ap.add_argument("--cap-ang", type=int, default=64, help="slab: angular candidate-list capacity")
     ap.add_argument("--midpoint-iters", type=int, default=0,
                     help="cube: cap of the self-consistent midpoint spin update (0: predictor-corrector)")
     ap.add_argument("--midpoint-tol", type=float, default=1e-6)

@@ -119,3 +119,26 @@ def test_mixed_midpoint_stays_close_to_fp64(params):
     assert np.abs(np.linalg.norm(gm["spins"], axis=1) - 1).max() < 1e-14
     m.destroy()
     d.destroy()
+
+
+def test_midpoint_replicas_in_a_batch_match_alone(params):
+    wls = [W.fege_cube(c, seed=120 + c, replica=c) for c in (4, 5)]
+    kw = dict(midpoint_iters=5, midpoint_tol=1e-8, anderson_depth=2)
+    alone = []
+    for w in wls:
+        s = S.system_from_workload(w, params, replica=w.seed - W.LANGEVIN_SEED0, **kw)
+        s.step(12, 1.0, 200.0, (0, 0, 0.2))
+        alone.append((s.get_state(), s.midpoint_evaluations()))
+        s.destroy()
+    syss = [S.system_from_workload(w, params, replica=w.seed - W.LANGEVIN_SEED0, **kw) for w in wls]
+    b = S.Batch(syss)
+    b.step(12, 1.0, 200.0, (0, 0, 0.2))
+    assert b.graph_launches() == 1
+    for s, (ref, ev) in zip(syss, alone):
+        g = s.get_state()
+        for key in ("positions", "velocities", "spins", "forces", "fields"):
+            assert np.array_equal(g[key], ref[key]), key
+        assert s.midpoint_evaluations() == ev
+    b.destroy()
+    for s in syss:
+        s.destroy()

@@ -316,3 +316,26 @@ def test_autotune_leaves_state_and_results_unchanged(params, prec):
         assert np.array_equal(ga[k], gb[k]), k
     a.destroy()
     b.destroy()
+
+
+@pytest.mark.parametrize("only", [0, 1])
+def test_single_species_systems_match_oracle(params, model, only):
+    """All-Fe and all-Ge systems (one species block, empty second block) in both precisions."""
+    wl = W.fege_cube(4, seed=95)
+    species = np.full(wl.n, only, np.int32)
+    B = (0.0, 0.1, 0.2)
+    for prec in (S.SL_PREC_FP64, S.SL_PREC_MIXED):
+        s = S.System(wl.positions, wl.spins, wl.box, wl.periodic, species, params, wl.velocities, precision=prec)
+        s.step(0, 1.0, 0.0, B)
+        r = s.energy_forces_fields()
+        pos, spin = gpu_state(s)
+        ref = O.evaluate(model, pos, spin, species, wl.box, wl.periodic, B)
+        if prec == S.SL_PREC_FP64:
+            assert maxrel(r["F"], ref["F"]) <= FP64_TOL and maxrel(r["H"], ref["H"]) <= FP64_TOL
+            assert abs(r["E"] - ref["E"]) <= FP64_TOL * abs(ref["E"])
+        else:
+            assert np.sqrt(((r["F"] - ref["F"]) ** 2).mean()) <= 1e-3
+            assert np.sqrt(((r["H"] - ref["H"]) ** 2).mean()) <= 1e-3
+        s.step(12, 1.0, 300.0, B)
+        assert np.isfinite(s.get_state()["positions"]).all()
+        s.destroy()

@@ -649,7 +649,7 @@ __device__ __forceinline__ void bwd_rows(const NepDev<R> &P, const Eval2Args<R> 
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128) k_bwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 2 : 1) k_bwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
     if (a.skip && *a.skip) return;
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

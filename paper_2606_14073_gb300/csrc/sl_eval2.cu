@@ -21,6 +21,8 @@
 //              dE_i/dS_i, virial) are reduced over the quad.
 // The force/field gather (sl_integrate.cu) then reads, for atom k, the records of
 // its in-cutoff slots only.
+#include <mutex>
+
 #include "sl_internal.h"
 #include "sl_eval2.cuh"
 
@@ -769,14 +771,20 @@ static constexpr size_t bwdf_smem(int qb = quad_block<R>()) { return (size_t)(qb
 
 int default_quad_block(int prec) { return prec == 0 ? quad_block<double>() : quad_block<float>(); }
 
+// Dynamic shared-memory limits of the quad kernels, set once per device (function
+// attributes belong to the device's context), safe to call from several threads.
 void eval2_init() {
-    static bool done = false;
-    if (done) return;
+    static std::mutex mu;
+    static uint64_t done = 0;   // bit d: device d is set up
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 64 && (done >> dev & 1u)) return;
     cudaFuncSetAttribute(k_ang_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<float>());
     cudaFuncSetAttribute(k_ang_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<double>());
     cudaFuncSetAttribute(k_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<float>());
     cudaFuncSetAttribute(k_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<double>());
-    done = true;
+    if (dev < 64) done |= 1ull << dev;
 }
 
 template <typename R>

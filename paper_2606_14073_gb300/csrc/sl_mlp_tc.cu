@@ -18,6 +18,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "sl_internal.h"
 
@@ -333,13 +334,17 @@ __global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDe
 }  // namespace tc
 
 void launch_network_tc(Sys &s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(tc::k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM_BYTES);
-        attr = true;
-    }
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
+    {   // the shared-memory limit is a per-device function attribute: set it once per device
+        static std::mutex mu;
+        static uint64_t done = 0;
+        std::lock_guard<std::mutex> lk(mu);
+        if (!(dev < 64 && (done >> dev & 1u))) {
+            cudaFuncSetAttribute(tc::k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM_BYTES);
+            if (dev < 64) done |= 1ull << dev;
+        }
+    }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t ntiles = (s.n + tc::TM - 1) / tc::TM;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * s.cfg.mlp_ctas_per_sm);

@@ -99,9 +99,20 @@ class GpuBackend:
         return s
 
     def step(self, handles, n_steps, dts, Ts, Bs):
-        b = self.S.Batch(handles)
-        b.step(n_steps, dts, Ts, Bs)
-        b.destroy()
+        # the batch (and its captured graph over all replicas) is kept while the set of
+        # active replicas does not change
+        key = tuple(id(h) for h in handles)
+        if getattr(self, "_batch_key", None) != key:
+            self._drop_batch()
+            self._batch = self.S.Batch(handles)
+            self._batch_key = key
+        self._batch.step(n_steps, dts, Ts, Bs)
+
+    def _drop_batch(self):
+        b = getattr(self, "_batch", None)
+        if b is not None:
+            b.destroy()
+        self._batch, self._batch_key = None, None
 
     def result(self, h) -> dict:
         st = h.get_state()
@@ -111,6 +122,7 @@ class GpuBackend:
         return h.n
 
     def destroy(self, h):
+        self._drop_batch()   # a batch must not outlive one of its systems
         h.destroy()
 
 

@@ -975,3 +975,12 @@ int or_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Threads used by the following calls (for timing the oracle on one core). */
+void or_set_num_threads(int t) {
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}

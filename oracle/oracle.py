@@ -76,6 +76,8 @@ def lib():
             for f in ("or_neighbors", "or_descriptors", "or_evaluate", "or_evaluate_subset", "or_run"):
                 getattr(_lib, f).restype = C.c_int
             _lib.or_num_threads.restype = C.c_int
+            _lib.or_set_num_threads.argtypes = [C.c_int]
+            _lib.or_set_num_threads.restype = None
         return _lib
 
 
@@ -263,6 +265,10 @@ def run(model: Model, st: State, n_steps: int, dt: float, T: float, B=(0.0, 0.0,
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_num_threads(t: int):
+    lib().or_set_num_threads(int(t))
 
 
 def kinetic_energy(vel, species, masses):

@@ -32,7 +32,9 @@
  *            (spin-weighted angular group, Section 5.1.2)
  *  - network (Section 5.2.3 "ANN", one hidden tanh layer):
  *      E_i = sum_h w1_h tanh(sum_v W0_hv s_v q_v - b0_h) - b1;
- *  - Zeeman: E_Z = -sum_i mu_i mu_B B_i.S_i, B_i = B + (optional per-atom part).
+ *  - Zeeman: E_Z = -sum_i mu_i mu_B B_i.S_i, B_i = B + (optional per-atom part);
+ *  - optional Landau onsite energy for variable moment lengths (longitudinal
+ *    fluctuation, Section 3): E_L = sum_i a_t |S_i|^2 + b_t |S_i|^4 per species t.
  * The angular channels are evaluated here as the plain Legendre double sum over
  * neighbour pairs (their definition), not through spherical harmonics.
  *
@@ -83,7 +85,18 @@ typedef struct {
     const double *moment_muB; /* [ns] */
     const double *B_atoms;    /* [n][3] per-atom external field, T, added to the uniform B;
                                  NULL: none (the same field on every atom)          */
+    const double *landau;     /* [ns][2] (a, b) of E_L = a|S|^2 + b|S|^4, eV; NULL: none */
 } or_params;
+
+/* Landau onsite energy of atom i and its field -dE_L/dS_i. */
+static double landau_at(const or_params *P, int t, const double S[3], double h[3]) {
+    if (!P->landau) { h[0] = h[1] = h[2] = 0.0; return 0.0; }
+    const double a = P->landau[2 * t], b = P->landau[2 * t + 1];
+    const double m2 = S[0] * S[0] + S[1] * S[1] + S[2] * S[2];
+    const double k = -(2.0 * a + 4.0 * b * m2);
+    for (int c = 0; c < 3; ++c) h[c] = k * S[c];
+    return a * m2 + b * m2 * m2;
+}
 
 /* External field on atom i: the uniform B plus the atom's own part. */
 static void field_at(const or_params *P, const double B[3], int64_t i, double out[3]) {
@@ -99,6 +112,8 @@ typedef struct {
     int32_t anderson_depth;   /* 0: plain fixed-point iteration; > 0: Anderson history     */
     double midpoint_tol;      /* stop when max_i |G_i - X_i| < tol (0: always the cap)      */
     double anderson_reg;      /* Tikhonov weight, relative to the mean diagonal              */
+    int32_t longitudinal;     /* 1: variable moment lengths (no renormalisation)            */
+    double alpha_long;        /* dimensionless damping of the longitudinal mode              */
 } or_dynamics;
 
 static int or_dim(int n_ch) { return 1 + 13 * n_ch; }
@@ -611,8 +626,10 @@ int or_evaluate(int64_t n, const double *pos, const double *spin, const int32_t 
         double zee = P->moment_muB[species[i]] * OR_MUB, Bi[3];
         field_at(P, B, i, Bi);
         Etot -= zee * (Bi[0] * spin[3 * i] + Bi[1] * spin[3 * i + 1] + Bi[2] * spin[3 * i + 2]);
+        double hl[3];
+        Etot += landau_at(P, species[i], spin + 3 * i, hl);
         if (H)
-            for (int c = 0; c < 3; ++c) H[3 * i + c] += -Gs[3 * i + c] + zee * Bi[c];
+            for (int c = 0; c < 3; ++c) H[3 * i + c] += -Gs[3 * i + c] + zee * Bi[c] + hl[c];
         for (int64_t p = nl.off[i]; p < nl.off[i + 1]; ++p) {
             int64_t j = nl.idx[p];
             if (F)
@@ -677,7 +694,9 @@ int or_evaluate_subset(int64_t n, const double *pos, const double *spin, const i
         double f[3] = {0, 0, 0}, h[3];
         double zee = P->moment_muB[species[k]] * OR_MUB, Bk[3];
         field_at(P, B, k, Bk);
-        for (int c = 0; c < 3; ++c) h[c] = -Gs[3 * ck + c] + zee * Bk[c];
+        double hl[3];
+        landau_at(P, species[k], spin + 3 * k, hl);
+        for (int c = 0; c < 3; ++c) h[c] = -Gs[3 * ck + c] + zee * Bk[c] + hl[c];
         /* own pairs */
         for (int64_t p = nl.off[k], a = 0; p < nl.off[k + 1]; ++p, ++a)
             for (int c = 0; c < 3; ++c) f[c] += D[3 * (poff[ck] + a) + c];
@@ -875,7 +894,17 @@ out:
  *   f_j = G_j - X_j;  dF, dG = differences of the last k+1 f_j, G_j (k = min(depth, m));
  *   (dF^T dF + delta I) g = dF^T f_m,  delta = anderson_reg * trace(dF^T dF) / k;
  *   X_{m+1} = G_m - dG g, each spin renormalised.
- * *iters_used (if not NULL) receives the number of midpoint evaluations over all steps. */
+ * *iters_used (if not NULL) receives the number of midpoint evaluations over all steps.
+ *
+ * Longitudinal mode (dyn->longitudinal = 1; the moment length |S_i| is free, Section 3).
+ * The spin equation is the Langevin form with longitudinal fluctuations of Ma and
+ * Dudarev (Phys. Rev. B 86, 054416, 2012), in this file's precession convention:
+ *   dS/dt = (H/hbar) x S + (alpha/hbar) H + xi,  <xi_a(t) xi_b(t')> = 2 alpha kT/hbar delta_ab delta(t-t'),
+ * whose stationary density is exp(-E/kT) over R^3.  The step keeps the lattice part and
+ * the predictor-corrector structure (Heun on the spin equation, the same noise in both):
+ *   Sstar = Rot(S, H dt/hbar) + alpha dt/hbar H + sqrt(2 alpha kT dt/hbar) zeta;
+ *   S <- Rot(S, (H + Hstar) dt/(2 hbar)) + alpha dt/hbar (H + Hstar)/2 + sqrt(2 alpha kT dt/hbar) zeta,
+ * with no renormalisation; lambda_spin is not used.  Not combined with the midpoint mode. */
 int or_run(int64_t n, double *pos, double *vel, double *spin, const int32_t *species, const double *box,
            const int32_t *per, const or_params *P, const or_dynamics *dyn, int64_t n_steps, double dt,
            double T, const double B[3], uint64_t step0, double *F, double *H, int have_fh,
@@ -884,6 +913,8 @@ int or_run(int64_t n, double *pos, double *vel, double *spin, const int32_t *spe
     if (dyn->midpoint_iters < 0 || dyn->anderson_depth < 0 || dyn->anderson_depth > OR_AA_MAX ||
         !(dyn->midpoint_tol >= 0.0) || !(dyn->anderson_reg >= 0.0))
         return -3;
+    const int lng = dyn->longitudinal != 0;
+    if (lng && (dyn->midpoint_iters > 0 || !(dyn->alpha_long >= 0.0))) return -3;
     if (iters_used) *iters_used = 0;
     int rc;
     if (!have_fh) {
@@ -897,8 +928,10 @@ int or_run(int64_t n, double *pos, double *vel, double *spin, const int32_t *spe
     double *pmid = malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     if (!S0 || !eta || !Fs || !Hs || !pmid) return -1;
     const double cfric = exp(-dyn->gamma_lattice * dt);
-    const double lam = dyn->lambda_spin;
-    const double sig_eta = (T > 0.0 && lam > 0.0) ? sqrt(2.0 * lam * OR_KB * T * OR_HBAR / dt) : 0.0;
+    const double lam = lng ? 0.0 : dyn->lambda_spin;
+    const double sig_eta = lng ? ((T > 0.0 && dyn->alpha_long > 0.0) ? sqrt(2.0 * dyn->alpha_long * OR_KB * T * dt / OR_HBAR) : 0.0)
+                               : ((T > 0.0 && lam > 0.0) ? sqrt(2.0 * lam * OR_KB * T * OR_HBAR / dt) : 0.0);
+    const double kdrift = lng ? dyn->alpha_long * dt / OR_HBAR : 0.0;   /* longitudinal drift per unit field */
     for (int64_t s = 0; s < n_steps; ++s) {
         uint64_t step = step0 + (uint64_t)s;
         for (int64_t i = 0; i < n; ++i) {
@@ -923,6 +956,13 @@ int or_run(int64_t n, double *pos, double *vel, double *spin, const int32_t *spe
                 eta[3 * i + c] = sig_eta * ze[c];
             }
             double Hp[3], w[3];
+            if (lng) {   /* eta is the additive noise displacement here */
+                for (int c = 0; c < 3; ++c) S0[3 * i + c] = spin[3 * i + c];
+                omega_of(S0 + 3 * i, H + 3 * i, 0.0, w);
+                or_rotate(S0 + 3 * i, w, dt, spin + 3 * i);
+                for (int c = 0; c < 3; ++c) spin[3 * i + c] += kdrift * H[3 * i + c] + eta[3 * i + c];
+                continue;
+            }
             for (int c = 0; c < 3; ++c) { S0[3 * i + c] = spin[3 * i + c]; Hp[c] = H[3 * i + c] + eta[3 * i + c]; }
             omega_of(S0 + 3 * i, Hp, lam, w);
             or_rotate(S0 + 3 * i, w, dt, spin + 3 * i);
@@ -947,6 +987,19 @@ int or_run(int64_t n, double *pos, double *vel, double *spin, const int32_t *spe
         for (int64_t i = 0; i < n; ++i) {
             double m = P->mass_amu[species[i]];
             double Hp0[3], Hp1[3], w0[3], w1[3], w[3], Snew[3];
+            if (lng) {
+                double Hb[3];
+                for (int c = 0; c < 3; ++c) Hb[c] = 0.5 * (H[3 * i + c] + Hs[3 * i + c]);
+                omega_of(S0 + 3 * i, Hb, 0.0, w);
+                or_rotate(S0 + 3 * i, w, dt, Snew);
+                for (int c = 0; c < 3; ++c) {
+                    spin[3 * i + c] = Snew[c] + kdrift * Hb[c] + eta[3 * i + c];
+                    vel[3 * i + c] += 0.5 * dt * Fs[3 * i + c] * OR_ACC / m;
+                    F[3 * i + c] = Fs[3 * i + c];
+                    H[3 * i + c] = Hs[3 * i + c];
+                }
+                continue;
+            }
             for (int c = 0; c < 3; ++c) {
                 Hp0[c] = H[3 * i + c] + eta[3 * i + c];
                 Hp1[c] = Hs[3 * i + c] + eta[3 * i + c];

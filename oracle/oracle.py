@@ -47,14 +47,16 @@ class _Params(C.Structure):
                 ("n_hidden", C.c_int32), ("rc_rad", C.c_double), ("rc_ang", C.c_double),
                 ("coeffs", C.c_void_p), ("q_scaler", C.c_void_p), ("w0", C.c_void_p),
                 ("b0", C.c_void_p), ("w1", C.c_void_p), ("b1", C.c_double),
-                ("mass_amu", C.c_void_p), ("moment_muB", C.c_void_p), ("B_atoms", C.c_void_p)]
+                ("mass_amu", C.c_void_p), ("moment_muB", C.c_void_p), ("B_atoms", C.c_void_p),
+                ("landau", C.c_void_p)]
 
 
 class _Dyn(C.Structure):
     _fields_ = [("gamma_lattice", C.c_double), ("lambda_spin", C.c_double),
                 ("seed", C.c_uint64), ("replica", C.c_uint64),
                 ("midpoint_iters", C.c_int32), ("anderson_depth", C.c_int32),
-                ("midpoint_tol", C.c_double), ("anderson_reg", C.c_double)]
+                ("midpoint_tol", C.c_double), ("anderson_reg", C.c_double),
+                ("longitudinal", C.c_int32), ("alpha_long", C.c_double)]
 
 
 def lib():
@@ -92,7 +94,9 @@ def _f64(a):
 class Model:
     """NEP-SPIN parameters in the oracle's layout (see nep_params in the package)."""
 
-    def __init__(self, p: dict):
+    def __init__(self, p: dict, landau=None):
+        """landau: optional [n_species][2] (a, b) of the onsite energy a|S|^2 + b|S|^4 (eV)."""
+        self.landau = None if landau is None else _f64(landau).reshape(-1, 2).ravel().copy()
         self.n_species = int(p["n_species"])
         self.n_ch = int(p["n_ch"])
         self.basis_k = int(p["basis_k"])
@@ -119,6 +123,7 @@ class Model:
         s.b0, s.w1, s.b1 = _p(self.b0), _p(self.w1), self.b1
         s.mass_amu, s.moment_muB = _p(self.mass), _p(self.moment)
         s.B_atoms = None if B_atoms is None else _p(B_atoms)
+        s.landau = _p(self.landau)
         return s
 
 
@@ -240,16 +245,17 @@ class State:
 
 def run(model: Model, st: State, n_steps: int, dt: float, T: float, B=(0.0, 0.0, 0.0), *,
         gamma=0.01, lam=0.1, seed=1234, replica=0, midpoint_iters=0, midpoint_tol=0.0, anderson_depth=0,
-        anderson_reg=1e-10, B_atoms=None):
+        anderson_reg=1e-10, B_atoms=None, longitudinal=False, alpha_long=0.0):
     """Advance st by n_steps steps (or_run).  midpoint_iters > 0 selects the self-consistent
     midpoint spin update (cap of the iteration, tolerance midpoint_tol, optional Anderson
     history anderson_depth with relative regularisation anderson_reg).  Returns st; the
     number of midpoint evaluations of the call is in st.last_iterations.  B_atoms is the
-    optional per-atom part of the external field ([n][3] tesla)."""
+    optional per-atom part of the external field ([n][3] tesla).  longitudinal=True frees the
+    moment lengths (Langevin form with longitudinal damping alpha_long; lam is then unused)."""
     ba = _batoms(B_atoms, st.pos.shape[0])
     P = model.c_struct(ba)
     dyn = _Dyn(gamma, lam, seed, replica, int(midpoint_iters), int(anderson_depth), float(midpoint_tol),
-               float(anderson_reg))
+               float(anderson_reg), int(bool(longitudinal)), float(alpha_long))
     Bv = _f64(B)
     it = np.zeros(1, dtype=np.int64)
     rc = lib().or_run(st.pos.shape[0], _p(st.pos), _p(st.vel), _p(st.spin), _p(st.species), _p(st.box),

@@ -150,7 +150,7 @@ int sl_get_state(const sl_system *sys, double *positions, double *velocities, do
 /* Replace the state.  positions/velocities/spins may not be NULL.  If forces and
  * fields are both given they become the carried integrator values; if both are
  * NULL they are re-evaluated at the new state.  Spins off unit length by more than
- * rounding are normalised.  ref_positions (may be NULL): the
+ * rounding are normalised (not in the longitudinal mode, sl_set_longitudinal).  ref_positions (may be NULL): the
  * lists are rebuilt from these positions instead of the new ones.  Given the
  * forces, fields and ref_positions of sl_get_state, the continued trajectory is
  * bit-identical to the uninterrupted one, in this or in any other system. */
@@ -179,6 +179,23 @@ int sl_get_info(const sl_system *sys, int64_t *n_atoms, int32_t *precision, int6
  * The paper's production protocol uses a field that steps along x (Fig. 7).
  * SL_EINVAL for a non-finite entry. */
 int sl_set_atom_fields(sl_system *sys, const double *B_atoms);
+
+/* Longitudinal moment mode (the paper's integrator includes longitudinal fluctuation of
+ * the magnetic moments, Section 3; it prints no equation, so this follows the Langevin
+ * form with longitudinal damping of Ma and Dudarev, Phys. Rev. B 86, 054416, 2012).
+ * With enable != 0 the spin lengths |S_i| become dynamical: the energy gains the Landau
+ * onsite term sum_i a_t |S_i|^2 + b_t |S_i|^4 (landau: [n_species][2] = (a, b) in eV,
+ * NULL for none; it also enters -dE/dS and the energy of sl_energy_forces_fields), the
+ * spin equation is dS/dt = (H/hbar) x S + (alpha/hbar) H + xi with <xi xi> = 2 alpha kB T/hbar
+ * (stationary density exp(-E/kT) over R^3), and each step is the predictor-corrector:
+ *   S* = Rot(S, H dt/hbar) + alpha dt/hbar H + s zeta,
+ *   S_next = Rot(S, (H + H*) dt/(2 hbar)) + alpha dt/hbar (H + H*)/2 + s zeta,
+ * s = sqrt(2 alpha kB T dt/hbar), zeta the spin stream's normals, no renormalisation;
+ * the options' lambda_spin is not used.  sl_set_state keeps the given spin lengths.
+ * enable = 0 returns to unit spins (each spin is normalised).  The carried forces and
+ * fields are re-evaluated.  SL_EINVAL for alpha < 0, a non-finite coefficient, or a
+ * system created with midpoint_iters > 0. */
+int sl_set_longitudinal(sl_system *sys, int32_t enable, double alpha, const double *landau);
 
 /* Texture diagnostics of a film with normal normal_axis (0, 1, 2), computed on the
  * device at the current state (Fig. 7 and Section 8 follow helix and skyrmion textures

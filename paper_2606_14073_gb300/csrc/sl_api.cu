@@ -149,12 +149,26 @@ void compute_step_params(const sl::Sys &s, double dt, double T, const double B[3
     P.lambda = s.lambda;
     P.wscale = 1.0 / ((1.0 + s.lambda * s.lambda) * HBAR);
     P.disp2 = 0.25 * s.skin * s.skin;
+    P.lng = s.lng;
+    P.lng_drift = 0.0;
+    P.lng_sig = 0.0;
+    for (int t = 0; t < NS; ++t) P.landau[t][0] = P.landau[t][1] = 0.0;
+    if (s.lng) {   // precession about H/hbar; damping and noise enter through the longitudinal terms
+        P.sig_eta = 0.0;
+        P.lambda = 0.0;
+        P.wscale = 1.0 / HBAR;
+        P.lng_drift = s.lng_alpha * dt / HBAR;
+        P.lng_sig = (T > 0 && s.lng_alpha > 0) ? std::sqrt(2.0 * s.lng_alpha * KB * T * dt / HBAR) : 0.0;
+        for (int t = 0; t < NS; ++t) { P.landau[t][0] = s.landau[t][0]; P.landau[t][1] = s.landau[t][1]; }
+    }
 }
 
 int upload_params(sl::Sys &s, double dt, double T, const double B[3]) {
     // the pinned host block may still be read by an earlier copy in flight
     CK(cudaStreamSynchronize(s.stream));
     compute_step_params(s, dt, T, B, *s.h_par);
+    s.last_dt = dt;
+    s.last_T = T;
     CK(cudaMemcpyAsync(s.d_par, s.h_par, sizeof(sl::StepDev), cudaMemcpyHostToDevice, s.stream));
     return SL_OK;
 }
@@ -697,7 +711,8 @@ int sl_set_state(sl_system *sys, const double *pos, const double *vel, const dou
             if (!std::isfinite(pos[i]) || !std::isfinite(vel[i]) || !std::isfinite(spins[i]) ||
                 (ref && !std::isfinite(ref[i])))
                 return fail(SL_EINVAL, "non-finite state value");
-        if ((rc = upload_vec(s, s.vel, vel, false)) || (rc = upload_vec(s, s.spin, spins, true))) return rc;
+        // unit spins are normalised on entry; in the longitudinal mode their lengths are state
+        if ((rc = upload_vec(s, s.vel, vel, false)) || (rc = upload_vec(s, s.spin, spins, !s.lng))) return rc;
         // lists from the reference positions (k_finish records them as the new reference)
         if ((rc = upload_vec(s, s.pos, ref ? ref : pos, false)) || (rc = refresh_copies(s))) return rc;
         CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
@@ -883,6 +898,34 @@ int sl_set_atom_fields(sl_system *sys, const double *B_atoms) {
     }
     if (s.n > 0 && (rc = upload_vec(s, s.Bat, B_atoms, false))) return rc;
     return SL_OK;
+}
+
+int sl_set_longitudinal(sl_system *sys, int32_t enable, double alpha, const double *landau) {
+    if (!sys) return fail(SL_EINVAL, "NULL system");
+    sl::Sys &s = sys->s;
+    if (enable) {
+        if (!(alpha >= 0) || !std::isfinite(alpha)) return fail(SL_EINVAL, "alpha must be finite and >= 0");
+        if (s.mid_iters > 0) return fail(SL_EINVAL, "the longitudinal mode does not combine with the midpoint update");
+        if (landau)
+            for (int k = 0; k < 2 * sl::NS; ++k)
+                if (!std::isfinite(landau[k])) return fail(SL_EINVAL, "non-finite Landau coefficient");
+    }
+    cudaSetDevice(s.device);
+    CK(cudaStreamSynchronize(s.stream));
+    const bool leaving = s.lng && !enable;
+    s.lng = enable ? 1 : 0;
+    s.lng_alpha = enable ? alpha : 0.0;
+    for (int t = 0; t < sl::NS; ++t)
+        for (int c = 0; c < 2; ++c)
+            s.landau[t][c] = (enable && landau) ? landau[2 * t + c] : 0.0;
+    int rc;
+    if ((rc = upload_params(s, s.last_dt, s.last_T, s.B))) return rc;
+    if (s.n == 0) return SL_OK;
+    CK(cudaMemsetAsync(s.status, 0, sizeof(int), s.stream));
+    if (leaving) sl::launch_normalise_spins(s);
+    // the carried forces and fields of the current state under the new energy
+    if ((rc = evaluate(s, false, true, false))) return rc;
+    return check_status(s);
 }
 
 int sl_texture_map(sl_system *sys, int32_t normal_axis, double cell, int32_t *n_a, int32_t *n_b, double *m,

@@ -10,7 +10,11 @@
 //   second half (k_second_half): gather F', H'; S = Rot(S, (omega(S,H+eta) + omega(S',H'+eta)) dt/2),
 //                                renormalised in FP64; v += dt/2 F'/m; (F, H) = (F', H')
 // omega(S, X) = (X + lambda S x X) / ((1 + lambda^2) hbar); Rot is the exact Rodrigues
-// rotation.  xi, zeta are Philox4x64-10 normals, streams 1 and 2, counter
+// rotation.  Longitudinal mode (variable |S|, Section 3; Langevin form with longitudinal
+// damping of Ma and Dudarev 2012): lambda = 0 and eta = 0 in the rotations, each spin
+// update adds alpha dt/hbar H (predictor: H; corrector: (H + H')/2) and the additive noise
+// sqrt(2 alpha kB T dt/hbar) zeta, and nothing is renormalised; the Landau onsite field
+// -(2a + 4b|S|^2) S joins H wherever the Zeeman field does.  xi, zeta are Philox4x64-10 normals, streams 1 and 2, counter
 // (step, caller index, stream, 0), key (seed, replica): the corrector regenerates
 // the predictor's eta bit for bit, so nothing is stored between the halves.
 #include "sl_internal.h"
@@ -34,6 +38,13 @@ struct IntArgs {
     int *rebuild, *status;
     uint64_t seed, replica;
 };
+
+// Landau onsite field -(2a + 4b|S|^2) S of atom i (species t), added to H.
+__device__ __forceinline__ void add_landau(const StepDev &P, int t, const double4 S, double H[3]) {
+    const double m2 = S.x * S.x + S.y * S.y + S.z * S.z;
+    const double k = -(2.0 * P.landau[t][0] + 4.0 * P.landau[t][1] * m2);
+    H[0] += k * S.x; H[1] += k * S.y; H[2] += k * S.z;
+}
 
 
 
@@ -85,11 +96,22 @@ __global__ void __launch_bounds__(256) k_first_half(IntArgs a) {
                    (float)H.y + fse * (float)ze[1], (float)H.z + fse * (float)ze[2], (float)P.lambda,
                    (float)P.wscale, w);
         rotate_delta_f((float)S.x, (float)S.y, (float)S.z, w[0], w[1], w[2], (float)P.dt, d);
+        if (P.lng) {
+            const float kd = (float)P.lng_drift, ks = (float)P.lng_sig;
+            d[0] += kd * (float)H.x + ks * (float)ze[0];
+            d[1] += kd * (float)H.y + ks * (float)ze[1];
+            d[2] += kd * (float)H.z + ks * (float)ze[2];
+        }
         Sp[0] = S.x + (double)d[0]; Sp[1] = S.y + (double)d[1]; Sp[2] = S.z + (double)d[2];
     } else {
         double w[3];
         omega_of(S.x, S.y, S.z, H.x + se * ze[0], H.y + se * ze[1], H.z + se * ze[2], P.lambda, P.wscale, w);
         rotate(S.x, S.y, S.z, w, P.dt, Sp);
+        if (P.lng) {
+            Sp[0] += P.lng_drift * H.x + P.lng_sig * ze[0];
+            Sp[1] += P.lng_drift * H.y + P.lng_sig * ze[1];
+            Sp[2] += P.lng_drift * H.z + P.lng_sig * ze[2];
+        }
     }
     a.pos[i] = r;
     a.vel[i] = v;
@@ -122,6 +144,7 @@ __global__ void __launch_bounds__(256) k_second_half(IntArgs a, GatherArgs<R> g)
         const double4 b = a.Bat[i];
         Hs[0] += P.mom[t] * b.x; Hs[1] += P.mom[t] * b.y; Hs[2] += P.mom[t] * b.z;
     }
+    if (P.lng) add_landau(P, t, a.spin[i], Hs);
     if constexpr (!SPIN) {
         double4 v = a.vel[i];
         const double hdt = P.half_dt, am = P.acc_m[t];
@@ -147,6 +170,12 @@ __global__ void __launch_bounds__(256) k_second_half(IntArgs a, GatherArgs<R> g)
                    (float)Hs[2] + fse * ze[2], lam, k, w1);
         rotate_delta_f((float)S0.x, (float)S0.y, (float)S0.z, 0.5f * (w0[0] + w1[0]), 0.5f * (w0[1] + w1[1]),
                        0.5f * (w0[2] + w1[2]), (float)P.dt, d);
+        if (P.lng) {
+            const float kd = (float)P.lng_drift, ks = (float)P.lng_sig;
+            d[0] += kd * (0.5f * ((float)H0.x + (float)Hs[0])) + ks * ze[0];
+            d[1] += kd * (0.5f * ((float)H0.y + (float)Hs[1])) + ks * ze[1];
+            d[2] += kd * (0.5f * ((float)H0.z + (float)Hs[2])) + ks * ze[2];
+        }
         Sn[0] = S0.x + (double)d[0]; Sn[1] = S0.y + (double)d[1]; Sn[2] = S0.z + (double)d[2];
     } else {
         double ze[3], w0[3], w1[3], w[3];
@@ -156,10 +185,16 @@ __global__ void __launch_bounds__(256) k_second_half(IntArgs a, GatherArgs<R> g)
                  w1);
         w[0] = 0.5 * (w0[0] + w1[0]); w[1] = 0.5 * (w0[1] + w1[1]); w[2] = 0.5 * (w0[2] + w1[2]);
         rotate(S0.x, S0.y, S0.z, w, P.dt, Sn);
+        if (P.lng) {
+            Sn[0] += P.lng_drift * (0.5 * (H0.x + Hs[0])) + P.lng_sig * ze[0];
+            Sn[1] += P.lng_drift * (0.5 * (H0.y + Hs[1])) + P.lng_sig * ze[1];
+            Sn[2] += P.lng_drift * (0.5 * (H0.z + Hs[2])) + P.lng_sig * ze[2];
+        }
     }
-    // renormalisation in FP64 after every rotation
-    const double inn = 1.0 / sqrt(Sn[0] * Sn[0] + Sn[1] * Sn[1] + Sn[2] * Sn[2]);
-    Sn[0] *= inn; Sn[1] *= inn; Sn[2] *= inn;
+    if (!P.lng) {   // renormalisation in FP64 after every rotation
+        const double inn = 1.0 / sqrt(Sn[0] * Sn[0] + Sn[1] * Sn[1] + Sn[2] * Sn[2]);
+        Sn[0] *= inn; Sn[1] *= inn; Sn[2] *= inn;
+    }
     double4 v = a.vel[i];
     const double hdt = P.half_dt, am = P.acc_m[t];
     v.x += hdt * Fs[0] * am; v.y += hdt * Fs[1] * am; v.z += hdt * Fs[2] * am;
@@ -176,7 +211,8 @@ __global__ void __launch_bounds__(256) k_second_half(IntArgs a, GatherArgs<R> g)
 // Forces and fields at the current state into (Fo, Ho).
 template <typename R>
 __global__ void __launch_bounds__(256) k_gather_only(GatherArgs<R> g, const StepDev *par, int64_t n_fe,
-                                                     double4 *Fo, double4 *Ho, int *status, const double4 *Bat) {
+                                                     double4 *Fo, double4 *Ho, int *status, const double4 *Bat,
+                                                     const double4 *spin) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     const int t = i < n_fe ? 0 : 1;
@@ -187,6 +223,7 @@ __global__ void __launch_bounds__(256) k_gather_only(GatherArgs<R> g, const Step
         const double4 b = Bat[i];
         Hs[0] += par->mom[t] * b.x; Hs[1] += par->mom[t] * b.y; Hs[2] += par->mom[t] * b.z;
     }
+    if (par->lng) add_landau(*par, t, spin[i], Hs);
     Fo[i] = make_double4(Fs[0], Fs[1], Fs[2], 0.0);
     Ho[i] = make_double4(Hs[0], Hs[1], Hs[2], 0.0);
     if (!(isfinite(Fs[0]) && isfinite(Fs[1]) && isfinite(Fs[2]) && isfinite(Hs[0]) && isfinite(Hs[1]) &&
@@ -239,10 +276,29 @@ void launch_gather(Sys &s, bool carried) {
     double4 *Fo = carried ? s.F : s.Fo, *Ho = carried ? s.H : s.Ho;
     if (s.prec == 0)
         k_gather_only<double><<<nblk(s.n, 256), 256, 0, s.stream>>>(gather_args<double>(s), s.d_par, s.n_fe, Fo, Ho,
-                                                                    s.status, s.Bat);
+                                                                    s.status, s.Bat, s.spin);
     else
         k_gather_only<float><<<nblk(s.n, 256), 256, 0, s.stream>>>(gather_args<float>(s), s.d_par, s.n_fe, Fo, Ho,
-                                                                   s.status, s.Bat);
+                                                                   s.status, s.Bat, s.spin);
+}
+
+// Unit length for every spin (leaving the longitudinal mode), FP64.
+__global__ void k_normalise_spins(double4 *spin, float4 *spinf, int64_t n, int *status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double4 S = spin[i];
+    const double n2 = S.x * S.x + S.y * S.y + S.z * S.z;
+    if (!(n2 > 0.0)) {
+        atomicOr(status, ST_NONFINITE);
+        return;
+    }
+    const double inn = 1.0 / sqrt(n2);
+    spin[i] = make_double4(S.x * inn, S.y * inn, S.z * inn, 0.0);
+    spinf[i] = make_float4((float)(S.x * inn), (float)(S.y * inn), (float)(S.z * inn), 0.f);
+}
+
+void launch_normalise_spins(Sys &s) {
+    if (s.n > 0) k_normalise_spins<<<nblk(s.n, 256), 256, 0, s.stream>>>(s.spin, s.spinf, s.n, s.status);
 }
 
 
@@ -269,6 +325,10 @@ __global__ void __launch_bounds__(256) k_reduce1(const R *__restrict__ ei, const
         if (Bat) {
             const double4 b = Bat[i];
             ez += par->mom[t] * (b.x * S.x + b.y * S.y + b.z * S.z);
+        }
+        if (par->lng) {
+            const double m2 = S.x * S.x + S.y * S.y + S.z * S.z;
+            ez -= par->landau[t][0] * m2 + par->landau[t][1] * m2 * m2;
         }
         acc[0] += (double)ei[i] - ez;
         if (want_virial)

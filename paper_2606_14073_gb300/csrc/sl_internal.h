@@ -24,6 +24,13 @@ struct StepDev {
     double zee[NS][3];          // mu_t muB B  (Zeeman field per species)
     double mom[NS];             // mu_t muB (scales the per-atom field part)
     double disp2;               // (skin/2)^2, rebuild threshold
+    // longitudinal mode (variable moment lengths): precession about H/hbar (lambda = 0,
+    // sig_eta = 0 above), plus the drift alpha dt/hbar H and the additive noise lng_sig zeta;
+    // no renormalisation.  landau: (a, b) of the onsite energy a|S|^2 + b|S|^4 per species.
+    int lng;
+    double lng_drift;           // alpha dt / hbar
+    double lng_sig;             // sqrt(2 alpha kB T dt / hbar)
+    double landau[NS][2];
 };
 
 // Device control block of the self-consistent midpoint iteration.
@@ -146,6 +153,13 @@ struct Sys {
     double *tex_part = nullptr;
     int64_t tex_cells = 0;
 
+    // longitudinal mode (sl_set_longitudinal) and the last step arguments, kept so the
+    // integrator constants can be rebuilt when the mode changes between steps
+    int lng = 0;
+    double lng_alpha = 0.0;
+    double landau[NS][2] = {{0, 0}, {0, 0}};
+    double last_dt = 1.0, last_T = 0.0;
+
     // self-consistent midpoint spin update (mid_iters = 0: predictor-corrector)
     int mid_iters = 0, aa_depth = 0;
     double mid_tol = 0.0, aa_reg = 1e-10;
@@ -186,6 +200,7 @@ size_t midpoint_scratch_doubles();
 int texture_grid(const Sys &s, int normal, double cell, int *na, int *nb);
 cudaError_t launch_texture(Sys &s, int normal, double cell, double *h_m, double *Q);
 void launch_gather(Sys &s, bool carried);
+void launch_normalise_spins(Sys &s);
 int reduce_energy_virial(Sys &s, double *E, double *W, bool want_virial);
 
 int launch_noalloc(const NepDev<double> &P, const double4 *pos, const double4 *spin, const int32_t *species, int n,

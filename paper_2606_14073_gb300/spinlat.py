@@ -24,7 +24,7 @@ EXPORTS = ["sl_default_options", "sl_create_system", "sl_step", "sl_energy_force
            "sl_destroy_system", "sl_last_error", "sl_batch_create", "sl_batch_step", "sl_batch_destroy",
            "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak", "sl_descriptors_energies_noalloc",
            "sl_estimate_device_bytes", "sl_get_midpoint_evaluations", "sl_set_atom_fields", "sl_texture_map",
-           "sl_batch_graph_launches", "sl_autotune"]
+           "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal"]
 KERNEL_GROUPS = ["first_half", "rebuild", "compact", "rad_fwd", "ang_fwd", "network", "backward", "second_half"]
 
 
@@ -73,6 +73,7 @@ def lib(path: str | None = None):
             L.sl_get_info.argtypes = [P, P, P, P, P]
             L.sl_get_midpoint_evaluations.argtypes = [P, P]
             L.sl_set_atom_fields.argtypes = [P, P]
+            L.sl_set_longitudinal.argtypes = [P, I32, D, P]
             L.sl_batch_graph_launches.argtypes = [P, P]
             L.sl_autotune.argtypes = [P, I32, P, P, P]
             L.sl_texture_map.argtypes = [P, I32, D, P, P, P, P]
@@ -95,7 +96,7 @@ def lib(path: str | None = None):
                       "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_batch_create",
                       "sl_batch_step", "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak",
                       "sl_descriptors_energies_noalloc", "sl_get_midpoint_evaluations", "sl_set_atom_fields",
-                      "sl_texture_map", "sl_batch_graph_launches", "sl_autotune"):
+                      "sl_texture_map", "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal"):
                 getattr(L, f).restype = C.c_int
             _lib = L
         return _lib
@@ -176,6 +177,15 @@ class System:
         if b is not None and b.shape != (self.n, 3):
             raise ValueError("B_atoms must have shape (n, 3)")
         _check(lib().sl_set_atom_fields(self.handle, _ptr(b)))
+
+    def set_longitudinal(self, enable: bool = True, alpha: float = 0.1, landau=None):
+        """Longitudinal moment mode: spin lengths become dynamical with damping alpha and the
+        optional Landau onsite energy landau [n_species][2] = (a, b), eV; enable=False returns
+        to unit spins."""
+        lan = None if landau is None else _f64(landau).reshape(-1)
+        if lan is not None and lan.shape != (4,):
+            raise ValueError("landau must have shape (2, 2)")
+        _check(lib().sl_set_longitudinal(self.handle, int(bool(enable)), float(alpha), _ptr(lan)))
 
     def texture(self, normal: int = 2, cell: float = 4.7):
         """(m [n_b][n_a][3], Q): coarse-grained film magnetisation and topological charge."""

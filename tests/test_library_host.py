@@ -96,3 +96,4 @@ def test_texture_grid_validation_needs_no_device():
     na, nb = C.c_int32(), C.c_int32()
     assert S.lib().sl_texture_map(None, 2, 4.7, C.byref(na), C.byref(nb), None, None) == S.SL_EINVAL
     assert S.lib().sl_set_atom_fields(None, None) == S.SL_EINVAL
+    assert S.lib().sl_set_longitudinal(None, 1, 0.1, None) == S.SL_EINVAL

@@ -63,6 +63,8 @@ def test_trajectory_matches_oracle(params, model):
     s = _long_system(params, wl, 0.2, steps_per_graph=10)
     st = s.get_state()
     o = O.State(st["positions"], st["velocities"], st["spins"], wl.species, wl.box, wl.periodic)
+    # the carried forces and fields (evaluated before the first step's field was given)
+    o.F, o.H, o.have_fh = st["forces"].copy(), st["fields"].copy(), True
     for chunk in (1, 4, 15):
         s.step(chunk, 1.0, 300.0, B)
         O.run(model, o, chunk, 1.0, 300.0, B, seed=wl.seed, longitudinal=True, alpha_long=0.2)

@@ -29,6 +29,19 @@
 namespace sl {
 
 // ------------------------------------------------------------------ helpers
+// Two independent multiply-adds per instruction where the hardware has them (FP32 pairs:
+// the packed FMA of sm_100 and later; each component rounds like fmaf), plain FMAs in FP64.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+template <typename R>
+__device__ __forceinline__ v2<R> pair2(R x, R y) {
+    v2<R> v;
+    v.x = x;
+    v.y = y;
+    return v;
+}
 template <typename R, int TI, int TJ, int G>
 __device__ __forceinline__ void contract_k(const NepDev<R> &P, const R f[NK], R g[NCH]) {
 #pragma unroll
@@ -300,9 +313,9 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_crad(const __gr
 }
 
 // ------------------------------------------------------------------ k_ang_fwd
-// stage of one angular pair: g_n (5), s g_n (5), pad (2), then the 24 harmonics in
-// lane-major order (position 12 + 6 ql + m holds p_lm of lm = ql + 4 m), so each quad
-// lane reads its six harmonics with three 2-wide loads
+// stage of one angular pair: (g_n, s g_n) interleaved for n = 0..4, pad (2), then the 24
+// harmonics in lane-major order (position 12 + 6 ql + m holds p_lm of lm = ql + 4 m), so
+// each quad lane reads its six harmonics with three 2-wide loads
 constexpr int FSTAGE = 36;
 constexpr int FQUAD = 4 * FSTAGE + 4;   // per quad, padded so quads start in different banks
 
@@ -319,9 +332,9 @@ __device__ __forceinline__ void ang_stage_fwd(const NepDev<R> &P, const Eval2Arg
     const R s = si.x * sj.x + si.y * sj.y + si.z * sj.z;
     v4<R> w0, w1;
     v2<R> w2;
-    w0.x = g[0]; w0.y = g[1]; w0.z = g[2]; w0.w = g[3];
-    w1.x = g[4]; w1.y = g[0] * s; w1.z = g[1] * s; w1.w = g[2] * s;
-    w2.x = g[3] * s; w2.y = g[4] * s;
+    w0.x = g[0]; w0.y = g[0] * s; w0.z = g[1]; w0.w = g[1] * s;
+    w1.x = g[2]; w1.y = g[2] * s; w1.z = g[3]; w1.w = g[3] * s;
+    w2.x = g[4]; w2.y = g[4] * s;
     reinterpret_cast<v4<R> *>(st)[0] = w0;
     reinterpret_cast<v4<R> *>(st)[1] = w1;
     reinterpret_cast<v2<R> *>(st)[4] = w2;
@@ -356,11 +369,11 @@ __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<
         na = c.y;
         ti = i < a.n_fe ? 0 : 1;
     }
-    R B[6][NCH], BS[6][NCH];
+    v2<R> BB[6][NCH];   // (B_nlm, BS_nlm) of the lane's six harmonics
 #pragma unroll
     for (int m = 0; m < 6; ++m)
 #pragma unroll
-        for (int n = 0; n < NCH; ++n) { B[m][n] = R(0); BS[m][n] = R(0); }
+        for (int n = 0; n < NCH; ++n) BB[m][n] = pair2<R>(R(0), R(0));
     const int nmax = __reduce_max_sync(0xffffffffu, na);
     // the lane's list entry two rounds ahead and its coordinates one round ahead are in flight
     v4<R> pjn, sjn;
@@ -396,19 +409,16 @@ __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<
             const v4<R> w0 = reinterpret_cast<const v4<R> *>(sp)[0];
             const v4<R> w1 = reinterpret_cast<const v4<R> *>(sp)[1];
             const v2<R> w2 = reinterpret_cast<const v2<R> *>(sp)[4];
-            const R g[NCH] = {w0.x, w0.y, w0.z, w0.w, w1.x};
-            const R gs[NCH] = {w1.y, w1.z, w1.w, w2.x, w2.y};
+            const v2<R> gg[NCH] = {pair2<R>(w0.x, w0.y), pair2<R>(w0.z, w0.w), pair2<R>(w1.x, w1.y),
+                                   pair2<R>(w1.z, w1.w), w2};
             const v2<R> *pp = reinterpret_cast<const v2<R> *>(sp + 12 + 6 * ql);
             const v2<R> p01 = pp[0], p23 = pp[1], p45 = pp[2];
             const R pv[6] = {p01.x, p01.y, p23.x, p23.y, p45.x, p45.y};
 #pragma unroll
             for (int m = 0; m < 6; ++m) {
-                const R pl = pv[m];
+                const v2<R> pl = pair2<R>(pv[m], pv[m]);
 #pragma unroll
-                for (int n = 0; n < NCH; ++n) {
-                    B[m][n] += g[n] * pl;
-                    BS[m][n] += gs[n] * pl;
-                }
+                for (int n = 0; n < NCH; ++n) BB[m][n] = fma2(gg[n], pl, BB[m][n]);
             }
         }
         __syncwarp();
@@ -426,11 +436,12 @@ __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<
         const R kap = kappa_of_lm<R>(lm);
 #pragma unroll
         for (int n = 0; n < NCH; ++n) {
+            const R Bv = BB[m][n].x, BSv = BB[m][n].y;
             if (valid) {
-                a.bsum[(int64_t)(n * NLM + lm) * N + i] = B[m][n];
-                a.bsum[(int64_t)(NCH * NLM + n * NLM + lm) * N + i] = BS[m][n];
+                a.bsum[(int64_t)(n * NLM + lm) * N + i] = Bv;
+                a.bsum[(int64_t)(NCH * NLM + n * NLM + lm) * N + i] = BSv;
             }
-            const R ka = kap * B[m][n] * B[m][n], ks = kap * BS[m][n] * BS[m][n];
+            const R ka = kap * Bv * Bv, ks = kap * BSv * BSv;
             // l is 1..4 depending on the lane: add into the matching slot
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
@@ -466,7 +477,7 @@ __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<
 
 // ------------------------------------------------------------------ k_bwd (fused)
 // Quad per atom, lanes over pairs.  Shared memory per atom: the angular adjoints
-// dE/dB_nlm, dE/dBS_nlm as 24 records of 12 (5 + 5 + pad), then the precontracted
+// dE/dB_nlm, dE/dBS_nlm as 24 records of 12 ((dE/dB, dE/dBS) interleaved per n, pad), then the precontracted
 // radial coefficients C^G_k = sum_n Fp^G_n c^G_{n k t_i t_j} for both neighbour
 // species (2 x 48).  Stride 388: 388 mod 32 = 4, so the eight atoms of a warp read
 // disjoint bank groups.
@@ -511,16 +522,15 @@ __device__ __forceinline__ void bwd_harm(const R *__restrict__ bb, R ux, R uy, R
     harm_one<R, LM>(ux, uy, uz, p, gx, gy, gz);
     const v4<R> *rec = reinterpret_cast<const v4<R> *>(bb + 12 * LM);
     const v4<R> r0 = rec[0], r1 = rec[1], r2 = rec[2];
-    const R B0[NCH] = {r0.x, r0.y, r0.z, r0.w, r1.x};
-    const R B1[NCH] = {r1.y, r1.z, r1.w, r2.x, r2.y};
-    R aA = R(0), aS = R(0), bA = R(0), bS = R(0);
+    const v2<R> Bp[NCH] = {pair2<R>(r0.x, r0.y), pair2<R>(r0.z, r0.w), pair2<R>(r1.x, r1.y), pair2<R>(r1.z, r1.w),
+                           pair2<R>(r2.x, r2.y)};   // (dE/dB_n, dE/dBS_n)
+    v2<R> aa = pair2<R>(R(0), R(0)), bq = pair2<R>(R(0), R(0));
 #pragma unroll
     for (int n = 0; n < NCH; ++n) {
-        aA += B0[n] * g[n];
-        aS += B1[n] * g[n];
-        bA += B0[n] * dg[n];
-        bS += B1[n] * dg[n];
+        aa = fma2(Bp[n], pair2<R>(g[n], g[n]), aa);
+        bq = fma2(Bp[n], pair2<R>(dg[n], dg[n]), bq);
     }
+    const R aA = aa.x, aS = aa.y, bA = bq.x, bS = bq.y;
     const R av = aA + s * aS, bv = bA + s * bS;
     accu += p * (bv - R(harm_l(LM)) * ir * av);
     avx += av * gx;
@@ -549,15 +559,19 @@ __device__ __forceinline__ void bwd_pair(const NepDev<R> &P, const Eval2Args<R> 
         const v4<R> c4 = cv[q];
         C[4 * q] = c4.x; C[4 * q + 1] = c4.y; C[4 * q + 2] = c4.z; C[4 * q + 3] = c4.w;
     }
-    R h1 = 0, h2 = 0, h3 = 0, h4 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0, e4 = 0;
+    R e0 = 0;
+    v2<R> he[4];   // (h_G, e_G) of the four magnetic groups
+#pragma unroll
+    for (int q = 0; q < 4; ++q) he[q] = pair2<R>(R(0), R(0));
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
         e0 += C[k] * df[k];
-        h1 += C[9 + k] * f[k]; e1 += C[9 + k] * df[k];
-        h2 += C[18 + k] * f[k]; e2 += C[18 + k] * df[k];
-        h3 += C[27 + k] * f[k]; e3 += C[27 + k] * df[k];
-        h4 += C[36 + k] * f[k]; e4 += C[36 + k] * df[k];
+        const v2<R> fd = pair2<R>(f[k], df[k]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) he[q] = fma2(pair2<R>(C[9 * (q + 1) + k], C[9 * (q + 1) + k]), fd, he[q]);
     }
+    const R h1 = he[0].x, e1 = he[0].y, h2 = he[1].x, e2 = he[1].y, h3 = he[2].x, e3 = he[2].y, h4 = he[3].x,
+            e4 = he[3].y;
     const R sij = si.x * sj.x + si.y * sj.y + si.z * sj.z;
     const R siu = si.x * ux + si.y * uy + si.z * uz;
     const R sju = sj.x * ux + sj.y * uy + sj.z * uz;
@@ -683,9 +697,9 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 2 : 1) k_bwd(const __gri
             }
             v4<R> *d = reinterpret_cast<v4<R> *>(sm + 12 * lm);
             v4<R> w0, w1, w2;
-            w0.x = bb[0]; w0.y = bb[1]; w0.z = bb[2]; w0.w = bb[3];
-            w1.x = bb[4]; w1.y = bb[5]; w1.z = bb[6]; w1.w = bb[7];
-            w2.x = bb[8]; w2.y = bb[9]; w2.z = R(0); w2.w = R(0);
+            w0.x = bb[0]; w0.y = bb[NCH]; w0.z = bb[1]; w0.w = bb[NCH + 1];
+            w1.x = bb[2]; w1.y = bb[NCH + 2]; w1.z = bb[3]; w1.w = bb[NCH + 3];
+            w2.x = bb[4]; w2.y = bb[NCH + 4]; w2.z = R(0); w2.w = R(0);
             d[0] = w0; d[1] = w1; d[2] = w2;
         }
         R FR[NCH], FX[4][NCH];

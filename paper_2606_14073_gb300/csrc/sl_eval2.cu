@@ -42,6 +42,22 @@ __device__ __forceinline__ v2<R> pair2(R x, R y) {
     v.y = y;
     return v;
 }
+// g_n = sum_k c_nk f_k and dg_n = sum_k c_nk df_k together, two multiply-adds per instruction
+template <typename R, int TI, int TJ, int G>
+__device__ __forceinline__ void contract_k2(const NepDev<R> &P, const R f[NK], const R df[NK], R g[NCH], R dg[NCH]) {
+#pragma unroll
+    for (int n = 0; n < NCH; ++n) {
+        v2<R> s = pair2<R>(R(0), R(0));
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const R c = P.c[TI][TJ][G][n][k];
+            s = fma2(pair2<R>(c, c), pair2<R>(f[k], df[k]), s);
+        }
+        g[n] = s.x;
+        dg[n] = s.y;
+    }
+}
+
 template <typename R, int TI, int TJ, int G>
 __device__ __forceinline__ void contract_k(const NepDev<R> &P, const R f[NK], R g[NCH]) {
 #pragma unroll
@@ -110,7 +126,8 @@ constexpr int CBB = 4;   // candidates per batch in B
 
 template <typename R>
 struct RadSums {
-    R b0[NK], b1[NK], b2[NK], b3[NK], b4[NK];
+    R b0[NK];
+    v2<R> b12[NK], b34[NK];   // (EX, DMI) and (ANI, SIA) sums, two per packed multiply-add
 };
 
 template <typename R>
@@ -128,10 +145,8 @@ __device__ __forceinline__ void rad_accumulate(const NepDev<R> &P, const v4<R> &
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
         b.b0[k] += f[k];
-        b.b1[k] += f[k] * sij;
-        b.b2[k] += f[k] * dmi;
-        b.b3[k] += f[k] * ani;
-        b.b4[k] += f[k] * sia;
+        b.b12[k] = fma2(pair2<R>(f[k], f[k]), pair2<R>(sij, dmi), b.b12[k]);
+        b.b34[k] = fma2(pair2<R>(f[k], f[k]), pair2<R>(ani, sia), b.b34[k]);
     }
 }
 
@@ -160,7 +175,10 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
                                              uint32_t (*smask)[128]) {
     RadSums<R> b;
 #pragma unroll
-    for (int k = 0; k < NK; ++k) { b.b0[k] = b.b1[k] = b.b2[k] = b.b3[k] = b.b4[k] = R(0); }
+    for (int k = 0; k < NK; ++k) {
+        b.b0[k] = R(0);
+        b.b12[k] = b.b34[k] = pair2<R>(R(0), R(0));
+    }
     const int64_t N = a.n;
     const int32_t *__restrict__ nbr = a.nbr;
     const int32_t *__restrict__ rev = a.rev;
@@ -275,12 +293,15 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
     constexpr int GG[5] = {G_R, G_EX, G_DMI, G_ANI, G_SIA};
 #pragma unroll
     for (int g = 0; g < 5; ++g) {
-        const R *bg = g == 0 ? b.b0 : g == 1 ? b.b1 : g == 2 ? b.b2 : g == 3 ? b.b3 : b.b4;
 #pragma unroll
         for (int n = 0; n < NCH; ++n) {
             R v = TJ == 0 ? R(0) : a.q[(GQ[g] + n) * N + i];
 #pragma unroll
-            for (int k = 0; k < NK; ++k) v += P.c[TI][TJ][GG[g]][n][k] * bg[k];
+            for (int k = 0; k < NK; ++k) {
+                const R bgk = g == 0 ? b.b0[k] : g == 1 ? b.b12[k].x : g == 2 ? b.b12[k].y : g == 3 ? b.b34[k].x
+                                                                                                 : b.b34[k].y;
+                v += P.c[TI][TJ][GG[g]][n][k] * bgk;
+            }
             a.q[(GQ[g] + n) * N + i] = v;
         }
     }
@@ -511,8 +532,7 @@ template <typename R, int TI, int TJ>
 __device__ __forceinline__ void ang_gdg(const NepDev<R> &P, R r, R inv_rc, R g[NCH], R dg[NCH]) {
     R f[NK], df[NK];
     carrier_fd(r, inv_rc, f, df);
-    contract_k<R, TI, TJ, G_A>(P, f, g);
-    contract_k<R, TI, TJ, G_A>(P, df, dg);
+    contract_k2<R, TI, TJ, G_A>(P, f, df, g, dg);
 }
 
 template <typename R, int LM>

@@ -43,6 +43,33 @@ __device__ __forceinline__ v2<R> pair2(R x, R y) {
     return v;
 }
 // g_n = sum_k c_nk f_k and dg_n = sum_k c_nk df_k together, two multiply-adds per instruction
+// The carrier of sl_common.cuh with the T_k and U_k recurrences advanced together.
+template <typename R>
+__device__ __forceinline__ void carrier_fd2(R r, R inv_rc, R f[NK], R df[NK]) {
+    const R t = r * inv_rc;
+    R sn, cs;
+    sincospi_(t, &sn, &cs);
+    const R fch = R(0.25) * (R(1) + cs);
+    const R dfch = R(-0.785398163397448309616) * inv_rc * sn;
+    const R y = t - R(1);
+    const R x = R(2) * y * y - R(1);
+    const R dxr = R(4) * y * inv_rc;
+    const R x2 = R(2) * x;
+    v2<R> tum = pair2<R>(R(1), R(1)), tuc = pair2<R>(x, x2);   // (T_0, U_0), (T_1, U_1)
+    f[0] = R(2) * fch;
+    df[0] = R(2) * dfch;
+    f[1] = (x + R(1)) * fch;
+    df[1] = dxr * fch + (x + R(1)) * dfch;
+#pragma unroll
+    for (int k = 2; k < NK; ++k) {
+        const v2<R> tun = fma2(pair2<R>(x2, x2), tuc, pair2<R>(-tum.x, -tum.y));
+        f[k] = (tun.x + R(1)) * fch;
+        df[k] = R(k) * tuc.y * dxr * fch + (tun.x + R(1)) * dfch;
+        tum = tuc;
+        tuc = tun;
+    }
+}
+
 template <typename R, int TI, int TJ, int G>
 __device__ __forceinline__ void contract_k2(const NepDev<R> &P, const R f[NK], const R df[NK], R g[NCH], R dg[NCH]) {
 #pragma unroll
@@ -531,7 +558,7 @@ __device__ __forceinline__ void bwd_coeffs(const NepDev<R> &P, const R FR[NCH], 
 template <typename R, int TI, int TJ>
 __device__ __forceinline__ void ang_gdg(const NepDev<R> &P, R r, R inv_rc, R g[NCH], R dg[NCH]) {
     R f[NK], df[NK];
-    carrier_fd(r, inv_rc, f, df);
+    carrier_fd2(r, inv_rc, f, df);
     contract_k2<R, TI, TJ, G_A>(P, f, df, g, dg);
 }
 
@@ -571,7 +598,7 @@ __device__ __forceinline__ void bwd_pair(const NepDev<R> &P, const Eval2Args<R> 
     const R ux = dx * ir, uy = dy * ir, uz = dz * ir;
     // radial and pairwise-magnetic part with the precontracted coefficients
     R f[NK], df[NK];
-    carrier_fd(r, P.inv_rc_r, f, df);
+    carrier_fd2(r, P.inv_rc_r, f, df);
     const v4<R> *cv = reinterpret_cast<const v4<R> *>(sm + BW_C + tj * 48);
     R C[48];
 #pragma unroll

@@ -680,8 +680,8 @@ __device__ __forceinline__ void bwd_rows(const NepDev<R> &P, const Eval2Args<R> 
                                          int split, const v4<R> &pi, const v4<R> &si, const R *sm,
                                          BwdAcc2<R> &acc) {
     const int64_t N = a.n;
-    int j1 = 0, t1 = 0, j2 = 0, t2 = 0;
-    v4<R> p1, s1;
+    int j1 = 0, t1 = 0, j2 = 0, t2 = 0, j3 = 0, t3 = 0;
+    v4<R> p1, s1, p2, s2;
     if (lo < hi) {
         j1 = a.clj[(int64_t)lo * N + i];
         t1 = a.cls[(int64_t)lo * N + i] >> 8;
@@ -690,22 +690,30 @@ __device__ __forceinline__ void bwd_rows(const NepDev<R> &P, const Eval2Args<R> 
         j2 = a.clj[(int64_t)(lo + 4) * N + i];
         t2 = a.cls[(int64_t)(lo + 4) * N + i] >> 8;
     }
+    if (lo + 8 < hi) {
+        j3 = a.clj[(int64_t)(lo + 8) * N + i];
+        t3 = a.cls[(int64_t)(lo + 8) * N + i] >> 8;
+    }
     if (lo < hi) {
         p1 = a.pos[j1];
         s1 = a.spin[j1];
     }
+    if (lo + 4 < hi) {
+        p2 = a.pos[j2];
+        s2 = a.spin[j2];
+    }
     for (int row = lo; row < hi; row += 4) {
         const int j = j1, t = t1;
         const v4<R> pj = p1, sj = s1;
-        if (row + 4 < hi) {
-            j1 = j2;
-            t1 = t2;
-            p1 = a.pos[j1];
-            s1 = a.spin[j1];
-        }
+        j1 = j2; t1 = t2; p1 = p2; s1 = s2;
+        j2 = j3; t2 = t3;
         if (row + 8 < hi) {
-            j2 = a.clj[(int64_t)(row + 8) * N + i];
-            t2 = a.cls[(int64_t)(row + 8) * N + i] >> 8;
+            p2 = a.pos[j2];
+            s2 = a.spin[j2];
+        }
+        if (row + 12 < hi) {
+            j3 = a.clj[(int64_t)(row + 12) * N + i];
+            t3 = a.cls[(int64_t)(row + 12) * N + i] >> 8;
         }
         bwd_pair<R, ANG>(P, a, ti, row < split ? 0 : 1, pi, si, pj, sj, j, t, sm, acc);
     }

@@ -423,23 +423,30 @@ __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<
 #pragma unroll
         for (int n = 0; n < NCH; ++n) BB[m][n] = pair2<R>(R(0), R(0));
     const int nmax = __reduce_max_sync(0xffffffffu, na);
-    // the lane's list entry two rounds ahead and its coordinates one round ahead are in flight
-    v4<R> pjn, sjn;
-    int jn2 = 0;
-    if (ql + 4 < na) jn2 = a.clj[(int64_t)(ql + 4) * N + i];
+    // the lane's list entry three rounds ahead and its coordinates two rounds ahead are in flight
+    v4<R> pjn, sjn, pjn2, sjn2;
+    int jn3 = 0;
     if (ql < na) {
         const int j = a.clj[(int64_t)ql * N + i];
         pjn = a.pos[j];
         sjn = a.spin[j];
     }
+    if (ql + 4 < na) {
+        const int j = a.clj[(int64_t)(ql + 4) * N + i];
+        pjn2 = a.pos[j];
+        sjn2 = a.spin[j];
+    }
+    if (ql + 8 < na) jn3 = a.clj[(int64_t)(ql + 8) * N + i];
     for (int base = 0; base < nmax; base += 4) {
         const int p = base + ql;
         const v4<R> pj = pjn, sj = sjn;
-        if (p + 4 < na) {
-            pjn = a.pos[jn2];
-            sjn = a.spin[jn2];
+        pjn = pjn2;
+        sjn = sjn2;
+        if (p + 8 < na) {
+            pjn2 = a.pos[jn3];
+            sjn2 = a.spin[jn3];
         }
-        if (p + 8 < na) jn2 = a.clj[(int64_t)(p + 8) * N + i];
+        if (p + 12 < na) jn3 = a.clj[(int64_t)(p + 12) * N + i];
         if (p < na) {
             R *st = stage + ql * FSTAGE;
             if (ti == 0) {

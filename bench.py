@@ -243,8 +243,9 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm
-def run_e2e(args, sysm, wl, world, barrier, dist, torch):
-    st = sysm.get_state()
+def run_e2e(args, sysm, wl, world, barrier, dist, torch, st):
+    """The timed steps again through the public API from host buffers: st is the state the
+    timed region started from, so the call replays the same trajectory (same work)."""
     host = {k: torch.from_numpy(np.ascontiguousarray(st[k])).pin_memory().numpy()
             for k in ("positions", "velocities", "spins", "forces", "fields", "ref_positions")}
     barrier()
@@ -259,7 +260,8 @@ def run_e2e(args, sysm, wl, world, barrier, dist, torch):
     d2h = sum(out[k].nbytes for k in ("positions", "velocities", "spins", "forces", "fields", "ref_positions"))
     e2e = {"value": whole_job_rate(wl.n, args.steps, world, e2e_s * 1e3), "unit": UNIT,
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-           "path": "sl_set_state(host) + sl_step(K) + sl_get_state(host), wall clock"}
+           "path": "sl_set_state(host) + sl_step(K) + sl_get_state(host), wall clock, replaying the timed steps "
+                   "from their start state", "_out": out}
 
     return e2e
 
@@ -653,6 +655,7 @@ def run_ours(args):
 
     # warm-up (graph capture happens here)
     sysm.step(args.warmup, DT, TEMP, FIELD)
+    start_state = None if args.skip_e2e else sysm.get_state()   # replayed by the end-to-end leg
     info0 = sysm.info()
     launches0 = info0["n_launches"]
     mid0 = sysm.midpoint_evaluations()
@@ -675,6 +678,7 @@ def run_ours(args):
     mid_evals = sysm.midpoint_evaluations() - mid0
     ms_max = max_over_ranks(ms, dist, "cuda")
     value = whole_job_rate(wl.n, args.steps, world, ms_max)
+    end_state = None if args.skip_e2e else sysm.get_state()
 
     # per-kernel device times (CUDA events between the kernel groups, same stream, no graphs)
     b0 = sysm.info()["n_builds"]
@@ -709,7 +713,9 @@ def run_ours(args):
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.skip_e2e:
-        e2e = run_e2e(args, sysm, wl, world, barrier, dist, torch)
+        e2e = run_e2e(args, sysm, wl, world, barrier, dist, torch, start_state)
+        e2e["replay_bit_identical"] = bool(all(np.array_equal(e2e.pop("_out")[k], end_state[k])
+                                               for k in ("positions", "velocities", "spins")))
 
     # continuous-batching serving run: Poisson sweep requests, p50/p99 time to completion
     serving = None

@@ -714,7 +714,8 @@ def run_ours(args):
     e2e = None
     if not args.skip_e2e:
         e2e = run_e2e(args, sysm, wl, world, barrier, dist, torch, start_state)
-        e2e["replay_bit_identical"] = bool(all(np.array_equal(e2e.pop("_out")[k], end_state[k])
+        out = e2e.pop("_out")
+        e2e["replay_bit_identical"] = bool(all(np.array_equal(out[k], end_state[k])
                                                for k in ("positions", "velocities", "spins")))
 
     # continuous-batching serving run: Poisson sweep requests, p50/p99 time to completion

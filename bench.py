@@ -733,10 +733,13 @@ def run_ours(args):
         O.set_num_threads(1)
         rate1, atoms1, secs1 = oracle_rate(2, 0, 10)
         O.set_num_threads(cores)
+        rate_c1, atoms_c1, secs_c1 = oracle_rate(100, 0, 4)   # the 512-atom system in full
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"2 oracle MD steps of a {cells}^3-cell ({atoms}-atom) block of the same recipe, {secs:.1f} s",
                "single_core": {"value": rate1, "unit": UNIT,
-                               "sample": f"2 oracle MD steps of a 10^3-cell ({atoms1}-atom) block, {secs1:.1f} s"}}
+                               "sample": f"2 oracle MD steps of a 10^3-cell ({atoms1}-atom) block, {secs1:.1f} s"},
+               "small_system": {"value": rate_c1, "unit": UNIT, "cores": cores,
+                                "sample": f"100 oracle MD steps of the {atoms_c1}-atom 4^3-cell system, {secs_c1:.1f} s"}}
 
     sysm.destroy()
     if rank == 0:

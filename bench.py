@@ -227,7 +227,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from oracle import oracle as O
-    cells, _ = pick_oracle_cells(args.steps + args.warmup, budget_s=150.0)
+    cells, _ = pick_oracle_cells(args.steps + args.warmup, budget_s=args.ref_budget_s)
     rate, atoms, secs = oracle_rate(args.steps, args.warmup, cells)
     cores = O.num_threads()
     sample = (f"{cells}^3 B20 cells = {atoms} atoms of the {WORKLOAD} recipe (same density, spins, 300 K), "
@@ -802,6 +802,8 @@ def main():
     ap.add_argument("--midpoint-tol", type=float, default=1e-6)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--anderson-depth", type=int, default=0)
+    ap.add_argument("--ref-budget-s", type=float, default=150.0,
+                    help="reference arm: seconds of oracle work the sample is sized for")
     ap.add_argument("--longitudinal", type=float, default=0.0,
                     help="cube: damping alpha of the longitudinal moment mode (0: unit spins)")
     ap.add_argument("--cells", type=int, default=48, help="B20 cells per side (48: the benchmark workload; "

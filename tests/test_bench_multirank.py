@@ -53,3 +53,30 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(3.25) == 3.25
     assert bench.whole_job_rate(884736, 200, 1, 1000.0) == pytest.approx(884736 * 200.0)
+
+
+def test_reference_arm_line_on_cpu():
+    """bench.py --impl reference times the FP64 oracle on the host cores and prints the
+    contract's line (a short budget here)."""
+    import json
+    import subprocess
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "3",
+           "--ref-budget-s", "3"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 3
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["higher_is_better"] is True and line["unit"] == "atom-steps/s"
+
+
+def test_reference_arm_other_ranks_exit_quietly(monkeypatch):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+
+    class A:
+        steps, warmup, ref_budget_s = 1, 3, 1.0
+    assert bench.run_reference(A()) == 0

@@ -92,6 +92,13 @@ __device__ __forceinline__ float cospi_<float>(float x) { return cospif(x); }
 template <>
 __device__ __forceinline__ double cospi_<double>(double x) { return cospi(x); }
 
+template <typename R>
+__device__ __forceinline__ R fma_(R a, R b, R c);
+template <>
+__device__ __forceinline__ float fma_<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <>
+__device__ __forceinline__ double fma_<double>(double a, double b, double c) { return fma(a, b, c); }
+
 // Radial carrier (Sections 5.2.3-5.2.4): f_c = (1 + cos(pi r/rc))/2,
 // x = 2 (r/rc - 1)^2 - 1, T_{k+1} = 2 x T_k - T_{k-1}, f_k = (T_k + 1) f_c / 2.
 template <typename R>
@@ -102,11 +109,11 @@ __device__ __forceinline__ void carrier_f(R r, R inv_rc, R f[NK]) {
     const R x = R(2) * y * y - R(1);
     R tm = R(1), tc = x;
     f[0] = R(2) * fch;
-    f[1] = (x + R(1)) * fch;
+    f[1] = fma_(x, fch, fch);                          // (T_1 + 1) f_c/2 with one rounding
 #pragma unroll
     for (int k = 2; k < NK; ++k) {
         const R tn = R(2) * x * tc - tm;
-        f[k] = (tn + R(1)) * fch;
+        f[k] = fma_(tn, fch, fch);
         tm = tc;
         tc = tn;
     }
@@ -123,16 +130,17 @@ __device__ __forceinline__ void carrier_fd(R r, R inv_rc, R f[NK], R df[NK]) {
     const R y = t - R(1);
     const R x = R(2) * y * y - R(1);
     const R dxr = R(4) * y * inv_rc;
+    const R dxf = dxr * fch;
     R tm = R(1), tc = x, um = R(1), uc = R(2) * x;   // T_0, T_1, U_0, U_1
     f[0] = R(2) * fch;
     df[0] = R(2) * dfch;
-    f[1] = (x + R(1)) * fch;
-    df[1] = dxr * fch + (x + R(1)) * dfch;            // dT_1/dx = U_0 = 1
+    f[1] = fma_(x, fch, fch);
+    df[1] = dxf + fma_(x, dfch, dfch);                // dT_1/dx = U_0 = 1
 #pragma unroll
     for (int k = 2; k < NK; ++k) {
         const R tn = R(2) * x * tc - tm;
-        f[k] = (tn + R(1)) * fch;
-        df[k] = R(k) * uc * dxr * fch + (tn + R(1)) * dfch;   // k U_{k-1}
+        f[k] = fma_(tn, fch, fch);
+        df[k] = fma_(R(k) * uc, dxf, fma_(tn, dfch, dfch));   // k U_{k-1}
         const R un = R(2) * x * uc - um;
         tm = tc; tc = tn; um = uc; uc = un;
     }

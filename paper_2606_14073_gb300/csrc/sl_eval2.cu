@@ -55,16 +55,17 @@ __device__ __forceinline__ void carrier_fd2(R r, R inv_rc, R f[NK], R df[NK]) {
     const R x = R(2) * y * y - R(1);
     const R dxr = R(4) * y * inv_rc;
     const R x2 = R(2) * x;
+    const R dxf = dxr * fch;
     v2<R> tum = pair2<R>(R(1), R(1)), tuc = pair2<R>(x, x2);   // (T_0, U_0), (T_1, U_1)
     f[0] = R(2) * fch;
     df[0] = R(2) * dfch;
-    f[1] = (x + R(1)) * fch;
-    df[1] = dxr * fch + (x + R(1)) * dfch;
+    f[1] = fma_(x, fch, fch);
+    df[1] = dxf + fma_(x, dfch, dfch);
 #pragma unroll
     for (int k = 2; k < NK; ++k) {
         const v2<R> tun = fma2(pair2<R>(x2, x2), tuc, pair2<R>(-tum.x, -tum.y));
-        f[k] = (tun.x + R(1)) * fch;
-        df[k] = R(k) * tuc.y * dxr * fch + (tun.x + R(1)) * dfch;
+        f[k] = fma_(tun.x, fch, fch);
+        df[k] = fma_(R(k) * tuc.y, dxf, fma_(tun.x, dfch, dfch));
         tum = tuc;
         tuc = tun;
     }

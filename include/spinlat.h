@@ -309,6 +309,13 @@ int sl_descriptors_energies_noalloc(const double *positions4, const double *spin
  * error of the harmonic gradients over n_samples random unit vectors. */
 int sl_selftest_harmonics(int32_t n_samples, double *max_addition_err, double *max_gradient_err);
 
+/* Device self-test of the mixed-precision radial carrier (Sections 5.2.3-5.2.4): the FP32
+ * basis f_k(r) and df_k/dr, whose cutoff factor is evaluated from Taylor polynomials of sin
+ * and cos, against the FP64 basis (the CUDA library's sincospi) at n_samples radii evenly
+ * spread over [0, rc).  Outputs the largest absolute differences divided by the largest
+ * FP64 magnitudes.  SL_EINVAL for n_samples < 1 or rc <= 0; SL_ECUDA without a device. */
+int sl_selftest_carrier(int32_t n_samples, double rc, double *max_rel_err_f, double *max_rel_err_df);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1228,6 +1228,17 @@ int sl_descriptors_energies_noalloc(const double *positions4, const double *spin
 }
 
 // ---------------------------------------------------------------- self checks
+int sl_selftest_carrier(int32_t n_samples, double rc, double *max_rel_err_f, double *max_rel_err_df) {
+    if (n_samples < 1 || !(rc > 0) || !std::isfinite(rc)) return fail(SL_EINVAL, "bad self-test arguments");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return fail(SL_ECUDA, "no usable CUDA device");
+    double out[4];
+    if (sl::selftest_carrier(n_samples, rc, out)) return fail(SL_ECUDA, "carrier self-test failed to run");
+    if (max_rel_err_f) *max_rel_err_f = out[0] / out[2];
+    if (max_rel_err_df) *max_rel_err_df = out[1] / out[3];
+    return SL_OK;
+}
+
 int sl_selftest_harmonics(int32_t n_samples, double *max_add, double *max_grad) {
     using namespace sl;
     if (n_samples < 1) return fail(SL_EINVAL, "n_samples < 1");

@@ -78,19 +78,6 @@ __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
 template <>
 __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
 
-template <typename R>
-__device__ __forceinline__ void sincospi_(R x, R *s, R *c);
-template <>
-__device__ __forceinline__ void sincospi_<float>(float x, float *s, float *c) { sincospif(x, s, c); }
-template <>
-__device__ __forceinline__ void sincospi_<double>(double x, double *s, double *c) { sincospi(x, s, c); }
-
-template <typename R>
-__device__ __forceinline__ R cospi_(R x);
-template <>
-__device__ __forceinline__ float cospi_<float>(float x) { return cospif(x); }
-template <>
-__device__ __forceinline__ double cospi_<double>(double x) { return cospi(x); }
 
 template <typename R>
 __device__ __forceinline__ R fma_(R a, R b, R c);
@@ -99,12 +86,56 @@ __device__ __forceinline__ float fma_<float>(float a, float b, float c) { return
 template <>
 __device__ __forceinline__ double fma_<double>(double a, double b, double c) { return fma(a, b, c); }
 
+// Cutoff half f_c/2 = (1 + cos(pi t))/4 (t = r/rc in [0, 1)) and d(f_c/2)/dr.
+// FP64: the CUDA library's cospi / sincospi.  FP32: written as cos^2(w)/2 with w = pi t/2 in
+// [0, pi/2] (no cancellation near t = 1) and d/dr = -(pi/2)/rc sin(w) cos(w), with sin w and
+// cos w from their Taylor series at 0 through w^11 and w^12 (Horner in w^2): the first
+// omitted terms are below (pi/2)^13/13! = 5.7e-8 and (pi/2)^14/14! = 6.4e-9 on the range.
+__device__ __forceinline__ void sincos_halfpi_taylor(float t, float &s, float &c) {
+    const float w = 1.57079632679489662f * t;
+    const float w2 = w * w;
+    constexpr float i2 = 1.f / 2.f, i4 = 1.f / 24.f, i6 = 1.f / 720.f, i8 = 1.f / 40320.f,
+                    i10 = 1.f / 3628800.f, i12 = 1.f / 479001600.f;
+    constexpr float i3 = 1.f / 6.f, i5 = 1.f / 120.f, i7 = 1.f / 5040.f, i9 = 1.f / 362880.f,
+                    i11 = 1.f / 39916800.f;
+    c = fmaf(w2, fmaf(w2, fmaf(w2, fmaf(w2, fmaf(w2, fmaf(w2, i12, -i10), i8), -i6), i4), -i2), 1.f);
+    s = w * fmaf(w2, fmaf(w2, fmaf(w2, fmaf(w2, fmaf(w2, -i11, i9), -i7), i5), -i3), 1.f);
+}
+
+template <typename R>
+__device__ __forceinline__ R cut_half(R t);
+template <>
+__device__ __forceinline__ float cut_half<float>(float t) {
+    float s, c;
+    sincos_halfpi_taylor(t, s, c);
+    return 0.5f * c * c;
+}
+template <>
+__device__ __forceinline__ double cut_half<double>(double t) { return 0.25 * (1.0 + cospi(t)); }
+
+template <typename R>
+__device__ __forceinline__ void cut_half_d(R t, R inv_rc, R &fch, R &dfch);
+template <>
+__device__ __forceinline__ void cut_half_d<float>(float t, float inv_rc, float &fch, float &dfch) {
+    float s, c;
+    sincos_halfpi_taylor(t, s, c);
+    fch = 0.5f * c * c;
+    dfch = -1.57079632679489662f * inv_rc * (s * c);
+}
+template <>
+__device__ __forceinline__ void cut_half_d<double>(double t, double inv_rc, double &fch, double &dfch) {
+    double sn, cs;
+    sincospi(t, &sn, &cs);
+    fch = 0.25 * (1.0 + cs);
+    dfch = -0.785398163397448309616 * inv_rc * sn;   // d(f_c/2)/dr = -(pi/4)/rc sin
+}
+
 // Radial carrier (Sections 5.2.3-5.2.4): f_c = (1 + cos(pi r/rc))/2,
 // x = 2 (r/rc - 1)^2 - 1, T_{k+1} = 2 x T_k - T_{k-1}, f_k = (T_k + 1) f_c / 2.
 template <typename R>
 __device__ __forceinline__ void carrier_f(R r, R inv_rc, R f[NK]) {
     const R t = r * inv_rc;
-    const R fch = R(0.25) * (R(1) + cospi_(t));   // f_c / 2
+    const R fch = cut_half(t);   // f_c / 2
     const R y = t - R(1);
     const R x = R(2) * y * y - R(1);
     R tm = R(1), tc = x;
@@ -123,10 +154,8 @@ __device__ __forceinline__ void carrier_f(R r, R inv_rc, R f[NK]) {
 template <typename R>
 __device__ __forceinline__ void carrier_fd(R r, R inv_rc, R f[NK], R df[NK]) {
     const R t = r * inv_rc;
-    R sn, cs;
-    sincospi_(t, &sn, &cs);
-    const R fch = R(0.25) * (R(1) + cs);
-    const R dfch = R(-0.785398163397448309616) * inv_rc * sn;   // d(f_c/2)/dr = -(pi/4)/rc sin
+    R fch, dfch;
+    cut_half_d(t, inv_rc, fch, dfch);
     const R y = t - R(1);
     const R x = R(2) * y * y - R(1);
     const R dxr = R(4) * y * inv_rc;

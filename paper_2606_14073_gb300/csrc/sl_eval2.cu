@@ -47,10 +47,8 @@ __device__ __forceinline__ v2<R> pair2(R x, R y) {
 template <typename R>
 __device__ __forceinline__ void carrier_fd2(R r, R inv_rc, R f[NK], R df[NK]) {
     const R t = r * inv_rc;
-    R sn, cs;
-    sincospi_(t, &sn, &cs);
-    const R fch = R(0.25) * (R(1) + cs);
-    const R dfch = R(-0.785398163397448309616) * inv_rc * sn;
+    R fch, dfch;
+    cut_half_d(t, inv_rc, fch, dfch);
     const R y = t - R(1);
     const R x = R(2) * y * y - R(1);
     const R dxr = R(4) * y * inv_rc;

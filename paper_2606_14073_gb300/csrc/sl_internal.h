@@ -208,5 +208,7 @@ int launch_noalloc(const NepDev<double> &P, const double4 *pos, const double4 *s
 int noalloc_max_atoms();
 // sl_peak.cu
 int measure_fma_peak(int precision, double *flops_per_s, double *elapsed_ms);
+// FP32 carrier against FP64 at n radii in [0, rc): out = {max |df|, max |d(df/dr)|, max |f|, max |df/dr|}
+int selftest_carrier(int n, double rc, double out[4]);
 
 }  // namespace sl

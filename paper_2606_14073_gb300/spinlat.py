@@ -24,7 +24,7 @@ EXPORTS = ["sl_default_options", "sl_create_system", "sl_step", "sl_energy_force
            "sl_destroy_system", "sl_last_error", "sl_batch_create", "sl_batch_step", "sl_batch_destroy",
            "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak", "sl_descriptors_energies_noalloc",
            "sl_estimate_device_bytes", "sl_get_midpoint_evaluations", "sl_set_atom_fields", "sl_texture_map",
-           "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal"]
+           "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal", "sl_selftest_carrier"]
 KERNEL_GROUPS = ["first_half", "rebuild", "compact", "rad_fwd", "ang_fwd", "network", "backward", "second_half"]
 
 
@@ -74,6 +74,7 @@ def lib(path: str | None = None):
             L.sl_get_midpoint_evaluations.argtypes = [P, P]
             L.sl_set_atom_fields.argtypes = [P, P]
             L.sl_set_longitudinal.argtypes = [P, I32, D, P]
+            L.sl_selftest_carrier.argtypes = [I32, D, P, P]
             L.sl_batch_graph_launches.argtypes = [P, P]
             L.sl_autotune.argtypes = [P, I32, P, P, P]
             L.sl_texture_map.argtypes = [P, I32, D, P, P, P, P]
@@ -96,7 +97,8 @@ def lib(path: str | None = None):
                       "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_batch_create",
                       "sl_batch_step", "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak",
                       "sl_descriptors_energies_noalloc", "sl_get_midpoint_evaluations", "sl_set_atom_fields",
-                      "sl_texture_map", "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal"):
+                      "sl_texture_map", "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal",
+                      "sl_selftest_carrier"):
                 getattr(L, f).restype = C.c_int
             _lib = L
         return _lib
@@ -319,6 +321,13 @@ def sl_selftest_harmonics(n_samples=1000):
     a, g = C.c_double(), C.c_double()
     _check(lib().sl_selftest_harmonics(int(n_samples), C.byref(a), C.byref(g)))
     return a.value, g.value
+
+
+def sl_selftest_carrier(n_samples=100000, rc=6.0):
+    """(relative error of f_k, of df_k/dr) of the FP32 radial carrier against FP64 on the device."""
+    a, b = C.c_double(), C.c_double()
+    _check(lib().sl_selftest_carrier(int(n_samples), float(rc), C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def sl_measure_fma_peak(precision=SL_PREC_MIXED):

@@ -339,3 +339,13 @@ def test_single_species_systems_match_oracle(params, model, only):
         s.step(12, 1.0, 300.0, B)
         assert np.isfinite(s.get_state()["positions"]).all()
         s.destroy()
+
+
+def test_fp32_carrier_matches_fp64_carrier():
+    """The FP32 carrier's cutoff factor comes from Taylor polynomials of sin and cos (truncation
+    below 6e-8 on its range); against the FP64 carrier (library sincospi) the basis and its
+    slope stay at the FP32 rounding level of the Chebyshev recurrence (about 4e-6 of the largest
+    value, the same with library cosines), at both cutoffs and in the tails near rc."""
+    for rc in (6.0, 4.0):
+        ef, edf = S.sl_selftest_carrier(200000, rc)
+        assert ef < 1e-5 and edf < 1e-5, (rc, ef, edf)

@@ -97,3 +97,10 @@ def test_texture_grid_validation_needs_no_device():
     assert S.lib().sl_texture_map(None, 2, 4.7, C.byref(na), C.byref(nb), None, None) == S.SL_EINVAL
     assert S.lib().sl_set_atom_fields(None, None) == S.SL_EINVAL
     assert S.lib().sl_set_longitudinal(None, 1, 0.1, None) == S.SL_EINVAL
+
+
+def test_carrier_selftest_argument_checks():
+    import ctypes as C
+    a, b = C.c_double(), C.c_double()
+    assert S.lib().sl_selftest_carrier(0, 6.0, C.byref(a), C.byref(b)) == S.SL_EINVAL
+    assert S.lib().sl_selftest_carrier(10, -1.0, C.byref(a), C.byref(b)) == S.SL_EINVAL

@@ -51,3 +51,28 @@ def test_full_size_neighbor_sample_bit_exact(setup):
     for i in sample:
         assert np.array_equal(rad[i], ref_r[i]) and np.array_equal(ang[i], ref_a[i])
     s.destroy()
+
+
+@pytest.mark.parametrize("prec", [S.SL_PREC_FP64, S.SL_PREC_MIXED])
+def test_largest_config_slab_sampled_parity(prec):
+    """The largest single-GPU configuration: the 3,276,800-atom helix slab (160 x 160 x 16
+    cells, free z, 0.2 T) after a few steps, sampled on 2,000 atoms (seeded, surface atoms
+    included by construction of the sample over all atoms)."""
+    p = nep_params.load()
+    model = O.Model(p)
+    wl = W.fege_slab_helix()
+    assert wl.n == 3276800 and list(wl.periodic) == [1, 1, 0]
+    sample = np.sort(np.random.default_rng(20260104).choice(wl.n, 2000, replace=False))
+    B = (0.0, 0.0, 0.2)
+    s = S.system_from_workload(wl, p, precision=prec)
+    s.step(3, 1.0, 50.0, B)
+    st = s.get_state()
+    r = s.energy_forces_fields(want_virial=False)
+    ref = O.evaluate_subset(model, st["positions"], st["spins"], wl.species, wl.box, wl.periodic, sample, B)
+    if prec == S.SL_PREC_FP64:
+        assert np.abs(r["F"][sample] - ref["F"]).max() <= 1e-10 * np.abs(ref["F"]).max()
+        assert np.abs(r["H"][sample] - ref["H"]).max() <= 1e-10 * np.abs(ref["H"]).max()
+    else:
+        assert np.sqrt(((r["F"][sample] - ref["F"]) ** 2).mean()) <= 1e-3
+        assert np.sqrt(((r["H"][sample] - ref["H"]) ** 2).mean()) <= 1e-3
+    s.destroy()

@@ -164,6 +164,9 @@ def committed_traffic(kernel: str):
         return None
 
 
+DTYPE_MIXED = ("f32 descriptor and backward, network on tensor cores as f16 hi/lo pairs with f32 accumulation, "
+               "f64 state and integration")
+
 # Landau onsite coefficients (a, b) per species for --longitudinal runs, eV: minimum at |S|^2 = 1.25
 LONG_LANDAU = [[-0.2, 0.08], [-0.2, 0.08]]
 
@@ -285,7 +288,7 @@ def run_serving(args, params, replica_offset=0):
 def _common_line(args, value, ms_total, steps, workload, config, clk, launches, extra):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup,
             "ms_per_step": ms_total / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 descriptor/backward, f32 network, f64 state/integration",
+            "dtype": DTYPE_MIXED,
             "data": "synthetic (seeded FeGe B20, random-init NEP of the paper's shape)",
             "config": dict(workload=workload, **config), "clocks": clk, "gpu_launches": launches}
     line.update(extra)
@@ -746,7 +749,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32 descriptor/backward, f32 network, f64 state/integration",
+                "dtype": DTYPE_MIXED,
                 "data": "synthetic (seeded FeGe B20, random-init NEP of the paper's shape)",
                 "config": {"workload": WORKLOAD if args.cells == 48 else wl.name, "atoms": wl.n, "precision": "mixed", "dt_fs": DT, "T_K": TEMP,
                            "B_T": list(FIELD), "steps_per_graph": args.graph_steps,

@@ -192,9 +192,9 @@ int sl_set_atom_fields(sl_system *sys, const double *B_atoms);
  *   S_next = Rot(S, (H + H*) dt/(2 hbar)) + alpha dt/hbar (H + H*)/2 + s zeta,
  * s = sqrt(2 alpha kB T dt/hbar), zeta the spin stream's normals, no renormalisation;
  * the options' lambda_spin is not used.  sl_set_state keeps the given spin lengths.
- * enable = 0 returns to unit spins (each spin is normalised).  The carried forces and
- * fields are re-evaluated.  SL_EINVAL for alpha < 0, a non-finite coefficient, or a
- * system created with midpoint_iters > 0. */
+ * enable = 0 returns to unit spins (each spin is normalised; a spin of zero length gives
+ * SL_ENONFINITE).  The carried forces and fields are re-evaluated.  SL_EINVAL for
+ * alpha < 0, a non-finite coefficient, or a system created with midpoint_iters > 0. */
 int sl_set_longitudinal(sl_system *sys, int32_t enable, double alpha, const double *landau);
 
 /* Texture diagnostics of a film with normal normal_axis (0, 1, 2), computed on the

@@ -316,6 +316,13 @@ int sl_selftest_harmonics(int32_t n_samples, double *max_addition_err, double *m
  * FP64 magnitudes.  SL_EINVAL for n_samples < 1 or rc <= 0; SL_ECUDA without a device. */
 int sl_selftest_carrier(int32_t n_samples, double rc, double *max_rel_err_f, double *max_rel_err_df);
 
+/* Device self-test of the bounded waits the tensor-core network kernel uses: one thread waits
+ * on a shared-memory mbarrier that nothing arrives at, gives up after max_polls polls and
+ * raises the timeout status bit, which the host reads.  Returns SL_ETIMEOUT (the expected
+ * outcome, the device and context stay usable), SL_OK if the wait completed, SL_EINVAL for
+ * max_polls outside [1, 2^22], SL_ECUDA without a device. */
+int sl_selftest_bounded_wait(int32_t max_polls);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,8 +18,18 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/spinlat.h"
 #include "sl_internal.h"
+
+// NVTX range over a host-side call (shows up in profilers that record NVTX; a no-op otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct sl_system {
     sl::Sys s;
@@ -342,6 +352,7 @@ const char *sl_last_error(void) { return g_err.c_str(); }
 int sl_create_system(const double *positions, const double *spins, const double box[3], const int32_t periodic[3],
                      const int32_t *species, int64_t n, const double *velocities, const sl_nep_params *params,
                      const sl_options *opt_in, sl_system **out) {
+    NvtxRange nvtx_range("sl_create_system");
     using namespace sl;
     if (!out) return fail(SL_EINVAL, "out is NULL");
     *out = nullptr;
@@ -616,6 +627,7 @@ static int finish_steps(sl::Sys &s, int64_t n_steps, const char *who) {
 }
 
 int sl_step(sl_system *sys, int64_t n_steps, double dt, double T, const double B[3]) {
+    NvtxRange nvtx_range("sl_step");
     if (!sys || !B) return fail(SL_EINVAL, "NULL argument");
     if (n_steps < 0 || !(dt > 0) || !(T >= 0) || !std::isfinite(dt) || !std::isfinite(T))
         return fail(SL_EINVAL, "bad step arguments");
@@ -633,6 +645,7 @@ int sl_step(sl_system *sys, int64_t n_steps, double dt, double T, const double B
 }
 
 int sl_energy_forces_fields(sl_system *sys, double *energy, double *forces, double *fields, double *virial) {
+    NvtxRange nvtx_range("sl_energy_forces_fields");
     if (!sys) return fail(SL_EINVAL, "NULL system");
     sl::Sys &s = sys->s;
     cudaSetDevice(s.device);
@@ -699,6 +712,7 @@ int sl_get_state(const sl_system *sys, double *pos, double *vel, double *spins, 
 
 int sl_set_state(sl_system *sys, const double *pos, const double *vel, const double *spins, const double *forces,
                  const double *fields, const double *ref, uint64_t step) {
+    NvtxRange nvtx_range("sl_set_state");
     if (!sys) return fail(SL_EINVAL, "NULL system");
     sl::Sys &s = sys->s;
     cudaSetDevice(s.device);
@@ -985,6 +999,7 @@ int64_t sl_estimate_device_bytes(int64_t n, const sl_options *opt_in) {
 }
 
 int sl_step_profiled(sl_system *sys, int64_t n_steps, double dt, double T, const double B[3], double *kernel_ms) {
+    NvtxRange nvtx_range("sl_step_profiled");
     if (!sys || !B || !kernel_ms) return fail(SL_EINVAL, "NULL argument");
     if (n_steps < 0 || !(dt > 0) || !(T >= 0)) return fail(SL_EINVAL, "bad step arguments");
     sl::Sys &s = sys->s;
@@ -1114,6 +1129,7 @@ static int batch_graph(sl_batch *b, int g) {
 }
 
 int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt, const double *T, const double *B) {
+    NvtxRange nvtx_range("sl_batch_step");
     if (!b || !n_steps || !dt || !T || !B) return fail(SL_EINVAL, "NULL argument");
     const int k = (int)b->sys.size();
     for (int i = 0; i < k; ++i) {
@@ -1236,6 +1252,16 @@ int sl_selftest_carrier(int32_t n_samples, double rc, double *max_rel_err_f, dou
     if (sl::selftest_carrier(n_samples, rc, out)) return fail(SL_ECUDA, "carrier self-test failed to run");
     if (max_rel_err_f) *max_rel_err_f = out[0] / out[2];
     if (max_rel_err_df) *max_rel_err_df = out[1] / out[3];
+    return SL_OK;
+}
+
+int sl_selftest_bounded_wait(int32_t max_polls) {
+    if (max_polls < 1 || max_polls > (1 << 22)) return fail(SL_EINVAL, "max_polls must be in [1, 2^22]");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return fail(SL_ECUDA, "no usable CUDA device");
+    int st = 0;
+    if (sl::selftest_bounded_wait(max_polls, &st)) return fail(SL_ECUDA, "bounded-wait self-test failed to run");
+    if (st & sl::ST_TIMEOUT) return fail(SL_ETIMEOUT, "a bounded device wait gave up (self-test)");
     return SL_OK;
 }
 

@@ -210,5 +210,7 @@ int noalloc_max_atoms();
 int measure_fma_peak(int precision, double *flops_per_s, double *elapsed_ms);
 // FP32 carrier against FP64 at n radii in [0, rc): out = {max |df|, max |d(df/dr)|, max |f|, max |df/dr|}
 int selftest_carrier(int n, double rc, double out[4]);
+// sl_mlp_tc.cu: a bounded mbarrier wait on a barrier nothing arrives at; *status_out gets the device status bits
+int selftest_bounded_wait(int limit, int *status_out);
 
 }  // namespace sl

@@ -90,8 +90,10 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 22); ++it) {
+constexpr int WAIT_LIMIT = 1 << 22;   // polls of a barrier before a wait gives up
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit = WAIT_LIMIT) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -331,7 +333,28 @@ __global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDe
     }
 }
 
+// Self-test of the bounded wait: one thread waits on a barrier that nothing ever arrives
+// at, gives up after `limit` polls and raises ST_TIMEOUT, as the network kernel does.
+__global__ void k_selftest_wait(int limit, int *status) {
+    __shared__ __align__(8) unsigned long long bar_storage;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bar_storage);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(bar, 0, limit)) atomicOr(status, ST_TIMEOUT);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
 }  // namespace tc
+
+int selftest_bounded_wait(int limit, int *status_out) {
+    int *d;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return -1;
+    cudaMemset(d, 0, sizeof(int));
+    tc::k_selftest_wait<<<1, 1>>>(limit, d);
+    cudaError_t e = cudaMemcpy(status_out, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? 0 : -1;
+}
 
 void launch_network_tc(Sys &s) {
     int dev = 0, sms = 148;

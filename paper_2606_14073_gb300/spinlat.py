@@ -24,7 +24,8 @@ EXPORTS = ["sl_default_options", "sl_create_system", "sl_step", "sl_energy_force
            "sl_destroy_system", "sl_last_error", "sl_batch_create", "sl_batch_step", "sl_batch_destroy",
            "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak", "sl_descriptors_energies_noalloc",
            "sl_estimate_device_bytes", "sl_get_midpoint_evaluations", "sl_set_atom_fields", "sl_texture_map",
-           "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal", "sl_selftest_carrier"]
+           "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal", "sl_selftest_carrier",
+           "sl_selftest_bounded_wait"]
 KERNEL_GROUPS = ["first_half", "rebuild", "compact", "rad_fwd", "ang_fwd", "network", "backward", "second_half"]
 
 
@@ -75,6 +76,7 @@ def lib(path: str | None = None):
             L.sl_set_atom_fields.argtypes = [P, P]
             L.sl_set_longitudinal.argtypes = [P, I32, D, P]
             L.sl_selftest_carrier.argtypes = [I32, D, P, P]
+            L.sl_selftest_bounded_wait.argtypes = [I32]
             L.sl_batch_graph_launches.argtypes = [P, P]
             L.sl_autotune.argtypes = [P, I32, P, P, P]
             L.sl_texture_map.argtypes = [P, I32, D, P, P, P, P]
@@ -98,7 +100,7 @@ def lib(path: str | None = None):
                       "sl_batch_step", "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak",
                       "sl_descriptors_energies_noalloc", "sl_get_midpoint_evaluations", "sl_set_atom_fields",
                       "sl_texture_map", "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal",
-                      "sl_selftest_carrier"):
+                      "sl_selftest_carrier", "sl_selftest_bounded_wait"):
                 getattr(L, f).restype = C.c_int
             _lib = L
         return _lib

@@ -349,3 +349,16 @@ def test_fp32_carrier_matches_fp64_carrier():
     for rc in (6.0, 4.0):
         ef, edf = S.sl_selftest_carrier(200000, rc)
         assert ef < 1e-5 and edf < 1e-5, (rc, ef, edf)
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(params, model):
+    """A device wait on a barrier nothing arrives at stops after its poll limit and reports
+    SL_ETIMEOUT through the status word; evaluations on the same context are unaffected."""
+    assert S.lib().sl_selftest_bounded_wait(1000) == S.SL_ETIMEOUT
+    wl = W.fege_small()
+    s = S.system_from_workload(wl, params, precision=S.SL_PREC_MIXED)   # the tensor-core network path
+    st = s.get_state()
+    r = s.energy_forces_fields(want_virial=False)
+    ref = O.evaluate(model, st["positions"], st["spins"], wl.species, wl.box, wl.periodic)
+    assert np.sqrt(((r["F"] - ref["F"]) ** 2).mean()) <= 1e-3
+    s.destroy()

@@ -104,3 +104,8 @@ def test_carrier_selftest_argument_checks():
     a, b = C.c_double(), C.c_double()
     assert S.lib().sl_selftest_carrier(0, 6.0, C.byref(a), C.byref(b)) == S.SL_EINVAL
     assert S.lib().sl_selftest_carrier(10, -1.0, C.byref(a), C.byref(b)) == S.SL_EINVAL
+
+
+def test_bounded_wait_selftest_argument_checks():
+    assert S.lib().sl_selftest_bounded_wait(0) == S.SL_EINVAL
+    assert S.lib().sl_selftest_bounded_wait(1 << 23) == S.SL_EINVAL

@@ -138,6 +138,7 @@ void free_sys(sl::Sys &s) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (s.h_par) cudaFreeHost(s.h_par);
+    if (s.h_stage) cudaFreeHost(s.h_stage);
     if (s.h_status) cudaFreeHost(s.h_status);
     if (s.h_red) cudaFreeHost(s.h_red);
     if (s.graph) cudaGraphExecDestroy(s.graph);
@@ -224,12 +225,22 @@ int check_status(sl::Sys &s) {
     return SL_OK;
 }
 
-// host (caller order) -> device (internal order)
+// Pinned staging buffer of n records for state transfers (allocated once per system).
+static double4 *stage_buffer(const sl::Sys &s) {
+    if (!s.h_stage && cudaMallocHost((void **)&s.h_stage, sizeof(double4) * (size_t)s.n) != cudaSuccess) {
+        s.h_stage = nullptr;
+        return nullptr;
+    }
+    return s.h_stage;
+}
+
+// host (caller order) -> device (internal order), through the pinned staging buffer
 int upload_vec(sl::Sys &s, double4 *dst, const double *src, bool normalise) {
-    std::vector<double4> h((size_t)s.n);
-    std::vector<int32_t> orig((size_t)s.n);
-    CK(cudaMemcpyAsync(orig.data(), s.orig, sizeof(int32_t) * s.n, cudaMemcpyDeviceToHost, s.stream));
+    double4 *h = stage_buffer(s);
+    if (!h) return fail(SL_ENOMEM, "pinned staging buffer allocation failed");
+    // the buffer may still be read by an earlier copy on this stream
     CK(cudaStreamSynchronize(s.stream));
+    const int32_t *orig = s.h_orig.data();
     for (int64_t i = 0; i < s.n; ++i) {
         const double *p = src + 3 * (int64_t)orig[i];
         double x = p[0], y = p[1], z = p[2];
@@ -244,18 +255,18 @@ int upload_vec(sl::Sys &s, double4 *dst, const double *src, bool normalise) {
         }
         h[i] = make_double4(x, y, z, 0.0);
     }
-    // ordered on the system's stream; synchronised before the host buffer is released
-    CK(cudaMemcpyAsync(dst, h.data(), sizeof(double4) * s.n, cudaMemcpyHostToDevice, s.stream));
+    // ordered on the system's stream; synchronised before the staging buffer is reused
+    CK(cudaMemcpyAsync(dst, h, sizeof(double4) * s.n, cudaMemcpyHostToDevice, s.stream));
     CK(cudaStreamSynchronize(s.stream));
     return SL_OK;
 }
 
 int download_vec(const sl::Sys &s, const double4 *src, double *dst) {
-    std::vector<double4> h((size_t)s.n);
-    std::vector<int32_t> orig((size_t)s.n);
-    CK(cudaMemcpyAsync(h.data(), src, sizeof(double4) * s.n, cudaMemcpyDeviceToHost, s.stream));
-    CK(cudaMemcpyAsync(orig.data(), s.orig, sizeof(int32_t) * s.n, cudaMemcpyDeviceToHost, s.stream));
+    double4 *h = stage_buffer(s);
+    if (!h) return fail(SL_ENOMEM, "pinned staging buffer allocation failed");
+    CK(cudaMemcpyAsync(h, src, sizeof(double4) * s.n, cudaMemcpyDeviceToHost, s.stream));
     CK(cudaStreamSynchronize(s.stream));
+    const int32_t *orig = s.h_orig.data();
     for (int64_t i = 0; i < s.n; ++i) {
         double *p = dst + 3 * (int64_t)orig[i];
         p[0] = h[i].x; p[1] = h[i].y; p[2] = h[i].z;
@@ -484,6 +495,7 @@ int sl_create_system(const double *positions, const double *spins, const double 
         inv[order[i]] = (int32_t)i;
         spec[i] = species[order[i]];
     }
+    s.h_orig = order;   // host copy of the permutation for state transfers
     s.n_fe = 0;
     for (int64_t i = 0; i < n; ++i) s.n_fe += spec[i] == 0;
 

@@ -133,6 +133,10 @@ struct Sys {
     int64_t n_launches = 0;    // kernels launched by step calls
     double *red = nullptr;     // reduction scratch (device)
     double *h_red = nullptr;   // pinned
+    // host side of state transfers: the internal -> caller order permutation (fixed at
+    // creation) and a pinned staging buffer of n records, allocated on first use
+    std::vector<int32_t> h_orig;
+    mutable double4 *h_stage = nullptr;
 
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;

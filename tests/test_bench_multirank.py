@@ -80,3 +80,35 @@ def test_reference_arm_other_ranks_exit_quietly(monkeypatch):
     class A:
         steps, warmup, ref_budget_s = 1, 3, 1.0
     assert bench.run_reference(A()) == 0
+
+
+def test_roofline_arithmetic_and_traffic_guard(tmp_path, monkeypatch):
+    """The per-kernel roofline is algorithmic work / measured time / peak, and a committed DRAM
+    capture is only used while the evaluation kernels' sources hash to the recorded value."""
+    import bench
+    from paper_2606_14073_gb300 import flops
+    fl = flops.per_atom(62.0, 16.0)
+    prof = {"rad_fwd": 2.0, "ang_fwd": 1.0, "network": 0.4, "backward": 4.0}   # ms over 2 steps
+    out = bench.kernel_rooflines(fl, prof, 2, 1_000_000, 80.0)
+    assert abs(out["backward"]["achieved_tflops"] - fl["backward"] * 1e6 / 2e-3 / 1e12) < 1e-9
+    assert abs(out["backward"]["frac"] - out["backward"]["achieved_tflops"] / 80.0) < 1e-12
+    assert abs(out["network"]["achieved_gbs"] - bench.NETWORK_BYTES_PER_ATOM * 1e6 / 0.2e-3 / 1e9) < 1e-6
+    # traffic: accepted with the current hash, refused with any other
+    prof_dir = tmp_path / "profiles"
+    prof_dir.mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "paper_2606_14073_gb300").symlink_to(os.path.join(ROOT, "paper_2606_14073_gb300"))
+    h = bench.kernel_source_hash()
+    (prof_dir / "traffic_backward.txt").write_text(f"kernel_sources_sha256_16: {h}\ndram_bytes_per_launch_full_size: 123\n")
+    assert bench.committed_traffic("backward") == 123.0
+    (prof_dir / "traffic_backward.txt").write_text("kernel_sources_sha256_16: 0000\ndram_bytes_per_launch_full_size: 123\n")
+    assert bench.committed_traffic("backward") is None
+
+
+def test_neighbour_counts_of_the_crystal():
+    """Mean neighbour counts inside 6 and 4 A on the seeded B20 cube: close to the density estimate
+    (0.0771 atoms/A^3) and to the values the algorithmic-work counts use."""
+    import bench
+    from paper_2606_14073_gb300 import workloads as W
+    nr, na = bench.neighbour_counts(W.fege_cube(8))
+    assert abs(nr - 62.0) < 1.0 and abs(na - 16.0) < 1.0

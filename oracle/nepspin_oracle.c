@@ -114,6 +114,8 @@ typedef struct {
     double anderson_reg;      /* Tikhonov weight, relative to the mean diagonal              */
     int32_t longitudinal;     /* 1: variable moment lengths (no renormalisation)            */
     double alpha_long;        /* dimensionless damping of the longitudinal mode              */
+    int32_t st_sweep;         /* 1: coloured Suzuki-Trotter spin sweep instead of the
+                                 predictor-corrector spin update                            */
 } or_dynamics;
 
 static int or_dim(int n_ch) { return 1 + 13 * n_ch; }
@@ -869,6 +871,49 @@ out:
     return rc;
 }
 
+/* Colouring for the coloured spin sweep: atoms i and j conflict when their minimum-image
+ * distance is below 2 rc (d^2 < (2 rc)^2, the neighbour-list arithmetic), since the field on a
+ * spin depends on every spin within 2 rc through the neighbours' descriptors.  Greedy in
+ * index order: colour(i) = the smallest c >= 0 used by no conflicting j < i.  Returns the
+ * number of colours (>= 1 when n > 0), or a negative code. */
+int or_colour(int64_t n, const double *pos, const double *box, const int32_t *per, double rc,
+              int32_t *colour) {
+    if (n == 0) return 0;
+    or_nlist nl;
+    if (build_nlist(n, pos, box, per, 2.0 * rc, n > 2000 ? 1 : 0, &nl)) return -1;
+    int64_t cap = 64;
+    unsigned char *used = (unsigned char *)calloc((size_t)cap, 1);
+    if (!used) return -1;
+    int32_t ncol = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t p = nl.off[i]; p < nl.off[i + 1]; ++p) {
+            int32_t j = nl.idx[p];
+            if (j < i) {
+                if (colour[j] >= cap) {
+                    int64_t nc2 = 2 * (int64_t)colour[j] + 2;
+                    unsigned char *u2 = (unsigned char *)realloc(used, (size_t)nc2);
+                    if (!u2) { free(used); free_nlist(&nl); return -1; }
+                    memset(u2 + cap, 0, (size_t)(nc2 - cap));
+                    used = u2;
+                    cap = nc2;
+                }
+                used[colour[j]] = 1;
+            }
+        }
+        int32_t c = 0;
+        while (c < cap && used[c]) ++c;
+        colour[i] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+        for (int64_t p = nl.off[i]; p < nl.off[i + 1]; ++p) {
+            int32_t j = nl.idx[p];
+            if (j < i) used[colour[j]] = 0;
+        }
+    }
+    free(used);
+    free_nlist(&nl);
+    return ncol;
+}
+
 /* Advance (pos, vel, spin) by n_steps steps of dt (fs) at temperature T (K) and
  * field B (T).  F and H carry the forces and fields of the current state between
  * calls (have_fh = 0: they are evaluated first).  One step, from (r, v, S, F, H):
@@ -904,7 +949,16 @@ out:
  * the predictor-corrector structure (Heun on the spin equation, the same noise in both):
  *   Sstar = Rot(S, H dt/hbar) + alpha dt/hbar H + sqrt(2 alpha kT dt/hbar) zeta;
  *   S <- Rot(S, (H + Hstar) dt/(2 hbar)) + alpha dt/hbar (H + Hstar)/2 + sqrt(2 alpha kT dt/hbar) zeta,
- * with no renormalisation; lambda_spin is not used.  Not combined with the midpoint mode. */
+ * with no renormalisation; lambda_spin is not used.  Not combined with the midpoint mode.
+ *
+ * Coloured Suzuki-Trotter spin sweep (dyn->st_sweep = 1; a splitting of the spin update
+ * into colour classes of mutually independent spins).  The lattice part is unchanged; at
+ * the new positions r the atoms are coloured (or_colour, conflict radius 2 rc_rad) and the
+ * spins are advanced by a symmetric sweep over the C colours, c = 0..C-1 then C-1..0: each
+ * sub-step evaluates H at (r, S) and rotates every spin of colour c by half a step,
+ *   S_i <- Rot(S_i, omega(S_i, H_i + eta_i) dt/2), renormalised,
+ * with the step's eta as in the predictor-corrector; then (F, H) at (r, S) and v += dt/2 F/m.
+ * 2C + 1 evaluations per step.  Not combined with the midpoint or the longitudinal mode. */
 int or_run(int64_t n, double *pos, double *vel, double *spin, const int32_t *species, const double *box,
            const int32_t *per, const or_params *P, const or_dynamics *dyn, int64_t n_steps, double dt,
            double T, const double B[3], uint64_t step0, double *F, double *H, int have_fh,
@@ -915,6 +969,10 @@ int or_run(int64_t n, double *pos, double *vel, double *spin, const int32_t *spe
         return -3;
     const int lng = dyn->longitudinal != 0;
     if (lng && (dyn->midpoint_iters > 0 || !(dyn->alpha_long >= 0.0))) return -3;
+    const int sts = dyn->st_sweep != 0;
+    if (sts && (dyn->midpoint_iters > 0 || lng)) return -3;
+    int32_t *colour = NULL;
+    if (sts && !(colour = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1)))) return -1;
     if (iters_used) *iters_used = 0;
     int rc;
     if (!have_fh) {
@@ -956,6 +1014,10 @@ int or_run(int64_t n, double *pos, double *vel, double *spin, const int32_t *spe
                 eta[3 * i + c] = sig_eta * ze[c];
             }
             double Hp[3], w[3];
+            if (sts) {   /* the spins wait for the colour sweep at the new positions */
+                for (int c = 0; c < 3; ++c) S0[3 * i + c] = spin[3 * i + c];
+                continue;
+            }
             if (lng) {   /* eta is the additive noise displacement here */
                 for (int c = 0; c < 3; ++c) S0[3 * i + c] = spin[3 * i + c];
                 omega_of(S0 + 3 * i, H + 3 * i, 0.0, w);
@@ -978,6 +1040,35 @@ int or_run(int64_t n, double *pos, double *vel, double *spin, const int32_t *spe
                     vel[3 * i + c] += 0.5 * dt * Fs[3 * i + c] * OR_ACC / m;
                     F[3 * i + c] = Fs[3 * i + c];
                     H[3 * i + c] = Hs[3 * i + c];
+                }
+            }
+            continue;
+        }
+        if (sts) {
+            const int ncol = or_colour(n, pos, box, per, P->rc_rad, colour);
+            if (ncol < 0) { rc = -1; break; }
+            for (int pass = 0; pass < 2 * ncol && !rc; ++pass) {
+                const int32_t c = pass < ncol ? pass : 2 * ncol - 1 - pass;
+                rc = or_evaluate(n, pos, spin, species, box, per, P, B, NULL, NULL, Fs, Hs, NULL);
+                for (int64_t i = 0; i < n && !rc; ++i) {
+                    if (colour[i] != c) continue;
+                    double Hp[3], w[3], Sn[3];
+                    for (int q = 0; q < 3; ++q) Hp[q] = Hs[3 * i + q] + eta[3 * i + q];
+                    omega_of(spin + 3 * i, Hp, lam, w);
+                    or_rotate(spin + 3 * i, w, 0.5 * dt, Sn);
+                    normalise3(Sn);
+                    for (int q = 0; q < 3; ++q) spin[3 * i + q] = Sn[q];
+                }
+            }
+            if (rc) break;
+            rc = or_evaluate(n, pos, spin, species, box, per, P, B, NULL, NULL, Fs, Hs, NULL);
+            if (rc) break;
+            for (int64_t i = 0; i < n; ++i) {
+                double m = P->mass_amu[species[i]];
+                for (int q = 0; q < 3; ++q) {
+                    vel[3 * i + q] += 0.5 * dt * Fs[3 * i + q] * OR_ACC / m;
+                    F[3 * i + q] = Fs[3 * i + q];
+                    H[3 * i + q] = Hs[3 * i + q];
                 }
             }
             continue;
@@ -1017,7 +1108,7 @@ int or_run(int64_t n, double *pos, double *vel, double *spin, const int32_t *spe
             }
         }
     }
-    free(S0); free(eta); free(Fs); free(Hs); free(pmid);
+    free(S0); free(eta); free(Fs); free(Hs); free(pmid); free(colour);
     return rc;
 }
 

@@ -56,7 +56,7 @@ class _Dyn(C.Structure):
                 ("seed", C.c_uint64), ("replica", C.c_uint64),
                 ("midpoint_iters", C.c_int32), ("anderson_depth", C.c_int32),
                 ("midpoint_tol", C.c_double), ("anderson_reg", C.c_double),
-                ("longitudinal", C.c_int32), ("alpha_long", C.c_double)]
+                ("longitudinal", C.c_int32), ("alpha_long", C.c_double), ("st_sweep", C.c_int32)]
 
 
 def lib():
@@ -79,6 +79,8 @@ def lib():
                 getattr(_lib, f).restype = C.c_int
             _lib.or_num_threads.restype = C.c_int
             _lib.or_set_num_threads.argtypes = [C.c_int]
+            _lib.or_colour.argtypes = [I, P, P, P, D, P]
+            _lib.or_colour.restype = C.c_int
             _lib.or_set_num_threads.restype = None
         return _lib
 
@@ -245,17 +247,19 @@ class State:
 
 def run(model: Model, st: State, n_steps: int, dt: float, T: float, B=(0.0, 0.0, 0.0), *,
         gamma=0.01, lam=0.1, seed=1234, replica=0, midpoint_iters=0, midpoint_tol=0.0, anderson_depth=0,
-        anderson_reg=1e-10, B_atoms=None, longitudinal=False, alpha_long=0.0):
+        anderson_reg=1e-10, B_atoms=None, longitudinal=False, alpha_long=0.0, st_sweep=False):
     """Advance st by n_steps steps (or_run).  midpoint_iters > 0 selects the self-consistent
     midpoint spin update (cap of the iteration, tolerance midpoint_tol, optional Anderson
     history anderson_depth with relative regularisation anderson_reg).  Returns st; the
     number of midpoint evaluations of the call is in st.last_iterations.  B_atoms is the
     optional per-atom part of the external field ([n][3] tesla).  longitudinal=True frees the
-    moment lengths (Langevin form with longitudinal damping alpha_long; lam is then unused)."""
+    moment lengths (Langevin form with longitudinal damping alpha_long; lam is then unused).
+    st_sweep=True replaces the predictor-corrector spin update by the coloured Suzuki-Trotter
+    sweep (or_colour colouring at the new positions, 2C + 1 evaluations per step)."""
     ba = _batoms(B_atoms, st.pos.shape[0])
     P = model.c_struct(ba)
     dyn = _Dyn(gamma, lam, seed, replica, int(midpoint_iters), int(anderson_depth), float(midpoint_tol),
-               float(anderson_reg), int(bool(longitudinal)), float(alpha_long))
+               float(anderson_reg), int(bool(longitudinal)), float(alpha_long), int(bool(st_sweep)))
     Bv = _f64(B)
     it = np.zeros(1, dtype=np.int64)
     rc = lib().or_run(st.pos.shape[0], _p(st.pos), _p(st.vel), _p(st.spin), _p(st.species), _p(st.box),
@@ -271,6 +275,17 @@ def run(model: Model, st: State, n_steps: int, dt: float, T: float, B=(0.0, 0.0,
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def colour(pos, box, periodic, rc):
+    """Greedy colouring (index order) of the conflict graph d < 2 rc (or_colour): (colours, count)."""
+    pos, box = _f64(pos), _f64(box)
+    periodic = np.ascontiguousarray(periodic, dtype=np.int32)
+    col = np.zeros(pos.shape[0], dtype=np.int32)
+    nc = lib().or_colour(pos.shape[0], _p(pos), _p(box), _p(periodic), float(rc), _p(col))
+    if nc < 0:
+        raise RuntimeError(f"or_colour failed: {nc}")
+    return col, int(nc)
 
 
 def set_num_threads(t: int):

@@ -197,6 +197,26 @@ int sl_set_atom_fields(sl_system *sys, const double *B_atoms);
  * alpha < 0, a non-finite coefficient, or a system created with midpoint_iters > 0. */
 int sl_set_longitudinal(sl_system *sys, int32_t enable, double alpha, const double *landau);
 
+/* Coloured Suzuki-Trotter spin sweep (a splitting of the spin update into classes of spins
+ * that do not see each other's fields; the paper integrates with the predictor-corrector and
+ * the midpoint iteration of Section 5.1.3, this is the coloured variant of that spin update).
+ * With enable != 0, each sl_step step keeps the lattice part and replaces the spin
+ * predictor-corrector by: colour the atoms at the new positions (atoms closer than 2 rc_rad
+ * conflict, because the field on a spin depends on every spin within 2 rc_rad through the
+ * neighbours' descriptors; greedy colouring in caller index order, the smallest colour unused
+ * by conflicting atoms of lower index), then for c = 0..C-1 and back C-1..0 evaluate the
+ * field at the current spins and rotate every spin of colour c by half a step,
+ * S <- Rot(S, omega(S, H + eta) dt/2), renormalised, with the step's thermal field eta; then
+ * forces and fields at the new state and the final lattice kick.  2C + 1 evaluations per
+ * step, driven from the host (no graph capture).  SL_EINVAL with the midpoint or the
+ * longitudinal mode; batches and sl_step_profiled refuse systems in this mode. */
+int sl_set_spin_sweep(sl_system *sys, int32_t enable);
+
+/* The colouring of the last coloured step: colours [n] in caller order (may be NULL; then no
+ * device copy), the number of colours and the evaluations made by coloured steps so far.
+ * SL_EINVAL for colours != NULL before any coloured step. */
+int sl_get_sweep_colours(const sl_system *sys, int32_t *colours, int32_t *n_colours, int64_t *evaluations);
+
 /* Texture diagnostics of a film with normal normal_axis (0, 1, 2), computed on the
  * device at the current state (Fig. 7 and Section 8 follow helix and skyrmion textures
  * in a thin stripe).  The two in-plane axes a < b are cut into n_a = max(1, floor(L_a /

@@ -134,7 +134,7 @@ void free_sys(sl::Sys &s) {
                     s.wpart, s.Fo, s.Ho,
                     s.status, s.rebuild, s.d_step, s.d_par, s.red, s.snap, s.d_builds,
                     s.posmid, s.posmidf, s.mids, s.midsf, s.mx, s.mg, s.aax, s.aag, s.aapart, s.md, s.Bat,
-                    s.tex_acc, s.tex_m, s.tex_part};
+                    s.tex_acc, s.tex_m, s.tex_part, s.colour};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (s.h_par) cudaFreeHost(s.h_par);
@@ -160,6 +160,7 @@ void compute_step_params(const sl::Sys &s, double dt, double T, const double B[3
     P.lambda = s.lambda;
     P.wscale = 1.0 / ((1.0 + s.lambda * s.lambda) * HBAR);
     P.disp2 = 0.25 * s.skin * s.skin;
+    P.sts = s.sts;
     P.lng = s.lng;
     P.lng_drift = 0.0;
     P.lng_sig = 0.0;
@@ -603,6 +604,126 @@ static int restore_state(sl::Sys &s) {
     return SL_OK;
 }
 
+// ------------------------------------------------------------------ coloured spin sweep
+// Squared minimum-image distance with one rounding per operation and no fused multiply-add
+// (the neighbour-list arithmetic): each intermediate goes through a volatile so that no
+// compiler contraction can change a borderline decision.
+static double exact_d2_host(const double *a, const double *b, const double *L, const int *per) {
+    volatile double t[3];
+    for (int k = 0; k < 3; ++k) {
+        volatile double u = b[k] - a[k];
+        if (per[k]) {
+            volatile double q = std::rint(u / L[k]);
+            volatile double m = L[k] * q;
+            u = u - m;
+        }
+        t[k] = u;
+    }
+    volatile double xx = t[0] * t[0], yy = t[1] * t[1], zz = t[2] * t[2];
+    volatile double sxy = xx + yy;
+    return sxy + zz;
+}
+
+// Greedy colouring, in caller index order, of the graph joining atoms closer than 2 rc_rad:
+// colour(i) = the smallest c used by no conflicting atom of lower caller index.  Positions
+// are the device state (internal order); the colours go back to the device in internal order.
+static int colour_atoms(sl::Sys &s) {
+    const int64_t n = s.n;
+    std::vector<double4> h((size_t)n);
+    CK(cudaMemcpyAsync(h.data(), s.pos, sizeof(double4) * n, cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaStreamSynchronize(s.stream));
+    // caller-order coordinates
+    std::vector<double> x((size_t)(3 * n));
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t c = s.h_orig[(size_t)k];
+        x[3 * c] = h[k].x; x[3 * c + 1] = h[k].y; x[3 * c + 2] = h[k].z;
+    }
+    const double cut = 2.0 * s.pd.rc_r, cut2 = cut * cut;
+    // cell list with cells of at least the conflict radius (all cells when a dimension has fewer than 3)
+    int nc[3];
+    for (int a = 0; a < 3; ++a) nc[a] = std::max(1, (int)std::floor(s.box[a] / (cut * (1.0 + 1e-9))));
+    const int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    std::vector<int64_t> cstart((size_t)ncell + 1, 0), catoms((size_t)n);
+    std::vector<int32_t> cof((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        int ci[3];
+        for (int a = 0; a < 3; ++a) {
+            double v = x[3 * i + a];
+            if (s.per[a]) v = v - s.box[a] * std::floor(v / s.box[a]);
+            ci[a] = std::min(std::max((int)std::floor(v / (s.box[a] / nc[a])), 0), nc[a] - 1);
+        }
+        cof[i] = (int32_t)(((int64_t)ci[2] * nc[1] + ci[1]) * nc[0] + ci[0]);
+        cstart[(size_t)cof[i] + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
+    {
+        std::vector<int64_t> fill(cstart.begin(), cstart.end() - 1);
+        for (int64_t i = 0; i < n; ++i) catoms[(size_t)fill[(size_t)cof[i]]++] = i;
+    }
+    std::vector<int32_t> col((size_t)n, -1);
+    std::vector<char> used;
+    int32_t ncol = 0;
+    std::vector<int32_t> seen;
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t cc = cof[i];
+        const int ci[3] = {(int)(cc % nc[0]), (int)((cc / nc[0]) % nc[1]), (int)(cc / ((int64_t)nc[0] * nc[1]))};
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            if (s.per[a] && nc[a] < 3) { lo[a] = 0; hi[a] = nc[a] - 1; }
+            else if (s.per[a]) { lo[a] = ci[a] - 1; hi[a] = ci[a] + 1; }
+            else { lo[a] = std::max(ci[a] - 1, 0); hi[a] = std::min(ci[a] + 1, nc[a] - 1); }
+        }
+        seen.clear();
+        for (int z = lo[2]; z <= hi[2]; ++z)
+            for (int y = lo[1]; y <= hi[1]; ++y)
+                for (int xx = lo[0]; xx <= hi[0]; ++xx) {
+                    const int wx = (xx % nc[0] + nc[0]) % nc[0], wy = (y % nc[1] + nc[1]) % nc[1],
+                              wz = (z % nc[2] + nc[2]) % nc[2];
+                    const int64_t c = ((int64_t)wz * nc[1] + wy) * nc[0] + wx;
+                    for (int64_t p = cstart[(size_t)c]; p < cstart[(size_t)c + 1]; ++p) {
+                        const int64_t j = catoms[(size_t)p];
+                        if (j >= i) continue;
+                        if (exact_d2_host(&x[3 * i], &x[3 * j], s.box, s.per) < cut2) seen.push_back(col[(size_t)j]);
+                    }
+                }
+        if ((int64_t)used.size() < (int64_t)ncol + 1) used.resize((size_t)ncol + 1, 0);
+        for (int32_t c : seen) used[(size_t)c] = 1;
+        int32_t c = 0;
+        while (c < ncol && used[(size_t)c]) ++c;
+        col[(size_t)i] = c;
+        ncol = std::max(ncol, c + 1);
+        for (int32_t q : seen) used[(size_t)q] = 0;
+    }
+    std::vector<int32_t> hint((size_t)n);
+    for (int64_t k = 0; k < n; ++k) hint[(size_t)k] = col[(size_t)s.h_orig[(size_t)k]];
+    CK(cudaMemcpyAsync(s.colour, hint.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s.stream));
+    CK(cudaStreamSynchronize(s.stream));
+    s.last_colours = ncol;
+    return SL_OK;
+}
+
+// One step with the coloured sweep: lattice first half (spins untouched), conditional list
+// rebuild, colouring at the new positions, 2C sub-steps (evaluation + half-step rotation of one
+// colour, colours 0..C-1 then C-1..0), the final evaluation and the lattice kick.  Driven from
+// the host: the colouring and the number of sub-steps depend on the positions.
+static int sweep_step(sl::Sys &s) {
+    sl::launch_first_half(s);
+    sl::launch_rebuild(s, true);
+    int rc;
+    if ((rc = colour_atoms(s))) return rc;
+    const int C = s.last_colours;
+    for (int pass = 0; pass < 2 * C; ++pass) {
+        sl::launch_eval(s, false);
+        sl::launch_sweep_rotate(s, pass < C ? pass : 2 * C - 1 - pass);
+    }
+    sl::launch_eval(s, false);
+    sl::launch_second_half_nospin(s);
+    CK(cudaGetLastError());
+    s.sweep_evaluations += 2 * C + 1;
+    s.n_launches += sl::KERNELS_PER_STEP + (int64_t)2 * C * 5;
+    return SL_OK;
+}
+
 // Queue n_steps steps on the system's stream: captured graphs of steps_per_graph steps,
 // then single steps for the remainder.
 static int queue_steps(sl::Sys &s, int64_t n_steps) {
@@ -652,7 +773,13 @@ int sl_step(sl_system *sys, int64_t n_steps, double dt, double T, const double B
         s.step += (uint64_t)n_steps;
         return SL_OK;
     }
-    if ((rc = snapshot_state(s)) || (rc = queue_steps(s, n_steps))) return rc;
+    if ((rc = snapshot_state(s))) return rc;
+    if (s.sts) {
+        for (int64_t t = 0; t < n_steps; ++t)
+            if ((rc = sweep_step(s))) return rc;
+    } else if ((rc = queue_steps(s, n_steps))) {
+        return rc;
+    }
     return finish_steps(s, n_steps, "");
 }
 
@@ -926,9 +1053,41 @@ int sl_set_atom_fields(sl_system *sys, const double *B_atoms) {
     return SL_OK;
 }
 
+int sl_set_spin_sweep(sl_system *sys, int32_t enable) {
+    if (!sys) return fail(SL_EINVAL, "NULL system");
+    sl::Sys &s = sys->s;
+    if (enable && s.mid_iters > 0) return fail(SL_EINVAL, "the coloured sweep does not combine with the midpoint update");
+    if (enable && s.lng) return fail(SL_EINVAL, "the coloured sweep does not combine with the longitudinal mode");
+    cudaSetDevice(s.device);
+    CK(cudaStreamSynchronize(s.stream));
+    if (enable && !s.colour && s.n > 0) {
+        int rc;
+        if ((rc = dalloc(&s.colour, (size_t)s.n))) return rc;
+    }
+    s.sts = enable ? 1 : 0;
+    return upload_params(s, s.last_dt, s.last_T, s.B);
+}
+
+int sl_get_sweep_colours(const sl_system *sys, int32_t *colours, int32_t *n_colours, int64_t *evaluations) {
+    if (!sys) return fail(SL_EINVAL, "NULL system");
+    const sl::Sys &s = sys->s;
+    if (n_colours) *n_colours = s.last_colours;
+    if (evaluations) *evaluations = s.sweep_evaluations;
+    if (colours && s.n > 0) {
+        if (!s.colour || s.last_colours == 0) return fail(SL_EINVAL, "no coloured step has been taken");
+        cudaSetDevice(s.device);
+        std::vector<int32_t> h((size_t)s.n);
+        CK(cudaMemcpyAsync(h.data(), s.colour, sizeof(int32_t) * s.n, cudaMemcpyDeviceToHost, s.stream));
+        CK(cudaStreamSynchronize(s.stream));
+        for (int64_t k = 0; k < s.n; ++k) colours[s.h_orig[(size_t)k]] = h[(size_t)k];
+    }
+    return SL_OK;
+}
+
 int sl_set_longitudinal(sl_system *sys, int32_t enable, double alpha, const double *landau) {
     if (!sys) return fail(SL_EINVAL, "NULL system");
     sl::Sys &s = sys->s;
+    if (enable && s.sts) return fail(SL_EINVAL, "the longitudinal mode does not combine with the coloured sweep");
     if (enable) {
         if (!(alpha >= 0) || !std::isfinite(alpha)) return fail(SL_EINVAL, "alpha must be finite and >= 0");
         if (s.mid_iters > 0) return fail(SL_EINVAL, "the longitudinal mode does not combine with the midpoint update");
@@ -1013,6 +1172,7 @@ int64_t sl_estimate_device_bytes(int64_t n, const sl_options *opt_in) {
 int sl_step_profiled(sl_system *sys, int64_t n_steps, double dt, double T, const double B[3], double *kernel_ms) {
     NvtxRange nvtx_range("sl_step_profiled");
     if (!sys || !B || !kernel_ms) return fail(SL_EINVAL, "NULL argument");
+    if (sys->s.sts) return fail(SL_EINVAL, "per-kernel profiling does not cover the coloured sweep");
     if (n_steps < 0 || !(dt > 0) || !(T >= 0)) return fail(SL_EINVAL, "bad step arguments");
     sl::Sys &s = sys->s;
     cudaSetDevice(s.device);
@@ -1144,6 +1304,8 @@ int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt, const d
     NvtxRange nvtx_range("sl_batch_step");
     if (!b || !n_steps || !dt || !T || !B) return fail(SL_EINVAL, "NULL argument");
     const int k = (int)b->sys.size();
+    for (int i = 0; i < k; ++i)
+        if (b->sys[i]->s.sts) return fail(SL_EINVAL, "replica %d uses the coloured sweep, which steps alone", i);
     for (int i = 0; i < k; ++i) {
         if (n_steps[i] < 0 || !(dt[i] > 0) || !(T[i] >= 0) || !std::isfinite(dt[i]) || !std::isfinite(T[i]))
             return fail(SL_EINVAL, "bad step arguments for replica %d", i);

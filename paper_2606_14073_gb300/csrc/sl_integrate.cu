@@ -89,7 +89,9 @@ __global__ void __launch_bounds__(256) k_first_half(IntArgs a) {
     if (a.per[2]) r.z = r.z - a.bd.L[2] * floor(r.z * a.bd.invL[2]);
     const double se = P.sig_eta;
     double Sp[3];
-    if constexpr (MIXED) {
+    if (P.sts) {   // coloured sweep: the spins are advanced at the new positions, colour by colour
+        Sp[0] = S.x; Sp[1] = S.y; Sp[2] = S.z;
+    } else if constexpr (MIXED) {
         float w[3], d[3];
         const float fse = (float)se;
         omega_of_f((float)S.x, (float)S.y, (float)S.z, (float)H.x + fse * (float)ze[0],
@@ -231,6 +233,50 @@ __global__ void __launch_bounds__(256) k_gather_only(GatherArgs<R> g, const Step
         atomicOr(status, ST_NONFINITE);
 }
 
+// Coloured sweep sub-step: every spin of colour c is rotated by half a step about its
+// field at the current configuration, S <- Rot(S, omega(S, H + eta) dt/2), renormalised in
+// FP64; eta is the step's thermal field (the spin stream's normals of this step, as in the
+// predictor-corrector).  The field is gathered from the pair records of the evaluation just
+// made; spins of other colours are left alone.
+template <typename R, bool MIXED>
+__global__ void __launch_bounds__(256) k_sweep_rotate(IntArgs a, GatherArgs<R> g, const int32_t *colour, int c) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n || colour[i] != c) return;
+    const StepDev &P = *a.par;
+    const int t = i < a.n_fe ? 0 : 1;
+    const uint64_t id = (uint64_t)a.orig[i];
+    const unsigned long long st = a.step[1];
+    double Fs[3], Hs[3];
+    gather<R>(g, i, Fs, Hs);
+    Hs[0] += P.zee[t][0]; Hs[1] += P.zee[t][1]; Hs[2] += P.zee[t][2];
+    if (a.Bat) {
+        const double4 b = a.Bat[i];
+        Hs[0] += P.mom[t] * b.x; Hs[1] += P.mom[t] * b.y; Hs[2] += P.mom[t] * b.z;
+    }
+    const double4 S = a.spin[i];
+    const double se = P.sig_eta;
+    double Sn[3];
+    if constexpr (MIXED) {
+        float ze[3], w[3], d[3];
+        gauss3f(st, id, 2, a.seed, a.replica, ze);
+        const float fse = (float)se;
+        omega_of_f((float)S.x, (float)S.y, (float)S.z, (float)Hs[0] + fse * ze[0], (float)Hs[1] + fse * ze[1],
+                   (float)Hs[2] + fse * ze[2], (float)P.lambda, (float)P.wscale, w);
+        rotate_delta_f((float)S.x, (float)S.y, (float)S.z, w[0], w[1], w[2], (float)P.half_dt, d);
+        Sn[0] = S.x + (double)d[0]; Sn[1] = S.y + (double)d[1]; Sn[2] = S.z + (double)d[2];
+    } else {
+        double ze[3], w[3];
+        gauss3(st, id, 2, a.seed, a.replica, ze);
+        omega_of(S.x, S.y, S.z, Hs[0] + se * ze[0], Hs[1] + se * ze[1], Hs[2] + se * ze[2], P.lambda, P.wscale, w);
+        rotate(S.x, S.y, S.z, w, P.half_dt, Sn);
+    }
+    const double inn = 1.0 / sqrt(Sn[0] * Sn[0] + Sn[1] * Sn[1] + Sn[2] * Sn[2]);
+    Sn[0] *= inn; Sn[1] *= inn; Sn[2] *= inn;
+    a.spin[i] = make_double4(Sn[0], Sn[1], Sn[2], 0.0);
+    a.spinf[i] = make_float4((float)Sn[0], (float)Sn[1], (float)Sn[2], 0.f);
+    if (!(isfinite(Hs[0]) && isfinite(Hs[1]) && isfinite(Hs[2]))) atomicOr(a.status, ST_NONFINITE);
+}
+
 static IntArgs int_args(Sys &s) {
     IntArgs a;
     a.pos = s.pos; a.vel = s.vel; a.spin = s.spin; a.spin_prev = s.spin_prev; a.F = s.F; a.H = s.H;
@@ -270,6 +316,15 @@ void launch_second_half_nospin(Sys &s) {
     if (s.prec == 0)
         k_second_half<double, false, false><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<double>(s));
     else k_second_half<float, true, false><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<float>(s));
+}
+
+void launch_sweep_rotate(Sys &s, int c) {
+    if (s.prec == 0)
+        k_sweep_rotate<double, false><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<double>(s),
+                                                                            s.colour, c);
+    else
+        k_sweep_rotate<float, true><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<float>(s),
+                                                                          s.colour, c);
 }
 
 void launch_gather(Sys &s, bool carried) {

@@ -31,6 +31,9 @@ struct StepDev {
     double lng_drift;           // alpha dt / hbar
     double lng_sig;             // sqrt(2 alpha kB T dt / hbar)
     double landau[NS][2];
+    // coloured spin sweep: the first half leaves the spins alone (they are advanced by the
+    // sweep over colour classes at the new positions)
+    int sts;
 };
 
 // Device control block of the self-consistent midpoint iteration.
@@ -164,6 +167,13 @@ struct Sys {
     double landau[NS][2] = {{0, 0}, {0, 0}};
     double last_dt = 1.0, last_T = 0.0;
 
+    // coloured Suzuki-Trotter spin sweep (sl_set_spin_sweep): colour of every atom (internal
+    // order, device) for the current step, and the colour count of the last step
+    int sts = 0;
+    int32_t *colour = nullptr;
+    int32_t last_colours = 0;
+    int64_t sweep_evaluations = 0;
+
     // self-consistent midpoint spin update (mid_iters = 0: predictor-corrector)
     int mid_iters = 0, aa_depth = 0;
     double mid_tol = 0.0, aa_reg = 1e-10;
@@ -195,6 +205,7 @@ constexpr int KERNELS_PER_STEP = 1 + 7 + 2 + 1 + 1 + 1;
 void launch_first_half(Sys &s);
 void launch_second_half(Sys &s);
 void launch_second_half_nospin(Sys &s);   // gather and final kick only (midpoint mode)
+void launch_sweep_rotate(Sys &s, int c);  // coloured sweep: half-step rotation of the spins of colour c
 // sl_midpoint.cu: the iteration of one step between the first half and the final evaluation;
 // returns the number of kernels it queued
 int launch_midpoint(Sys &s);

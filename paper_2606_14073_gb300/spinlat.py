@@ -25,7 +25,7 @@ EXPORTS = ["sl_default_options", "sl_create_system", "sl_step", "sl_energy_force
            "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak", "sl_descriptors_energies_noalloc",
            "sl_estimate_device_bytes", "sl_get_midpoint_evaluations", "sl_set_atom_fields", "sl_texture_map",
            "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal", "sl_selftest_carrier",
-           "sl_selftest_bounded_wait"]
+           "sl_selftest_bounded_wait", "sl_set_spin_sweep", "sl_get_sweep_colours"]
 KERNEL_GROUPS = ["first_half", "rebuild", "compact", "rad_fwd", "ang_fwd", "network", "backward", "second_half"]
 
 
@@ -77,6 +77,8 @@ def lib(path: str | None = None):
             L.sl_set_longitudinal.argtypes = [P, I32, D, P]
             L.sl_selftest_carrier.argtypes = [I32, D, P, P]
             L.sl_selftest_bounded_wait.argtypes = [I32]
+            L.sl_set_spin_sweep.argtypes = [P, I32]
+            L.sl_get_sweep_colours.argtypes = [P, P, P, P]
             L.sl_batch_graph_launches.argtypes = [P, P]
             L.sl_autotune.argtypes = [P, I32, P, P, P]
             L.sl_texture_map.argtypes = [P, I32, D, P, P, P, P]
@@ -100,7 +102,8 @@ def lib(path: str | None = None):
                       "sl_batch_step", "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak",
                       "sl_descriptors_energies_noalloc", "sl_get_midpoint_evaluations", "sl_set_atom_fields",
                       "sl_texture_map", "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal",
-                      "sl_selftest_carrier", "sl_selftest_bounded_wait"):
+                      "sl_selftest_carrier", "sl_selftest_bounded_wait", "sl_set_spin_sweep",
+                      "sl_get_sweep_colours"):
                 getattr(L, f).restype = C.c_int
             _lib = L
         return _lib
@@ -190,6 +193,18 @@ class System:
         if lan is not None and lan.shape != (4,):
             raise ValueError("landau must have shape (2, 2)")
         _check(lib().sl_set_longitudinal(self.handle, int(bool(enable)), float(alpha), _ptr(lan)))
+
+    def set_spin_sweep(self, enable: bool = True):
+        """Coloured Suzuki-Trotter spin sweep instead of the predictor-corrector spin update."""
+        _check(lib().sl_set_spin_sweep(self.handle, int(bool(enable))))
+
+    def sweep_colours(self, with_colours: bool = True):
+        """(colours [n] caller order or None, number of colours, evaluations so far) of the
+        last coloured step."""
+        nc, ev = C.c_int32(), C.c_int64()
+        col = np.zeros(self.n, np.int32) if with_colours else None
+        _check(lib().sl_get_sweep_colours(self.handle, _ptr(col), C.byref(nc), C.byref(ev)))
+        return col, nc.value, ev.value
 
     def texture(self, normal: int = 2, cell: float = 4.7):
         """(m [n_b][n_a][3], Q): coarse-grained film magnetisation and topological charge."""

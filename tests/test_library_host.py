@@ -109,3 +109,8 @@ def test_carrier_selftest_argument_checks():
 def test_bounded_wait_selftest_argument_checks():
     assert S.lib().sl_selftest_bounded_wait(0) == S.SL_EINVAL
     assert S.lib().sl_selftest_bounded_wait(1 << 23) == S.SL_EINVAL
+
+
+def test_spin_sweep_entry_points_need_a_system():
+    assert S.lib().sl_set_spin_sweep(None, 1) == S.SL_EINVAL
+    assert S.lib().sl_get_sweep_colours(None, None, None, None) == S.SL_EINVAL

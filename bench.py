@@ -300,6 +300,7 @@ def run_sweep(args):
     s.set_spin_sweep(True)
     s.step(args.warmup, DT, TEMP, FIELD)
     _, _, ev0 = s.sweep_colours(with_colours=False)
+    launches0 = s.info()["n_launches"]
     clocks = ClockSampler(0)
     clocks.start()
     torch.cuda.synchronize()
@@ -309,7 +310,7 @@ def run_sweep(args):
     secs = time.perf_counter() - t0
     clk = clocks.stop()
     _, nc, ev1 = s.sweep_colours(with_colours=False)
-    launches = s.info()["n_launches"]
+    launches = s.info()["n_launches"] - launches0
     s.destroy()
     value = wl.n * args.steps / secs
     line = _common_line(args, value, 1e3 * secs, args.steps, wl.name,

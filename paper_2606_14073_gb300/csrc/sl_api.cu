@@ -6,6 +6,7 @@
 // crossing the ABI are host arrays in caller atom order; internally atoms are
 // stored species-major and in Morton order of 7 A cells for locality.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstddef>
@@ -16,6 +17,7 @@
 #include <new>
 #include <tuple>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -235,6 +237,23 @@ static double4 *stage_buffer(const sl::Sys &s) {
     return s.h_stage;
 }
 
+// fn(lo, hi) over [0, n) in contiguous chunks on up to 8 host threads (one thread for small n);
+// every index is handled by exactly one thread, so results do not depend on the split.
+template <typename F>
+static void parallel_chunks(int64_t n, F fn) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int64_t nt = n < 65536 ? 1 : std::min<int64_t>(std::min<unsigned>(hw, 8u), n / 32768);
+    if (nt <= 1) {
+        fn((int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve((size_t)nt - 1);
+    for (int64_t t = 1; t < nt; ++t) th.emplace_back(fn, n * t / nt, n * (t + 1) / nt);
+    fn((int64_t)0, n / nt);
+    for (auto &x : th) x.join();
+}
+
 // host (caller order) -> device (internal order), through the pinned staging buffer
 int upload_vec(sl::Sys &s, double4 *dst, const double *src, bool normalise) {
     double4 *h = stage_buffer(s);
@@ -242,20 +261,27 @@ int upload_vec(sl::Sys &s, double4 *dst, const double *src, bool normalise) {
     // the buffer may still be read by an earlier copy on this stream
     CK(cudaStreamSynchronize(s.stream));
     const int32_t *orig = s.h_orig.data();
-    for (int64_t i = 0; i < s.n; ++i) {
-        const double *p = src + 3 * (int64_t)orig[i];
-        double x = p[0], y = p[1], z = p[2];
-        if (normalise) {
-            // spins that are unit to rounding are kept bit for bit (exact resume)
-            const double n2 = x * x + y * y + z * z;
-            if (!(n2 > 0)) return fail(SL_EINVAL, "zero spin vector");
-            if (std::fabs(n2 - 1.0) > 1e-13) {
-                const double nn = std::sqrt(n2);
-                x /= nn; y /= nn; z /= nn;
+    std::atomic<int> zero{0};
+    parallel_chunks(s.n, [&](int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) {
+            const double *p = src + 3 * (int64_t)orig[i];
+            double x = p[0], y = p[1], z = p[2];
+            if (normalise) {
+                // spins that are unit to rounding are kept bit for bit (exact resume)
+                const double n2 = x * x + y * y + z * z;
+                if (!(n2 > 0)) {
+                    zero.store(1);
+                    continue;
+                }
+                if (std::fabs(n2 - 1.0) > 1e-13) {
+                    const double nn = std::sqrt(n2);
+                    x /= nn; y /= nn; z /= nn;
+                }
             }
+            h[i] = make_double4(x, y, z, 0.0);
         }
-        h[i] = make_double4(x, y, z, 0.0);
-    }
+    });
+    if (zero.load()) return fail(SL_EINVAL, "zero spin vector");
     // ordered on the system's stream; synchronised before the staging buffer is reused
     CK(cudaMemcpyAsync(dst, h, sizeof(double4) * s.n, cudaMemcpyHostToDevice, s.stream));
     CK(cudaStreamSynchronize(s.stream));
@@ -268,10 +294,12 @@ int download_vec(const sl::Sys &s, const double4 *src, double *dst) {
     CK(cudaMemcpyAsync(h, src, sizeof(double4) * s.n, cudaMemcpyDeviceToHost, s.stream));
     CK(cudaStreamSynchronize(s.stream));
     const int32_t *orig = s.h_orig.data();
-    for (int64_t i = 0; i < s.n; ++i) {
-        double *p = dst + 3 * (int64_t)orig[i];
-        p[0] = h[i].x; p[1] = h[i].y; p[2] = h[i].z;
-    }
+    parallel_chunks(s.n, [&](int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) {
+            double *p = dst + 3 * (int64_t)orig[i];
+            p[0] = h[i].x; p[1] = h[i].y; p[2] = h[i].z;
+        }
+    });
     return SL_OK;
 }
 

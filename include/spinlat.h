@@ -296,11 +296,11 @@ void sl_batch_destroy(sl_batch *b);
 
 /* ---------------------------------------------------------------- no device allocation
  * Per-atom descriptors and network energies of a small system, for callers that
- * cannot allocate device memory: code that runs while its host framework captures
- * a CUDA graph (allocation is not allowed there), plugins of engines that hand all
- * device memory to their own pool, and real-time loops that cannot take the
- * device-wide synchronisation an allocation may imply.  The paper has no
- * counterpart; this is a service of this library.
+ * cannot allocate device memory: plugins of simulation engines that hand every
+ * device byte to their own pool allocator (a cudaMalloc behind the pool's back would
+ * break its accounting or fail against its reservation), and real-time loops that
+ * cannot take the device-wide synchronisation cudaMalloc and cudaFree may imply.
+ * The paper has no counterpart; this is a service of this library.
  *   positions4, spins4  DEVICE arrays [n][4] of double (x, y, z, unused)
  *   species             DEVICE array [n] of int32
  *   q                   DEVICE output [n][66] (unscaled descriptors) or NULL
@@ -314,9 +314,10 @@ void sl_batch_destroy(sl_batch *b);
  * word) is one fixed array compiled into the library, resident on every GPU that
  * loads it until the process exits.  No call allocates device memory; n above
  * 2048 atoms returns SL_EINVAL, more than 160 neighbours inside rc_rad returns
- * SL_ENBR_OVERFLOW.  The first call on a device looks up the array's device
- * address (and may load the library's device code); make that first call before
- * any stream capture.  Every call uses the same array, so calls whose work
+ * SL_ENBR_OVERFLOW, and a species value outside [0, n_species) (checked on the
+ * device, where the array lives) returns SL_EINVAL.  The first call on a device
+ * looks up the array's device address (and may load the library's device code);
+ * make that first call before any stream capture.  Every call uses the same array, so calls whose work
  * overlaps on the GPU (other streams, other host threads) race: serialise them. */
 int sl_descriptors_energies_noalloc(const double *positions4, const double *spins4, const int32_t *species,
                                     int64_t n, const double box[3], const int32_t periodic[3],

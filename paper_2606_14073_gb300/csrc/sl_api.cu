@@ -247,10 +247,17 @@ static void parallel_chunks(int64_t n, F fn) {
         fn((int64_t)0, n);
         return;
     }
+    // a thread that cannot be created (std::system_error, or bad_alloc for its vector slot)
+    // leaves its chunk, and every later one, to the calling thread: no exception crosses the ABI
     std::vector<std::thread> th;
-    th.reserve((size_t)nt - 1);
-    for (int64_t t = 1; t < nt; ++t) th.emplace_back(fn, n * t / nt, n * (t + 1) / nt);
+    int64_t started = 1;   // chunks [1, started) run on their own threads
+    try {
+        th.reserve((size_t)nt - 1);
+        for (; started < nt; ++started) th.emplace_back(fn, n * started / nt, n * (started + 1) / nt);
+    } catch (...) {
+    }
     fn((int64_t)0, n / nt);
+    for (int64_t t = started; t < nt; ++t) fn(n * t / nt, n * (t + 1) / nt);
     for (auto &x : th) x.join();
 }
 
@@ -1441,6 +1448,7 @@ int sl_descriptors_energies_noalloc(const double *positions4, const double *spin
         cudaError_t e = cudaGetLastError();
         return fail(SL_ECUDA, "no-allocation evaluation failed: %s", cudaGetErrorString(e));
     }
+    if (st & ST_BAD_SPECIES) return fail(SL_EINVAL, "a species value outside [0, %d)", NS);
     if (st & ST_NBR_OVERFLOW) return fail(SL_ENBR_OVERFLOW, "more than 160 neighbours inside rc_rad");
     return SL_OK;
 }

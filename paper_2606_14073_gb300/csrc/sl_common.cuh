@@ -326,5 +326,6 @@ constexpr int ST_NBR_OVERFLOW = 1;
 constexpr int ST_NONFINITE = 2;
 constexpr int ST_TIMEOUT = 4;
 constexpr int ST_MID_RANGE = 8;     // midpoint configuration beyond the neighbour-list skin
+constexpr int ST_BAD_SPECIES = 16;  // a species value outside [0, NS) (no-allocation entry point)
 
 }  // namespace sl

@@ -257,6 +257,14 @@ __global__ void __launch_bounds__(128) k_eval_noalloc(const __grid_constant__ Ne
     double *q = reinterpret_cast<double *>(scratch + OFF_Q);
     double *bsum = reinterpret_cast<double *>(scratch + OFF_B);
     int *status = reinterpret_cast<int *>(scratch + OFF_STATUS);
+    // species index the per-species coefficient tables: a value outside [0, NS) in this
+    // atom or in any atom it would pair with is reported and the atom is skipped (the
+    // host then rejects the whole call)
+    const int ti = species[i];
+    if (ti < 0 || ti >= NS) {
+        atomicOr(status, ST_BAD_SPECIES);
+        return;
+    }
     // brute-force neighbours inside rc_rad, inserted in (segment, index) order
     // straight into this atom's scratch column (slot-major, stride n)
     const double4 pi = pos[i];
@@ -269,8 +277,13 @@ __global__ void __launch_bounds__(128) k_eval_noalloc(const __grid_constant__ Ne
         minimg(box, dx, dy, dz);
         const double d2 = dx * dx + dy * dy + dz * dz;
         if (!(d2 < P.rc_r2)) continue;
+        const int tj = species[j];
+        if (tj < 0 || tj >= NS) {
+            atomicOr(status, ST_BAD_SPECIES);
+            return;
+        }
         if (m >= MAX_NBR) { overflow = true; continue; }
-        const int key = ((d2 < P.rc_a2 ? 0 : 2) + species[j]) * MAX_ATOMS + j;
+        const int key = ((d2 < P.rc_a2 ? 0 : 2) + tj) * MAX_ATOMS + j;
         int v = m - 1;
         while (v >= 0) {
             const int jv = nbr[(int64_t)v * n + i];
@@ -297,11 +310,12 @@ __global__ void __launch_bounds__(128) k_eval_noalloc(const __grid_constant__ Ne
     }
     for (int t = 1; t < 4; ++t) ends[t] = max(ends[t], ends[t - 1]);
     seg[i] = make_int4(ends[0], ends[1], ends[2], ends[3]);
-    // descriptor through the same per-atom code as k_fwd
+    // descriptor by fwd_atom (one thread per atom, harmonic form of the angular channels;
+    // the step's kernels in sl_eval2.cu compute the same sums with another work split)
     EvalArgs<double> a;
     a.pos = pos; a.spin = spin; a.nbr = nbr; a.seg = seg; a.n = n; a.n_fe = 0; a.box = box;
     a.q = q; a.bsum = bsum;
-    if (species[i] == 0) fwd_atom<double, 0>(P, a, i);
+    if (ti == 0) fwd_atom<double, 0>(P, a, i);
     else fwd_atom<double, 1>(P, a, i);
     // network energy E_i = sum_h w1_h tanh(sum_v W0_hv s_v q_v - b0_h) - b1
     double x[DIM];

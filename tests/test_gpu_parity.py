@@ -4,7 +4,8 @@ Tolerances:
   FP64 mode   |gpu - oracle| <= 1e-10 * max|oracle| per output array (E, F, H, W, q);
               trajectories: 1e-9 after 100 steps (chaotic growth of the 1e-16
               rounding differences over 100 fs stays far below that).
-  mixed mode  RMSE(F) <= 1e-3 eV/A and RMSE(H) <= 1e-3 eV against the oracle.
+  mixed mode  RMSE(F) <= 1e-3 eV/A and RMSE(H) <= 1e-3 eV against the oracle, every atom's
+              |dF_i| <= 2e-3 eV/A and |dH_i| <= 2e-3 eV, virial within 1e-4 of max |W|.
   neighbours  bit-exact sets.
 Sizes span several thread blocks and end in ragged tails (512, 1728, 1725, slab).
 """
@@ -17,6 +18,11 @@ from paper_2606_14073_gb300 import nep_params, spinlat as S, workloads as W
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
+# mixed precision (FP32 descriptors and backward, FP16 hi/lo network): besides the RMSE bars,
+# every atom's force and field error vector is bounded (eV/A and eV), and the virial relative
+# to its largest entry
+MIXED_ATOM_TOL = 2e-3
+MIXED_VIRIAL_TOL = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -137,7 +143,13 @@ def test_mixed_precision_force_field_error(params, model, name):
     rmse_f = np.sqrt(((r["F"] - ref["F"]) ** 2).mean())
     rmse_h = np.sqrt(((r["H"] - ref["H"]) ** 2).mean())
     assert rmse_f <= 1e-3 and rmse_h <= 1e-3, (rmse_f, rmse_h)
+    # no single atom far off: per-atom error vectors within MIXED_ATOM_TOL
+    err_f = np.linalg.norm(r["F"] - ref["F"], axis=1).max()
+    err_h = np.linalg.norm(r["H"] - ref["H"], axis=1).max()
+    assert err_f <= MIXED_ATOM_TOL and err_h <= MIXED_ATOM_TOL, (err_f, err_h)
     assert abs(r["E"] - ref["E"]) / wl.n <= 1e-4
+    # virial (eV) within MIXED_VIRIAL_TOL of the largest oracle entry
+    assert np.abs(r["W"] - ref["W"]).max() <= MIXED_VIRIAL_TOL * np.abs(ref["W"]).max(), (r["W"], ref["W"])
     s.destroy()
 
 

@@ -39,8 +39,16 @@ METRIC = "atom-steps/s on 1 GB300, mixed vs FP64 at stated force error; p99 repl
 UNIT = "atom-steps/s"
 WORKLOAD = "fege_b20_48c_884736"
 DT, TEMP, FIELD = 1.0, 300.0, (0.0, 0.0, 0.0)
-SM_COUNT_GB300 = 152
-FP32_LANES_PER_SM = 128
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM on sm_100-class GPUs
+
+
+def fp32_peak_tflops(device: int, sm_max_mhz: float | None):
+    """FP32 FMA peak of the device: SM count from the device attribute x 128 lanes x 2 FLOP x the
+    maximum SM clock (nvidia-smi's clocks.max.sm seen during the run, else MEASURED_PEAKS.json)."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = sm_max_mhz or float((measured_peaks() or {}).get("sm_max_mhz", 2070.0))
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, sms, mhz
 
 
 def env_rank():
@@ -49,7 +57,7 @@ def env_rank():
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples (every 50 ms) during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -65,7 +73,7 @@ class ClockSampler:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -267,6 +275,21 @@ def run_e2e(args, sysm, wl, world, barrier, dist, torch, st):
                    "from their start state", "_out": out}
 
     return e2e
+
+
+def forced_rebuild_ms(sysm, repeats=3):
+    """Device time of one neighbour-list rebuild of the system's current state: the state is
+    set again with list reference positions 10 A away, so the rebuild group of the next profiled
+    step runs; the state is restored afterwards (median of `repeats`)."""
+    st = sysm.get_state()
+    times = []
+    for _ in range(repeats):
+        sysm.set_state(st["positions"], st["velocities"], st["spins"], st["forces"], st["fields"], st["step"],
+                       ref_positions=st["positions"] + 10.0)
+        times.append(sysm.step_profiled(1, DT, TEMP, FIELD)["rebuild"])
+    sysm.set_state(st["positions"], st["velocities"], st["spins"], st["forces"], st["fields"], st["step"],
+                   ref_positions=st["ref_positions"])
+    return float(statistics.median(times))
 
 
 def run_serving(args, params, replica_offset=0):
@@ -740,13 +763,15 @@ def run_ours(args):
     dom = max(("rad_fwd", "ang_fwd", "network", "backward"), key=lambda k: prof[k])
     launch_ms = prof[dom] / args.profile_steps
     achieved = fl[dom] * wl.n / (launch_ms * 1e-3) / 1e12
-    peak_derived = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    peak_derived, n_sms, peak_mhz = fp32_peak_tflops(local, (clk or {}).get("sm_max_mhz"))
     fma32, _ = S.sl_measure_fma_peak(S.SL_PREC_MIXED)
     fma64, _ = S.sl_measure_fma_peak(S.SL_PREC_FP64)
     roofline = {"bound": "alu", "kernel": {"rad_fwd": "k_crad<float>", "ang_fwd": "k_ang_fwd<float>",
                                            "network": "k_mlp_tc", "backward": "k_bwd<float>"}[dom],
                 "achieved": achieved, "peak": peak_derived, "unit": "TFLOP/s", "frac": achieved / peak_derived,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FP32 FMA pipe)",
+                "peak_source": (f"derived: {n_sms} SMs (device attribute) x 128 FP32 lanes x 2 FLOP x {peak_mhz:.0f} MHz "
+                                f"(maximum SM clock), FP32 FMA pipe; the FMA microbenchmark measured "
+                                f"{fma32 / 1e12:.1f} TFLOP/s"),
                 "peak_measured_fp32_fma_tflops": fma32 / 1e12, "peak_measured_fp64_fma_tflops": fma64 / 1e12,
                 "algorithmic_flop_per_atom": fl[dom], "mean_neighbours_6A": n_r, "mean_neighbours_4A": n_a,
                 "neighbours_counted_at": "the state the profiled steps start from",
@@ -760,6 +785,31 @@ def run_ours(args):
         out = e2e.pop("_out")
         e2e["replay_bit_identical"] = bool(all(np.array_equal(out[k], end_state[k])
                                                for k in ("positions", "velocities", "spins")))
+
+    # steady state: a longer window at the run's own pace, neighbour-list rebuilds included (the
+    # K-step window above is short enough to hold none); then the cost of one forced rebuild
+    steady = None
+    if args.steady_steps > 0:
+        info_s0 = sysm.info()
+        clocks_s = ClockSampler(local)
+        clocks_s.start()
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sysm.step(args.steady_steps, DT, TEMP, FIELD)
+        e1.record(stream)
+        e1.synchronize()
+        ms_s = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+        clk_s = clocks_s.stop()
+        builds_s = sysm.info()["n_builds"] - info_s0["n_builds"]
+        build_ms = forced_rebuild_ms(sysm)
+        steady = {"value": whole_job_rate(wl.n, args.steady_steps, world, ms_s), "unit": UNIT,
+                  "steps": args.steady_steps, "ms_per_step": ms_s / args.steady_steps,
+                  "neighbour_builds": builds_s, "ms_per_build": build_ms,
+                  "rebuild_share": (builds_s * build_ms / ms_s) if build_ms is not None else None,
+                  "clocks": clk_s,
+                  "window": "the steps after the timed K steps and their end-to-end replay, graphs of "
+                            f"{args.graph_steps} steps, the rebuild check on the device every step"}
 
     # continuous-batching serving run: Poisson sweep requests, p50/p99 time to completion
     serving = None
@@ -801,7 +851,8 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (~10 GB working set)", "parallelism": f"replicas x{world}"},
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "neighbour_builds": {"timed_region": builds_timed, "profiled_steps": builds_prof,
-                                     "ms_per_build": ms_per_build},
+                                     "ms_per_build": (steady or {}).get("ms_per_build", ms_per_build)},
+                "steady_state": steady,
                 "kernel_share": shares, "kernel_ms_per_step": per_step,
                 "kernel_roofline": kernel_rooflines(fl, prof, args.profile_steps, wl.n, peak_derived),
                 "fp64": fp64, "mixed_error_vs_fp64": err, "serving": serving, "cpu_baseline": cpu,
@@ -822,7 +873,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--graph-steps", type=int, default=10)
     ap.add_argument("--profile-steps", type=int, default=10)
-    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=20)
+    ap.add_argument("--steady-steps", type=int, default=200,
+                    help="cube: steps of the steady-state window with list rebuilds (0: skip)")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")

@@ -542,11 +542,11 @@ int sl_create_system(const double *positions, const double *spins, const double 
         (rc = dalloc(&s.posref, N)) || (rc = dalloc(&s.posf, N)) || (rc = dalloc(&s.spinf, N)) ||
         (rc = dalloc(&s.species, N)) || (rc = dalloc(&s.orig, N)) || (rc = dalloc(&s.inv, N)) ||
         (rc = dalloc(&s.nbr, N * s.cap)) || (rc = dalloc(&s.rev, N * s.cap)) ||
-        (rc = dalloc(&s.nbr_orig, N * s.cap)) || (rc = dalloc(&s.cells.posf, N)) || (rc = dalloc(&s.cells.key, N)) || (rc = dalloc(&s.seg, N)) ||
+        (rc = dalloc(&s.nbr_orig, N * sl::nbr_orig_stride(s.cap))) || (rc = dalloc(&s.cells.posf, N)) || (rc = dalloc(&s.cells.key, N)) || (rc = dalloc(&s.seg, N)) ||
         (rc = dalloc(&s.cells.count, (size_t)s.cells.ncell)) || (rc = dalloc(&s.cells.start, (size_t)s.cells.ncell + 1)) ||
         (rc = dalloc(&s.cells.fill, (size_t)s.cells.ncell)) || (rc = dalloc(&s.cells.atoms, N)) ||
         (rc = dalloc(&s.cells.of, N)) || (rc = dalloc((char **)&s.q, R * DIM * N)) ||
-        (rc = dalloc((char **)&s.bsum, R * NB * N)) || (rc = dalloc((char **)&s.fp, R * DIM * N)) ||
+        (rc = dalloc((char **)&s.bsum, R * NBREC * N)) || (rc = dalloc((char **)&s.fp, R * DIM * N)) ||
         (rc = dalloc((char **)&s.ei, R * N)) || (rc = dalloc((char **)&s.pairs, R * 8 * N * s.cap)) ||
         (rc = dalloc(&s.clj, N * (size_t)(s.cap + s.cap_ang))) || (rc = dalloc(&s.cls, N * (size_t)(s.cap + s.cap_ang))) ||
         (rc = dalloc(&s.cnt, N)) || (rc = dalloc(&s.cmask, N * (size_t)((s.cap + 31) / 32))) || (rc = dalloc((char **)&s.fown, R * 4 * N)) ||
@@ -1193,10 +1193,10 @@ int64_t sl_estimate_device_bytes(int64_t n, const sl_options *opt_in) {
     const int64_t cap = opt.nbr_cap_rad, ca = opt.nbr_cap_ang;
     int64_t per = 7 * 32 + 2 * 16                      // state (double4) and FP32 copies
                   + 3 * 4 + 4 + 16 + 16 + 4            // species, caller index maps, list segments, cell copies
-                  + 3 * 4 * cap                        // candidate lists (index and caller index), reverse slots
+                  + 5 * cap + 4 * sl::nbr_orig_stride((int)cap)   // candidate lists, reverse slots (1 byte), caller-index rows
                   + 6 * (ca + cap) + 16                // compact rows, counts
                   + 4 * ((cap + 31) / 32)              // in-cutoff slot mask
-                  + R * (2 * sl::DIM + sl::NB + 1 + 9) // q, Fp, angular sums, E_i, virial parts
+                  + R * (2 * sl::DIM + sl::NBREC + 1 + 9) // q, Fp, angular sums, E_i, virial parts
                   + R * 8 * cap + 2 * R * 4            // pair records, per-atom sums
                   + 2 * 32 + 5 * 32 + 3 * 4;           // evaluation outputs, snapshot, cell arrays
     if (opt.midpoint_iters > 0)                        // midpoint positions and spins, iterate, image, rings

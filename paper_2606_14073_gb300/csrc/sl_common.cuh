@@ -18,6 +18,11 @@ constexpr int NH = 30;    // hidden units
 constexpr int NLM = 24;   // real solid harmonics, l = 1..4
 constexpr int DIM = 66;   // descriptor length
 constexpr int NB = 2 * NCH * NLM;   // 240 angular sums kept for the backward pass
+// The angular sums are stored atom-major as one 12-entry record per harmonic lm:
+// (B_0lm, BS_0lm, B_1lm, BS_1lm, ..., B_4lm, BS_4lm, 0, 0), 48 bytes in FP32 (three
+// 16-byte words), the layout the backward kernel keeps its adjoints in.
+constexpr int BREC = 12;
+constexpr int NBREC = NLM * BREC;   // 288 stored entries per atom
 
 // coefficient groups
 constexpr int G_R = 0, G_A = 1, G_EX = 2, G_DMI = 3, G_ANI = 4, G_SIA = 5;

@@ -207,7 +207,7 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
     }
     const int64_t N = a.n;
     const int32_t *__restrict__ nbr = a.nbr;
-    const int32_t *__restrict__ rev = a.rev;
+    const uint8_t *__restrict__ rev = a.rev;
     const v4<R> *__restrict__ pos = a.pos;
     const v4<R> *__restrict__ spin = a.spin;
 
@@ -488,13 +488,17 @@ __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<
         const int lm = lm_of(ql, m);
         const int l = l_of_lm(lm) - 1;
         const R kap = kappa_of_lm<R>(lm);
+        if (valid) {   // the harmonic's record: (B_n, BS_n) for n = 0..4, two zeros
+            v4<R> *rec = reinterpret_cast<v4<R> *>(a.bsum + ((int64_t)i * NLM + lm) * BREC);
+            v4<R> w0, w1, w2;
+            w0.x = BB[m][0].x; w0.y = BB[m][0].y; w0.z = BB[m][1].x; w0.w = BB[m][1].y;
+            w1.x = BB[m][2].x; w1.y = BB[m][2].y; w1.z = BB[m][3].x; w1.w = BB[m][3].y;
+            w2.x = BB[m][4].x; w2.y = BB[m][4].y; w2.z = R(0); w2.w = R(0);
+            rec[0] = w0; rec[1] = w1; rec[2] = w2;
+        }
 #pragma unroll
         for (int n = 0; n < NCH; ++n) {
             const R Bv = BB[m][n].x, BSv = BB[m][n].y;
-            if (valid) {
-                a.bsum[(int64_t)(n * NLM + lm) * N + i] = Bv;
-                a.bsum[(int64_t)(NCH * NLM + n * NLM + lm) * N + i] = BSv;
-            }
             const R ka = kap * Bv * Bv, ks = kap * BSv * BSv;
             // l is 1..4 depending on the lane: add into the matching slot
 #pragma unroll
@@ -573,7 +577,7 @@ __device__ __forceinline__ void bwd_harm(const R *__restrict__ bb, R ux, R uy, R
                                          const R dg[NCH], R &accu, R &avx, R &avy, R &avz, R &cj) {
     R p, gx, gy, gz;
     harm_one<R, LM>(ux, uy, uz, p, gx, gy, gz);
-    const v4<R> *rec = reinterpret_cast<const v4<R> *>(bb + 12 * LM);
+    const v4<R> *rec = reinterpret_cast<const v4<R> *>(bb + BREC * LM);
     const v4<R> r0 = rec[0], r1 = rec[1], r2 = rec[2];
     const v2<R> Bp[NCH] = {pair2<R>(r0.x, r0.y), pair2<R>(r0.z, r0.w), pair2<R>(r1.x, r1.y), pair2<R>(r1.z, r1.w),
                            pair2<R>(r2.x, r2.y)};   // (dE/dB_n, dE/dBS_n)
@@ -743,24 +747,20 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 2 : 1) k_bwd(const __gri
         const int ti = i < a.n_fe ? 0 : 1;
         const v4<R> pi = a.pos[i], si = a.spin[i];
         const int4 c = a.cnt[i];
-        // angular adjoints of this lane's harmonics lm = ql + 4 m into shared memory
+        // angular adjoints of this lane's harmonics lm = ql + 4 m from their records (three
+        // 16-byte loads each), the gradient entries straight from global memory
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
             const int lm = lm_of(ql, m);
             const int l = l_of_lm(lm);
             const R k2 = R(2) * kappa_of_lm<R>(lm);
-            R bb[10];
-#pragma unroll
-            for (int n = 0; n < NCH; ++n) {
-                bb[n] = k2 * a.fp[(int64_t)(Q_A + n * 4 + l - 1) * N + i] * a.bsum[(int64_t)(n * NLM + lm) * N + i];
-                bb[NCH + n] = k2 * a.fp[(int64_t)(Q_SA + n * 4 + l - 1) * N + i] *
-                              a.bsum[(int64_t)(NCH * NLM + n * NLM + lm) * N + i];
-            }
-            v4<R> *d = reinterpret_cast<v4<R> *>(sm + 12 * lm);
-            v4<R> w0, w1, w2;
-            w0.x = bb[0]; w0.y = bb[NCH]; w0.z = bb[1]; w0.w = bb[NCH + 1];
-            w1.x = bb[2]; w1.y = bb[NCH + 2]; w1.z = bb[3]; w1.w = bb[NCH + 3];
-            w2.x = bb[4]; w2.y = bb[NCH + 4]; w2.z = R(0); w2.w = R(0);
+            const v4<R> *src = reinterpret_cast<const v4<R> *>(a.bsum + ((int64_t)i * NLM + lm) * BREC);
+            v4<R> w0 = src[0], w1 = src[1], w2 = src[2];
+            const R *fa = a.fp + (int64_t)(Q_A + l - 1) * N + i, *fs = a.fp + (int64_t)(Q_SA + l - 1) * N + i;
+            w0.x *= k2 * fa[0]; w0.y *= k2 * fs[0]; w0.z *= k2 * fa[4 * N]; w0.w *= k2 * fs[4 * N];
+            w1.x *= k2 * fa[8 * N]; w1.y *= k2 * fs[8 * N]; w1.z *= k2 * fa[12 * N]; w1.w *= k2 * fs[12 * N];
+            w2.x *= k2 * fa[16 * N]; w2.y *= k2 * fs[16 * N]; w2.z = R(0); w2.w = R(0);
+            v4<R> *d = reinterpret_cast<v4<R> *>(sm + BREC * lm);
             d[0] = w0; d[1] = w1; d[2] = w2;
         }
         R FR[NCH], FX[4][NCH];
@@ -772,12 +772,12 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 2 : 1) k_bwd(const __gri
             FX[2][n] = a.fp[(int64_t)(Q_ANI + n) * N + i];
             FX[3][n] = a.fp[(int64_t)(Q_SIA + n) * N + i];
         }
-        if (ti == 0) bwd_coeffs<R, 0>(P, FR, FX, ql, sm + BW_C);
-        else bwd_coeffs<R, 1>(P, FR, FX, ql, sm + BW_C);
         if (ql == 0) {   // onsite term dE_i/dS_i = 2 Fp_O S_i, counted once per atom
             const R fo = R(2) * a.fp[(int64_t)Q_O * N + i];
             acc.hx = fo * si.x; acc.hy = fo * si.y; acc.hz = fo * si.z;
         }
+        if (ti == 0) bwd_coeffs<R, 0>(P, FR, FX, ql, sm + BW_C);
+        else bwd_coeffs<R, 1>(P, FR, FX, ql, sm + BW_C);
         __syncwarp(0xfu << (quad * 4));
         const int ca = a.cap_ang;
         bwd_rows<R, true>(P, a, i, ti, ql, c.y, c.x, pi, si, sm, acc);

@@ -21,7 +21,8 @@ struct PairRec {
 template <typename R>
 struct Eval2Args {
     const v4<R> *pos, *spin;
-    const int32_t *nbr, *rev;
+    const int32_t *nbr;
+    const uint8_t *rev;   // [cap][n] slot of i in the list of nbr[s][i]
     const int4 *seg;
     int64_t n, n_fe;
     BoxDev<R> box;

@@ -102,13 +102,14 @@ struct Sys {
 
     // neighbour lists: nbr and rev slot-major [slot][atom]; nbr_orig (caller index of
     // each entry, searched by the reverse-slot build) atom-major [atom][slot]
-    int32_t *nbr = nullptr, *rev = nullptr, *nbr_orig = nullptr;
+    int32_t *nbr = nullptr, *nbr_orig = nullptr;
+    uint8_t *rev = nullptr;    // [cap][n] reverse slots (a slot index fits one byte: cap <= 256)
     int4 *seg = nullptr;       // per atom: ends of (ang t0, ang t1, rad t0, rad t1)
     Cells cells;
 
     // evaluation buffers (element type = compute precision)
     void *q = nullptr;         // [DIM][n]
-    void *bsum = nullptr;      // [NB][n]
+    void *bsum = nullptr;      // [n][NLM][BREC] angular-sum records
     void *fp = nullptr;        // [DIM][n]
     void *ei = nullptr;        // [n]
     void *pairs = nullptr;     // [cap][n] pair records (see sl_eval2.cuh)
@@ -188,6 +189,9 @@ struct Sys {
 };
 
 // launchers (sl_neighbors.cu)
+// row stride of the atom-major caller-index copy of the lists: cap rounded up to a multiple
+// of 4 entries, so every row starts on a 16-byte boundary
+inline int nbr_orig_stride(int cap) { return (cap + 3) & ~3; }
 void nbr_setup(Sys &s);
 void launch_rebuild(Sys &s, bool conditional);
 // sl_nep.cu

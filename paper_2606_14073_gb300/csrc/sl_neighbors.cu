@@ -107,9 +107,9 @@ struct ListArgs {
     const int *cell_start, *cell_atoms, *cell_of;
     const float4 *cposf;      // cell-ordered FP32 positions
     const uint32_t *ckey;     // cell-ordered (species << 30 | caller index)
-    int32_t *nbr_orig;        // [n][cap] caller index of each list entry (atom-major)
+    int32_t *nbr_orig;        // [n][capr] caller index of each list entry (atom-major rows of capr)
     int64_t n;
-    int cap, cap_ang;
+    int cap, cap_ang, capr;
     double cut_r2, cut_a2;
     float cut_r2f_lo, cut_r2f_hi, cut_a2f_lo, cut_a2f_hi;   // FP32 pre-test band
     BoxDev<double> bd;
@@ -122,22 +122,18 @@ struct ListArgs {
 };
 
 struct RevArgs {
-    const double4 *pos;
     const int32_t *species, *orig;
-    const int32_t *nbr, *nbr_orig;   // nbr_orig atom-major [n][cap]
+    const int32_t *nbr, *nbr_orig;   // nbr_orig atom-major [n][capr], capr a multiple of 4
     const int4 *seg;
-    int cap;
+    int cap, capr;
     int64_t n;
-    double cut_a2;
-    BoxDev<double> bd;
-    int per[3];
-    int32_t *rev;
+    uint8_t *rev;         // [cap][n] reverse slots (cap <= 256)
     int *status;
     const int *flag;
 };
 
 
-// Warp per atom.  Lanes take the candidates of each stencil cell 32 at a time;
+// Warp per atom.  Lanes take the candidates of the stencil cells 32 at a time;
 // pairs inside the list cutoff are appended to a per-warp shared-memory buffer
 // (ballot/popc, so the append order is the scan order), the buffer is sorted
 // by (segment, caller index) with a warp bitonic sort, and written out.
@@ -195,6 +191,7 @@ constexpr int SORT_MAX = 256;
 __global__ void __launch_bounds__(LB_WARPS * 32) k_build_lists_warp(ListArgs a) {
     if (a.flag && *a.flag == 0) return;
     __shared__ uint32_t skey[LB_WARPS][SORT_MAX];
+    __shared__ int soff[LB_WARPS][32], sp0[LB_WARPS][32];   // stencil cells of the warp's atom
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t *key = skey[w];
     const unsigned lt = (1u << lane) - 1u;
@@ -211,52 +208,92 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_build_lists_warp(ListArgs a) 
             else { lo[d] = max(ci[d] - 1, 0); hi[d] = min(ci[d] + 1, a.g.nc[d] - 1); }
         }
         const uint32_t self = (uint32_t)a.orig[i];
+        // The stencil cells' candidates are walked as one flattened sequence in the cell order
+        // below (z, y, x), 32 per round, with the next round's keys and positions in flight
+        // while the current round is tested.  Lane c < nst holds cell c's first cell-ordered
+        // position and its exclusive offset in the sequence.
+        const int sx = hi[0] - lo[0] + 1, sy = hi[1] - lo[1] + 1, sz = hi[2] - lo[2] + 1;
+        const int nst = sx * sy * sz;   // at most 27 cells
+        int my_p0 = 0, my_len = 0;
+        if (lane < nst) {
+            const int x = lo[0] + lane % sx, y = lo[1] + (lane / sx) % sy, z = lo[2] + lane / (sx * sy);
+            const int c = (wrap_cell(z, a.g.nc[2]) * a.g.nc[1] + wrap_cell(y, a.g.nc[1])) * a.g.nc[0] +
+                          wrap_cell(x, a.g.nc[0]);
+            my_p0 = a.cell_start[c];
+            my_len = a.cell_start[c + 1] - my_p0;
+        }
+        int incl = my_len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int *off = soff[w], *p0 = sp0[w];
+        if (lane < nst) {
+            off[lane] = incl - my_len;
+            p0[lane] = my_p0;
+        }
+        __syncwarp();
+        // cell-ordered position of candidate f of the sequence (the last cell whose offset is
+        // <= f holds it; empty cells share the offset of the cell after them)
+        auto position_of = [&](int f) {
+            int l = 0, h = nst - 1;
+            while (l < h) {
+                const int mid = (l + h + 1) >> 1;
+                if (off[mid] <= f) l = mid;
+                else h = mid - 1;
+            }
+            return p0[l] + (f - off[l]);
+        };
+        int pn = -1;
+        uint32_t kn = 0;
+        float4 fn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane < total) {
+            pn = position_of(lane);
+            kn = a.ckey[pn];
+            fn = a.cposf[pn];
+        }
         int m = 0, nang = 0;
-        for (int z = lo[2]; z <= hi[2]; ++z)
-            for (int y = lo[1]; y <= hi[1]; ++y)
-                for (int x = lo[0]; x <= hi[0]; ++x) {
-                    const int wx = wrap_cell(x, a.g.nc[0]);
-                    const int wy = wrap_cell(y, a.g.nc[1]);
-                    const int wz = wrap_cell(z, a.g.nc[2]);
-                    const int c = (wz * a.g.nc[1] + wy) * a.g.nc[0] + wx;
-                    const int p0 = a.cell_start[c], p1 = a.cell_start[c + 1];
-                    for (int base = p0; base < p1; base += 32) {
-                        const int p = base + lane;
-                        bool in_r = false, in_a = false;
-                        uint32_t k = 0;
-                        if (p < p1) {
-                            k = a.ckey[p];
-                            if ((k & 0x3FFFFFFFu) != self) {
-                                const float4 pfj = a.cposf[p];
-                                float dx = pfj.x - pfi.x, dy = pfj.y - pfi.y, dz = pfj.z - pfi.z;
-                                minimg(a.bf, dx, dy, dz);
-                                const float d2f = dx * dx + dy * dy + dz * dz;
-                                if (d2f < a.cut_r2f_hi) {
-                                    if (d2f < a.cut_r2f_lo && (d2f < a.cut_a2f_lo || d2f >= a.cut_a2f_hi)) {
-                                        in_r = true;
-                                        in_a = d2f < a.cut_a2f_lo;
-                                    } else {   // near a cutoff: the exact FP64 test decides
-                                        const double4 pj = a.pos[a.cell_atoms[p]];
-                                        const double d2 = exact_d2(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z, a.bd, a.g.per);
-                                        in_r = d2 < a.cut_r2;
-                                        in_a = d2 < a.cut_a2;
-                                    }
-                                }
-                            }
-                        }
-                        const unsigned mr = __ballot_sync(0xffffffffu, in_r);
-                        const unsigned ma = __ballot_sync(0xffffffffu, in_a);
-                        if (in_r) {
-                            const int pos = m + __popc(mr & lt);
-                            // segment (angular? 0 : 2) + species of j in bits 30-31 above the caller index;
-                            // species is 0 or 1, so (seg << 30) fits with the caller index below 2^30
-                            const uint32_t sg = (in_a ? 0u : 2u) + (k >> 30);
-                            if (pos < SORT_MAX) key[pos] = (sg << 30) | (k & 0x3FFFFFFFu);
-                        }
-                        m += __popc(mr);
-                        nang += __popc(ma);
+        for (int base = 0; base < total; base += 32) {
+            const int p = pn;
+            const uint32_t k = kn;
+            const float4 pfj = fn;
+            pn = -1;
+            if (base + 32 + lane < total) {   // the next round's candidates in flight
+                pn = position_of(base + 32 + lane);
+                kn = a.ckey[pn];
+                fn = a.cposf[pn];
+            }
+            bool in_r = false, in_a = false;
+            if (p >= 0 && (k & 0x3FFFFFFFu) != self) {
+                float dx = pfj.x - pfi.x, dy = pfj.y - pfi.y, dz = pfj.z - pfi.z;
+                minimg(a.bf, dx, dy, dz);
+                const float d2f = dx * dx + dy * dy + dz * dz;
+                if (d2f < a.cut_r2f_hi) {
+                    if (d2f < a.cut_r2f_lo && (d2f < a.cut_a2f_lo || d2f >= a.cut_a2f_hi)) {
+                        in_r = true;
+                        in_a = d2f < a.cut_a2f_lo;
+                    } else {   // near a cutoff: the exact FP64 test decides
+                        const double4 pj = a.pos[a.cell_atoms[p]];
+                        const double d2 = exact_d2(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z, a.bd, a.g.per);
+                        in_r = d2 < a.cut_r2;
+                        in_a = d2 < a.cut_a2;
                     }
                 }
+            }
+            const unsigned mr = __ballot_sync(0xffffffffu, in_r);
+            const unsigned ma = __ballot_sync(0xffffffffu, in_a);
+            if (in_r) {
+                const int pos = m + __popc(mr & lt);
+                // segment (angular? 0 : 2) + species of j in bits 30-31 above the caller index;
+                // species is 0 or 1, so (seg << 30) fits with the caller index below 2^30
+                const uint32_t sg = (in_a ? 0u : 2u) + (k >> 30);
+                if (pos < SORT_MAX) key[pos] = (sg << 30) | (k & 0x3FFFFFFFu);
+            }
+            m += __popc(mr);
+            nang += __popc(ma);
+        }
         const bool overflow = m > a.cap || nang > a.cap_ang;
         const int mm = min(m, SORT_MAX);
         __syncwarp();
@@ -272,7 +309,7 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_build_lists_warp(ListArgs a) 
                 const uint32_t k = key[s];
                 sg = k >> 30;
                 a.nbr[(int64_t)s * a.n + i] = a.inv[k & 0x3FFFFFFFu];
-                a.nbr_orig[i * a.cap + s] = (int32_t)(k & 0x3FFFFFFFu);   // atom-major: one row per atom
+                a.nbr_orig[i * a.capr + s] = (int32_t)(k & 0x3FFFFFFFu);   // atom-major: one row per atom
             }
 #pragma unroll
             for (int t = 0; t < 4; ++t) ends[t] += __popc(__ballot_sync(0xffffffffu, sg <= (unsigned)t));
@@ -285,44 +322,86 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_build_lists_warp(ListArgs a) 
     }
 }
 
-// Warp per atom, lanes over slots: rev[s][i] = slot of i in the list of j = nbr[s][i].
-__global__ void __launch_bounds__(128) k_build_rev_warp(RevArgs a, const float4 *__restrict__ posf, float band_lo,
-                                                        float band_hi, BoxDev<float> bf) {
+// Slot of caller index oi inside [lo, hi) of the atom-major list row `row` (16-byte aligned),
+// or -1.  The segment is read with independent 16-byte loads, 32 entries per round (a binary
+// search needs one memory round trip per halving); the entries of a sorted segment are
+// distinct, so at most one matches.  `first` holds the first round's 32 entries from
+// lo & ~3, already loaded by the caller.
+__device__ __forceinline__ int match_round(const int4 (&v)[8], int b, int lo, int hi, int oi) {
+    int found = -1;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int k = b + 4 * u + c;
+            if (e[c] == oi && k >= lo && k < hi) found = k;
+        }
+    }
+    return found;
+}
+__device__ __forceinline__ void load_round(const int32_t *__restrict__ row, int b, int hi, int4 (&v)[8]) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        v[u] = b + 4 * u < hi ? *reinterpret_cast<const int4 *>(row + b + 4 * u) : make_int4(-1, -1, -1, -1);
+}
+__device__ __forceinline__ int find_rest(const int32_t *__restrict__ row, int b, int lo, int hi, int oi) {
+    int found = -1;
+    for (; b < hi && found < 0; b += 32) {
+        int4 v[8];
+        load_round(row, b, hi, v);
+        found = match_round(v, b, lo, hi, oi);
+    }
+    return found;
+}
+
+// Warp per atom, lanes over slots: rev[s][i] = slot of i in the list of j = nbr[s][i].  The
+// lists are symmetric and each pair's segment kind is too (the cutoff test gives the same
+// result for (i, j) and (j, i)), so i sits in the segment of j's list for (kind of slot s, t_i).
+// Each lane takes four slots 32 apart: their list entries, then their neighbours' segment
+// bounds, then two first search rounds at a time are in flight together.
+__global__ void __launch_bounds__(128) k_build_rev_warp(RevArgs a) {
     if (a.flag && *a.flag == 0) return;
     const int lane = threadIdx.x & 31;
     for (int64_t i = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5); i < a.n; i += (int64_t)gridDim.x * 4) {
         const int4 sg = a.seg[i];
-        const double4 pi = a.pos[i];
-        const float4 pfi = posf[i];
         const int oi = a.orig[i];
         const int ti = a.species[i];
-        for (int s = lane; s < sg.w; s += 32) {
-            const int j = a.nbr[(int64_t)s * a.n + i];
-            // angular membership of the pair, decided exactly as the list build decides it
-            const float4 pfj = posf[j];
-            float dx = pfi.x - pfj.x, dy = pfi.y - pfj.y, dz = pfi.z - pfj.z;
-            minimg(bf, dx, dy, dz);
-            const float d2f = dx * dx + dy * dy + dz * dz;
-            bool in_a;
-            if (d2f < band_lo) in_a = true;
-            else if (d2f >= band_hi) in_a = false;
-            else {
-                const double4 pj = a.pos[j];
-                in_a = exact_d2(pj.x, pj.y, pj.z, pi.x, pi.y, pi.z, a.bd, a.per) < a.cut_a2;
+        for (int s0 = 0; s0 < sg.w; s0 += 128) {
+            int j[4];
+            int4 sj[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int s = s0 + lane + 32 * u;
+                j[u] = s < sg.w ? a.nbr[(int64_t)s * a.n + i] : -1;
             }
-            const int sgi = (in_a ? 0 : 2) + ti;
-            const int4 sj = a.seg[j];
-            const int e[4] = {sj.x, sj.y, sj.z, sj.w};
-            int lo = sgi == 0 ? 0 : e[sgi - 1], hi = e[sgi];
-            int found = -1;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                const int om = a.nbr_orig[(int64_t)j * a.cap + mid];
-                if (om == oi) { found = mid; break; }
-                if (om < oi) lo = mid + 1; else hi = mid;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) sj[u] = j[u] >= 0 ? a.seg[j[u]] : make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int u = 0; u < 4; u += 2) {
+                int lo[2], hi[2], b[2];
+                int4 v[2][8];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int s = s0 + lane + 32 * (u + h);
+                    const int sgi = (s < sg.y ? 0 : 2) + ti;
+                    const int e[4] = {sj[u + h].x, sj[u + h].y, sj[u + h].z, sj[u + h].w};
+                    lo[h] = sgi == 0 ? 0 : e[sgi - 1];
+                    hi[h] = j[u + h] >= 0 ? e[sgi] : 0;
+                    b[h] = lo[h] & ~3;
+                    load_round(a.nbr_orig + (int64_t)max(j[u + h], 0) * a.capr, b[h], hi[h], v[h]);
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (j[u + h] < 0) continue;
+                    const int s = s0 + lane + 32 * (u + h);
+                    int found = match_round(v[h], b[h], lo[h], hi[h], oi);
+                    if (found < 0 && b[h] + 32 < hi[h])
+                        found = find_rest(a.nbr_orig + (int64_t)j[u + h] * a.capr, b[h] + 32, lo[h], hi[h], oi);
+                    if (found < 0) { atomicOr(a.status, ST_NBR_OVERFLOW); found = 0; }
+                    a.rev[(int64_t)s * a.n + i] = (uint8_t)found;
+                }
             }
-            if (found < 0) { atomicOr(a.status, ST_NBR_OVERFLOW); found = 0; }
-            a.rev[(int64_t)s * a.n + i] = found;
         }
     }
 }
@@ -380,7 +459,7 @@ void launch_rebuild(Sys &s, bool conditional) {
     la.pos = s.pos; la.posf = s.posf; la.species = s.species; la.orig = s.orig; la.inv = s.inv;
     la.cell_start = s.cells.start; la.cell_atoms = s.cells.atoms; la.cell_of = s.cells.of;
     la.cposf = s.cells.posf; la.ckey = s.cells.key; la.nbr_orig = s.nbr_orig;
-    la.n = n; la.cap = s.cap; la.cap_ang = s.cap_ang;
+    la.n = n; la.cap = s.cap; la.cap_ang = s.cap_ang; la.capr = nbr_orig_stride(s.cap);
     la.cut_r2 = s.cut_r2; la.cut_a2 = s.cut_a2;
     // FP32 separations of positions below 1e4 A carry an absolute d2 error far
     // below 0.05 A^2 at these distances; pairs inside that band take the FP64 test.
@@ -390,11 +469,10 @@ void launch_rebuild(Sys &s, bool conditional) {
     la.nbr = s.nbr; la.seg = s.seg; la.status = s.status; la.flag = flag;
     k_build_lists_warp<<<capped(n, LB_WARPS), LB_WARPS * 32, 0, s.stream>>>(la);
     RevArgs ra;
-    ra.pos = s.pos; ra.species = s.species; ra.orig = s.orig; ra.nbr = s.nbr; ra.nbr_orig = s.nbr_orig; ra.seg = s.seg;
-    ra.n = n; ra.cap = s.cap; ra.cut_a2 = s.cut_a2; ra.bd = s.boxd;
-    for (int a = 0; a < 3; ++a) ra.per[a] = s.per[a];
+    ra.species = s.species; ra.orig = s.orig; ra.nbr = s.nbr; ra.nbr_orig = s.nbr_orig; ra.seg = s.seg;
+    ra.n = n; ra.cap = s.cap; ra.capr = nbr_orig_stride(s.cap);
     ra.rev = s.rev; ra.status = s.status; ra.flag = flag;
-    k_build_rev_warp<<<capped(n, 4), 128, 0, s.stream>>>(ra, s.posf, la.cut_a2f_lo, la.cut_a2f_hi, s.boxf);
+    k_build_rev_warp<<<capped(n, 4), 128, 0, s.stream>>>(ra);
     const int64_t m = n > s.cells.ncell ? n : s.cells.ncell;
     k_finish<<<capped(m, T), T, 0, s.stream>>>(s.pos, s.posref, n, s.cells.count, s.cells.fill, s.cells.ncell,
                                                flag, s.d_builds);

@@ -14,7 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_bench_line_on_a_small_cube():
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cells", "8", "--steps", "6", "--warmup", "3",
-           "--skip-serving", "--skip-cpu-baseline", "--fp64-steps", "1", "--profile-steps", "2"]
+           "--skip-serving", "--skip-cpu-baseline", "--fp64-steps", "1", "--profile-steps", "2",
+           "--steady-steps", "12"]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads(r.stdout.strip().splitlines()[-1])
@@ -31,3 +32,6 @@ def test_bench_line_on_a_small_cube():
     assert 0 < rf["frac"] < 1.5
     assert line["fp64"]["value"] > 0
     assert line["mixed_error_vs_fp64"]["force_rmse_eV_per_A"] < 1e-3
+    st = line["steady_state"]
+    assert st["steps"] == 12 and st["value"] > 0 and st["ms_per_build"] > 0
+    assert 0 <= st["rebuild_share"] < 1

@@ -537,6 +537,7 @@ int sl_create_system(const double *positions, const double *spins, const double 
 
     const size_t N = (size_t)n;
     const size_t R = s.prec == SL_PREC_FP64 ? 8 : 4;
+    s.qs = (n + 3) & ~(int64_t)3;
     if ((rc = dalloc(&s.pos, N)) || (rc = dalloc(&s.vel, N)) || (rc = dalloc(&s.spin, N)) ||
         (rc = dalloc(&s.spin_prev, N)) || (rc = dalloc(&s.F, N)) || (rc = dalloc(&s.H, N)) ||
         (rc = dalloc(&s.posref, N)) || (rc = dalloc(&s.posf, N)) || (rc = dalloc(&s.spinf, N)) ||
@@ -545,7 +546,7 @@ int sl_create_system(const double *positions, const double *spins, const double 
         (rc = dalloc(&s.nbr_orig, N * sl::nbr_orig_stride(s.cap))) || (rc = dalloc(&s.cells.posf, N)) || (rc = dalloc(&s.cells.key, N)) || (rc = dalloc(&s.seg, N)) ||
         (rc = dalloc(&s.cells.count, (size_t)s.cells.ncell)) || (rc = dalloc(&s.cells.start, (size_t)s.cells.ncell + 1)) ||
         (rc = dalloc(&s.cells.fill, (size_t)s.cells.ncell)) || (rc = dalloc(&s.cells.atoms, N)) ||
-        (rc = dalloc(&s.cells.of, N)) || (rc = dalloc((char **)&s.q, R * DIM * N)) ||
+        (rc = dalloc(&s.cells.of, N)) || (rc = dalloc((char **)&s.q, R * DIM * (size_t)s.qs)) ||
         (rc = dalloc((char **)&s.bsum, R * NBREC * N)) || (rc = dalloc((char **)&s.fp, R * DIM * N)) ||
         (rc = dalloc((char **)&s.ei, R * N)) || (rc = dalloc((char **)&s.pairs, R * 8 * N * s.cap)) ||
         (rc = dalloc(&s.clj, N * (size_t)(s.cap + s.cap_ang))) || (rc = dalloc(&s.cls, N * (size_t)(s.cap + s.cap_ang))) ||
@@ -555,6 +556,8 @@ int sl_create_system(const double *positions, const double *spins, const double 
         (rc = dalloc(&s.rebuild, 1)) || (rc = dalloc(&s.d_step, 2)) || (rc = dalloc(&s.d_par, 1)) ||
         (rc = dalloc(&s.red, 256 * 10 + 10)) || (rc = dalloc(&s.snap, 5 * N)) || (rc = dalloc(&s.d_builds, 1)))
         return bail(rc);
+    if (s.prec == SL_PREC_MIXED && n > 0 && sl::make_q_tensor_map(s))
+        return bail(fail(SL_ECUDA, "the TMA map of the descriptor array could not be encoded"));
     if (s.mid_iters > 0) {
         const size_t ring = (size_t)(s.aa_depth > 0 ? s.aa_depth + 1 : 0) * N;
         if ((rc = dalloc(&s.posmid, N)) || (rc = dalloc(&s.posmidf, N)) || (rc = dalloc(&s.mids, N)) ||
@@ -848,8 +851,8 @@ int sl_get_descriptors(sl_system *sys, double *q, double *atom_energy) {
     if (s.n == 0) return SL_OK;
     int rc;
     if ((rc = evaluate(s, false, false, false))) return rc;
-    const size_t N = (size_t)s.n, R = s.prec == 0 ? 8 : 4;
-    std::vector<char> hq(R * sl::DIM * N), he(R * N);
+    const size_t N = (size_t)s.n, R = s.prec == 0 ? 8 : 4, QS = (size_t)s.qs;
+    std::vector<char> hq(R * sl::DIM * QS), he(R * N);
     std::vector<int32_t> orig(N);
     CK(cudaMemcpyAsync(hq.data(), s.q, hq.size(), cudaMemcpyDeviceToHost, s.stream));
     CK(cudaMemcpyAsync(he.data(), s.ei, he.size(), cudaMemcpyDeviceToHost, s.stream));
@@ -860,7 +863,7 @@ int sl_get_descriptors(sl_system *sys, double *q, double *atom_energy) {
     };
     for (size_t i = 0; i < N; ++i) {
         if (q)
-            for (int v = 0; v < sl::DIM; ++v) q[(size_t)orig[i] * sl::DIM + v] = get(hq, (size_t)v * N + i);
+            for (int v = 0; v < sl::DIM; ++v) q[(size_t)orig[i] * sl::DIM + v] = get(hq, (size_t)v * QS + i);
         if (atom_energy) atom_energy[orig[i]] = get(he, i);
     }
     return SL_OK;

@@ -321,14 +321,14 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
     for (int g = 0; g < 5; ++g) {
 #pragma unroll
         for (int n = 0; n < NCH; ++n) {
-            R v = TJ == 0 ? R(0) : a.q[(GQ[g] + n) * N + i];
+            R v = TJ == 0 ? R(0) : a.q[(GQ[g] + n) * a.qs + i];
 #pragma unroll
             for (int k = 0; k < NK; ++k) {
                 const R bgk = g == 0 ? b.b0[k] : g == 1 ? b.b12[k].x : g == 2 ? b.b12[k].y : g == 3 ? b.b34[k].x
                                                                                                  : b.b34[k].y;
                 v += P.c[TI][TJ][GG[g]][n][k] * bgk;
             }
-            a.q[(GQ[g] + n) * N + i] = v;
+            a.q[(GQ[g] + n) * a.qs + i] = v;
         }
     }
 }
@@ -346,7 +346,7 @@ __device__ __forceinline__ void crad_atom(const NepDev<R> &P, const Eval2Args<R>
     crad_species<R, TI, 1>(P, a, i, pi, si, sg.x, sg.y, sg.z, sg.w, na, nr, smask);
     a.cnt[i] = make_int4(na0, na, nr0, nr);
     for (int w = 0; w < a.maskw; ++w) a.mask[(int64_t)w * N + i] = smask[w][threadIdx.x];
-    a.q[Q_O * N + i] = si.x * si.x + si.y * si.y + si.z * si.z;
+    a.q[Q_O * a.qs + i] = si.x * si.x + si.y * si.y + si.z * si.z;
 }
 
 template <typename R>
@@ -527,8 +527,8 @@ __global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<
                 va = ql == t ? qa[n][t] : va;
                 vs = ql == t ? qs[n][t] : vs;
             }
-            a.q[(int64_t)(Q_A + n * 4 + ql) * N + i] = va;
-            a.q[(int64_t)(Q_SA + n * 4 + ql) * N + i] = vs;
+            a.q[(int64_t)(Q_A + n * 4 + ql) * a.qs + i] = va;
+            a.q[(int64_t)(Q_SA + n * 4 + ql) * a.qs + i] = vs;
         }
     }
 }
@@ -831,7 +831,7 @@ static Eval2Args<R> args2(Sys &s, bool want_virial) {
     a.nbr = s.nbr; a.seg = s.seg; a.rev = s.rev; a.n = s.n; a.n_fe = s.n_fe;
     a.cap = s.cap; a.cap_ang = s.cap_ang;
     a.clj = s.clj; a.cls = s.cls; a.cnt = s.cnt; a.mask = s.cmask; a.maskw = s.maskw;
-    a.q = (R *)s.q; a.bsum = (R *)s.bsum; a.fp = (R *)s.fp; a.ei = (R *)s.ei;
+    a.q = (R *)s.q; a.qs = s.qs; a.bsum = (R *)s.bsum; a.fp = (R *)s.fp; a.ei = (R *)s.ei;
     a.pd = (PairRec<R> *)s.pairs; a.fown = (v4<R> *)s.fown; a.gii = (v4<R> *)s.gii;
     a.wpart = (R *)s.wpart; a.want_virial = want_virial; a.status = s.status;
     return a;

@@ -33,6 +33,7 @@ struct Eval2Args {
     uint32_t *mask;    // [maskw][n]: bit s of word s/32 set when candidate slot s is inside rc_rad
     int maskw;
     R *q, *bsum, *fp, *ei;
+    int64_t qs;        // row stride of q ([DIM][qs])
     PairRec<R> *pd;    // [cap][n]
     v4<R> *fown, *gii;
     R *wpart;

@@ -1,6 +1,7 @@
 // sl_internal.h -- host-side system object and kernel launchers (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -108,7 +109,9 @@ struct Sys {
     Cells cells;
 
     // evaluation buffers (element type = compute precision)
-    void *q = nullptr;         // [DIM][n]
+    void *q = nullptr;         // [DIM][qs]: descriptor v of atom i at v * qs + i
+    int64_t qs = 0;            // row stride of q: n rounded up to a multiple of 4 (16-byte rows)
+    alignas(64) CUtensorMap qmap;   // TMA map of q (mixed precision): [DIM] rows x n atoms, 128 x 66 boxes
     void *bsum = nullptr;      // [n][NLM][BREC] angular-sum records
     void *fp = nullptr;        // [DIM][n]
     void *ei = nullptr;        // [n]
@@ -202,6 +205,7 @@ void eval2_init();
 int default_quad_block(int prec);   // threads per block of the quad kernels by default
 void launch_network(Sys &s, cudaEvent_t *ev);   // sl_nep.cu
 void launch_network_tc(Sys &s);                  // sl_mlp_tc.cu (mixed precision)
+int make_q_tensor_map(Sys &s);                   // sl_mlp_tc.cu: the TMA map of s.q; 0 on success
 // first half, rebuild group (7), compaction with radial forward, angular forward, network, backward,
 // second half
 constexpr int KERNELS_PER_STEP = 1 + 7 + 2 + 1 + 1 + 1;

@@ -13,8 +13,10 @@
 // ~1e-6 relative of FP32 arithmetic.  One thread issues the MMAs; completion is
 // signalled through an mbarrier (tcgen05.commit); the 128 threads read their
 // atom's row back with tcgen05.ld (TMEM lane = atom row).  Persistent CTAs loop
-// over tiles; the weights are staged once per CTA.  Every wait is bounded: on
-// timeout the kernel raises ST_TIMEOUT, frees its tensor memory and returns.
+// over tiles; the weights are staged once per CTA; each tile's 66 x 128 descriptors arrive
+// by one TMA tile load (cp.async.bulk.tensor) issued while the previous tile is in the
+// tensor cores.  Every wait is bounded: on timeout the kernel raises ST_TIMEOUT, waits for
+// its own loads and MMAs, frees its tensor memory and returns.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -45,12 +47,13 @@ constexpr uint32_t OFF_B1H = OFF_A1L + SZ_A1, OFF_B1L = OFF_B1H + SZ_B1;
 constexpr uint32_t OFF_A2H = OFF_A1H, OFF_A2L = OFF_A2H + SZ_A2;
 static_assert(2 * SZ_A2 <= SZ_A1, "A2 must fit in the A1 hi region");
 constexpr uint32_t OFF_B2H = OFF_B1L + SZ_B1, OFF_B2L = OFF_B2H + SZ_B2;
-constexpr uint32_t OFF_BAR = OFF_B2L + SZ_B2;            // 8-byte mbarrier
-constexpr uint32_t OFF_TMEM = OFF_BAR + 8;                // tensor-memory base address
-// FP32 descriptors of the next tile, [DIM][TM], filled by asynchronous copies while the
-// current tile is in the tensor cores (each thread copies and later reads its own column)
-constexpr uint32_t OFF_Q = (OFF_TMEM + 8 + 15) & ~15u;
-constexpr uint32_t SZ_Q = DIM * TM * 4;                   // 33792
+constexpr uint32_t OFF_BAR = OFF_B2L + SZ_B2;            // 8-byte mbarrier: MMA completion
+constexpr uint32_t OFF_BARQ = OFF_BAR + 8;                // 8-byte mbarrier: descriptor tile arrival
+constexpr uint32_t OFF_TMEM = OFF_BARQ + 8;               // tensor-memory base address
+// FP32 descriptors of the next tile, [DIM][TM] (the 66 x 128 box of the descriptor array),
+// brought in by one TMA tile load while the current tile is in the tensor cores
+constexpr uint32_t OFF_Q = (OFF_TMEM + 8 + 127) & ~127u;
+constexpr uint32_t SZ_Q = DIM * TM * 4;                   // 33792, the TMA transaction size
 constexpr uint32_t SMEM_BYTES = OFF_Q + SZ_Q;
 
 // byte offset of element (row, k) of a [rows x K] 16-bit operand in the canonical
@@ -120,12 +123,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(r[t]);
 }
 
-// 4-byte asynchronous global -> shared copy; bytes = 0 fills the destination with zero
-__device__ __forceinline__ void cp_async4(uint32_t dst, const float *src, uint32_t bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+// One TMA tile load of the descriptor box (atoms x0 .. x0+127, all 66 rows) into shared
+// memory; its completion (SZ_Q bytes, zero-filled past the last atom) is counted on mbarrier
+// `bar`, armed here with the expected byte count.  Issued by one thread.
+__device__ __forceinline__ void tma_load_q(uint32_t dst, const CUtensorMap *map, int x0, uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(SZ_Q) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x0), "r"(0), "r"(bar)
+        : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -147,7 +154,8 @@ __device__ __forceinline__ void split8(const float x[8], uint4 &hi, uint4 &lo) {
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-__global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDev<float> P, const float *__restrict__ q,
+__global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDev<float> P,
+                                                   const __grid_constant__ CUtensorMap qmap,
                                                    float *__restrict__ fp, float *__restrict__ ei, int64_t n,
                                                    int *status, const int *skip) {
     // uniform for the whole CTA and before any shared-memory or TMEM use
@@ -155,7 +163,7 @@ __global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDe
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
-    const uint32_t bar = sbase + OFF_BAR;
+    const uint32_t bar = sbase + OFF_BAR, barq = sbase + OFF_BARQ;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + OFF_TMEM);
 
     // weights, once per CTA: B1[h][v] = W0[h][v], B2[v][h] = W0[h][v]; zero padding
@@ -181,6 +189,7 @@ __global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDe
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barq) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -196,26 +205,22 @@ __global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDe
     const uint32_t t_z = tmem, t_g = tmem + N1;
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;   // this warp's TMEM lane quadrant
     constexpr uint32_t IDESC1 = instr_desc(TM, N1), IDESC2 = instr_desc(TM, N2);
-    uint32_t phase = 0;
+    uint32_t phase = 0, phase_q = 0;
     bool ok = true;
+    bool q_in_flight = false;   // a descriptor tile load has been issued and not yet waited for
     const int64_t ntiles = (n + TM - 1) / TM;
 
     const float *stage = reinterpret_cast<const float *>(smem + OFF_Q);
-    // descriptors of one tile into this thread's column of the stage (zeros past n)
-    auto fetch_tile = [&](int64_t t) {
-        const int64_t a = t * TM + tid;
-        const bool in = a < n;
-        const float *src = q + (in ? a : 0);
-        for (int v = 0; v < DIM; ++v)
-            cp_async4(sbase + OFF_Q + (uint32_t)(v * TM + tid) * 4u, src + (int64_t)v * n, in ? 4u : 0u);
-        cp_async_commit();
-    };
-    if (blockIdx.x < ntiles) fetch_tile(blockIdx.x);
+    if (tid == 0 && blockIdx.x < ntiles) tma_load_q(sbase + OFF_Q, &qmap, (int)(blockIdx.x * TM), barq);
+    q_in_flight = blockIdx.x < ntiles;
 
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int64_t i = tile * TM + tid;
         const bool valid = i < n;
-        cp_async_wait_all();
+        // this tile's descriptors (every thread waits; the block agrees on the outcome)
+        if (!__syncthreads_and(mbar_wait(barq, phase_q))) { ok = false; break; }
+        phase_q ^= 1u;
+        q_in_flight = false;
         // A1 row: s_v q_v, hi/lo
 #pragma unroll
         for (int c = 0; c < K1 / 8; ++c) {
@@ -230,11 +235,15 @@ __global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDe
             *reinterpret_cast<uint4 *>(smem + OFF_A1H + cm_off(tid, c * 8, K1)) = hi;
             *reinterpret_cast<uint4 *>(smem + OFF_A1L + cm_off(tid, c * 8, K1)) = lo;
         }
-        // this thread's column is consumed: the next tile's copies overlap this tile's MMAs
-        if (tile + gridDim.x < ntiles) fetch_tile(tile + gridDim.x);
+        // every thread's reads of the stage are ordered before the next tile load, which
+        // overlaps this tile's MMAs
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
+        if (tile + gridDim.x < ntiles) {
+            if (tid == 0) tma_load_q(sbase + OFF_Q, &qmap, (int)((tile + gridDim.x) * TM), barq);
+            q_in_flight = true;
+        }
         if (tid == 0) {
             tc_fence_after();
             uint32_t acc = 0;
@@ -319,11 +328,12 @@ __global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDe
         tc_fence_before();
         __syncthreads();   // TMEM and the A tiles are free for the next tile
     }
-    cp_async_wait_all();   // no copy may land after the CTA is gone
     if (!ok) {
         if (tid == 0) atomicOr(status, ST_TIMEOUT);
-        // let any MMA still in flight finish before the memory is released (bounded)
+        // let any MMA and any tile load still in flight finish before the memory is released
+        // (bounded waits)
         mbar_wait(bar, phase);
+        if (q_in_flight) mbar_wait(barq, phase_q);
     }
     tc_fence_before();
     __syncthreads();
@@ -356,6 +366,30 @@ int selftest_bounded_wait(int limit, int *status_out) {
     return e == cudaSuccess ? 0 : -1;
 }
 
+// TMA map of the FP32 descriptor array: a 2-D tensor of DIM rows x n atoms (atoms innermost,
+// row stride qs * 4 bytes, a multiple of 16), read in boxes of 128 atoms x 66 rows; atoms past
+// n read as zero.  The encode entry point is taken from the driver through the runtime.
+int make_q_tensor_map(Sys &s) {
+    if (s.prec == 0 || s.n == 0) return 0;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+        qr != cudaDriverEntryPointSuccess || !fn)
+        return -1;
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    const cuuint64_t dims[2] = {(cuuint64_t)s.n, (cuuint64_t)DIM};
+    const cuuint64_t strides[1] = {(cuuint64_t)s.qs * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)tc::TM, (cuuint32_t)DIM};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = reinterpret_cast<Encode>(fn)(&s.qmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, s.q, dims, strides, box,
+                                                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -1;
+}
+
 void launch_network_tc(Sys &s) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -371,8 +405,8 @@ void launch_network_tc(Sys &s) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t ntiles = (s.n + tc::TM - 1) / tc::TM;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * s.cfg.mlp_ctas_per_sm);
-    tc::k_mlp_tc<<<grid, 128, tc::SMEM_BYTES, s.stream>>>(s.pf, (const float *)s.q, (float *)s.fp, (float *)s.ei, s.n,
-                                                       s.status, s.at.skip);
+    tc::k_mlp_tc<<<grid, 128, tc::SMEM_BYTES, s.stream>>>(s.pf, s.qmap, (float *)s.fp, (float *)s.ei, s.n, s.status,
+                                                       s.at.skip);
 }
 
 }  // namespace sl

@@ -235,16 +235,13 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_build_lists_warp(ListArgs a) 
             p0[lane] = my_p0;
         }
         __syncwarp();
-        // cell-ordered position of candidate f of the sequence (the last cell whose offset is
-        // <= f holds it; empty cells share the offset of the cell after them)
+        // cell-ordered position of candidate f of the sequence: the last cell whose offset is
+        // <= f holds it (empty cells share the offset of the cell after them).  f grows by 32
+        // per round, so each lane moves its cell pointer forward instead of searching.
+        int cl = 0;
         auto position_of = [&](int f) {
-            int l = 0, h = nst - 1;
-            while (l < h) {
-                const int mid = (l + h + 1) >> 1;
-                if (off[mid] <= f) l = mid;
-                else h = mid - 1;
-            }
-            return p0[l] + (f - off[l]);
+            while (cl + 1 < nst && off[cl + 1] <= f) ++cl;
+            return p0[cl] + (f - off[cl]);
         };
         int pn = -1;
         uint32_t kn = 0;
@@ -355,11 +352,14 @@ __device__ __forceinline__ int find_rest(const int32_t *__restrict__ row, int b,
     return found;
 }
 
-// Warp per atom, lanes over slots: rev[s][i] = slot of i in the list of j = nbr[s][i].  The
-// lists are symmetric and each pair's segment kind is too (the cutoff test gives the same
-// result for (i, j) and (j, i)), so i sits in the segment of j's list for (kind of slot s, t_i).
-// Each lane takes four slots 32 apart: their list entries, then their neighbours' segment
-// bounds, then two first search rounds at a time are in flight together.
+// Warp per atom, lanes over slots: for every list entry j = nbr[s][i] with j > i, the slot t
+// of i in the list of j is found and both reverse slots are written, rev[s][i] = t and
+// rev[t][j] = s (the entries with j < i are written by j's warp): one search per unordered
+// pair.  The lists are symmetric and so is each pair's segment kind (the cutoff test gives the
+// same result for (i, j) and (j, i)), so i sits in the segment of j's list for (kind of slot
+// s, t_i).  Each lane takes four slots 32 apart: their list entries, then their neighbours'
+// segment bounds, then two first search rounds at a time are in flight together.  A pair
+// found in one list only (a list cut at its capacity) raises the overflow status.
 __global__ void __launch_bounds__(128) k_build_rev_warp(RevArgs a) {
     if (a.flag && *a.flag == 0) return;
     const int lane = threadIdx.x & 31;
@@ -373,7 +373,8 @@ __global__ void __launch_bounds__(128) k_build_rev_warp(RevArgs a) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int s = s0 + lane + 32 * u;
-                j[u] = s < sg.w ? a.nbr[(int64_t)s * a.n + i] : -1;
+                const int jj = s < sg.w ? a.nbr[(int64_t)s * a.n + i] : -1;
+                j[u] = jj > i ? jj : -1;   // the lower-indexed atom of the pair searches
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) sj[u] = j[u] >= 0 ? a.seg[j[u]] : make_int4(0, 0, 0, 0);
@@ -398,8 +399,13 @@ __global__ void __launch_bounds__(128) k_build_rev_warp(RevArgs a) {
                     int found = match_round(v[h], b[h], lo[h], hi[h], oi);
                     if (found < 0 && b[h] + 32 < hi[h])
                         found = find_rest(a.nbr_orig + (int64_t)j[u + h] * a.capr, b[h] + 32, lo[h], hi[h], oi);
-                    if (found < 0) { atomicOr(a.status, ST_NBR_OVERFLOW); found = 0; }
+                    if (found < 0) {
+                        atomicOr(a.status, ST_NBR_OVERFLOW);
+                        a.rev[(int64_t)s * a.n + i] = 0;
+                        continue;
+                    }
                     a.rev[(int64_t)s * a.n + i] = (uint8_t)found;
+                    a.rev[(int64_t)found * a.n + j[u + h]] = (uint8_t)s;
                 }
             }
         }

@@ -181,13 +181,14 @@ __device__ __forceinline__ void fwd_atom(const NepDev<R> &P, const EvalArgs<R> &
 // Fp_v = s_v sum_h w1_h (1 - tanh^2 z_h) W0_hv.
 template <typename R>
 __global__ void __launch_bounds__(128) k_mlp(const __grid_constant__ NepDev<R> P, const R *__restrict__ q,
-                                             R *__restrict__ fp, R *__restrict__ ei, int64_t n, const int *skip) {
+                                             R *__restrict__ fp, R *__restrict__ ei, int64_t n, int64_t qs,
+                                             const int *skip) {
     if (skip && *skip) return;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     R x[DIM];
 #pragma unroll
-    for (int v = 0; v < DIM; ++v) x[v] = q[(int64_t)v * n + i] * P.scal[v];
+    for (int v = 0; v < DIM; ++v) x[v] = q[(int64_t)v * qs + i] * P.scal[v];
     R t[NH];
     R E = -P.b1;
 #pragma unroll
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(128) k_mlp(const __grid_constant__ NepDev<R> P
 template <typename R>
 static void network_impl(Sys &s, const NepDev<R> &P) {
     const unsigned nb = (unsigned)((s.n + 127) / 128);
-    k_mlp<R><<<nb, 128, 0, s.stream>>>(P, (const R *)s.q, (R *)s.fp, (R *)s.ei, s.n, s.at.skip);
+    k_mlp<R><<<nb, 128, 0, s.stream>>>(P, (const R *)s.q, (R *)s.fp, (R *)s.ei, s.n, s.qs, s.at.skip);
 }
 
 // FP64 mode: CUDA-core network in FP64; mixed mode: the tensor-core network (sl_mlp_tc.cu)

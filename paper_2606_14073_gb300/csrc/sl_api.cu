@@ -542,7 +542,7 @@ int sl_create_system(const double *positions, const double *spins, const double 
         (rc = dalloc(&s.spin_prev, N)) || (rc = dalloc(&s.F, N)) || (rc = dalloc(&s.H, N)) ||
         (rc = dalloc(&s.posref, N)) || (rc = dalloc(&s.posf, N)) || (rc = dalloc(&s.spinf, N)) ||
         (rc = dalloc(&s.species, N)) || (rc = dalloc(&s.orig, N)) || (rc = dalloc(&s.inv, N)) ||
-        (rc = dalloc(&s.nbr, N * s.cap)) || (rc = dalloc(&s.rev, N * s.cap)) ||
+        (rc = dalloc(&s.nbr, N * sl::nbr_orig_stride(s.cap))) || (rc = dalloc(&s.rev, N * sl::nbr_orig_stride(s.cap))) ||
         (rc = dalloc(&s.nbr_orig, N * sl::nbr_orig_stride(s.cap))) || (rc = dalloc(&s.cells.posf, N)) || (rc = dalloc(&s.cells.key, N)) || (rc = dalloc(&s.seg, N)) ||
         (rc = dalloc(&s.cells.count, (size_t)s.cells.ncell)) || (rc = dalloc(&s.cells.start, (size_t)s.cells.ncell + 1)) ||
         (rc = dalloc(&s.cells.fill, (size_t)s.cells.ncell)) || (rc = dalloc(&s.cells.atoms, N)) ||
@@ -938,9 +938,10 @@ int sl_get_neighbors(sl_system *sys, int32_t cap, int32_t *counts_rad, int32_t *
     int rc = check_status(s);
     if (rc) return rc;
     const size_t N = (size_t)s.n;
-    std::vector<int32_t> nbr(N * s.cap), orig(N);
+    std::vector<int32_t> nbr(N * sl::nbr_orig_stride(s.cap)), orig(N);
     std::vector<int4> seg(N);
-    CK(cudaMemcpyAsync(nbr.data(), s.nbr, sizeof(int32_t) * N * s.cap, cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaMemcpyAsync(nbr.data(), s.nbr, sizeof(int32_t) * N * sl::nbr_orig_stride(s.cap), cudaMemcpyDeviceToHost,
+                       s.stream));
     CK(cudaMemcpyAsync(orig.data(), s.orig, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s.stream));
     CK(cudaMemcpyAsync(seg.data(), s.seg, sizeof(int4) * N, cudaMemcpyDeviceToHost, s.stream));
     CK(cudaStreamSynchronize(s.stream));
@@ -949,7 +950,7 @@ int sl_get_neighbors(sl_system *sys, int32_t cap, int32_t *counts_rad, int32_t *
         const int c = orig[i];
         std::vector<int32_t> rad, ang;
         for (int t = 0; t < seg[i].w; ++t) {
-            const int32_t j = orig[nbr[(size_t)t * N + i]];
+            const int32_t j = orig[nbr[(size_t)i * sl::nbr_orig_stride(s.cap) + t]];
             rad.push_back(j);
             if (t < seg[i].y) ang.push_back(j);
         }

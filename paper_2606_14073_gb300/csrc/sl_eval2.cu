@@ -147,8 +147,6 @@ __device__ __forceinline__ R kappa_of_lm(int lm) {
 // from 1 and 3), for the angular and backward kernels and the gather.  The sums are
 // contracted with the coefficients once per neighbour species (q^R, q^EX, q^DMI, q^ANI,
 // q^SIA); q^O = |S|^2.
-constexpr int CB = 4;    // candidates per batch in A
-constexpr int CBB = 4;   // candidates per batch in B
 
 template <typename R>
 struct RadSums {
@@ -206,40 +204,45 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
         b.b12[k] = b.b34[k] = pair2<R>(R(0), R(0));
     }
     const int64_t N = a.n;
-    const int32_t *__restrict__ nbr = a.nbr;
-    const uint8_t *__restrict__ rev = a.rev;
+    // this atom's candidate list and reverse slots: one row each, read in aligned chunks of 4
+    // entries (a 16-byte and a 4-byte load), two chunks ahead of the one being tested
+    const int32_t *__restrict__ nrow = a.nbr + i * a.capr;
+    const uint8_t *__restrict__ rrow = a.rev + i * a.capr;
     const v4<R> *__restrict__ pos = a.pos;
     const v4<R> *__restrict__ spin = a.spin;
-
-    // A: angular candidates, compaction and sums; the next batch's list entries are in flight
-    {
-        const int len = hi0 - lo0;
-        int jn[CB], tn[CB];
-#pragma unroll
-        for (int u = 0; u < CB; ++u) {
-            jn[u] = u < len ? nbr[(int64_t)(lo0 + u) * N + i] : -1;
-            tn[u] = u < len ? rev[(int64_t)(lo0 + u) * N + i] : 0;
+    auto chunk = [&](int c, int hi, int4 &jq, uchar4 &tq) {
+        if (c < hi) {
+            jq = *reinterpret_cast<const int4 *>(nrow + c);
+            tq = *reinterpret_cast<const uchar4 *>(rrow + c);
         }
+    };
+
+    // A: angular candidates, compaction and sums
+    {
+        int4 jq1 = make_int4(-1, -1, -1, -1), jq2 = jq1;
+        uchar4 tq1 = make_uchar4(0, 0, 0, 0), tq2 = tq1;
+        const int c0 = lo0 & ~3;
+        chunk(c0, hi0, jq1, tq1);
+        chunk(c0 + 4, hi0, jq2, tq2);
 #pragma unroll 1
-        for (int t0 = 0; t0 < len; t0 += CB) {
-            int jj[CB], tt[CB];
-            v4<R> pp[CB], ss[CB];
+        for (int c = c0; c < hi0; c += 4) {
+            int jj[4] = {jq1.x, jq1.y, jq1.z, jq1.w};
+            const int tt[4] = {tq1.x, tq1.y, tq1.z, tq1.w};
 #pragma unroll
-            for (int u = 0; u < CB; ++u) { jj[u] = jn[u]; tt[u] = tn[u]; }
+            for (int u = 0; u < 4; ++u)
+                if (c + u < lo0 || c + u >= hi0) jj[u] = -1;   // another segment's entry
+            v4<R> pp[4], ss[4];
 #pragma unroll
-            for (int u = 0; u < CB; ++u) {
+            for (int u = 0; u < 4; ++u) {
                 const int j = jj[u] >= 0 ? jj[u] : (int)i;
                 pp[u] = pos[j];
                 ss[u] = spin[j];
             }
+            jq1 = jq2;
+            tq1 = tq2;
+            chunk(c + 8, hi0, jq2, tq2);
 #pragma unroll
-            for (int u = 0; u < CB; ++u) {
-                const int t = t0 + CB + u;
-                jn[u] = t < len ? nbr[(int64_t)(lo0 + t) * N + i] : -1;
-                tn[u] = t < len ? rev[(int64_t)(lo0 + t) * N + i] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < CB; ++u) {
+            for (int u = 0; u < 4; ++u) {
                 if (jj[u] < 0) continue;
                 R dx, dy, dz;
                 sep(a.box, pi, pp[u], dx, dy, dz);
@@ -248,38 +251,35 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
                 const int row = take_row(P, a, d2, na, nr);
                 if (row < 0) continue;
                 a.clj[(int64_t)row * N + i] = jj[u];
-                a.cls[(int64_t)row * N + i] = (uint16_t)((lo0 + t0 + u) | (tt[u] << 8));
-                mark_slot(smask, lo0 + t0 + u);
+                a.cls[(int64_t)row * N + i] = (uint16_t)((c + u) | (tt[u] << 8));
+                mark_slot(smask, c + u);
                 rad_accumulate(P, si, ss[u], dx, dy, dz, d2, b);
             }
         }
     }
-    // B: radial-shell candidates, compaction only; the next batch's list entries are in flight
+    // B: radial-shell candidates, compaction only
     const int naB = na, nrB = nr;
     {
-        const int len = hi1 - lo1;
-        int jn[CBB], tn[CBB];
-#pragma unroll
-        for (int u = 0; u < CBB; ++u) {
-            jn[u] = u < len ? nbr[(int64_t)(lo1 + u) * N + i] : -1;
-            tn[u] = u < len ? rev[(int64_t)(lo1 + u) * N + i] : 0;
-        }
+        int4 jq1 = make_int4(-1, -1, -1, -1), jq2 = jq1;
+        uchar4 tq1 = make_uchar4(0, 0, 0, 0), tq2 = tq1;
+        const int c0 = lo1 & ~3;
+        chunk(c0, hi1, jq1, tq1);
+        chunk(c0 + 4, hi1, jq2, tq2);
 #pragma unroll 1
-        for (int t0 = 0; t0 < len; t0 += CBB) {
-            int jj[CBB], tt[CBB];
-            v4<R> pp[CBB];
+        for (int c = c0; c < hi1; c += 4) {
+            int jj[4] = {jq1.x, jq1.y, jq1.z, jq1.w};
+            const int tt[4] = {tq1.x, tq1.y, tq1.z, tq1.w};
 #pragma unroll
-            for (int u = 0; u < CBB; ++u) { jj[u] = jn[u]; tt[u] = tn[u]; }
+            for (int u = 0; u < 4; ++u)
+                if (c + u < lo1 || c + u >= hi1) jj[u] = -1;
+            v4<R> pp[4];
 #pragma unroll
-            for (int u = 0; u < CBB; ++u) pp[u] = pos[jj[u] >= 0 ? jj[u] : (int)i];
+            for (int u = 0; u < 4; ++u) pp[u] = pos[jj[u] >= 0 ? jj[u] : (int)i];
+            jq1 = jq2;
+            tq1 = tq2;
+            chunk(c + 8, hi1, jq2, tq2);
 #pragma unroll
-            for (int u = 0; u < CBB; ++u) {
-                const int t = t0 + CBB + u;
-                jn[u] = t < len ? nbr[(int64_t)(lo1 + t) * N + i] : -1;
-                tn[u] = t < len ? rev[(int64_t)(lo1 + t) * N + i] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < CBB; ++u) {
+            for (int u = 0; u < 4; ++u) {
                 if (jj[u] < 0) continue;
                 R dx, dy, dz;
                 sep(a.box, pi, pp[u], dx, dy, dz);
@@ -288,8 +288,8 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
                 const int row = take_row(P, a, d2, na, nr);
                 if (row < 0) continue;
                 a.clj[(int64_t)row * N + i] = jj[u];
-                a.cls[(int64_t)row * N + i] = (uint16_t)((lo1 + t0 + u) | (tt[u] << 8));
-                mark_slot(smask, lo1 + t0 + u);
+                a.cls[(int64_t)row * N + i] = (uint16_t)((c + u) | (tt[u] << 8));
+                mark_slot(smask, c + u);
             }
         }
     }
@@ -828,7 +828,7 @@ static Eval2Args<R> args2(Sys &s, bool want_virial) {
         a.box = *reinterpret_cast<const BoxDev<R> *>(&s.boxf);
     }
     a.skip = s.at.skip;
-    a.nbr = s.nbr; a.seg = s.seg; a.rev = s.rev; a.n = s.n; a.n_fe = s.n_fe;
+    a.nbr = s.nbr; a.seg = s.seg; a.rev = s.rev; a.capr = nbr_orig_stride(s.cap); a.n = s.n; a.n_fe = s.n_fe;
     a.cap = s.cap; a.cap_ang = s.cap_ang;
     a.clj = s.clj; a.cls = s.cls; a.cnt = s.cnt; a.mask = s.cmask; a.maskw = s.maskw;
     a.q = (R *)s.q; a.qs = s.qs; a.bsum = (R *)s.bsum; a.fp = (R *)s.fp; a.ei = (R *)s.ei;

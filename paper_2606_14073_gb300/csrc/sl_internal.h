@@ -101,10 +101,11 @@ struct Sys {
     int32_t *species = nullptr, *orig = nullptr, *inv = nullptr;
     int64_t n_fe = 0;          // atoms [0, n_fe) are species 0
 
-    // neighbour lists: nbr and rev slot-major [slot][atom]; nbr_orig (caller index of
-    // each entry, searched by the reverse-slot build) atom-major [atom][slot]
+    // neighbour lists, atom-major rows of nbr_orig_stride(cap) entries: nbr (internal index of
+    // each candidate), rev (slot of the atom in its candidate's list; cap <= 256, one byte),
+    // nbr_orig (caller index of each candidate, searched by the reverse-slot build)
     int32_t *nbr = nullptr, *nbr_orig = nullptr;
-    uint8_t *rev = nullptr;    // [cap][n] reverse slots (a slot index fits one byte: cap <= 256)
+    uint8_t *rev = nullptr;
     int4 *seg = nullptr;       // per atom: ends of (ang t0, ang t1, rad t0, rad t1)
     Cells cells;
 

@@ -115,7 +115,7 @@ struct ListArgs {
     BoxDev<double> bd;
     BoxDev<float> bf;
     GridArgs g;
-    int32_t *nbr;
+    int32_t *nbr;             // [n][capr] candidate lists, atom-major
     int4 *seg;
     int *status;
     const int *flag;
@@ -127,7 +127,7 @@ struct RevArgs {
     const int4 *seg;
     int cap, capr;
     int64_t n;
-    uint8_t *rev;         // [cap][n] reverse slots (cap <= 256)
+    uint8_t *rev;         // [n][capr] reverse slots (cap <= 256)
     int *status;
     const int *flag;
 };
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_build_lists_warp(ListArgs a) 
             if (s < cnt) {
                 const uint32_t k = key[s];
                 sg = k >> 30;
-                a.nbr[(int64_t)s * a.n + i] = a.inv[k & 0x3FFFFFFFu];
+                a.nbr[i * a.capr + s] = a.inv[k & 0x3FFFFFFFu];
                 a.nbr_orig[i * a.capr + s] = (int32_t)(k & 0x3FFFFFFFu);   // atom-major: one row per atom
             }
 #pragma unroll
@@ -352,9 +352,9 @@ __device__ __forceinline__ int find_rest(const int32_t *__restrict__ row, int b,
     return found;
 }
 
-// Warp per atom, lanes over slots: for every list entry j = nbr[s][i] with j > i, the slot t
-// of i in the list of j is found and both reverse slots are written, rev[s][i] = t and
-// rev[t][j] = s (the entries with j < i are written by j's warp): one search per unordered
+// Warp per atom, lanes over slots: for every list entry j = nbr[i][s] with j > i, the slot t
+// of i in the list of j is found and both reverse slots are written, rev[i][s] = t and
+// rev[j][t] = s (the entries with j < i are written by j's warp): one search per unordered
 // pair.  The lists are symmetric and so is each pair's segment kind (the cutoff test gives the
 // same result for (i, j) and (j, i)), so i sits in the segment of j's list for (kind of slot
 // s, t_i).  Each lane takes four slots 32 apart: their list entries, then their neighbours'
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(128) k_build_rev_warp(RevArgs a) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int s = s0 + lane + 32 * u;
-                const int jj = s < sg.w ? a.nbr[(int64_t)s * a.n + i] : -1;
+                const int jj = s < sg.w ? a.nbr[i * a.capr + s] : -1;
                 j[u] = jj > i ? jj : -1;   // the lower-indexed atom of the pair searches
             }
 #pragma unroll
@@ -401,11 +401,11 @@ __global__ void __launch_bounds__(128) k_build_rev_warp(RevArgs a) {
                         found = find_rest(a.nbr_orig + (int64_t)j[u + h] * a.capr, b[h] + 32, lo[h], hi[h], oi);
                     if (found < 0) {
                         atomicOr(a.status, ST_NBR_OVERFLOW);
-                        a.rev[(int64_t)s * a.n + i] = 0;
+                        a.rev[i * a.capr + s] = 0;
                         continue;
                     }
-                    a.rev[(int64_t)s * a.n + i] = (uint8_t)found;
-                    a.rev[(int64_t)found * a.n + j[u + h]] = (uint8_t)s;
+                    a.rev[i * a.capr + s] = (uint8_t)found;
+                    a.rev[(int64_t)j[u + h] * a.capr + found] = (uint8_t)s;
                 }
             }
         }

@@ -717,7 +717,10 @@ def run_ours(args):
         del sysd
 
     # launch shapes of the evaluation kernels picked by the library's autotuner
-    tuned = sysm.autotune(repeats=5) if not args.no_autotune else None
+    tuned = None
+    if not args.no_autotune:
+        tuned = sysm.autotune(repeats=5)
+        tuned["config"] = sysm.launch_config()
 
     # warm-up (graph capture happens here)
     sysm.step(args.warmup, DT, TEMP, FIELD)

@@ -38,6 +38,7 @@ extern "C" {
 #define SL_ENONFINITE (-4)      /* a force or field became NaN/Inf                 */
 #define SL_ETIMEOUT (-5)        /* a bounded device wait gave up                   */
 #define SL_ECUDA (-6)           /* CUDA runtime error or no usable device          */
+#define SL_EINTERNAL (-7)       /* a self-check of the library failed              */
 
 #define SL_PREC_FP64 0          /* everything in FP64                               */
 #define SL_PREC_MIXED 1         /* FP32 descriptors/backward, FP16 tensor-core MLP, */
@@ -232,7 +233,9 @@ int sl_texture_map(sl_system *sys, int32_t normal_axis, double cell, int32_t *n_
                    double *Q);
 
 /* Autotuner of the evaluation kernels' launch shapes (atoms per block of the radial,
- * angular and backward kernels; persistent CTAs per SM of the tensor-core network).
+ * angular and backward kernels, and in mixed precision their register budgets, i.e. the
+ * resident blocks per SM the compiled kernel is held to; persistent CTAs per SM of the
+ * tensor-core network).
  * Times the candidate shapes with CUDA events over `repeats` evaluations of the current
  * state (which it leaves unchanged), keeps the fastest shape per kernel for this system
  * and for later systems of the process on the same device, precision and size (a
@@ -242,6 +245,17 @@ int sl_texture_map(sl_system *sys, int32_t normal_axis, double cell, int32_t *n_
  * (may be NULL): summed median time of the four kernel groups with the previous and the
  * chosen shapes.  SL_EINVAL for repeats outside [1, 1000]. */
 int sl_autotune(sl_system *sys, int32_t repeats, int32_t *chosen, double *eval_ms_before, double *eval_ms_after);
+
+/* The evaluation kernels' current launch configuration, cfg[8]: radial block (threads),
+ * radial register budget (0: default of 4 blocks per SM, 3: 3 blocks per SM), angular
+ * block, angular budget (0: default, 5: 5 blocks per SM), backward block, backward budget
+ * (0: default of 2 blocks per SM, 4: 4 blocks per SM), network CTAs per SM, 0.  landscape
+ * [16] (may be NULL): the last sl_autotune's median ms of the radial, angular, network and
+ * backward kernels under each of its 4 candidate shapes (candidate-major; -1 where not
+ * timed: never tuned, or FP64 mode, which has 2 candidates).  Candidates: 0 half blocks and
+ * 1 network CTA, 1 full blocks and 2 CTAs, 2 and 3 the same with the register-budget
+ * variants.  SL_EINVAL for NULL sys or cfg. */
+int sl_get_launch_config(const sl_system *sys, int32_t *cfg, double *landscape);
 
 /* Midpoint evaluations executed by all steps so far (0 in the predictor-corrector
  * mode); the mean iteration count per step is this over the steps taken. */

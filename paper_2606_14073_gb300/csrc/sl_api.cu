@@ -1025,28 +1025,75 @@ int sl_autotune(sl_system *sys, int32_t repeats, int32_t *chosen, double *eval_m
         for (auto &e : ev) cudaEventDestroy(e);
         return SL_OK;
     };
+    // Candidate shapes: block size (half or full default) x register budget (the default, or
+    // the kernel's variant, mixed precision only); network CTAs per SM 1 or 2.  Each kernel's
+    // time depends on its own shape only, so one evaluation per candidate times every kernel
+    // and each kernel takes its fastest.
     const int q = sl::default_quad_block(s.prec);
-    sl::LaunchCfg small, large;
-    small.crad_block = 64; small.ang_block = q / 2; small.bwd_block = q / 2; small.mlp_ctas_per_sm = 1;
-    large.crad_block = 128; large.ang_block = q; large.bwd_block = q; large.mlp_ctas_per_sm = 2;
-    double ms0[5], msS[5], msL[5];
+    const int ncand = s.prec == 0 ? 2 : 4;
+    sl::LaunchCfg cand[4];
+    for (int c = 0; c < ncand; ++c) {
+        const bool half = (c & 1) == 0, var = c >= 2;
+        cand[c].crad_block = half ? 64 : 128;
+        cand[c].ang_block = half ? q / 2 : q;
+        cand[c].bwd_block = half ? q / 2 : q;
+        cand[c].mlp_ctas_per_sm = half ? 1 : 2;
+        cand[c].crad_minb = var ? 3 : 0;
+        cand[c].ang_minb = var ? 5 : 0;
+        cand[c].bwd_minb = var ? 4 : 0;
+    }
+    double ms0[5], msc[4][5];
     int rc;
-    if ((rc = time_cfg(before, ms0)) || (rc = time_cfg(small, msS)) || (rc = time_cfg(large, msL))) {
-        s.cfg = before;
+    // the shapes must not change any result: the forces and fields gathered after each
+    // candidate's evaluations are compared bit for bit with those of the starting shape
+    double4 *ref = nullptr;
+    int *diff = nullptr;
+    if ((rc = dalloc(&ref, 2 * (size_t)s.n)) || (rc = dalloc(&diff, 1))) {
+        if (ref) cudaFree(ref);
         return rc;
     }
-    // each kernel's time depends on its own shape only: pick per kernel
-    sl::LaunchCfg best = large;
-    if (msS[1] < msL[1]) best.crad_block = small.crad_block;
-    if (msS[2] < msL[2]) best.ang_block = small.ang_block;
-    if (s.prec != 0 && msS[3] < msL[3]) best.mlp_ctas_per_sm = small.mlp_ctas_per_sm;
-    if (msS[4] < msL[4]) best.bwd_block = small.bwd_block;
-    double after = 0.0, b0 = 0.0;
+    auto cleanup = [&]() {
+        cudaFree(ref);
+        cudaFree(diff);
+        s.cfg = before;
+    };
+    if ((rc = time_cfg(before, ms0))) {
+        cleanup();
+        return rc;
+    }
+    sl::launch_gather(s, false);
+    CK(cudaMemcpyAsync(ref, s.Fo, sizeof(double4) * s.n, cudaMemcpyDeviceToDevice, s.stream));
+    CK(cudaMemcpyAsync(ref + s.n, s.Ho, sizeof(double4) * s.n, cudaMemcpyDeviceToDevice, s.stream));
+    CK(cudaMemsetAsync(diff, 0, sizeof(int), s.stream));
+    for (int c = 0; c < ncand; ++c) {
+        if ((rc = time_cfg(cand[c], msc[c]))) {
+            cleanup();
+            return rc;
+        }
+        sl::launch_gather(s, false);
+        sl::launch_compare_bits(s, ref, diff);
+    }
+    int h_diff = 0;
+    CK(cudaMemcpyAsync(&h_diff, diff, sizeof(int), cudaMemcpyDeviceToHost, s.stream));
+    CK(cudaStreamSynchronize(s.stream));
+    cleanup();
+    if (h_diff) return fail(SL_EINTERNAL, "a launch shape changed the forces or fields");
+    auto argmin = [&](int g) {
+        int m = 0;
+        for (int c = 1; c < ncand; ++c)
+            if (msc[c][g] < msc[m][g]) m = c;
+        return m;
+    };
+    const int kc = argmin(1), ka = argmin(2), km = argmin(3), kb = argmin(4);
+    sl::LaunchCfg best;
+    best.crad_block = cand[kc].crad_block; best.crad_minb = cand[kc].crad_minb;
+    best.ang_block = cand[ka].ang_block; best.ang_minb = cand[ka].ang_minb;
+    best.mlp_ctas_per_sm = s.prec != 0 ? cand[km].mlp_ctas_per_sm : before.mlp_ctas_per_sm;
+    best.bwd_block = cand[kb].bwd_block; best.bwd_minb = cand[kb].bwd_minb;
+    double after = msc[kc][1] + msc[ka][2] + msc[s.prec != 0 ? km : 0][3] + msc[kb][4], b0 = 0.0;
     for (int g = 1; g < 5; ++g) b0 += ms0[g];
-    after += best.crad_block == small.crad_block ? msS[1] : msL[1];
-    after += best.ang_block == small.ang_block ? msS[2] : msL[2];
-    after += best.mlp_ctas_per_sm == small.mlp_ctas_per_sm && s.prec != 0 ? msS[3] : msL[3];
-    after += best.bwd_block == small.bwd_block ? msS[4] : msL[4];
+    for (int c = 0; c < 4; ++c)
+        for (int g = 0; g < 4; ++g) s.tune_ms[c][g] = c < ncand ? msc[c][g + 1] : -1.0;
     s.cfg = before;
     set_cfg(s, best);
     {
@@ -1056,6 +1103,19 @@ int sl_autotune(sl_system *sys, int32_t repeats, int32_t *chosen, double *eval_m
     report(best);
     if (eval_ms_before) *eval_ms_before = b0;
     if (eval_ms_after) *eval_ms_after = after;
+    return SL_OK;
+}
+
+int sl_get_launch_config(const sl_system *sys, int32_t *cfg, double *landscape) {
+    if (!sys || !cfg) return fail(SL_EINVAL, "NULL argument");
+    const sl::Sys &s = sys->s;
+    const int q = sl::default_quad_block(s.prec);
+    const sl::LaunchCfg &c = s.cfg;
+    const int32_t v[8] = {c.crad_block, c.crad_minb, c.ang_block ? c.ang_block : q, c.ang_minb,
+                          c.bwd_block ? c.bwd_block : q, c.bwd_minb, c.mlp_ctas_per_sm, 0};
+    for (int k = 0; k < 8; ++k) cfg[k] = v[k];
+    if (landscape)
+        for (int k = 0; k < 16; ++k) landscape[k] = s.tune_ms[k / 4][k % 4];
     return SL_OK;
 }
 

@@ -349,8 +349,10 @@ __device__ __forceinline__ void crad_atom(const NepDev<R> &P, const Eval2Args<R>
     a.q[Q_O * a.qs + i] = si.x * si.x + si.y * si.y + si.z * si.z;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_crad(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+// MINB: minimum resident blocks per SM the register allocation is held to (the autotuner's
+// register-budget dimension); the default is the first value of each kernel's list below.
+template <typename R, int MINB = sizeof(R) == 4 ? 4 : 2>
+__global__ void __launch_bounds__(128, MINB) k_crad(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
     if (a.skip && *a.skip) return;
     __shared__ uint32_t smask[MASKW_MAX][128];   // blocks have at most 128 threads
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -396,8 +398,8 @@ __device__ __forceinline__ void ang_stage_fwd(const NepDev<R> &P, const Eval2Arg
     }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(128) k_ang_fwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+template <typename R, int MINB = 1>
+__global__ void __launch_bounds__(128, MINB) k_ang_fwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
     if (a.skip && *a.skip) return;
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -729,8 +731,8 @@ __device__ __forceinline__ void bwd_rows(const NepDev<R> &P, const Eval2Args<R> 
     }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 2 : 1) k_bwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+template <typename R, int MINB = sizeof(R) == 4 ? 2 : 1>
+__global__ void __launch_bounds__(128, MINB) k_bwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
     if (a.skip && *a.skip) return;
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -856,8 +858,10 @@ void eval2_init() {
     std::lock_guard<std::mutex> lk(mu);
     if (dev < 64 && (done >> dev & 1u)) return;
     cudaFuncSetAttribute(k_ang_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<float>());
+    cudaFuncSetAttribute(k_ang_fwd<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<float>());
     cudaFuncSetAttribute(k_ang_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<double>());
     cudaFuncSetAttribute(k_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<float>());
+    cudaFuncSetAttribute(k_bwd<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<float>());
     cudaFuncSetAttribute(k_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<double>());
     if (dev < 64) done |= 1ull << dev;
 }
@@ -874,13 +878,29 @@ static void eval2_impl(Sys &s, const NepDev<R> &P, bool want_virial, cudaEvent_t
     if (ev) cudaEventRecord(ev[0], s.stream);
     // compaction and radial channels in one kernel: the compaction group is empty
     if (ev) cudaEventRecord(ev[1], s.stream);
-    k_crad<R><<<nb, cb, 0, s.stream>>>(P, a);
+    // register-budget variants exist for the mixed-precision kernels (sl_autotune chooses them)
+    bool variant = false;
+    if constexpr (sizeof(R) == 4) {
+        variant = s.cfg.crad_minb == 3;
+        if (variant) k_crad<R, 3><<<nb, cb, 0, s.stream>>>(P, a);
+    }
+    if (!variant) k_crad<R><<<nb, cb, 0, s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[2], s.stream);
-    k_ang_fwd<R><<<nqa, qa, fwd_smem<R>(qa), s.stream>>>(P, a);
+    variant = false;
+    if constexpr (sizeof(R) == 4) {
+        variant = s.cfg.ang_minb == 5;
+        if (variant) k_ang_fwd<R, 5><<<nqa, qa, fwd_smem<R>(qa), s.stream>>>(P, a);
+    }
+    if (!variant) k_ang_fwd<R><<<nqa, qa, fwd_smem<R>(qa), s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[3], s.stream);
     launch_network(s, nullptr);
     if (ev) cudaEventRecord(ev[4], s.stream);
-    k_bwd<R><<<nqw, qw, bwdf_smem<R>(qw), s.stream>>>(P, a);
+    variant = false;
+    if constexpr (sizeof(R) == 4) {
+        variant = s.cfg.bwd_minb == 4;
+        if (variant) k_bwd<R, 4><<<nqw, qw, bwdf_smem<R>(qw), s.stream>>>(P, a);
+    }
+    if (!variant) k_bwd<R><<<nqw, qw, bwdf_smem<R>(qw), s.stream>>>(P, a);
     if (ev) cudaEventRecord(ev[5], s.stream);
 }
 

@@ -56,6 +56,11 @@ struct LaunchCfg {
     int ang_block = 0;         // threads per block of k_ang_fwd (four per atom); 0: the precision's default
     int bwd_block = 0;         // threads per block of k_bwd
     int mlp_ctas_per_sm = 2;   // persistent CTAs per SM of the tensor-core network
+    // register budgets of the mixed-precision kernels, as the minimum resident blocks per SM
+    // the compiler holds the allocation to (0: the kernel's default budget)
+    int crad_minb = 0;         // 0 (4 blocks: 128 registers) or 3 (170 registers)
+    int ang_minb = 0;          // 0 (unconstrained) or 5 (102 registers)
+    int bwd_minb = 0;          // 0 (2 blocks: the compiler takes 168) or 4 (128 registers)
 };
 
 // Where an evaluation reads positions and spins (null: the state arrays) and an
@@ -155,6 +160,9 @@ struct Sys {
     // evaluation point used by launch_eval / launch_network while it is set
     EvalAt at;
     LaunchCfg cfg;
+    // the last sl_autotune's measured landscape: median ms of the radial, angular, network and
+    // backward kernels under each of its candidate shapes (-1: not timed)
+    double tune_ms[4][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}};
 
     // per-atom part of the external field (tesla, internal order); null: uniform field only
     double4 *Bat = nullptr;
@@ -224,6 +232,7 @@ size_t midpoint_scratch_doubles();
 int texture_grid(const Sys &s, int normal, double cell, int *na, int *nb);
 cudaError_t launch_texture(Sys &s, int normal, double cell, double *h_m, double *Q);
 void launch_gather(Sys &s, bool carried);
+void launch_compare_bits(Sys &s, const double4 *ref, int *diff);   // *diff |= 1 if (Fo, Ho) != ref bitwise
 void launch_normalise_spins(Sys &s);
 int reduce_energy_virial(Sys &s, double *E, double *W, bool want_virial);
 

@@ -14,10 +14,12 @@ import numpy as np
 
 from . import build as _build
 
-SL_OK, SL_EINVAL, SL_ENOMEM, SL_ENBR_OVERFLOW, SL_ENONFINITE, SL_ETIMEOUT, SL_ECUDA = 0, -1, -2, -3, -4, -5, -6
+SL_OK, SL_EINVAL, SL_ENOMEM, SL_ENBR_OVERFLOW, SL_ENONFINITE, SL_ETIMEOUT, SL_ECUDA, SL_EINTERNAL = \
+    0, -1, -2, -3, -4, -5, -6, -7
 SL_PREC_FP64, SL_PREC_MIXED = 0, 1
 _NAMES = {SL_EINVAL: "SL_EINVAL", SL_ENOMEM: "SL_ENOMEM", SL_ENBR_OVERFLOW: "SL_ENBR_OVERFLOW",
-          SL_ENONFINITE: "SL_ENONFINITE", SL_ETIMEOUT: "SL_ETIMEOUT", SL_ECUDA: "SL_ECUDA"}
+          SL_ENONFINITE: "SL_ENONFINITE", SL_ETIMEOUT: "SL_ETIMEOUT", SL_ECUDA: "SL_ECUDA",
+          SL_EINTERNAL: "SL_EINTERNAL"}
 
 EXPORTS = ["sl_default_options", "sl_create_system", "sl_step", "sl_energy_forces_fields", "sl_get_descriptors",
            "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_get_stream",
@@ -25,7 +27,7 @@ EXPORTS = ["sl_default_options", "sl_create_system", "sl_step", "sl_energy_force
            "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak", "sl_descriptors_energies_noalloc",
            "sl_estimate_device_bytes", "sl_get_midpoint_evaluations", "sl_set_atom_fields", "sl_texture_map",
            "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal", "sl_selftest_carrier",
-           "sl_selftest_bounded_wait", "sl_set_spin_sweep", "sl_get_sweep_colours"]
+           "sl_selftest_bounded_wait", "sl_set_spin_sweep", "sl_get_sweep_colours", "sl_get_launch_config"]
 KERNEL_GROUPS = ["first_half", "rebuild", "compact", "rad_fwd", "ang_fwd", "network", "backward", "second_half"]
 
 
@@ -81,6 +83,7 @@ def lib(path: str | None = None):
             L.sl_get_sweep_colours.argtypes = [P, P, P, P]
             L.sl_batch_graph_launches.argtypes = [P, P]
             L.sl_autotune.argtypes = [P, I32, P, P, P]
+            L.sl_get_launch_config.argtypes = [P, P, P]
             L.sl_texture_map.argtypes = [P, I32, D, P, P, P, P]
             L.sl_step_profiled.argtypes = [P, I64, D, D, P, P]
             L.sl_measure_fma_peak.argtypes = [I32, P, P]
@@ -103,7 +106,7 @@ def lib(path: str | None = None):
                       "sl_descriptors_energies_noalloc", "sl_get_midpoint_evaluations", "sl_set_atom_fields",
                       "sl_texture_map", "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal",
                       "sl_selftest_carrier", "sl_selftest_bounded_wait", "sl_set_spin_sweep",
-                      "sl_get_sweep_colours"):
+                      "sl_get_sweep_colours", "sl_get_launch_config"):
                 getattr(L, f).restype = C.c_int
             _lib = L
         return _lib
@@ -223,6 +226,18 @@ class System:
         _check(lib().sl_autotune(self.handle, int(repeats), _ptr(ch), C.byref(b), C.byref(a)))
         return dict(crad_block=int(ch[0]), ang_block=int(ch[1]), bwd_block=int(ch[2]), mlp_ctas_per_sm=int(ch[3]),
                     eval_ms_before=b.value, eval_ms_after=a.value)
+
+    def launch_config(self) -> dict:
+        """Current launch shapes of the evaluation kernels and the last autotuning landscape
+        (sl_get_launch_config)."""
+        cfg = np.zeros(8, dtype=np.int32)
+        land = np.zeros(16)
+        _check(lib().sl_get_launch_config(self.handle, _ptr(cfg), _ptr(land)))
+        names = ("radial", "angular", "network", "backward")
+        return dict(crad_block=int(cfg[0]), crad_minb=int(cfg[1]), ang_block=int(cfg[2]), ang_minb=int(cfg[3]),
+                    bwd_block=int(cfg[4]), bwd_minb=int(cfg[5]), mlp_ctas_per_sm=int(cfg[6]),
+                    landscape_ms=[{k: float(land[4 * c + g]) for g, k in enumerate(names)} for c in range(4)
+                                  if land[4 * c] >= 0])
 
     def midpoint_evaluations(self) -> int:
         v = C.c_int64()

@@ -318,6 +318,13 @@ def test_autotune_leaves_state_and_results_unchanged(params, prec):
     q = 64 if prec == S.SL_PREC_FP64 else 128
     assert info["crad_block"] in (64, 128) and info["ang_block"] in (q // 2, q) and info["bwd_block"] in (q // 2, q)
     assert info["mlp_ctas_per_sm"] in (1, 2) and info["eval_ms_after"] <= info["eval_ms_before"] * 1.5
+    # the search covered block sizes and (mixed precision) register budgets; the library
+    # checked that every candidate left forces and fields unchanged bit for bit
+    cfg = a.launch_config()
+    assert len(cfg["landscape_ms"]) == (2 if prec == S.SL_PREC_FP64 else 4)
+    assert cfg["crad_minb"] in (0, 3) and cfg["ang_minb"] in (0, 5) and cfg["bwd_minb"] in (0, 4)
+    if prec == S.SL_PREC_FP64:
+        assert cfg["crad_minb"] == cfg["ang_minb"] == cfg["bwd_minb"] == 0
     st1 = a.get_state()
     for k in ("positions", "velocities", "spins", "forces", "fields"):
         assert np.array_equal(st0[k], st1[k]), k

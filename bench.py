@@ -293,19 +293,21 @@ def forced_rebuild_ms(sysm, repeats=3):
 
 
 def run_serving(args, params, replica_offset=0):
-    """Sweep requests (B20 replicas of 12^3-20^3 cells, 50-320 K, 0-0.5 T, 100-400 steps) arriving
+    """Sweep requests (B20 replicas of 12^3-40^3 cells, 50-320 K, 0-0.5 T, 200-2000 steps) arriving
     as a Poisson process, served with admission by free device memory and chunked batching."""
     from paper_2606_14073_gb300.serving import GpuBackend, Server, poisson_requests
-    reqs = poisson_requests(args.serve_requests, args.serve_rate, cells=(12, 20), steps=(100, 400))
+    reqs = poisson_requests(args.serve_requests, args.serve_rate)
     for r in reqs:
         r.replica += replica_offset
     be = GpuBackend(params)
     out = Server(be, max_active=32, chunk=50).run(reqs)
+    stats = be.batch_stats()
+    be.close()
     return {"requests": out["requests"], "arrival_rate_per_s": args.serve_rate,
             "throughput_atom_steps_per_s": out["throughput_atom_steps_per_s"],
             "latency_p50_s": out["latency_p50_s"], "latency_p99_s": out["latency_p99_s"],
-            "makespan_s": out["makespan_s"], "memory_waits": out["memory_waits"],
-            "recipe": "cells U{12..20}, T U(50,320) K, B_z U(0,0.5) T, steps U{100..400}, mixed precision"}
+            "makespan_s": out["makespan_s"], "memory_waits": out["memory_waits"], "batch": stats,
+            "recipe": "cells U{12..40}, T U(50,320) K, B_z U(0,0.5) T, steps U{200..2000}, mixed precision"}
 
 
 def run_sweep(args):
@@ -484,7 +486,7 @@ def run_replicas(args):
                 for k, w in enumerate(wls)]
         bt = S.Batch(syss)
         bt.step(args.warmup, DT, Ts, Bs)
-        l0 = sum(s.info()["n_launches"] for s in syss)
+        st0 = bt.stats()
         torch.cuda.synchronize()
         clocks = ClockSampler(0)
         clocks.start()
@@ -492,14 +494,28 @@ def run_replicas(args):
         bt.step(steps, DT, Ts, Bs)     # returns after every replica's stream is done
         secs = time.perf_counter() - t0
         clk = clocks.stop()
-        launches = sum(s.info()["n_launches"] for s in syss) - l0
+        st1 = bt.stats()
         bt.destroy()
         for s in syss:
             s.destroy()
-        return atoms * steps / secs, secs, clk, launches
+        return atoms * steps / secs, secs, clk, st1["kernel_launches"] - st0["kernel_launches"], \
+            {k: st1[k] - st0[k] for k in st1}
 
-    v64, s64, _, _ = timed(S.SL_PREC_FP64, args.fp64_steps)
-    value, secs, clk, launches = timed(S.SL_PREC_MIXED, args.steps)
+    def single(steps):
+        """One 884,736-atom cube (48^3 cells), timed the same way (host-synchronous call)."""
+        w = W.fege_884k()
+        s = S.system_from_workload(w, params, precision=S.SL_PREC_MIXED, steps_per_graph=args.graph_steps)
+        s.step(args.warmup, DT, 300.0, (0, 0, 0))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(steps, DT, 300.0, (0, 0, 0))
+        secs = time.perf_counter() - t0
+        s.destroy()
+        return w.n * steps / secs
+
+    v64, s64, _, _, _ = timed(S.SL_PREC_FP64, args.fp64_steps)
+    value, secs, clk, launches, bstats = timed(S.SL_PREC_MIXED, args.steps)
+    v1 = single(args.steps)
     line = _common_line(args, value, secs * 1e3, args.steps, "fege_b20_64_replicas_4096_262144",
                         {"atoms": atoms, "replicas": 64, "precision": "mixed", "dt_fs": DT,
                          "T_K": "U(100,300) per replica", "B_T": "z, U(0,0.5) per replica",
@@ -507,6 +523,10 @@ def run_replicas(args):
                          "parallelism": "replicas x1 GPU, one batched call"},
                         clk, launches,
                         {"mode": "replicas", "timing": "wall clock around one sl_batch_step (host-synchronous)",
+                         "batch": bstats,
+                         "single_system": {"value": v1, "unit": UNIT, "atoms": 884736,
+                                           "timing": "wall clock around one sl_step of the same steps"},
+                         "vs_single_system": value / v1,
                          "fp64": {"value": v64, "unit": UNIT, "steps": args.fp64_steps},
                          "mixed_error_vs_fp64": err,
                          "replica_atoms": [int(w.n) for w in wls]})

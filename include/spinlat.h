@@ -248,8 +248,9 @@ int sl_autotune(sl_system *sys, int32_t repeats, int32_t *chosen, double *eval_m
 
 /* The evaluation kernels' current launch configuration, cfg[8]: radial block (threads),
  * radial register budget (0: default of 4 blocks per SM, 3: 3 blocks per SM), angular
- * block, angular budget (0: default, 5: 5 blocks per SM), backward block, backward budget
- * (0: default of 2 blocks per SM, 4: 4 blocks per SM), network CTAs per SM, 0.  landscape
+ * block, angular budget (0: default of 4 blocks per SM, 1: unconstrained), backward block,
+ * backward budget (0: default of 4 blocks per SM, 3: 3 blocks per SM), network CTAs per
+ * SM, 0.  landscape
  * [16] (may be NULL): the last sl_autotune's median ms of the radial, angular, network and
  * backward kernels under each of its 4 candidate shapes (candidate-major; -1 where not
  * timed: never tuned, or FP64 mode, which has 2 candidates).  Candidates: 0 half blocks and
@@ -292,20 +293,50 @@ void sl_destroy_system(sl_system *sys);
 const char *sl_last_error(void);
 
 /* ---------------------------------------------------------------- batches
- * Independent replicas (temperature/field sweeps) stepped together: one launch of
- * each kernel covers every replica's atoms.  All systems of a batch must share the
- * precision mode and the model parameters.  Replicas keep their own state, RNG key
- * and neighbour lists; a replica's trajectory is bit-identical alone and in a batch. */
+ * Independent replicas (temperature/field sweeps) stepped together, in a fixed number of
+ * slots.  Replicas keep their own state, RNG key and neighbour lists; a replica's trajectory
+ * is bit-identical alone and in a batch, whatever else the batch holds.
+ *
+ * When the replicas taking part in a call share the device and the model parameters and none
+ * uses the midpoint iteration, they take the fused step: each kernel of the step is ONE
+ * launch over every replica (a persistent grid walking a device table of per-slot argument
+ * blocks; a replica's blocks are those of its own launches).  A one-block plan kernel at the
+ * start of every step builds the step's work maps from per-slot budgets of steps left, so
+ * replicas with different step counts share the launches until each budget is spent, and the
+ * two captured graphs (steps_per_graph steps, one step) survive admissions and retirements:
+ * sl_batch_set rewrites a slot's table entry, not the graphs (up to the atom capacity, see
+ * sl_batch_reserve).  Otherwise the replicas run on their own streams (one fork/join graph
+ * when every occupied slot takes part).
+ *
+ * A system must leave every batch (sl_batch_set(b, slot, NULL)) before it is destroyed.  All
+ * systems of a batch share the precision mode; the coloured sweep steps alone. */
 typedef struct sl_batch sl_batch;
 
+/* k slots (1 <= k <= 4096); systems[i] may be NULL (an empty slot); no system in two slots. */
 int sl_batch_create(sl_system *const *systems, int32_t k, sl_batch **out);
-/* n_steps[k]: steps each replica still takes in this call (0 = idle this call);
- * dt/T/B per replica. */
+/* Put sys into slot (NULL: empty the slot).  SL_EINVAL for a slot outside [0, k), a precision
+ * mode other than the occupied slots', or a system that already holds another slot. */
+int sl_batch_set(sl_batch *b, int32_t slot, sl_system *sys);
+/* n_steps[k]: steps each slot's replica takes in this call (0 = idle; must be 0 for an empty
+ * slot); dt/T/B per slot.  Returns after every replica's steps are done; on a list overflow or a
+ * non-finite value the failing replicas go back to their state before the call, the others
+ * keep their steps, and the first error is returned. */
 int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt_fs, const double *T_K,
                   const double *B_tesla /* [k][3] */);
-/* Number of single graph launches that advanced every replica of the batch together
- * (each covers steps_per_graph steps of all replicas). */
+/* Number of graph launches of the batch stream (fused graphs, or fork/join graphs that
+ * advanced every replica together by steps_per_graph steps). */
 int sl_batch_graph_launches(const sl_batch *b, int64_t *launches);
+/* stats[7]: graph launches, captures of the fused graphs, fused steps executed (each advances
+ * every replica with budget left by one step), kernel launches queued by the batch's calls,
+ * calls that took the fused step, calls that ran the replicas on their own streams, and the
+ * atom capacity the fused launches are sized for. */
+int sl_batch_stats(const sl_batch *b, int64_t *stats);
+/* Size the fused launches for up to `atoms` atoms over all slots (default: 65,536, raised to
+ * the next power of two whenever the slots' atoms exceed it).  The kernels of the step that
+ * take one work item per block launch that many blocks whatever the slots hold (blocks past
+ * the current work return at once), so the captured graphs survive every admission up to
+ * the capacity; growing it captures them again.  SL_EINVAL for a negative count. */
+int sl_batch_reserve(sl_batch *b, int64_t atoms);
 void sl_batch_destroy(sl_batch *b);
 
 /* ---------------------------------------------------------------- no device allocation

@@ -24,6 +24,7 @@
 
 #include "../../include/spinlat.h"
 #include "sl_internal.h"
+#include "sl_batch.h"
 
 // NVTX range over a host-side call (shows up in profilers that record NVTX; a no-op otherwise).
 struct NvtxRange {
@@ -37,18 +38,25 @@ struct sl_system {
     sl::Sys s;
 };
 
-// Replicas stepped together.  When every replica takes at least steps_per_graph steps in a
-// call, one captured graph holding all replicas' steps (each replica's kernels on its own
-// stream, forked from and joined to the batch stream) advances them all with a single
-// launch; otherwise each replica's own graphs are queued on its stream.
+// Replicas stepped together, in a fixed number of slots (null: empty).  When the replicas
+// taking part in a call share the device and the model and none uses the midpoint iteration,
+// they take the fused step (sl_batch.h): one launch of each kernel covers all of them, from
+// captured graphs over device tables that outlive admissions and retirements.  Otherwise,
+// when every occupied slot takes at least steps_per_graph steps, one captured graph holding
+// every replica's steps (each on its own stream, forked from and joined to the batch stream)
+// advances them together; else each replica's own graphs are queued on its stream.
 struct sl_batch {
-    std::vector<sl_system *> sys;
+    std::vector<sl_system *> sys;     // slots
     cudaStream_t stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;  // the fork/join graph
     int graph_steps = 0;
-    std::vector<uint64_t> versions;   // capture versions of the replicas when the graph was built
-    std::vector<cudaEvent_t> ev;      // fork/join events: [0] batch, [1 + i] replica i
+    std::vector<uint64_t> graph_uids;     // unique ids of the slots' systems when it was built (0: empty)
+    std::vector<uint64_t> versions;   // and their capture versions
+    std::vector<cudaEvent_t> ev;      // fork/join events: [0] batch, [1 + i] slot i
     int64_t graph_launches = 0;
+    int64_t fused_steps = 0, kernel_launches = 0, fused_calls = 0, replica_calls = 0;
+    int64_t reserve_atoms = 0;        // atoms the fused launches are sized for (sl_batch_reserve)
+    sl::FusedBatch fused;
     ~sl_batch() {
         if (graph) cudaGraphExecDestroy(graph);
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
@@ -139,6 +147,7 @@ void free_sys(sl::Sys &s) {
                     s.tex_acc, s.tex_m, s.tex_part, s.colour};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    sl::solo_free(s);
     if (s.h_par) cudaFreeHost(s.h_par);
     if (s.h_stage) cudaFreeHost(s.h_stage);
     if (s.h_status) cudaFreeHost(s.h_status);
@@ -452,6 +461,8 @@ int sl_create_system(const double *positions, const double *spins, const double 
     if (opt.device >= dev_count) return fail(SL_EINVAL, "device %d not present (%d devices)", opt.device, dev_count);
     if (opt.device >= 0 && (ce = cudaSetDevice(opt.device)) != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
     sl_system *sys = new (std::nothrow) sl_system();
+    static std::atomic<uint64_t> next_uid{1};
+    if (sys) sys->s.uid = next_uid.fetch_add(1);
     if (!sys) return fail(SL_ENOMEM, "host allocation failed");
     Sys &s = sys->s;
     cudaGetDevice(&s.device);
@@ -604,6 +615,7 @@ int sl_create_system(const double *positions, const double *spins, const double 
             (ce = cudaStreamSynchronize(st)))
             return bail(cuda_fail(ce, "upload"));
     }
+    if (sl::solo_refresh(s)) return bail(fail(SL_ENOMEM, "the system's argument tables"));
     const double B0[3] = {0, 0, 0};
     if ((rc = upload_params(s, 1.0, 0.0, B0)) || (rc = refresh_copies(s)) || (rc = evaluate(s, true, true, false)) ||
         (rc = check_status(s)))
@@ -1039,8 +1051,8 @@ int sl_autotune(sl_system *sys, int32_t repeats, int32_t *chosen, double *eval_m
         cand[c].bwd_block = half ? q / 2 : q;
         cand[c].mlp_ctas_per_sm = half ? 1 : 2;
         cand[c].crad_minb = var ? 3 : 0;
-        cand[c].ang_minb = var ? 5 : 0;
-        cand[c].bwd_minb = var ? 4 : 0;
+        cand[c].ang_minb = var ? 1 : 0;
+        cand[c].bwd_minb = var ? 3 : 0;
     }
     double ms0[5], msc[4][5];
     int rc;
@@ -1138,6 +1150,7 @@ int sl_set_atom_fields(sl_system *sys, const double *B_atoms) {
             cudaFree(s.Bat);
             s.Bat = nullptr;
             drop_graph();
+            if (sl::solo_refresh(s)) return fail(SL_ECUDA, "the system's argument tables");
         }
         return SL_OK;
     }
@@ -1147,6 +1160,7 @@ int sl_set_atom_fields(sl_system *sys, const double *B_atoms) {
     if (!s.Bat) {
         if ((rc = dalloc(&s.Bat, (size_t)(s.n > 0 ? s.n : 1)))) return rc;
         drop_graph();
+        if (sl::solo_refresh(s)) return fail(SL_ECUDA, "the system's argument tables");
     }
     if (s.n > 0 && (rc = upload_vec(s, s.Bat, B_atoms, false))) return rc;
     return SL_OK;
@@ -1347,12 +1361,24 @@ void sl_destroy_system(sl_system *sys) {
 }
 
 // ---------------------------------------------------------------- batches
+// precision of the batch's occupied slots (-1: none)
+static int batch_precision(const sl_batch *b, int skip = -1) {
+    for (int i = 0; i < (int)b->sys.size(); ++i)
+        if (i != skip && b->sys[i]) return b->sys[i]->s.prec;
+    return -1;
+}
+
 int sl_batch_create(sl_system *const *systems, int32_t k, sl_batch **out) {
     if (!out || k < 1 || !systems) return fail(SL_EINVAL, "bad arguments");
     *out = nullptr;
+    if (k > sl::FUSED_MAX_SLOTS) return fail(SL_EINVAL, "at most %d slots in a batch", sl::FUSED_MAX_SLOTS);
+    int prec = -1;
     for (int i = 0; i < k; ++i) {
-        if (!systems[i]) return fail(SL_EINVAL, "NULL system in batch");
-        if (systems[i]->s.prec != systems[0]->s.prec) return fail(SL_EINVAL, "mixed precision modes in a batch");
+        if (!systems[i]) continue;
+        if (prec >= 0 && systems[i]->s.prec != prec) return fail(SL_EINVAL, "mixed precision modes in a batch");
+        prec = systems[i]->s.prec;
+        for (int j = 0; j < i; ++j)
+            if (systems[j] == systems[i]) return fail(SL_EINVAL, "a system in two slots of a batch");
     }
     sl_batch *b = new (std::nothrow) sl_batch();
     if (!b) return fail(SL_ENOMEM, "host allocation failed");
@@ -1361,27 +1387,37 @@ int sl_batch_create(sl_system *const *systems, int32_t k, sl_batch **out) {
     return SL_OK;
 }
 
-// Build (or reuse) the batch graph of g steps for every replica.
+int sl_batch_set(sl_batch *b, int32_t slot, sl_system *sys) {
+    if (!b) return fail(SL_EINVAL, "NULL batch");
+    if (slot < 0 || slot >= (int)b->sys.size()) return fail(SL_EINVAL, "slot %d outside [0, %d)", slot, (int)b->sys.size());
+    if (sys) {
+        const int prec = batch_precision(b, slot);
+        if (prec >= 0 && sys->s.prec != prec) return fail(SL_EINVAL, "mixed precision modes in a batch");
+        for (int i = 0; i < (int)b->sys.size(); ++i)
+            if (i != slot && b->sys[i] == sys) return fail(SL_EINVAL, "the system already holds slot %d", i);
+    }
+    b->sys[slot] = sys;
+    return SL_OK;
+}
+
+// Build (or reuse) the fork/join graph of g steps for every occupied slot.
 static int batch_graph(sl_batch *b, int g) {
     const int k = (int)b->sys.size();
-    bool fresh = b->graph && b->graph_steps == g && (int)b->versions.size() == k;
-    for (int i = 0; fresh && i < k; ++i) fresh = b->versions[i] == b->sys[i]->s.capture_version;
+    // systems are told apart by id: one created after another was destroyed may reuse its address
+    bool fresh = b->graph && b->graph_steps == g && (int)b->graph_uids.size() == k;
+    for (int i = 0; fresh && i < k; ++i)
+        fresh = b->graph_uids[i] == (b->sys[i] ? b->sys[i]->s.uid : 0) &&
+                (!b->sys[i] || b->versions[i] == b->sys[i]->s.capture_version);
     if (fresh) return SL_OK;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
-    cudaSetDevice(b->sys[0]->s.device);
-    if (!b->stream) CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
-    if ((int)b->ev.size() != k + 1) {
-        for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
-        b->ev.assign((size_t)k + 1, nullptr);
-        for (auto &e : b->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    }
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     CK(cudaEventRecord(b->ev[0], b->stream));
     for (int i = 0; i < k; ++i) {
+        if (!b->sys[i]) continue;
         sl::Sys &s = b->sys[i]->s;
         CK(cudaStreamWaitEvent(s.stream, b->ev[0], 0));
         for (int t = 0; t < g; ++t) enqueue_step(s);
@@ -1394,8 +1430,109 @@ static int batch_graph(sl_batch *b, int g) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "batch graph instantiate");
     b->graph_steps = g;
-    b->versions.resize((size_t)k);
-    for (int i = 0; i < k; ++i) b->versions[i] = b->sys[i]->s.capture_version;
+    b->graph_uids.assign((size_t)k, 0);
+    b->versions.assign((size_t)k, 0);
+    for (int i = 0; i < k; ++i)
+        if (b->sys[i]) {
+            b->graph_uids[i] = b->sys[i]->s.uid;
+            b->versions[i] = b->sys[i]->s.capture_version;
+        }
+    return SL_OK;
+}
+
+// Whether the replicas taking part can take the fused step: one device, one model, no
+// midpoint iteration.
+static bool fusable(const sl_batch *b, const std::vector<int> &active) {
+    if (active.empty()) return false;
+    const sl::Sys &m = b->sys[active[0]]->s;
+    for (int i : active) {
+        const sl::Sys &s = b->sys[i]->s;
+        if (s.device != m.device || s.mid_iters > 0) return false;
+        if (std::memcmp(&s.pd, &m.pd, sizeof m.pd) != 0 || std::memcmp(&s.pf, &m.pf, sizeof m.pf) != 0) return false;
+    }
+    return true;
+}
+
+// The fused step for the replicas taking part: their budgets (n_steps) go to the device, then
+// g-step graphs and one-step graphs run until the largest budget is spent.
+static int fused_steps(sl_batch *b, const std::vector<int> &active, const int64_t *n_steps) {
+    const int k = (int)b->sys.size();
+    const sl::Sys &m = b->sys[active[0]]->s;
+    sl::FusedBatch &f = b->fused;
+    if (!f.ready(m.prec, k, m.device) && !f.setup(m.prec, k, m.device))
+        return fail(SL_ENOMEM, "fused batch tables (%d slots)", k);
+    for (int i = 0; i < k; ++i) f.assign(i, b->sys[i] ? &b->sys[i]->s : nullptr);
+    f.reserve(b->reserve_atoms);
+    std::vector<int64_t> left((size_t)k, 0);
+    int64_t most = 0;
+    for (int i : active) {
+        left[(size_t)i] = n_steps[i];
+        most = std::max(most, n_steps[i]);
+    }
+    CK(f.upload(left.data(), b->stream));   // may grow the grids, which drops the graphs
+    const int g = std::max(1, m.steps_per_graph);
+    if (!f.graphs(g, m, b->stream)) {
+        cudaGetLastError();
+        return fail(SL_ECUDA, "fused batch graph capture");
+    }
+    for (int i : active) {   // the batch stream waits for each replica's uploads
+        sl::Sys &s = b->sys[i]->s;
+        CK(cudaEventRecord(b->ev[1 + i], s.stream));
+        CK(cudaStreamWaitEvent(b->stream, b->ev[1 + i], 0));
+    }
+    for (int64_t r = 0; r < most / g; ++r) CK(cudaGraphLaunch(f.graph_g, b->stream));
+    for (int64_t r = 0; r < most % g; ++r) CK(cudaGraphLaunch(f.graph_1, b->stream));
+    b->graph_launches += most / g + most % g;
+    b->fused_steps += most;
+    b->kernel_launches += most * sl::FUSED_LAUNCHES_PER_STEP;
+    ++b->fused_calls;
+    CK(cudaEventRecord(b->ev[0], b->stream));
+    for (int i : active) CK(cudaStreamWaitEvent(b->sys[i]->s.stream, b->ev[0], 0));   // and each replica waits for it
+    return SL_OK;
+}
+
+// Replicas on their own streams: the fork/join graph when every occupied slot takes part,
+// then each replica's own graphs and single steps for the rest.
+static int replica_steps(sl_batch *b, const std::vector<int> &active, const int64_t *n_steps) {
+    const int k = (int)b->sys.size();
+    int occupied = 0;
+    for (int i = 0; i < k; ++i) occupied += b->sys[i] != nullptr;
+    int rc;
+    const int g = b->sys[active[0]]->s.steps_per_graph;
+    bool common = g > 0 && (int)active.size() == occupied;
+    int64_t shared = INT64_MAX;
+    for (int i : active) {
+        const sl::Sys &s = b->sys[i]->s;
+        common = common && s.steps_per_graph == g && s.device == b->sys[active[0]]->s.device;
+        shared = std::min<int64_t>(shared, n_steps[i]);
+    }
+    const int64_t rounds = common ? shared / g : 0;
+    if (rounds > 0) {
+        if ((rc = batch_graph(b, g))) return rc;
+        for (int i : active) {   // the batch stream waits for each replica's uploads
+            sl::Sys &s = b->sys[i]->s;
+            CK(cudaEventRecord(b->ev[1 + i], s.stream));
+            CK(cudaStreamWaitEvent(b->stream, b->ev[1 + i], 0));
+        }
+        for (int64_t r = 0; r < rounds; ++r) CK(cudaGraphLaunch(b->graph, b->stream));
+        b->graph_launches += rounds;
+        CK(cudaEventRecord(b->ev[0], b->stream));
+        for (int i : active) {   // and each replica's stream waits for the batch
+            sl::Sys &s = b->sys[i]->s;
+            CK(cudaStreamWaitEvent(s.stream, b->ev[0], 0));
+            s.n_launches += rounds * g * kernels_per_step(s);
+            b->kernel_launches += rounds * g * kernels_per_step(s);
+        }
+    }
+    for (int i : active) {
+        sl::Sys &s = b->sys[i]->s;
+        const int64_t left = n_steps[i] - rounds * g;
+        if (left > 0) {
+            if ((rc = queue_steps(s, left))) return rc;
+            b->kernel_launches += left * kernels_per_step(s);
+        }
+    }
+    ++b->replica_calls;
     return SL_OK;
 }
 
@@ -1403,15 +1540,19 @@ int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt, const d
     NvtxRange nvtx_range("sl_batch_step");
     if (!b || !n_steps || !dt || !T || !B) return fail(SL_EINVAL, "NULL argument");
     const int k = (int)b->sys.size();
-    for (int i = 0; i < k; ++i)
-        if (b->sys[i]->s.sts) return fail(SL_EINVAL, "replica %d uses the coloured sweep, which steps alone", i);
     for (int i = 0; i < k; ++i) {
+        if (!b->sys[i]) {
+            if (n_steps[i] != 0) return fail(SL_EINVAL, "steps for empty slot %d", i);
+            continue;
+        }
+        if (b->sys[i]->s.sts) return fail(SL_EINVAL, "replica %d uses the coloured sweep, which steps alone", i);
         if (n_steps[i] < 0 || !(dt[i] > 0) || !(T[i] >= 0) || !std::isfinite(dt[i]) || !std::isfinite(T[i]))
             return fail(SL_EINVAL, "bad step arguments for replica %d", i);
     }
     int rc;
     std::vector<int> active;
     for (int i = 0; i < k; ++i) {
+        if (!b->sys[i]) continue;
         sl::Sys &s = b->sys[i]->s;
         cudaSetDevice(s.device);
         if ((rc = upload_params(s, dt[i], T[i], B + 3 * i))) return rc;
@@ -1420,38 +1561,16 @@ int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt, const d
         if ((rc = snapshot_state(s))) return rc;
         active.push_back(i);
     }
-    // the common graph: every replica active, on one device, with the same steps per graph
-    const int g = b->sys[0]->s.steps_per_graph;
-    bool common = g > 0 && (int)active.size() == k;
-    int64_t shared = INT64_MAX;
-    for (int i = 0; common && i < k; ++i) {
-        const sl::Sys &s = b->sys[i]->s;
-        common = s.steps_per_graph == g && s.device == b->sys[0]->s.device;
-        shared = std::min<int64_t>(shared, n_steps[i]);
+    if (active.empty()) return SL_OK;
+    cudaSetDevice(b->sys[active[0]]->s.device);
+    if (!b->stream) CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    if ((int)b->ev.size() != k + 1) {
+        for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+        b->ev.assign((size_t)k + 1, nullptr);
+        for (auto &e : b->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    int64_t rounds = common ? shared / g : 0;
-    if (rounds > 0) {
-        if ((rc = batch_graph(b, g))) return rc;
-        for (int i = 0; i < k; ++i) {   // the batch stream waits for each replica's uploads
-            sl::Sys &s = b->sys[i]->s;
-            CK(cudaEventRecord(b->ev[1 + i], s.stream));
-            CK(cudaStreamWaitEvent(b->stream, b->ev[1 + i], 0));
-        }
-        for (int64_t r = 0; r < rounds; ++r) CK(cudaGraphLaunch(b->graph, b->stream));
-        b->graph_launches += rounds;
-        CK(cudaEventRecord(b->ev[0], b->stream));
-        for (int i = 0; i < k; ++i) {   // and each replica's stream waits for the batch
-            sl::Sys &s = b->sys[i]->s;
-            CK(cudaStreamWaitEvent(s.stream, b->ev[0], 0));
-            s.n_launches += rounds * g * kernels_per_step(s);
-        }
-    }
-    // the rest: each replica's own graphs and single steps on its own stream
-    for (int i : active) {
-        sl::Sys &s = b->sys[i]->s;
-        const int64_t left = n_steps[i] - rounds * g;
-        if (left > 0 && (rc = queue_steps(s, left))) return rc;
-    }
+    rc = fusable(b, active) ? fused_steps(b, active, n_steps) : replica_steps(b, active, n_steps);
+    if (rc) return rc;
     // every replica is finished (and restored where it failed) before the first error is returned
     int first = SL_OK;
     std::string first_msg;
@@ -1467,13 +1586,36 @@ int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt, const d
     return SL_OK;
 }
 
+int sl_batch_reserve(sl_batch *b, int64_t atoms) {
+    if (!b || atoms < 0) return fail(SL_EINVAL, "bad arguments");
+    b->reserve_atoms = std::max(b->reserve_atoms, atoms);
+    return SL_OK;
+}
+
 int sl_batch_graph_launches(const sl_batch *b, int64_t *launches) {
     if (!b || !launches) return fail(SL_EINVAL, "NULL argument");
     *launches = b->graph_launches;
     return SL_OK;
 }
 
-void sl_batch_destroy(sl_batch *b) { delete b; }
+int sl_batch_stats(const sl_batch *b, int64_t *stats) {
+    if (!b || !stats) return fail(SL_EINVAL, "NULL argument");
+    stats[0] = b->graph_launches;
+    stats[1] = b->fused.captures;
+    stats[2] = b->fused_steps;
+    stats[3] = b->kernel_launches;
+    stats[4] = b->fused_calls;
+    stats[5] = b->replica_calls;
+    stats[6] = b->fused.atom_capacity();
+    return SL_OK;
+}
+
+void sl_batch_destroy(sl_batch *b) {
+    if (!b) return;
+    if (b->fused.device() >= 0) cudaSetDevice(b->fused.device());
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    delete b;
+}
 
 // ---------------------------------------------------------------- no device allocation
 int sl_descriptors_energies_noalloc(const double *positions4, const double *spins4, const int32_t *species,

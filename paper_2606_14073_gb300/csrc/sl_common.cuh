@@ -62,6 +62,36 @@ template <> struct V4<float> { using t = float4; };
 template <> struct V4<double> { using t = double4; };
 template <typename R> using v4 = typename V4<R>::t;
 
+// Loads through the read-only (non-coherent) path, for data the calling kernel never writes.
+// The kernels read their argument blocks from tables, so the compiler cannot prove that by
+// itself from the pointers.
+__device__ __forceinline__ float4 ro(const float4 *p) { return __ldg(p); }
+__device__ __forceinline__ int4 ro(const int4 *p) { return __ldg(p); }
+__device__ __forceinline__ uchar4 ro(const uchar4 *p) { return __ldg(p); }
+__device__ __forceinline__ int ro(const int *p) { return __ldg(p); }
+__device__ __forceinline__ unsigned ro(const unsigned *p) { return __ldg(p); }
+__device__ __forceinline__ unsigned short ro(const unsigned short *p) { return __ldg(p); }
+__device__ __forceinline__ float ro(const float *p) { return __ldg(p); }
+__device__ __forceinline__ double ro(const double *p) { return __ldg(p); }
+__device__ __forceinline__ double4 ro(const double4 *p) {
+    const double2 lo = __ldg(reinterpret_cast<const double2 *>(p)), hi = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return make_double4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// Stores typed as global-memory stores.  The kernels read their argument blocks from shared
+// memory; a store through a plain (generic) pointer might, as far as the compiler can tell,
+// land there, and every argument would be read again after it.
+__device__ __forceinline__ void stg(int *p, int v) { __stwb(p, v); }
+__device__ __forceinline__ void stg(unsigned short *p, unsigned short v) { __stwb(p, v); }
+__device__ __forceinline__ void stg(float *p, float v) { __stwb(p, v); }
+__device__ __forceinline__ void stg(double *p, double v) { __stwb(p, v); }
+__device__ __forceinline__ void stg(float4 *p, const float4 &v) { __stwb(p, v); }
+__device__ __forceinline__ void stg(int4 *p, const int4 &v) { __stwb(p, v); }
+__device__ __forceinline__ void stg(double4 *p, const double4 &v) {
+    __stwb(reinterpret_cast<double2 *>(p), make_double2(v.x, v.y));
+    __stwb(reinterpret_cast<double2 *>(p) + 1, make_double2(v.z, v.w));
+}
+
 template <typename R>
 __device__ __forceinline__ R rint_(R x);
 template <>

@@ -21,10 +21,13 @@
 //              dE_i/dS_i, virial) are reduced over the quad.
 // The force/field gather (sl_integrate.cu) then reads, for atom k, the records of
 // its in-cutoff slots only.
+#include <cstddef>
 #include <mutex>
 
 #include "sl_internal.h"
 #include "sl_eval2.cuh"
+#include "sl_batch.h"
+#include "sl_fused.cuh"
 
 namespace sl {
 
@@ -174,12 +177,14 @@ __device__ __forceinline__ void rad_accumulate(const NepDev<R> &P, const v4<R> &
     }
 }
 
-// Row of an in-cutoff pair, or -1 (angular rows full: only after a list overflow).
+// Row of an in-cutoff pair, or -1 (angular rows full: only after a list overflow, which ovf
+// records; the atom reports it once its rows are written).
 template <typename R>
-__device__ __forceinline__ int take_row(const NepDev<R> &P, const Eval2Args<R> &a, R d2, int &na, int &nr) {
+__device__ __forceinline__ int take_row(const NepDev<R> &P, const Eval2Args<R> &a, R d2, int &na, int &nr,
+                                        bool &ovf) {
     if (d2 < P.rc_a2) {
         if (na >= a.cap_ang) {
-            atomicOr(a.status, ST_NBR_OVERFLOW);
+            ovf = true;
             return -1;
         }
         return na++;
@@ -196,7 +201,7 @@ __device__ __forceinline__ void mark_slot(uint32_t (*sm)[128], int slot) {
 template <typename R, int TI, int TJ>
 __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, const v4<R> &pi,
                                              const v4<R> &si, int lo0, int hi0, int lo1, int hi1, int &na, int &nr,
-                                             uint32_t (*smask)[128]) {
+                                             bool &ovf, uint32_t (*smask)[128]) {
     RadSums<R> b;
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
@@ -248,10 +253,10 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
                 sep(a.box, pi, pp[u], dx, dy, dz);
                 const R d2 = dx * dx + dy * dy + dz * dz;
                 if (!(d2 < P.rc_r2)) continue;
-                const int row = take_row(P, a, d2, na, nr);
+                const int row = take_row(P, a, d2, na, nr, ovf);
                 if (row < 0) continue;
-                a.clj[(int64_t)row * N + i] = jj[u];
-                a.cls[(int64_t)row * N + i] = (uint16_t)((c + u) | (tt[u] << 8));
+                stg(a.clj + (int64_t)row * N + i, jj[u]);
+                stg(a.cls + (int64_t)row * N + i, (uint16_t)((c + u) | (tt[u] << 8)));
                 mark_slot(smask, c + u);
                 rad_accumulate(P, si, ss[u], dx, dy, dz, d2, b);
             }
@@ -285,10 +290,10 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
                 sep(a.box, pi, pp[u], dx, dy, dz);
                 const R d2 = dx * dx + dy * dy + dz * dz;
                 if (!(d2 < P.rc_r2)) continue;
-                const int row = take_row(P, a, d2, na, nr);
+                const int row = take_row(P, a, d2, na, nr, ovf);
                 if (row < 0) continue;
-                a.clj[(int64_t)row * N + i] = jj[u];
-                a.cls[(int64_t)row * N + i] = (uint16_t)((c + u) | (tt[u] << 8));
+                stg(a.clj + (int64_t)row * N + i, jj[u]);
+                stg(a.cls + (int64_t)row * N + i, (uint16_t)((c + u) | (tt[u] << 8)));
                 mark_slot(smask, c + u);
             }
         }
@@ -328,7 +333,7 @@ __device__ __forceinline__ void crad_species(const NepDev<R> &P, const Eval2Args
                                                                                                  : b.b34[k].y;
                 v += P.c[TI][TJ][GG[g]][n][k] * bgk;
             }
-            a.q[(GQ[g] + n) * a.qs + i] = v;
+            stg(a.q + (GQ[g] + n) * a.qs + i, v);
         }
     }
 }
@@ -340,26 +345,32 @@ __device__ __forceinline__ void crad_atom(const NepDev<R> &P, const Eval2Args<R>
     const v4<R> pi = a.pos[i], si = a.spin[i];
     const int4 sg = a.seg[i];
     int na = 0, nr = 0;
+    bool ovf = false;
     for (int w = 0; w < a.maskw; ++w) smask[w][threadIdx.x] = 0u;
-    crad_species<R, TI, 0>(P, a, i, pi, si, 0, sg.x, sg.y, sg.z, na, nr, smask);
+    crad_species<R, TI, 0>(P, a, i, pi, si, 0, sg.x, sg.y, sg.z, na, nr, ovf, smask);
     const int na0 = na, nr0 = nr;
-    crad_species<R, TI, 1>(P, a, i, pi, si, sg.x, sg.y, sg.z, sg.w, na, nr, smask);
-    a.cnt[i] = make_int4(na0, na, nr0, nr);
-    for (int w = 0; w < a.maskw; ++w) a.mask[(int64_t)w * N + i] = smask[w][threadIdx.x];
-    a.q[Q_O * a.qs + i] = si.x * si.x + si.y * si.y + si.z * si.z;
+    crad_species<R, TI, 1>(P, a, i, pi, si, sg.x, sg.y, sg.z, sg.w, na, nr, ovf, smask);
+    if (ovf) atomicOr(a.status, ST_NBR_OVERFLOW);
+    stg(a.cnt + i, make_int4(na0, na, nr0, nr));
+    for (int w = 0; w < a.maskw; ++w) stg(reinterpret_cast<int *>(a.mask) + (int64_t)w * N + i, (int)smask[w][threadIdx.x]);
+    stg(a.q + Q_O * a.qs + i, si.x * si.x + si.y * si.y + si.z * si.z);
 }
 
 // MINB: minimum resident blocks per SM the register allocation is held to (the autotuner's
 // register-budget dimension); the default is the first value of each kernel's list below.
-template <typename R, int MINB = sizeof(R) == 4 ? 4 : 2>
-__global__ void __launch_bounds__(128, MINB) k_crad(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+template <typename R>
+__device__ __forceinline__ void crad_body(const NepDev<R> &P, const Eval2Args<R> &args, int64_t blk,
+                                          uint32_t (*smask)[128]) {
+    // the arguments as values: read once from the block's copy, so nothing in the loops below
+    // depends on where they are stored
+    const Eval2Args<R> a = args;
     if (a.skip && *a.skip) return;
-    __shared__ uint32_t smask[MASKW_MAX][128];   // blocks have at most 128 threads
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = blk * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     if (i < a.n_fe) crad_atom<R, 0>(P, a, i, smask);
     else crad_atom<R, 1>(P, a, i, smask);
 }
+
 
 // ------------------------------------------------------------------ k_ang_fwd
 // stage of one angular pair: (g_n, s g_n) interleaved for n = 0..4, pad (2), then the 24
@@ -398,13 +409,16 @@ __device__ __forceinline__ void ang_stage_fwd(const NepDev<R> &P, const Eval2Arg
     }
 }
 
-template <typename R, int MINB = 1>
-__global__ void __launch_bounds__(128, MINB) k_ang_fwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+template <typename R>
+__device__ __forceinline__ void ang_fwd_body(const NepDev<R> &P, const Eval2Args<R> &args, int64_t blk,
+                                             unsigned char *smem_raw) {
+    // the arguments as values: read once from the block's copy, so nothing in the loops below
+    // depends on where they are stored
+    const Eval2Args<R> a = args;
     if (a.skip && *a.skip) return;
-    extern __shared__ __align__(32) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int quad = lane >> 2, ql = lane & 3;
-    const int64_t i = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 8 + quad;
+    const int64_t i = (blk * (blockDim.x >> 5) + warp) * 8 + quad;
     const bool valid = i < a.n;
     R *stage = reinterpret_cast<R *>(smem_raw) + (warp * 8 + quad) * FQUAD;
     const int64_t N = a.n;
@@ -496,7 +510,7 @@ __global__ void __launch_bounds__(128, MINB) k_ang_fwd(const __grid_constant__ N
             w0.x = BB[m][0].x; w0.y = BB[m][0].y; w0.z = BB[m][1].x; w0.w = BB[m][1].y;
             w1.x = BB[m][2].x; w1.y = BB[m][2].y; w1.z = BB[m][3].x; w1.w = BB[m][3].y;
             w2.x = BB[m][4].x; w2.y = BB[m][4].y; w2.z = R(0); w2.w = R(0);
-            rec[0] = w0; rec[1] = w1; rec[2] = w2;
+            stg(rec, w0); stg(rec + 1, w1); stg(rec + 2, w2);
         }
 #pragma unroll
         for (int n = 0; n < NCH; ++n) {
@@ -529,11 +543,12 @@ __global__ void __launch_bounds__(128, MINB) k_ang_fwd(const __grid_constant__ N
                 va = ql == t ? qa[n][t] : va;
                 vs = ql == t ? qs[n][t] : vs;
             }
-            a.q[(int64_t)(Q_A + n * 4 + ql) * a.qs + i] = va;
-            a.q[(int64_t)(Q_SA + n * 4 + ql) * a.qs + i] = vs;
+            stg(a.q + (int64_t)(Q_A + n * 4 + ql) * a.qs + i, va);
+            stg(a.q + (int64_t)(Q_SA + n * 4 + ql) * a.qs + i, vs);
         }
     }
 }
+
 
 // ------------------------------------------------------------------ k_bwd (fused)
 // Quad per atom, lanes over pairs.  Shared memory per atom: the angular adjoints
@@ -678,10 +693,12 @@ __device__ __forceinline__ void bwd_pair(const NepDev<R> &P, const Eval2Args<R> 
         acc.w[3] -= dy * Dx; acc.w[4] -= dy * Dy; acc.w[5] -= dy * Dz;
         acc.w[6] -= dz * Dx; acc.w[7] -= dz * Dy; acc.w[8] -= dz * Dz;
     }
-    PairRec<R> rec;
-    rec.a.x = Dx; rec.a.y = Dy; rec.a.z = Dz; rec.a.w = Gx;
-    rec.b.x = Gy; rec.b.y = Gz; rec.b.z = R(0); rec.b.w = R(0);
-    a.pd[(int64_t)t * a.n + j] = rec;
+    PairRec<R> *rec = a.pd + (int64_t)t * a.n + j;
+    v4<R> ra, rb;
+    ra.x = Dx; ra.y = Dy; ra.z = Dz; ra.w = Gx;
+    rb.x = Gy; rb.y = Gz; rb.z = R(0); rb.w = R(0);
+    stg(&rec->a, ra);
+    stg(&rec->b, rb);
 }
 
 // rows lo, lo+4, ... of one range for lane ql.  Two-level prefetch: the list entry of the
@@ -695,24 +712,24 @@ __device__ __forceinline__ void bwd_rows(const NepDev<R> &P, const Eval2Args<R> 
     int j1 = 0, t1 = 0, j2 = 0, t2 = 0, j3 = 0, t3 = 0;
     v4<R> p1, s1, p2, s2;
     if (lo < hi) {
-        j1 = a.clj[(int64_t)lo * N + i];
-        t1 = a.cls[(int64_t)lo * N + i] >> 8;
+        j1 = ro(a.clj + (int64_t)lo * N + i);
+        t1 = ro(a.cls + (int64_t)lo * N + i) >> 8;
     }
     if (lo + 4 < hi) {
-        j2 = a.clj[(int64_t)(lo + 4) * N + i];
-        t2 = a.cls[(int64_t)(lo + 4) * N + i] >> 8;
+        j2 = ro(a.clj + (int64_t)(lo + 4) * N + i);
+        t2 = ro(a.cls + (int64_t)(lo + 4) * N + i) >> 8;
     }
     if (lo + 8 < hi) {
-        j3 = a.clj[(int64_t)(lo + 8) * N + i];
-        t3 = a.cls[(int64_t)(lo + 8) * N + i] >> 8;
+        j3 = ro(a.clj + (int64_t)(lo + 8) * N + i);
+        t3 = ro(a.cls + (int64_t)(lo + 8) * N + i) >> 8;
     }
     if (lo < hi) {
-        p1 = a.pos[j1];
-        s1 = a.spin[j1];
+        p1 = ro(a.pos + j1);
+        s1 = ro(a.spin + j1);
     }
     if (lo + 4 < hi) {
-        p2 = a.pos[j2];
-        s2 = a.spin[j2];
+        p2 = ro(a.pos + j2);
+        s2 = ro(a.spin + j2);
     }
     for (int row = lo; row < hi; row += 4) {
         const int j = j1, t = t1;
@@ -720,24 +737,27 @@ __device__ __forceinline__ void bwd_rows(const NepDev<R> &P, const Eval2Args<R> 
         j1 = j2; t1 = t2; p1 = p2; s1 = s2;
         j2 = j3; t2 = t3;
         if (row + 8 < hi) {
-            p2 = a.pos[j2];
-            s2 = a.spin[j2];
+            p2 = ro(a.pos + j2);
+            s2 = ro(a.spin + j2);
         }
         if (row + 12 < hi) {
-            j3 = a.clj[(int64_t)(row + 12) * N + i];
-            t3 = a.cls[(int64_t)(row + 12) * N + i] >> 8;
+            j3 = ro(a.clj + (int64_t)(row + 12) * N + i);
+            t3 = ro(a.cls + (int64_t)(row + 12) * N + i) >> 8;
         }
         bwd_pair<R, ANG>(P, a, ti, row < split ? 0 : 1, pi, si, pj, sj, j, t, sm, acc);
     }
 }
 
-template <typename R, int MINB = sizeof(R) == 4 ? 2 : 1>
-__global__ void __launch_bounds__(128, MINB) k_bwd(const __grid_constant__ NepDev<R> P, const Eval2Args<R> a) {
+template <typename R>
+__device__ __forceinline__ void bwd_body(const NepDev<R> &P, const Eval2Args<R> &args, int64_t blk,
+                                         unsigned char *smem_raw) {
+    // the arguments as values: read once from the block's copy, so nothing in the loops below
+    // depends on where they are stored
+    const Eval2Args<R> a = args;
     if (a.skip && *a.skip) return;
-    extern __shared__ __align__(32) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int quad = lane >> 2, ql = lane & 3;
-    const int64_t i = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 8 + quad;
+    const int64_t i = (blk * (blockDim.x >> 5) + warp) * 8 + quad;
     const bool valid = i < a.n;
     const int64_t N = a.n;
     R *sm = reinterpret_cast<R *>(smem_raw) + (warp * 8 + quad) * BW_ATOM;
@@ -747,8 +767,8 @@ __global__ void __launch_bounds__(128, MINB) k_bwd(const __grid_constant__ NepDe
     for (int t = 0; t < 9; ++t) acc.w[t] = R(0);
     if (valid) {
         const int ti = i < a.n_fe ? 0 : 1;
-        const v4<R> pi = a.pos[i], si = a.spin[i];
-        const int4 c = a.cnt[i];
+        const v4<R> pi = ro(a.pos + i), si = ro(a.spin + i);
+        const int4 c = ro(a.cnt + i);
         // angular adjoints of this lane's harmonics lm = ql + 4 m from their records (three
         // 16-byte loads each), the gradient entries straight from global memory
 #pragma unroll
@@ -757,25 +777,26 @@ __global__ void __launch_bounds__(128, MINB) k_bwd(const __grid_constant__ NepDe
             const int l = l_of_lm(lm);
             const R k2 = R(2) * kappa_of_lm<R>(lm);
             const v4<R> *src = reinterpret_cast<const v4<R> *>(a.bsum + ((int64_t)i * NLM + lm) * BREC);
-            v4<R> w0 = src[0], w1 = src[1], w2 = src[2];
+            v4<R> w0 = ro(src), w1 = ro(src + 1), w2 = ro(src + 2);
             const R *fa = a.fp + (int64_t)(Q_A + l - 1) * N + i, *fs = a.fp + (int64_t)(Q_SA + l - 1) * N + i;
-            w0.x *= k2 * fa[0]; w0.y *= k2 * fs[0]; w0.z *= k2 * fa[4 * N]; w0.w *= k2 * fs[4 * N];
-            w1.x *= k2 * fa[8 * N]; w1.y *= k2 * fs[8 * N]; w1.z *= k2 * fa[12 * N]; w1.w *= k2 * fs[12 * N];
-            w2.x *= k2 * fa[16 * N]; w2.y *= k2 * fs[16 * N]; w2.z = R(0); w2.w = R(0);
+            w0.x *= k2 * ro(fa); w0.y *= k2 * ro(fs); w0.z *= k2 * ro(fa + 4 * N); w0.w *= k2 * ro(fs + 4 * N);
+            w1.x *= k2 * ro(fa + 8 * N); w1.y *= k2 * ro(fs + 8 * N); w1.z *= k2 * ro(fa + 12 * N);
+            w1.w *= k2 * ro(fs + 12 * N);
+            w2.x *= k2 * ro(fa + 16 * N); w2.y *= k2 * ro(fs + 16 * N); w2.z = R(0); w2.w = R(0);
             v4<R> *d = reinterpret_cast<v4<R> *>(sm + BREC * lm);
             d[0] = w0; d[1] = w1; d[2] = w2;
         }
         R FR[NCH], FX[4][NCH];
 #pragma unroll
         for (int n = 0; n < NCH; ++n) {
-            FR[n] = a.fp[(int64_t)(Q_R + n) * N + i];
-            FX[0][n] = a.fp[(int64_t)(Q_EX + n) * N + i];
-            FX[1][n] = a.fp[(int64_t)(Q_DMI + n) * N + i];
-            FX[2][n] = a.fp[(int64_t)(Q_ANI + n) * N + i];
-            FX[3][n] = a.fp[(int64_t)(Q_SIA + n) * N + i];
+            FR[n] = ro(a.fp + (int64_t)(Q_R + n) * N + i);
+            FX[0][n] = ro(a.fp + (int64_t)(Q_EX + n) * N + i);
+            FX[1][n] = ro(a.fp + (int64_t)(Q_DMI + n) * N + i);
+            FX[2][n] = ro(a.fp + (int64_t)(Q_ANI + n) * N + i);
+            FX[3][n] = ro(a.fp + (int64_t)(Q_SIA + n) * N + i);
         }
         if (ql == 0) {   // onsite term dE_i/dS_i = 2 Fp_O S_i, counted once per atom
-            const R fo = R(2) * a.fp[(int64_t)Q_O * N + i];
+            const R fo = R(2) * ro(a.fp + (int64_t)Q_O * N + i);
             acc.hx = fo * si.x; acc.hy = fo * si.y; acc.hz = fo * si.z;
         }
         if (ti == 0) bwd_coeffs<R, 0>(P, FR, FX, ql, sm + BW_C);
@@ -806,30 +827,58 @@ __global__ void __launch_bounds__(128, MINB) k_bwd(const __grid_constant__ NepDe
         v4<R> f4, g4;
         f4.x = acc.fx; f4.y = acc.fy; f4.z = acc.fz; f4.w = R(0);
         g4.x = acc.hx; g4.y = acc.hy; g4.z = acc.hz; g4.w = R(0);
-        a.fown[i] = f4;
-        a.gii[i] = g4;
+        stg(a.fown + i, f4);
+        stg(a.gii + i, g4);
         if (a.want_virial) {
 #pragma unroll
-            for (int t = 0; t < 9; ++t) a.wpart[(int64_t)t * N + i] = acc.w[t];
+            for (int t = 0; t < 9; ++t) stg(a.wpart + (int64_t)t * N + i, acc.w[t]);
         }
     }
 }
 
+
+// The evaluation kernels over an argument table (sl_batch.h: a system's own table or a
+// batch's).  MINB: the register budget, as the minimum resident blocks per SM.  The
+// mixed-precision kernels default to 4 blocks (128 registers) and have a second budget each,
+// which sl_autotune may choose: radial 3 blocks, angular unconstrained, backward 3 blocks.
+template <typename R, int MINB = sizeof(R) == 4 ? 4 : 2>
+__global__ void __launch_bounds__(128, MINB) k_crad(const __grid_constant__ NepDev<R> P,
+                                                    const Eval2Args<R> *__restrict__ tab, SlotMap sm,
+                                                    const __grid_constant__ Eval2Args<R> solo) {
+    __shared__ uint32_t smask[MASKW_MAX][128];   // blocks have at most 128 threads
+    one_work(tab, sm, solo, [&](const Eval2Args<R> &a, int64_t blk, int64_t) { crad_body(P, a, blk, smask); });
+}
+template <typename R, int MINB = sizeof(R) == 4 ? 4 : 1>
+__global__ void __launch_bounds__(128, MINB) k_ang_fwd(const __grid_constant__ NepDev<R> P,
+                                                       const Eval2Args<R> *__restrict__ tab, SlotMap sm,
+                                                       const __grid_constant__ Eval2Args<R> solo) {
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    one_work(tab, sm, solo,
+             [&](const Eval2Args<R> &a, int64_t blk, int64_t) { ang_fwd_body(P, a, blk, smem_raw); });
+}
+template <typename R, int MINB = sizeof(R) == 4 ? 4 : 1>
+__global__ void __launch_bounds__(128, MINB) k_bwd(const __grid_constant__ NepDev<R> P,
+                                                   const Eval2Args<R> *__restrict__ tab, SlotMap sm,
+                                                   const __grid_constant__ Eval2Args<R> solo) {
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    one_work(tab, sm, solo, [&](const Eval2Args<R> &a, int64_t blk, int64_t) { bwd_body(P, a, blk, smem_raw); });
+}
+
 // ------------------------------------------------------------------ launch
+// The arguments of an evaluation at `at` (null members: the state).
 template <typename R>
-static Eval2Args<R> args2(Sys &s, bool want_virial) {
+static Eval2Args<R> args2(Sys &s, const EvalAt &at, bool want_virial) {
     Eval2Args<R> a;
-    // the evaluation point: the state, or the one set in s.at (midpoint iteration)
     if constexpr (sizeof(R) == 8) {
-        a.pos = reinterpret_cast<const v4<R> *>(s.at.pos ? s.at.pos : s.pos);
-        a.spin = reinterpret_cast<const v4<R> *>(s.at.spin ? s.at.spin : s.spin);
+        a.pos = reinterpret_cast<const v4<R> *>(at.pos ? at.pos : s.pos);
+        a.spin = reinterpret_cast<const v4<R> *>(at.spin ? at.spin : s.spin);
         a.box = *reinterpret_cast<const BoxDev<R> *>(&s.boxd);
     } else {
-        a.pos = reinterpret_cast<const v4<R> *>(s.at.posf ? s.at.posf : s.posf);
-        a.spin = reinterpret_cast<const v4<R> *>(s.at.spinf ? s.at.spinf : s.spinf);
+        a.pos = reinterpret_cast<const v4<R> *>(at.posf ? at.posf : s.posf);
+        a.spin = reinterpret_cast<const v4<R> *>(at.spinf ? at.spinf : s.spinf);
         a.box = *reinterpret_cast<const BoxDev<R> *>(&s.boxf);
     }
-    a.skip = s.at.skip;
+    a.skip = at.skip;
     a.nbr = s.nbr; a.seg = s.seg; a.rev = s.rev; a.capr = nbr_orig_stride(s.cap); a.n = s.n; a.n_fe = s.n_fe;
     a.cap = s.cap; a.cap_ang = s.cap_ang;
     a.clj = s.clj; a.cls = s.cls; a.cnt = s.cnt; a.mask = s.cmask; a.maskw = s.maskw;
@@ -858,56 +907,91 @@ void eval2_init() {
     std::lock_guard<std::mutex> lk(mu);
     if (dev < 64 && (done >> dev & 1u)) return;
     cudaFuncSetAttribute(k_ang_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<float>());
-    cudaFuncSetAttribute(k_ang_fwd<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<float>());
+    cudaFuncSetAttribute(k_ang_fwd<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<float>());
     cudaFuncSetAttribute(k_ang_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<double>());
     cudaFuncSetAttribute(k_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<float>());
-    cudaFuncSetAttribute(k_bwd<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<float>());
+    cudaFuncSetAttribute(k_bwd<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<float>());
     cudaFuncSetAttribute(k_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<double>());
     if (dev < 64) done |= 1ull << dev;
 }
 
-template <typename R>
-static void eval2_impl(Sys &s, const NepDev<R> &P, bool want_virial, cudaEvent_t *ev) {
-    const Eval2Args<R> a = args2<R>(s, want_virial);
-    const int cb = s.cfg.crad_block;
-    const unsigned nb = (unsigned)((s.n + cb - 1) / cb);
-    const int qa = s.cfg.ang_block ? s.cfg.ang_block : quad_block<R>();
-    const int qw = s.cfg.bwd_block ? s.cfg.bwd_block : quad_block<R>();
-    const unsigned nqa = (unsigned)((s.n + qa / 4 - 1) / (qa / 4));
-    const unsigned nqw = (unsigned)((s.n + qw / 4 - 1) / (qw / 4));
-    if (ev) cudaEventRecord(ev[0], s.stream);
-    // compaction and radial channels in one kernel: the compaction group is empty
-    if (ev) cudaEventRecord(ev[1], s.stream);
-    // register-budget variants exist for the mixed-precision kernels (sl_autotune chooses them)
-    bool variant = false;
-    if constexpr (sizeof(R) == 4) {
-        variant = s.cfg.crad_minb == 3;
-        if (variant) k_crad<R, 3><<<nb, cb, 0, s.stream>>>(P, a);
+// ---- argument tables (sl_batch.h)
+size_t fused_eval_size(int prec) { return prec == 0 ? sizeof(Eval2Args<double>) : sizeof(Eval2Args<float>); }
+
+// slot kinds: the step's evaluation (at the state, no virial), the full one (with the virial
+// parts) and the midpoint iteration's (at its point, with its skip flag)
+static EvalAt eval_point(const Sys &s, int kind) {
+    EvalAt at;
+    if (kind == SK_MID && s.mid_iters > 0) {
+        at.pos = s.posmid; at.posf = s.posmidf; at.spin = s.mids; at.spinf = s.midsf;
+        at.skip = reinterpret_cast<const int *>(reinterpret_cast<const char *>(s.md) + offsetof(MidDev, converged));
     }
-    if (!variant) k_crad<R><<<nb, cb, 0, s.stream>>>(P, a);
-    if (ev) cudaEventRecord(ev[2], s.stream);
-    variant = false;
-    if constexpr (sizeof(R) == 4) {
-        variant = s.cfg.ang_minb == 5;
-        if (variant) k_ang_fwd<R, 5><<<nqa, qa, fwd_smem<R>(qa), s.stream>>>(P, a);
-    }
-    if (!variant) k_ang_fwd<R><<<nqa, qa, fwd_smem<R>(qa), s.stream>>>(P, a);
-    if (ev) cudaEventRecord(ev[3], s.stream);
-    launch_network(s, nullptr);
-    if (ev) cudaEventRecord(ev[4], s.stream);
-    variant = false;
-    if constexpr (sizeof(R) == 4) {
-        variant = s.cfg.bwd_minb == 4;
-        if (variant) k_bwd<R, 4><<<nqw, qw, bwdf_smem<R>(qw), s.stream>>>(P, a);
-    }
-    if (!variant) k_bwd<R><<<nqw, qw, bwdf_smem<R>(qw), s.stream>>>(P, a);
-    if (ev) cudaEventRecord(ev[5], s.stream);
+    return at;
 }
 
+void fused_put_eval(Sys &s, int r, int kind, const FusedTables &t, unsigned char *img, int64_t *blocks) {
+    const EvalAt at = eval_point(s, kind);
+    if (s.prec == 0) reinterpret_cast<Eval2Args<double> *>(img + t.o_eval)[r] = args2<double>(s, at, kind == SK_FULL);
+    else reinterpret_cast<Eval2Args<float> *>(img + t.o_eval)[r] = args2<float>(s, at, kind == SK_FULL);
+    const int qb = default_quad_block(s.prec);
+    blocks[FK_CRAD] = (s.n + 127) / 128;
+    blocks[FK_ANG] = blocks[FK_BWD] = (s.n + qb / 4 - 1) / (qb / 4);
+}
+
+// Radial, angular, network and backward over a table, each launch in its own shape
+// (L[k].block threads, 0: the default) and register budget (L[k].minb, 0: the default).
+template <typename R>
+void launch_eval_t(const FusedTables &t, const NepDev<R> &P, const Launch *L, cudaStream_t st, cudaEvent_t *ev) {
+    // a system's own launch passes its argument block as a kernel parameter; a batch's reads
+    // the table (the same for the four kernels of one launch group)
+    const Eval2Args<R> *tab = L[0].solo ? nullptr : t.at<Eval2Args<R>>(t.o_eval);
+    const Eval2Args<R> so = solo_args<Eval2Args<R>>(L[0]);
+    const SlotMap s0 = L[0].slots(), s1 = L[1].slots(), s3 = L[3].slots();
+    const int cb = L[0].block ? L[0].block : 128;
+    const int qa = L[1].block ? L[1].block : quad_block<R>();
+    const int qw = L[3].block ? L[3].block : quad_block<R>();
+    if (ev) cudaEventRecord(ev[0], st);
+    // compaction and radial channels in one kernel: the compaction group is empty
+    if (ev) cudaEventRecord(ev[1], st);
+    bool variant = false;
+    if constexpr (sizeof(R) == 4) {
+        variant = L[0].minb == 3;
+        if (variant) k_crad<R, 3><<<L[0].grid, cb, 0, st>>>(P, tab, s0, so);
+    }
+    if (!variant) k_crad<R><<<L[0].grid, cb, 0, st>>>(P, tab, s0, so);
+    if (ev) cudaEventRecord(ev[2], st);
+    variant = false;
+    if constexpr (sizeof(R) == 4) {
+        variant = L[1].minb == 1;
+        if (variant) k_ang_fwd<R, 1><<<L[1].grid, qa, fwd_smem<R>(qa), st>>>(P, tab, s1, so);
+    }
+    if (!variant) k_ang_fwd<R><<<L[1].grid, qa, fwd_smem<R>(qa), st>>>(P, tab, s1, so);
+    if (ev) cudaEventRecord(ev[3], st);
+    if constexpr (sizeof(R) == 4) launch_net_t_tc(t, P, L[2], st);
+    else launch_net_t_fp64(t, P, L[2], st);
+    if (ev) cudaEventRecord(ev[4], st);
+    variant = false;
+    if constexpr (sizeof(R) == 4) {
+        variant = L[3].minb == 3;
+        if (variant) k_bwd<R, 3><<<L[3].grid, qw, bwdf_smem<R>(qw), st>>>(P, tab, s3, so);
+    }
+    if (!variant) k_bwd<R><<<L[3].grid, qw, bwdf_smem<R>(qw), st>>>(P, tab, s3, so);
+    if (ev) cudaEventRecord(ev[5], st);
+}
+template void launch_eval_t<float>(const FusedTables &, const NepDev<float> &, const Launch *, cudaStream_t,
+                                   cudaEvent_t *);
+template void launch_eval_t<double>(const FusedTables &, const NepDev<double> &, const Launch *, cudaStream_t,
+                                    cudaEvent_t *);
+
+// The system's own evaluation: at the midpoint point while s.at is set (the midpoint
+// iteration), else at the state, with the virial parts when asked for.
 void launch_eval(Sys &s, bool want_virial, cudaEvent_t *ev) {
     if (s.n == 0) return;
-    if (s.prec == 0) eval2_impl<double>(s, s.pd, want_virial, ev);
-    else eval2_impl<float>(s, s.pf, want_virial, ev);
+    const int kind = s.at.pos ? SK_MID : want_virial ? SK_FULL : SK_STEP;
+    const Launch L[4] = {solo_launch(s, FK_CRAD, kind), solo_launch(s, FK_ANG, kind), solo_launch(s, FK_NET, kind),
+                         solo_launch(s, FK_BWD, kind)};
+    if (s.prec == 0) launch_eval_t<double>(s.solo->t, s.pd, L, s.stream, ev);
+    else launch_eval_t<float>(s.solo->t, s.pf, L, s.stream, ev);
 }
 
 }  // namespace sl

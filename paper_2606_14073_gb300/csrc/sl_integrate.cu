@@ -19,6 +19,8 @@
 // the predictor's eta bit for bit, so nothing is stored between the halves.
 #include "sl_internal.h"
 #include "sl_eval2.cuh"
+#include "sl_batch.h"
+#include "sl_fused.cuh"
 #include "sl_spin.cuh"
 
 namespace sl {
@@ -49,8 +51,8 @@ __device__ __forceinline__ void add_landau(const StepDev &P, int t, const double
 
 
 template <bool MIXED>
-__global__ void __launch_bounds__(256) k_first_half(IntArgs a) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void first_half_body(const IntArgs &a, int64_t blk) {
+    const int64_t i = blk * (int64_t)blockDim.x + threadIdx.x;
     const unsigned long long st = a.step[0];
     if (i == 0) a.step[1] = st;
     if (i >= a.n) return;
@@ -131,8 +133,8 @@ __global__ void __launch_bounds__(256) k_first_half(IntArgs a) {
 // SPIN = false (midpoint mode): the spins were already advanced by the midpoint
 // iteration; only the gather, the final kick and the carried F, H remain.
 template <typename R, bool MIXED, bool SPIN = true>
-__global__ void __launch_bounds__(256) k_second_half(IntArgs a, GatherArgs<R> g) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void second_half_body(const IntArgs &a, const GatherArgs<R> &g, int64_t blk) {
+    const int64_t i = blk * (int64_t)blockDim.x + threadIdx.x;
     if (i == 0) a.step[0] = a.step[1] + 1;
     if (i >= a.n) return;
     const StepDev &P = *a.par;
@@ -208,6 +210,25 @@ __global__ void __launch_bounds__(256) k_second_half(IntArgs a, GatherArgs<R> g)
     if (!(isfinite(Fs[0]) && isfinite(Fs[1]) && isfinite(Fs[2]) && isfinite(Hs[0]) && isfinite(Hs[1]) &&
           isfinite(Hs[2])))
         atomicOr(a.status, ST_NONFINITE);
+}
+
+// The halves over an argument table (sl_batch.h: a system's own table or a batch's), one
+// 256-thread block per 256 atoms of a slot.
+template <typename R>
+struct HalfArgs {
+    IntArgs a;
+    GatherArgs<R> g;
+};
+template <bool MIXED>
+__global__ void __launch_bounds__(256) k_first_half(const IntArgs *__restrict__ tab, SlotMap sm,
+                                                    const __grid_constant__ IntArgs solo) {
+    one_work(tab, sm, solo, [](const IntArgs &a, int64_t blk, int64_t) { first_half_body<MIXED>(a, blk); });
+}
+template <typename R, bool MIXED, bool SPIN>
+__global__ void __launch_bounds__(256) k_second_half(const HalfArgs<R> *__restrict__ tab, SlotMap sm,
+                                                     const __grid_constant__ HalfArgs<R> solo) {
+    one_work(tab, sm, solo,
+             [](const HalfArgs<R> &h, int64_t blk, int64_t) { second_half_body<R, MIXED, SPIN>(h.a, h.g, blk); });
 }
 
 // Forces and fields at the current state into (Fo, Ho).
@@ -301,21 +322,32 @@ static GatherArgs<R> gather_args(Sys &s) {
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-void launch_first_half(Sys &s) {
-    if (s.prec == 0) k_first_half<false><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s));
-    else k_first_half<true><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s));
+void launch_first_half_t(const FusedTables &t, const Launch &L, cudaStream_t st) {
+    const IntArgs *tab = L.solo ? nullptr : t.at<IntArgs>(t.o_first);
+    const IntArgs so = solo_args<IntArgs>(L);
+    if (t.prec == 0) k_first_half<false><<<L.grid, 256, 0, st>>>(tab, L.slots(), so);
+    else k_first_half<true><<<L.grid, 256, 0, st>>>(tab, L.slots(), so);
 }
 
+template <typename R, bool MIXED>
+static void second_half_t(const FusedTables &t, const Launch &L, bool spin, cudaStream_t st) {
+    const HalfArgs<R> *tab = L.solo ? nullptr : t.at<HalfArgs<R>>(t.o_second);
+    const HalfArgs<R> so = solo_args<HalfArgs<R>>(L);
+    if (spin) k_second_half<R, MIXED, true><<<L.grid, 256, 0, st>>>(tab, L.slots(), so);
+    else k_second_half<R, MIXED, false><<<L.grid, 256, 0, st>>>(tab, L.slots(), so);
+}
+void launch_second_half_t(const FusedTables &t, const Launch &L, bool spin, cudaStream_t st) {
+    if (t.prec == 0) second_half_t<double, false>(t, L, spin, st);
+    else second_half_t<float, true>(t, L, spin, st);
+}
+
+// a system's own launches, over its table
+void launch_first_half(Sys &s) { launch_first_half_t(s.solo->t, solo_launch(s, FK_FIRST, SK_STEP), s.stream); }
 void launch_second_half(Sys &s) {
-    if (s.prec == 0)
-        k_second_half<double, false><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<double>(s));
-    else k_second_half<float, true><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<float>(s));
+    launch_second_half_t(s.solo->t, solo_launch(s, FK_SECOND, SK_STEP), true, s.stream);
 }
-
 void launch_second_half_nospin(Sys &s) {
-    if (s.prec == 0)
-        k_second_half<double, false, false><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<double>(s));
-    else k_second_half<float, true, false><<<nblk(s.n, 256), 256, 0, s.stream>>>(int_args(s), gather_args<float>(s));
+    launch_second_half_t(s.solo->t, solo_launch(s, FK_SECOND, SK_STEP), false, s.stream);
 }
 
 void launch_sweep_rotate(Sys &s, int c) {
@@ -351,6 +383,20 @@ __global__ void k_compare_bits(const double4 *__restrict__ Fo, const double4 *__
                       __double_as_longlong(h.y) == __double_as_longlong(rh.y) &&
                       __double_as_longlong(h.z) == __double_as_longlong(rh.z);
     if (!same) atomicOr(diff, 1);
+}
+
+// ---- fused batch step (sl_batch.h)
+void fused_half_sizes(int prec, size_t *first, size_t *second) {
+    *first = sizeof(IntArgs);
+    *second = prec == 0 ? sizeof(HalfArgs<double>) : sizeof(HalfArgs<float>);
+}
+
+void fused_put_half(Sys &s, int r, const FusedTables &t, unsigned char *img, int64_t *blocks) {
+    const IntArgs a = int_args(s);
+    reinterpret_cast<IntArgs *>(img + t.o_first)[r] = a;
+    if (s.prec == 0) reinterpret_cast<HalfArgs<double> *>(img + t.o_second)[r] = HalfArgs<double>{a, gather_args<double>(s)};
+    else reinterpret_cast<HalfArgs<float> *>(img + t.o_second)[r] = HalfArgs<float>{a, gather_args<float>(s)};
+    blocks[FK_FIRST] = blocks[FK_SECOND] = nblk(s.n, 256);
 }
 
 void launch_compare_bits(Sys &s, const double4 *ref, int *diff) {

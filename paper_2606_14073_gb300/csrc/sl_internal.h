@@ -58,9 +58,9 @@ struct LaunchCfg {
     int mlp_ctas_per_sm = 2;   // persistent CTAs per SM of the tensor-core network
     // register budgets of the mixed-precision kernels, as the minimum resident blocks per SM
     // the compiler holds the allocation to (0: the kernel's default budget)
-    int crad_minb = 0;         // 0 (4 blocks: 128 registers) or 3 (170 registers)
-    int ang_minb = 0;          // 0 (unconstrained) or 5 (102 registers)
-    int bwd_minb = 0;          // 0 (2 blocks: the compiler takes 168) or 4 (128 registers)
+    int crad_minb = 0;         // 0 (4 blocks: 128 registers) or 3 (3 blocks)
+    int ang_minb = 0;          // 0 (4 blocks: 128 registers) or 1 (unconstrained)
+    int bwd_minb = 0;          // 0 (4 blocks: 128 registers) or 3 (3 blocks)
 };
 
 // Where an evaluation reads positions and spins (null: the state arrays) and an
@@ -71,6 +71,8 @@ struct EvalAt {
     const int *skip = nullptr;
 };
 
+struct SoloTables;   // sl_batch.h
+
 struct Cells {
     int nc[3];
     int ncell;
@@ -80,6 +82,7 @@ struct Cells {
 };
 
 struct Sys {
+    uint64_t uid = 0;          // unique in the process (a batch tells its slots' systems apart by it)
     int64_t n = 0;
     int prec = 0;
     uint64_t seed = 0, replica = 0;
@@ -117,7 +120,7 @@ struct Sys {
     // evaluation buffers (element type = compute precision)
     void *q = nullptr;         // [DIM][qs]: descriptor v of atom i at v * qs + i
     int64_t qs = 0;            // row stride of q: n rounded up to a multiple of 4 (16-byte rows)
-    alignas(64) CUtensorMap qmap;   // TMA map of q (mixed precision): [DIM] rows x n atoms, 128 x 66 boxes
+    CUtensorMap qmap;          // TMA map of q (mixed precision): [DIM] rows x n atoms, 128 x 66 boxes
     void *bsum = nullptr;      // [n][NLM][BREC] angular-sum records
     void *fp = nullptr;        // [DIM][n]
     void *ei = nullptr;        // [n]
@@ -157,7 +160,11 @@ struct Sys {
     // snapshot for error recovery
     double4 *snap = nullptr;   // 5 n: pos, vel, spin, F, H
 
-    // evaluation point used by launch_eval / launch_network while it is set
+    // the system's own argument tables of the step kernels (sl_batch.h)
+    SoloTables *solo = nullptr;
+
+    // set while launch_eval evaluates at the midpoint iteration's point (the system's tables
+    // hold that point)
     EvalAt at;
     LaunchCfg cfg;
     // the last sl_autotune's measured landscape: median ms of the radial, angular, network and
@@ -200,20 +207,23 @@ struct Sys {
     MidDev *md = nullptr;
 };
 
+// the system's own argument tables (sl_batch.cu): written for its current buffers (not during
+// a stream capture; 0 on success), and released
+int solo_refresh(Sys &s);
+void solo_free(Sys &s);
+
 // launchers (sl_neighbors.cu)
 // row stride of the atom-major caller-index copy of the lists: cap rounded up to a multiple
 // of 4 entries, so every row starts on a 16-byte boundary
 inline int nbr_orig_stride(int cap) { return (cap + 3) & ~3; }
 void nbr_setup(Sys &s);
 void launch_rebuild(Sys &s, bool conditional);
-// sl_nep.cu
-// ev (optional, 6 events): recorded before each of the five evaluation kernels and
-// after the last one (sl_eval2.cu).
+// sl_eval2.cu: the system's evaluation at the state (with the virial parts when asked for), or
+// at the midpoint point while s.at is set; ev (optional, 6 events): recorded before the
+// radial kernel, after it, after the angular kernel, the network and the backward.
 void launch_eval(Sys &s, bool want_virial, cudaEvent_t *ev = nullptr);
-void eval2_init();
+void eval2_init();   // dynamic shared-memory limits of the evaluation kernels (once per device)
 int default_quad_block(int prec);   // threads per block of the quad kernels by default
-void launch_network(Sys &s, cudaEvent_t *ev);   // sl_nep.cu
-void launch_network_tc(Sys &s);                  // sl_mlp_tc.cu (mixed precision)
 int make_q_tensor_map(Sys &s);                   // sl_mlp_tc.cu: the TMA map of s.q; 0 on success
 // first half, rebuild group (7), compaction with radial forward, angular forward, network, backward,
 // second half

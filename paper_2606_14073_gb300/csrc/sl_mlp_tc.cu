@@ -23,6 +23,8 @@
 #include <mutex>
 
 #include "sl_internal.h"
+#include "sl_batch.h"
+#include "sl_fused.cuh"
 
 namespace sl {
 namespace tc {
@@ -134,6 +136,13 @@ __device__ __forceinline__ void tma_load_q(uint32_t dst, const CUtensorMap *map,
         : "memory");
 }
 
+// A tensor map read from global memory (the fused launch's replica table, written by a host
+// copy): acquire it for the tensor-map proxy before the first copy through it.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -154,12 +163,21 @@ __device__ __forceinline__ void split8(const float x[8], uint4 &hi, uint4 &lo) {
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-__global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDev<float> P,
-                                                   const __grid_constant__ CUtensorMap qmap,
-                                                   float *__restrict__ fp, float *__restrict__ ei, int64_t n,
-                                                   int *status, const int *skip) {
-    // uniform for the whole CTA and before any shared-memory or TMEM use
-    if (skip && *skip) return;
+// What a tile of the network needs: the descriptor map and first atom of its system, the
+// system's atom count, outputs and status word.
+struct MlpTile {
+    const CUtensorMap *qmap;
+    int x0;
+    int64_t n;
+    float *fp, *ei;
+    int *status;
+    bool gmem_map;   // the map lives in global memory (acquired before use)
+};
+
+// Body of the network kernel over the tiles src(0 .. total-1), each CTA taking tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...
+template <typename Src>
+__device__ __forceinline__ void mlp_tc_body(const NepDev<float> &P, int64_t ntiles, Src src) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
@@ -208,15 +226,34 @@ __global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDe
     uint32_t phase = 0, phase_q = 0;
     bool ok = true;
     bool q_in_flight = false;   // a descriptor tile load has been issued and not yet waited for
-    const int64_t ntiles = (n + TM - 1) / TM;
+    int *status = nullptr;   // the status word of the last tile's system (timeouts are reported there)
 
     const float *stage = reinterpret_cast<const float *>(smem + OFF_Q);
-    if (tid == 0 && blockIdx.x < ntiles) tma_load_q(sbase + OFF_Q, &qmap, (int)(blockIdx.x * TM), barq);
+    // the next tile's source, read while the current tile is in the tensor cores; thread 0
+    // acquires each tensor map it has not used yet before the first copy through it
+    const CUtensorMap *acquired = nullptr;
+    auto issue = [&](const MlpTile &t) {
+        if (t.gmem_map && t.qmap != acquired) {
+            tensormap_acquire(t.qmap);
+            acquired = t.qmap;
+        }
+        tma_load_q(sbase + OFF_Q, t.qmap, t.x0, barq);
+    };
+    MlpTile nxt;
+    if (blockIdx.x < ntiles) {
+        nxt = src(blockIdx.x);
+        if (tid == 0) issue(nxt);
+    }
     q_in_flight = blockIdx.x < ntiles;
 
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int64_t i = tile * TM + tid;
-        const bool valid = i < n;
+        const MlpTile cur = nxt;
+        status = cur.status;
+        const int64_t i = cur.x0 + tid;
+        const bool valid = i < cur.n;
+        float *__restrict__ fp = cur.fp;
+        float *__restrict__ ei = cur.ei;
+        const int64_t n = cur.n;
         // this tile's descriptors (every thread waits; the block agrees on the outcome)
         if (!__syncthreads_and(mbar_wait(barq, phase_q))) { ok = false; break; }
         phase_q ^= 1u;
@@ -241,7 +278,8 @@ __global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDe
         tc_fence_before();
         __syncthreads();
         if (tile + gridDim.x < ntiles) {
-            if (tid == 0) tma_load_q(sbase + OFF_Q, &qmap, (int)((tile + gridDim.x) * TM), barq);
+            nxt = src(tile + gridDim.x);
+            if (tid == 0) issue(nxt);
             q_in_flight = true;
         }
         if (tid == 0) {
@@ -329,7 +367,7 @@ __global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDe
         __syncthreads();   // TMEM and the A tiles are free for the next tile
     }
     if (!ok) {
-        if (tid == 0) atomicOr(status, ST_TIMEOUT);
+        if (tid == 0 && status) atomicOr(status, ST_TIMEOUT);
         // let any MMA and any tile load still in flight finish before the memory is released
         // (bounded waits)
         mbar_wait(bar, phase);
@@ -341,6 +379,31 @@ __global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDe
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
+}
+
+// The network over the 128-atom tiles of a work map (sl_batch.h): a batch's (tab non-null;
+// each slot's arguments and TMA map from the table, in global memory) or a system's own (tab
+// null; its arguments, map included, as the kernel parameter solo).
+__global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDev<float> P,
+                                                   const MlpArgs *__restrict__ tab, WorkMap m,
+                                                   const __grid_constant__ MlpArgs solo) {
+    const int64_t total = __ldg(m.w0 + m.nrep);
+    // the skip flag (the midpoint iteration's own launches only): uniform for the whole CTA and
+    // before any shared-memory or TMEM use
+    if (!tab && solo.skip && *solo.skip) return;
+    mlp_tc_body(P, total, [&](int64_t g) {
+        const int r = work_replica(m, g);
+        const MlpArgs &a = tab ? tab[r] : solo;
+        MlpTile t;
+        t.qmap = &a.qmap;
+        t.x0 = (int)((g - __ldg(m.w0 + r)) * TM);
+        t.n = a.n;
+        t.fp = a.fp;
+        t.ei = a.ei;
+        t.status = a.status;
+        t.gmem_map = tab != nullptr;
+        return t;
+    });
 }
 
 // Self-test of the bounded wait: one thread waits on a barrier that nothing ever arrives
@@ -390,23 +453,35 @@ int make_q_tensor_map(Sys &s) {
     return r == CUDA_SUCCESS ? 0 : -1;
 }
 
-void launch_network_tc(Sys &s) {
+// ---- argument tables (sl_batch.h): persistent CTAs over the slots' tiles
+// the shared-memory limit is a per-device function attribute: set once per device
+static void tc_smem_attribute(int dev) {
+    static std::mutex mu;
+    static uint64_t done = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!(dev < 64 && (done >> dev & 1u))) {
+        cudaFuncSetAttribute(tc::k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM_BYTES);
+        if (dev < 64) done |= 1ull << dev;
+    }
+}
+
+// the persistent grid of the tensor-core network (the FP64 network takes one work item per
+// block: its grid follows the batch's atom capacity)
+void fused_grid_net(FusedTables &t) {
+    if (t.prec == 0) return;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
-    {   // the shared-memory limit is a per-device function attribute: set it once per device
-        static std::mutex mu;
-        static uint64_t done = 0;
-        std::lock_guard<std::mutex> lk(mu);
-        if (!(dev < 64 && (done >> dev & 1u))) {
-            cudaFuncSetAttribute(tc::k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM_BYTES);
-            if (dev < 64) done |= 1ull << dev;
-        }
-    }
+    tc_smem_attribute(dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t ntiles = (s.n + tc::TM - 1) / tc::TM;
-    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * s.cfg.mlp_ctas_per_sm);
-    tc::k_mlp_tc<<<grid, 128, tc::SMEM_BYTES, s.stream>>>(s.pf, s.qmap, (float *)s.fp, (float *)s.ei, s.n, s.status,
-                                                       s.at.skip);
+    t.grid[FK_NET] = (unsigned)(sms * LaunchCfg().mlp_ctas_per_sm);
+}
+
+void launch_net_t_tc(const FusedTables &t, const NepDev<float> &P, const Launch &L, cudaStream_t st) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    tc_smem_attribute(dev);
+    tc::k_mlp_tc<<<L.grid, 128, tc::SMEM_BYTES, st>>>(P, L.solo ? nullptr : t.at<MlpArgs>(t.o_net), L.m,
+                                                       solo_args<MlpArgs>(L));
 }
 
 }  // namespace sl

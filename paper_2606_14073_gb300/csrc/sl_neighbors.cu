@@ -13,9 +13,13 @@
 // of neighbour species 0 and 1, then the remaining radial candidates of species
 // 0 and 1 -- and each segment is ordered by the neighbour's caller index, so every
 // per-atom sum runs in an order that does not depend on the internal atom order.
+#include <algorithm>
 #include <cstdio>
 
 #include "sl_internal.h"
+#include "sl_batch.h"
+#include "sl_fused.cuh"
+#include "sl_rebuild.cuh"
 
 namespace sl {
 
@@ -34,17 +38,13 @@ __device__ __forceinline__ double exact_d2(double xi, double yi, double zi, doub
     return __dadd_rn(__dadd_rn(__dmul_rn(t[0], t[0]), __dmul_rn(t[1], t[1])), __dmul_rn(t[2], t[2]));
 }
 
-struct GridArgs {
-    int nc[3];
-    double w[3];
-    int per[3];
-};
 
-__global__ void k_bin(const double4 *__restrict__ pos, int64_t n, GridArgs g, int *__restrict__ count,
-                      int *__restrict__ of, const int *__restrict__ flag) {
-    if (flag && *flag == 0) return;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double4 p = pos[i];
+
+__device__ __forceinline__ void bin_body(const BinArgs &r, int64_t blk, int64_t nblk) {
+    if (r.flag && *r.flag == 0) return;
+    const GridArgs &g = r.g;
+    for (int64_t i = blk * (int64_t)blockDim.x + threadIdx.x; i < r.n; i += nblk * blockDim.x) {
+    const double4 p = r.pos[i];
     const double x[3] = {p.x, p.y, p.z};
     int c[3];
 #pragma unroll
@@ -53,16 +53,17 @@ __global__ void k_bin(const double4 *__restrict__ pos, int64_t n, GridArgs g, in
         c[a] = min(max(ci, 0), g.nc[a] - 1);
     }
     const int cell = (c[2] * g.nc[1] + c[1]) * g.nc[0] + c[0];
-    of[i] = cell;
-    atomicAdd(count + cell, 1);
+    r.of[i] = cell;
+    atomicAdd(r.count + cell, 1);
     }
 }
 
-// Exclusive scan of count[0..m) into start[0..m], one block.
-__global__ void k_scan(const int *__restrict__ count, int *__restrict__ start, int m, const int *__restrict__ flag) {
-    if (flag && *flag == 0) return;
-    __shared__ int s_part[1024];
-    __shared__ int s_carry;
+// Exclusive scan of count[0..m) into start[0..m] by one whole block (s_part: blockDim.x ints).
+__device__ __forceinline__ void scan_body(const BinArgs &r, int *s_part, int &s_carry) {
+    if (r.flag && *r.flag == 0) return;
+    const int *__restrict__ count = r.count;
+    int *__restrict__ start = r.start;
+    const int m = r.ncell;
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
     for (int base = 0; base < m; base += blockDim.x) {
@@ -82,55 +83,23 @@ __global__ void k_scan(const int *__restrict__ count, int *__restrict__ start, i
         __syncthreads();
     }
     if (threadIdx.x == 0) start[m] = s_carry;
+    __syncthreads();   // the block's next work item reuses s_part and s_carry
 }
 
 // Atoms into their cells, with a cell-ordered copy of the FP32 position and of the
 // key (species << 30 | caller index) so the list build reads candidates contiguously.
-__global__ void k_scatter(const int *__restrict__ of, int64_t n, const int *__restrict__ start, int *__restrict__ fill,
-                          int *__restrict__ atoms, const float4 *__restrict__ posf, const int32_t *__restrict__ species,
-                          const int32_t *__restrict__ orig, float4 *__restrict__ cposf, uint32_t *__restrict__ ckey,
-                          const int *__restrict__ flag) {
-    if (flag && *flag == 0) return;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = of[i];
-        const int p = start[c] + atomicAdd(fill + c, 1);
-        atoms[p] = (int)i;
-        cposf[p] = posf[i];
-        ckey[p] = ((uint32_t)species[i] << 30) | (uint32_t)orig[i];
+__device__ __forceinline__ void scatter_body(const BinArgs &r, int64_t blk, int64_t nblk) {
+    if (r.flag && *r.flag == 0) return;
+    for (int64_t i = blk * (int64_t)blockDim.x + threadIdx.x; i < r.n; i += nblk * blockDim.x) {
+        const int c = r.of[i];
+        const int p = r.start[c] + atomicAdd(r.fill + c, 1);
+        r.atoms[p] = (int)i;
+        r.cposf[p] = r.posf[i];
+        r.ckey[p] = ((uint32_t)r.species[i] << 30) | (uint32_t)r.orig[i];
     }
 }
 
-struct ListArgs {
-    const double4 *pos;
-    const float4 *posf;
-    const int32_t *species, *orig, *inv;
-    const int *cell_start, *cell_atoms, *cell_of;
-    const float4 *cposf;      // cell-ordered FP32 positions
-    const uint32_t *ckey;     // cell-ordered (species << 30 | caller index)
-    int32_t *nbr_orig;        // [n][capr] caller index of each list entry (atom-major rows of capr)
-    int64_t n;
-    int cap, cap_ang, capr;
-    double cut_r2, cut_a2;
-    float cut_r2f_lo, cut_r2f_hi, cut_a2f_lo, cut_a2f_hi;   // FP32 pre-test band
-    BoxDev<double> bd;
-    BoxDev<float> bf;
-    GridArgs g;
-    int32_t *nbr;             // [n][capr] candidate lists, atom-major
-    int4 *seg;
-    int *status;
-    const int *flag;
-};
 
-struct RevArgs {
-    const int32_t *species, *orig;
-    const int32_t *nbr, *nbr_orig;   // nbr_orig atom-major [n][capr], capr a multiple of 4
-    const int4 *seg;
-    int cap, capr;
-    int64_t n;
-    uint8_t *rev;         // [n][capr] reverse slots (cap <= 256)
-    int *status;
-    const int *flag;
-};
 
 
 // Warp per atom.  Lanes take the candidates of the stencil cells 32 at a time;
@@ -185,17 +154,19 @@ __device__ __forceinline__ void sort_and_store(const uint32_t *key, int mm, int 
 
 __device__ __forceinline__ int wrap_cell(int x, int nc) { return x < 0 ? x + nc : (x >= nc ? x - nc : x); }
 
-constexpr int LB_WARPS = 4;
 constexpr int SORT_MAX = 256;
 
-__global__ void __launch_bounds__(LB_WARPS * 32) k_build_lists_warp(ListArgs a) {
+struct ListSmem {
+    uint32_t key[LB_WARPS][SORT_MAX];
+    int off[LB_WARPS][32], p0[LB_WARPS][32];   // stencil cells of each warp's atom
+};
+
+__device__ __forceinline__ void lists_body(const ListArgs &a, int64_t blk, int64_t nblk, ListSmem &sm) {
     if (a.flag && *a.flag == 0) return;
-    __shared__ uint32_t skey[LB_WARPS][SORT_MAX];
-    __shared__ int soff[LB_WARPS][32], sp0[LB_WARPS][32];   // stencil cells of the warp's atom
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t *key = skey[w];
+    uint32_t *key = sm.key[w];
     const unsigned lt = (1u << lane) - 1u;
-    for (int64_t i = (int64_t)blockIdx.x * LB_WARPS + w; i < a.n; i += (int64_t)gridDim.x * LB_WARPS) {
+    for (int64_t i = blk * LB_WARPS + w; i < a.n; i += nblk * LB_WARPS) {
         const double4 pi = a.pos[i];
         const float4 pfi = a.posf[i];
         const int cc = a.cell_of[i];
@@ -229,7 +200,7 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_build_lists_warp(ListArgs a) 
             if (lane >= o) incl += t;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        int *off = soff[w], *p0 = sp0[w];
+        int *off = sm.off[w], *p0 = sm.p0[w];
         if (lane < nst) {
             off[lane] = incl - my_len;
             p0[lane] = my_p0;
@@ -360,10 +331,10 @@ __device__ __forceinline__ int find_rest(const int32_t *__restrict__ row, int b,
 // s, t_i).  Each lane takes four slots 32 apart: their list entries, then their neighbours'
 // segment bounds, then two first search rounds at a time are in flight together.  A pair
 // found in one list only (a list cut at its capacity) raises the overflow status.
-__global__ void __launch_bounds__(128) k_build_rev_warp(RevArgs a) {
+__device__ __forceinline__ void rev_body(const RevArgs &a, int64_t blk, int64_t nblk) {
     if (a.flag && *a.flag == 0) return;
     const int lane = threadIdx.x & 31;
-    for (int64_t i = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5); i < a.n; i += (int64_t)gridDim.x * 4) {
+    for (int64_t i = blk * 4 + (threadIdx.x >> 5); i < a.n; i += nblk * 4) {
         const int4 sg = a.seg[i];
         const int oi = a.orig[i];
         const int ti = a.species[i];
@@ -412,19 +383,64 @@ __global__ void __launch_bounds__(128) k_build_rev_warp(RevArgs a) {
     }
 }
 
-__global__ void k_finish(const double4 *__restrict__ pos, double4 *__restrict__ ref, int64_t n, int *count,
-                         int *fill, int ncell, const int *flag, unsigned long long *builds) {
-    if (flag && *flag == 0) return;
-    const int64_t m = n > ncell ? n : ncell;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < n) ref[i] = pos[i];
-        if (i < ncell) { count[i] = 0; fill[i] = 0; }
+__device__ __forceinline__ void finish_body(const BinArgs &r, int64_t blk, int64_t nblk) {
+    if (r.flag && *r.flag == 0) return;
+    const int64_t m = r.n > r.ncell ? r.n : r.ncell;
+    for (int64_t i = blk * (int64_t)blockDim.x + threadIdx.x; i < m; i += nblk * blockDim.x) {
+        if (i < r.n) r.posref[i] = r.pos[i];
+        if (i < r.ncell) { r.count[i] = 0; r.fill[i] = 0; }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *builds += 1ULL;
-    // the flag itself is cleared by k_clear_flag, the last kernel that reads it
+    if (blk == 0 && threadIdx.x == 0) *r.builds += 1ULL;
+    // the flag itself is cleared by the last kernel of the group, after everything that reads it
 }
 
-__global__ void k_clear_flag(int *flag) { *flag = 0; }
+// The group over an argument table (sl_batch.h: a system's own table or a batch's), one
+// launch per kernel; a slot with no rebuild due this step is passed over as a whole.
+// quick (a system's own conditional launch: its rebuild flag): return at once, before any
+// table lookup, when no rebuild is due.
+template <typename A>
+__device__ __forceinline__ bool no_rebuild(const A &a) { return a.flag && *a.flag == 0; }
+
+__global__ void k_bin(const BinArgs *__restrict__ tab, WorkMap m, const int *quick) {
+    if (quick && *quick == 0) return;
+    for_each_work_unless(tab, m, no_rebuild<BinArgs>,
+                         [](const BinArgs &r, int64_t blk, int64_t nblk) { bin_body(r, blk, nblk); });
+}
+__global__ void k_scan(const BinArgs *__restrict__ tab, WorkMap m, const int *quick) {
+    if (quick && *quick == 0) return;
+    __shared__ int s_part[1024];
+    __shared__ int s_carry;
+    for_each_work_unless(tab, m, no_rebuild<BinArgs>,
+                         [&](const BinArgs &r, int64_t, int64_t) { scan_body(r, s_part, s_carry); });
+}
+__global__ void k_scatter(const BinArgs *__restrict__ tab, WorkMap m, const int *quick) {
+    if (quick && *quick == 0) return;
+    for_each_work_unless(tab, m, no_rebuild<BinArgs>,
+                         [](const BinArgs &r, int64_t blk, int64_t nblk) { scatter_body(r, blk, nblk); });
+}
+__global__ void __launch_bounds__(LB_WARPS * 32) k_lists(const ListArgs *__restrict__ tab, WorkMap m,
+                                                        const int *quick) {
+    if (quick && *quick == 0) return;
+    __shared__ ListSmem sm;
+    for_each_work_unless(tab, m, no_rebuild<ListArgs>,
+                         [&](const ListArgs &a, int64_t blk, int64_t nblk) { lists_body(a, blk, nblk, sm); });
+}
+__global__ void __launch_bounds__(128) k_rev(const RevArgs *__restrict__ tab, WorkMap m, const int *quick) {
+    if (quick && *quick == 0) return;
+    for_each_work_unless(tab, m, no_rebuild<RevArgs>,
+                         [](const RevArgs &a, int64_t blk, int64_t nblk) { rev_body(a, blk, nblk); });
+}
+__global__ void k_finish(const BinArgs *__restrict__ tab, WorkMap m, const int *quick) {
+    if (quick && *quick == 0) return;
+    for_each_work_unless(tab, m, no_rebuild<BinArgs>,
+                         [](const BinArgs &r, int64_t blk, int64_t nblk) { finish_body(r, blk, nblk); });
+}
+// clears the rebuild flag of every slot with a conditional rebuild in the launch (after the
+// whole group has read it); m is the binning kernel's map, in which every such slot has blocks
+__global__ void k_clear_flags(const BinArgs *__restrict__ tab, WorkMap m) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m.nrep; r += gridDim.x * blockDim.x)
+        if (m.w0[r + 1] > m.w0[r] && tab[r].flag) *tab[r].rebuild = 0;
+}
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -439,7 +455,9 @@ void nbr_setup(Sys &s) {
     s.cells.ncell = s.cells.nc[0] * s.cells.nc[1] * s.cells.nc[2];
 }
 
-void launch_rebuild(Sys &s, bool conditional) {
+// The rebuild group's argument blocks of system s and each kernel's block count for it.
+RebuildPlan rebuild_plan(Sys &s, bool conditional) {
+    RebuildPlan pl;
     const int *flag = conditional ? s.rebuild : nullptr;
     GridArgs g;
     for (int a = 0; a < 3; ++a) {
@@ -448,20 +466,12 @@ void launch_rebuild(Sys &s, bool conditional) {
         g.per[a] = s.per[a];
     }
     const int64_t n = s.n;
-    const int T = 256;
-    // grids are capped (grid-stride loops): when no rebuild is due every kernel returns at once
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    auto capped = [&](int64_t items, int per_block) {
-        const int64_t b = (items + per_block - 1) / per_block;
-        return (unsigned)(b < (int64_t)sms * 16 ? (b > 0 ? b : 1) : (int64_t)sms * 16);
-    };
-    k_bin<<<capped(n, T), T, 0, s.stream>>>(s.pos, n, g, s.cells.count, s.cells.of, flag);
-    k_scan<<<1, 1024, 0, s.stream>>>(s.cells.count, s.cells.start, s.cells.ncell, flag);
-    k_scatter<<<capped(n, T), T, 0, s.stream>>>(s.cells.of, n, s.cells.start, s.cells.fill, s.cells.atoms, s.posf,
-                                                s.species, s.orig, s.cells.posf, s.cells.key, flag);
-    ListArgs la;
+    BinArgs &r = pl.bin;
+    r.pos = s.pos; r.posf = s.posf; r.species = s.species; r.orig = s.orig; r.n = n; r.g = g;
+    r.ncell = s.cells.ncell; r.count = s.cells.count; r.start = s.cells.start; r.fill = s.cells.fill;
+    r.atoms = s.cells.atoms; r.of = s.cells.of; r.cposf = s.cells.posf; r.ckey = s.cells.key;
+    r.posref = s.posref; r.builds = s.d_builds; r.rebuild = s.rebuild; r.flag = flag;
+    ListArgs &la = pl.lists;
     la.pos = s.pos; la.posf = s.posf; la.species = s.species; la.orig = s.orig; la.inv = s.inv;
     la.cell_start = s.cells.start; la.cell_atoms = s.cells.atoms; la.cell_of = s.cells.of;
     la.cposf = s.cells.posf; la.ckey = s.cells.key; la.nbr_orig = s.nbr_orig;
@@ -473,16 +483,73 @@ void launch_rebuild(Sys &s, bool conditional) {
     la.cut_a2f_lo = (float)(s.cut_a2 - 0.05); la.cut_a2f_hi = (float)(s.cut_a2 + 0.05);
     la.bd = s.boxd; la.bf = s.boxf; la.g = g;
     la.nbr = s.nbr; la.seg = s.seg; la.status = s.status; la.flag = flag;
-    k_build_lists_warp<<<capped(n, LB_WARPS), LB_WARPS * 32, 0, s.stream>>>(la);
-    RevArgs ra;
+    RevArgs &ra = pl.rev;
     ra.species = s.species; ra.orig = s.orig; ra.nbr = s.nbr; ra.nbr_orig = s.nbr_orig; ra.seg = s.seg;
     ra.n = n; ra.cap = s.cap; ra.capr = nbr_orig_stride(s.cap);
     ra.rev = s.rev; ra.status = s.status; ra.flag = flag;
-    k_build_rev_warp<<<capped(n, 4), 128, 0, s.stream>>>(ra);
+    // grids are capped (grid-stride loops): when no rebuild is due every kernel returns at once
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto capped = [&](int64_t items, int per_block) -> int64_t {
+        const int64_t b = (items + per_block - 1) / per_block;
+        return b < (int64_t)sms * 16 ? (b > 0 ? b : 1) : (int64_t)sms * 16;
+    };
     const int64_t m = n > s.cells.ncell ? n : s.cells.ncell;
-    k_finish<<<capped(m, T), T, 0, s.stream>>>(s.pos, s.posref, n, s.cells.count, s.cells.fill, s.cells.ncell,
-                                               flag, s.d_builds);
-    if (conditional) k_clear_flag<<<1, 1, 0, s.stream>>>(s.rebuild);
+    pl.blocks[RB_BIN] = capped(n, RB_THREADS);
+    pl.blocks[RB_SCAN] = 1;
+    pl.blocks[RB_SCATTER] = capped(n, RB_THREADS);
+    pl.blocks[RB_LISTS] = capped(n, LB_WARPS);
+    pl.blocks[RB_REV] = capped(n, 4);
+    pl.blocks[RB_FINISH] = capped(m, RB_THREADS);
+    return pl;
+}
+
+// The system's own rebuild group: conditional (a step's, on the flag the first half raised;
+// the flag is cleared afterwards) or unconditional.
+void launch_rebuild(Sys &s, bool conditional) {
+    const int kind = conditional ? SK_STEP : SK_FULL;
+    Launch L[RB_KERNELS];
+    for (int k = 0; k < RB_KERNELS; ++k) L[k] = solo_launch(s, FK_BIN + k, kind);
+    launch_rebuild_t(s.solo->t, L, conditional, s.stream);
+}
+
+// ---- argument tables (sl_batch.h)
+void fused_put_rebuild(Sys &s, int r, int kind, const FusedTables &t, unsigned char *img, int64_t *blocks) {
+    const RebuildPlan pl = rebuild_plan(s, kind != SK_FULL);
+    reinterpret_cast<BinArgs *>(img + t.o_bin)[r] = pl.bin;
+    reinterpret_cast<ListArgs *>(img + t.o_lists)[r] = pl.lists;
+    reinterpret_cast<RevArgs *>(img + t.o_rev)[r] = pl.rev;
+    for (int k = 0; k < RB_KERNELS; ++k) blocks[FK_BIN + k] = pl.blocks[k];
+}
+
+// persistent grids: every SM filled to the kernel's occupancy (the scan: one block per slot)
+void fused_grids_rebuild(FusedTables &t) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto full = [&](const void *fn, int threads) -> unsigned {
+        int per = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0) != cudaSuccess || per < 1) per = 1;
+        return (unsigned)(sms * per);
+    };
+    t.grid[FK_BIN] = full((const void *)k_bin, RB_THREADS);
+    t.grid[FK_SCAN] = std::min<unsigned>((unsigned)t.cap, full((const void *)k_scan, 1024));
+    t.grid[FK_SCATTER] = full((const void *)k_scatter, RB_THREADS);
+    t.grid[FK_LISTS] = full((const void *)k_lists, LB_WARPS * 32);
+    t.grid[FK_REV] = full((const void *)k_rev, 128);
+    t.grid[FK_FINISH] = full((const void *)k_finish, RB_THREADS);
+}
+
+void launch_rebuild_t(const FusedTables &t, const Launch *L, bool clear, cudaStream_t st) {
+    const BinArgs *bin = t.at<BinArgs>(t.o_bin);
+    k_bin<<<L[RB_BIN].grid, RB_THREADS, 0, st>>>(bin, L[RB_BIN].m, L[RB_BIN].quick);
+    k_scan<<<L[RB_SCAN].grid, 1024, 0, st>>>(bin, L[RB_SCAN].m, L[RB_SCAN].quick);
+    k_scatter<<<L[RB_SCATTER].grid, RB_THREADS, 0, st>>>(bin, L[RB_SCATTER].m, L[RB_SCATTER].quick);
+    k_lists<<<L[RB_LISTS].grid, LB_WARPS * 32, 0, st>>>(t.at<ListArgs>(t.o_lists), L[RB_LISTS].m, L[RB_LISTS].quick);
+    k_rev<<<L[RB_REV].grid, 128, 0, st>>>(t.at<RevArgs>(t.o_rev), L[RB_REV].m, L[RB_REV].quick);
+    k_finish<<<L[RB_FINISH].grid, RB_THREADS, 0, st>>>(bin, L[RB_FINISH].m, L[RB_FINISH].quick);
+    if (clear) k_clear_flags<<<1, 128, 0, st>>>(bin, L[RB_BIN].m);
 }
 
 }  // namespace sl

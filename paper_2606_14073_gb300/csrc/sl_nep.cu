@@ -20,9 +20,12 @@
 // Atoms are stored species-major, so a warp almost always has one centre species;
 // the neighbour list is segmented by neighbour species, so inside a segment both
 // species are compile-time constants and every coefficient is a constant operand.
+#include <cstddef>
 #include <mutex>
 
 #include "sl_internal.h"
+#include "sl_batch.h"
+#include "sl_fused.cuh"
 
 namespace sl {
 
@@ -180,12 +183,8 @@ __device__ __forceinline__ void fwd_atom(const NepDev<R> &P, const EvalArgs<R> &
 // E_i = sum_h w1_h tanh(z_h) - b1, z_h = sum_v W0_hv s_v q_v - b0_h;
 // Fp_v = s_v sum_h w1_h (1 - tanh^2 z_h) W0_hv.
 template <typename R>
-__global__ void __launch_bounds__(128) k_mlp(const __grid_constant__ NepDev<R> P, const R *__restrict__ q,
-                                             R *__restrict__ fp, R *__restrict__ ei, int64_t n, int64_t qs,
-                                             const int *skip) {
-    if (skip && *skip) return;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+__device__ __forceinline__ void mlp_atom(const NepDev<R> &P, const R *__restrict__ q, R *__restrict__ fp,
+                                         R *__restrict__ ei, int64_t n, int64_t qs, int64_t i) {
     R x[DIM];
 #pragma unroll
     for (int v = 0; v < DIM; ++v) x[v] = q[(int64_t)v * qs + i] * P.scal[v];
@@ -210,18 +209,43 @@ __global__ void __launch_bounds__(128) k_mlp(const __grid_constant__ NepDev<R> P
     ei[i] = E;
 }
 
-// ------------------------------------------------------------------ launch
+// over an argument table (sl_batch.h), one 128-thread block per 128 atoms of a slot
 template <typename R>
-static void network_impl(Sys &s, const NepDev<R> &P) {
-    const unsigned nb = (unsigned)((s.n + 127) / 128);
-    k_mlp<R><<<nb, 128, 0, s.stream>>>(P, (const R *)s.q, (R *)s.fp, (R *)s.ei, s.n, s.qs, s.at.skip);
+__global__ void __launch_bounds__(128) k_mlp(const __grid_constant__ NepDev<R> P, const NetArgs<R> *__restrict__ tab,
+                                             SlotMap sm, const __grid_constant__ NetArgs<R> solo) {
+    one_work(tab, sm, solo, [&](const NetArgs<R> &a, int64_t blk, int64_t) {
+        if (a.skip && *a.skip) return;
+        const int64_t i = blk * 128 + threadIdx.x;
+        if (i < a.n) mlp_atom(P, a.q, a.fp, a.ei, a.n, a.qs, i);
+    });
 }
 
-// FP64 mode: CUDA-core network in FP64; mixed mode: the tensor-core network (sl_mlp_tc.cu)
-void launch_network(Sys &s, cudaEvent_t *) {
-    if (s.n == 0) return;
-    if (s.prec == 0) network_impl<double>(s, s.pd);
-    else launch_network_tc(s);
+// ---- argument tables (sl_batch.h): the FP64 network over NetArgs, the mixed one
+// (sl_mlp_tc.cu) over MlpArgs holding each slot's TMA map
+size_t fused_net_size(int prec) { return prec == 0 ? sizeof(NetArgs<double>) : sizeof(MlpArgs); }
+
+void fused_put_net(Sys &s, int r, int kind, const FusedTables &t, unsigned char *img, int64_t *blocks) {
+    // the midpoint iteration's evaluations stop once it has converged
+    const int *skip = kind == SK_MID && s.md ? reinterpret_cast<const int *>(reinterpret_cast<const char *>(s.md) +
+                                                                             offsetof(MidDev, converged))
+                                             : nullptr;
+    if (s.prec == 0) {
+        NetArgs<double> a;
+        a.q = (const double *)s.q; a.fp = (double *)s.fp; a.ei = (double *)s.ei; a.n = s.n; a.qs = s.qs;
+        a.skip = skip;
+        reinterpret_cast<NetArgs<double> *>(img + t.o_net)[r] = a;
+    } else {
+        MlpArgs a;
+        a.qmap = s.qmap; a.n = s.n; a.fp = (float *)s.fp; a.ei = (float *)s.ei; a.status = s.status;
+        a.skip = skip;
+        reinterpret_cast<MlpArgs *>(img + t.o_net)[r] = a;
+    }
+    blocks[FK_NET] = (s.n + 127) / 128;   // atoms of 128-thread blocks, or 128-atom tensor-core tiles
+}
+
+void launch_net_t_fp64(const FusedTables &t, const NepDev<double> &P, const Launch &L, cudaStream_t st) {
+    k_mlp<double><<<L.grid, 128, 0, st>>>(P, L.solo ? nullptr : t.at<NetArgs<double>>(t.o_net), L.slots(),
+                                          solo_args<NetArgs<double>>(L));
 }
 
 // ------------------------------------------------------------------ no-allocation variant

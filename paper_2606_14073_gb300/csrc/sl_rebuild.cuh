@@ -1,0 +1,79 @@
+// sl_rebuild.cuh -- argument blocks of the neighbour-list rebuild kernels (sl_neighbors.cu);
+// a fused batch keeps one of each per replica slot (sl_batch.h).
+#pragma once
+
+#include "sl_internal.h"
+#include "sl_fused.cuh"
+
+namespace sl {
+
+constexpr int LB_WARPS = 4;      // warps per block of the list build (one atom per warp)
+constexpr int RB_THREADS = 256;  // threads per block of the binning kernels
+
+struct GridArgs {
+    int nc[3];
+    double w[3];
+    int per[3];
+};
+
+// Every rebuild kernel's arguments for one system (binning, scan, scatter, finish).
+struct BinArgs {
+    const double4 *pos;
+    const float4 *posf;
+    const int32_t *species, *orig;
+    int64_t n;
+    GridArgs g;
+    int ncell;
+    int *count, *start, *fill, *atoms, *of;
+    float4 *cposf;
+    uint32_t *ckey;
+    double4 *posref;
+    unsigned long long *builds;
+    int *rebuild;          // the system's rebuild flag (cleared after a conditional rebuild)
+    const int *flag;       // null: unconditional; else the kernels return at once unless *flag
+};
+
+struct ListArgs {
+    const double4 *pos;
+    const float4 *posf;
+    const int32_t *species, *orig, *inv;
+    const int *cell_start, *cell_atoms, *cell_of;
+    const float4 *cposf;      // cell-ordered FP32 positions
+    const uint32_t *ckey;     // cell-ordered (species << 30 | caller index)
+    int32_t *nbr_orig;        // [n][capr] caller index of each list entry (atom-major rows of capr)
+    int64_t n;
+    int cap, cap_ang, capr;
+    double cut_r2, cut_a2;
+    float cut_r2f_lo, cut_r2f_hi, cut_a2f_lo, cut_a2f_hi;   // FP32 pre-test band
+    BoxDev<double> bd;
+    BoxDev<float> bf;
+    GridArgs g;
+    int32_t *nbr;             // [n][capr] candidate lists, atom-major
+    int4 *seg;
+    int *status;
+    const int *flag;
+};
+
+struct RevArgs {
+    const int32_t *species, *orig;
+    const int32_t *nbr, *nbr_orig;   // nbr_orig atom-major [n][capr], capr a multiple of 4
+    const int4 *seg;
+    int cap, capr;
+    int64_t n;
+    uint8_t *rev;         // [n][capr] reverse slots (cap <= 256)
+    int *status;
+    const int *flag;
+};
+
+// kernels of the group, in launch order (the flag is cleared after the last)
+constexpr int RB_BIN = 0, RB_SCAN = 1, RB_SCATTER = 2, RB_LISTS = 3, RB_REV = 4, RB_FINISH = 5, RB_KERNELS = 6;
+
+struct RebuildPlan {
+    BinArgs bin;
+    ListArgs lists;
+    RevArgs rev;
+    int64_t blocks[RB_KERNELS];   // each kernel's block count for this system
+};
+RebuildPlan rebuild_plan(Sys &s, bool conditional);
+
+}  // namespace sl

@@ -69,18 +69,19 @@ __device__ __forceinline__ void omega_of_f(float sx, float sy, float sz, float h
 // read at one slot are neighbours in memory (slot-major layout).
 template <typename R>
 __device__ __forceinline__ void gather(const GatherArgs<R> &g, int64_t k, double F[3], double H[3]) {
-    const v4<R> fo = g.fown[k], gi = g.gii[k];
+    const v4<R> fo = ro(g.fown + k), gi = ro(g.gii + k);
     R fx = fo.x, fy = fo.y, fz = fo.z, hx = -gi.x, hy = -gi.y, hz = -gi.z;
     const int64_t N = g.n;
 #pragma unroll 1
     for (int w = 0; w < g.maskw; ++w) {
-        const uint32_t word = g.mask[(int64_t)w * N + k];
+        const uint32_t word = ro(g.mask + (int64_t)w * N + k);
 #pragma unroll 4
         for (int b = 0; b < 32; ++b) {
             if ((word >> b) & 1u) {
-                const PairRec<R> e = g.pd[(int64_t)(w * 32 + b) * N + k];
-                fx -= e.a.x; fy -= e.a.y; fz -= e.a.z;
-                hx -= e.a.w; hy -= e.b.x; hz -= e.b.y;
+                const PairRec<R> *e = g.pd + (int64_t)(w * 32 + b) * N + k;
+                const v4<R> ea = ro(&e->a), eb = ro(&e->b);
+                fx -= ea.x; fy -= ea.y; fz -= ea.z;
+                hx -= ea.w; hy -= eb.x; hz -= eb.y;
             }
         }
     }

@@ -6,12 +6,14 @@ over time.  The server
   * admits a waiting request as soon as a slot is free and the device has room
     for its state (the library's own estimate against the free device memory,
     keeping a reserve), creating the replica's state on the device;
-  * steps every admitted replica together in chunks: each chunk issues the
-    replicas' captured step graphs on their own CUDA streams before waiting for
-    any of them (one sl_batch_step call), so replicas of uneven size overlap on
-    the device;
+  * steps every admitted replica together in chunks (one sl_batch_step call
+    each): the replicas sit in the slots of one batch, whose fused step launches
+    each kernel once over all of them; a replica with fewer steps left than the
+    chunk drops out of the launches when they are done;
   * retires a replica when its steps are done, records its result and its
     time from arrival to completion, and frees its memory for the next request.
+    Admission and retirement rewrite a slot of the batch's device tables; the
+    batch's captured graphs are kept.
 
 A replica's trajectory does not depend on what else runs beside it: its kernels
 read only its own state, and its noise is keyed by (seed, replica).
@@ -71,9 +73,10 @@ def poisson_requests(count: int, rate: float, *, seed: int = 20260105, cells=(12
 
 
 class GpuBackend:
-    """Replicas as libspinlat systems (mixed precision by default)."""
+    """Replicas as libspinlat systems (mixed precision by default) in the slots of one batch."""
 
-    def __init__(self, params: dict, precision=None, reserve_bytes: int = 2 << 30, steps_per_graph: int = 10):
+    def __init__(self, params: dict, precision=None, reserve_bytes: int = 2 << 30, steps_per_graph: int = 10,
+                 slots: int = 64):
         from . import spinlat as S
         import torch
         self.S = S
@@ -82,6 +85,9 @@ class GpuBackend:
         self.precision = S.SL_PREC_MIXED if precision is None else precision
         self.reserve = reserve_bytes
         self.steps_per_graph = steps_per_graph
+        self.slots = slots
+        self._batch = None
+        self._slot = {}                # id(system) -> slot
 
     def bytes_needed(self, req: Request) -> int:
         return self.S.sl_estimate_device_bytes(8 * req.cells ** 3, self.precision)
@@ -96,23 +102,23 @@ class GpuBackend:
         s = self.S.System(wl.positions, wl.spins, wl.box, wl.periodic, wl.species, self.params, wl.velocities,
                           precision=self.precision, seed=wl.seed, replica=req.replica,
                           steps_per_graph=self.steps_per_graph)
+        if self._batch is None:
+            self._batch = self.S.Batch([None] * self.slots)
+        free = self._batch.systems.index(None)     # the server admits at most `slots` replicas
+        self._batch.set(free, s)
+        self._slot[id(s)] = free
         return s
 
     def step(self, handles, n_steps, dts, Ts, Bs):
-        # the batch (and its captured graph over all replicas) is kept while the set of
-        # active replicas does not change
-        key = tuple(id(h) for h in handles)
-        if getattr(self, "_batch_key", None) != key:
-            self._drop_batch()
-            self._batch = self.S.Batch(handles)
-            self._batch_key = key
-        self._batch.step(n_steps, dts, Ts, Bs)
+        k = self.slots
+        ns, d, t, b = np.zeros(k, np.int64), np.ones(k), np.zeros(k), np.zeros((k, 3))
+        for h, n, dt, T, B in zip(handles, n_steps, dts, Ts, Bs):
+            r = self._slot[id(h)]
+            ns[r], d[r], t[r], b[r] = n, dt, T, B
+        self._batch.step(ns, d, t, b)
 
-    def _drop_batch(self):
-        b = getattr(self, "_batch", None)
-        if b is not None:
-            b.destroy()
-        self._batch, self._batch_key = None, None
+    def batch_stats(self) -> dict:
+        return self._batch.stats() if self._batch is not None else {}
 
     def result(self, h) -> dict:
         st = h.get_state()
@@ -122,8 +128,13 @@ class GpuBackend:
         return h.n
 
     def destroy(self, h):
-        self._drop_batch()   # a batch must not outlive one of its systems
+        self._batch.set(self._slot.pop(id(h)), None)   # a system leaves the batch before it is destroyed
         h.destroy()
+
+    def close(self):
+        if self._batch is not None:
+            self._batch.destroy()
+            self._batch = None
 
 
 class RealClock:
@@ -141,6 +152,8 @@ class Server:
     """Admission by free device memory, chunked continuous batching, latency records."""
 
     def __init__(self, backend, *, max_active: int = 64, chunk: int = 50, clock=None):
+        if getattr(backend, "slots", max_active) < max_active:
+            raise ValueError(f"backend has {backend.slots} slots for up to {max_active} active replicas")
         self.b = backend
         self.max_active = max_active
         self.chunk = chunk

@@ -26,7 +26,8 @@ EXPORTS = ["sl_default_options", "sl_create_system", "sl_step", "sl_energy_force
            "sl_destroy_system", "sl_last_error", "sl_batch_create", "sl_batch_step", "sl_batch_destroy",
            "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak", "sl_descriptors_energies_noalloc",
            "sl_estimate_device_bytes", "sl_get_midpoint_evaluations", "sl_set_atom_fields", "sl_texture_map",
-           "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal", "sl_selftest_carrier",
+           "sl_batch_graph_launches", "sl_batch_set", "sl_batch_stats", "sl_batch_reserve", "sl_autotune",
+           "sl_set_longitudinal", "sl_selftest_carrier",
            "sl_selftest_bounded_wait", "sl_set_spin_sweep", "sl_get_sweep_colours", "sl_get_launch_config"]
 KERNEL_GROUPS = ["first_half", "rebuild", "compact", "rad_fwd", "ang_fwd", "network", "backward", "second_half"]
 
@@ -82,6 +83,9 @@ def lib(path: str | None = None):
             L.sl_set_spin_sweep.argtypes = [P, I32]
             L.sl_get_sweep_colours.argtypes = [P, P, P, P]
             L.sl_batch_graph_launches.argtypes = [P, P]
+            L.sl_batch_set.argtypes = [P, I32, P]
+            L.sl_batch_stats.argtypes = [P, P]
+            L.sl_batch_reserve.argtypes = [P, I64]
             L.sl_autotune.argtypes = [P, I32, P, P, P]
             L.sl_get_launch_config.argtypes = [P, P, P]
             L.sl_texture_map.argtypes = [P, I32, D, P, P, P, P]
@@ -104,7 +108,8 @@ def lib(path: str | None = None):
                       "sl_get_state", "sl_set_state", "sl_get_neighbors", "sl_get_info", "sl_batch_create",
                       "sl_batch_step", "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak",
                       "sl_descriptors_energies_noalloc", "sl_get_midpoint_evaluations", "sl_set_atom_fields",
-                      "sl_texture_map", "sl_batch_graph_launches", "sl_autotune", "sl_set_longitudinal",
+                      "sl_texture_map", "sl_batch_graph_launches", "sl_batch_set", "sl_batch_stats", "sl_batch_reserve",
+                      "sl_autotune", "sl_set_longitudinal",
                       "sl_selftest_carrier", "sl_selftest_bounded_wait", "sl_set_spin_sweep",
                       "sl_get_sweep_colours", "sl_get_launch_config"):
                 getattr(L, f).restype = C.c_int
@@ -311,18 +316,24 @@ class System:
 
 
 class Batch:
-    """Replicas stepped together (sl_batch_*)."""
+    """Replicas stepped together (sl_batch_*), in fixed slots; None is an empty slot."""
 
     def __init__(self, systems):
         self.systems = list(systems)
-        arr = (C.c_void_p * len(self.systems))(*[s.handle for s in self.systems])
+        arr = (C.c_void_p * len(self.systems))(*[s.handle if s is not None else None for s in self.systems])
         h = C.c_void_p()
         _check(lib().sl_batch_create(arr, len(self.systems), C.byref(h)))
         self.handle = h
 
+    def set(self, slot: int, system):
+        """Put `system` into `slot` (None: empty the slot)."""
+        _check(lib().sl_batch_set(self.handle, int(slot), system.handle if system is not None else None))
+        self.systems[slot] = system
+
     def step(self, n_steps, dt, T, B):
         k = len(self.systems)
-        ns = np.ascontiguousarray(np.broadcast_to(n_steps, (k,)), dtype=np.int64)
+        ns = np.array(np.broadcast_to(n_steps, (k,)), dtype=np.int64)
+        ns[[i for i, x in enumerate(self.systems) if x is None]] = 0   # empty slots take no steps
         d = np.ascontiguousarray(np.broadcast_to(dt, (k,)), dtype=np.float64)
         t = np.ascontiguousarray(np.broadcast_to(T, (k,)), dtype=np.float64)
         b = np.ascontiguousarray(np.broadcast_to(np.asarray(B, dtype=np.float64), (k, 3)))
@@ -332,6 +343,16 @@ class Batch:
         v = C.c_int64()
         _check(lib().sl_batch_graph_launches(self.handle, C.byref(v)))
         return int(v.value)
+
+    def stats(self) -> dict:
+        v = (C.c_int64 * 7)()
+        _check(lib().sl_batch_stats(self.handle, v))
+        return dict(graph_launches=v[0], fused_captures=v[1], fused_steps=v[2], kernel_launches=v[3],
+                    fused_calls=v[4], replica_calls=v[5], atom_capacity=v[6])
+
+    def reserve(self, atoms: int):
+        """Size the fused launches for up to `atoms` atoms over all slots."""
+        _check(lib().sl_batch_reserve(self.handle, int(atoms)))
 
     def destroy(self):
         if getattr(self, "handle", None):

@@ -1,8 +1,9 @@
 """Served replicas against the same replicas run alone: bit-identical states.
 
-The server admits requests as they arrive and steps all admitted replicas
-together in chunks (each on its own stream); a replica's trajectory must not
-depend on what runs beside it."""
+The server admits requests as they arrive into the slots of one batch and steps all
+admitted replicas together in chunks (fused launches over every replica); a replica's
+trajectory must not depend on what runs beside it, and admissions and retirements keep
+the batch's captured graphs."""
 import numpy as np
 import pytest
 
@@ -22,6 +23,8 @@ def test_each_result_same_alone_and_in_the_mix():
     be = GpuBackend(params, reserve_bytes=0)
     out = Server(be, max_active=3, chunk=20).run(reqs)
     assert out["requests"] == len(reqs)
+    st = be.batch_stats()
+    assert st["fused_captures"] == 1 and st["replica_calls"] == 0 and st["fused_calls"] > 1
     for d in out["done"]:
         req = reqs[d.rid]
         h = be.create(req)
@@ -32,3 +35,4 @@ def test_each_result_same_alone_and_in_the_mix():
             assert np.array_equal(alone[k], d.result[k]), (d.rid, k)
         assert alone["step"] == d.result["step"] == req.n_steps
     assert out["latency_p99_s"] >= out["latency_p50_s"] > 0
+    be.close()

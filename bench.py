@@ -300,7 +300,7 @@ def run_serving(args, params, replica_offset=0):
     for r in reqs:
         r.replica += replica_offset
     be = GpuBackend(params)
-    out = Server(be, max_active=32, chunk=50).run(reqs)
+    out = Server(be, max_active=32, chunk=50, creators=4).run(reqs)
     stats = be.batch_stats()
     be.close()
     return {"requests": out["requests"], "arrival_rate_per_s": args.serve_rate,
@@ -545,18 +545,20 @@ def run_serve_sweep(args):
     params = nep_params.load()
     be = GpuBackend(params)
     burst = poisson_requests(args.serve_requests, 0.0)
-    out = Server(be, max_active=32, chunk=50).run(burst)
+    out = Server(be, max_active=32, chunk=50, creators=4).run(burst)
     work = np.mean([8 * r.cells ** 3 * r.n_steps for r in burst])
     sat_rate = out["throughput_atom_steps_per_s"] / work
     rows = [{"rate_multiple": "burst", "arrival_rate_per_s": None,
              **{k: out[k] for k in ("throughput_atom_steps_per_s", "latency_p50_s", "latency_p99_s", "makespan_s",
-                                    "memory_waits", "requests")}}]
-    for m in (0.25, 0.5, 1.0, 2.0, 4.0):
+                                    "memory_waits", "requests", "chunks", "chunk_seconds",
+                                    "chunk_atom_steps_per_s")}}]
+    for m in [float(x) for x in args.serve_rates.split(",") if x.strip()]:
         reqs = poisson_requests(args.serve_requests, m * sat_rate, seed=20260105 + int(100 * m))
-        o = Server(be, max_active=32, chunk=50).run(reqs)
+        o = Server(be, max_active=32, chunk=50, creators=4).run(reqs)
         rows.append({"rate_multiple": m, "arrival_rate_per_s": m * sat_rate,
                      **{k: o[k] for k in ("throughput_atom_steps_per_s", "latency_p50_s", "latency_p99_s",
-                                          "makespan_s", "memory_waits", "requests")}})
+                                          "makespan_s", "memory_waits", "requests", "chunks", "chunk_seconds",
+                                          "chunk_atom_steps_per_s")}})
     peak = max(r["throughput_atom_steps_per_s"] for r in rows)
     line = _common_line(args, peak, 0.0, 1, "fege_serving_sweep",
                         {"requests_per_rate": args.serve_requests, "precision": "mixed",
@@ -905,6 +907,8 @@ def main():
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=8.0, help="request arrivals per second")
+    ap.add_argument("--serve-rates", default="0.25,0.5,1,2,4",
+                    help="serve-sweep: arrival rates as multiples of the saturation rate (after the burst)")
     ap.add_argument("--workload", choices=["cube", "slab", "replicas", "serve-sweep", "protocol", "accuracy",
                                            "sweep"],
                     default="cube",

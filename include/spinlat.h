@@ -323,6 +323,14 @@ int sl_batch_set(sl_batch *b, int32_t slot, sl_system *sys);
  * keep their steps, and the first error is returned. */
 int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt_fs, const double *T_K,
                   const double *B_tesla /* [k][3] */);
+/* sl_batch_step in two halves: submit queues the call's steps on the device and returns at
+ * once; wait finishes them (status, restores, step counters) and returns the first error.
+ * Between the two, the replicas taking part must not be used and their slots not changed
+ * (SL_EINVAL); empty slots may be filled, and other systems created and used, meanwhile.
+ * A second submit before the wait is SL_EINVAL; wait with nothing in flight is SL_OK. */
+int sl_batch_submit(sl_batch *b, const int64_t *n_steps, const double *dt_fs, const double *T_K,
+                    const double *B_tesla /* [k][3] */);
+int sl_batch_wait(sl_batch *b);
 /* Number of graph launches of the batch stream (fused graphs, or fork/join graphs that
  * advanced every replica together by steps_per_graph steps). */
 int sl_batch_graph_launches(const sl_batch *b, int64_t *launches);

@@ -56,6 +56,8 @@ struct sl_batch {
     int64_t graph_launches = 0;
     int64_t fused_steps = 0, kernel_launches = 0, fused_calls = 0, replica_calls = 0;
     int64_t reserve_atoms = 0;        // atoms the fused launches are sized for (sl_batch_reserve)
+    // a submitted call not yet waited for: the slots taking part and their step counts
+    std::vector<std::pair<int, int64_t>> in_flight;
     sl::FusedBatch fused;
     ~sl_batch() {
         if (graph) cudaGraphExecDestroy(graph);
@@ -1390,6 +1392,8 @@ int sl_batch_create(sl_system *const *systems, int32_t k, sl_batch **out) {
 int sl_batch_set(sl_batch *b, int32_t slot, sl_system *sys) {
     if (!b) return fail(SL_EINVAL, "NULL batch");
     if (slot < 0 || slot >= (int)b->sys.size()) return fail(SL_EINVAL, "slot %d outside [0, %d)", slot, (int)b->sys.size());
+    for (const auto &f : b->in_flight)
+        if (f.first == slot) return fail(SL_EINVAL, "slot %d takes part in a call not yet waited for", slot);
     if (sys) {
         const int prec = batch_precision(b, slot);
         if (prec >= 0 && sys->s.prec != prec) return fail(SL_EINVAL, "mixed precision modes in a batch");
@@ -1536,9 +1540,12 @@ static int replica_steps(sl_batch *b, const std::vector<int> &active, const int6
     return SL_OK;
 }
 
-int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt, const double *T, const double *B) {
-    NvtxRange nvtx_range("sl_batch_step");
+// Queue a call's steps (fused or on the replicas' own streams) and return; the replicas taking
+// part are recorded as in flight.
+int sl_batch_submit(sl_batch *b, const int64_t *n_steps, const double *dt, const double *T, const double *B) {
+    NvtxRange nvtx_range("sl_batch_submit");
     if (!b || !n_steps || !dt || !T || !B) return fail(SL_EINVAL, "NULL argument");
+    if (!b->in_flight.empty()) return fail(SL_EINVAL, "a submitted call has not been waited for");
     const int k = (int)b->sys.size();
     for (int i = 0; i < k; ++i) {
         if (!b->sys[i]) {
@@ -1570,20 +1577,40 @@ int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt, const d
         for (auto &e : b->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     rc = fusable(b, active) ? fused_steps(b, active, n_steps) : replica_steps(b, active, n_steps);
-    if (rc) return rc;
-    // every replica is finished (and restored where it failed) before the first error is returned
-    int first = SL_OK;
+    if (rc) {   // nothing is left running for the caller to wait for
+        for (int i : active) cudaStreamSynchronize(b->sys[i]->s.stream);
+        if (b->stream) cudaStreamSynchronize(b->stream);
+        return rc;
+    }
+    for (int i : active) b->in_flight.emplace_back(i, n_steps[i]);
+    return SL_OK;
+}
+
+// Finish the submitted call: every replica is finished (and restored to its state before the
+// call where it failed) before the first error is returned.
+int sl_batch_wait(sl_batch *b) {
+    NvtxRange nvtx_range("sl_batch_wait");
+    if (!b) return fail(SL_EINVAL, "NULL batch");
+    std::vector<std::pair<int, int64_t>> flight;
+    flight.swap(b->in_flight);
+    int first = SL_OK, rc;
     std::string first_msg;
-    for (int i : active) {
-        sl::Sys &s = b->sys[i]->s;
+    for (const auto &f : flight) {
+        sl::Sys &s = b->sys[f.first]->s;
         cudaSetDevice(s.device);
         char who[32];
-        std::snprintf(who, sizeof who, "replica %d: ", i);
-        rc = finish_steps(s, n_steps[i], who);
+        std::snprintf(who, sizeof who, "replica %d: ", f.first);
+        rc = finish_steps(s, f.second, who);
         if (rc && first == SL_OK) { first = rc; first_msg = g_err; }
     }
     if (first != SL_OK) return fail(first, "%s", first_msg.c_str());
     return SL_OK;
+}
+
+int sl_batch_step(sl_batch *b, const int64_t *n_steps, const double *dt, const double *T, const double *B) {
+    const int rc = sl_batch_submit(b, n_steps, dt, T, B);
+    if (rc) return rc;
+    return sl_batch_wait(b);
 }
 
 int sl_batch_reserve(sl_batch *b, int64_t atoms) {

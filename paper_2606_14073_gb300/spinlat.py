@@ -26,8 +26,8 @@ EXPORTS = ["sl_default_options", "sl_create_system", "sl_step", "sl_energy_force
            "sl_destroy_system", "sl_last_error", "sl_batch_create", "sl_batch_step", "sl_batch_destroy",
            "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak", "sl_descriptors_energies_noalloc",
            "sl_estimate_device_bytes", "sl_get_midpoint_evaluations", "sl_set_atom_fields", "sl_texture_map",
-           "sl_batch_graph_launches", "sl_batch_set", "sl_batch_stats", "sl_batch_reserve", "sl_autotune",
-           "sl_set_longitudinal", "sl_selftest_carrier",
+           "sl_batch_graph_launches", "sl_batch_set", "sl_batch_stats", "sl_batch_reserve", "sl_batch_submit",
+           "sl_batch_wait", "sl_autotune", "sl_set_longitudinal", "sl_selftest_carrier",
            "sl_selftest_bounded_wait", "sl_set_spin_sweep", "sl_get_sweep_colours", "sl_get_launch_config"]
 KERNEL_GROUPS = ["first_half", "rebuild", "compact", "rad_fwd", "ang_fwd", "network", "backward", "second_half"]
 
@@ -86,6 +86,8 @@ def lib(path: str | None = None):
             L.sl_batch_set.argtypes = [P, I32, P]
             L.sl_batch_stats.argtypes = [P, P]
             L.sl_batch_reserve.argtypes = [P, I64]
+            L.sl_batch_submit.argtypes = [P, P, P, P, P]
+            L.sl_batch_wait.argtypes = [P]
             L.sl_autotune.argtypes = [P, I32, P, P, P]
             L.sl_get_launch_config.argtypes = [P, P, P]
             L.sl_texture_map.argtypes = [P, I32, D, P, P, P, P]
@@ -109,7 +111,7 @@ def lib(path: str | None = None):
                       "sl_batch_step", "sl_selftest_harmonics", "sl_step_profiled", "sl_measure_fma_peak",
                       "sl_descriptors_energies_noalloc", "sl_get_midpoint_evaluations", "sl_set_atom_fields",
                       "sl_texture_map", "sl_batch_graph_launches", "sl_batch_set", "sl_batch_stats", "sl_batch_reserve",
-                      "sl_autotune", "sl_set_longitudinal",
+                      "sl_batch_submit", "sl_batch_wait", "sl_autotune", "sl_set_longitudinal",
                       "sl_selftest_carrier", "sl_selftest_bounded_wait", "sl_set_spin_sweep",
                       "sl_get_sweep_colours", "sl_get_launch_config"):
                 getattr(L, f).restype = C.c_int
@@ -330,14 +332,26 @@ class Batch:
         _check(lib().sl_batch_set(self.handle, int(slot), system.handle if system is not None else None))
         self.systems[slot] = system
 
-    def step(self, n_steps, dt, T, B):
+    def _args(self, n_steps, dt, T, B):
         k = len(self.systems)
         ns = np.array(np.broadcast_to(n_steps, (k,)), dtype=np.int64)
         ns[[i for i, x in enumerate(self.systems) if x is None]] = 0   # empty slots take no steps
         d = np.ascontiguousarray(np.broadcast_to(dt, (k,)), dtype=np.float64)
         t = np.ascontiguousarray(np.broadcast_to(T, (k,)), dtype=np.float64)
         b = np.ascontiguousarray(np.broadcast_to(np.asarray(B, dtype=np.float64), (k, 3)))
+        return ns, d, t, b
+
+    def step(self, n_steps, dt, T, B):
+        ns, d, t, b = self._args(n_steps, dt, T, B)
         _check(lib().sl_batch_step(self.handle, _ptr(ns), _ptr(d), _ptr(t), _ptr(b)))
+
+    def submit(self, n_steps, dt, T, B):
+        """Queue the steps and return at once; wait() finishes them."""
+        ns, d, t, b = self._args(n_steps, dt, T, B)
+        _check(lib().sl_batch_submit(self.handle, _ptr(ns), _ptr(d), _ptr(t), _ptr(b)))
+
+    def wait(self):
+        _check(lib().sl_batch_wait(self.handle))
 
     def graph_launches(self) -> int:
         v = C.c_int64()

@@ -141,3 +141,29 @@ def test_slot_errors(params):
     b.destroy()
     m.destroy()
     f.destroy()
+
+
+def test_submit_and_wait(params):
+    """A submitted call runs while the host fills an empty slot; the slots taking part are locked
+    until the wait, and a second submit before it is refused; results match the runs alone."""
+    prec = S.SL_PREC_MIXED
+    wa, wb = W.fege_cube(5, seed=370, replica=50), W.fege_cube(4, seed=371, replica=51)
+    a = _system(params, wa, prec)
+    batch = S.Batch([a, None])
+    batch.submit([11, 0], 1.0, [200.0, 0.0], (0, 0, 0.2))
+    b = _system(params, wb, prec)          # created while the call runs
+    batch.set(1, b)                        # an empty slot may be filled
+    with pytest.raises(S.SpinlatError) as e:
+        batch.set(0, None)                 # a slot taking part may not
+    assert e.value.code == S.SL_EINVAL
+    with pytest.raises(S.SpinlatError) as e:
+        batch.submit([1, 1], 1.0, [200.0, 200.0], (0, 0, 0.2))
+    assert e.value.code == S.SL_EINVAL
+    batch.wait()
+    batch.wait()                           # nothing in flight
+    batch.step([4, 9], 1.0, [200.0, 100.0], (0, 0, 0.2))
+    _same(a.get_state(), _alone(params, wa, prec, [(11, 200.0, 0.2), (4, 200.0, 0.2)]))
+    _same(b.get_state(), _alone(params, wb, prec, [(9, 100.0, 0.2)]))
+    batch.destroy()
+    a.destroy()
+    b.destroy()

@@ -13,7 +13,8 @@ from paper_2606_14073_gb300.serving import GpuBackend, Request, Server
 pytestmark = pytest.mark.gpu
 
 
-def test_each_result_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("creators", [0, 2])
+def test_each_result_same_alone_and_in_the_mix(creators):
     params = nep_params.load()
     reqs = [Request(0, cells=6, T=300.0, B=(0, 0, 0.2), n_steps=60, arrival=0.0, replica=0),
             Request(1, cells=4, T=150.0, B=(0, 0, 0.0), n_steps=35, arrival=0.0, replica=1),
@@ -21,13 +22,14 @@ def test_each_result_same_alone_and_in_the_mix():
             Request(3, cells=7, T=80.0, B=(0, 0, 0.1), n_steps=23, arrival=0.05, replica=3),
             Request(4, cells=4, T=320.0, B=(0, 0, 0.5), n_steps=71, arrival=0.08, replica=4)]
     be = GpuBackend(params, reserve_bytes=0)
-    out = Server(be, max_active=3, chunk=20).run(reqs)
+    out = Server(be, max_active=3, chunk=20, creators=creators).run(reqs)
     assert out["requests"] == len(reqs)
     st = be.batch_stats()
     assert st["fused_captures"] == 1 and st["replica_calls"] == 0 and st["fused_calls"] > 1
     for d in out["done"]:
         req = reqs[d.rid]
         h = be.create(req)
+        be.attach(h)
         h.step(req.n_steps, req.dt, req.T, req.B)
         alone = be.result(h)
         be.destroy(h)

@@ -102,3 +102,58 @@ def test_poisson_request_family():
     gaps = np.diff([r.arrival for r in reqs])
     assert (gaps > 0).all() and abs(gaps.mean() - 0.5) < 0.25
     assert all(12 <= r.cells <= 40 and 200 <= r.n_steps <= 2000 for r in reqs)
+
+
+class SlowCreateBackend(FakeBackend):
+    """Creating a replica costs `create_s` seconds of host time."""
+
+    def __init__(self, clock, create_s=0.5, **kw):
+        super().__init__(clock, **kw)
+        self.create_s = create_s
+
+    def create(self, req):
+        self.clock.t += self.create_s
+        return super().create(req)
+
+
+class AsyncBackend(SlowCreateBackend):
+    """Chunks are submitted and run on simulated device time while the host goes on (creating
+    replicas); wait() returns when the device is done."""
+
+    def __init__(self, clock, **kw):
+        super().__init__(clock, **kw)
+        self.busy_until = 0.0
+        self.flight = None
+
+    def submit(self, handles, n_steps, dts, Ts, Bs):
+        assert self.flight is None
+        work = sum(8 * self.live[h].cells ** 3 * n for h, n in zip(handles, n_steps))
+        self.busy_until = max(self.clock.t, self.busy_until) + work / self.rate
+        self.flight = list(zip(handles, n_steps))
+
+    def wait(self):
+        for h, n in self.flight:
+            self.steps_done[h] += n
+        self.flight = None
+        self.clock.t = max(self.clock.t, self.busy_until)
+
+    def destroy(self, h):
+        assert self.flight is None or all(h != f for f, _ in self.flight)   # never while in flight
+        super().destroy(h)
+
+
+def test_admission_overlaps_the_chunk_in_flight():
+    """With submit/wait the server creates newly arrived replicas while a chunk runs, so host
+    creation time hides behind device time; every request still gets exactly its steps."""
+    reqs = [Request(k, cells=10, T=300.0, B=(0, 0, 0), n_steps=200 + 50 * k, arrival=0.3 * k) for k in range(8)]
+    results = {}
+    for name, cls in (("sync", SlowCreateBackend), ("overlap", AsyncBackend)):
+        clock = FakeClock()
+        be = cls(clock, capacity=10 ** 9, rate=2e6, create_s=0.4)
+        out = Server(be, max_active=4, chunk=50, clock=clock).run([Request(**vars(r)) for r in reqs])
+        assert out["requests"] == len(reqs) and be.used == 0
+        for d in out["done"]:
+            assert d.result["steps"] == d.n_steps
+            assert d.finished >= d.admitted >= d.arrival
+        results[name] = out["makespan_s"]
+    assert results["overlap"] < results["sync"]

@@ -75,7 +75,7 @@ void FusedBatch::enqueue(cudaStream_t st) const {
     launch_first_half_t(t, L(FK_FIRST), st);
     Launch rb[FK_FINISH - FK_BIN + 1];
     for (int k = FK_BIN; k <= FK_FINISH; ++k) rb[k - FK_BIN] = L(k);
-    launch_rebuild_t(t, rb, true, st);
+    launch_rebuild_t(t, rb, true, true, st);
     const Launch ev[4] = {L(FK_CRAD), L(FK_ANG), L(FK_NET), L(FK_BWD)};
     if (t.prec == 0) launch_eval_t<double>(t, pd, ev, st, nullptr);
     else launch_eval_t<float>(t, pf, ev, st, nullptr);

@@ -110,8 +110,9 @@ void launch_fused_plan(const FusedTables &t, cudaStream_t st);
 void launch_first_half_t(const FusedTables &t, const Launch &L, cudaStream_t st);
 void launch_second_half_t(const FusedTables &t, const Launch &L, bool spin, cudaStream_t st);
 // the rebuild group: L[0 .. 5] for the binning, scan, scatter, lists, reverse slots and finish
-// kernels; clear: then the flags of the conditional slots in L[0]'s map are cleared
-void launch_rebuild_t(const FusedTables &t, const Launch *L, bool clear, cudaStream_t st);
+// kernels; clear: then the flags of the conditional slots in L[0]'s map are cleared; loop: the
+// persistent form (a batch's), else one work item per block (a system's own launches)
+void launch_rebuild_t(const FusedTables &t, const Launch *L, bool clear, bool loop, cudaStream_t st);
 // radial, angular, network, backward; ev (optional, 6 events): recorded before the radial
 // kernel, after it, after the angular kernel, after the network and after the backward
 template <typename R>

@@ -118,6 +118,19 @@ __device__ __forceinline__ void one_work(const A *__restrict__ tab, const SlotMa
     body(*reinterpret_cast<const A *>(s_args), blk, 0);
 }
 
+// body(args of the item's slot, local block, local block count) for work item blockIdx.x of
+// the map alone: one item per block (blocks past the map's total return at once), without the
+// loop's state living across the body.
+template <typename A, typename Body>
+__device__ __forceinline__ void map_item(const A *__restrict__ tab, const WorkMap &m, Body body) {
+    const int64_t w = blockIdx.x;
+    if (w >= __ldg(m.w0 + m.nrep)) return;   // block-uniform
+    const int r = work_replica(m, w);
+    const int64_t b0 = __ldg(m.w0 + r);
+    int cur = -1;
+    body(slot_args(tab, r, cur), w - b0, __ldg(m.w0 + r + 1) - b0);
+}
+
 // The same as for_each_work, passing over every item of a slot for which idle(args) holds (block-uniform:
 // the block moves on to its first item past the slot's range).
 template <typename A, typename Idle, typename Body>

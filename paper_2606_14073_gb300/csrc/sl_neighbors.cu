@@ -161,7 +161,8 @@ struct ListSmem {
     int off[LB_WARPS][32], p0[LB_WARPS][32];   // stencil cells of each warp's atom
 };
 
-__device__ __forceinline__ void lists_body(const ListArgs &a, int64_t blk, int64_t nblk, ListSmem &sm) {
+__device__ __forceinline__ void lists_body(const ListArgs &args, int64_t blk, int64_t nblk, ListSmem &sm) {
+    const ListArgs a = args;   // as values: the stores below cannot make the compiler re-read them
     if (a.flag && *a.flag == 0) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t *key = sm.key[w];
@@ -331,7 +332,8 @@ __device__ __forceinline__ int find_rest(const int32_t *__restrict__ row, int b,
 // s, t_i).  Each lane takes four slots 32 apart: their list entries, then their neighbours'
 // segment bounds, then two first search rounds at a time are in flight together.  A pair
 // found in one list only (a list cut at its capacity) raises the overflow status.
-__device__ __forceinline__ void rev_body(const RevArgs &a, int64_t blk, int64_t nblk) {
+__device__ __forceinline__ void rev_body(const RevArgs &args, int64_t blk, int64_t nblk) {
+    const RevArgs a = args;   // as values: the stores below cannot make the compiler re-read them
     if (a.flag && *a.flag == 0) return;
     const int lane = threadIdx.x & 31;
     for (int64_t i = blk * 4 + (threadIdx.x >> 5); i < a.n; i += nblk * 4) {
@@ -395,45 +397,60 @@ __device__ __forceinline__ void finish_body(const BinArgs &r, int64_t blk, int64
 }
 
 // The group over an argument table (sl_batch.h: a system's own table or a batch's), one
-// launch per kernel; a slot with no rebuild due this step is passed over as a whole.
+// launch per kernel.  LOOP: a batch's persistent grid walks the work map, passing over a slot
+// with no rebuild due as a whole; otherwise (a system's own launch, whose grid is its block
+// count) one item per block, which keeps the loop's state out of the latency-bound bodies'
+// registers.  The lists do not depend on the form: integer work, an FP32 pre-test that decides
+// only far from the cutoffs, and an FP64 test in explicitly rounded operations.
 // quick (a system's own conditional launch: its rebuild flag): return at once, before any
 // table lookup, when no rebuild is due.
 template <typename A>
 __device__ __forceinline__ bool no_rebuild(const A &a) { return a.flag && *a.flag == 0; }
 
+template <bool LOOP, typename A, typename Body>
+__device__ __forceinline__ void rebuild_items(const A *__restrict__ tab, const WorkMap &m, Body body) {
+    if constexpr (LOOP) for_each_work_unless(tab, m, no_rebuild<A>, body);
+    else map_item(tab, m, body);
+}
+
+// register budget of a system's own list build: the latency-bound walk wants occupancy
+#ifndef LISTS_MINB
+#define LISTS_MINB 8
+#endif
+
+template <bool LOOP>
 __global__ void k_bin(const BinArgs *__restrict__ tab, WorkMap m, const int *quick) {
     if (quick && *quick == 0) return;
-    for_each_work_unless(tab, m, no_rebuild<BinArgs>,
-                         [](const BinArgs &r, int64_t blk, int64_t nblk) { bin_body(r, blk, nblk); });
+    rebuild_items<LOOP>(tab, m, [](const BinArgs &r, int64_t blk, int64_t nblk) { bin_body(r, blk, nblk); });
 }
+template <bool LOOP>
 __global__ void k_scan(const BinArgs *__restrict__ tab, WorkMap m, const int *quick) {
     if (quick && *quick == 0) return;
     __shared__ int s_part[1024];
     __shared__ int s_carry;
-    for_each_work_unless(tab, m, no_rebuild<BinArgs>,
-                         [&](const BinArgs &r, int64_t, int64_t) { scan_body(r, s_part, s_carry); });
+    rebuild_items<LOOP>(tab, m, [&](const BinArgs &r, int64_t, int64_t) { scan_body(r, s_part, s_carry); });
 }
+template <bool LOOP>
 __global__ void k_scatter(const BinArgs *__restrict__ tab, WorkMap m, const int *quick) {
     if (quick && *quick == 0) return;
-    for_each_work_unless(tab, m, no_rebuild<BinArgs>,
-                         [](const BinArgs &r, int64_t blk, int64_t nblk) { scatter_body(r, blk, nblk); });
+    rebuild_items<LOOP>(tab, m, [](const BinArgs &r, int64_t blk, int64_t nblk) { scatter_body(r, blk, nblk); });
 }
-__global__ void __launch_bounds__(LB_WARPS * 32) k_lists(const ListArgs *__restrict__ tab, WorkMap m,
-                                                        const int *quick) {
+template <bool LOOP>
+__global__ void __launch_bounds__(LB_WARPS * 32, LOOP ? 4 : LISTS_MINB) k_lists(const ListArgs *__restrict__ tab,
+                                                                              WorkMap m, const int *quick) {
     if (quick && *quick == 0) return;
     __shared__ ListSmem sm;
-    for_each_work_unless(tab, m, no_rebuild<ListArgs>,
-                         [&](const ListArgs &a, int64_t blk, int64_t nblk) { lists_body(a, blk, nblk, sm); });
+    rebuild_items<LOOP>(tab, m, [&](const ListArgs &a, int64_t blk, int64_t nblk) { lists_body(a, blk, nblk, sm); });
 }
+template <bool LOOP>
 __global__ void __launch_bounds__(128) k_rev(const RevArgs *__restrict__ tab, WorkMap m, const int *quick) {
     if (quick && *quick == 0) return;
-    for_each_work_unless(tab, m, no_rebuild<RevArgs>,
-                         [](const RevArgs &a, int64_t blk, int64_t nblk) { rev_body(a, blk, nblk); });
+    rebuild_items<LOOP>(tab, m, [](const RevArgs &a, int64_t blk, int64_t nblk) { rev_body(a, blk, nblk); });
 }
+template <bool LOOP>
 __global__ void k_finish(const BinArgs *__restrict__ tab, WorkMap m, const int *quick) {
     if (quick && *quick == 0) return;
-    for_each_work_unless(tab, m, no_rebuild<BinArgs>,
-                         [](const BinArgs &r, int64_t blk, int64_t nblk) { finish_body(r, blk, nblk); });
+    rebuild_items<LOOP>(tab, m, [](const BinArgs &r, int64_t blk, int64_t nblk) { finish_body(r, blk, nblk); });
 }
 // clears the rebuild flag of every slot with a conditional rebuild in the launch (after the
 // whole group has read it); m is the binning kernel's map, in which every such slot has blocks
@@ -511,7 +528,7 @@ void launch_rebuild(Sys &s, bool conditional) {
     const int kind = conditional ? SK_STEP : SK_FULL;
     Launch L[RB_KERNELS];
     for (int k = 0; k < RB_KERNELS; ++k) L[k] = solo_launch(s, FK_BIN + k, kind);
-    launch_rebuild_t(s.solo->t, L, conditional, s.stream);
+    launch_rebuild_t(s.solo->t, L, conditional, false, s.stream);
 }
 
 // ---- argument tables (sl_batch.h)
@@ -533,23 +550,29 @@ void fused_grids_rebuild(FusedTables &t) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0) != cudaSuccess || per < 1) per = 1;
         return (unsigned)(sms * per);
     };
-    t.grid[FK_BIN] = full((const void *)k_bin, RB_THREADS);
-    t.grid[FK_SCAN] = std::min<unsigned>((unsigned)t.cap, full((const void *)k_scan, 1024));
-    t.grid[FK_SCATTER] = full((const void *)k_scatter, RB_THREADS);
-    t.grid[FK_LISTS] = full((const void *)k_lists, LB_WARPS * 32);
-    t.grid[FK_REV] = full((const void *)k_rev, 128);
-    t.grid[FK_FINISH] = full((const void *)k_finish, RB_THREADS);
+    t.grid[FK_BIN] = full((const void *)k_bin<true>, RB_THREADS);
+    t.grid[FK_SCAN] = std::min<unsigned>((unsigned)t.cap, full((const void *)k_scan<true>, 1024));
+    t.grid[FK_SCATTER] = full((const void *)k_scatter<true>, RB_THREADS);
+    t.grid[FK_LISTS] = full((const void *)k_lists<true>, LB_WARPS * 32);
+    t.grid[FK_REV] = full((const void *)k_rev<true>, 128);
+    t.grid[FK_FINISH] = full((const void *)k_finish<true>, RB_THREADS);
 }
 
-void launch_rebuild_t(const FusedTables &t, const Launch *L, bool clear, cudaStream_t st) {
+template <bool LOOP>
+static void rebuild_t(const FusedTables &t, const Launch *L, bool clear, cudaStream_t st) {
     const BinArgs *bin = t.at<BinArgs>(t.o_bin);
-    k_bin<<<L[RB_BIN].grid, RB_THREADS, 0, st>>>(bin, L[RB_BIN].m, L[RB_BIN].quick);
-    k_scan<<<L[RB_SCAN].grid, 1024, 0, st>>>(bin, L[RB_SCAN].m, L[RB_SCAN].quick);
-    k_scatter<<<L[RB_SCATTER].grid, RB_THREADS, 0, st>>>(bin, L[RB_SCATTER].m, L[RB_SCATTER].quick);
-    k_lists<<<L[RB_LISTS].grid, LB_WARPS * 32, 0, st>>>(t.at<ListArgs>(t.o_lists), L[RB_LISTS].m, L[RB_LISTS].quick);
-    k_rev<<<L[RB_REV].grid, 128, 0, st>>>(t.at<RevArgs>(t.o_rev), L[RB_REV].m, L[RB_REV].quick);
-    k_finish<<<L[RB_FINISH].grid, RB_THREADS, 0, st>>>(bin, L[RB_FINISH].m, L[RB_FINISH].quick);
+    k_bin<LOOP><<<L[RB_BIN].grid, RB_THREADS, 0, st>>>(bin, L[RB_BIN].m, L[RB_BIN].quick);
+    k_scan<LOOP><<<L[RB_SCAN].grid, 1024, 0, st>>>(bin, L[RB_SCAN].m, L[RB_SCAN].quick);
+    k_scatter<LOOP><<<L[RB_SCATTER].grid, RB_THREADS, 0, st>>>(bin, L[RB_SCATTER].m, L[RB_SCATTER].quick);
+    k_lists<LOOP><<<L[RB_LISTS].grid, LB_WARPS * 32, 0, st>>>(t.at<ListArgs>(t.o_lists), L[RB_LISTS].m,
+                                                              L[RB_LISTS].quick);
+    k_rev<LOOP><<<L[RB_REV].grid, 128, 0, st>>>(t.at<RevArgs>(t.o_rev), L[RB_REV].m, L[RB_REV].quick);
+    k_finish<LOOP><<<L[RB_FINISH].grid, RB_THREADS, 0, st>>>(bin, L[RB_FINISH].m, L[RB_FINISH].quick);
     if (clear) k_clear_flags<<<1, 128, 0, st>>>(bin, L[RB_BIN].m);
+}
+void launch_rebuild_t(const FusedTables &t, const Launch *L, bool clear, bool loop, cudaStream_t st) {
+    if (loop) rebuild_t<true>(t, L, clear, st);
+    else rebuild_t<false>(t, L, clear, st);
 }
 
 }  // namespace sl

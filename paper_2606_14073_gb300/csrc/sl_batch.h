@@ -21,7 +21,7 @@ namespace sl {
 
 // kernels of one step, in launch order
 enum FusedKernel {
-    FK_FIRST, FK_BIN, FK_SCAN, FK_SCATTER, FK_LISTS, FK_REV, FK_FINISH,
+    FK_FIRST, FK_BIN, FK_SCAN, FK_SCATTER, FK_CELLSORT, FK_LISTS, FK_REV, FK_FINISH,
     FK_CRAD, FK_ANG, FK_NET, FK_BWD, FK_SECOND, FK_N
 };
 constexpr int FUSED_LAUNCHES_PER_STEP = 1 + FK_N + 1;   // plan, the kernels, the flag clear

@@ -227,7 +227,7 @@ int default_quad_block(int prec);   // threads per block of the quad kernels by 
 int make_q_tensor_map(Sys &s);                   // sl_mlp_tc.cu: the TMA map of s.q; 0 on success
 // first half, rebuild group (7), compaction with radial forward, angular forward, network, backward,
 // second half
-constexpr int KERNELS_PER_STEP = 1 + 7 + 2 + 1 + 1 + 1;
+constexpr int KERNELS_PER_STEP = 1 + 8 + 2 + 1 + 1 + 1;
 // sl_integrate.cu
 void launch_first_half(Sys &s);
 void launch_second_half(Sys &s);

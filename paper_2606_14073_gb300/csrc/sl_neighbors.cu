@@ -11,9 +11,11 @@
 // cutoff; only pairs within a margin of it take the exact FP64 test.
 // Each list is split in four segments -- angular candidates (d2 < (rc_ang+skin)^2)
 // of neighbour species 0 and 1, then the remaining radial candidates of species
-// 0 and 1 -- and each segment is ordered by the neighbour's caller index, so every
-// per-atom sum runs in an order that does not depend on the internal atom order.
+// 0 and 1 -- and each segment is in the order of the stencil walk (cells z-major,
+// each cell's atoms by caller index), so every per-atom sum runs in an order set by
+// the positions and caller indices alone, never by the internal atom order.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 
 #include "sl_internal.h"
@@ -25,12 +27,15 @@ namespace sl {
 
 namespace {
 
+// The list definition's d2.  |t| <= L/2 gives |t/L| <= 1/2, so the rounded quotient lies in
+// [-1/2, 1/2] and rint (ties to even) returns a zero: t is then left as it is, without the
+// division, and the result (up to the sign of a zero, which squaring removes) is the same.
 __device__ __forceinline__ double exact_d2(double xi, double yi, double zi, double xj, double yj, double zj,
                                            const BoxDev<double> &b, const int per[3]) {
     double t[3] = {__dsub_rn(xj, xi), __dsub_rn(yj, yi), __dsub_rn(zj, zi)};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (per[a]) {
+        if (per[a] && fabs(t[a]) > 0.5 * b.L[a]) {
             const double q = rint(__ddiv_rn(t[a], b.L[a]));
             t[a] = __dsub_rn(t[a], __dmul_rn(b.L[a], q));
         }
@@ -86,31 +91,33 @@ __device__ __forceinline__ void scan_body(const BinArgs &r, int *s_part, int &s_
     __syncthreads();   // the block's next work item reuses s_part and s_carry
 }
 
-// Atoms into their cells, with a cell-ordered copy of the FP32 position and of the
-// key (species << 30 | caller index) so the list build reads candidates contiguously.
+// Atoms into their cells, with a cell-ordered copy of the key (species << 30 | caller index)
+// and of the position relative to the cell's corner in FP32 (NaN for an atom more than a
+// cell width outside its cell, which only a non-periodic axis can hold), so the list build
+// reads candidates contiguously.
 __device__ __forceinline__ void scatter_body(const BinArgs &r, int64_t blk, int64_t nblk) {
     if (r.flag && *r.flag == 0) return;
+    const GridArgs &g = r.g;
     for (int64_t i = blk * (int64_t)blockDim.x + threadIdx.x; i < r.n; i += nblk * blockDim.x) {
         const int c = r.of[i];
         const int p = r.start[c] + atomicAdd(r.fill + c, 1);
+        const double4 x = r.pos[i];
+        const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
+        const double u[3] = {x.x - cx * g.w[0], x.y - cy * g.w[1], x.z - cz * g.w[2]};
+        bool near = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) near = near && u[d] >= -g.w[d] && u[d] <= 2.0 * g.w[d];
         r.atoms[p] = (int)i;
-        r.cposf[p] = r.posf[i];
+        r.cposf[p] = near ? make_float4((float)u[0], (float)u[1], (float)u[2], 0.f)
+                          : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
         r.ckey[p] = ((uint32_t)r.species[i] << 30) | (uint32_t)r.orig[i];
     }
 }
 
-
-
-
-// Warp per atom.  Lanes take the candidates of the stencil cells 32 at a time;
-// pairs inside the list cutoff are appended to a per-warp shared-memory buffer
-// (ballot/popc, so the append order is the scan order), the buffer is sorted
-// by (segment, caller index) with a warp bitonic sort, and written out.
-
-// Ascending bitonic sort of 32*E keys held E per lane (element r*32 + lane in
+// Ascending bitonic sort of 32*E 64-bit keys held E per lane (element r*32 + lane in
 // register r): strides below 32 exchange through shuffles, larger ones inside the lane.
 template <int E>
-__device__ __forceinline__ void warp_bitonic(uint32_t (&k)[E], int lane) {
+__device__ __forceinline__ void warp_bitonic64(uint64_t (&k)[E], int lane) {
 #pragma unroll
     for (int size = 2; size <= 32 * E; size <<= 1) {
 #pragma unroll
@@ -122,13 +129,13 @@ __device__ __forceinline__ void warp_bitonic(uint32_t (&k)[E], int lane) {
                 if (stride >= 32) {
                     const int rp = r ^ (stride >> 5);
                     if (rp > r) {
-                        const uint32_t u = k[r], v = k[rp];
+                        const uint64_t u = k[r], v = k[rp];
                         const bool sw = (u > v) == asc;
                         k[r] = sw ? v : u;
                         k[rp] = sw ? u : v;
                     }
                 } else {
-                    const uint32_t v = __shfl_xor_sync(0xffffffffu, k[r], stride);
+                    const uint64_t v = __shfl_xor_sync(0xffffffffu, k[r], stride);
                     const bool lower = (lane & stride) == 0;
                     k[r] = (lower == asc) ? min(k[r], v) : max(k[r], v);
                 }
@@ -137,251 +144,386 @@ __device__ __forceinline__ void warp_bitonic(uint32_t (&k)[E], int lane) {
     }
 }
 
-template <int E>
-__device__ __forceinline__ void sort_and_store(const uint32_t *key, int mm, int lane, uint32_t *out) {
-    uint32_t k[E];
+// Each cell's atoms in ascending key order (species << 30 | caller index), one warp per cell:
+// the scatter fills a cell in the order of its atomic increments, and the list build walks the
+// cells' atoms in their stored order, so sorted cells make every list independent of that order
+// and of the internal atom order.  Cells of up to 64 atoms are sorted in registers; a larger one
+// (only in boxes of very few cells) by lane 0 in place.
+__device__ __forceinline__ void cellsort_body(const BinArgs &r, int64_t blk, int64_t nblk) {
+    if (r.flag && *r.flag == 0) return;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int64_t c = blk * wpb + (threadIdx.x >> 5); c < r.ncell; c += nblk * wpb) {
+        const int p0 = r.start[c], len = r.start[c + 1] - p0;
+        if (len <= 1) continue;
+        if (len <= 64) {
+            uint64_t v[2];
+            int at[2];
+            float4 pf[2];
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-        const int e = r * 32 + lane;
-        k[r] = e < mm ? key[e] : 0xFFFFFFFFu;
+            for (int q = 0; q < 2; ++q) {
+                const int e = q * 32 + lane;
+                v[q] = ~0ull;
+                at[q] = 0;
+                pf[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (e < len) {
+                    v[q] = ((uint64_t)r.ckey[p0 + e] << 32) | (uint32_t)e;
+                    at[q] = r.atoms[p0 + e];
+                    pf[q] = r.cposf[p0 + e];
+                }
+            }
+            warp_bitonic64<2>(v, lane);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int e = q * 32 + lane;
+                const int src = (int)(v[q] & 0xffffffffu), sl = src & 31, sq = src >> 5;
+                const int a0 = __shfl_sync(0xffffffffu, at[0], sl), a1 = __shfl_sync(0xffffffffu, at[1], sl);
+                float4 f0, f1;
+                f0.x = __shfl_sync(0xffffffffu, pf[0].x, sl); f1.x = __shfl_sync(0xffffffffu, pf[1].x, sl);
+                f0.y = __shfl_sync(0xffffffffu, pf[0].y, sl); f1.y = __shfl_sync(0xffffffffu, pf[1].y, sl);
+                f0.z = __shfl_sync(0xffffffffu, pf[0].z, sl); f1.z = __shfl_sync(0xffffffffu, pf[1].z, sl);
+                f0.w = __shfl_sync(0xffffffffu, pf[0].w, sl); f1.w = __shfl_sync(0xffffffffu, pf[1].w, sl);
+                if (e < len) {
+                    r.ckey[p0 + e] = (uint32_t)(v[q] >> 32);
+                    r.atoms[p0 + e] = sq == 0 ? a0 : a1;
+                    r.cposf[p0 + e] = sq == 0 ? f0 : f1;
+                }
+            }
+        } else if (lane == 0) {
+            for (int x = 1; x < len; ++x) {
+                const uint32_t k = r.ckey[p0 + x];
+                const int at = r.atoms[p0 + x];
+                const float4 pf = r.cposf[p0 + x];
+                int y = x - 1;
+                for (; y >= 0 && r.ckey[p0 + y] > k; --y) {
+                    r.ckey[p0 + y + 1] = r.ckey[p0 + y];
+                    r.atoms[p0 + y + 1] = r.atoms[p0 + y];
+                    r.cposf[p0 + y + 1] = r.cposf[p0 + y];
+                }
+                r.ckey[p0 + y + 1] = k;
+                r.atoms[p0 + y + 1] = at;
+                r.cposf[p0 + y + 1] = pf;
+            }
+        }
+        __syncwarp();
     }
-    warp_bitonic<E>(k, lane);
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < E; ++r) out[r * 32 + lane] = k[r];
-    __syncwarp();
 }
+
+// The lists are built cell by cell: a block takes one cell, copies the candidates of its
+// stencil (the 27 surrounding cells, each cell's atoms contiguous and sorted by key) into
+// shared memory once, and its warps build the lists of the cell's atoms from there, one atom
+// per warp: lanes take the candidates 32 at a time, pairs inside the list cutoff are appended
+// to a per-warp buffer in walk order (ballot/popc), and the buffer is written out partitioned
+// by segment, each segment in walk order.  The walk order (stencil cells z-major, each cell by
+// key) depends on the positions and caller indices only.
+//
+// FP32 pre-test.  The scatter stores each atom's position relative to its own cell's corner
+// (FP64 difference, then rounded), so the FP32 separation of a pair is the difference of two
+// numbers below two cell widths plus the stencil cell's corner offset (a whole number of cell
+// widths, which with at least 3 cells along every periodic axis already carries the periodic
+// image; with fewer the minimum image is taken in FP32).  Its error is a few FP32 roundings
+// of a cell width, independent of the box size, and the host sets the band around each cutoff
+// from that bound (rebuild_plan); pairs inside the band, and any pair with an atom more than a
+// cell width outside its cell (stored as NaN, which fails every comparison), take the exact
+// FP64 test.
 
 __device__ __forceinline__ int wrap_cell(int x, int nc) { return x < 0 ? x + nc : (x >= nc ? x - nc : x); }
 
 constexpr int SORT_MAX = 256;
+constexpr int STAGE_MAX = 1024;   // staged candidates; a larger stencil is walked in global memory
 
 struct ListSmem {
+    float4 p[STAGE_MAX];      // FP32 positions of the stencil's candidates relative to the centre cell's corner
+    uint32_t k[STAGE_MAX];    // their keys (species << 30 | caller index)
+    int j[STAGE_MAX];         // their internal indices
     uint32_t key[LB_WARPS][SORT_MAX];
-    int off[LB_WARPS][32], p0[LB_WARPS][32];   // stencil cells of each warp's atom
+    int off[32], p0[32];      // stencil cells: offset in the walk, first cell-ordered position
+    float4 org[32];           // stencil cells: corner relative to the centre cell's corner (its image)
+    int nst, total;
 };
 
-__device__ __forceinline__ void lists_body(const ListArgs &args, int64_t blk, int64_t nblk, ListSmem &sm) {
-    const ListArgs a = args;   // as values: the stores below cannot make the compiler re-read them
-    if (a.flag && *a.flag == 0) return;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t *key = sm.key[w];
+// One atom's list from the candidates f = 0 .. total-1 of its cell's stencil.  pfi: the atom's
+// FP32 position relative to its cell's corner; cand(f, k, p) gives candidate f's key and FP32
+// position relative to the same corner, jof(f) its internal index (the exact test), and
+// ident(f, j, o) its internal and caller indices for the list entry.
+template <typename Cand, typename Jof, typename Ident>
+__device__ __forceinline__ void list_atom(const ListArgs &a, int64_t i, float4 pfi, uint32_t *key, int lane,
+                                          int total, bool image_placed, Cand cand, Jof jof, Ident ident) {
     const unsigned lt = (1u << lane) - 1u;
-    for (int64_t i = blk * LB_WARPS + w; i < a.n; i += nblk * LB_WARPS) {
-        const double4 pi = a.pos[i];
-        const float4 pfi = a.posf[i];
-        const int cc = a.cell_of[i];
-        int ci[3] = {cc % a.g.nc[0], (cc / a.g.nc[0]) % a.g.nc[1], cc / (a.g.nc[0] * a.g.nc[1])};
-        int lo[3], hi[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (a.g.per[d] && a.g.nc[d] < 3) { lo[d] = 0; hi[d] = a.g.nc[d] - 1; }
-            else if (a.g.per[d]) { lo[d] = ci[d] - 1; hi[d] = ci[d] + 1; }
-            else { lo[d] = max(ci[d] - 1, 0); hi[d] = min(ci[d] + 1, a.g.nc[d] - 1); }
-        }
-        const uint32_t self = (uint32_t)a.orig[i];
-        // The stencil cells' candidates are walked as one flattened sequence in the cell order
-        // below (z, y, x), 32 per round, with the next round's keys and positions in flight
-        // while the current round is tested.  Lane c < nst holds cell c's first cell-ordered
-        // position and its exclusive offset in the sequence.
-        const int sx = hi[0] - lo[0] + 1, sy = hi[1] - lo[1] + 1, sz = hi[2] - lo[2] + 1;
-        const int nst = sx * sy * sz;   // at most 27 cells
-        int my_p0 = 0, my_len = 0;
-        if (lane < nst) {
-            const int x = lo[0] + lane % sx, y = lo[1] + (lane / sx) % sy, z = lo[2] + lane / (sx * sy);
-            const int c = (wrap_cell(z, a.g.nc[2]) * a.g.nc[1] + wrap_cell(y, a.g.nc[1])) * a.g.nc[0] +
-                          wrap_cell(x, a.g.nc[0]);
-            my_p0 = a.cell_start[c];
-            my_len = a.cell_start[c + 1] - my_p0;
-        }
-        int incl = my_len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        int *off = sm.off[w], *p0 = sm.p0[w];
-        if (lane < nst) {
-            off[lane] = incl - my_len;
-            p0[lane] = my_p0;
-        }
-        __syncwarp();
-        // cell-ordered position of candidate f of the sequence: the last cell whose offset is
-        // <= f holds it (empty cells share the offset of the cell after them).  f grows by 32
-        // per round, so each lane moves its cell pointer forward instead of searching.
-        int cl = 0;
-        auto position_of = [&](int f) {
-            while (cl + 1 < nst && off[cl + 1] <= f) ++cl;
-            return p0[cl] + (f - off[cl]);
-        };
-        int pn = -1;
-        uint32_t kn = 0;
-        float4 fn = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (lane < total) {
-            pn = position_of(lane);
-            kn = a.ckey[pn];
-            fn = a.cposf[pn];
-        }
-        int m = 0, nang = 0;
-        for (int base = 0; base < total; base += 32) {
-            const int p = pn;
-            const uint32_t k = kn;
-            const float4 pfj = fn;
-            pn = -1;
-            if (base + 32 + lane < total) {   // the next round's candidates in flight
-                pn = position_of(base + 32 + lane);
-                kn = a.ckey[pn];
-                fn = a.cposf[pn];
-            }
-            bool in_r = false, in_a = false;
-            if (p >= 0 && (k & 0x3FFFFFFFu) != self) {
+    const uint32_t self = (uint32_t)a.orig[i];
+    int m = 0;
+    for (int base = 0; base < total; base += 32) {
+        const int f = base + lane;
+        bool in_r = false, in_a = false;
+        uint32_t k = 0;
+        if (f < total) {
+            float4 pfj;
+            cand(f, k, pfj);
+            if ((k & 0x3FFFFFFFu) != self) {
                 float dx = pfj.x - pfi.x, dy = pfj.y - pfi.y, dz = pfj.z - pfi.z;
-                minimg(a.bf, dx, dy, dz);
+                if (!image_placed) minimg(a.bf, dx, dy, dz);
                 const float d2f = dx * dx + dy * dy + dz * dz;
-                if (d2f < a.cut_r2f_hi) {
+                if (!(d2f >= a.cut_r2f_hi)) {   // NaN (an atom far outside its cell) goes on
                     if (d2f < a.cut_r2f_lo && (d2f < a.cut_a2f_lo || d2f >= a.cut_a2f_hi)) {
                         in_r = true;
                         in_a = d2f < a.cut_a2f_lo;
                     } else {   // near a cutoff: the exact FP64 test decides
-                        const double4 pj = a.pos[a.cell_atoms[p]];
+                        const double4 pi = a.pos[i], pj = a.pos[jof(f)];
                         const double d2 = exact_d2(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z, a.bd, a.g.per);
                         in_r = d2 < a.cut_r2;
                         in_a = d2 < a.cut_a2;
                     }
                 }
             }
-            const unsigned mr = __ballot_sync(0xffffffffu, in_r);
-            const unsigned ma = __ballot_sync(0xffffffffu, in_a);
-            if (in_r) {
-                const int pos = m + __popc(mr & lt);
-                // segment (angular? 0 : 2) + species of j in bits 30-31 above the caller index;
-                // species is 0 or 1, so (seg << 30) fits with the caller index below 2^30
-                const uint32_t sg = (in_a ? 0u : 2u) + (k >> 30);
-                if (pos < SORT_MAX) key[pos] = (sg << 30) | (k & 0x3FFFFFFFu);
-            }
-            m += __popc(mr);
-            nang += __popc(ma);
         }
-        const bool overflow = m > a.cap || nang > a.cap_ang;
-        const int mm = min(m, SORT_MAX);
-        __syncwarp();
-        if (mm <= 64) sort_and_store<2>(key, mm, lane, key);
-        else if (mm <= 128) sort_and_store<4>(key, mm, lane, key);
-        else sort_and_store<8>(key, mm, lane, key);
-        const int cnt = min(mm, a.cap);
-        int ends[4] = {0, 0, 0, 0};
-        for (int s0 = 0; s0 < cnt; s0 += 32) {
-            const int s = s0 + lane;
-            unsigned sg = 4u;
-            if (s < cnt) {
-                const uint32_t k = key[s];
-                sg = k >> 30;
-                a.nbr[i * a.capr + s] = a.inv[k & 0x3FFFFFFFu];
-                a.nbr_orig[i * a.capr + s] = (int32_t)(k & 0x3FFFFFFFu);   // atom-major: one row per atom
-            }
+        const unsigned mr = __ballot_sync(0xffffffffu, in_r);
+        if (in_r) {
+            const int pos = m + __popc(mr & lt);
+            // segment (angular? 0 : 2) + species of j in bits 30-31 above the walk index
+            const uint32_t sg = (in_a ? 0u : 2u) + (k >> 30);
+            if (pos < SORT_MAX) key[pos] = (sg << 30) | (uint32_t)f;
+        }
+        m += __popc(mr);
+    }
+    const int mm = min(m, SORT_MAX);
+    __syncwarp();
+    // entries per segment, then each segment's entries in walk order from its offset (a stable
+    // partition); an overflowing list keeps its first `cap` entries and raises the status
+    int cnt4[4] = {0, 0, 0, 0};
+    for (int s0 = 0; s0 < mm; s0 += 32) {
+        const int e = s0 + lane;
+        const unsigned sg = e < mm ? key[e] >> 30 : 4u;
 #pragma unroll
-            for (int t = 0; t < 4; ++t) ends[t] += __popc(__ballot_sync(0xffffffffu, sg <= (unsigned)t));
+        for (int t = 0; t < 4; ++t) cnt4[t] += __popc(__ballot_sync(0xffffffffu, sg == (unsigned)t));
+    }
+    const bool overflow = m > a.cap || cnt4[0] + cnt4[1] > a.cap_ang;
+    int run[4] = {0, cnt4[0], cnt4[0] + cnt4[1], cnt4[0] + cnt4[1] + cnt4[2]};
+    const int ends_all[4] = {run[1], run[2], run[3], run[3] + cnt4[3]};
+    for (int s0 = 0; s0 < mm; s0 += 32) {
+        const int e = s0 + lane;
+        const uint32_t k = e < mm ? key[e] : 0u;
+        const unsigned sg = e < mm ? k >> 30 : 4u;
+        int pos = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const unsigned b = __ballot_sync(0xffffffffu, sg == (unsigned)t);
+            if (sg == (unsigned)t) pos = run[t] + __popc(b & lt);
+            run[t] += __popc(b);
         }
-        if (lane == 0) {
-            a.seg[i] = make_int4(ends[0], ends[1], ends[2], ends[3]);
-            if (overflow) atomicOr(a.status, ST_NBR_OVERFLOW);
+        if (e < mm && pos < a.cap) {
+            int jx, oj;
+            ident((int)(k & 0x3FFFFFFFu), jx, oj);
+            a.nbr[i * a.capr + pos] = jx;
+            a.nbr_orig[i * a.capr + pos] = oj;   // atom-major: one row per atom
         }
-        __syncwarp();
+    }
+    if (lane == 0) {
+        a.seg[i] = make_int4(min(ends_all[0], a.cap), min(ends_all[1], a.cap), min(ends_all[2], a.cap),
+                             min(ends_all[3], a.cap));
+        if (overflow) atomicOr(a.status, ST_NBR_OVERFLOW);
+    }
+    __syncwarp();
+}
+
+// Cells blk, blk + nblk, ... of the grid (a block-uniform loop).
+__device__ __forceinline__ void lists_body(const ListArgs &args, int64_t blk, int64_t nblk, ListSmem &sm) {
+    const ListArgs a = args;   // as values: the stores below cannot make the compiler re-read them
+    if (a.flag && *a.flag == 0) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int ncell = a.g.nc[0] * a.g.nc[1] * a.g.nc[2];
+    // with at least 3 cells along every periodic axis each stencil cell is one image, placed by
+    // its corner offset; otherwise the walk takes the minimum image
+    bool image_placed = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) image_placed = image_placed && (!a.g.per[d] || a.g.nc[d] >= 3);
+    for (int64_t c = blk; c < ncell; c += nblk) {
+        // the stencil: cells lo..hi per axis (wrapped where periodic), z-major, and each one's
+        // offset in the walk (warp 0)
+        if (w == 0) {
+            const int ci[3] = {(int)(c % a.g.nc[0]), (int)((c / a.g.nc[0]) % a.g.nc[1]),
+                               (int)(c / ((int64_t)a.g.nc[0] * a.g.nc[1]))};
+            int lo[3], hi[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (a.g.per[d] && a.g.nc[d] < 3) { lo[d] = 0; hi[d] = a.g.nc[d] - 1; }
+                else if (a.g.per[d]) { lo[d] = ci[d] - 1; hi[d] = ci[d] + 1; }
+                else { lo[d] = max(ci[d] - 1, 0); hi[d] = min(ci[d] + 1, a.g.nc[d] - 1); }
+            }
+            const int sx = hi[0] - lo[0] + 1, sy = hi[1] - lo[1] + 1, sz = hi[2] - lo[2] + 1;
+            const int nst = sx * sy * sz;   // at most 27 cells
+            int my_p0 = 0, my_len = 0;
+            if (lane < nst) {
+                const int x = lo[0] + lane % sx, y = lo[1] + (lane / sx) % sy, z = lo[2] + lane / (sx * sy);
+                const int wx = wrap_cell(x, a.g.nc[0]), wy = wrap_cell(y, a.g.nc[1]), wz = wrap_cell(z, a.g.nc[2]);
+                const int cc = (wz * a.g.nc[1] + wy) * a.g.nc[0] + wx;
+                my_p0 = a.cell_start[cc];
+                my_len = a.cell_start[cc + 1] - my_p0;
+                // x, y, z are unwrapped: a cell across a periodic face sits one box length away
+                sm.org[lane] = make_float4((float)(x - ci[0]) * a.wf[0], (float)(y - ci[1]) * a.wf[1],
+                                           (float)(z - ci[2]) * a.wf[2], 0.f);
+            }
+            int incl = my_len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane < nst) {
+                sm.off[lane] = incl - my_len;
+                sm.p0[lane] = my_p0;
+            }
+            if (lane == 31) {
+                sm.total = incl;
+                sm.nst = nst;
+            }
+        }
+        __syncthreads();
+        const int total = sm.total, nst = sm.nst;
+        // stencil cell of candidate f of the walk: the last one whose offset is <= f (empty
+        // cells share the offset of the cell after them)
+        auto cell_of = [&](int f) {
+            int cl = 0;
+            while (cl + 1 < nst && sm.off[cl + 1] <= f) ++cl;
+            return cl;
+        };
+        auto placed = [&](int cl, float4 pf) {
+            const float4 o = sm.org[cl];
+            pf.x += o.x; pf.y += o.y; pf.z += o.z;
+            return pf;
+        };
+        const bool staged = total <= STAGE_MAX;
+        if (staged) {
+            for (int f = threadIdx.x; f < total; f += blockDim.x) {
+                const int cl = cell_of(f);
+                const int p = sm.p0[cl] + (f - sm.off[cl]);
+                sm.p[f] = placed(cl, a.cposf[p]);
+                sm.k[f] = a.ckey[p];
+                sm.j[f] = a.cell_atoms[p];
+            }
+        }
+        __syncthreads();
+        // the cell's own atoms, one per warp
+        const int c0 = a.cell_start[c], nc0 = a.cell_start[c + 1] - c0;
+        for (int q = w; q < nc0; q += LB_WARPS) {
+            const int64_t i = a.cell_atoms[c0 + q];
+            const float4 pfi = a.cposf[c0 + q];
+            if (staged) {
+                list_atom(
+                    a, i, pfi, sm.key[w], lane, total, image_placed,
+                    [&](int f, uint32_t &k, float4 &pf) {
+                        k = sm.k[f];
+                        pf = sm.p[f];
+                    },
+                    [&](int f) { return sm.j[f]; },
+                    [&](int f, int &jx, int &oj) {
+                        jx = sm.j[f];
+                        oj = (int)(sm.k[f] & 0x3FFFFFFFu);
+                    });
+            } else {
+                auto position_of = [&](int f) {
+                    const int cl = cell_of(f);
+                    return sm.p0[cl] + (f - sm.off[cl]);
+                };
+                list_atom(
+                    a, i, pfi, sm.key[w], lane, total, image_placed,
+                    [&](int f, uint32_t &k, float4 &pf) {
+                        const int cl = cell_of(f);
+                        const int p = sm.p0[cl] + (f - sm.off[cl]);
+                        k = a.ckey[p];
+                        pf = placed(cl, a.cposf[p]);
+                    },
+                    [&](int f) { return a.cell_atoms[position_of(f)]; },
+                    [&](int f, int &jx, int &oj) {
+                        const int p = position_of(f);
+                        jx = a.cell_atoms[p];
+                        oj = (int)(a.ckey[p] & 0x3FFFFFFFu);
+                    });
+            }
+        }
+        __syncthreads();   // the next cell reuses the staging
     }
 }
 
-// Slot of caller index oi inside [lo, hi) of the atom-major list row `row` (16-byte aligned),
-// or -1.  The segment is read with independent 16-byte loads, 32 entries per round (a binary
-// search needs one memory round trip per halving); the entries of a sorted segment are
-// distinct, so at most one matches.  `first` holds the first round's 32 entries from
-// lo & ~3, already loaded by the caller.
-__device__ __forceinline__ int match_round(const int4 (&v)[8], int b, int lo, int hi, int oi) {
-    int found = -1;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int k = b + 4 * u + c;
-            if (e[c] == oi && k >= lo && k < hi) found = k;
-        }
-    }
-    return found;
-}
+// 32 entries of a list row from b on (16-byte aligned), as eight independent 16-byte loads;
+// the 4-entry groups that start at or past hi read as -1 (no caller index).
 __device__ __forceinline__ void load_round(const int32_t *__restrict__ row, int b, int hi, int4 (&v)[8]) {
 #pragma unroll
     for (int u = 0; u < 8; ++u)
         v[u] = b + 4 * u < hi ? *reinterpret_cast<const int4 *>(row + b + 4 * u) : make_int4(-1, -1, -1, -1);
 }
-__device__ __forceinline__ int find_rest(const int32_t *__restrict__ row, int b, int lo, int hi, int oi) {
+
+// Slot of caller index oi in [lo, hi) of a list row, or -1.  A caller index appears at most
+// once in a row's entries [0, seg.w), so the first match in a round that starts at lo & ~3 is
+// the only one below hi; a match at or past hi is a stale entry past the row's end or in no
+// segment of this kind, and counts as none.
+__device__ __forceinline__ int find_slot(const int32_t *__restrict__ row, int lo, int hi, int oi) {
     int found = -1;
-    for (; b < hi && found < 0; b += 32) {
+    for (int b = lo & ~3; b < hi && found < 0; b += 32) {
         int4 v[8];
         load_round(row, b, hi, v);
-        found = match_round(v, b, lo, hi, oi);
+#pragma unroll
+        for (int u = 7; u >= 0; --u) {   // descending: the lowest match is kept
+            found = v[u].w == oi ? b + 4 * u + 3 : found;
+            found = v[u].z == oi ? b + 4 * u + 2 : found;
+            found = v[u].y == oi ? b + 4 * u + 1 : found;
+            found = v[u].x == oi ? b + 4 * u : found;
+        }
+        if (found >= hi) found = -1;
     }
     return found;
 }
 
-// Warp per atom, lanes over slots: for every list entry j = nbr[i][s] with j > i, the slot t
-// of i in the list of j is found and both reverse slots are written, rev[i][s] = t and
-// rev[j][t] = s (the entries with j < i are written by j's warp): one search per unordered
-// pair.  The lists are symmetric and so is each pair's segment kind (the cutoff test gives the
-// same result for (i, j) and (j, i)), so i sits in the segment of j's list for (kind of slot
-// s, t_i).  Each lane takes four slots 32 apart: their list entries, then their neighbours'
-// segment bounds, then two first search rounds at a time are in flight together.  A pair
-// found in one list only (a list cut at its capacity) raises the overflow status.
-__device__ __forceinline__ void rev_body(const RevArgs &args, int64_t blk, int64_t nblk) {
+constexpr int REV_WARPS = 4;
+struct RevSmem {
+    int s[REV_WARPS][256];   // each warp's pairs: slot in the atom's list (the capacity is at most 256)
+    int j[REV_WARPS][256];   //   and the neighbour's internal index
+};
+
+// Warp per atom i.  The entries j = nbr[i][s] with j > i are compacted (ballot) into the warp's
+// pair list; each lane then takes one pair, reads j's segment bounds for the kind of slot s,
+// finds the slot t of i in that segment of j's caller-index row and writes both reverse slots,
+// rev[i][s] = t and rev[j][t] = s (the entries with j < i are written by j's warp): one search
+// per unordered pair.  The lists are symmetric and so is each pair's segment kind (the cutoff
+// test gives the same result for (i, j) and (j, i)), so i sits in the segment of j's list for
+// (kind of slot s, species of i).  A pair found in one list only (a list cut at its capacity)
+// raises the overflow status.
+__device__ __forceinline__ void rev_body(const RevArgs &args, int64_t blk, int64_t nblk, RevSmem &sm) {
     const RevArgs a = args;   // as values: the stores below cannot make the compiler re-read them
     if (a.flag && *a.flag == 0) return;
-    const int lane = threadIdx.x & 31;
-    for (int64_t i = blk * 4 + (threadIdx.x >> 5); i < a.n; i += nblk * 4) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t i = blk * REV_WARPS + w; i < a.n; i += nblk * REV_WARPS) {
         const int4 sg = a.seg[i];
         const int oi = a.orig[i];
         const int ti = a.species[i];
-        for (int s0 = 0; s0 < sg.w; s0 += 128) {
-            int j[4];
-            int4 sj[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int s = s0 + lane + 32 * u;
-                const int jj = s < sg.w ? a.nbr[i * a.capr + s] : -1;
-                j[u] = jj > i ? jj : -1;   // the lower-indexed atom of the pair searches
+        int cnt = 0;
+        for (int s0 = 0; s0 < sg.w; s0 += 32) {
+            const int s = s0 + lane;
+            const int jj = s < sg.w ? a.nbr[i * a.capr + s] : -1;
+            const bool act = jj > i;   // the lower-indexed atom of the pair searches
+            const unsigned bal = __ballot_sync(0xffffffffu, act);
+            if (act) {
+                sm.s[w][cnt + __popc(bal & lt)] = s;
+                sm.j[w][cnt + __popc(bal & lt)] = jj;
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) sj[u] = j[u] >= 0 ? a.seg[j[u]] : make_int4(0, 0, 0, 0);
-#pragma unroll
-            for (int u = 0; u < 4; u += 2) {
-                int lo[2], hi[2], b[2];
-                int4 v[2][8];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int s = s0 + lane + 32 * (u + h);
-                    const int sgi = (s < sg.y ? 0 : 2) + ti;
-                    const int e[4] = {sj[u + h].x, sj[u + h].y, sj[u + h].z, sj[u + h].w};
-                    lo[h] = sgi == 0 ? 0 : e[sgi - 1];
-                    hi[h] = j[u + h] >= 0 ? e[sgi] : 0;
-                    b[h] = lo[h] & ~3;
-                    load_round(a.nbr_orig + (int64_t)max(j[u + h], 0) * a.capr, b[h], hi[h], v[h]);
-                }
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (j[u + h] < 0) continue;
-                    const int s = s0 + lane + 32 * (u + h);
-                    int found = match_round(v[h], b[h], lo[h], hi[h], oi);
-                    if (found < 0 && b[h] + 32 < hi[h])
-                        found = find_rest(a.nbr_orig + (int64_t)j[u + h] * a.capr, b[h] + 32, lo[h], hi[h], oi);
-                    if (found < 0) {
-                        atomicOr(a.status, ST_NBR_OVERFLOW);
-                        a.rev[i * a.capr + s] = 0;
-                        continue;
-                    }
-                    a.rev[i * a.capr + s] = (uint8_t)found;
-                    a.rev[(int64_t)j[u + h] * a.capr + found] = (uint8_t)s;
-                }
-            }
+            cnt += __popc(bal);
         }
+        __syncwarp();
+        for (int p = lane; p < cnt; p += 32) {
+            const int s = sm.s[w][p], j = sm.j[w][p];
+            const int4 sj = a.seg[j];
+            const int sgi = (s < sg.y ? 0 : 2) + ti;
+            const int lo = sgi == 0 ? 0 : sgi == 1 ? sj.x : sgi == 2 ? sj.y : sj.z;
+            const int hi = sgi == 0 ? sj.x : sgi == 1 ? sj.y : sgi == 2 ? sj.z : sj.w;
+            const int t = find_slot(a.nbr_orig + (int64_t)j * a.capr, lo, hi, oi);
+            if (t < 0) {
+                atomicOr(a.status, ST_NBR_OVERFLOW);
+                a.rev[i * a.capr + s] = 0;
+                continue;
+            }
+            a.rev[i * a.capr + s] = (uint8_t)t;
+            a.rev[(int64_t)j * a.capr + t] = (uint8_t)s;
+        }
+        __syncwarp();   // the next atom reuses the pair list
     }
 }
 
@@ -413,10 +555,8 @@ __device__ __forceinline__ void rebuild_items(const A *__restrict__ tab, const W
     else map_item(tab, m, body);
 }
 
-// register budget of a system's own list build: the latency-bound walk wants occupancy
-#ifndef LISTS_MINB
-#define LISTS_MINB 8
-#endif
+// register budget of a system's own list build (its 29 KB of staging allow 7 blocks per SM)
+constexpr int LISTS_MINB = 6;
 
 template <bool LOOP>
 __global__ void k_bin(const BinArgs *__restrict__ tab, WorkMap m, const int *quick) {
@@ -436,6 +576,11 @@ __global__ void k_scatter(const BinArgs *__restrict__ tab, WorkMap m, const int 
     rebuild_items<LOOP>(tab, m, [](const BinArgs &r, int64_t blk, int64_t nblk) { scatter_body(r, blk, nblk); });
 }
 template <bool LOOP>
+__global__ void k_cellsort(const BinArgs *__restrict__ tab, WorkMap m, const int *quick) {
+    if (quick && *quick == 0) return;
+    rebuild_items<LOOP>(tab, m, [](const BinArgs &r, int64_t blk, int64_t nblk) { cellsort_body(r, blk, nblk); });
+}
+template <bool LOOP>
 __global__ void __launch_bounds__(LB_WARPS * 32, LOOP ? 4 : LISTS_MINB) k_lists(const ListArgs *__restrict__ tab,
                                                                               WorkMap m, const int *quick) {
     if (quick && *quick == 0) return;
@@ -443,9 +588,11 @@ __global__ void __launch_bounds__(LB_WARPS * 32, LOOP ? 4 : LISTS_MINB) k_lists(
     rebuild_items<LOOP>(tab, m, [&](const ListArgs &a, int64_t blk, int64_t nblk) { lists_body(a, blk, nblk, sm); });
 }
 template <bool LOOP>
-__global__ void __launch_bounds__(128) k_rev(const RevArgs *__restrict__ tab, WorkMap m, const int *quick) {
+__global__ void __launch_bounds__(REV_WARPS * 32, LOOP ? 6 : 8) k_rev(const RevArgs *__restrict__ tab, WorkMap m,
+                                                                     const int *quick) {
     if (quick && *quick == 0) return;
-    rebuild_items<LOOP>(tab, m, [](const RevArgs &a, int64_t blk, int64_t nblk) { rev_body(a, blk, nblk); });
+    __shared__ RevSmem sm;
+    rebuild_items<LOOP>(tab, m, [&](const RevArgs &a, int64_t blk, int64_t nblk) { rev_body(a, blk, nblk, sm); });
 }
 template <bool LOOP>
 __global__ void k_finish(const BinArgs *__restrict__ tab, WorkMap m, const int *quick) {
@@ -489,15 +636,36 @@ RebuildPlan rebuild_plan(Sys &s, bool conditional) {
     r.atoms = s.cells.atoms; r.of = s.cells.of; r.cposf = s.cells.posf; r.ckey = s.cells.key;
     r.posref = s.posref; r.builds = s.d_builds; r.rebuild = s.rebuild; r.flag = flag;
     ListArgs &la = pl.lists;
-    la.pos = s.pos; la.posf = s.posf; la.species = s.species; la.orig = s.orig; la.inv = s.inv;
+    la.pos = s.pos; la.species = s.species; la.orig = s.orig;
     la.cell_start = s.cells.start; la.cell_atoms = s.cells.atoms; la.cell_of = s.cells.of;
     la.cposf = s.cells.posf; la.ckey = s.cells.key; la.nbr_orig = s.nbr_orig;
     la.n = n; la.cap = s.cap; la.cap_ang = s.cap_ang; la.capr = nbr_orig_stride(s.cap);
     la.cut_r2 = s.cut_r2; la.cut_a2 = s.cut_a2;
-    // FP32 separations of positions below 1e4 A carry an absolute d2 error far
-    // below 0.05 A^2 at these distances; pairs inside that band take the FP64 test.
-    la.cut_r2f_lo = (float)(s.cut_r2 - 0.05); la.cut_r2f_hi = (float)(s.cut_r2 + 0.05);
-    la.cut_a2f_lo = (float)(s.cut_a2 - 0.05); la.cut_a2f_hi = (float)(s.cut_a2 + 0.05);
+    // Band of the FP32 pre-test.  Each FP32 separation component is (u_j + o) - u_i with
+    // |u| <= 2w (positions relative to their cells' corners, rounded once from FP64) and o a
+    // corner offset of at most one cell width (one rounding of w); every rounding is at most
+    // 2^-24 of a value below 5w, and the FP32 minimum image (fewer than 3 cells along a
+    // periodic axis) adds roundings below 2^-24 of 2L.  So each component is off by at most
+    // E = 2^-24 (16 w + 4 L'), with w the largest cell width and L' the largest periodic box
+    // length where the minimum image is taken (else 0), and d2 (at most R^2, R the list
+    // cutoff plus a margin) by at most 2 sqrt(3) R E + 3 E^2 + 4 2^-24 R^2.  The band is twice
+    // that; pairs inside it take the FP64 test.
+    {
+        const double u32 = std::ldexp(1.0, -24);
+        double wmax = 0.0, lmin = 0.0;
+        bool placed = true;
+        for (int a = 0; a < 3; ++a) placed = placed && (!s.per[a] || s.cells.nc[a] >= 3);
+        for (int a = 0; a < 3; ++a) {
+            wmax = std::max(wmax, g.w[a]);
+            if (!placed && s.per[a]) lmin = std::max(lmin, s.box[a]);
+        }
+        const double E = u32 * (16.0 * wmax + 4.0 * lmin);
+        const double R = std::sqrt(std::max(s.cut_r2, s.cut_a2)) + 1.0;
+        const double band = 2.0 * (2.0 * std::sqrt(3.0) * R * E + 3.0 * E * E + 4.0 * u32 * R * R);
+        la.cut_r2f_lo = (float)(s.cut_r2 - band); la.cut_r2f_hi = (float)(s.cut_r2 + band);
+        la.cut_a2f_lo = (float)(s.cut_a2 - band); la.cut_a2f_hi = (float)(s.cut_a2 + band);
+        for (int a = 0; a < 3; ++a) la.wf[a] = (float)g.w[a];
+    }
     la.bd = s.boxd; la.bf = s.boxf; la.g = g;
     la.nbr = s.nbr; la.seg = s.seg; la.status = s.status; la.flag = flag;
     RevArgs &ra = pl.rev;
@@ -516,8 +684,9 @@ RebuildPlan rebuild_plan(Sys &s, bool conditional) {
     pl.blocks[RB_BIN] = capped(n, RB_THREADS);
     pl.blocks[RB_SCAN] = 1;
     pl.blocks[RB_SCATTER] = capped(n, RB_THREADS);
-    pl.blocks[RB_LISTS] = capped(n, LB_WARPS);
-    pl.blocks[RB_REV] = capped(n, 4);
+    pl.blocks[RB_CELLSORT] = capped(s.cells.ncell, RB_THREADS / 32);   // a warp per cell
+    pl.blocks[RB_LISTS] = capped(s.cells.ncell, 1);   // one cell per block and item
+    pl.blocks[RB_REV] = capped(n, REV_WARPS);
     pl.blocks[RB_FINISH] = capped(m, RB_THREADS);
     return pl;
 }
@@ -553,8 +722,9 @@ void fused_grids_rebuild(FusedTables &t) {
     t.grid[FK_BIN] = full((const void *)k_bin<true>, RB_THREADS);
     t.grid[FK_SCAN] = std::min<unsigned>((unsigned)t.cap, full((const void *)k_scan<true>, 1024));
     t.grid[FK_SCATTER] = full((const void *)k_scatter<true>, RB_THREADS);
+    t.grid[FK_CELLSORT] = full((const void *)k_cellsort<true>, RB_THREADS);
     t.grid[FK_LISTS] = full((const void *)k_lists<true>, LB_WARPS * 32);
-    t.grid[FK_REV] = full((const void *)k_rev<true>, 128);
+    t.grid[FK_REV] = full((const void *)k_rev<true>, REV_WARPS * 32);
     t.grid[FK_FINISH] = full((const void *)k_finish<true>, RB_THREADS);
 }
 
@@ -564,9 +734,10 @@ static void rebuild_t(const FusedTables &t, const Launch *L, bool clear, cudaStr
     k_bin<LOOP><<<L[RB_BIN].grid, RB_THREADS, 0, st>>>(bin, L[RB_BIN].m, L[RB_BIN].quick);
     k_scan<LOOP><<<L[RB_SCAN].grid, 1024, 0, st>>>(bin, L[RB_SCAN].m, L[RB_SCAN].quick);
     k_scatter<LOOP><<<L[RB_SCATTER].grid, RB_THREADS, 0, st>>>(bin, L[RB_SCATTER].m, L[RB_SCATTER].quick);
+    k_cellsort<LOOP><<<L[RB_CELLSORT].grid, RB_THREADS, 0, st>>>(bin, L[RB_CELLSORT].m, L[RB_CELLSORT].quick);
     k_lists<LOOP><<<L[RB_LISTS].grid, LB_WARPS * 32, 0, st>>>(t.at<ListArgs>(t.o_lists), L[RB_LISTS].m,
                                                               L[RB_LISTS].quick);
-    k_rev<LOOP><<<L[RB_REV].grid, 128, 0, st>>>(t.at<RevArgs>(t.o_rev), L[RB_REV].m, L[RB_REV].quick);
+    k_rev<LOOP><<<L[RB_REV].grid, REV_WARPS * 32, 0, st>>>(t.at<RevArgs>(t.o_rev), L[RB_REV].m, L[RB_REV].quick);
     k_finish<LOOP><<<L[RB_FINISH].grid, RB_THREADS, 0, st>>>(bin, L[RB_FINISH].m, L[RB_FINISH].quick);
     if (clear) k_clear_flags<<<1, 128, 0, st>>>(bin, L[RB_BIN].m);
 }

@@ -35,16 +35,16 @@ struct BinArgs {
 
 struct ListArgs {
     const double4 *pos;
-    const float4 *posf;
-    const int32_t *species, *orig, *inv;
+    const int32_t *species, *orig;
     const int *cell_start, *cell_atoms, *cell_of;
-    const float4 *cposf;      // cell-ordered FP32 positions
+    const float4 *cposf;      // cell-ordered FP32 positions relative to each cell's corner
     const uint32_t *ckey;     // cell-ordered (species << 30 | caller index)
     int32_t *nbr_orig;        // [n][capr] caller index of each list entry (atom-major rows of capr)
     int64_t n;
     int cap, cap_ang, capr;
     double cut_r2, cut_a2;
     float cut_r2f_lo, cut_r2f_hi, cut_a2f_lo, cut_a2f_hi;   // FP32 pre-test band
+    float wf[3];              // cell widths in FP32 (the stencil cells' corner offsets)
     BoxDev<double> bd;
     BoxDev<float> bf;
     GridArgs g;
@@ -66,7 +66,8 @@ struct RevArgs {
 };
 
 // kernels of the group, in launch order (the flag is cleared after the last)
-constexpr int RB_BIN = 0, RB_SCAN = 1, RB_SCATTER = 2, RB_LISTS = 3, RB_REV = 4, RB_FINISH = 5, RB_KERNELS = 6;
+constexpr int RB_BIN = 0, RB_SCAN = 1, RB_SCATTER = 2, RB_CELLSORT = 3, RB_LISTS = 4, RB_REV = 5, RB_FINISH = 6,
+              RB_KERNELS = 7;
 
 struct RebuildPlan {
     BinArgs bin;

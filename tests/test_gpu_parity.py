@@ -78,6 +78,34 @@ def test_neighbor_lists_bit_exact(params, name):
     s.destroy()
 
 
+def test_neighbor_lists_bit_exact_with_atoms_far_outside_a_free_axis(params):
+    """The highest and the lowest atom of the slab, each with the atoms within 4 A of it,
+    moved 25 A further out along the free axis: they sit more than a cell width beyond the edge
+    cells that hold them, so every pair of theirs is decided by the exact FP64 test (their FP32
+    cell-relative positions are not kept); the pairs inside each group keep their distances."""
+    wl = small_slab()
+
+    def group(k):
+        d = wl.positions - wl.positions[k]
+        d -= wl.box * wl.periodic * np.rint(d / wl.box)
+        return np.flatnonzero(np.linalg.norm(d, axis=1) < 4.0)
+
+    up, down = group(int(np.argmax(wl.positions[:, 2]))), group(int(np.argmin(wl.positions[:, 2])))
+    assert len(up) > 1 and len(down) > 1 and not set(up) & set(down)
+    wl.positions[up, 2] += 25.0
+    wl.positions[down, 2] -= 25.0
+    s = S.system_from_workload(wl, params)
+    pos, _ = gpu_state(s)
+    assert pos[:, 2].max() > wl.box[2] + 15.0 and pos[:, 2].min() < -15.0
+    rad, ang = s.get_neighbors()
+    ref_r = O.neighbors(pos, wl.box, wl.periodic, 7.0, method=0)
+    ref_a = O.neighbors(pos, wl.box, wl.periodic, 5.0, method=0)
+    assert all(np.array_equal(a, b) for a, b in zip(rad, ref_r))
+    assert all(np.array_equal(a, b) for a, b in zip(ang, ref_a))
+    assert all(len(rad[i]) > 0 for i in np.concatenate([up, down]))
+    s.destroy()
+
+
 @pytest.mark.parametrize("name", list(WORKLOADS))
 def test_descriptors_fp64(params, model, name):
     wl = WORKLOADS[name]()

@@ -215,7 +215,7 @@ void solo_free(Sys &s);
 // launchers (sl_neighbors.cu)
 // row stride of the atom-major caller-index copy of the lists: cap rounded up to a multiple
 // of 4 entries, so every row starts on a 16-byte boundary
-inline int nbr_orig_stride(int cap) { return (cap + 3) & ~3; }
+inline int nbr_orig_stride(int cap) { return (cap + 7) & ~7; }   // rows of 32-byte multiples
 void nbr_setup(Sys &s);
 void launch_rebuild(Sys &s, bool conditional);
 // sl_eval2.cu: the system's evaluation at the state (with the virial parts when asked for), or

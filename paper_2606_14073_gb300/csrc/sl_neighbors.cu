@@ -93,8 +93,8 @@ __device__ __forceinline__ void scan_body(const BinArgs &r, int *s_part, int &s_
 
 // Atoms into their cells, with a cell-ordered copy of the key (species << 30 | caller index)
 // and of the position relative to the cell's corner in FP32 (NaN for an atom more than a
-// cell width outside its cell, which only a non-periodic axis can hold), so the list build
-// reads candidates contiguously.
+// cell width outside its cell, which only a non-periodic axis can hold; the species bits in
+// w), so the list build reads candidates contiguously.
 __device__ __forceinline__ void scatter_body(const BinArgs &r, int64_t blk, int64_t nblk) {
     if (r.flag && *r.flag == 0) return;
     const GridArgs &g = r.g;
@@ -108,8 +108,9 @@ __device__ __forceinline__ void scatter_body(const BinArgs &r, int64_t blk, int6
 #pragma unroll
         for (int d = 0; d < 3; ++d) near = near && u[d] >= -g.w[d] && u[d] <= 2.0 * g.w[d];
         r.atoms[p] = (int)i;
-        r.cposf[p] = near ? make_float4((float)u[0], (float)u[1], (float)u[2], 0.f)
-                          : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+        const float sp = __int_as_float(r.species[i]);   // the species bits ride in w
+        r.cposf[p] = near ? make_float4((float)u[0], (float)u[1], (float)u[2], sp)
+                          : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, sp);
         r.ckey[p] = ((uint32_t)r.species[i] << 30) | (uint32_t)r.orig[i];
     }
 }
@@ -232,57 +233,64 @@ constexpr int SORT_MAX = 256;
 constexpr int STAGE_MAX = 1024;   // staged candidates; a larger stencil is walked in global memory
 
 struct ListSmem {
-    float4 p[STAGE_MAX];      // FP32 positions of the stencil's candidates relative to the centre cell's corner
+    // FP32 positions of the stencil's candidates relative to the centre cell's corner, the
+    // species bits in w; padded to a whole number of warps with candidates far away
+    float4 p[STAGE_MAX];
     uint32_t k[STAGE_MAX];    // their keys (species << 30 | caller index)
     int j[STAGE_MAX];         // their internal indices
     uint32_t key[LB_WARPS][SORT_MAX];
     int off[32], p0[32];      // stencil cells: offset in the walk, first cell-ordered position
     float4 org[32];           // stencil cells: corner relative to the centre cell's corner (its image)
-    int nst, total;
+    int nst, total, self0;    // self0: walk offset of the centre cell
 };
 
-// One atom's list from the candidates f = 0 .. total-1 of its cell's stencil.  pfi: the atom's
-// FP32 position relative to its cell's corner; cand(f, k, p) gives candidate f's key and FP32
-// position relative to the same corner, jof(f) its internal index (the exact test), and
-// ident(f, j, o) its internal and caller indices for the list entry.
+// One atom's list from the candidates f = 0 .. total-1 of its cell's stencil (fself: the
+// atom's own walk index).  pfi: the atom's FP32 position relative to its cell's corner;
+// cand(f) gives candidate f's FP32 position relative to the same corner with its species bits
+// in w (candidates at f >= total far away), jof(f) its internal index (the exact test), and
+// ident(f, j, o) its internal and caller indices for the list entry.  The FP32 decision is
+// branch-free; a warp takes the exact test's branch only when one of its lanes is in a band.
 template <typename Cand, typename Jof, typename Ident>
-__device__ __forceinline__ void list_atom(const ListArgs &a, int64_t i, float4 pfi, uint32_t *key, int lane,
-                                          int total, bool image_placed, Cand cand, Jof jof, Ident ident) {
+__device__ __forceinline__ void list_atom(const ListArgs &a, int64_t i, float4 pfi, int fself, uint32_t *key,
+                                          int lane, int total, bool image_placed, Cand cand, Jof jof,
+                                          Ident ident) {
     const unsigned lt = (1u << lane) - 1u;
-    const uint32_t self = (uint32_t)a.orig[i];
     int m = 0;
-    for (int base = 0; base < total; base += 32) {
-        const int f = base + lane;
-        bool in_r = false, in_a = false;
-        uint32_t k = 0;
-        if (f < total) {
-            float4 pfj;
-            cand(f, k, pfj);
-            if ((k & 0x3FFFFFFFu) != self) {
-                float dx = pfj.x - pfi.x, dy = pfj.y - pfi.y, dz = pfj.z - pfi.z;
-                if (!image_placed) minimg(a.bf, dx, dy, dz);
-                const float d2f = dx * dx + dy * dy + dz * dz;
-                if (!(d2f >= a.cut_r2f_hi)) {   // NaN (an atom far outside its cell) goes on
-                    if (d2f < a.cut_r2f_lo && (d2f < a.cut_a2f_lo || d2f >= a.cut_a2f_hi)) {
-                        in_r = true;
-                        in_a = d2f < a.cut_a2f_lo;
-                    } else {   // near a cutoff: the exact FP64 test decides
-                        const double4 pi = a.pos[i], pj = a.pos[jof(f)];
-                        const double d2 = exact_d2(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z, a.bd, a.g.per);
-                        in_r = d2 < a.cut_r2;
-                        in_a = d2 < a.cut_a2;
-                    }
-                }
-            }
-        }
+    auto classify = [&](int f, const float4 &pj, bool &in_r, bool &in_a, bool &near) {
+        float dx = pj.x - pfi.x, dy = pj.y - pfi.y, dz = pj.z - pfi.z;
+        if (!image_placed) minimg(a.bf, dx, dy, dz);
+        const float d2f = dx * dx + dy * dy + dz * dz;
+        const bool other = f != fself && f < total;   // a real candidate, not the atom itself
+        in_r = d2f < a.cut_r2f_lo && other;
+        in_a = d2f < a.cut_a2f_lo;
+        // inside a band, or NaN (an atom far outside its cell): the exact FP64 test decides
+        near = other && !(d2f >= a.cut_r2f_hi) && !(d2f < a.cut_r2f_lo && (d2f < a.cut_a2f_lo || d2f >= a.cut_a2f_hi));
+    };
+    auto exact = [&](int f, bool &in_r, bool &in_a) {
+        const double4 qi = a.pos[i], qj = a.pos[jof(f)];
+        const double d2 = exact_d2(qi.x, qi.y, qi.z, qj.x, qj.y, qj.z, a.bd, a.g.per);
+        in_r = d2 < a.cut_r2;
+        in_a = d2 < a.cut_a2;
+    };
+    auto append = [&](int f, const float4 &pj, bool in_r, bool in_a) {
         const unsigned mr = __ballot_sync(0xffffffffu, in_r);
-        if (in_r) {
-            const int pos = m + __popc(mr & lt);
-            // segment (angular? 0 : 2) + species of j in bits 30-31 above the walk index
-            const uint32_t sg = (in_a ? 0u : 2u) + (k >> 30);
-            if (pos < SORT_MAX) key[pos] = (sg << 30) | (uint32_t)f;
-        }
+        const int pos = m + __popc(mr & lt);
+        // segment (angular? 0 : 2) + species of j in bits 30-31 above the walk index
+        if (in_r && pos < SORT_MAX) key[pos] = (((in_a ? 0u : 2u) + (uint32_t)__float_as_int(pj.w)) << 30) | (uint32_t)f;
         m += __popc(mr);
+    };
+    for (int base = 0; base < total; base += 64) {   // two chunks of 32 candidates at a time
+        const int f0 = base + lane, f1 = base + 32 + lane;
+        const float4 p0 = cand(f0), p1 = cand(f1);
+        bool r0, a0, n0, r1, a1, n1;
+        classify(f0, p0, r0, a0, n0);
+        classify(f1, p1, r1, a1, n1);
+        if (__any_sync(0xffffffffu, n0 || n1)) {
+            if (n0) exact(f0, r0, a0);
+            if (n1) exact(f1, r1, a1);
+        }
+        append(f0, p0, r0, a0);
+        append(f1, p1, r1, a1);
     }
     const int mm = min(m, SORT_MAX);
     __syncwarp();
@@ -335,6 +343,7 @@ __device__ __forceinline__ void lists_body(const ListArgs &args, int64_t blk, in
     bool image_placed = true;
 #pragma unroll
     for (int d = 0; d < 3; ++d) image_placed = image_placed && (!a.g.per[d] || a.g.nc[d] >= 3);
+    const float4 far = make_float4(1e30f, 1e30f, 1e30f, 0.f);
     for (int64_t c = blk; c < ncell; c += nblk) {
         // the stencil: cells lo..hi per axis (wrapped where periodic), z-major, and each one's
         // offset in the walk (warp 0)
@@ -350,6 +359,7 @@ __device__ __forceinline__ void lists_body(const ListArgs &args, int64_t blk, in
             }
             const int sx = hi[0] - lo[0] + 1, sy = hi[1] - lo[1] + 1, sz = hi[2] - lo[2] + 1;
             const int nst = sx * sy * sz;   // at most 27 cells
+            const int centre = ((ci[2] - lo[2]) * sy + (ci[1] - lo[1])) * sx + (ci[0] - lo[0]);
             int my_p0 = 0, my_len = 0;
             if (lane < nst) {
                 const int x = lo[0] + lane % sx, y = lo[1] + (lane / sx) % sy, z = lo[2] + lane / (sx * sy);
@@ -371,13 +381,32 @@ __device__ __forceinline__ void lists_body(const ListArgs &args, int64_t blk, in
                 sm.off[lane] = incl - my_len;
                 sm.p0[lane] = my_p0;
             }
+            if (lane == centre) sm.self0 = incl - my_len;
             if (lane == 31) {
                 sm.total = incl;
                 sm.nst = nst;
             }
         }
         __syncthreads();
-        const int total = sm.total, nst = sm.nst;
+        const int total = sm.total, nst = sm.nst, self0 = sm.self0;
+        auto placed = [&](int cl, float4 pf) {
+            const float4 o = sm.org[cl];
+            pf.x += o.x; pf.y += o.y; pf.z += o.z;
+            return pf;
+        };
+        const bool staged = ((total + 63) & ~63) <= STAGE_MAX;
+        if (staged) {   // a warp per stencil cell, a lane per atom
+            for (int cl = w; cl < nst; cl += LB_WARPS) {
+                const int o = sm.off[cl], p0 = sm.p0[cl], len = (cl + 1 < nst ? sm.off[cl + 1] : total) - o;
+                for (int e = lane; e < len; e += 32) {
+                    sm.p[o + e] = placed(cl, a.cposf[p0 + e]);
+                    sm.k[o + e] = a.ckey[p0 + e];
+                    sm.j[o + e] = a.cell_atoms[p0 + e];
+                }
+            }
+            for (int f = total + threadIdx.x; f < ((total + 63) & ~63); f += blockDim.x) sm.p[f] = far;
+        }
+        __syncthreads();
         // stencil cell of candidate f of the walk: the last one whose offset is <= f (empty
         // cells share the offset of the cell after them)
         auto cell_of = [&](int f) {
@@ -385,22 +414,6 @@ __device__ __forceinline__ void lists_body(const ListArgs &args, int64_t blk, in
             while (cl + 1 < nst && sm.off[cl + 1] <= f) ++cl;
             return cl;
         };
-        auto placed = [&](int cl, float4 pf) {
-            const float4 o = sm.org[cl];
-            pf.x += o.x; pf.y += o.y; pf.z += o.z;
-            return pf;
-        };
-        const bool staged = total <= STAGE_MAX;
-        if (staged) {
-            for (int f = threadIdx.x; f < total; f += blockDim.x) {
-                const int cl = cell_of(f);
-                const int p = sm.p0[cl] + (f - sm.off[cl]);
-                sm.p[f] = placed(cl, a.cposf[p]);
-                sm.k[f] = a.ckey[p];
-                sm.j[f] = a.cell_atoms[p];
-            }
-        }
-        __syncthreads();
         // the cell's own atoms, one per warp
         const int c0 = a.cell_start[c], nc0 = a.cell_start[c + 1] - c0;
         for (int q = w; q < nc0; q += LB_WARPS) {
@@ -408,11 +421,7 @@ __device__ __forceinline__ void lists_body(const ListArgs &args, int64_t blk, in
             const float4 pfi = a.cposf[c0 + q];
             if (staged) {
                 list_atom(
-                    a, i, pfi, sm.key[w], lane, total, image_placed,
-                    [&](int f, uint32_t &k, float4 &pf) {
-                        k = sm.k[f];
-                        pf = sm.p[f];
-                    },
+                    a, i, pfi, self0 + q, sm.key[w], lane, total, image_placed, [&](int f) { return sm.p[f]; },
                     [&](int f) { return sm.j[f]; },
                     [&](int f, int &jx, int &oj) {
                         jx = sm.j[f];
@@ -424,12 +433,11 @@ __device__ __forceinline__ void lists_body(const ListArgs &args, int64_t blk, in
                     return sm.p0[cl] + (f - sm.off[cl]);
                 };
                 list_atom(
-                    a, i, pfi, sm.key[w], lane, total, image_placed,
-                    [&](int f, uint32_t &k, float4 &pf) {
+                    a, i, pfi, self0 + q, sm.key[w], lane, total, image_placed,
+                    [&](int f) {
+                        if (f >= total) return far;
                         const int cl = cell_of(f);
-                        const int p = sm.p0[cl] + (f - sm.off[cl]);
-                        k = a.ckey[p];
-                        pf = placed(cl, a.cposf[p]);
+                        return placed(cl, a.cposf[sm.p0[cl] + (f - sm.off[cl])]);
                     },
                     [&](int f) { return a.cell_atoms[position_of(f)]; },
                     [&](int f, int &jx, int &oj) {
@@ -443,30 +451,34 @@ __device__ __forceinline__ void lists_body(const ListArgs &args, int64_t blk, in
     }
 }
 
-// 32 entries of a list row from b on (16-byte aligned), as eight independent 16-byte loads;
-// the 4-entry groups that start at or past hi read as -1 (no caller index).
-__device__ __forceinline__ void load_round(const int32_t *__restrict__ row, int b, int hi, int4 (&v)[8]) {
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-        v[u] = b + 4 * u < hi ? *reinterpret_cast<const int4 *>(row + b + 4 * u) : make_int4(-1, -1, -1, -1);
+// Eight entries of a list row at p (32-byte aligned) in one 256-bit load.
+__device__ __forceinline__ void ld_v8(const int32_t *p, int *r) {
+    asm("ld.global.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "l"(p));
 }
 
-// Slot of caller index oi in [lo, hi) of a list row, or -1.  A caller index appears at most
-// once in a row's entries [0, seg.w), so the first match in a round that starts at lo & ~3 is
-// the only one below hi; a match at or past hi is a stale entry past the row's end or in no
-// segment of this kind, and counts as none.
+// Slot of caller index oi in [lo, hi) of a list row (32-byte aligned rows), or -1.  The row is
+// read from lo & ~7 in rounds of 32 entries, four independent 32-byte loads each (the 8-entry
+// pieces that start at or past hi are not read).  A caller index appears at most once in a
+// row's entries [0, seg.w), and the entries before lo belong to other segments, so the first
+// match below hi is the slot; a match at or past hi (a stale entry past the row's end, or
+// another segment) counts as none.
 __device__ __forceinline__ int find_slot(const int32_t *__restrict__ row, int lo, int hi, int oi) {
     int found = -1;
-    for (int b = lo & ~3; b < hi && found < 0; b += 32) {
-        int4 v[8];
-        load_round(row, b, hi, v);
+    for (int b = lo & ~7; b < hi && found < 0; b += 32) {
+        int v[32];
 #pragma unroll
-        for (int u = 7; u >= 0; --u) {   // descending: the lowest match is kept
-            found = v[u].w == oi ? b + 4 * u + 3 : found;
-            found = v[u].z == oi ? b + 4 * u + 2 : found;
-            found = v[u].y == oi ? b + 4 * u + 1 : found;
-            found = v[u].x == oi ? b + 4 * u : found;
+        for (int u = 0; u < 4; ++u) {
+            if (b + 8 * u < hi) {
+                ld_v8(row + b + 8 * u, v + 8 * u);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) v[8 * u + c] = -1;
+            }
         }
+#pragma unroll
+        for (int e = 31; e >= 0; --e) found = v[e] == oi ? b + e : found;   // descending: the lowest match is kept
         if (found >= hi) found = -1;
     }
     return found;

@@ -56,7 +56,7 @@ struct ListArgs {
 
 struct RevArgs {
     const int32_t *species, *orig;
-    const int32_t *nbr, *nbr_orig;   // nbr_orig atom-major [n][capr], capr a multiple of 4
+    const int32_t *nbr, *nbr_orig;   // nbr_orig atom-major [n][capr], capr a multiple of 8 (32-byte rows)
     const int4 *seg;
     int cap, capr;
     int64_t n;

@@ -141,8 +141,8 @@ void fill_params(sl::NepDev<R> &P, const sl_nep_params *p) {
 
 void free_sys(sl::Sys &s) {
     void *ptrs[] = {s.pos, s.vel, s.spin, s.spin_prev, s.F, s.H, s.posref, s.posf, s.spinf, s.species, s.orig,
-                    s.inv, s.nbr, s.rev, s.nbr_orig, s.cells.posf, s.cells.key, s.seg, s.cells.count, s.cells.start, s.cells.fill, s.cells.atoms,
-                    s.cells.of, s.q, s.bsum, s.fp, s.ei, s.pairs, s.clj, s.cls, s.cnt, s.cmask, s.fown, s.gii,
+                    s.inv, s.nbr, s.rev, s.cells.posf, s.cells.key, s.seg, s.cells.count, s.cells.start, s.cells.fill, s.cells.atoms,
+                    s.cells.of, s.cells.sub, s.q, s.bsum, s.fp, s.ei, s.pairs, s.clj, s.cls, s.cnt, s.cmask, s.fown, s.gii,
                     s.wpart, s.Fo, s.Ho,
                     s.status, s.rebuild, s.d_step, s.d_par, s.red, s.snap, s.d_builds,
                     s.posmid, s.posmidf, s.mids, s.midsf, s.mx, s.mg, s.aax, s.aag, s.aapart, s.md, s.Bat,
@@ -555,11 +555,11 @@ int sl_create_system(const double *positions, const double *spins, const double 
         (rc = dalloc(&s.spin_prev, N)) || (rc = dalloc(&s.F, N)) || (rc = dalloc(&s.H, N)) ||
         (rc = dalloc(&s.posref, N)) || (rc = dalloc(&s.posf, N)) || (rc = dalloc(&s.spinf, N)) ||
         (rc = dalloc(&s.species, N)) || (rc = dalloc(&s.orig, N)) || (rc = dalloc(&s.inv, N)) ||
-        (rc = dalloc(&s.nbr, N * sl::nbr_orig_stride(s.cap))) || (rc = dalloc(&s.rev, N * sl::nbr_orig_stride(s.cap))) ||
-        (rc = dalloc(&s.nbr_orig, N * sl::nbr_orig_stride(s.cap))) || (rc = dalloc(&s.cells.posf, N)) || (rc = dalloc(&s.cells.key, N)) || (rc = dalloc(&s.seg, N)) ||
+        (rc = dalloc(&s.nbr, N * sl::nbr_stride(s.cap))) || (rc = dalloc(&s.rev, N * sl::nbr_stride(s.cap))) ||
+        (rc = dalloc(&s.cells.posf, N)) || (rc = dalloc(&s.cells.key, N)) || (rc = dalloc(&s.seg, N)) ||
         (rc = dalloc(&s.cells.count, (size_t)s.cells.ncell)) || (rc = dalloc(&s.cells.start, (size_t)s.cells.ncell + 1)) ||
         (rc = dalloc(&s.cells.fill, (size_t)s.cells.ncell)) || (rc = dalloc(&s.cells.atoms, N)) ||
-        (rc = dalloc(&s.cells.of, N)) || (rc = dalloc((char **)&s.q, R * DIM * (size_t)s.qs)) ||
+        (rc = dalloc(&s.cells.of, N)) || (rc = dalloc(&s.cells.sub, (size_t)s.cells.ncell * 8)) || (rc = dalloc((char **)&s.q, R * DIM * (size_t)s.qs)) ||
         (rc = dalloc((char **)&s.bsum, R * NBREC * N)) || (rc = dalloc((char **)&s.fp, R * DIM * N)) ||
         (rc = dalloc((char **)&s.ei, R * N)) || (rc = dalloc((char **)&s.pairs, R * 8 * N * s.cap)) ||
         (rc = dalloc(&s.clj, N * (size_t)(s.cap + s.cap_ang))) || (rc = dalloc(&s.cls, N * (size_t)(s.cap + s.cap_ang))) ||
@@ -952,9 +952,9 @@ int sl_get_neighbors(sl_system *sys, int32_t cap, int32_t *counts_rad, int32_t *
     int rc = check_status(s);
     if (rc) return rc;
     const size_t N = (size_t)s.n;
-    std::vector<int32_t> nbr(N * sl::nbr_orig_stride(s.cap)), orig(N);
+    std::vector<int32_t> nbr(N * sl::nbr_stride(s.cap)), orig(N);
     std::vector<int4> seg(N);
-    CK(cudaMemcpyAsync(nbr.data(), s.nbr, sizeof(int32_t) * N * sl::nbr_orig_stride(s.cap), cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(nbr.data(), s.nbr, sizeof(int32_t) * N * sl::nbr_stride(s.cap), cudaMemcpyDeviceToHost,
                        s.stream));
     CK(cudaMemcpyAsync(orig.data(), s.orig, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s.stream));
     CK(cudaMemcpyAsync(seg.data(), s.seg, sizeof(int4) * N, cudaMemcpyDeviceToHost, s.stream));
@@ -964,7 +964,7 @@ int sl_get_neighbors(sl_system *sys, int32_t cap, int32_t *counts_rad, int32_t *
         const int c = orig[i];
         std::vector<int32_t> rad, ang;
         for (int t = 0; t < seg[i].w; ++t) {
-            const int32_t j = orig[nbr[(size_t)i * sl::nbr_orig_stride(s.cap) + t]];
+            const int32_t j = orig[nbr[(size_t)i * sl::nbr_stride(s.cap) + t]];
             rad.push_back(j);
             if (t < seg[i].y) ang.push_back(j);
         }
@@ -1273,12 +1273,12 @@ int64_t sl_estimate_device_bytes(int64_t n, const sl_options *opt_in) {
     const int64_t cap = opt.nbr_cap_rad, ca = opt.nbr_cap_ang;
     int64_t per = 7 * 32 + 2 * 16                      // state (double4) and FP32 copies
                   + 3 * 4 + 4 + 16 + 16 + 4            // species, caller index maps, list segments, cell copies
-                  + 5 * cap + 4 * sl::nbr_orig_stride((int)cap)   // candidate lists, reverse slots (1 byte), caller-index rows
+                  + 5 * sl::nbr_stride((int)cap)     // candidate lists, reverse slots (1 byte)
                   + 6 * (ca + cap) + 16                // compact rows, counts
                   + 4 * ((cap + 31) / 32)              // in-cutoff slot mask
                   + R * (2 * sl::DIM + sl::NBREC + 1 + 9) // q, Fp, angular sums, E_i, virial parts
                   + R * 8 * cap + 2 * R * 4            // pair records, per-atom sums
-                  + 2 * 32 + 5 * 32 + 3 * 4;           // evaluation outputs, snapshot, cell arrays
+                  + 2 * 32 + 5 * 32 + 4 * 4;           // evaluation outputs, snapshot, cell arrays
     if (opt.midpoint_iters > 0)                        // midpoint positions and spins, iterate, image, rings
         per += 4 * 32 + 2 * 16 + (opt.anderson_depth > 0 ? 2 * 32 * (opt.anderson_depth + 1) : 0);
     return n * per + (1 << 20);

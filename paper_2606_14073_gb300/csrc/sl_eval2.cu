@@ -879,7 +879,7 @@ static Eval2Args<R> args2(Sys &s, const EvalAt &at, bool want_virial) {
         a.box = *reinterpret_cast<const BoxDev<R> *>(&s.boxf);
     }
     a.skip = at.skip;
-    a.nbr = s.nbr; a.seg = s.seg; a.rev = s.rev; a.capr = nbr_orig_stride(s.cap); a.n = s.n; a.n_fe = s.n_fe;
+    a.nbr = s.nbr; a.seg = s.seg; a.rev = s.rev; a.capr = nbr_stride(s.cap); a.n = s.n; a.n_fe = s.n_fe;
     a.cap = s.cap; a.cap_ang = s.cap_ang;
     a.clj = s.clj; a.cls = s.cls; a.cnt = s.cnt; a.mask = s.cmask; a.maskw = s.maskw;
     a.q = (R *)s.q; a.qs = s.qs; a.bsum = (R *)s.bsum; a.fp = (R *)s.fp; a.ei = (R *)s.ei;

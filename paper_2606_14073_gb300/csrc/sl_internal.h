@@ -79,6 +79,7 @@ struct Cells {
     int *count = nullptr, *start = nullptr, *fill = nullptr, *atoms = nullptr, *of = nullptr;
     float4 *posf = nullptr;    // cell-ordered FP32 positions (list build)
     uint32_t *key = nullptr;   // cell-ordered species << 30 | caller index
+    int *sub = nullptr;        // [ncell][8] first position of each half-width sub-cell, relative to its cell
 };
 
 struct Sys {
@@ -109,10 +110,9 @@ struct Sys {
     int32_t *species = nullptr, *orig = nullptr, *inv = nullptr;
     int64_t n_fe = 0;          // atoms [0, n_fe) are species 0
 
-    // neighbour lists, atom-major rows of nbr_orig_stride(cap) entries: nbr (internal index of
-    // each candidate), rev (slot of the atom in its candidate's list; cap <= 256, one byte),
-    // nbr_orig (caller index of each candidate, searched by the reverse-slot build)
-    int32_t *nbr = nullptr, *nbr_orig = nullptr;
+    // neighbour lists, atom-major rows of nbr_stride(cap) entries: nbr (internal index of
+    // each candidate) and rev (slot of the atom in its candidate's list; cap <= 256, one byte)
+    int32_t *nbr = nullptr;
     uint8_t *rev = nullptr;
     int4 *seg = nullptr;       // per atom: ends of (ang t0, ang t1, rad t0, rad t1)
     Cells cells;
@@ -215,7 +215,7 @@ void solo_free(Sys &s);
 // launchers (sl_neighbors.cu)
 // row stride of the atom-major caller-index copy of the lists: cap rounded up to a multiple
 // of 4 entries, so every row starts on a 16-byte boundary
-inline int nbr_orig_stride(int cap) { return (cap + 7) & ~7; }   // rows of 32-byte multiples
+inline int nbr_stride(int cap) { return (cap + 7) & ~7; }   // rows of 32-byte multiples
 void nbr_setup(Sys &s);
 void launch_rebuild(Sys &s, bool conditional);
 // sl_eval2.cu: the system's evaluation at the state (with the virial parts when asked for), or

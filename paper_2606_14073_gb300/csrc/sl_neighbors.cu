@@ -43,23 +43,26 @@ __device__ __forceinline__ double exact_d2(double xi, double yi, double zi, doub
     return __dadd_rn(__dadd_rn(__dmul_rn(t[0], t[0]), __dmul_rn(t[1], t[1])), __dmul_rn(t[2], t[2]));
 }
 
-
-
+// Cell of each atom and its half-width sub-cell inside it (bit 0 x, 1 y, 2 z): the sub-cell
+// index along an axis is floor(2 x / w) clamped to [0, 2 nc), and the cell is half of it, the
+// same cell as floor(x / w) clamped (2 x / w is the rounded x / w doubled exactly).
 __device__ __forceinline__ void bin_body(const BinArgs &r, int64_t blk, int64_t nblk) {
     if (r.flag && *r.flag == 0) return;
     const GridArgs &g = r.g;
     for (int64_t i = blk * (int64_t)blockDim.x + threadIdx.x; i < r.n; i += nblk * blockDim.x) {
-    const double4 p = r.pos[i];
-    const double x[3] = {p.x, p.y, p.z};
-    int c[3];
+        const double4 p = r.pos[i];
+        const double x[3] = {p.x, p.y, p.z};
+        int c[3], sb = 0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        int ci = (int)floor(x[a] / g.w[a]);
-        c[a] = min(max(ci, 0), g.nc[a] - 1);
-    }
-    const int cell = (c[2] * g.nc[1] + c[1]) * g.nc[0] + c[0];
-    r.of[i] = cell;
-    atomicAdd(r.count + cell, 1);
+        for (int a = 0; a < 3; ++a) {
+            // the conversion saturates, so far outside positions clamp too
+            const int hi = min(max((int)floor(2.0 * (x[a] / g.w[a])), 0), 2 * g.nc[a] - 1);
+            c[a] = hi >> 1;
+            sb |= (hi & 1) << a;
+        }
+        const int cell = (c[2] * g.nc[1] + c[1]) * g.nc[0] + c[0];
+        r.of[i] = (cell << 3) | sb;
+        atomicAdd(r.count + cell, 1);
     }
 }
 
@@ -93,13 +96,14 @@ __device__ __forceinline__ void scan_body(const BinArgs &r, int *s_part, int &s_
 
 // Atoms into their cells, with a cell-ordered copy of the key (species << 30 | caller index)
 // and of the position relative to the cell's corner in FP32 (NaN for an atom more than a
-// cell width outside its cell, which only a non-periodic axis can hold; the species bits in
-// w), so the list build reads candidates contiguously.
+// cell width outside its cell, which only a non-periodic axis can hold); w carries the
+// species (bit 0) and the sub-cell (bits 1-3) as integer bits.  The list build reads the
+// candidates contiguously.
 __device__ __forceinline__ void scatter_body(const BinArgs &r, int64_t blk, int64_t nblk) {
     if (r.flag && *r.flag == 0) return;
     const GridArgs &g = r.g;
     for (int64_t i = blk * (int64_t)blockDim.x + threadIdx.x; i < r.n; i += nblk * blockDim.x) {
-        const int c = r.of[i];
+        const int cs = r.of[i], c = cs >> 3;
         const int p = r.start[c] + atomicAdd(r.fill + c, 1);
         const double4 x = r.pos[i];
         const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
@@ -108,9 +112,9 @@ __device__ __forceinline__ void scatter_body(const BinArgs &r, int64_t blk, int6
 #pragma unroll
         for (int d = 0; d < 3; ++d) near = near && u[d] >= -g.w[d] && u[d] <= 2.0 * g.w[d];
         r.atoms[p] = (int)i;
-        const float sp = __int_as_float(r.species[i]);   // the species bits ride in w
-        r.cposf[p] = near ? make_float4((float)u[0], (float)u[1], (float)u[2], sp)
-                          : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, sp);
+        const float tag = __int_as_float(r.species[i] | ((cs & 7) << 1));
+        r.cposf[p] = near ? make_float4((float)u[0], (float)u[1], (float)u[2], tag)
+                          : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, tag);
         r.ckey[p] = ((uint32_t)r.species[i] << 30) | (uint32_t)r.orig[i];
     }
 }
@@ -145,18 +149,21 @@ __device__ __forceinline__ void warp_bitonic64(uint64_t (&k)[E], int lane) {
     }
 }
 
-// Each cell's atoms in ascending key order (species << 30 | caller index), one warp per cell:
-// the scatter fills a cell in the order of its atomic increments, and the list build walks the
-// cells' atoms in their stored order, so sorted cells make every list independent of that order
-// and of the internal atom order.  Cells of up to 64 atoms are sorted in registers; a larger one
-// (only in boxes of very few cells) by lane 0 in place.
+__device__ __forceinline__ int sub_of(const float4 &pf) { return (__float_as_int(pf.w) >> 1) & 7; }
+
+// Each cell's atoms in ascending (sub-cell, key) order (key: species << 30 | caller index),
+// one warp per cell, and the first position of each sub-cell relative to the cell's start:
+// the scatter fills a cell in the order of its atomic increments, and the list build walks
+// the cells' atoms in their stored order, so sorted cells make every list independent of that
+// order and of the internal atom order.  Cells of up to 64 atoms are sorted in registers; a
+// larger one (only in boxes of very few cells) by lane 0 in place.
 __device__ __forceinline__ void cellsort_body(const BinArgs &r, int64_t blk, int64_t nblk) {
     if (r.flag && *r.flag == 0) return;
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int64_t c = blk * wpb + (threadIdx.x >> 5); c < r.ncell; c += nblk * wpb) {
         const int p0 = r.start[c], len = r.start[c + 1] - p0;
-        if (len <= 1) continue;
         if (len <= 64) {
+            // (sub-cell << 61) | (key << 29) | element: distinct, so the order is unique
             uint64_t v[2];
             int at[2];
             float4 pf[2];
@@ -167,35 +174,46 @@ __device__ __forceinline__ void cellsort_body(const BinArgs &r, int64_t blk, int
                 at[q] = 0;
                 pf[q] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (e < len) {
-                    v[q] = ((uint64_t)r.ckey[p0 + e] << 32) | (uint32_t)e;
                     at[q] = r.atoms[p0 + e];
                     pf[q] = r.cposf[p0 + e];
+                    v[q] = ((uint64_t)sub_of(pf[q]) << 61) | ((uint64_t)r.ckey[p0 + e] << 29) | (uint64_t)e;
                 }
             }
             warp_bitonic64<2>(v, lane);
+            int below[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // sorted elements of a sub-cell below k
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int e = q * 32 + lane;
-                const int src = (int)(v[q] & 0xffffffffu), sl = src & 31, sq = src >> 5;
+                const int src = (int)(v[q] & 63u), sl = src & 31, sq = src >> 5;
                 const int a0 = __shfl_sync(0xffffffffu, at[0], sl), a1 = __shfl_sync(0xffffffffu, at[1], sl);
                 float4 f0, f1;
                 f0.x = __shfl_sync(0xffffffffu, pf[0].x, sl); f1.x = __shfl_sync(0xffffffffu, pf[1].x, sl);
                 f0.y = __shfl_sync(0xffffffffu, pf[0].y, sl); f1.y = __shfl_sync(0xffffffffu, pf[1].y, sl);
                 f0.z = __shfl_sync(0xffffffffu, pf[0].z, sl); f1.z = __shfl_sync(0xffffffffu, pf[1].z, sl);
                 f0.w = __shfl_sync(0xffffffffu, pf[0].w, sl); f1.w = __shfl_sync(0xffffffffu, pf[1].w, sl);
+                const int sub = e < len ? (int)(v[q] >> 61) : 8;
+#pragma unroll
+                for (int k = 1; k < 8; ++k) below[k] += __popc(__ballot_sync(0xffffffffu, sub < k));
                 if (e < len) {
-                    r.ckey[p0 + e] = (uint32_t)(v[q] >> 32);
+                    r.ckey[p0 + e] = (uint32_t)(v[q] >> 29);
                     r.atoms[p0 + e] = sq == 0 ? a0 : a1;
                     r.cposf[p0 + e] = sq == 0 ? f0 : f1;
                 }
             }
+            if (lane < 8) {
+                int mine = 0;
+#pragma unroll
+                for (int k = 1; k < 8; ++k) mine = lane == k ? below[k] : mine;
+                r.sub[c * 8 + lane] = mine;
+            }
         } else if (lane == 0) {
+            auto before = [&](int s1, uint32_t k1, int s2, uint32_t k2) { return s1 < s2 || (s1 == s2 && k1 < k2); };
             for (int x = 1; x < len; ++x) {
                 const uint32_t k = r.ckey[p0 + x];
                 const int at = r.atoms[p0 + x];
                 const float4 pf = r.cposf[p0 + x];
                 int y = x - 1;
-                for (; y >= 0 && r.ckey[p0 + y] > k; --y) {
+                for (; y >= 0 && before(sub_of(pf), k, sub_of(r.cposf[p0 + y]), r.ckey[p0 + y]); --y) {
                     r.ckey[p0 + y + 1] = r.ckey[p0 + y];
                     r.atoms[p0 + y + 1] = r.atoms[p0 + y];
                     r.cposf[p0 + y + 1] = r.cposf[p0 + y];
@@ -204,18 +222,29 @@ __device__ __forceinline__ void cellsort_body(const BinArgs &r, int64_t blk, int
                 r.atoms[p0 + y + 1] = at;
                 r.cposf[p0 + y + 1] = pf;
             }
+            int k = 0;
+            for (int e = 0; e < len; ++e)
+                for (const int s = sub_of(r.cposf[p0 + e]); k <= s; ++k) r.sub[c * 8 + k] = e;
+            for (; k < 8; ++k) r.sub[c * 8 + k] = len;
         }
         __syncwarp();
     }
 }
 
 // The lists are built cell by cell: a block takes one cell, copies the candidates of its
-// stencil (the 27 surrounding cells, each cell's atoms contiguous and sorted by key) into
-// shared memory once, and its warps build the lists of the cell's atoms from there, one atom
-// per warp: lanes take the candidates 32 at a time, pairs inside the list cutoff are appended
-// to a per-warp buffer in walk order (ballot/popc), and the buffer is written out partitioned
-// by segment, each segment in walk order.  The walk order (stencil cells z-major, each cell by
-// key) depends on the positions and caller indices only.
+// stencil (the 27 surrounding cells, each cell's atoms contiguous and sorted by sub-cell and
+// key) into shared memory once, and its warps build the lists of the cell's atoms from there,
+// one atom per warp: lanes take the candidates 32 at a time, pairs inside the list cutoff are
+// appended to a per-warp buffer in walk order (ballot/popc), and the buffer is written out
+// partitioned by segment, each segment in walk order.
+//
+// With at least 3 cells along every periodic axis an atom walks only the 5 x 5 x 5 half-width
+// sub-cells around its own (a neighbour within the cutoff, at most two sub-cell widths away,
+// lies in one of them: about 58% of the 27 cells' candidates): the block lists the staged
+// indices of that walk once for each of the 8 sub-cell positions in the centre cell, sub-cells
+// z-major, each by key.  Otherwise the walk is the whole stencil (lo..hi per axis, z-major,
+// each cell by sub-cell and key).  Either order depends on the positions and caller indices
+// only.
 //
 // FP32 pre-test.  The scatter stores each atom's position relative to its own cell's corner
 // (FP64 difference, then rounded), so the FP32 separation of a pair is the difference of two
@@ -231,29 +260,31 @@ __device__ __forceinline__ int wrap_cell(int x, int nc) { return x < 0 ? x + nc 
 
 constexpr int SORT_MAX = 256;
 constexpr int STAGE_MAX = 1024;   // staged candidates; a larger stencil is walked in global memory
+constexpr int WALK_MAX = 640;     // a sub-cell walk's staged indices (a longer one takes the whole stencil)
 
 struct ListSmem {
-    // FP32 positions of the stencil's candidates relative to the centre cell's corner, the
-    // species bits in w; padded to a whole number of warps with candidates far away
+    // FP32 positions of the stencil's candidates relative to the centre cell's corner, with the
+    // species and sub-cell bits in w; padded past the end with candidates far away
     float4 p[STAGE_MAX];
-    uint32_t k[STAGE_MAX];    // their keys (species << 30 | caller index)
     int j[STAGE_MAX];         // their internal indices
     uint32_t key[LB_WARPS][SORT_MAX];
+    uint16_t walk[8][WALK_MAX];   // per sub-cell position of the centre cell: its walk's staged indices
+    int wlen[8];
     int off[32], p0[32];      // stencil cells: offset in the walk, first cell-ordered position
+    int soff[27][9];          // stencil cells (27-cell form): sub-cell starts relative to the cell, and its size
     float4 org[32];           // stencil cells: corner relative to the centre cell's corner (its image)
     int nst, total, self0;    // self0: walk offset of the centre cell
 };
 
-// One atom's list from the candidates f = 0 .. total-1 of its cell's stencil (fself: the
-// atom's own walk index).  pfi: the atom's FP32 position relative to its cell's corner;
-// cand(f) gives candidate f's FP32 position relative to the same corner with its species bits
-// in w (candidates at f >= total far away), jof(f) its internal index (the exact test), and
-// ident(f, j, o) its internal and caller indices for the list entry.  The FP32 decision is
-// branch-free; a warp takes the exact test's branch only when one of its lanes is in a band.
-template <typename Cand, typename Jof, typename Ident>
+// One atom's list from its walk fw = 0 .. nwalk-1 over the staged or stencil candidates
+// (total of them; fself: the atom's own candidate index).  pfi: the atom's FP32 position
+// relative to its cell's corner; cand(fw, f) gives walk step fw's candidate index f (f >= total:
+// none) and FP32 position relative to the same corner with the species in bit 0 of w, and
+// jof(f) its internal index (the exact test and the list entry).  The FP32 decision is branch-free; a warp takes the exact test's branch only
+// when one of its lanes is in a band.
+template <typename Cand, typename Jof>
 __device__ __forceinline__ void list_atom(const ListArgs &a, int64_t i, float4 pfi, int fself, uint32_t *key,
-                                          int lane, int total, bool image_placed, Cand cand, Jof jof,
-                                          Ident ident) {
+                                          int lane, int nwalk, int total, bool image_placed, Cand cand, Jof jof) {
     const unsigned lt = (1u << lane) - 1u;
     int m = 0;
     auto classify = [&](int f, const float4 &pj, bool &in_r, bool &in_a, bool &near) {
@@ -275,13 +306,16 @@ __device__ __forceinline__ void list_atom(const ListArgs &a, int64_t i, float4 p
     auto append = [&](int f, const float4 &pj, bool in_r, bool in_a) {
         const unsigned mr = __ballot_sync(0xffffffffu, in_r);
         const int pos = m + __popc(mr & lt);
-        // segment (angular? 0 : 2) + species of j in bits 30-31 above the walk index
-        if (in_r && pos < SORT_MAX) key[pos] = (((in_a ? 0u : 2u) + (uint32_t)__float_as_int(pj.w)) << 30) | (uint32_t)f;
+        // segment (angular? 0 : 2) + species of j in bits 30-31 above the candidate index
+        if (in_r && pos < SORT_MAX)
+            key[pos] = (((in_a ? 0u : 2u) + ((uint32_t)__float_as_int(pj.w) & 1u)) << 30) | (uint32_t)f;
         m += __popc(mr);
     };
-    for (int base = 0; base < total; base += 64) {   // two chunks of 32 candidates at a time
-        const int f0 = base + lane, f1 = base + 32 + lane;
-        const float4 p0 = cand(f0), p1 = cand(f1);
+    for (int base = 0; base < nwalk; base += 64) {   // two chunks of 32 candidates at a time
+        int f0, f1;
+        float4 p0, p1;
+        cand(base + lane, f0, p0);
+        cand(base + 32 + lane, f1, p1);
         bool r0, a0, n0, r1, a1, n1;
         classify(f0, p0, r0, a0, n0);
         classify(f1, p1, r1, a1, n1);
@@ -317,12 +351,7 @@ __device__ __forceinline__ void list_atom(const ListArgs &a, int64_t i, float4 p
             if (sg == (unsigned)t) pos = run[t] + __popc(b & lt);
             run[t] += __popc(b);
         }
-        if (e < mm && pos < a.cap) {
-            int jx, oj;
-            ident((int)(k & 0x3FFFFFFFu), jx, oj);
-            a.nbr[i * a.capr + pos] = jx;
-            a.nbr_orig[i * a.capr + pos] = oj;   // atom-major: one row per atom
-        }
+        if (e < mm && pos < a.cap) a.nbr[i * a.capr + pos] = jof((int)(k & 0x3FFFFFFFu));   // atom-major rows
     }
     if (lane == 0) {
         a.seg[i] = make_int4(min(ends_all[0], a.cap), min(ends_all[1], a.cap), min(ends_all[2], a.cap),
@@ -339,34 +368,54 @@ __device__ __forceinline__ void lists_body(const ListArgs &args, int64_t blk, in
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int ncell = a.g.nc[0] * a.g.nc[1] * a.g.nc[2];
     // with at least 3 cells along every periodic axis each stencil cell is one image, placed by
-    // its corner offset; otherwise the walk takes the minimum image
+    // its corner offset, and the sub-cell walks apply; otherwise the walk takes the minimum image
     bool image_placed = true;
 #pragma unroll
     for (int d = 0; d < 3; ++d) image_placed = image_placed && (!a.g.per[d] || a.g.nc[d] >= 3);
     const float4 far = make_float4(1e30f, 1e30f, 1e30f, 0.f);
     for (int64_t c = blk; c < ncell; c += nblk) {
-        // the stencil: cells lo..hi per axis (wrapped where periodic), z-major, and each one's
-        // offset in the walk (warp 0)
+        // the stencil and each cell's offset in it (warp 0): the 27 cells around (an empty one
+        // past a non-periodic face) when the images are placed, else lo..hi per axis, z-major
         if (w == 0) {
             const int ci[3] = {(int)(c % a.g.nc[0]), (int)((c / a.g.nc[0]) % a.g.nc[1]),
                                (int)(c / ((int64_t)a.g.nc[0] * a.g.nc[1]))};
-            int lo[3], hi[3];
+            int lo[3], sx, sy, nst, centre;
+            if (image_placed) {
+                lo[0] = ci[0] - 1; lo[1] = ci[1] - 1; lo[2] = ci[2] - 1;
+                sx = sy = 3;
+                nst = 27;
+                centre = 13;
+            } else {
+                int hi[3];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                if (a.g.per[d] && a.g.nc[d] < 3) { lo[d] = 0; hi[d] = a.g.nc[d] - 1; }
-                else if (a.g.per[d]) { lo[d] = ci[d] - 1; hi[d] = ci[d] + 1; }
-                else { lo[d] = max(ci[d] - 1, 0); hi[d] = min(ci[d] + 1, a.g.nc[d] - 1); }
+                for (int d = 0; d < 3; ++d) {
+                    if (a.g.per[d] && a.g.nc[d] < 3) { lo[d] = 0; hi[d] = a.g.nc[d] - 1; }
+                    else if (a.g.per[d]) { lo[d] = ci[d] - 1; hi[d] = ci[d] + 1; }
+                    else { lo[d] = max(ci[d] - 1, 0); hi[d] = min(ci[d] + 1, a.g.nc[d] - 1); }
+                }
+                sx = hi[0] - lo[0] + 1;
+                sy = hi[1] - lo[1] + 1;
+                nst = sx * sy * (hi[2] - lo[2] + 1);   // at most 27 cells
+                centre = ((ci[2] - lo[2]) * sy + (ci[1] - lo[1])) * sx + (ci[0] - lo[0]);
             }
-            const int sx = hi[0] - lo[0] + 1, sy = hi[1] - lo[1] + 1, sz = hi[2] - lo[2] + 1;
-            const int nst = sx * sy * sz;   // at most 27 cells
-            const int centre = ((ci[2] - lo[2]) * sy + (ci[1] - lo[1])) * sx + (ci[0] - lo[0]);
             int my_p0 = 0, my_len = 0;
             if (lane < nst) {
                 const int x = lo[0] + lane % sx, y = lo[1] + (lane / sx) % sy, z = lo[2] + lane / (sx * sy);
+                const int xyz[3] = {x, y, z};
+                bool inside = true;   // false only past a non-periodic face
+#pragma unroll
+                for (int d = 0; d < 3; ++d) inside = inside && (a.g.per[d] || (xyz[d] >= 0 && xyz[d] < a.g.nc[d]));
                 const int wx = wrap_cell(x, a.g.nc[0]), wy = wrap_cell(y, a.g.nc[1]), wz = wrap_cell(z, a.g.nc[2]);
                 const int cc = (wz * a.g.nc[1] + wy) * a.g.nc[0] + wx;
-                my_p0 = a.cell_start[cc];
-                my_len = a.cell_start[cc + 1] - my_p0;
+                if (inside) {
+                    my_p0 = a.cell_start[cc];
+                    my_len = a.cell_start[cc + 1] - my_p0;
+                }
+                if (image_placed) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) sm.soff[lane][k] = inside ? a.cell_sub[(int64_t)cc * 8 + k] : 0;
+                    sm.soff[lane][8] = my_len;
+                }
                 // x, y, z are unwrapped: a cell across a periodic face sits one box length away
                 sm.org[lane] = make_float4((float)(x - ci[0]) * a.wf[0], (float)(y - ci[1]) * a.wf[1],
                                            (float)(z - ci[2]) * a.wf[2], 0.f);
@@ -394,21 +443,58 @@ __device__ __forceinline__ void lists_body(const ListArgs &args, int64_t blk, in
             pf.x += o.x; pf.y += o.y; pf.z += o.z;
             return pf;
         };
-        const bool staged = ((total + 63) & ~63) <= STAGE_MAX;
+        // staged when the candidates and a far one after them fit
+        const bool staged = ((total + 64) & ~63) <= STAGE_MAX;
         if (staged) {   // a warp per stencil cell, a lane per atom
             for (int cl = w; cl < nst; cl += LB_WARPS) {
                 const int o = sm.off[cl], p0 = sm.p0[cl], len = (cl + 1 < nst ? sm.off[cl + 1] : total) - o;
                 for (int e = lane; e < len; e += 32) {
                     sm.p[o + e] = placed(cl, a.cposf[p0 + e]);
-                    sm.k[o + e] = a.ckey[p0 + e];
                     sm.j[o + e] = a.cell_atoms[p0 + e];
                 }
             }
-            for (int f = total + threadIdx.x; f < ((total + 63) & ~63); f += blockDim.x) sm.p[f] = far;
+            for (int f = total + threadIdx.x; f < ((total + 64) & ~63); f += blockDim.x) sm.p[f] = far;
+        }
+        // the sub-cell walks: for sub-cell position sb = (bz, by, bx) of the centre cell, the
+        // sub-cells (X, Y, Z) in [b - 2, b + 2] per axis (in sub-cell units from the centre
+        // cell's corner), z-major; sub-cell X lies in stencil cell X >> 1 (floor), half X & 1
+        bool walks = staged && image_placed;
+        if (walks) {
+            for (int sb = w; sb < 8; sb += LB_WARPS) {
+                const int bx = sb & 1, by = (sb >> 1) & 1, bz = sb >> 2;
+                const int X = bx - 2 + lane % 5, Y = by - 2 + lane / 5;   // lanes 0..24: one z-layer
+                int run = 0;
+                for (int Z = bz - 2; Z <= bz + 2; ++Z) {
+                    int start = 0, len = 0;
+                    if (lane < 25) {
+                        const int cl = (((Z >> 1) + 1) * 3 + ((Y >> 1) + 1)) * 3 + ((X >> 1) + 1);
+                        const int h = ((Z & 1) << 2) | ((Y & 1) << 1) | (X & 1);
+                        start = sm.off[cl] + sm.soff[cl][h];
+                        len = sm.soff[cl][h + 1] - sm.soff[cl][h];
+                    }
+                    int incl = len;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += t;
+                    }
+                    const int o = run + incl - len;
+                    for (int t = 0; t < len; ++t)
+                        if (o + t < WALK_MAX) sm.walk[sb][o + t] = (uint16_t)(start + t);
+                    run += __shfl_sync(0xffffffffu, incl, 31);
+                }
+                // padded to whole pairs of chunks with the far candidate at index total
+                for (int t = run + lane; t < ((run + 63) & ~63) && t < WALK_MAX; t += 32) sm.walk[sb][t] = (uint16_t)total;
+                if (lane == 0) sm.wlen[sb] = run;
+            }
         }
         __syncthreads();
-        // stencil cell of candidate f of the walk: the last one whose offset is <= f (empty
-        // cells share the offset of the cell after them)
+        if (walks) {
+#pragma unroll
+            for (int sb = 0; sb < 8; ++sb) walks = walks && ((sm.wlen[sb] + 63) & ~63) <= WALK_MAX;
+        }
+        // stencil cell of candidate f: the last one whose offset is <= f (empty cells share the
+        // offset of the cell after them)
         auto cell_of = [&](int f) {
             int cl = 0;
             while (cl + 1 < nst && sm.off[cl + 1] <= f) ++cl;
@@ -419,32 +505,42 @@ __device__ __forceinline__ void lists_body(const ListArgs &args, int64_t blk, in
         for (int q = w; q < nc0; q += LB_WARPS) {
             const int64_t i = a.cell_atoms[c0 + q];
             const float4 pfi = a.cposf[c0 + q];
-            if (staged) {
+            auto jof = [&](int f) { return sm.j[f]; };
+            if (walks) {
+                const int sb = sub_of(pfi);
+                const uint16_t *wk = sm.walk[sb];
                 list_atom(
-                    a, i, pfi, self0 + q, sm.key[w], lane, total, image_placed, [&](int f) { return sm.p[f]; },
-                    [&](int f) { return sm.j[f]; },
-                    [&](int f, int &jx, int &oj) {
-                        jx = sm.j[f];
-                        oj = (int)(sm.k[f] & 0x3FFFFFFFu);
-                    });
+                    a, i, pfi, self0 + q, sm.key[w], lane, sm.wlen[sb], total, true,
+                    [&](int fw, int &f, float4 &pf) {
+                        f = wk[fw];
+                        pf = sm.p[f];
+                    },
+                    jof);
+            } else if (staged) {
+                list_atom(
+                    a, i, pfi, self0 + q, sm.key[w], lane, total, total, image_placed,
+                    [&](int fw, int &f, float4 &pf) {
+                        f = fw;
+                        pf = sm.p[fw];
+                    },
+                    jof);
             } else {
                 auto position_of = [&](int f) {
                     const int cl = cell_of(f);
                     return sm.p0[cl] + (f - sm.off[cl]);
                 };
                 list_atom(
-                    a, i, pfi, self0 + q, sm.key[w], lane, total, image_placed,
-                    [&](int f) {
-                        if (f >= total) return far;
-                        const int cl = cell_of(f);
-                        return placed(cl, a.cposf[sm.p0[cl] + (f - sm.off[cl])]);
+                    a, i, pfi, self0 + q, sm.key[w], lane, total, total, image_placed,
+                    [&](int fw, int &f, float4 &pf) {
+                        f = fw;
+                        if (fw >= total) {
+                            pf = far;
+                            return;
+                        }
+                        const int cl = cell_of(fw);
+                        pf = placed(cl, a.cposf[sm.p0[cl] + (fw - sm.off[cl])]);
                     },
-                    [&](int f) { return a.cell_atoms[position_of(f)]; },
-                    [&](int f, int &jx, int &oj) {
-                        const int p = position_of(f);
-                        jx = a.cell_atoms[p];
-                        oj = (int)(a.ckey[p] & 0x3FFFFFFFu);
-                    });
+                    [&](int f) { return a.cell_atoms[position_of(f)]; });
             }
         }
         __syncthreads();   // the next cell reuses the staging
@@ -458,13 +554,13 @@ __device__ __forceinline__ void ld_v8(const int32_t *p, int *r) {
         : "l"(p));
 }
 
-// Slot of caller index oi in [lo, hi) of a list row (32-byte aligned rows), or -1.  The row is
+// Slot of atom index ai in [lo, hi) of a list row (32-byte aligned rows), or -1.  The row is
 // read from lo & ~7 in rounds of 32 entries, four independent 32-byte loads each (the 8-entry
-// pieces that start at or past hi are not read).  A caller index appears at most once in a
-// row's entries [0, seg.w), and the entries before lo belong to other segments, so the first
-// match below hi is the slot; a match at or past hi (a stale entry past the row's end, or
-// another segment) counts as none.
-__device__ __forceinline__ int find_slot(const int32_t *__restrict__ row, int lo, int hi, int oi) {
+// pieces that start at or past hi are not read).  An atom appears at most once in a row's
+// entries [0, seg.w), and the entries before lo belong to other segments, so the first match
+// below hi is the slot; a match at or past hi (a stale entry past the row's end, or another
+// segment) counts as none.
+__device__ __forceinline__ int find_slot(const int32_t *__restrict__ row, int lo, int hi, int ai) {
     int found = -1;
     for (int b = lo & ~7; b < hi && found < 0; b += 32) {
         int v[32];
@@ -478,7 +574,7 @@ __device__ __forceinline__ int find_slot(const int32_t *__restrict__ row, int lo
             }
         }
 #pragma unroll
-        for (int e = 31; e >= 0; --e) found = v[e] == oi ? b + e : found;   // descending: the lowest match is kept
+        for (int e = 31; e >= 0; --e) found = v[e] == ai ? b + e : found;   // descending: the lowest match is kept
         if (found >= hi) found = -1;
     }
     return found;
@@ -492,7 +588,7 @@ struct RevSmem {
 
 // Warp per atom i.  The entries j = nbr[i][s] with j > i are compacted (ballot) into the warp's
 // pair list; each lane then takes one pair, reads j's segment bounds for the kind of slot s,
-// finds the slot t of i in that segment of j's caller-index row and writes both reverse slots,
+// finds the slot t of i in that segment of j's list row and writes both reverse slots,
 // rev[i][s] = t and rev[j][t] = s (the entries with j < i are written by j's warp): one search
 // per unordered pair.  The lists are symmetric and so is each pair's segment kind (the cutoff
 // test gives the same result for (i, j) and (j, i)), so i sits in the segment of j's list for
@@ -505,7 +601,6 @@ __device__ __forceinline__ void rev_body(const RevArgs &args, int64_t blk, int64
     const unsigned lt = (1u << lane) - 1u;
     for (int64_t i = blk * REV_WARPS + w; i < a.n; i += nblk * REV_WARPS) {
         const int4 sg = a.seg[i];
-        const int oi = a.orig[i];
         const int ti = a.species[i];
         int cnt = 0;
         for (int s0 = 0; s0 < sg.w; s0 += 32) {
@@ -526,7 +621,7 @@ __device__ __forceinline__ void rev_body(const RevArgs &args, int64_t blk, int64
             const int sgi = (s < sg.y ? 0 : 2) + ti;
             const int lo = sgi == 0 ? 0 : sgi == 1 ? sj.x : sgi == 2 ? sj.y : sj.z;
             const int hi = sgi == 0 ? sj.x : sgi == 1 ? sj.y : sgi == 2 ? sj.z : sj.w;
-            const int t = find_slot(a.nbr_orig + (int64_t)j * a.capr, lo, hi, oi);
+            const int t = find_slot(a.nbr + (int64_t)j * a.capr, lo, hi, (int)i);
             if (t < 0) {
                 atomicOr(a.status, ST_NBR_OVERFLOW);
                 a.rev[i * a.capr + s] = 0;
@@ -646,12 +741,13 @@ RebuildPlan rebuild_plan(Sys &s, bool conditional) {
     r.pos = s.pos; r.posf = s.posf; r.species = s.species; r.orig = s.orig; r.n = n; r.g = g;
     r.ncell = s.cells.ncell; r.count = s.cells.count; r.start = s.cells.start; r.fill = s.cells.fill;
     r.atoms = s.cells.atoms; r.of = s.cells.of; r.cposf = s.cells.posf; r.ckey = s.cells.key;
+    r.sub = s.cells.sub;
     r.posref = s.posref; r.builds = s.d_builds; r.rebuild = s.rebuild; r.flag = flag;
     ListArgs &la = pl.lists;
-    la.pos = s.pos; la.species = s.species; la.orig = s.orig;
-    la.cell_start = s.cells.start; la.cell_atoms = s.cells.atoms; la.cell_of = s.cells.of;
-    la.cposf = s.cells.posf; la.ckey = s.cells.key; la.nbr_orig = s.nbr_orig;
-    la.n = n; la.cap = s.cap; la.cap_ang = s.cap_ang; la.capr = nbr_orig_stride(s.cap);
+    la.pos = s.pos;
+    la.cell_start = s.cells.start; la.cell_atoms = s.cells.atoms; la.cell_sub = s.cells.sub;
+    la.cposf = s.cells.posf;
+    la.n = n; la.cap = s.cap; la.cap_ang = s.cap_ang; la.capr = nbr_stride(s.cap);
     la.cut_r2 = s.cut_r2; la.cut_a2 = s.cut_a2;
     // Band of the FP32 pre-test.  Each FP32 separation component is (u_j + o) - u_i with
     // |u| <= 2w (positions relative to their cells' corners, rounded once from FP64) and o a
@@ -681,8 +777,8 @@ RebuildPlan rebuild_plan(Sys &s, bool conditional) {
     la.bd = s.boxd; la.bf = s.boxf; la.g = g;
     la.nbr = s.nbr; la.seg = s.seg; la.status = s.status; la.flag = flag;
     RevArgs &ra = pl.rev;
-    ra.species = s.species; ra.orig = s.orig; ra.nbr = s.nbr; ra.nbr_orig = s.nbr_orig; ra.seg = s.seg;
-    ra.n = n; ra.cap = s.cap; ra.capr = nbr_orig_stride(s.cap);
+    ra.species = s.species; ra.nbr = s.nbr; ra.seg = s.seg;
+    ra.n = n; ra.cap = s.cap; ra.capr = nbr_stride(s.cap);
     ra.rev = s.rev; ra.status = s.status; ra.flag = flag;
     // grids are capped (grid-stride loops): when no rebuild is due every kernel returns at once
     int dev = 0, sms = 148;

@@ -24,7 +24,8 @@ struct BinArgs {
     int64_t n;
     GridArgs g;
     int ncell;
-    int *count, *start, *fill, *atoms, *of;
+    int *count, *start, *fill, *atoms, *of;   // of: cell << 3 | sub-cell of each atom
+    int *sub;              // [ncell][8] first position of each sub-cell, relative to its cell's start
     float4 *cposf;
     uint32_t *ckey;
     double4 *posref;
@@ -35,11 +36,8 @@ struct BinArgs {
 
 struct ListArgs {
     const double4 *pos;
-    const int32_t *species, *orig;
-    const int *cell_start, *cell_atoms, *cell_of;
-    const float4 *cposf;      // cell-ordered FP32 positions relative to each cell's corner
-    const uint32_t *ckey;     // cell-ordered (species << 30 | caller index)
-    int32_t *nbr_orig;        // [n][capr] caller index of each list entry (atom-major rows of capr)
+    const int *cell_start, *cell_atoms, *cell_sub;
+    const float4 *cposf;      // cell-ordered FP32 positions relative to each cell's corner, species and sub-cell bits in w
     int64_t n;
     int cap, cap_ang, capr;
     double cut_r2, cut_a2;
@@ -55,8 +53,8 @@ struct ListArgs {
 };
 
 struct RevArgs {
-    const int32_t *species, *orig;
-    const int32_t *nbr, *nbr_orig;   // nbr_orig atom-major [n][capr], capr a multiple of 8 (32-byte rows)
+    const int32_t *species;
+    const int32_t *nbr;   // atom-major [n][capr], capr a multiple of 8 (32-byte rows)
     const int4 *seg;
     int cap, capr;
     int64_t n;

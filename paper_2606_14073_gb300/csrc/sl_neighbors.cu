@@ -66,32 +66,52 @@ __device__ __forceinline__ void bin_body(const BinArgs &r, int64_t blk, int64_t 
     }
 }
 
-// Exclusive scan of count[0..m) into start[0..m] by one whole block (s_part: blockDim.x ints).
-__device__ __forceinline__ void scan_body(const BinArgs &r, int *s_part, int &s_carry) {
+// Exclusive scan of count[0..m) into start[0..m] by one whole block (s_part: 32 ints): each
+// thread sums a contiguous chunk (a multiple of 4 cells, read 16 bytes at a time), the chunk
+// sums are scanned across the block through warp shuffles, and each thread writes its chunk's
+// starts.
+__device__ __forceinline__ void scan_body(const BinArgs &r, int *s_part) {
     if (r.flag && *r.flag == 0) return;
     const int *__restrict__ count = r.count;
     int *__restrict__ start = r.start;
-    const int m = r.ncell;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (int base = 0; base < m; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        const int v = i < m ? count[i] : 0;
-        s_part[threadIdx.x] = v;
-        __syncthreads();
-        for (int off = 1; off < blockDim.x; off <<= 1) {
-            const int t = threadIdx.x >= off ? s_part[threadIdx.x - off] : 0;
-            __syncthreads();
-            s_part[threadIdx.x] += t;
-            __syncthreads();
+    const int m = r.ncell, T = blockDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int chunk = ((m + T - 1) / T + 3) & ~3;
+    const int b0 = min((int)threadIdx.x * chunk, m), b1 = min(b0 + chunk, m);
+    int sum = 0;
+    for (int k = b0; k < b1; k += 4) {
+        if (k + 4 <= b1) {
+            const int4 v = *reinterpret_cast<const int4 *>(count + k);
+            sum += v.x + v.y + v.z + v.w;
+        } else {
+            for (int kk = k; kk < b1; ++kk) sum += count[kk];
         }
-        if (i < m) start[i] = s_carry + s_part[threadIdx.x] - v;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) s_carry += s_part[threadIdx.x];
-        __syncthreads();
     }
-    if (threadIdx.x == 0) start[m] = s_carry;
-    __syncthreads();   // the block's next work item reuses s_part and s_carry
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_part[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = T >> 5;
+        int v = lane < nw ? s_part[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane < nw) s_part[lane] = v;   // inclusive warp totals
+    }
+    __syncthreads();
+    int run = (wid > 0 ? s_part[wid - 1] : 0) + incl - sum;
+    for (int k = b0; k < b1; ++k) {
+        start[k] = run;
+        run += count[k];
+    }
+    if (threadIdx.x == T - 1) start[m] = s_part[(T >> 5) - 1];
+    __syncthreads();   // the block's next work item reuses s_part
 }
 
 // Atoms into their cells, with a cell-ordered copy of the key (species << 30 | caller index)
@@ -673,9 +693,8 @@ __global__ void k_bin(const BinArgs *__restrict__ tab, WorkMap m, const int *qui
 template <bool LOOP>
 __global__ void k_scan(const BinArgs *__restrict__ tab, WorkMap m, const int *quick) {
     if (quick && *quick == 0) return;
-    __shared__ int s_part[1024];
-    __shared__ int s_carry;
-    rebuild_items<LOOP>(tab, m, [&](const BinArgs &r, int64_t, int64_t) { scan_body(r, s_part, s_carry); });
+    __shared__ int s_part[32];
+    rebuild_items<LOOP>(tab, m, [&](const BinArgs &r, int64_t, int64_t) { scan_body(r, s_part); });
 }
 template <bool LOOP>
 __global__ void k_scatter(const BinArgs *__restrict__ tab, WorkMap m, const int *quick) {

@@ -106,6 +106,37 @@ def test_neighbor_lists_bit_exact_with_atoms_far_outside_a_free_axis(params):
     s.destroy()
 
 
+def mixed_cells_box(seed=73):
+    """3 x 6 x 6 B20 cells, periodic: 14.1 A along x holds 2 binning cells (the list build's
+    whole-axis walk with the minimum image), 28.2 A along y and z hold 4 (placed images)."""
+    pos, species, box = W.b20_lattice(3, 6, 6)
+    rng = np.random.default_rng(seed)
+    pos = W.wrap(pos + rng.normal(0.0, 0.05, pos.shape), box, np.ones(3, np.int32))
+    return pos, W.random_unit_vectors(rng, len(pos)), species, box, np.ones(3, np.int32)
+
+
+def free_cluster():
+    """A 3 x 3 x 3-cell B20 fragment with free boundaries in a 100 A binning box."""
+    return W.isolated_cluster(3, seed=74)
+
+
+@pytest.mark.parametrize("make", [mixed_cells_box, free_cluster], ids=["mixed_cells_3x6x6", "free_cluster_3"])
+def test_lists_and_fp64_forces_on_odd_grids(params, model, make):
+    pos, spin, species, box, per = make()
+    s = S.System(pos, spin, box, per, species, params)
+    st = s.get_state()
+    rad, ang = s.get_neighbors()
+    ref_r = O.neighbors(st["positions"], box, per, 7.0, method=0)
+    ref_a = O.neighbors(st["positions"], box, per, 5.0, method=0)
+    assert all(np.array_equal(a, b) for a, b in zip(rad, ref_r))
+    assert all(np.array_equal(a, b) for a, b in zip(ang, ref_a))
+    r = s.energy_forces_fields()
+    ref = O.evaluate(model, st["positions"], st["spins"], species, box, per)
+    assert maxrel(r["F"], ref["F"]) <= FP64_TOL and maxrel(r["H"], ref["H"]) <= FP64_TOL
+    assert maxrel(r["W"], ref["W"]) <= FP64_TOL
+    s.destroy()
+
+
 @pytest.mark.parametrize("name", list(WORKLOADS))
 def test_descriptors_fp64(params, model, name):
     wl = WORKLOADS[name]()

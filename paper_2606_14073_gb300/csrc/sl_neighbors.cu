@@ -11,9 +11,11 @@
 // cutoff; only pairs within a margin of it take the exact FP64 test.
 // Each list is split in four segments -- angular candidates (d2 < (rc_ang+skin)^2)
 // of neighbour species 0 and 1, then the remaining radial candidates of species
-// 0 and 1 -- and each segment is in the order of the stencil walk (cells z-major,
-// each cell's atoms by caller index), so every per-atom sum runs in an order set by
-// the positions and caller indices alone, never by the internal atom order.
+// 0 and 1 -- and each segment is in the order of the list build's walk (the half-width
+// sub-cells around the atom z-major, or the whole stencil's cells z-major in a box with
+// fewer than 3 cells along a periodic axis; each sub-cell's or cell's atoms by species,
+// then caller index), so every per-atom sum runs in an order set by the positions and caller indices
+// alone, never by the internal atom order.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>

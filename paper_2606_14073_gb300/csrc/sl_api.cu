@@ -141,7 +141,7 @@ void fill_params(sl::NepDev<R> &P, const sl_nep_params *p) {
 
 void free_sys(sl::Sys &s) {
     void *ptrs[] = {s.pos, s.vel, s.spin, s.spin_prev, s.F, s.H, s.posref, s.posf, s.spinf, s.species, s.orig,
-                    s.inv, s.nbr, s.rev, s.cells.posf, s.cells.key, s.seg, s.cells.count, s.cells.start, s.cells.fill, s.cells.atoms,
+                    s.inv, s.nbr, s.rev, s.nbr_hash, s.cells.posf, s.cells.key, s.seg, s.cells.count, s.cells.start, s.cells.fill, s.cells.atoms,
                     s.cells.of, s.cells.sub, s.q, s.bsum, s.fp, s.ei, s.pairs, s.clj, s.cls, s.cnt, s.cmask, s.fown, s.gii,
                     s.wpart, s.Fo, s.Ho,
                     s.status, s.rebuild, s.d_step, s.d_par, s.red, s.snap, s.d_builds,
@@ -556,6 +556,7 @@ int sl_create_system(const double *positions, const double *spins, const double 
         (rc = dalloc(&s.posref, N)) || (rc = dalloc(&s.posf, N)) || (rc = dalloc(&s.spinf, N)) ||
         (rc = dalloc(&s.species, N)) || (rc = dalloc(&s.orig, N)) || (rc = dalloc(&s.inv, N)) ||
         (rc = dalloc(&s.nbr, N * sl::nbr_stride(s.cap))) || (rc = dalloc(&s.rev, N * sl::nbr_stride(s.cap))) ||
+        (rc = dalloc(&s.nbr_hash, N * sl::nbr_stride(s.cap))) ||
         (rc = dalloc(&s.cells.posf, N)) || (rc = dalloc(&s.cells.key, N)) || (rc = dalloc(&s.seg, N)) ||
         (rc = dalloc(&s.cells.count, (size_t)s.cells.ncell)) || (rc = dalloc(&s.cells.start, (size_t)s.cells.ncell + 1)) ||
         (rc = dalloc(&s.cells.fill, (size_t)s.cells.ncell)) || (rc = dalloc(&s.cells.atoms, N)) ||
@@ -1273,7 +1274,7 @@ int64_t sl_estimate_device_bytes(int64_t n, const sl_options *opt_in) {
     const int64_t cap = opt.nbr_cap_rad, ca = opt.nbr_cap_ang;
     int64_t per = 7 * 32 + 2 * 16                      // state (double4) and FP32 copies
                   + 3 * 4 + 4 + 16 + 16 + 4            // species, caller index maps, list segments, cell copies
-                  + 5 * sl::nbr_stride((int)cap)     // candidate lists, reverse slots (1 byte)
+                  + 6 * sl::nbr_stride((int)cap)     // candidate lists, reverse slots and index hashes (1 byte each)
                   + 6 * (ca + cap) + 16                // compact rows, counts
                   + 4 * ((cap + 31) / 32)              // in-cutoff slot mask
                   + R * (2 * sl::DIM + sl::NBREC + 1 + 9) // q, Fp, angular sums, E_i, virial parts

@@ -23,7 +23,7 @@ struct Eval2Args {
     const v4<R> *pos, *spin;
     const int32_t *nbr;   // [n][capr] candidate list of atom i (internal indices), atom-major
     const uint8_t *rev;   // [n][capr] rev[i][s] = slot of i in the list of nbr[i][s]
-    int capr;             // row stride of nbr and rev: cap rounded up to a multiple of 8
+    int capr;             // row stride of nbr and rev: cap rounded up to a multiple of 32
     const int4 *seg;
     int64_t n, n_fe;
     BoxDev<R> box;

@@ -111,9 +111,10 @@ struct Sys {
     int64_t n_fe = 0;          // atoms [0, n_fe) are species 0
 
     // neighbour lists, atom-major rows of nbr_stride(cap) entries: nbr (internal index of
-    // each candidate) and rev (slot of the atom in its candidate's list; cap <= 256, one byte)
+    // each candidate), rev (slot of the atom in its candidate's list; cap <= 256, one byte) and
+    // nbr_hash (an 8-bit hash of each candidate's index: the reverse-slot search's filter)
     int32_t *nbr = nullptr;
-    uint8_t *rev = nullptr;
+    uint8_t *rev = nullptr, *nbr_hash = nullptr;
     int4 *seg = nullptr;       // per atom: ends of (ang t0, ang t1, rad t0, rad t1)
     Cells cells;
 
@@ -215,7 +216,7 @@ void solo_free(Sys &s);
 // launchers (sl_neighbors.cu)
 // row stride of the atom-major caller-index copy of the lists: cap rounded up to a multiple
 // of 4 entries, so every row starts on a 16-byte boundary
-inline int nbr_stride(int cap) { return (cap + 7) & ~7; }   // rows of 32-byte multiples
+inline int nbr_stride(int cap) { return (cap + 31) & ~31; }   // byte rows of 32-byte multiples
 void nbr_setup(Sys &s);
 void launch_rebuild(Sys &s, bool conditional);
 // sl_eval2.cu: the system's evaluation at the state (with the virial parts when asked for), or

@@ -280,6 +280,10 @@ __device__ __forceinline__ void cellsort_body(const BinArgs &r, int64_t blk, int
 
 __device__ __forceinline__ int wrap_cell(int x, int nc) { return x < 0 ? x + nc : (x >= nc ? x - nc : x); }
 
+// 8-bit hash of an atom index (the top byte of a multiplicative hash), stored beside each list
+// entry so that the reverse-slot search reads one byte per entry
+__device__ __forceinline__ uint32_t index_hash8(int x) { return ((uint32_t)x * 0x9E3779B1u) >> 24; }
+
 constexpr int SORT_MAX = 256;
 constexpr int STAGE_MAX = 1024;   // staged candidates; a larger stencil is walked in global memory
 constexpr int WALK_MAX = 640;     // a sub-cell walk's staged indices (a longer one takes the whole stencil)
@@ -373,7 +377,11 @@ __device__ __forceinline__ void list_atom(const ListArgs &a, int64_t i, float4 p
             if (sg == (unsigned)t) pos = run[t] + __popc(b & lt);
             run[t] += __popc(b);
         }
-        if (e < mm && pos < a.cap) a.nbr[i * a.capr + pos] = jof((int)(k & 0x3FFFFFFFu));   // atom-major rows
+        if (e < mm && pos < a.cap) {
+            const int jx = jof((int)(k & 0x3FFFFFFFu));
+            a.nbr[i * a.capr + pos] = jx;   // atom-major rows
+            a.hash[i * a.capr + pos] = (uint8_t)index_hash8(jx);
+        }
     }
     if (lane == 0) {
         a.seg[i] = make_int4(min(ends_all[0], a.cap), min(ends_all[1], a.cap), min(ends_all[2], a.cap),
@@ -569,37 +577,53 @@ __device__ __forceinline__ void lists_body(const ListArgs &args, int64_t blk, in
     }
 }
 
-// Eight entries of a list row at p (32-byte aligned) in one 256-bit load.
-__device__ __forceinline__ void ld_v8(const int32_t *p, int *r) {
+// 32 bytes of a row at p (32-byte aligned) in one 256-bit load.
+__device__ __forceinline__ void ld_v8u(const uint8_t *p, uint32_t *r) {
     asm("ld.global.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
         : "l"(p));
 }
 
-// Slot of atom index ai in [lo, hi) of a list row (32-byte aligned rows), or -1.  The row is
-// read from lo & ~7 in rounds of 32 entries, four independent 32-byte loads each (the 8-entry
-// pieces that start at or past hi are not read).  An atom appears at most once in a row's
-// entries [0, seg.w), and the entries before lo belong to other segments, so the first match
-// below hi is the slot; a match at or past hi (a stale entry past the row's end, or another
-// segment) counts as none.
-__device__ __forceinline__ int find_slot(const int32_t *__restrict__ row, int lo, int hi, int ai) {
-    int found = -1;
-    for (int b = lo & ~7; b < hi && found < 0; b += 32) {
-        int v[32];
+// Bit k (k = 0..3) set where byte k of x is zero.  Adding 0x7F to the low seven bits of a
+// byte sets its top bit unless they are all zero (no carry leaves the byte); with the byte's
+// own top bit that marks the nonzero bytes.  The four top bits are then gathered by one
+// multiplication whose partial products fall on distinct bits.
+__device__ __forceinline__ uint32_t zero_bytes4(uint32_t x) {
+    const uint32_t hb = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);   // 0x80 in each zero byte
+    return (((hb >> 7) * 0x00204081u) >> 21) & 0xFu;
+}
+
+// Slot of atom index ai in [lo, hi) of a list row, or -1.  The row's hash bytes are read from
+// lo & ~31 in windows of 64 (two 32-byte loads), and the entries whose hash equals ai's are
+// the candidates.  An atom appears at most once in a row's entries [0, seg.w), and when the
+// search runs the atom is in the segment unless a list was cut at its capacity (which the list
+// build has already reported): so a window that holds the whole segment and a single candidate
+// gives the slot; otherwise each candidate's entry is compared, in order.
+__device__ __forceinline__ int find_slot(const int32_t *__restrict__ row, const uint8_t *__restrict__ hrow, int lo,
+                                         int hi, int ai) {
+    const uint32_t hh = index_hash8(ai) * 0x01010101u;
+    for (int b = lo & ~31; b < hi; b += 64) {
+        uint32_t w[16];
+        ld_v8u(hrow + b, w);
+        if (b + 32 < hi) {
+            ld_v8u(hrow + b + 32, w + 8);
+        } else {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (b + 8 * u < hi) {
-                ld_v8(row + b + 8 * u, v + 8 * u);
-            } else {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) v[8 * u + c] = -1;
-            }
+            for (int q = 8; q < 16; ++q) w[q] = ~hh;   // no byte matches
         }
+        uint64_t m = 0;
 #pragma unroll
-        for (int e = 31; e >= 0; --e) found = v[e] == ai ? b + e : found;   // descending: the lowest match is kept
-        if (found >= hi) found = -1;
+        for (int q = 0; q < 16; ++q) m |= (uint64_t)zero_bytes4(w[q] ^ hh) << (4 * q);
+        const int l0 = max(lo - b, 0), h0 = min(hi - b, 64);
+        m &= (h0 >= 64 ? ~0ull : ((1ull << h0) - 1ull)) & ~((1ull << l0) - 1ull);
+        if (hi <= b + 64 && __popcll(m) == 1) return b + __ffsll(m) - 1;
+        while (m) {
+            const int k = __ffsll(m) - 1;
+            m &= m - 1;
+            if (row[b + k] == ai) return b + k;
+        }
     }
-    return found;
+    return -1;
 }
 
 constexpr int REV_WARPS = 4;
@@ -610,7 +634,8 @@ struct RevSmem {
 
 // Warp per atom i.  The entries j = nbr[i][s] with j > i are compacted (ballot) into the warp's
 // pair list; each lane then takes one pair, reads j's segment bounds for the kind of slot s,
-// finds the slot t of i in that segment of j's list row and writes both reverse slots,
+// finds the slot t of i in that segment of j's list row (through the row's hash bytes) and
+// writes both reverse slots,
 // rev[i][s] = t and rev[j][t] = s (the entries with j < i are written by j's warp): one search
 // per unordered pair.  The lists are symmetric and so is each pair's segment kind (the cutoff
 // test gives the same result for (i, j) and (j, i)), so i sits in the segment of j's list for
@@ -643,7 +668,7 @@ __device__ __forceinline__ void rev_body(const RevArgs &args, int64_t blk, int64
             const int sgi = (s < sg.y ? 0 : 2) + ti;
             const int lo = sgi == 0 ? 0 : sgi == 1 ? sj.x : sgi == 2 ? sj.y : sj.z;
             const int hi = sgi == 0 ? sj.x : sgi == 1 ? sj.y : sgi == 2 ? sj.z : sj.w;
-            const int t = find_slot(a.nbr + (int64_t)j * a.capr, lo, hi, (int)i);
+            const int t = find_slot(a.nbr + (int64_t)j * a.capr, a.hash + (int64_t)j * a.capr, lo, hi, (int)i);
             if (t < 0) {
                 atomicOr(a.status, ST_NBR_OVERFLOW);
                 a.rev[i * a.capr + s] = 0;
@@ -796,9 +821,9 @@ RebuildPlan rebuild_plan(Sys &s, bool conditional) {
         for (int a = 0; a < 3; ++a) la.wf[a] = (float)g.w[a];
     }
     la.bd = s.boxd; la.bf = s.boxf; la.g = g;
-    la.nbr = s.nbr; la.seg = s.seg; la.status = s.status; la.flag = flag;
+    la.nbr = s.nbr; la.hash = s.nbr_hash; la.seg = s.seg; la.status = s.status; la.flag = flag;
     RevArgs &ra = pl.rev;
-    ra.species = s.species; ra.nbr = s.nbr; ra.seg = s.seg;
+    ra.species = s.species; ra.nbr = s.nbr; ra.hash = s.nbr_hash; ra.seg = s.seg;
     ra.n = n; ra.cap = s.cap; ra.capr = nbr_stride(s.cap);
     ra.rev = s.rev; ra.status = s.status; ra.flag = flag;
     // grids are capped (grid-stride loops): when no rebuild is due every kernel returns at once

@@ -47,6 +47,7 @@ struct ListArgs {
     BoxDev<float> bf;
     GridArgs g;
     int32_t *nbr;             // [n][capr] candidate lists, atom-major
+    uint8_t *hash;            // [n][capr] 8-bit hash of each entry (index_hash8)
     int4 *seg;
     int *status;
     const int *flag;
@@ -54,7 +55,8 @@ struct ListArgs {
 
 struct RevArgs {
     const int32_t *species;
-    const int32_t *nbr;   // atom-major [n][capr], capr a multiple of 8 (32-byte rows)
+    const int32_t *nbr;   // atom-major [n][capr], capr a multiple of 32
+    const uint8_t *hash;  // [n][capr] 8-bit hash of each entry (32-byte rows)
     const int4 *seg;
     int cap, capr;
     int64_t n;

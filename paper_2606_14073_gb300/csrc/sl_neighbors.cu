@@ -46,8 +46,10 @@ __device__ __forceinline__ double exact_d2(double xi, double yi, double zi, doub
 }
 
 // Cell of each atom and its half-width sub-cell inside it (bit 0 x, 1 y, 2 z): the sub-cell
-// index along an axis is floor(2 x / w) clamped to [0, 2 nc), and the cell is half of it, the
-// same cell as floor(x / w) clamped (2 x / w is the rounded x / w doubled exactly).
+// index along an axis is floor(x * 2/w) clamped to [0, 2 nc), and the cell is half of it.  A
+// position within a rounding of a boundary may land on either side; the cells are at least
+// (1 + 1e-9) times the list cutoff wide, far more than that, so the stencil still holds every
+// pair.
 __device__ __forceinline__ void bin_body(const BinArgs &r, int64_t blk, int64_t nblk) {
     if (r.flag && *r.flag == 0) return;
     const GridArgs &g = r.g;
@@ -58,7 +60,7 @@ __device__ __forceinline__ void bin_body(const BinArgs &r, int64_t blk, int64_t 
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             // the conversion saturates, so far outside positions clamp too
-            const int hi = min(max((int)floor(2.0 * (x[a] / g.w[a])), 0), 2 * g.nc[a] - 1);
+            const int hi = min(max((int)floor(x[a] * g.inv2w[a]), 0), 2 * g.nc[a] - 1);
             c[a] = hi >> 1;
             sb |= (hi & 1) << a;
         }
@@ -68,36 +70,24 @@ __device__ __forceinline__ void bin_body(const BinArgs &r, int64_t blk, int64_t 
     }
 }
 
-// Exclusive scan of count[0..m) into start[0..m] by one whole block (s_part: 32 ints): each
-// thread sums a contiguous chunk (a multiple of 4 cells, read 16 bytes at a time), the chunk
-// sums are scanned across the block through warp shuffles, and each thread writes its chunk's
-// starts.
+// Exclusive scan of count[0..m) into start[0..m] by one whole block (s_part: 32 ints): warp w
+// takes the w-th contiguous chunk (a multiple of 32 cells) and reads it 32 cells at a time,
+// coalesced, twice: once for its total, then, after the warps' totals are scanned through
+// shared memory, for the starts it writes (a shuffle scan per 32 cells with a running carry).
 __device__ __forceinline__ void scan_body(const BinArgs &r, int *s_part) {
     if (r.flag && *r.flag == 0) return;
     const int *__restrict__ count = r.count;
     int *__restrict__ start = r.start;
-    const int m = r.ncell, T = blockDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int chunk = ((m + T - 1) / T + 3) & ~3;
-    const int b0 = min((int)threadIdx.x * chunk, m), b1 = min(b0 + chunk, m);
+    const int m = r.ncell, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int chunk = ((m + nw - 1) / nw + 31) & ~31;
+    const int b0 = min(wid * chunk, m), b1 = min(b0 + chunk, m);
     int sum = 0;
-    for (int k = b0; k < b1; k += 4) {
-        if (k + 4 <= b1) {
-            const int4 v = *reinterpret_cast<const int4 *>(count + k);
-            sum += v.x + v.y + v.z + v.w;
-        } else {
-            for (int kk = k; kk < b1; ++kk) sum += count[kk];
-        }
-    }
-    int incl = sum;
+    for (int k = b0 + lane; k < b1; k += 32) sum += count[k];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_part[wid] = incl;
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) s_part[wid] = sum;
     __syncthreads();
     if (wid == 0) {
-        const int nw = T >> 5;
         int v = lane < nw ? s_part[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -107,12 +97,20 @@ __device__ __forceinline__ void scan_body(const BinArgs &r, int *s_part) {
         if (lane < nw) s_part[lane] = v;   // inclusive warp totals
     }
     __syncthreads();
-    int run = (wid > 0 ? s_part[wid - 1] : 0) + incl - sum;
-    for (int k = b0; k < b1; ++k) {
-        start[k] = run;
-        run += count[k];
+    int carry = wid > 0 ? s_part[wid - 1] : 0;
+    for (int k0 = b0; k0 < b1; k0 += 32) {
+        const int k = k0 + lane;
+        const int c = k < b1 ? count[k] : 0;
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (k < b1) start[k] = carry + incl - c;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (threadIdx.x == T - 1) start[m] = s_part[(T >> 5) - 1];
+    if (threadIdx.x == 0) start[m] = s_part[nw - 1];
     __syncthreads();   // the block's next work item reuses s_part
 }
 
@@ -280,9 +278,10 @@ __device__ __forceinline__ void cellsort_body(const BinArgs &r, int64_t blk, int
 
 __device__ __forceinline__ int wrap_cell(int x, int nc) { return x < 0 ? x + nc : (x >= nc ? x - nc : x); }
 
-// 8-bit hash of an atom index (the top byte of a multiplicative hash), stored beside each list
-// entry so that the reverse-slot search reads one byte per entry
-__device__ __forceinline__ uint32_t index_hash8(int x) { return ((uint32_t)x * 0x9E3779B1u) >> 24; }
+// 8-bit hash of an atom index, stored beside each list entry so that the reverse-slot search
+// reads one byte per entry: the low byte (a row's entries are atoms near each other in the
+// Morton-ordered internal order, so their low bytes seldom coincide)
+__device__ __forceinline__ uint32_t index_hash8(int x) { return (uint32_t)x & 0xFFu; }
 
 constexpr int SORT_MAX = 256;
 constexpr int STAGE_MAX = 1024;   // staged candidates; a larger stencil is walked in global memory
@@ -780,6 +779,7 @@ RebuildPlan rebuild_plan(Sys &s, bool conditional) {
     for (int a = 0; a < 3; ++a) {
         g.nc[a] = s.cells.nc[a];
         g.w[a] = s.box[a] / s.cells.nc[a];
+        g.inv2w[a] = 2.0 / g.w[a];
         g.per[a] = s.per[a];
     }
     const int64_t n = s.n;

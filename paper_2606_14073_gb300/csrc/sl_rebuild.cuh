@@ -13,6 +13,7 @@ constexpr int RB_THREADS = 256;  // threads per block of the binning kernels
 struct GridArgs {
     int nc[3];
     double w[3];
+    double inv2w[3];   // 2 / w: the half-width sub-cell index of x is floor(x * 2/w)
     int per[3];
 };
 

@@ -171,61 +171,78 @@ __device__ __forceinline__ void warp_bitonic64(uint64_t (&k)[E], int lane) {
 
 __device__ __forceinline__ int sub_of(const float4 &pf) { return (__float_as_int(pf.w) >> 1) & 7; }
 
+// One cell of up to 32 E atoms sorted in registers (E per lane), its sub-cell starts recorded.
+template <int E>
+__device__ __forceinline__ void cellsort_regs(const BinArgs &r, int64_t c, int p0, int len, int lane) {
+    // (sub-cell << 61) | (key << 29) | element: distinct, so the order is unique
+    uint64_t v[E];
+    int at[E];
+    float4 pf[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        const int e = q * 32 + lane;
+        v[q] = ~0ull;
+        at[q] = 0;
+        pf[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < len) {
+            at[q] = r.atoms[p0 + e];
+            pf[q] = r.cposf[p0 + e];
+            v[q] = ((uint64_t)sub_of(pf[q]) << 61) | ((uint64_t)r.ckey[p0 + e] << 29) | (uint64_t)e;
+        }
+    }
+    warp_bitonic64<E>(v, lane);
+    int below[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // sorted elements of a sub-cell below k
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        const int e = q * 32 + lane;
+        const int src = (int)(v[q] & 63u), sl = src & 31, sq = src >> 5;
+        int an = 0;
+        float4 fn = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < E; ++u) {   // element src sits in register sq of lane sl
+            const int a = __shfl_sync(0xffffffffu, at[u], sl);
+            float4 f;
+            f.x = __shfl_sync(0xffffffffu, pf[u].x, sl);
+            f.y = __shfl_sync(0xffffffffu, pf[u].y, sl);
+            f.z = __shfl_sync(0xffffffffu, pf[u].z, sl);
+            f.w = __shfl_sync(0xffffffffu, pf[u].w, sl);
+            if (sq == u) {
+                an = a;
+                fn = f;
+            }
+        }
+        const int sub = e < len ? (int)(v[q] >> 61) : 8;
+#pragma unroll
+        for (int k = 1; k < 8; ++k) below[k] += __popc(__ballot_sync(0xffffffffu, sub < k));
+        if (e < len) {
+            r.ckey[p0 + e] = (uint32_t)(v[q] >> 29);
+            r.atoms[p0 + e] = an;
+            r.cposf[p0 + e] = fn;
+        }
+    }
+    if (lane < 8) {
+        int mine = 0;
+#pragma unroll
+        for (int k = 1; k < 8; ++k) mine = lane == k ? below[k] : mine;
+        r.sub[c * 8 + lane] = mine;
+    }
+}
+
 // Each cell's atoms in ascending (sub-cell, key) order (key: species << 30 | caller index),
 // one warp per cell, and the first position of each sub-cell relative to the cell's start:
 // the scatter fills a cell in the order of its atomic increments, and the list build walks
 // the cells' atoms in their stored order, so sorted cells make every list independent of that
-// order and of the internal atom order.  Cells of up to 64 atoms are sorted in registers; a
+// order and of the internal atom order.  Cells of up to 32 or 64 atoms are sorted in registers; a
 // larger one (only in boxes of very few cells) by lane 0 in place.
 __device__ __forceinline__ void cellsort_body(const BinArgs &r, int64_t blk, int64_t nblk) {
     if (r.flag && *r.flag == 0) return;
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int64_t c = blk * wpb + (threadIdx.x >> 5); c < r.ncell; c += nblk * wpb) {
         const int p0 = r.start[c], len = r.start[c + 1] - p0;
-        if (len <= 64) {
-            // (sub-cell << 61) | (key << 29) | element: distinct, so the order is unique
-            uint64_t v[2];
-            int at[2];
-            float4 pf[2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int e = q * 32 + lane;
-                v[q] = ~0ull;
-                at[q] = 0;
-                pf[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (e < len) {
-                    at[q] = r.atoms[p0 + e];
-                    pf[q] = r.cposf[p0 + e];
-                    v[q] = ((uint64_t)sub_of(pf[q]) << 61) | ((uint64_t)r.ckey[p0 + e] << 29) | (uint64_t)e;
-                }
-            }
-            warp_bitonic64<2>(v, lane);
-            int below[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // sorted elements of a sub-cell below k
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int e = q * 32 + lane;
-                const int src = (int)(v[q] & 63u), sl = src & 31, sq = src >> 5;
-                const int a0 = __shfl_sync(0xffffffffu, at[0], sl), a1 = __shfl_sync(0xffffffffu, at[1], sl);
-                float4 f0, f1;
-                f0.x = __shfl_sync(0xffffffffu, pf[0].x, sl); f1.x = __shfl_sync(0xffffffffu, pf[1].x, sl);
-                f0.y = __shfl_sync(0xffffffffu, pf[0].y, sl); f1.y = __shfl_sync(0xffffffffu, pf[1].y, sl);
-                f0.z = __shfl_sync(0xffffffffu, pf[0].z, sl); f1.z = __shfl_sync(0xffffffffu, pf[1].z, sl);
-                f0.w = __shfl_sync(0xffffffffu, pf[0].w, sl); f1.w = __shfl_sync(0xffffffffu, pf[1].w, sl);
-                const int sub = e < len ? (int)(v[q] >> 61) : 8;
-#pragma unroll
-                for (int k = 1; k < 8; ++k) below[k] += __popc(__ballot_sync(0xffffffffu, sub < k));
-                if (e < len) {
-                    r.ckey[p0 + e] = (uint32_t)(v[q] >> 29);
-                    r.atoms[p0 + e] = sq == 0 ? a0 : a1;
-                    r.cposf[p0 + e] = sq == 0 ? f0 : f1;
-                }
-            }
-            if (lane < 8) {
-                int mine = 0;
-#pragma unroll
-                for (int k = 1; k < 8; ++k) mine = lane == k ? below[k] : mine;
-                r.sub[c * 8 + lane] = mine;
-            }
+        if (len <= 32) {
+            cellsort_regs<1>(r, c, p0, len, lane);
+        } else if (len <= 64) {
+            cellsort_regs<2>(r, c, p0, len, lane);
         } else if (lane == 0) {
             auto before = [&](int s1, uint32_t k1, int s2, uint32_t k2) { return s1 < s2 || (s1 == s2 && k1 < k2); };
             for (int x = 1; x < len; ++x) {

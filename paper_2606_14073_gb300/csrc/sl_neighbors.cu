@@ -801,7 +801,7 @@ RebuildPlan rebuild_plan(Sys &s, bool conditional) {
     }
     const int64_t n = s.n;
     BinArgs &r = pl.bin;
-    r.pos = s.pos; r.posf = s.posf; r.species = s.species; r.orig = s.orig; r.n = n; r.g = g;
+    r.pos = s.pos; r.species = s.species; r.orig = s.orig; r.n = n; r.g = g;
     r.ncell = s.cells.ncell; r.count = s.cells.count; r.start = s.cells.start; r.fill = s.cells.fill;
     r.atoms = s.cells.atoms; r.of = s.cells.of; r.cposf = s.cells.posf; r.ckey = s.cells.key;
     r.sub = s.cells.sub;
@@ -810,7 +810,7 @@ RebuildPlan rebuild_plan(Sys &s, bool conditional) {
     la.pos = s.pos;
     la.cell_start = s.cells.start; la.cell_atoms = s.cells.atoms; la.cell_sub = s.cells.sub;
     la.cposf = s.cells.posf;
-    la.n = n; la.cap = s.cap; la.cap_ang = s.cap_ang; la.capr = nbr_stride(s.cap);
+    la.cap = s.cap; la.cap_ang = s.cap_ang; la.capr = nbr_stride(s.cap);
     la.cut_r2 = s.cut_r2; la.cut_a2 = s.cut_a2;
     // Band of the FP32 pre-test.  Each FP32 separation component is (u_j + o) - u_i with
     // |u| <= 2w (positions relative to their cells' corners, rounded once from FP64) and o a

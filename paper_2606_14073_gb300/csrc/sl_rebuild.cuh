@@ -20,7 +20,6 @@ struct GridArgs {
 // Every rebuild kernel's arguments for one system (binning, scan, scatter, finish).
 struct BinArgs {
     const double4 *pos;
-    const float4 *posf;
     const int32_t *species, *orig;
     int64_t n;
     GridArgs g;
@@ -39,7 +38,6 @@ struct ListArgs {
     const double4 *pos;
     const int *cell_start, *cell_atoms, *cell_sub;
     const float4 *cposf;      // cell-ordered FP32 positions relative to each cell's corner, species and sub-cell bits in w
-    int64_t n;
     int cap, cap_ang, capr;
     double cut_r2, cut_a2;
     float cut_r2f_lo, cut_r2f_hi, cut_a2f_lo, cut_a2f_hi;   // FP32 pre-test band

@@ -614,7 +614,21 @@ __device__ __forceinline__ void bwd_harm(const R *__restrict__ bb, R ux, R uy, R
     if constexpr (LM + 1 < NLM) bwd_harm<R, LM + 1>(bb, ux, uy, uz, ir, s, g, dg, accu, avx, avy, avz, cj);
 }
 
-template <typename R, bool ANG>
+// one pair record: FP32 as a single 256-bit store (the record is one 32-byte sector), FP64 as
+// two 32-byte stores
+__device__ __forceinline__ void store_rec(PairRec<float> *p, const float4 &a, const float4 &b) {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a.x), "f"(a.y), "f"(a.z),
+                 "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
+}
+__device__ __forceinline__ void store_rec(PairRec<double> *p, const double4 &a, const double4 &b) {
+    stg(&p->a, a);
+    stg(&p->b, b);
+}
+
+// VIR: the evaluation accumulates the virial parts (a compile-time switch, so the step's
+// evaluation keeps no virial accumulators live across its row loops)
+template <typename R, bool ANG, bool VIR>
 __device__ __forceinline__ void bwd_pair(const NepDev<R> &P, const Eval2Args<R> &a, int ti, int tj, const v4<R> &pi,
                                          const v4<R> &si, const v4<R> &pj, const v4<R> &sj, int j, int t,
                                          const R *sm, BwdAcc2<R> &acc) {
@@ -688,7 +702,7 @@ __device__ __forceinline__ void bwd_pair(const NepDev<R> &P, const Eval2Args<R> 
     const R Gy = cg * si.y + h2 * (uz * si.x - ux * si.z) + h3 * siu * uy;
     const R Gz = cg * si.z + h2 * (ux * si.y - uy * si.x) + h3 * siu * uz;
     acc.fx += Dx; acc.fy += Dy; acc.fz += Dz;
-    if (a.want_virial) {
+    if constexpr (VIR) {
         acc.w[0] -= dx * Dx; acc.w[1] -= dx * Dy; acc.w[2] -= dx * Dz;
         acc.w[3] -= dy * Dx; acc.w[4] -= dy * Dy; acc.w[5] -= dy * Dz;
         acc.w[6] -= dz * Dx; acc.w[7] -= dz * Dy; acc.w[8] -= dz * Dz;
@@ -697,14 +711,13 @@ __device__ __forceinline__ void bwd_pair(const NepDev<R> &P, const Eval2Args<R> 
     v4<R> ra, rb;
     ra.x = Dx; ra.y = Dy; ra.z = Dz; ra.w = Gx;
     rb.x = Gy; rb.y = Gz; rb.z = R(0); rb.w = R(0);
-    stg(&rec->a, ra);
-    stg(&rec->b, rb);
+    store_rec(rec, ra, rb);
 }
 
 // rows lo, lo+4, ... of one range for lane ql.  Two-level prefetch: the list entry of the
 // row two steps ahead and the coordinates of the next row are in flight while a pair is
 // computed, so no load waits on a load issued in the same step.
-template <typename R, bool ANG>
+template <typename R, bool ANG, bool VIR>
 __device__ __forceinline__ void bwd_rows(const NepDev<R> &P, const Eval2Args<R> &a, int64_t i, int ti, int lo, int hi,
                                          int split, const v4<R> &pi, const v4<R> &si, const R *sm,
                                          BwdAcc2<R> &acc) {
@@ -744,11 +757,11 @@ __device__ __forceinline__ void bwd_rows(const NepDev<R> &P, const Eval2Args<R> 
             j3 = ro(a.clj + (int64_t)(row + 12) * N + i);
             t3 = ro(a.cls + (int64_t)(row + 12) * N + i) >> 8;
         }
-        bwd_pair<R, ANG>(P, a, ti, row < split ? 0 : 1, pi, si, pj, sj, j, t, sm, acc);
+        bwd_pair<R, ANG, VIR>(P, a, ti, row < split ? 0 : 1, pi, si, pj, sj, j, t, sm, acc);
     }
 }
 
-template <typename R>
+template <typename R, bool VIR>
 __device__ __forceinline__ void bwd_body(const NepDev<R> &P, const Eval2Args<R> &args, int64_t blk,
                                          unsigned char *smem_raw) {
     // the arguments as values: read once from the block's copy, so nothing in the loops below
@@ -803,8 +816,8 @@ __device__ __forceinline__ void bwd_body(const NepDev<R> &P, const Eval2Args<R> 
         else bwd_coeffs<R, 1>(P, FR, FX, ql, sm + BW_C);
         __syncwarp(0xfu << (quad * 4));
         const int ca = a.cap_ang;
-        bwd_rows<R, true>(P, a, i, ti, ql, c.y, c.x, pi, si, sm, acc);
-        bwd_rows<R, false>(P, a, i, ti, ca + ql, ca + c.w, ca + c.z, pi, si, sm, acc);
+        bwd_rows<R, true, VIR>(P, a, i, ti, ql, c.y, c.x, pi, si, sm, acc);
+        bwd_rows<R, false, VIR>(P, a, i, ti, ca + ql, ca + c.w, ca + c.z, pi, si, sm, acc);
     }
     // per-atom sums over the quad
 #pragma unroll
@@ -816,7 +829,7 @@ __device__ __forceinline__ void bwd_body(const NepDev<R> &P, const Eval2Args<R> 
         acc.hy += __shfl_xor_sync(0xffffffffu, acc.hy, o);
         acc.hz += __shfl_xor_sync(0xffffffffu, acc.hz, o);
     }
-    if (a.want_virial) {
+    if constexpr (VIR) {
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
             acc.w[t] += __shfl_xor_sync(0xffffffffu, acc.w[t], 1);
@@ -829,7 +842,7 @@ __device__ __forceinline__ void bwd_body(const NepDev<R> &P, const Eval2Args<R> 
         g4.x = acc.hx; g4.y = acc.hy; g4.z = acc.hz; g4.w = R(0);
         stg(a.fown + i, f4);
         stg(a.gii + i, g4);
-        if (a.want_virial) {
+        if constexpr (VIR) {
 #pragma unroll
             for (int t = 0; t < 9; ++t) stg(a.wpart + (int64_t)t * N + i, acc.w[t]);
         }
@@ -856,12 +869,13 @@ __global__ void __launch_bounds__(128, MINB) k_ang_fwd(const __grid_constant__ N
     one_work(tab, sm, solo,
              [&](const Eval2Args<R> &a, int64_t blk, int64_t) { ang_fwd_body(P, a, blk, smem_raw); });
 }
-template <typename R, int MINB = sizeof(R) == 4 ? 4 : 1>
+template <typename R, int MINB = sizeof(R) == 4 ? 4 : 1, bool VIR = false>
 __global__ void __launch_bounds__(128, MINB) k_bwd(const __grid_constant__ NepDev<R> P,
                                                    const Eval2Args<R> *__restrict__ tab, SlotMap sm,
                                                    const __grid_constant__ Eval2Args<R> solo) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    one_work(tab, sm, solo, [&](const Eval2Args<R> &a, int64_t blk, int64_t) { bwd_body(P, a, blk, smem_raw); });
+    one_work(tab, sm, solo,
+             [&](const Eval2Args<R> &a, int64_t blk, int64_t) { bwd_body<R, VIR>(P, a, blk, smem_raw); });
 }
 
 // ------------------------------------------------------------------ launch
@@ -911,7 +925,11 @@ void eval2_init() {
     cudaFuncSetAttribute(k_ang_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<double>());
     cudaFuncSetAttribute(k_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<float>());
     cudaFuncSetAttribute(k_bwd<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<float>());
+    cudaFuncSetAttribute(k_bwd<float, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<float>());
+    cudaFuncSetAttribute(k_bwd<float, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<float>());
     cudaFuncSetAttribute(k_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwdf_smem<double>());
+    cudaFuncSetAttribute(k_bwd<double, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwdf_smem<double>());
     if (dev < 64) done |= 1ull << dev;
 }
 
@@ -970,12 +988,17 @@ void launch_eval_t(const FusedTables &t, const NepDev<R> &P, const Launch *L, cu
     if constexpr (sizeof(R) == 4) launch_net_t_tc(t, P, L[2], st);
     else launch_net_t_fp64(t, P, L[2], st);
     if (ev) cudaEventRecord(ev[4], st);
+    // the virial parts: only a system's own full evaluation asks for them (a batch's slots are
+    // set up for the step's evaluation, which has none)
+    const bool vir = L[3].solo && so.want_virial;
     variant = false;
     if constexpr (sizeof(R) == 4) {
         variant = L[3].minb == 3;
-        if (variant) k_bwd<R, 3><<<L[3].grid, qw, bwdf_smem<R>(qw), st>>>(P, tab, s3, so);
+        if (variant && vir) k_bwd<R, 3, true><<<L[3].grid, qw, bwdf_smem<R>(qw), st>>>(P, tab, s3, so);
+        else if (variant) k_bwd<R, 3><<<L[3].grid, qw, bwdf_smem<R>(qw), st>>>(P, tab, s3, so);
     }
-    if (!variant) k_bwd<R><<<L[3].grid, qw, bwdf_smem<R>(qw), st>>>(P, tab, s3, so);
+    if (!variant && vir) k_bwd<R, sizeof(R) == 4 ? 4 : 1, true><<<L[3].grid, qw, bwdf_smem<R>(qw), st>>>(P, tab, s3, so);
+    else if (!variant) k_bwd<R><<<L[3].grid, qw, bwdf_smem<R>(qw), st>>>(P, tab, s3, so);
     if (ev) cudaEventRecord(ev[5], st);
 }
 template void launch_eval_t<float>(const FusedTables &, const NepDev<float> &, const Launch *, cudaStream_t,

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "sl_batch.h"
@@ -65,7 +66,7 @@ void FusedBatch::enqueue(cudaStream_t st) const {
         if (c >= 0) {
             x.item_slot = items + item_off[c];
             x.start = starts + (size_t)c * t.cap;
-            x.grid = (unsigned)item_cap[c];
+            x.grid = (unsigned)std::max<int64_t>(grid_items[c], 1);
         } else {
             x.grid = t.grid[k];
         }
@@ -115,6 +116,11 @@ FusedBatch::~FusedBatch() { release(); }
 void FusedBatch::release_graphs() {
     if (graph_g) cudaGraphExecDestroy(graph_g);
     if (graph_1) cudaGraphExecDestroy(graph_1);
+    for (cudaGraph_t &x : tmpl) {
+        if (x) cudaGraphDestroy(x);
+        x = nullptr;
+    }
+    item_nodes.clear();
     graph_g = graph_1 = nullptr;
     g = 0;
 }
@@ -142,6 +148,8 @@ void FusedBatch::release() {
     version.clear();
     stale.clear();
     have_model = false;
+    follow = true;
+    for (int64_t &x : grid_items) x = 0;
 }
 
 bool FusedBatch::setup(int prec, int cap, int device) {
@@ -189,6 +197,57 @@ bool FusedBatch::same_model(const Sys &s) const {
     return have_model && std::memcmp(&s.pd, &pd, sizeof pd) == 0 && std::memcmp(&s.pf, &pf, sizeof pf) == 0;
 }
 
+// The one-item-per-block class of a kernel of the step by its name (mangled: the identifier
+// after its length; demangled: the identifier before its template or parameter list): the
+// halves, the radial, angular and backward kernels and the FP64 network (the tensor-core
+// network, k_mlp_tc, is persistent); -1 for the others.
+static int item_kernel_class(const char *name) {
+    struct { const char *id; int cls; } const k[] = {
+        {"k_first_half", IC_HALF}, {"k_second_half", IC_HALF}, {"k_crad", IC_ATOM},
+        {"k_mlp", IC_ATOM}, {"k_ang_fwd", IC_QUAD}, {"k_bwd", IC_QUAD}};
+    for (const auto &x : k) {
+        const std::string id(x.id);
+        const std::string forms[3] = {std::to_string(id.size()) + id + "I", id + "<", id + "("};
+        for (const std::string &f : forms)
+            if (std::strstr(name, f.c_str())) return x.cls;
+    }
+    return -1;
+}
+
+bool FusedBatch::find_item_nodes(cudaGraph_t graph, cudaGraphExec_t exec, int steps) {
+    size_t cnt = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &cnt) != cudaSuccess) return false;
+    std::vector<cudaGraphNode_t> nodes(cnt);
+    if (cnt && cudaGraphGetNodes(graph, nodes.data(), &cnt) != cudaSuccess) return false;
+    int64_t found = 0;
+    for (cudaGraphNode_t node : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(node, &ty) != cudaSuccess) return false;
+        if (ty != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams p;
+        if (cudaGraphKernelNodeGetParams(node, &p) != cudaSuccess) return false;
+        const char *name = nullptr;
+        if (cudaFuncGetName(&name, p.func) != cudaSuccess || !name) return false;
+        const int c = item_kernel_class(name);
+        if (c < 0) continue;
+        if ((int64_t)p.gridDim.x != std::max<int64_t>(grid_items[c], 1)) return false;
+        item_nodes.push_back(ItemNode{exec, node, c});
+        ++found;
+    }
+    // per step: the two halves, the radial kernel (and the FP64 network), angular, backward
+    return found == (int64_t)steps * (t.prec == 0 ? 6 : 5);
+}
+
+bool FusedBatch::resize_item_nodes() {
+    for (const ItemNode &x : item_nodes) {
+        cudaKernelNodeParams p;
+        if (cudaGraphKernelNodeGetParams(x.node, &p) != cudaSuccess) return false;
+        p.gridDim.x = (unsigned)std::max<int64_t>(grid_items[x.cls], 1);
+        if (cudaGraphExecKernelNodeSetParams(x.exec, x.node, &p) != cudaSuccess) return false;
+    }
+    return true;
+}
+
 bool FusedBatch::graphs(int steps, const Sys &m, cudaStream_t st) {
     if (graph_g && g == steps && same_model(m)) return true;
     release_graphs();
@@ -201,13 +260,20 @@ bool FusedBatch::graphs(int steps, const Sys &m, cudaStream_t st) {
         if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
         for (int k = 0; k < n; ++k) enqueue(st);
         if (cudaStreamEndCapture(st, &graph) != cudaSuccess) return false;
+        tmpl[which] = graph;   // kept: its kernel nodes name the ones a new layout resizes
         cudaGraphExec_t &exec = which == 0 ? graph_g : graph_1;
         const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
             exec = nullptr;
             release_graphs();
             return false;
+        }
+        if (follow && !find_item_nodes(graph, exec, n)) {
+            // the graphs' grids cannot follow the layout: capacity grids from now on
+            follow = false;
+            for (int c = 0; c < IC_N; ++c) grid_items[c] = item_cap[c];
+            release_graphs();
+            return graphs(steps, m, st);
         }
     }
     g = steps;
@@ -293,11 +359,15 @@ cudaError_t FusedBatch::upload(const int64_t *left, cudaStream_t st) {
                 for (int64_t b = 0; b < nb; ++b) it[o + b] = r;
                 o += nb;
             }
+            grid_items[c] = follow ? std::max<int64_t>(o, 1) : item_cap[c];
             for (; o < item_cap[c]; ++o) it[o] = -1;
         }
         e = cudaMemcpyAsync(starts, h_starts, item_bytes, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return e;
         layout_dirty = false;
+        // the captured graphs launch the new layout's blocks (the resize affects only their
+        // later launches); where that fails they are captured again at the next step
+        if (graph_g && !resize_item_nodes()) release_graphs();
     }
     std::memcpy(img + t.o_left, left, sizeof(int64_t) * t.cap);
     if (dirty) e = cudaMemcpyAsync(t.dev, img, t.upload_bytes, cudaMemcpyHostToDevice, st);

@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cstring>
+#include <vector>
 
 #include "sl_internal.h"
 #include "sl_fused.cuh"
@@ -146,10 +147,12 @@ public:
     int device() const { return dev_; }
     // the slots' step budgets (and the tables, where an entry changed) to the device, on st
     cudaError_t upload(const int64_t *left, cudaStream_t st);
-    // grids for up to `atoms` atoms over all slots: the kernels that take one work item per
-    // block get one block per atoms-per-block of the capacity plus one partial block per
-    // slot.  The capacity only grows (to a power of two); growing drops the graphs.  False
-    // when the layout cannot be allocated.
+    // block -> slot layouts for up to `atoms` atoms over all slots: one block per
+    // atoms-per-block of the capacity plus one partial block per slot for each kernel that
+    // takes one work item per block.  The capacity only grows (to a power of two); growing
+    // drops the graphs.  Those kernels' grids cover the occupied slots' blocks only (upload
+    // resizes them in the captured graphs), so a capacity above the resident atoms launches
+    // no idle blocks.  False when the layout cannot be allocated.
     bool reserve(int64_t atoms);
     int64_t atom_capacity() const { return atom_cap; }
     // one step of every slot with a budget left, queued on st
@@ -164,7 +167,24 @@ private:
     void release_graphs();
     void release_items();
     void release();
+    // the kernel nodes of the one-item-per-block kernels in the graph just captured (with its
+    // executable graph); false when they cannot all be told apart
+    bool find_item_nodes(cudaGraph_t graph, cudaGraphExec_t exec, int steps);
+    // those nodes' grids set to grid_items in the executable graphs; false on failure
+    bool resize_item_nodes();
     int dev_ = -1;
+    // grid of each one-item-per-block class in the launches and captured graphs: the occupied
+    // slots' blocks of the current layout (follow), else the capacity's blocks (when the
+    // captured nodes could not be found)
+    int64_t grid_items[IC_N] = {};
+    bool follow = true;
+    struct ItemNode {
+        cudaGraphExec_t exec;
+        cudaGraphNode_t node;   // in tmpl[...], which stays alive with the executable graph
+        int cls;
+    };
+    std::vector<ItemNode> item_nodes;
+    cudaGraph_t tmpl[2] = {};
     int64_t atom_cap = 0;
     // block -> slot layout per atoms-per-block class (device; pinned host copy), and each
     // slot's first block per class

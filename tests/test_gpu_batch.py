@@ -87,6 +87,32 @@ def test_slots_admit_and_retire_without_new_capture(params):
         s.destroy()
 
 
+@pytest.mark.parametrize("prec", [S.SL_PREC_FP64, S.SL_PREC_MIXED])
+def test_launch_grids_follow_the_occupied_slots(params, prec):
+    """The one-item-per-block kernels launch only the occupied slots' blocks: in a batch
+    reserved for far more atoms than it holds, whose slots fill and empty between calls (the
+    captured graphs' grids grow and shrink without a new capture), every replica follows its
+    trajectory alone."""
+    wls = [W.fege_cube(c, seed=380 + i, replica=50 + i) for i, c in enumerate((4, 8, 5))]
+    a, b_, c = (_system(params, w, prec) for w in wls)
+    batch = S.Batch([a, None, None])
+    batch.reserve(1 << 20)
+    batch.step([6, 0, 0], 1.0, [200.0, 0.0, 0.0], (0, 0, 0.1))
+    batch.set(1, b_)                    # eight times a's atoms: the grids grow
+    batch.step([5, 7, 0], 1.0, [200.0, 250.0, 0.0], (0, 0, 0.1))
+    batch.set(0, None)                  # a leaves, c joins: they shrink
+    batch.set(2, c)
+    batch.step([0, 4, 9], 1.0, [0.0, 250.0, 150.0], (0, 0, 0.1))
+    st = batch.stats()
+    assert st["fused_captures"] == 1 and st["fused_calls"] == 3 and st["atom_capacity"] == 1 << 20
+    _same(a.get_state(), _alone(params, wls[0], prec, [(6, 200.0, 0.1), (5, 200.0, 0.1)]))
+    _same(b_.get_state(), _alone(params, wls[1], prec, [(7, 250.0, 0.1), (4, 250.0, 0.1)]))
+    _same(c.get_state(), _alone(params, wls[2], prec, [(9, 150.0, 0.1)]))
+    batch.destroy()
+    for s in (a, b_, c):
+        s.destroy()
+
+
 def test_slot_reused_by_a_system_created_after_a_destroy(params):
     """A replica retired and destroyed, then a new one admitted into the same slot: the new
     system (which may sit at the destroyed one's address) gets its own table entries."""

@@ -304,8 +304,8 @@ const char *sl_last_error(void);
  * start of every step builds the step's work maps from per-slot budgets of steps left, so
  * replicas with different step counts share the launches until each budget is spent, and the
  * two captured graphs (steps_per_graph steps, one step) survive admissions and retirements:
- * sl_batch_set rewrites a slot's table entry, not the graphs (up to the atom capacity, see
- * sl_batch_reserve).  Otherwise the replicas run on their own streams (one fork/join graph
+ * sl_batch_set rewrites a slot's table entry and the grids of the graphs' one-item-per-block
+ * kernels, not the graphs themselves (up to the atom capacity, see sl_batch_reserve).  Otherwise the replicas run on their own streams (one fork/join graph
  * when every occupied slot takes part).
  *
  * A system must leave every batch (sl_batch_set(b, slot, NULL)) before it is destroyed.  All
@@ -340,10 +340,11 @@ int sl_batch_graph_launches(const sl_batch *b, int64_t *launches);
  * atom capacity the fused launches are sized for. */
 int sl_batch_stats(const sl_batch *b, int64_t *stats);
 /* Size the fused launches for up to `atoms` atoms over all slots (default: 65,536, raised to
- * the next power of two whenever the slots' atoms exceed it).  The kernels of the step that
- * take one work item per block launch that many blocks whatever the slots hold (blocks past
- * the current work return at once), so the captured graphs survive every admission up to
- * the capacity; growing it captures them again.  SL_EINVAL for a negative count. */
+ * the next power of two whenever the slots' atoms exceed it).  The captured graphs survive
+ * every admission and retirement up to the capacity; growing it captures them again.  The
+ * kernels of the step that take one work item per block launch only the occupied slots'
+ * blocks: an admission or retirement resizes their grids in the captured graphs, so a
+ * capacity above the resident atoms costs no idle blocks.  SL_EINVAL for a negative count. */
 int sl_batch_reserve(sl_batch *b, int64_t atoms);
 void sl_batch_destroy(sl_batch *b);
 

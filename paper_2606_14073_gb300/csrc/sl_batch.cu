@@ -269,7 +269,9 @@ bool FusedBatch::graphs(int steps, const Sys &m, cudaStream_t st) {
             return false;
         }
         if (follow && !find_item_nodes(graph, exec, n)) {
-            // the graphs' grids cannot follow the layout: capacity grids from now on
+            // the graphs' grids cannot follow the layout: capacity grids from now on (the
+            // failed query's error is not left for the next launch check)
+            cudaGetLastError();
             follow = false;
             for (int c = 0; c < IC_N; ++c) grid_items[c] = item_cap[c];
             release_graphs();
@@ -367,7 +369,10 @@ cudaError_t FusedBatch::upload(const int64_t *left, cudaStream_t st) {
         layout_dirty = false;
         // the captured graphs launch the new layout's blocks (the resize affects only their
         // later launches); where that fails they are captured again at the next step
-        if (graph_g && !resize_item_nodes()) release_graphs();
+        if (graph_g && !resize_item_nodes()) {
+            cudaGetLastError();
+            release_graphs();
+        }
     }
     std::memcpy(img + t.o_left, left, sizeof(int64_t) * t.cap);
     if (dirty) e = cudaMemcpyAsync(t.dev, img, t.upload_bytes, cudaMemcpyHostToDevice, st);

@@ -146,7 +146,7 @@ void free_sys(sl::Sys &s) {
                     s.wpart, s.Fo, s.Ho,
                     s.status, s.rebuild, s.d_step, s.d_par, s.red, s.snap, s.d_builds,
                     s.posmid, s.posmidf, s.mids, s.midsf, s.mx, s.mg, s.aax, s.aag, s.aapart, s.md, s.Bat,
-                    s.tex_acc, s.tex_m, s.tex_part, s.colour};
+                    s.tex_acc, s.tex_m, s.tex_part, s.colour, s.mlp_img};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     sl::solo_free(s);
@@ -572,6 +572,8 @@ int sl_create_system(const double *positions, const double *spins, const double 
         return bail(rc);
     if (s.prec == SL_PREC_MIXED && n > 0 && sl::make_q_tensor_map(s))
         return bail(fail(SL_ECUDA, "the TMA map of the descriptor array could not be encoded"));
+    if (s.prec == SL_PREC_MIXED && n > 0 && sl::make_mlp_image(s))
+        return bail(fail(SL_ENOMEM, "the network weights' operand images could not be made"));
     if (s.mid_iters > 0) {
         const size_t ring = (size_t)(s.aa_depth > 0 ? s.aa_depth + 1 : 0) * N;
         if ((rc = dalloc(&s.posmid, N)) || (rc = dalloc(&s.posmidf, N)) || (rc = dalloc(&s.mids, N)) ||

@@ -29,6 +29,7 @@ struct MlpArgs {
     float *fp, *ei;
     int *status;
     const int *skip;     // non-null: the slot's tiles are passed over while *skip
+    const void *wimg;    // the weights' FP16 hi/lo operand images (20,480 bytes, 16-byte aligned)
 };
 static_assert(alignof(CUtensorMap) >= 64, "tensor maps are 64-byte aligned");
 

@@ -122,6 +122,7 @@ struct Sys {
     void *q = nullptr;         // [DIM][qs]: descriptor v of atom i at v * qs + i
     int64_t qs = 0;            // row stride of q: n rounded up to a multiple of 4 (16-byte rows)
     CUtensorMap qmap;          // TMA map of q (mixed precision): [DIM] rows x n atoms, 128 x 66 boxes
+    void *mlp_img = nullptr;   // the network weights as the tensor-core kernel's FP16 hi/lo operand images
     void *bsum = nullptr;      // [n][NLM][BREC] angular-sum records
     void *fp = nullptr;        // [DIM][n]
     void *ei = nullptr;        // [n]
@@ -226,6 +227,7 @@ void launch_eval(Sys &s, bool want_virial, cudaEvent_t *ev = nullptr);
 void eval2_init();   // dynamic shared-memory limits of the evaluation kernels (once per device)
 int default_quad_block(int prec);   // threads per block of the quad kernels by default
 int make_q_tensor_map(Sys &s);                   // sl_mlp_tc.cu: the TMA map of s.q; 0 on success
+int make_mlp_image(Sys &s);                      // sl_mlp_tc.cu: s.mlp_img from s.pf; 0 on success
 // first half, rebuild group (7), compaction with radial forward, angular forward, network, backward,
 // second half
 constexpr int KERNELS_PER_STEP = 1 + 8 + 2 + 1 + 1 + 1;

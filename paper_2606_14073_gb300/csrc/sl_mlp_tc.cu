@@ -49,6 +49,11 @@ constexpr uint32_t OFF_B1H = OFF_A1L + SZ_A1, OFF_B1L = OFF_B1H + SZ_B1;
 constexpr uint32_t OFF_A2H = OFF_A1H, OFF_A2L = OFF_A2H + SZ_A2;
 static_assert(2 * SZ_A2 <= SZ_A1, "A2 must fit in the A1 hi region");
 constexpr uint32_t OFF_B2H = OFF_B1L + SZ_B1, OFF_B2L = OFF_B2H + SZ_B2;
+// the four weight operands are one contiguous region, copied from a global image made once
+constexpr uint32_t SZ_W = 2 * SZ_B1 + 2 * SZ_B2;         // 20480
+static_assert(OFF_B1L == OFF_B1H + SZ_B1 && OFF_B2H == OFF_B1L + SZ_B1 && OFF_B2L == OFF_B2H + SZ_B2 &&
+                  OFF_B1H % 16 == 0,
+              "weight operands contiguous and 16-byte aligned");
 constexpr uint32_t OFF_BAR = OFF_B2L + SZ_B2;            // 8-byte mbarrier: MMA completion
 constexpr uint32_t OFF_BARQ = OFF_BAR + 8;                // 8-byte mbarrier: descriptor tile arrival
 constexpr uint32_t OFF_TMEM = OFF_BARQ + 8;               // tensor-memory base address
@@ -174,37 +179,52 @@ struct MlpTile {
     bool gmem_map;   // the map lives in global memory (acquired before use)
 };
 
-// Body of the network kernel over the tiles src(0 .. total-1), each CTA taking tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...
-template <typename Src>
-__device__ __forceinline__ void mlp_tc_body(const NepDev<float> &P, int64_t ntiles, Src src) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
-    const uint32_t bar = sbase + OFF_BAR, barq = sbase + OFF_BARQ;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + OFF_TMEM);
-
-    // weights, once per CTA: B1[h][v] = W0[h][v], B2[v][h] = W0[h][v]; zero padding
-    for (int c = tid; c < N1 * (K1 / 8); c += blockDim.x) {      // B1: 32 rows x 10 chunks
+// The weights' operand images: B1[h][v] = W0[h][v], B2[v][h] = W0[h][v] (zero padding), each
+// FP32 value split into FP16 hi and lo, in the canonical layout at the byte offsets the tile
+// kernel's shared memory uses (relative to OFF_B1H).  `dst` is shared or global memory.
+__device__ __forceinline__ void weight_images(const NepDev<float> &P, unsigned char *dst, int tid, int nthreads) {
+    for (int c = tid; c < N1 * (K1 / 8); c += nthreads) {      // B1: 32 rows x 10 chunks
         const int h = c / (K1 / 8), k0 = (c % (K1 / 8)) * 8;
         float x[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) x[t] = (h < NH && k0 + t < DIM) ? P.w0[h][k0 + t] : 0.f;
         uint4 hi, lo;
         split8(x, hi, lo);
-        *reinterpret_cast<uint4 *>(smem + OFF_B1H + cm_off(h, k0, K1)) = hi;
-        *reinterpret_cast<uint4 *>(smem + OFF_B1L + cm_off(h, k0, K1)) = lo;
+        *reinterpret_cast<uint4 *>(dst + (OFF_B1H - OFF_B1H) + cm_off(h, k0, K1)) = hi;
+        *reinterpret_cast<uint4 *>(dst + (OFF_B1L - OFF_B1H) + cm_off(h, k0, K1)) = lo;
     }
-    for (int c = tid; c < N2 * (K2 / 8); c += blockDim.x) {      // B2: 80 rows x 4 chunks
+    for (int c = tid; c < N2 * (K2 / 8); c += nthreads) {      // B2: 80 rows x 4 chunks
         const int v = c / (K2 / 8), k0 = (c % (K2 / 8)) * 8;
         float x[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) x[t] = (v < DIM && k0 + t < NH) ? P.w0[k0 + t][v] : 0.f;
         uint4 hi, lo;
         split8(x, hi, lo);
-        *reinterpret_cast<uint4 *>(smem + OFF_B2H + cm_off(v, k0, K2)) = hi;
-        *reinterpret_cast<uint4 *>(smem + OFF_B2L + cm_off(v, k0, K2)) = lo;
+        *reinterpret_cast<uint4 *>(dst + (OFF_B2H - OFF_B1H) + cm_off(v, k0, K2)) = hi;
+        *reinterpret_cast<uint4 *>(dst + (OFF_B2L - OFF_B1H) + cm_off(v, k0, K2)) = lo;
     }
+}
+
+// the images of one model, made once per system
+__global__ void __launch_bounds__(128) k_weight_images(const __grid_constant__ NepDev<float> P, unsigned char *img) {
+    weight_images(P, img, threadIdx.x, blockDim.x);
+}
+
+// Body of the network kernel over the tiles src(0 .. total-1), each CTA taking tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...; wimg: the weights' operand images (global)
+template <typename Src>
+__device__ __forceinline__ void mlp_tc_body(const NepDev<float> &P, int64_t ntiles, const uint4 *__restrict__ wimg,
+                                            Src src) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t bar = sbase + OFF_BAR, barq = sbase + OFF_BARQ;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + OFF_TMEM);
+
+    // weights, once per CTA: a coalesced copy of the images (the same bytes the split of P.w0
+    // gives, made once per system by k_weight_images)
+    for (int k = tid; k < (int)(SZ_W / 16); k += blockDim.x)
+        reinterpret_cast<uint4 *>(smem + OFF_B1H)[k] = __ldg(wimg + k);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barq) : "memory");
@@ -391,7 +411,11 @@ __global__ void __launch_bounds__(128, 2) k_mlp_tc(const __grid_constant__ NepDe
     // the skip flag (the midpoint iteration's own launches only): uniform for the whole CTA and
     // before any shared-memory or TMEM use
     if (!tab && solo.skip && *solo.skip) return;
-    mlp_tc_body(P, total, [&](int64_t g) {
+    // a CTA without a tile returns before any shared-memory or TMEM use (uniform)
+    if ((int64_t)blockIdx.x >= total) return;
+    // the slots taking part share the model: the weight images of the slot of this CTA's first tile
+    const void *wimg = tab ? tab[work_replica(m, blockIdx.x)].wimg : solo.wimg;
+    mlp_tc_body(P, total, reinterpret_cast<const uint4 *>(wimg), [&](int64_t g) {
         const int r = work_replica(m, g);
         const MlpArgs &a = tab ? tab[r] : solo;
         MlpTile t;
@@ -451,6 +475,18 @@ int make_q_tensor_map(Sys &s) {
                                                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                                                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+// The network weights as the tensor-core kernel's operand images, made on the system's
+// stream (ordered before its first evaluation) from its FP32 model parameters.
+int make_mlp_image(Sys &s) {
+    if (s.prec == 0 || s.n == 0) return 0;
+    if (!s.mlp_img && cudaMalloc(&s.mlp_img, tc::SZ_W) != cudaSuccess) {
+        s.mlp_img = nullptr;
+        return -1;
+    }
+    tc::k_weight_images<<<1, 128, 0, s.stream>>>(s.pf, static_cast<unsigned char *>(s.mlp_img));
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // ---- argument tables (sl_batch.h): persistent CTAs over the slots' tiles

@@ -237,7 +237,7 @@ void fused_put_net(Sys &s, int r, int kind, const FusedTables &t, unsigned char 
     } else {
         MlpArgs a;
         a.qmap = s.qmap; a.n = s.n; a.fp = (float *)s.fp; a.ei = (float *)s.ei; a.status = s.status;
-        a.skip = skip;
+        a.skip = skip; a.wimg = s.mlp_img;
         reinterpret_cast<MlpArgs *>(img + t.o_net)[r] = a;
     }
     blocks[FK_NET] = (s.n + 127) / 128;   // atoms of 128-thread blocks, or 128-atom tensor-core tiles
